@@ -1,0 +1,703 @@
+/*
+ * lpp_oracle.c -- plain, slow, single-threaded CPU presolver (the test oracle).
+ *
+ * TEST INFRASTRUCTURE ONLY: used by tests/, the smoke check and the CPU
+ * baseline leg of bench.py; never by the library path.  Shares no code with
+ * the CUDA library.  Compile with -ffp-contract=off so every product and
+ * difference below is rounded on its own (no fused multiply-add).
+ *
+ * The loop follows Cederberg & Boyd:
+ *   Sec. 2.1 (Eq. 1)    the LP form and the +-inf conventions,
+ *   Sec. 2.1            reductions = presolve transform + postsolve record
+ *                       (fix a variable: index + value; remove a constraint),
+ *   Sec. 3.1            min/max activities, implied bounds, rounds until no
+ *                       bound tightens or a fixed round cap,
+ *   Sec. 3.2            parallel rows a_i = lambda a_j: hash on pattern and
+ *                       coefficients, then an explicit check against a leader
+ *                       (first equality row of the group, else first row).
+ * The paper fixes no formulas, tolerances or step order.  The readings used
+ * here (Jacobi rounds, rule order, tolerances, snapping, the empty-column dual
+ * fix, the bounded leader iteration) are listed in the design notes; the CUDA
+ * library implements the same readings independently.
+ *
+ * Each round, in this order, every step reading the state left by the step
+ * before it (and bounds read at the round start inside a step):
+ *   S1 activities   S2 row classes   S3 implied bounds (+ singleton bounds)
+ *   S3' bound finalise (infeasible / snap)   S4 fixing   S5 parallel rows
+ *   S6 empty columns (dual)   S7 side shift + compaction   S8 stop test.
+ *
+ * Beside the verdicts the oracle keeps a forward error bound for every value
+ * that comes from a sum (activities, shifted sides, implied bounds) and, for
+ * every comparison that decides a reduction, the ratio of the comparison's
+ * margin to that bound (the "tie audit").  An instance whose smallest ratio
+ * is large cannot have a decision flipped by a different summation order.
+ */
+#include "lpp_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define UROUND 1.1102230246251565e-16 /* 2^-53, unit roundoff of binary64 */
+
+static double dmax(double a, double b) { return a > b ? a : b; }
+static int isfin(double x) { return x > -INFINITY && x < INFINITY; }
+/* feasibility tolerance around a value: feas_tol * max(1, |x|) */
+static double tol_at(double feas_tol, double x) { return feas_tol * dmax(1.0, fabs(x)); }
+
+void lppo_opts_default(lppo_opts *o)
+{
+    o->feas_tol = 1e-9;
+    o->bound_tol = 1e-6;
+    o->huge = 1e20;
+    o->max_implied = 1e10;
+    o->par_tol = 1e-12;
+    o->max_rounds = 20;
+    o->dual_reductions = 1;
+    o->hash_qbits = 20;
+    o->par_max_iter = 8;
+}
+
+/* ---------------------------------------------------------------- audit */
+typedef struct {
+    double min_ratio;
+    int64_t n, below;
+} audit_t;
+
+static void audit(audit_t *a, double margin, double eb)
+{
+    double r;
+    a->n++;
+    if (!(eb > 0.0)) return; /* both sides compute this value bit for bit */
+    r = fabs(margin) / eb;
+    if (r < a->min_ratio) a->min_ratio = r;
+    if (r < 1e3) a->below++;
+}
+
+/* error bound of a sum of `cnt` terms with absolute sum `s`, the terms being
+   rounded products that both sides compute identically: any two summation
+   orders differ by at most (cnt-1) * u * s (two terms commute exactly). */
+static double sum_eb(int64_t cnt, double s) { return cnt >= 3 ? (double)(cnt - 1) * UROUND * s : 0.0; }
+
+/* ---------------------------------------------------------------- input */
+static double norm_inf(double x, double huge)
+{
+    if (x >= huge) return INFINITY;
+    if (x <= -huge) return -INFINITY;
+    return x;
+}
+
+static int validate(const lppo_lp *lp)
+{
+    int32_t i;
+    int64_t k;
+    if (lp->m < 0 || lp->n < 0 || lp->nnz < 0 || lp->nnz >= 2147483647LL) return 0;
+    if (lp->m > 0 && !lp->row_ptr) return 0;
+    if (lp->row_ptr && lp->row_ptr[0] != 0) return 0;
+    if (lp->m > 0 && lp->row_ptr[lp->m] != lp->nnz) return 0;
+    if (lp->m == 0 && lp->nnz != 0) return 0;
+    for (i = 0; i < lp->m; i++) {
+        if (lp->row_ptr[i + 1] < lp->row_ptr[i]) return 0;
+        for (k = lp->row_ptr[i]; k < lp->row_ptr[i + 1]; k++) {
+            int32_t j = lp->col_idx[k];
+            double a = lp->val[k];
+            if (j < 0 || j >= lp->n) return 0;
+            if (k > lp->row_ptr[i] && lp->col_idx[k - 1] >= j) return 0;
+            if (!isfin(a) || a == 0.0) return 0;
+        }
+        if (isnan(lp->lhs[i]) || isnan(lp->rhs[i])) return 0;
+        if (lp->lhs[i] == INFINITY || lp->rhs[i] == -INFINITY) return 0;
+    }
+    for (i = 0; i < lp->n; i++) {
+        if (!isfin(lp->c[i])) return 0;
+        if (isnan(lp->lb[i]) || isnan(lp->ub[i])) return 0;
+        if (lp->lb[i] == INFINITY || lp->ub[i] == -INFINITY) return 0;
+    }
+    return 1;
+}
+
+/* ------------------------------------------------------------- S1 (Sec. 3.1)
+ * Minimum activity of row i over the box lb <= x <= ub: each entry a_ij
+ * contributes a_ij*lb_j if a_ij > 0 and a_ij*ub_j if a_ij < 0; maximum
+ * activity the other bound.  An infinite bound is not added but counted. */
+static void row_activity(const int32_t *rp, const int32_t *ci, const double *v,
+                         const double *l, const double *u, int32_t i,
+                         double *mn, double *mx, int32_t *nmn, int32_t *nmx,
+                         double *smn, double *smx)
+{
+    int64_t k;
+    double a_mn = 0.0, a_mx = 0.0, s_mn = 0.0, s_mx = 0.0;
+    int32_t c_mn = 0, c_mx = 0;
+    for (k = rp[i]; k < rp[i + 1]; k++) {
+        double a = v[k];
+        int32_t j = ci[k];
+        double bmin = a > 0 ? l[j] : u[j]; /* bound giving the smallest a*x_j */
+        double bmax = a > 0 ? u[j] : l[j]; /* bound giving the largest a*x_j  */
+        if (isfin(bmin)) { double t = a * bmin; a_mn += t; s_mn += fabs(t); }
+        else c_mn++;
+        if (isfin(bmax)) { double t = a * bmax; a_mx += t; s_mx += fabs(t); }
+        else c_mx++;
+    }
+    *mn = a_mn; *mx = a_mx; *nmn = c_mn; *nmx = c_mx;
+    if (smn) *smn = s_mn;
+    if (smx) *smx = s_mx;
+}
+
+int lppo_activities(const lppo_lp *lp, double huge, double *act_min, double *act_max,
+                    int32_t *ninf_min, int32_t *ninf_max)
+{
+    double *l, *u;
+    int32_t i;
+    if (!validate(lp)) return LPPO_ERR_INVALID;
+    l = (double *)malloc(sizeof(double) * (size_t)(lp->n + 1));
+    u = (double *)malloc(sizeof(double) * (size_t)(lp->n + 1));
+    if (!l || !u) { free(l); free(u); return LPPO_ERR_OOM; }
+    for (i = 0; i < lp->n; i++) { l[i] = norm_inf(lp->lb[i], huge); u[i] = norm_inf(lp->ub[i], huge); }
+    for (i = 0; i < lp->m; i++)
+        row_activity(lp->row_ptr, lp->col_idx, lp->val, l, u, i, &act_min[i], &act_max[i],
+                     &ninf_min[i], &ninf_max[i], NULL, NULL);
+    free(l); free(u);
+    return LPPO_OK;
+}
+
+/* ------------------------------------------------------- S5 key ordering
+ * Key of a row for parallel-row grouping (Sec. 3.2): its length, its column
+ * pattern and its coefficients normalised by the first one and rounded to
+ * qbits mantissa bits.  Rows are grouped by exact key equality. */
+typedef struct {
+    int32_t row, len;
+    const int32_t *cols;
+    const uint64_t *q;
+} pkey_t;
+
+static uint64_t quantise(double x, int qbits)
+{
+    uint64_t b;
+    int drop = 52 - qbits;
+    memcpy(&b, &x, sizeof b);
+    if (drop <= 0) return b;
+    b += (uint64_t)1 << (drop - 1);        /* round to nearest on the bit pattern */
+    b &= ~(((uint64_t)1 << drop) - 1);
+    return b;
+}
+
+static int cmp_key(const void *pa, const void *pb)
+{
+    const pkey_t *a = (const pkey_t *)pa, *b = (const pkey_t *)pb;
+    int32_t k;
+    if (a->len != b->len) return a->len < b->len ? -1 : 1;
+    for (k = 0; k < a->len; k++)
+        if (a->cols[k] != b->cols[k]) return a->cols[k] < b->cols[k] ? -1 : 1;
+    for (k = 0; k < a->len; k++)
+        if (a->q[k] != b->q[k]) return a->q[k] < b->q[k] ? -1 : 1;
+    return a->row < b->row ? -1 : (a->row > b->row);
+}
+
+/* ------------------------------------------------------------ the loop */
+typedef struct {
+    int32_t m, n;
+    int32_t *rp, *ci;
+    double *v;
+    double *L, *U, *l, *u, *c;
+    int32_t *rmap, *cmap;
+    double *ebL, *ebU, *ebl, *ebu; /* forward error bounds (audit) */
+    double offset;
+} state_t;
+
+#define ALLOC(p, cnt) do { (p) = calloc((size_t)(cnt) + 1, sizeof(*(p))); if (!(p)) goto oom; } while (0)
+
+int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
+{
+    state_t s;
+    audit_t au;
+    const double ft = o->feas_tol;
+    int32_t i, j, r, m0 = lp->m, n0 = lp->n;
+    int64_t k;
+    int status = LPPO_OK;
+    /* per-round scratch */
+    double *mna = NULL, *mxa = NULL, *smn = NULL, *smx = NULL, *ebmn = NULL, *ebmx = NULL;
+    int32_t *nmn = NULL, *nmx = NULL, *kind = NULL, *fixed = NULL, *colcnt = NULL;
+    double *nl = NULL, *nu = NULL, *ebnl = NULL, *ebnu = NULL, *fixv = NULL;
+    double *mL = NULL, *mU = NULL, *ebmL = NULL, *ebmU = NULL;
+    int32_t *hasf = NULL, *alive = NULL, *nrow = NULL, *ncol = NULL;
+    pkey_t *keys = NULL;
+    uint64_t *qbuf = NULL;
+    int32_t *nrp = NULL, *nci = NULL;
+    double *nv = NULL;
+
+    memset(&s, 0, sizeof s);
+    if (!validate(lp)) return LPPO_ERR_INVALID;
+
+    /* state := input, infinities normalised */
+    s.m = m0; s.n = n0; s.offset = lp->obj_offset;
+    ALLOC(s.rp, m0 + 1); ALLOC(s.ci, lp->nnz); ALLOC(s.v, lp->nnz);
+    ALLOC(s.L, m0); ALLOC(s.U, m0); ALLOC(s.l, n0); ALLOC(s.u, n0); ALLOC(s.c, n0);
+    ALLOC(s.rmap, m0); ALLOC(s.cmap, n0);
+    ALLOC(s.ebL, m0); ALLOC(s.ebU, m0); ALLOC(s.ebl, n0); ALLOC(s.ebu, n0);
+    if (m0 > 0) memcpy(s.rp, lp->row_ptr, sizeof(int32_t) * (size_t)(m0 + 1));
+    if (lp->nnz > 0) {
+        memcpy(s.ci, lp->col_idx, sizeof(int32_t) * (size_t)lp->nnz);
+        memcpy(s.v, lp->val, sizeof(double) * (size_t)lp->nnz);
+    }
+    for (i = 0; i < m0; i++) {
+        s.L[i] = norm_inf(lp->lhs[i], o->huge);
+        s.U[i] = norm_inf(lp->rhs[i], o->huge);
+        s.rmap[i] = i;
+    }
+    for (j = 0; j < n0; j++) {
+        s.l[j] = norm_inf(lp->lb[j], o->huge);
+        s.u[j] = norm_inf(lp->ub[j], o->huge);
+        s.c[j] = lp->c[j];
+        s.cmap[j] = j;
+    }
+
+    ALLOC(mna, m0); ALLOC(mxa, m0); ALLOC(smn, m0); ALLOC(smx, m0); ALLOC(ebmn, m0); ALLOC(ebmx, m0);
+    ALLOC(nmn, m0); ALLOC(nmx, m0); ALLOC(kind, m0); ALLOC(fixed, n0); ALLOC(colcnt, n0);
+    ALLOC(nl, n0); ALLOC(nu, n0); ALLOC(ebnl, n0); ALLOC(ebnu, n0); ALLOC(fixv, n0);
+    ALLOC(mL, m0); ALLOC(mU, m0); ALLOC(ebmL, m0); ALLOC(ebmU, m0);
+    ALLOC(hasf, m0); ALLOC(alive, m0); ALLOC(nrow, m0); ALLOC(ncol, n0);
+    ALLOC(keys, m0); ALLOC(qbuf, lp->nnz);
+    ALLOC(nrp, m0 + 1); ALLOC(nci, lp->nnz); ALLOC(nv, lp->nnz);
+
+    for (i = 0; i < m0; i++) {
+        out->row_kind[i] = LPPO_ROW_KEPT; out->row_round[i] = 0; out->row_aux[i] = -1; out->row_val[i] = 0.0;
+    }
+    for (j = 0; j < n0; j++) { out->col_kind[j] = LPPO_COL_KEPT; out->col_round[j] = 0; out->col_val[j] = 0.0; }
+    out->where = LPPO_WHERE_NONE; out->index = -1; out->round = 0; out->rounds = 0;
+    au.min_ratio = INFINITY; au.n = 0; au.below = 0;
+
+    for (r = 1; r <= o->max_rounds; r++) {
+        const int32_t m = s.m, n = s.n;
+        int32_t removed = 0, nfixed = 0, bchanged = 0, bad = -1;
+        int64_t nnz = s.rp[m];
+        out->rounds = r;
+        if (out->round_nnz) out->round_nnz[r - 1] = nnz;
+
+        /* ---- S1: activities at the round start (Sec. 3.1) */
+        for (i = 0; i < m0; i++) {
+            out->ninf_min[i] = -1; out->ninf_max[i] = -1;
+            out->act_min[i] = NAN; out->act_max[i] = NAN;
+            out->act_scale_min[i] = NAN; out->act_scale_max[i] = NAN;
+        }
+        for (i = 0; i < m; i++) {
+            int32_t len = s.rp[i + 1] - s.rp[i];
+            double eb_mn = 0.0, eb_mx = 0.0;
+            row_activity(s.rp, s.ci, s.v, s.l, s.u, i, &mna[i], &mxa[i], &nmn[i], &nmx[i], &smn[i], &smx[i]);
+            for (k = s.rp[i]; k < s.rp[i + 1]; k++) { /* propagated bound errors */
+                double a = s.v[k];
+                int32_t jj = s.ci[k];
+                eb_mn += fabs(a) * (a > 0 ? s.ebl[jj] : s.ebu[jj]);
+                eb_mx += fabs(a) * (a > 0 ? s.ebu[jj] : s.ebl[jj]);
+            }
+            ebmn[i] = sum_eb(len - nmn[i], smn[i]) + eb_mn;
+            ebmx[i] = sum_eb(len - nmx[i], smx[i]) + eb_mx;
+            out->act_min[s.rmap[i]] = mna[i]; out->act_max[s.rmap[i]] = mxa[i];
+            out->ninf_min[s.rmap[i]] = nmn[i]; out->ninf_max[s.rmap[i]] = nmx[i];
+            out->act_scale_min[s.rmap[i]] = smn[i]; out->act_scale_max[s.rmap[i]] = smx[i];
+        }
+
+        /* ---- S2: row classes, first match wins:
+               infeasible sides, infeasible activity, empty, redundant, singleton */
+        for (i = 0; i < m && bad < 0; i++) {
+            const double L = s.L[i], U = s.U[i];
+            const int32_t len = s.rp[i + 1] - s.rp[i];
+            int lo_ok, hi_ok;
+            kind[i] = LPPO_ROW_KEPT;
+            if (isfin(L) && isfin(U)) {
+                double d = ft * dmax(1.0, dmax(fabs(L), fabs(U)));
+                audit(&au, (L - U) - d, s.ebL[i] + s.ebU[i]);
+                if (L - U > d) { bad = i; break; }
+            }
+            if (nmn[i] == 0 && isfin(U)) {
+                audit(&au, mna[i] - (U + tol_at(ft, U)), ebmn[i] + s.ebU[i]);
+                if (mna[i] > U + tol_at(ft, U)) { bad = i; break; }
+            }
+            if (nmx[i] == 0 && isfin(L)) {
+                audit(&au, mxa[i] - (L - tol_at(ft, L)), ebmx[i] + s.ebL[i]);
+                if (mxa[i] < L - tol_at(ft, L)) { bad = i; break; }
+            }
+            if (len == 0) { /* activity is 0: the two tests above already decided feasibility */
+                kind[i] = LPPO_ROW_EMPTY;
+                continue;
+            }
+            if (L == -INFINITY) lo_ok = 1;
+            else if (nmn[i] != 0) lo_ok = 0;
+            else {
+                audit(&au, mna[i] - (L - tol_at(ft, L)), ebmn[i] + s.ebL[i]);
+                lo_ok = mna[i] >= L - tol_at(ft, L);
+            }
+            if (lo_ok) {
+                if (U == INFINITY) hi_ok = 1;
+                else if (nmx[i] != 0) hi_ok = 0;
+                else {
+                    audit(&au, mxa[i] - (U + tol_at(ft, U)), ebmx[i] + s.ebU[i]);
+                    hi_ok = mxa[i] <= U + tol_at(ft, U);
+                }
+                if (hi_ok) { kind[i] = LPPO_ROW_REDUNDANT; continue; }
+            }
+            if (len == 1) kind[i] = LPPO_ROW_SINGLETON;
+        }
+        if (bad >= 0) {
+            status = LPPO_INFEASIBLE; out->where = LPPO_WHERE_ROW; out->index = s.rmap[bad]; out->round = r;
+            break;
+        }
+        for (i = 0; i < m; i++) {
+            if (kind[i] == LPPO_ROW_KEPT) continue;
+            out->row_kind[s.rmap[i]] = kind[i];
+            out->row_round[s.rmap[i]] = r;
+            removed++;
+            if (kind[i] == LPPO_ROW_SINGLETON) {
+                out->row_aux[s.rmap[i]] = s.cmap[s.ci[s.rp[i]]];
+                out->row_val[s.rmap[i]] = s.v[s.rp[i]];
+            }
+        }
+
+        /* ---- S3: implied bounds from residual activities (Sec. 3.1), Jacobi:
+               every candidate is judged against the bounds of the round start
+               and the accepted ones are combined by min / max. */
+        for (j = 0; j < n; j++) { nl[j] = s.l[j]; nu[j] = s.u[j]; ebnl[j] = s.ebl[j]; ebnu[j] = s.ebu[j]; }
+        for (i = 0; i < m; i++) {
+            const double L = s.L[i], U = s.U[i];
+            if (kind[i] != LPPO_ROW_KEPT || s.rp[i + 1] - s.rp[i] < 2) continue;
+            for (k = s.rp[i]; k < s.rp[i + 1]; k++) {
+                const double a = s.v[k];
+                const int32_t jj = s.ci[k];
+                const double bmin = a > 0 ? s.l[jj] : s.u[jj];
+                const double bmax = a > 0 ? s.u[jj] : s.l[jj];
+                const double ebbmin = a > 0 ? s.ebl[jj] : s.ebu[jj];
+                const double ebbmax = a > 0 ? s.ebu[jj] : s.ebl[jj];
+                int rmin_ok, rmax_ok;
+                double rmin = 0, rmax = 0, eb_rmin = 0, eb_rmax = 0;
+                double cand[2], ebc[2];
+                int is_upper[2], nc = 0, t;
+                if (!isfin(bmin)) { rmin_ok = nmn[i] == 1; rmin = mna[i]; eb_rmin = ebmn[i]; }
+                else {
+                    rmin_ok = nmn[i] == 0;
+                    rmin = mna[i] - a * bmin;
+                    eb_rmin = ebmn[i] + fabs(a) * ebbmin + UROUND * fabs(rmin);
+                }
+                if (!isfin(bmax)) { rmax_ok = nmx[i] == 1; rmax = mxa[i]; eb_rmax = ebmx[i]; }
+                else {
+                    rmax_ok = nmx[i] == 0;
+                    rmax = mxa[i] - a * bmax;
+                    eb_rmax = ebmx[i] + fabs(a) * ebbmax + UROUND * fabs(rmax);
+                }
+                /* a x_j <= U - rmin  and  a x_j >= L - rmax */
+                if (isfin(U) && rmin_ok) {
+                    cand[nc] = (U - rmin) / a;
+                    ebc[nc] = (s.ebU[i] + eb_rmin) / fabs(a) + UROUND * fabs(cand[nc]);
+                    is_upper[nc++] = a > 0;
+                }
+                if (isfin(L) && rmax_ok) {
+                    cand[nc] = (L - rmax) / a;
+                    ebc[nc] = (s.ebL[i] + eb_rmax) / fabs(a) + UROUND * fabs(cand[nc]);
+                    is_upper[nc++] = a < 0;
+                }
+                for (t = 0; t < nc; t++) {
+                    const double cv = cand[t];
+                    audit(&au, fabs(cv) - o->max_implied, ebc[t]);
+                    if (fabs(cv) > o->max_implied) continue;
+                    if (is_upper[t]) {
+                        if (isfin(s.u[jj])) {
+                            double thr = s.u[jj] - o->bound_tol * dmax(1.0, fabs(s.u[jj]));
+                            audit(&au, cv - thr, ebc[t] + s.ebu[jj]);
+                            if (!(cv < thr)) continue;
+                        }
+                        if (cv < nu[jj]) { nu[jj] = cv; ebnu[jj] = ebc[t]; }
+                    } else {
+                        if (isfin(s.l[jj])) {
+                            double thr = s.l[jj] + o->bound_tol * dmax(1.0, fabs(s.l[jj]));
+                            audit(&au, cv - thr, ebc[t] + s.ebl[jj]);
+                            if (!(cv > thr)) continue;
+                        }
+                        if (cv > nl[jj]) { nl[jj] = cv; ebnl[jj] = ebc[t]; }
+                    }
+                }
+            }
+        }
+        /* singleton rows become bounds: L <= a x_j <= U, always applied */
+        for (i = 0; i < m; i++) {
+            double a, L = s.L[i], U = s.U[i], cl, cu, ebcl, ebcu;
+            if (kind[i] != LPPO_ROW_SINGLETON) continue;
+            a = s.v[s.rp[i]];
+            j = s.ci[s.rp[i]];
+            if (a > 0) {
+                cl = isfin(L) ? L / a : -INFINITY; ebcl = s.ebL[i] / fabs(a) + UROUND * fabs(cl);
+                cu = isfin(U) ? U / a : INFINITY;  ebcu = s.ebU[i] / fabs(a) + UROUND * fabs(cu);
+            } else {
+                cl = isfin(U) ? U / a : -INFINITY; ebcl = s.ebU[i] / fabs(a) + UROUND * fabs(cl);
+                cu = isfin(L) ? L / a : INFINITY;  ebcu = s.ebL[i] / fabs(a) + UROUND * fabs(cu);
+            }
+            if (isfin(cl) && isfin(s.l[j])) audit(&au, cl - s.l[j], ebcl + s.ebl[j]);
+            if (isfin(cu) && isfin(s.u[j])) audit(&au, cu - s.u[j], ebcu + s.ebu[j]);
+            if (cl > nl[j]) { nl[j] = cl; ebnl[j] = ebcl; }
+            if (cu < nu[j]) { nu[j] = cu; ebnu[j] = ebcu; }
+        }
+
+        /* ---- S3': finalise bounds: crossing by more than the tolerance is
+               infeasible, bounds within the tolerance are snapped together */
+        for (j = 0; j < n && bad < 0; j++) {
+            double lp_ = nl[j], up_ = nu[j];
+            if (isfin(lp_) && isfin(up_)) {
+                double d = ft * dmax(1.0, dmax(fabs(lp_), fabs(up_)));
+                audit(&au, (lp_ - up_) - d, ebnl[j] + ebnu[j]);
+                if (lp_ - up_ > d) { bad = j; break; }
+                audit(&au, fabs(lp_ - up_) - d, ebnl[j] + ebnu[j]);
+                if (lp_ != up_ && fabs(lp_ - up_) <= d) {
+                    double mid = 0.5 * (lp_ + up_);
+                    double e = dmax(ebnl[j], ebnu[j]) + UROUND * fabs(mid);
+                    lp_ = up_ = mid; ebnl[j] = ebnu[j] = e;
+                }
+            }
+            if (lp_ != s.l[j] || up_ != s.u[j]) bchanged++;
+            s.l[j] = lp_; s.u[j] = up_; s.ebl[j] = ebnl[j]; s.ebu[j] = ebnu[j];
+        }
+        if (bad >= 0) {
+            status = LPPO_INFEASIBLE; out->where = LPPO_WHERE_COL; out->index = s.cmap[bad]; out->round = r;
+            break;
+        }
+
+        /* ---- S4: a column with lb == ub is fixed at that value (Sec. 2.1) */
+        for (j = 0; j < n; j++) {
+            fixed[j] = s.l[j] == s.u[j];
+            fixv[j] = s.l[j];
+            if (fixed[j]) {
+                out->col_kind[s.cmap[j]] = LPPO_COL_FIXED; out->col_round[s.cmap[j]] = r;
+                out->col_val[s.cmap[j]] = fixv[j];
+                nfixed++;
+            }
+        }
+
+        /* ---- S5: parallel rows (Sec. 3.2) among the rows S2 kept with
+               length >= 2, on the coefficients of the round start. */
+        {
+            int32_t np = 0, g0, g1;
+            int64_t qo = 0;
+            for (i = 0; i < m; i++) {
+                int32_t len = s.rp[i + 1] - s.rp[i];
+                hasf[i] = 0; mL[i] = -INFINITY; mU[i] = INFINITY; ebmL[i] = 0; ebmU[i] = 0;
+                if (kind[i] != LPPO_ROW_KEPT || len < 2) continue;
+                {
+                    const double a0 = s.v[s.rp[i]];
+                    keys[np].row = i; keys[np].len = len;
+                    keys[np].cols = s.ci + s.rp[i];
+                    keys[np].q = qbuf + qo;
+                    for (k = s.rp[i]; k < s.rp[i + 1]; k++) qbuf[qo++] = quantise(s.v[k] / a0, o->hash_qbits);
+                    np++;
+                }
+            }
+            qsort(keys, (size_t)np, sizeof(pkey_t), cmp_key);
+            for (g0 = 0; g0 < np; g0 = g1) {
+                int32_t it, gsz;
+                pkey_t probe = keys[g0];
+                for (g1 = g0 + 1; g1 < np; g1++) {
+                    probe.row = keys[g1].row; /* compare keys only */
+                    if (cmp_key(&probe, &keys[g1]) != 0) break;
+                }
+                gsz = g1 - g0;
+                if (gsz < 2) continue;
+                for (k = g0; k < g1; k++) alive[k - g0] = 1;
+                for (it = 0; it < o->par_max_iter; it++) {
+                    int32_t cnt = 0, lead = -1, li, t;
+                    for (t = 0; t < gsz; t++) if (alive[t]) cnt++;
+                    if (cnt < 2) break;
+                    /* leader: first equality row of the group, else first row (Sec. 3.2) */
+                    for (t = 0; t < gsz && lead < 0; t++) {
+                        int32_t rr = keys[g0 + t].row;
+                        if (alive[t] && isfin(s.L[rr]) && s.L[rr] == s.U[rr]) lead = t;
+                    }
+                    for (t = 0; t < gsz && lead < 0; t++) if (alive[t]) lead = t;
+                    alive[lead] = 0;
+                    li = keys[g0 + lead].row;
+                    for (t = 0; t < gsz; t++) {
+                        int32_t fj = keys[g0 + t].row, len = s.rp[fj + 1] - s.rp[fj], q;
+                        const double *ai = s.v + s.rp[li], *aj = s.v + s.rp[fj];
+                        double lam, lo, hi, eblo, ebhi;
+                        int par = 1;
+                        if (!alive[t]) continue;
+                        lam = aj[0] / ai[0];
+                        for (q = 0; q < len && par; q++) {
+                            double la = lam * ai[q];
+                            if (!(fabs(aj[q] - la) <= o->par_tol * dmax(fabs(aj[q]), fabs(la)))) par = 0;
+                        }
+                        if (!par) continue;
+                        alive[t] = 0;
+                        kind[fj] = LPPO_ROW_PARALLEL;
+                        out->row_kind[s.rmap[fj]] = LPPO_ROW_PARALLEL; out->row_round[s.rmap[fj]] = r;
+                        out->row_aux[s.rmap[fj]] = s.rmap[li]; out->row_val[s.rmap[fj]] = lam;
+                        removed++;
+                        /* L_j <= lam a_i x <= U_j, divided by lam */
+                        if (lam > 0) {
+                            lo = isfin(s.L[fj]) ? s.L[fj] / lam : -INFINITY; eblo = s.ebL[fj] / fabs(lam);
+                            hi = isfin(s.U[fj]) ? s.U[fj] / lam : INFINITY;  ebhi = s.ebU[fj] / fabs(lam);
+                        } else {
+                            lo = isfin(s.U[fj]) ? s.U[fj] / lam : -INFINITY; eblo = s.ebU[fj] / fabs(lam);
+                            hi = isfin(s.L[fj]) ? s.L[fj] / lam : INFINITY;  ebhi = s.ebL[fj] / fabs(lam);
+                        }
+                        hasf[li] = 1;
+                        if (lo > mL[li]) { mL[li] = lo; ebmL[li] = eblo + UROUND * fabs(lo); }
+                        if (hi < mU[li]) { mU[li] = hi; ebmU[li] = ebhi + UROUND * fabs(hi); }
+                    }
+                }
+            }
+            /* merge the followers' sides into each leader, in row order */
+            for (i = 0; i < m && bad < 0; i++) {
+                double nL, nU, enL, enU;
+                if (!hasf[i]) continue;
+                nL = s.L[i]; enL = s.ebL[i];
+                nU = s.U[i]; enU = s.ebU[i];
+                if (mL[i] > nL) { nL = mL[i]; enL = ebmL[i]; }
+                if (mU[i] < nU) { nU = mU[i]; enU = ebmU[i]; }
+                if (isfin(nL) && isfin(nU)) {
+                    double d = ft * dmax(1.0, dmax(fabs(nL), fabs(nU)));
+                    audit(&au, (nL - nU) - d, enL + enU);
+                    if (nL - nU > d) { bad = i; break; }
+                    audit(&au, fabs(nL - nU) - d, enL + enU);
+                    if (nL != nU && fabs(nL - nU) <= d) {
+                        double mid = 0.5 * (nL + nU);
+                        nL = nU = mid; enL = enU = dmax(enL, enU) + UROUND * fabs(mid);
+                    }
+                }
+                s.L[i] = nL; s.U[i] = nU; s.ebL[i] = enL; s.ebU[i] = enU;
+            }
+            if (bad >= 0) {
+                status = LPPO_INFEASIBLE; out->where = LPPO_WHERE_ROW; out->index = s.rmap[bad]; out->round = r;
+                break;
+            }
+        }
+
+        /* ---- S6: a column with no entry left in a kept row is fixed at the
+               bound its cost prefers (dual reduction) */
+        if (o->dual_reductions) {
+            for (j = 0; j < n; j++) colcnt[j] = 0;
+            for (i = 0; i < m; i++) {
+                if (kind[i] != LPPO_ROW_KEPT) continue;
+                for (k = s.rp[i]; k < s.rp[i + 1]; k++) colcnt[s.ci[k]]++;
+            }
+            for (j = 0; j < n && bad < 0; j++) {
+                double v;
+                if (fixed[j] || colcnt[j] != 0) continue;
+                if (s.c[j] > 0) v = s.l[j];
+                else if (s.c[j] < 0) v = s.u[j];
+                else v = isfin(s.l[j]) ? s.l[j] : (isfin(s.u[j]) ? s.u[j] : 0.0);
+                if (!isfin(v)) { bad = j; break; }
+                fixed[j] = 2; fixv[j] = v;
+                out->col_kind[s.cmap[j]] = LPPO_COL_EMPTY; out->col_round[s.cmap[j]] = r;
+                out->col_val[s.cmap[j]] = v;
+                nfixed++;
+            }
+            if (bad >= 0) {
+                status = LPPO_UNBOUNDED; out->where = LPPO_WHERE_COL; out->index = s.cmap[bad]; out->round = r;
+                break;
+            }
+        }
+        for (j = 0; j < n; j++) /* objective constant, column order */
+            if (fixed[j]) s.offset += s.c[j] * fixv[j];
+
+        /* ---- S7: shift the sides of kept rows by their fixed columns, then
+               drop removed rows and fixed columns, keeping relative order */
+        {
+            int32_t mr = 0, nr = 0;
+            int64_t w = 0;
+            for (j = 0; j < n; j++) ncol[j] = fixed[j] ? -1 : nr++;
+            for (i = 0; i < m; i++) {
+                double sh = 0.0, ssh = 0.0, esh = 0.0;
+                int32_t cnt = 0;
+                if (kind[i] != LPPO_ROW_KEPT) { nrow[i] = -1; continue; }
+                for (k = s.rp[i]; k < s.rp[i + 1]; k++) {
+                    int32_t jj = s.ci[k];
+                    if (!fixed[jj]) continue;
+                    sh += s.v[k] * fixv[jj];
+                    ssh += fabs(s.v[k] * fixv[jj]);
+                    esh += fabs(s.v[k]) * s.ebl[jj];
+                    cnt++;
+                }
+                if (cnt > 0) {
+                    double e = sum_eb(cnt, ssh) + esh;
+                    if (isfin(s.L[i])) { s.L[i] = s.L[i] - sh; s.ebL[i] += e + UROUND * fabs(s.L[i]); }
+                    if (isfin(s.U[i])) { s.U[i] = s.U[i] - sh; s.ebU[i] += e + UROUND * fabs(s.U[i]); }
+                }
+                nrow[i] = mr++;
+            }
+            nrp[0] = 0;
+            for (i = 0; i < m; i++) {
+                if (nrow[i] < 0) continue;
+                for (k = s.rp[i]; k < s.rp[i + 1]; k++) {
+                    int32_t jj = s.ci[k];
+                    if (ncol[jj] < 0) continue;
+                    nci[w] = ncol[jj]; nv[w] = s.v[k]; w++;
+                }
+                nrp[nrow[i] + 1] = (int32_t)w;
+                s.L[nrow[i]] = s.L[i]; s.U[nrow[i]] = s.U[i];
+                s.ebL[nrow[i]] = s.ebL[i]; s.ebU[nrow[i]] = s.ebU[i];
+                s.rmap[nrow[i]] = s.rmap[i];
+            }
+            for (j = 0; j < n; j++) {
+                if (ncol[j] < 0) continue;
+                s.l[ncol[j]] = s.l[j]; s.u[ncol[j]] = s.u[j]; s.c[ncol[j]] = s.c[j];
+                s.ebl[ncol[j]] = s.ebl[j]; s.ebu[ncol[j]] = s.ebu[j];
+                s.cmap[ncol[j]] = s.cmap[j];
+            }
+            memcpy(s.rp, nrp, sizeof(int32_t) * (size_t)(mr + 1));
+            if (w > 0) { memcpy(s.ci, nci, sizeof(int32_t) * (size_t)w); memcpy(s.v, nv, sizeof(double) * (size_t)w); }
+            s.m = mr; s.n = nr;
+        }
+
+        if (out->round_rows_removed) out->round_rows_removed[r - 1] = removed;
+        if (out->round_cols_fixed) out->round_cols_fixed[r - 1] = nfixed;
+        if (out->round_bounds_changed) out->round_bounds_changed[r - 1] = bchanged;
+        /* ---- S8: stop when the round changed nothing (Sec. 3.1) */
+        if (removed == 0 && nfixed == 0 && bchanged == 0) break;
+    }
+
+    /* ---- outputs */
+    out->status = status;
+    out->m_red = s.m; out->n_red = s.n; out->nnz_red = s.rp[s.m];
+    out->obj_offset = s.offset;
+    memcpy(out->row_ptr, s.rp, sizeof(int32_t) * (size_t)(s.m + 1));
+    if (s.rp[s.m] > 0) {
+        memcpy(out->col_idx, s.ci, sizeof(int32_t) * (size_t)s.rp[s.m]);
+        memcpy(out->val, s.v, sizeof(double) * (size_t)s.rp[s.m]);
+    }
+    for (i = 0; i < s.m; i++) { out->lhs[i] = s.L[i]; out->rhs[i] = s.U[i]; out->row_map[i] = s.rmap[i]; }
+    for (j = 0; j < s.n; j++) {
+        out->lb[j] = s.l[j]; out->ub[j] = s.u[j]; out->c[j] = s.c[j]; out->col_map[j] = s.cmap[j];
+    }
+    for (j = 0; j < n0; j++) { out->col_lb[j] = NAN; out->col_ub[j] = NAN; }
+    for (j = 0; j < s.n; j++) { out->col_lb[s.cmap[j]] = s.l[j]; out->col_ub[s.cmap[j]] = s.u[j]; }
+    for (j = 0; j < n0; j++)
+        if (out->col_kind[j] != LPPO_COL_KEPT) { out->col_lb[j] = out->col_val[j]; out->col_ub[j] = out->col_val[j]; }
+    out->audit_min_ratio = au.min_ratio; out->audit_decisions = au.n; out->audit_below_1e3 = au.below;
+
+    free(s.rp); free(s.ci); free(s.v); free(s.L); free(s.U); free(s.l); free(s.u); free(s.c);
+    free(s.rmap); free(s.cmap); free(s.ebL); free(s.ebU); free(s.ebl); free(s.ebu);
+    free(mna); free(mxa); free(smn); free(smx); free(ebmn); free(ebmx); free(nmn); free(nmx);
+    free(kind); free(fixed); free(colcnt); free(nl); free(nu); free(ebnl); free(ebnu); free(fixv);
+    free(mL); free(mU); free(ebmL); free(ebmU); free(hasf); free(alive); free(nrow); free(ncol);
+    free(keys); free(qbuf); free(nrp); free(nci); free(nv);
+    return status;
+oom:
+    free(s.rp); free(s.ci); free(s.v); free(s.L); free(s.U); free(s.l); free(s.u); free(s.c);
+    free(s.rmap); free(s.cmap); free(s.ebL); free(s.ebU); free(s.ebl); free(s.ebu);
+    free(mna); free(mxa); free(smn); free(smx); free(ebmn); free(ebmx); free(nmn); free(nmx);
+    free(kind); free(fixed); free(colcnt); free(nl); free(nu); free(ebnl); free(ebnu); free(fixv);
+    free(mL); free(mU); free(ebmL); free(ebmU); free(hasf); free(alive); free(nrow); free(ncol);
+    free(keys); free(qbuf); free(nrp); free(nci); free(nv);
+    return LPPO_ERR_OOM;
+}
+
+/* Postsolve, primal part (Sec. 2.1, postsolver paragraph; Sec. 3.3): every
+   kept column takes its reduced value, every fixed column its record value.
+   Row removals and bound changes need no primal postsolve step. */
+int lppo_postsolve_primal(int32_t n_orig, int32_t n_red, const int32_t *col_map,
+                          const int32_t *col_kind, const double *col_val,
+                          const double *x_red, double *x_orig)
+{
+    int32_t j;
+    for (j = 0; j < n_orig; j++) x_orig[j] = col_kind[j] != LPPO_COL_KEPT ? col_val[j] : NAN;
+    for (j = 0; j < n_red; j++) {
+        if (col_map[j] < 0 || col_map[j] >= n_orig) return LPPO_ERR_INVALID;
+        x_orig[col_map[j]] = x_red[j];
+    }
+    return LPPO_OK;
+}

@@ -1,0 +1,498 @@
+"""Seeded synthetic LP generators (inputs only).
+
+This module builds LPs of the form of Eq. 1 (Sec. 2.1) with NumPy and a
+fixed seed.  It holds no presolve arithmetic: it draws a matrix, bounds, a
+point x0 inside the bounds and sides around A x0, and plants structures that
+the presolve rules are meant to find.  Both the CUDA library's tests and the
+oracle's tests draw their inputs from here, so the two sides see the same LP.
+
+Shapes follow the paper's large-scale workloads (Sec. 3.1: median row of 2
+nonzeros, a few rows with a large share of the nonzeros; Sec. 4.1: LP
+relaxations) at the sizes of the benchmark configurations:
+
+* ``tiny``     m=200, n=300, ~1.5k nnz with planted empty / singleton /
+               redundant / parallel rows and fixed columns;
+* ``skewed``   m=2M, n=3M, ~20M nnz, row lengths 1+Zipf(2) capped at 500k,
+               column weights Zipf(1.8), lognormal values;
+* ``lprelax``  m=500k, n=1M, 8M nnz, 10 dense columns, planted parallel rows,
+               doubleton equations and dominated bounds;
+* ``batch``    many tiny-like LPs of ragged size;
+* ``serve_stream`` Poisson arrivals of skewed-like LPs.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import numpy as np
+
+INF = np.inf
+
+
+@dataclass
+class LP:
+    """An LP of Eq. 1 in CSR form (row_ptr/col_idx int32, everything else f64)."""
+    m: int
+    n: int
+    row_ptr: np.ndarray
+    col_idx: np.ndarray
+    val: np.ndarray
+    c: np.ndarray
+    lhs: np.ndarray
+    rhs: np.ndarray
+    lb: np.ndarray
+    ub: np.ndarray
+    obj_offset: float = 0.0
+    planted: dict = field(default_factory=dict)
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1]) if self.m > 0 else 0
+
+    def arrays(self):
+        return dict(row_ptr=self.row_ptr, col_idx=self.col_idx, val=self.val, c=self.c,
+                    lhs=self.lhs, rhs=self.rhs, lb=self.lb, ub=self.ub)
+
+    def nbytes(self) -> int:
+        return sum(a.nbytes for a in self.arrays().values())
+
+
+# --------------------------------------------------------------------- helpers
+def _ptr_from_lengths(lengths: np.ndarray) -> np.ndarray:
+    ptr = np.zeros(len(lengths) + 1, dtype=np.int64)
+    np.cumsum(lengths, out=ptr[1:])
+    return ptr
+
+
+def _row_of_entry(ptr: np.ndarray) -> np.ndarray:
+    lengths = np.diff(ptr)
+    return np.repeat(np.arange(len(lengths), dtype=np.int64), lengths)
+
+
+def _sort_rows(rows: np.ndarray, cols: np.ndarray, vals: np.ndarray, m: int):
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=m), out=ptr[1:])
+    return ptr, cols, vals
+
+
+def _dot_rows(ptr, cols, vals, x, m):
+    rows = _row_of_entry(ptr)
+    return np.bincount(rows, weights=vals * x[cols], minlength=m)
+
+
+def _sides_around(rng, ax, eq_mask, one_side_p=0.3):
+    """Equality rows: lhs = rhs = a.x0.  Inequalities: a slack on each side,
+    lognormal(0,1)*(1+|a.x0|), one side dropped to infinity with prob. 0.3."""
+    m = len(ax)
+    s1 = rng.lognormal(0.0, 1.0, m) * (1.0 + np.abs(ax))
+    s2 = rng.lognormal(0.0, 1.0, m) * (1.0 + np.abs(ax))
+    lhs = ax - s1
+    rhs = ax + s2
+    drop = rng.random(m) < one_side_p
+    which = rng.random(m) < 0.5
+    lhs = np.where(drop & which, -INF, lhs)
+    rhs = np.where(drop & ~which, INF, rhs)
+    lhs = np.where(eq_mask, ax, lhs)
+    rhs = np.where(eq_mask, ax, rhs)
+    return lhs, rhs
+
+
+def _point_in_box(rng, lb, ub):
+    """x0 inside the bounds: uniform when both are finite, one unit inside a
+    single finite bound, standard normal when free."""
+    n = len(lb)
+    x = np.empty(n)
+    fl, fu = np.isfinite(lb), np.isfinite(ub)
+    both = fl & fu
+    x[both] = lb[both] + rng.random(both.sum()) * (ub[both] - lb[both])
+    x[fl & ~fu] = lb[fl & ~fu] + 1.0
+    x[~fl & fu] = ub[~fl & fu] - 1.0
+    free = ~fl & ~fu
+    x[free] = rng.standard_normal(free.sum())
+    return x
+
+
+def _finish(m, n, ptr, cols, vals, c, lhs, rhs, lb, ub, planted, name) -> LP:
+    assert ptr[-1] < 2**31 - 1
+    return LP(m=m, n=n, row_ptr=ptr.astype(np.int32), col_idx=cols.astype(np.int32),
+              val=vals.astype(np.float64), c=c.astype(np.float64), lhs=lhs.astype(np.float64),
+              rhs=rhs.astype(np.float64), lb=lb.astype(np.float64), ub=ub.astype(np.float64),
+              planted=planted, name=name)
+
+
+def _cost(rng, lb, ub):
+    """c ~ U[-1,1], signed so that moving a variable towards an infinite bound
+    never lowers the cost (c > 0 needs a finite lb, c < 0 a finite ub, free
+    variables cost 0); the generated LPs are therefore never reported
+    unbounded by an empty column."""
+    c = rng.uniform(-1.0, 1.0, len(lb))
+    fl, fu = np.isfinite(lb), np.isfinite(ub)
+    c = np.where(fl & ~fu, np.abs(c), c)
+    c = np.where(~fl & fu, -np.abs(c), c)
+    return np.where(~fl & ~fu, 0.0, c)
+
+
+def _draw_magnitudes(rng, k, lo=-10.0, hi=10.0):
+    v = rng.uniform(lo, hi, k)
+    small = np.abs(v) < 1e-2
+    while small.any():
+        v[small] = rng.uniform(lo, hi, small.sum())
+        small = np.abs(v) < 1e-2
+    return v
+
+
+# ------------------------------------------------------------------ tiny mix
+def tiny(seed: int, m: int = 200, n: int = 300, mean_len: float = 9.0,
+         n_empty: int = 10, n_single: int = 15, n_fixed: int = 20,
+         n_redundant: int = 10, n_parallel: int = 8, eq_frac: float = 0.5,
+         inf_ub_frac: float = 0.1) -> LP:
+    """The small mixed LP: values U[-10,10] without (near-)zeros, lb = 0,
+    ub ~ U[1,100] with 10% +inf, about half equality rows, and planted
+    empty rows, singleton rows, fixed columns, redundant rows and scaled
+    copies of rows (parallel pairs).  Planted rows sit at random positions."""
+    rng = np.random.default_rng(seed)
+    n_base = m - n_empty - n_single - n_redundant - n_parallel
+    assert n_base >= n_parallel and n >= 16
+    lb = np.zeros(n)
+    ub = rng.uniform(1.0, 100.0, n)
+    ub[rng.random(n) < inf_ub_frac] = INF
+    fixed_cols = rng.choice(n, size=min(n_fixed, n), replace=False)
+    fv = rng.uniform(1.0, 10.0, len(fixed_cols))
+    lb[fixed_cols] = fv
+    ub[fixed_cols] = fv
+    x0 = _point_in_box(rng, lb, ub)
+
+    rows_cols, rows_vals, kinds = [], [], []
+    hi_len = max(3, int(round(2 * mean_len - 2)))
+    for _ in range(n_base):
+        ln = int(rng.integers(2, hi_len + 1))
+        ln = min(ln, n)
+        cols = np.sort(rng.choice(n, size=ln, replace=False))
+        rows_cols.append(cols)
+        rows_vals.append(_draw_magnitudes(rng, ln))
+        kinds.append("base")
+    base_ids = list(range(n_base))
+    par_src = rng.choice(base_ids, size=n_parallel, replace=False)
+    lambdas = rng.uniform(0.5, 4.0, n_parallel) * np.where(rng.random(n_parallel) < 0.5, -1.0, 1.0)
+    for src, lam in zip(par_src, lambdas):
+        rows_cols.append(rows_cols[src].copy())
+        rows_vals.append(rows_vals[src] * lam)
+        kinds.append("parallel")
+    for _ in range(n_single):
+        rows_cols.append(np.array([rng.integers(0, n)]))
+        rows_vals.append(_draw_magnitudes(rng, 1))
+        kinds.append("singleton")
+    finite_cols = np.flatnonzero(np.isfinite(ub))
+    for _ in range(n_redundant):
+        ln = int(rng.integers(2, 6))
+        cols = np.sort(rng.choice(finite_cols, size=ln, replace=False))
+        rows_cols.append(cols)
+        rows_vals.append(_draw_magnitudes(rng, ln))
+        kinds.append("redundant")
+    for _ in range(n_empty):
+        rows_cols.append(np.array([], dtype=np.int64))
+        rows_vals.append(np.array([]))
+        kinds.append("empty")
+
+    perm = rng.permutation(len(kinds))
+    where = np.empty(len(kinds), dtype=np.int64)
+    where[perm] = np.arange(len(kinds))  # old position -> new row index
+    pairs = [(int(where[src]), int(where[n_base + t])) for t, src in enumerate(par_src)]
+    rows_cols = [rows_cols[p] for p in perm]
+    rows_vals = [rows_vals[p] for p in perm]
+    kinds = [kinds[p] for p in perm]
+    lengths = np.array([len(c) for c in rows_cols], dtype=np.int64)
+    ptr = _ptr_from_lengths(lengths)
+    cols = np.concatenate(rows_cols).astype(np.int64) if ptr[-1] else np.zeros(0, np.int64)
+    vals = np.concatenate(rows_vals) if ptr[-1] else np.zeros(0)
+    ax = _dot_rows(ptr, cols, vals, x0, m)
+    eq = rng.random(m) < eq_frac
+    lhs, rhs = _sides_around(rng, ax, eq)
+    kinds = np.array(kinds)
+    # redundant rows: sides outside a crude bound on |a.x| over the box
+    for i in np.flatnonzero(kinds == "redundant"):
+        sl = slice(ptr[i], ptr[i + 1])
+        big = np.sum(np.abs(vals[sl]) * np.maximum(np.abs(lb[cols[sl]]), np.abs(ub[cols[sl]])))
+        margin = 1.0 + rng.uniform(0.0, 1.0) * big
+        lhs[i] = -big - margin if rng.random() < 0.7 else -INF
+        rhs[i] = big + margin
+    # empty rows: sides that contain 0
+    for i in np.flatnonzero(kinds == "empty"):
+        if rng.random() < 0.3:
+            lhs[i] = rhs[i] = 0.0
+        else:
+            lhs[i] = -rng.uniform(0.0, 5.0) if rng.random() < 0.7 else -INF
+            rhs[i] = rng.uniform(0.0, 5.0) if rng.random() < 0.7 else INF
+    c = _cost(rng, lb, ub)
+    planted = dict(empty=n_empty, singleton=n_single, fixed=len(fixed_cols), redundant=n_redundant,
+                   parallel=n_parallel, x0=x0, kinds=kinds, pairs=pairs, lambdas=lambdas)
+    return _finish(m, n, ptr, cols, vals, c, lhs, rhs, lb, ub, planted, f"tiny-{seed}")
+
+
+# --------------------------------------------------------------- skewed large
+def _zipf_capped(rng, s, size, cap):
+    z = rng.zipf(s, size).astype(np.int64)
+    np.minimum(z, cap, out=z)
+    return z
+
+
+def _assign_columns(rng, lengths, n, col_weight_s, weight_cap):
+    """Configuration model: every column gets one entry first (so no column
+    starts empty), the other entries pick a column with probability
+    proportional to a Zipf(col_weight_s) weight; a column drawn twice in one
+    row is drawn again until every row holds distinct columns."""
+    m = len(lengths)
+    ptr = _ptr_from_lengths(lengths)
+    nnz = int(ptr[-1])
+    rows = _row_of_entry(ptr)
+    w = _zipf_capped(rng, col_weight_s, n, weight_cap).astype(np.float64)
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+
+    def draw(k):
+        return np.minimum(np.searchsorted(cdf, rng.random(k), side="right"), n - 1)
+
+    cols = draw(nnz)
+    fixed = np.zeros(nnz, dtype=bool)
+    if nnz >= n:
+        slots = rng.choice(nnz, size=n, replace=False)
+        cols[slots] = rng.permutation(n)
+        fixed[slots] = True
+    for _ in range(200):
+        key = rows * n + cols
+        order = np.argsort(key, kind="stable")
+        ks = key[order]
+        dup_pos = np.flatnonzero(ks[1:] == ks[:-1])
+        if dup_pos.size == 0:
+            break
+        # of each equal pair redraw the member that is not a guaranteed slot
+        a, b = order[dup_pos], order[dup_pos + 1]
+        redo = np.where(fixed[b], a, b)
+        redo = np.unique(redo)
+        cols[redo] = draw(redo.size)
+    else:
+        raise RuntimeError("column assignment did not converge")
+    return ptr, rows, cols
+
+
+def skewed(seed: int = 0, m: int = 2_000_000, n: int = 3_000_000, target_nnz: int = 20_000_000,
+           row_s: float = 2.0, row_cap: int = 500_000, col_s: float = 1.8,
+           eq_frac: float = 0.3, inf_frac: float = 0.2, singleton_frac: float = 0.05,
+           redundant_frac: float = 0.03) -> LP:
+    """The skewed large LP: row lengths 1 + Zipf(2) capped, column weights
+    Zipf(1.8), values lognormal(0,1) with a random sign, 30% equality rows,
+    each bound infinite with probability 0.2, 5% singleton rows and 3% rows
+    planted redundant.  The actual nnz is reported by ``LP.nnz``."""
+    rng = np.random.default_rng(seed)
+    lengths = 1 + _zipf_capped(rng, row_s, m, row_cap)
+    total = lengths.sum()
+    if total < target_nnz:  # stretch the long rows towards the target size
+        f = target_nnz / total
+        lengths = np.where(lengths > 2, np.minimum(np.rint(lengths * f).astype(np.int64), row_cap), lengths)
+    lengths = np.minimum(lengths, n)
+    single = rng.random(m) < singleton_frac
+    lengths[single] = 1
+    ptr, rows, cols = _assign_columns(rng, lengths, n, col_s, max(2, m // 4))
+    order = np.lexsort((cols, rows))
+    cols = cols[order]
+    nnz = int(ptr[-1])
+    vals = rng.lognormal(0.0, 1.0, nnz) * np.where(rng.random(nnz) < 0.5, -1.0, 1.0)
+
+    lb = -rng.uniform(0.0, 10.0, n)
+    ub = rng.uniform(1.0, 100.0, n)
+    lb[rng.random(n) < inf_frac] = -INF
+    ub[rng.random(n) < inf_frac] = INF
+    x0 = _point_in_box(rng, lb, ub)
+    ax = _dot_rows(ptr, cols, vals, x0, m)
+    eq = rng.random(m) < eq_frac
+    lhs, rhs = _sides_around(rng, ax, eq)
+
+    # planted redundant rows: one-sided rows whose rhs exceeds a crude bound
+    # sum |a_k| |b_k| over the bound b_k that caps a_k x_k from above
+    need = np.where(vals > 0, ub[cols], lb[cols])
+    ok_entry = np.isfinite(need)
+    row_ok = np.bincount(rows, weights=ok_entry.astype(np.float64), minlength=m) == lengths
+    cand = np.flatnonzero(row_ok & (lengths >= 2))
+    k = min(len(cand), int(round(redundant_frac * m)))
+    red = rng.choice(cand, size=k, replace=False) if k else np.zeros(0, np.int64)
+    crude = np.bincount(rows, weights=np.where(ok_entry, np.abs(vals * need), 0.0), minlength=m)
+    margin = 1.0 + rng.uniform(0.0, 1.0, m) * crude
+    rhs[red] = crude[red] + margin[red]
+    lhs[red] = -INF
+    c = _cost(rng, lb, ub)
+    planted = dict(singleton=int(single.sum()), redundant=int(k), x0=x0)
+    return _finish(m, n, ptr, cols, vals, c, lhs, rhs, lb, ub, planted, f"skewed-{seed}")
+
+
+# ----------------------------------------------------------- LP-relaxation-like
+def lprelax(seed: int = 0, m: int = 500_000, n: int = 1_000_000, target_nnz: int = 8_000_000,
+            n_dense: int = 10, dense_len: int = 200_000, parallel_frac: float = 0.05,
+            doubleton_frac: float = 0.04, dominated_frac: float = 0.02) -> LP:
+    """LP-relaxation-like: ``n_dense`` dense columns of ``dense_len`` entries,
+    5% of rows scaled copies of other rows (factor U[0.5,4], random sign),
+    4% doubleton equations, 2% columns with a loose explicit upper bound that
+    one of their rows implies much tighter (dominated bounds)."""
+    rng = np.random.default_rng(seed)
+    dense_len = min(dense_len, m)
+    n_par = int(round(parallel_frac * m))
+    n_dbl = int(round(doubleton_frac * m))
+    n_src = m - n_par
+    sparse_nnz = max(target_nnz - n_dense * dense_len, 2 * m)
+    # the sparse part: lengths 2 + Poisson, doubletons exactly 2
+    mean_len = sparse_nnz / m
+    lengths = 2 + rng.poisson(max(mean_len - 2.0, 0.0), n_src)
+    dbl = rng.choice(n_src, size=n_dbl, replace=False)
+    lengths[dbl] = 2
+    rows_s = np.repeat(np.arange(n_src, dtype=np.int64), lengths)
+    cols_s = rng.integers(n_dense, n, rows_s.size)
+    # dense columns 0..n_dense-1 hit dense_len random source rows each
+    drows = np.concatenate([rng.choice(n_src, size=dense_len, replace=False) for _ in range(n_dense)]) \
+        if n_dense else np.zeros(0, np.int64)
+    dcols = np.repeat(np.arange(n_dense, dtype=np.int64), dense_len)
+    is_dbl = np.zeros(n_src, dtype=bool)
+    is_dbl[dbl] = True
+    keep_d = ~is_dbl[drows]  # doubletons keep exactly two entries
+    rows_all = np.concatenate([rows_s, drows[keep_d]])
+    cols_all = np.concatenate([cols_s, dcols[keep_d]])
+    key = np.unique(rows_all * n + cols_all)  # drop repeated (row, col)
+    rows_all, cols_all = key // n, key % n
+    # doubleton rows may have lost an entry to a repeat: give them a fresh one
+    cnt = np.bincount(rows_all, minlength=n_src)
+    short = np.flatnonzero(cnt < 2)
+    if short.size:
+        extra_c = rng.integers(n_dense, n, short.size)
+        have = {int(r): int(c) for r, c in zip(rows_all, cols_all) if cnt[r] < 2}
+        for idx, r in enumerate(short):
+            if have.get(int(r)) == int(extra_c[idx]):
+                extra_c[idx] = n_dense + (int(extra_c[idx]) + 1 - n_dense) % (n - n_dense)
+        rows_all = np.concatenate([rows_all, short])
+        cols_all = np.concatenate([cols_all, extra_c])
+    vals_all = rng.lognormal(0.0, 1.0, rows_all.size) * np.where(rng.random(rows_all.size) < 0.5, -1.0, 1.0)
+    ptr_s, cols_s2, vals_s2 = _sort_rows(rows_all, cols_all, vals_all, n_src)
+    # parallel copies of random non-doubleton source rows
+    src = rng.choice(np.flatnonzero(~is_dbl), size=n_par, replace=False)
+    lam = rng.uniform(0.5, 4.0, n_par) * np.where(rng.random(n_par) < 0.5, -1.0, 1.0)
+    lens_src = np.diff(ptr_s)
+    rows_list = [np.repeat(np.arange(n_src, dtype=np.int64), lens_src)]
+    cols_list = [cols_s2]
+    vals_list = [vals_s2]
+    cp_len = lens_src[src]
+    starts = ptr_s[src]
+    idx = np.repeat(starts - np.concatenate(([0], np.cumsum(cp_len)[:-1])), cp_len) + np.arange(cp_len.sum())
+    rows_list.append(np.repeat(np.arange(n_src, m, dtype=np.int64), cp_len))
+    cols_list.append(cols_s2[idx])
+    vals_list.append(vals_s2[idx] * np.repeat(lam, cp_len))
+    rows = np.concatenate(rows_list)
+    cols = np.concatenate(cols_list)
+    vals = np.concatenate(vals_list)
+    perm = rng.permutation(m)  # scatter the copies among the rows
+    rows = perm[rows]
+    ptr, cols, vals = _sort_rows(rows, cols, vals, m)
+
+    lb = np.zeros(n)
+    ub = rng.uniform(1.0, 100.0, n)
+    ub[rng.random(n) < 0.1] = INF
+    x0 = _point_in_box(rng, lb, ub)
+    ax = _dot_rows(ptr, cols, vals, x0, m)
+    eq = rng.random(m) < 0.3
+    eq[perm[dbl]] = True
+    eq[perm[np.arange(n_src, m)]] = eq[perm[src]]  # a copy has the kind of its source
+    lhs, rhs = _sides_around(rng, ax, eq)
+    # dominated bounds: loosen the explicit upper bound by a large factor
+    dom = rng.choice(np.arange(n_dense, n), size=int(round(dominated_frac * n)), replace=False)
+    ub[dom] = np.where(np.isfinite(ub[dom]), ub[dom] * 1e3, ub[dom])
+    c = _cost(rng, lb, ub)
+    planted = dict(parallel=n_par, doubleton=n_dbl, dominated=len(dom), x0=x0)
+    return _finish(m, n, ptr, cols, vals, c, lhs, rhs, lb, ub, planted, f"lprelax-{seed}")
+
+
+# ------------------------------------------------------------------- batches
+def batch(seed: int = 0, count: int = 4096, m_lo: int = 50, m_hi: int = 5000,
+          nnz_per_row: float = 6.0) -> list[LP]:
+    """Ragged batch: m log-uniform in [m_lo, m_hi], n = 1.5 m, about
+    ``nnz_per_row`` entries per row, the planted mix of ``tiny`` scaled by
+    m/200.  LP k uses seed ``seed * 1_000_003 + k``."""
+    rng = np.random.default_rng(seed)
+    ms = np.exp(rng.uniform(np.log(m_lo), np.log(m_hi), count)).astype(np.int64)
+    out = []
+    for k, m in enumerate(ms):
+        f = m / 200.0
+        out.append(tiny(seed * 1_000_003 + k, m=int(m), n=int(1.5 * m), mean_len=nnz_per_row,
+                        n_empty=max(1, int(10 * f)), n_single=max(1, int(15 * f)),
+                        n_fixed=max(1, int(20 * f)), n_redundant=max(1, int(10 * f)),
+                        n_parallel=max(1, int(8 * f))))
+    return out
+
+
+def serve_stream(seed: int = 0, count: int = 2000, nnz_lo: float = 1e3, nnz_hi: float = 1e7,
+                 rate_per_s: float = 100.0):
+    """Arrival trace: Poisson arrivals (exponential gaps at ``rate_per_s``),
+    per-request nnz log-uniform in [nnz_lo, nnz_hi]; request k is the skewed
+    LP with m = nnz/10, n = 1.5 m and seed ``seed * 1_000_003 + k``.
+    Returns a list of (arrival_time_s, nnz, seed) and leaves building the LPs
+    to the caller (see ``skewed_like``)."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate_per_s, count)
+    t = np.cumsum(gaps)
+    nnz = np.exp(rng.uniform(np.log(nnz_lo), np.log(nnz_hi), count)).astype(np.int64)
+    return [(float(t[k]), int(nnz[k]), seed * 1_000_003 + k) for k in range(count)]
+
+
+def skewed_like(seed: int, nnz: int) -> LP:
+    """A skewed LP with about ``nnz`` entries, m = nnz/10, n = 1.5 m."""
+    m = max(10, nnz // 10)
+    n = max(15, int(1.5 * m))
+    return skewed(seed, m=m, n=n, target_nnz=nnz, row_cap=max(2, min(500_000, m // 4)))
+
+
+# --------------------------------------------------------------------- micro
+def micro(seed: int, m: int = 5, n: int = 6, slack: float = 0.5) -> LP:
+    """A very small LP with every bound finite (for brute-force vertex
+    enumeration): dense-ish random rows, tight sides (slack U[0, slack]),
+    and, drawn at random, a fixed column, a singleton row, an empty row, a
+    scaled copy of a row and a row far from binding."""
+    rng = np.random.default_rng(seed)
+    lb = -rng.uniform(0.0, 5.0, n)
+    ub = lb + rng.uniform(0.5, 5.0, n)
+    if rng.random() < 0.5:
+        j = rng.integers(0, n)
+        ub[j] = lb[j]
+    x0 = _point_in_box(rng, lb, ub)
+    rows_cols, rows_vals = [], []
+    kinds = rng.choice(["base", "base", "base", "single", "empty", "copy", "loose"], size=m)
+    for i in range(m):
+        k = kinds[i]
+        if k == "single":
+            cols = np.array([rng.integers(0, n)])
+        elif k == "empty":
+            cols = np.zeros(0, np.int64)
+        elif k == "copy" and i > 0 and len(rows_cols[i - 1]) >= 2:
+            rows_cols.append(rows_cols[i - 1].copy())
+            rows_vals.append(rows_vals[i - 1] * rng.uniform(0.5, 4.0) * rng.choice([-1.0, 1.0]))
+            continue
+        else:
+            ln = int(rng.integers(2, n + 1))
+            cols = np.sort(rng.choice(n, size=ln, replace=False))
+        rows_cols.append(cols)
+        rows_vals.append(_draw_magnitudes(rng, len(cols), -5.0, 5.0))
+    lengths = np.array([len(c) for c in rows_cols], dtype=np.int64)
+    ptr = _ptr_from_lengths(lengths)
+    cols = np.concatenate(rows_cols).astype(np.int64) if ptr[-1] else np.zeros(0, np.int64)
+    vals = np.concatenate(rows_vals) if ptr[-1] else np.zeros(0)
+    ax = _dot_rows(ptr, cols, vals, x0, m)
+    lhs = ax - rng.uniform(0.0, slack, m)
+    rhs = ax + rng.uniform(0.0, slack, m)
+    eq = rng.random(m) < 0.3
+    lhs[eq] = ax[eq]
+    rhs[eq] = ax[eq]
+    one = rng.random(m) < 0.3
+    lhs[one & ~eq] = -INF
+    loose = kinds == "loose"
+    rhs[loose] = ax[loose] + 1e3
+    lhs[loose] = ax[loose] - 1e3
+    empty = lengths == 0
+    lhs[empty] = np.minimum(lhs[empty], 0.0)
+    rhs[empty] = np.maximum(rhs[empty], 0.0)
+    c = _cost(rng, lb, ub)
+    return _finish(m, n, ptr, cols, vals, c, lhs, rhs, lb, ub, dict(x0=x0, kinds=kinds), f"micro-{seed}")
