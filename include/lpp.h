@@ -1,0 +1,223 @@
+/*
+ * lpp.h -- C ABI of the GB300 LP presolve library (liblpp.so).
+ *
+ * The library presolves linear programs of the form (Cederberg & Boyd,
+ * "GPU-Accelerated Presolving for Linear Programming", Sec. 2.1, Eq. 1)
+ *
+ *     minimize    c^T x
+ *     subject to  lhs <= A x <= rhs
+ *                 lb  <=  x  <= ub
+ *
+ * with A an m x n sparse matrix in CSR form.  Infinite entries are allowed in
+ * lhs, rhs, lb and ub; any value with |v| >= opts.huge is treated as +-inf.
+ * An equality row has lhs == rhs.
+ *
+ * Presolve runs in rounds until a round changes nothing or opts.max_rounds
+ * rounds have run (Sec. 3.1).  Each round, on the GPU:
+ *   S1  row min/max activities with separate counts of infinite terms (Sec. 3.1)
+ *   S2  removal of empty, redundant and singleton rows; infeasibility checks
+ *   S3  activity-based bound tightening, Jacobi form (Sec. 3.1)
+ *   S4  fixing of variables whose bounds meet (Sec. 2.1, "fixing a variable")
+ *   S5  parallel rows by hashing plus a leader check (Sec. 3.2)
+ *   S6  empty columns fixed at the bound their cost prefers (dual rule)
+ *   S7  compaction of the CSR and CSC matrices and of all row/column vectors
+ * The reduced LP has the same form (Sec. 3.3) and stays in device memory; the
+ * postsolve record (Sec. 2.1, postsolver; Sec. 3.3) lives on the host.
+ *
+ * All floating point is IEEE binary64; all index work is exact int32/int64.
+ *
+ * Error behaviour: every entry point returns an lpp_status and never throws.
+ * LPP_INFEASIBLE and LPP_UNBOUNDED are results, not errors: the postsolve
+ * record then holds where (row or column, original index) and in which round
+ * the verdict was reached.  Negative values are errors; lpp_last_error()
+ * returns a message for the calling thread's most recent error.
+ *
+ * Ownership: input arrays are borrowed, read only, and may be freed after the
+ * call returns.  Every object the library returns is owned by the library and
+ * released with the matching lpp_free_* / lpp_server_destroy call.  Pointers
+ * returned by accessors stay valid until their owning object is freed.
+ *
+ * Threads: calls on different objects may run concurrently from different
+ * host threads; one object must not be used by two threads at once.
+ */
+#ifndef LPP_H
+#define LPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LPP_ABI_VERSION 1
+
+typedef enum lpp_status {
+    LPP_OK = 0,
+    LPP_INFEASIBLE = 1,    /* a row or column proves the LP infeasible            */
+    LPP_UNBOUNDED = 2,     /* an empty column can decrease the cost without limit */
+    LPP_ERR_INVALID = -1,  /* malformed input (see lpp_presolve)                  */
+    LPP_ERR_OOM = -2,      /* device or host allocation failed                    */
+    LPP_ERR_CUDA = -3,     /* a CUDA call failed (message in lpp_last_error)      */
+    LPP_ERR_TIMEOUT = -4,  /* a bounded device wait gave up                       */
+    LPP_ERR_BUDGET = -5    /* a request does not fit the server's memory budget   */
+} lpp_status;
+
+/* Per-original-row record kinds (what removed the row). */
+#define LPP_ROW_KEPT 0
+#define LPP_ROW_EMPTY 1       /* no entry, sides contain 0                        */
+#define LPP_ROW_REDUNDANT 2   /* activities lie inside the sides                  */
+#define LPP_ROW_SINGLETON 3   /* one entry: turned into a bound on that column    */
+#define LPP_ROW_PARALLEL 4    /* a multiple of a leader row, sides merged into it */
+/* Per-original-column record kinds. */
+#define LPP_COL_KEPT 0
+#define LPP_COL_FIXED 1       /* lb == ub: fixed at that value (primal)           */
+#define LPP_COL_EMPTY 2       /* no entry left: fixed at the cheaper bound (dual) */
+/* Where a verdict was found. */
+#define LPP_WHERE_NONE 0
+#define LPP_WHERE_ROW 1
+#define LPP_WHERE_COL 2
+
+/* An LP of Eq. 1 in CSR form.
+ *   row_ptr[m+1], col_idx[nnz] int32; col_idx strictly increasing within a row,
+ *   in [0, n); val[nnz] finite and nonzero; c[n] finite; lhs/rhs[m] and
+ *   lb/ub[n] may be +-inf, lhs != +inf, rhs != -inf, lb != +inf, ub != -inf.
+ *   nnz < 2^31.  on_device = 1: all pointers are CUDA device pointers;
+ *   on_device = 0: host pointers (copied to the device inside the call). */
+typedef struct lpp_lp {
+    int32_t m, n;
+    int64_t nnz;
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+    const double *val;
+    const double *c, *lhs, *rhs, *lb, *ub;
+    double obj_offset;
+    int32_t on_device;
+} lpp_lp;
+
+/* Options; lpp_opts_default() fills the defaults given in brackets. */
+typedef struct lpp_opts {
+    double feas_tol;        /* [1e-9]  tolerance of side/bound comparisons, times max(1,|x|) */
+    double bound_tol;       /* [1e-6]  relative improvement a new implied bound must reach  */
+    double huge;            /* [1e20]  |v| >= huge means infinite                            */
+    double max_implied;     /* [1e10]  implied bounds larger in magnitude are dropped        */
+    double par_tol;         /* [1e-12] relative tolerance of the parallel-row check          */
+    int32_t max_rounds;     /* [20]    round cap                                             */
+    int32_t dual_reductions;/* [1]     enable S6 (empty columns)                             */
+    int32_t par_max_iter;   /* [16]    leader passes per group of equal keys (S5)            */
+    int32_t timing;         /* [0]     1: time every kernel launch with CUDA events           */
+    int32_t device;         /* [0]     CUDA device ordinal                                   */
+    void *stream;           /* [NULL]  cudaStream_t to run on; NULL: a library-owned stream  */
+} lpp_opts;
+
+typedef struct lpp_reduced lpp_reduced;     /* reduced LP, device resident */
+typedef struct lpp_postsolve lpp_postsolve; /* verdict, records, counters; host resident */
+
+/* Summary of one presolve. */
+typedef struct lpp_info {
+    int32_t status;       /* lpp_status of the presolve result (OK / INFEASIBLE / UNBOUNDED) */
+    int32_t where;        /* LPP_WHERE_* of a verdict                                     */
+    int32_t index;        /* original row or column index of a verdict, else -1           */
+    int32_t round;        /* round of a verdict (1-based), else 0                         */
+    int32_t rounds;       /* rounds executed                                              */
+    int32_t m, n;         /* original sizes                                               */
+    int32_t m_red, n_red; /* reduced sizes                                                */
+    int64_t nnz, nnz_red;
+    double obj_offset;    /* constant to add to c_red^T x_red                             */
+    double presolve_ms;   /* device time of the round loop (transfers excluded)          */
+    int64_t nnz_processed;/* sum over rounds of the nonzeros present at the round start  */
+} lpp_info;
+
+/* Time and traffic of one kernel family, summed over its launches
+   (filled only when opts.timing = 1). */
+typedef struct lpp_kernel_stat {
+    char name[32];
+    int32_t launches;
+    double ms;            /* summed CUDA-event time of its launches               */
+    double bytes;         /* algorithmic DRAM bytes of those launches             */
+} lpp_kernel_stat;
+
+void lpp_opts_default(lpp_opts *opts);
+
+/* Presolve one LP (Sec. 3.3: an LP of the form (1) in, a reduced LP of the
+ * same form out).  `in` is validated first (LPP_ERR_INVALID on a malformed
+ * CSR, explicit zeros, non-finite coefficients or costs, NaN sides/bounds,
+ * lhs = +inf, rhs = -inf, lb = +inf, ub = -inf, nnz >= 2^31).  On any status
+ * >= 0 *out and *rec are set and must be freed by the caller. */
+lpp_status lpp_presolve(const lpp_lp *in, const lpp_opts *opts, lpp_reduced **out, lpp_postsolve **rec);
+
+/* Reduced LP as an lpp_lp.  on_device = 1: device pointers into the reduced
+ * object; on_device = 0: host copies owned by the reduced object. */
+lpp_status lpp_reduced_view(lpp_reduced *red, lpp_lp *view, int32_t on_device);
+/* A^T of the reduced LP in CSR form (= CSC of A), device pointers:
+ * col_ptr[n_red+1], row_idx[nnz_red] (increasing within a column), val[nnz_red]. */
+lpp_status lpp_reduced_csc(const lpp_reduced *red, const int32_t **col_ptr, const int32_t **row_idx,
+                           const double **val);
+/* Maps reduced -> original index, device pointers: row_map[m_red], col_map[n_red]. */
+lpp_status lpp_reduced_maps(const lpp_reduced *red, const int32_t **row_map, const int32_t **col_map);
+
+lpp_status lpp_result_info(const lpp_postsolve *rec, lpp_info *info);
+/* Per original row (host arrays of m): record kind, round, aux (singleton:
+ * its column; parallel: its leader row, original indices; else -1), value
+ * (singleton: its coefficient; parallel: lambda with row = lambda * leader). */
+lpp_status lpp_result_rows(const lpp_postsolve *rec, int32_t *kind, int32_t *round, int32_t *aux, double *val);
+/* Per original column (host arrays of n): kind, round, fixed value, and the
+ * final bounds (a fixed column reports its value as both bounds). */
+lpp_status lpp_result_cols(const lpp_postsolve *rec, int32_t *kind, int32_t *round, double *val, double *lb,
+                           double *ub);
+/* Activities of the last executed round per original row (host arrays of m);
+ * rows not present at that round's start get NaN and -1. */
+lpp_status lpp_result_activity(const lpp_postsolve *rec, double *act_min, double *act_max, int32_t *ninf_min,
+                               int32_t *ninf_max);
+/* Per-round counters (arrays of cap entries; any pointer may be NULL):
+ * nonzeros at the round start, rows removed, columns fixed, bounds changed,
+ * device milliseconds of the round.  Returns the round count in *rounds. */
+lpp_status lpp_result_rounds(const lpp_postsolve *rec, int32_t cap, int64_t *nnz, int32_t *rows_removed,
+                             int32_t *cols_fixed, int32_t *bounds_changed, float *ms, int32_t *rounds);
+/* Kernel statistics (opts.timing = 1): up to cap entries, count in *count. */
+lpp_status lpp_result_kernels(const lpp_postsolve *rec, int32_t cap, lpp_kernel_stat *stats, int32_t *count);
+
+/* Primal postsolve on the CPU (Sec. 2.1 postsolver; Sec. 3.3): x_red[n_red]
+ * -> x_orig[n] (host arrays): kept columns take their reduced value, fixed
+ * columns their recorded value. */
+lpp_status lpp_postsolve_primal(const lpp_postsolve *rec, const double *x_red, double *x_orig);
+
+void lpp_free_reduced(lpp_reduced *red);
+void lpp_free_postsolve(lpp_postsolve *rec);
+const char *lpp_last_error(void);
+
+/* Batched presolve: `count` independent LPs (all host or all device inputs)
+ * presolved together in one device arena, each round one set of launches for
+ * all LPs, the round sequence captured once in a CUDA graph and replayed.
+ * Each LP gets the result it would get alone.  outs[k], recs[k], per_lp[k]
+ * as for lpp_presolve.  Returns LPP_OK unless the batch itself failed. */
+lpp_status lpp_presolve_batch(const lpp_lp *ins, int32_t count, const lpp_opts *opts, lpp_reduced **outs,
+                              lpp_postsolve **recs, lpp_status *per_lp);
+
+/* Serving: a request loop on one device with continuous batching.
+ * lpp_server_create reserves nothing up front; hbm_budget bounds the device
+ * memory that resident LPs may hold.  submit copies the LP (host or device
+ * input) into a queue and returns a ticket; a worker thread admits queued
+ * LPs while they fit the budget, runs one presolve round over all resident
+ * unfinished LPs per tick, and keeps finished LPs resident until taken.
+ * take waits up to wait_ms (-1 = forever) for the ticket's result
+ * (LPP_ERR_TIMEOUT if not ready) and hands over the reduced LP and record. */
+typedef struct lpp_server lpp_server;
+typedef struct lpp_server_stats {
+    int64_t submitted, admitted, finished, taken;
+    int64_t ticks;          /* batched rounds run                    */
+    int64_t resident_bytes; /* device bytes held by resident LPs now */
+    int64_t peak_resident_bytes;
+    int32_t max_concurrent; /* most LPs resident in one tick         */
+} lpp_server_stats;
+lpp_status lpp_server_create(size_t hbm_budget, const lpp_opts *opts, lpp_server **srv);
+lpp_status lpp_server_submit(lpp_server *srv, const lpp_lp *lp, uint64_t *ticket);
+lpp_status lpp_server_take(lpp_server *srv, uint64_t ticket, int32_t wait_ms, lpp_reduced **out,
+                           lpp_postsolve **rec);
+lpp_status lpp_server_stats_get(lpp_server *srv, lpp_server_stats *stats);
+void lpp_server_destroy(lpp_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -54,8 +54,7 @@ void lppo_opts_default(lppo_opts *o)
     o->par_tol = 1e-12;
     o->max_rounds = 20;
     o->dual_reductions = 1;
-    o->hash_qbits = 20;
-    o->par_max_iter = 8;
+    o->par_max_iter = 16;
 }
 
 /* ---------------------------------------------------------------- audit */
@@ -74,10 +73,11 @@ static void audit(audit_t *a, double margin, double eb)
     if (r < 1e3) a->below++;
 }
 
-/* error bound of a sum of `cnt` terms with absolute sum `s`, the terms being
-   rounded products that both sides compute identically: any two summation
-   orders differ by at most (cnt-1) * u * s (two terms commute exactly). */
-static double sum_eb(int64_t cnt, double s) { return cnt >= 3 ? (double)(cnt - 1) * UROUND * s : 0.0; }
+/* bound on the difference between two evaluations of a sum of `cnt`
+   products with absolute sum `s`, in any order, each product either rounded
+   on its own or fused into the addition: 2 * cnt * u * s.  A single product
+   is computed identically either way. */
+static double sum_eb(int64_t cnt, double s) { return cnt >= 2 ? 2.0 * (double)cnt * UROUND * s : 0.0; }
 
 /* ---------------------------------------------------------------- input */
 static double norm_inf(double x, double huge)
@@ -161,25 +161,19 @@ int lppo_activities(const lppo_lp *lp, double huge, double *act_min, double *act
 }
 
 /* ------------------------------------------------------- S5 key ordering
- * Key of a row for parallel-row grouping (Sec. 3.2): its length, its column
- * pattern and its coefficients normalised by the first one and rounded to
- * qbits mantissa bits.  Rows are grouped by exact key equality. */
+ * Key of a row for parallel-row grouping (Sec. 3.2, two-level hash on the
+ * pattern and the coefficients): its length, its column pattern, and for
+ * each coefficient whether its sign differs from the sign of the first one.
+ * The sign pattern is the part of the coefficients that is exactly invariant
+ * under scaling by any lambda != 0, so a_i and lambda*a_i always share a key.
+ * Rows are grouped by exact key equality. */
 typedef struct {
     int32_t row, len;
     const int32_t *cols;
-    const uint64_t *q;
+    const uint64_t *q;  /* 1 where the sign differs from the first coefficient's */
 } pkey_t;
 
-static uint64_t quantise(double x, int qbits)
-{
-    uint64_t b;
-    int drop = 52 - qbits;
-    memcpy(&b, &x, sizeof b);
-    if (drop <= 0) return b;
-    b += (uint64_t)1 << (drop - 1);        /* round to nearest on the bit pattern */
-    b &= ~(((uint64_t)1 << drop) - 1);
-    return b;
-}
+static uint64_t rel_sign(double a, double a0) { return (a < 0) != (a0 < 0); }
 
 static int cmp_key(const void *pa, const void *pb)
 {
@@ -374,13 +368,13 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                 else {
                     rmin_ok = nmn[i] == 0;
                     rmin = mna[i] - a * bmin;
-                    eb_rmin = ebmn[i] + fabs(a) * ebbmin + UROUND * fabs(rmin);
+                    eb_rmin = ebmn[i] + fabs(a) * ebbmin + UROUND * (fabs(rmin) + fabs(a * bmin));
                 }
                 if (!isfin(bmax)) { rmax_ok = nmx[i] == 1; rmax = mxa[i]; eb_rmax = ebmx[i]; }
                 else {
                     rmax_ok = nmx[i] == 0;
                     rmax = mxa[i] - a * bmax;
-                    eb_rmax = ebmx[i] + fabs(a) * ebbmax + UROUND * fabs(rmax);
+                    eb_rmax = ebmx[i] + fabs(a) * ebbmax + UROUND * (fabs(rmax) + fabs(a * bmax));
                 }
                 /* a x_j <= U - rmin  and  a x_j >= L - rmax */
                 if (isfin(U) && rmin_ok) {
@@ -482,7 +476,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                     keys[np].row = i; keys[np].len = len;
                     keys[np].cols = s.ci + s.rp[i];
                     keys[np].q = qbuf + qo;
-                    for (k = s.rp[i]; k < s.rp[i + 1]; k++) qbuf[qo++] = quantise(s.v[k] / a0, o->hash_qbits);
+                    for (k = s.rp[i]; k < s.rp[i + 1]; k++) qbuf[qo++] = rel_sign(s.v[k], a0);
                     np++;
                 }
             }

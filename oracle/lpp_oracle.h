@@ -66,8 +66,7 @@ typedef struct {
     double  par_tol;       /* 1e-12 */
     int32_t max_rounds;    /* 20    */
     int32_t dual_reductions; /* 1   */
-    int32_t hash_qbits;    /* 20    */
-    int32_t par_max_iter;  /* 8     */
+    int32_t par_max_iter;  /* 16    */
 } lppo_opts;
 
 /* All arrays are allocated by the caller with the sizes given. */

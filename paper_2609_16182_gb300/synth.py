@@ -241,7 +241,9 @@ def _assign_columns(rng, lengths, n, col_weight_s, weight_cap):
     """Configuration model: every column gets one entry first (so no column
     starts empty), the other entries pick a column with probability
     proportional to a Zipf(col_weight_s) weight; a column drawn twice in one
-    row is drawn again until every row holds distinct columns."""
+    row is drawn again (by weight for three passes, then uniformly, so that
+    long rows that already hold every heavy column settle quickly) until
+    every row holds distinct columns."""
     m = len(lengths)
     ptr = _ptr_from_lengths(lengths)
     nnz = int(ptr[-1])
@@ -259,7 +261,7 @@ def _assign_columns(rng, lengths, n, col_weight_s, weight_cap):
         slots = rng.choice(nnz, size=n, replace=False)
         cols[slots] = rng.permutation(n)
         fixed[slots] = True
-    for _ in range(200):
+    for it in range(200):
         key = rows * n + cols
         order = np.argsort(key, kind="stable")
         ks = key[order]
@@ -270,7 +272,7 @@ def _assign_columns(rng, lengths, n, col_weight_s, weight_cap):
         a, b = order[dup_pos], order[dup_pos + 1]
         redo = np.where(fixed[b], a, b)
         redo = np.unique(redo)
-        cols[redo] = draw(redo.size)
+        cols[redo] = draw(redo.size) if it < 3 else rng.integers(0, n, redo.size)
     else:
         raise RuntimeError("column assignment did not converge")
     return ptr, rows, cols
