@@ -149,12 +149,14 @@ lpp_status lpp_presolve(const lpp_lp *in, const lpp_opts *opts, lpp_reduced **ou
 /* Reduced LP as an lpp_lp.  on_device = 1: device pointers into the reduced
  * object; on_device = 0: host copies owned by the reduced object. */
 lpp_status lpp_reduced_view(lpp_reduced *red, lpp_lp *view, int32_t on_device);
-/* A^T of the reduced LP in CSR form (= CSC of A), device pointers:
- * col_ptr[n_red+1], row_idx[nnz_red] (increasing within a column), val[nnz_red]. */
-lpp_status lpp_reduced_csc(const lpp_reduced *red, const int32_t **col_ptr, const int32_t **row_idx,
-                           const double **val);
-/* Maps reduced -> original index, device pointers: row_map[m_red], col_map[n_red]. */
-lpp_status lpp_reduced_maps(const lpp_reduced *red, const int32_t **row_map, const int32_t **col_map);
+/* A^T of the reduced LP in CSR form (= CSC of A): col_ptr[n_red+1],
+ * row_idx[nnz_red] (increasing within a column), val[nnz_red].
+ * on_device = 1: device pointers; 0: host copies owned by the reduced object. */
+lpp_status lpp_reduced_csc(lpp_reduced *red, const int32_t **col_ptr, const int32_t **row_idx, const double **val,
+                           int32_t on_device);
+/* Maps reduced -> original index: row_map[m_red], col_map[n_red]
+ * (on_device as for lpp_reduced_csc). */
+lpp_status lpp_reduced_maps(lpp_reduced *red, const int32_t **row_map, const int32_t **col_map, int32_t on_device);
 
 lpp_status lpp_result_info(const lpp_postsolve *rec, lpp_info *info);
 /* Per original row (host arrays of m): record kind, round, aux (singleton:

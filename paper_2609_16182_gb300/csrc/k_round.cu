@@ -1,0 +1,625 @@
+// k_round.cu -- the kernels of one presolve round up to compaction:
+//   S1 activities, S2 row classes, S3 implied bounds (fused, one pass over the
+//   CSR), S3'/S4 bound finalisation and fixing, S5 parallel rows.
+//
+// Load balance (Sec. 3.1, "length-based load balancing"): rows are grouped
+// by length class.  Class c <= 5 gives each row a group of W = 2^c lanes of a
+// warp (lane t walks entries t, t+W, ...; the group then reduces with an xor
+// butterfly), class 6 (more than 4096 entries) splits the row into chunks of
+// 4096 entries, one thread block each, whose partial results are combined in
+// chunk order.  The order of every floating-point sum depends only on the
+// row's own length.
+//
+// Bound tightening follows Sec. 3.1 in Jacobi form: activities and the
+// acceptance tests read the bounds of the round start, accepted implied
+// bounds are combined with atomicMin / atomicMax on an order-preserving
+// integer encoding, which is exact and independent of the order of updates.
+//
+// FP64 is scarce on this GPU (about two DFMA per SM and clock), so every
+// per-entry sign, finiteness and max(1,|x|) test runs on integer pipes, the
+// activity sums are fused multiply-adds, and an implied bound is divided out
+// only after an exact FMA sign test (x - thr*a) says it will be accepted.
+#include "lpp_launch.h"
+
+namespace lpp {
+
+namespace {
+
+__device__ __forceinline__ double pinf() { return __longlong_as_double(0x7ff0000000000000LL); }
+__device__ __forceinline__ double ninf_() { return __longlong_as_double((long long)0xfff0000000000000ULL); }
+
+__device__ __forceinline__ int32_t lp_of_row(const Ctx &C, int32_t i) { return C.lp_row ? C.lp_row[i] : 0; }
+__device__ __forceinline__ int32_t lp_of_col(const Ctx &C, int32_t j) { return C.lp_col ? C.lp_col[j] : 0; }
+
+// Implied upper bound x/a on column j (from a*x_j <= x with a > 0, or
+// a*x_j >= x with a < 0).  Accepted iff |x/a| <= max_implied and
+// (uold = +inf or x/a < uold - bound_tol*max(1,|uold|)).  Both tests are
+// decided exactly on the real quotient by the sign of one fused multiply-add.
+__device__ __forceinline__ void try_upper(const Ctx &C, int32_t j, double x, double a, double uold) {
+    if (fma(-C.max_implied, fabs(a), fabs(x)) > 0.0) return;
+    if (is_fin(uold)) {
+        const double thr = uold - C.bound_tol * max1abs(uold);
+        const double s = fma(-thr, a, x);
+        if (is_neg(a) ? !(s > 0.0) : !(s < 0.0)) return;
+    }
+    atomic_min_dbl(&C.cand_u[j], x / a);
+}
+// Implied lower bound x/a: accepted iff |x/a| <= max_implied and
+// (lold = -inf or x/a > lold + bound_tol*max(1,|lold|)).
+__device__ __forceinline__ void try_lower(const Ctx &C, int32_t j, double x, double a, double lold) {
+    if (fma(-C.max_implied, fabs(a), fabs(x)) > 0.0) return;
+    if (is_fin(lold)) {
+        const double thr = lold + C.bound_tol * max1abs(lold);
+        const double s = fma(-thr, a, x);
+        if (is_neg(a) ? !(s < 0.0) : !(s > 0.0)) return;
+    }
+    atomic_max_dbl(&C.cand_l[j], x / a);
+}
+
+// candidates of one entry (S3); smin/smax, nmin/nmax are the row's activities
+__device__ __forceinline__ void tighten_entry(const Ctx &C, int32_t j, double a, double Lv, double Uv, bool up_row,
+                                              bool lo_row, double smin, double smax, int nmin, int nmax) {
+    const double2 b = C.lu[j];
+    const bool neg = is_neg(a);
+    const double bmin = neg ? b.y : b.x, bmax = neg ? b.x : b.y;
+    const bool fmn = is_fin(bmin), fmx = is_fin(bmax);
+    if (up_row && (fmn ? nmin == 0 : nmin == 1)) {
+        // a x_j <= U - (min activity of the other entries)
+        const double rmin = fmn ? fma(-a, bmin, smin) : smin;
+        const double x = Uv - rmin;
+        if (!neg) try_upper(C, j, x, a, b.y);
+        else try_lower(C, j, x, a, b.x);
+    }
+    if (lo_row && (fmx ? nmax == 0 : nmax == 1)) {
+        // a x_j >= L - (max activity of the other entries)
+        const double rmax = fmx ? fma(-a, bmax, smax) : smax;
+        const double x = Lv - rmax;
+        if (!neg) try_lower(C, j, x, a, b.x);
+        else try_upper(C, j, x, a, b.y);
+    }
+}
+
+// S2: class of a row from its activities, first match wins: infeasible
+// sides, infeasible activity, empty, redundant, singleton.  Returns false if
+// the row proves the LP infeasible.
+__device__ __forceinline__ bool classify(const Ctx &C, double Lv, double Uv, int32_t len, double smin, double smax,
+                                         int nmin, int nmax, uint8_t &kind) {
+    const double ft = C.feas_tol;
+    const bool Lf = is_fin(Lv), Uf = is_fin(Uv);
+    kind = RK_KEPT;
+    if (Lf && Uf) {
+        const double d = ft * fmax(1.0, fmax(fabs(Lv), fabs(Uv)));
+        if (Lv - Uv > d) return false;
+    }
+    if (nmin == 0 && Uf && smin > Uv + ft * max1abs(Uv)) return false;
+    if (nmax == 0 && Lf && smax < Lv - ft * max1abs(Lv)) return false;
+    if (len == 0) {
+        kind = RK_EMPTY;
+        return true;
+    }
+    const bool lo_ok = !Lf || (nmin == 0 && smin >= Lv - ft * max1abs(Lv));
+    if (lo_ok) {
+        const bool hi_ok = !Uf || (nmax == 0 && smax <= Uv + ft * max1abs(Uv));
+        if (hi_ok) {
+            kind = RK_REDUNDANT;
+            return true;
+        }
+    }
+    if (len == 1) kind = RK_SINGLETON;
+    return true;
+}
+
+__device__ __forceinline__ int32_t lp_round(const Ctx &C, int32_t lp) {
+    (void)lp;
+    return C.round;
+}
+
+// writes the row's S1/S2 results and records; applies a singleton row as a bound
+__device__ __forceinline__ int32_t finish_row(const Ctx &C, int32_t i, int32_t beg, int32_t len, double Lv,
+                                              double Uv, double smin, double smax, int nmin, int nmax,
+                                              unsigned long long h, uint8_t &kind) {
+    const bool ok = classify(C, Lv, Uv, len, smin, smax, nmin, nmax, kind);
+    C.act[i] = make_double2(smin, smax);
+    C.ninf[i] = make_int2(nmin, nmax);
+    C.hrow[i] = h;
+    const int32_t lp = lp_of_row(C, i);
+    if (!ok) {
+        atomicMin(&C.verdict[lp * V_SLOTS + V_S2_ROW], C.rmap[i]);
+        kind = RK_KEPT;
+        C.rkind[i] = RK_KEPT;
+        return 0;
+    }
+    C.rkind[i] = kind;
+    if (kind == RK_KEPT) return 0;
+    const int32_t o = C.rmap[i];
+    C.rec_rk[o] = kind;
+    C.rec_rr[o] = lp_round(C, lp);
+    C.lp_changed[lp] = 1;
+    if (kind == RK_SINGLETON) {
+        // L <= a x_j <= U becomes a bound on x_j, always applied (no threshold)
+        const double a = C.A.val[beg];
+        const int32_t j = C.A.idx[beg];
+        C.rec_ra[o] = C.cmap[j];
+        C.rec_rv[o] = a;
+        const bool Lf = is_fin(Lv), Uf = is_fin(Uv);
+        double cl, cu;
+        if (!is_neg(a)) {
+            cl = Lf ? Lv / a : ninf_();
+            cu = Uf ? Uv / a : pinf();
+        } else {
+            cl = Uf ? Uv / a : ninf_();
+            cu = Lf ? Lv / a : pinf();
+        }
+        if (is_fin(cl)) atomic_max_dbl(&C.cand_l[j], cl);
+        if (is_fin(cu)) atomic_min_dbl(&C.cand_u[j], cu);
+    } else {
+        C.rec_ra[o] = -1;
+        C.rec_rv[o] = 0.0;
+    }
+    return 1;
+}
+
+__device__ __forceinline__ unsigned long long entry_hash(int32_t j, bool flip) {
+    return mix64(((unsigned long long)(uint32_t)j << 1) | (unsigned long long)flip);
+}
+__device__ __forceinline__ unsigned long long len_hash(int32_t len) {
+    return mix64(0xa0761d6478bd642fULL ^ (unsigned long long)(uint32_t)len);
+}
+
+// ------------------------------------------------------- S1 + S2 + S3 groups
+template <int W>
+__device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, int32_t &removed) {
+    const unsigned mask = group_mask<W>();
+    const int lane = threadIdx.x & (W - 1);
+    int32_t beg = 0, end = 0;
+    if (valid) {
+        beg = C.A.ptr[i];
+        end = C.A.ptr[i + 1];
+    }
+    const bool neg0 = end > beg ? is_neg(C.A.val[beg]) : false;
+    double smin = 0.0, smax = 0.0;
+    int nmin = 0, nmax = 0;
+    unsigned long long h = 0;
+    for (int32_t k = beg + lane; k < end; k += W) {
+        const int32_t j = C.A.idx[k];
+        const double a = C.A.val[k];
+        const double2 b = C.lu[j];
+        const bool neg = is_neg(a);
+        const double bmin = neg ? b.y : b.x, bmax = neg ? b.x : b.y;
+        if (is_fin(bmin)) smin = fma(a, bmin, smin);
+        else nmin++;
+        if (is_fin(bmax)) smax = fma(a, bmax, smax);
+        else nmax++;
+        h += entry_hash(j, neg != neg0);
+    }
+    smin = group_sum<W>(smin, mask);
+    smax = group_sum<W>(smax, mask);
+    nmin = group_sum<W>(nmin, mask);
+    nmax = group_sum<W>(nmax, mask);
+    h = group_sum<W>(h, mask);
+    if (!valid) return;
+    const int32_t len = end - beg;
+    h += len_hash(len);
+    const double Lv = C.L[i], Uv = C.U[i];
+    uint8_t kind = RK_KEPT;
+    if (lane == 0) removed += finish_row(C, i, beg, len, Lv, Uv, smin, smax, nmin, nmax, h, kind);
+    kind = (uint8_t)__shfl_sync(mask, (int)kind, 0, W);
+    if (kind != RK_KEPT || len < 2) return;
+    const bool up_row = is_fin(Uv) && nmin <= 1, lo_row = is_fin(Lv) && nmax <= 1;
+    if (!up_row && !lo_row) return;
+    for (int32_t k = beg + lane; k < end; k += W)
+        tighten_entry(C, C.A.idx[k], C.A.val[k], Lv, Uv, up_row, lo_row, smin, smax, nmin, nmax);
+}
+
+__global__ void __launch_bounds__(kBlock) k_prop_groups(Ctx C, GroupGrid g) {
+    const int c = grid_class(g, blockIdx.x);
+    const int32_t lb = blockIdx.x - g.blk_start[c];
+    int32_t removed = 0;
+    const int W = 1 << c;
+    const int32_t pos = C.A.cls_start[c] + lb * (kBlock / W) + threadIdx.x / W;
+    const bool valid = pos < C.A.cls_start[c + 1];
+    const int32_t i = valid ? C.A.order[pos] : 0;
+    switch (c) {
+        case 0: prop_group<1>(C, i, valid, removed); break;
+        case 1: prop_group<2>(C, i, valid, removed); break;
+        case 2: prop_group<4>(C, i, valid, removed); break;
+        case 3: prop_group<8>(C, i, valid, removed); break;
+        case 4: prop_group<16>(C, i, valid, removed); break;
+        default: prop_group<32>(C, i, valid, removed); break;
+    }
+    block_add(removed, &C.st->rows_removed);
+}
+
+// fixed-order block reduction (warp butterflies, then warps in order)
+template <typename T>
+__device__ __forceinline__ T block_reduce_ordered(T v, T *s_w) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    T t = T(0);
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kBlock / 32; w++) t += s_w[w];
+    __syncthreads();
+    return t;  // thread 0
+}
+
+// ------------------------------------------------------------ long rows
+__global__ void __launch_bounds__(kBlock) k_prop_long_partial(Ctx C, unsigned long long *ch_hash) {
+    __shared__ double s_d[kBlock / 32];
+    __shared__ int s_i[kBlock / 32];
+    __shared__ unsigned long long s_h[kBlock / 32];
+    const Chunk ch = C.A.chunks[blockIdx.x];
+    const bool neg0 = is_neg(C.A.val[C.A.ptr[ch.seg]]);
+    double smin = 0.0, smax = 0.0;
+    int nmin = 0, nmax = 0;
+    unsigned long long h = 0;
+    for (int32_t k = ch.begin + threadIdx.x; k < ch.end; k += kBlock) {
+        const int32_t j = C.A.idx[k];
+        const double a = C.A.val[k];
+        const double2 b = C.lu[j];
+        const bool neg = is_neg(a);
+        const double bmin = neg ? b.y : b.x, bmax = neg ? b.x : b.y;
+        if (is_fin(bmin)) smin = fma(a, bmin, smin);
+        else nmin++;
+        if (is_fin(bmax)) smax = fma(a, bmax, smax);
+        else nmax++;
+        h += entry_hash(j, neg != neg0);
+    }
+    smin = block_reduce_ordered(smin, s_d);
+    smax = block_reduce_ordered(smax, s_d);
+    nmin = block_reduce_ordered(nmin, s_i);
+    nmax = block_reduce_ordered(nmax, s_i);
+    h = block_reduce_ordered(h, s_h);
+    if (threadIdx.x == 0) {
+        C.ch_act[blockIdx.x] = make_double2(smin, smax);
+        C.ch_ninf[blockIdx.x] = make_int2(nmin, nmax);
+        ch_hash[blockIdx.x] = h;
+    }
+}
+
+__global__ void k_prop_long_combine(Ctx C, const unsigned long long *ch_hash) {
+    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t nlong = C.A.cls_start[7] - C.A.cls_start[6];
+    int32_t removed = 0;
+    if (t < nlong) {
+        const int32_t i = C.A.order[C.A.cls_start[6] + t];
+        double smin = 0.0, smax = 0.0;
+        int nmin = 0, nmax = 0;
+        unsigned long long h = 0;
+        for (int32_t q = C.A.lfirst[t]; q < C.A.lfirst[t + 1]; q++) {
+            const double2 a = C.ch_act[q];
+            const int2 c = C.ch_ninf[q];
+            smin += a.x;
+            smax += a.y;
+            nmin += c.x;
+            nmax += c.y;
+            h += ch_hash[q];
+        }
+        const int32_t beg = C.A.ptr[i], len = C.A.ptr[i + 1] - beg;
+        h += len_hash(len);
+        const double Lv = C.L[i], Uv = C.U[i];
+        uint8_t kind;
+        removed = finish_row(C, i, beg, len, Lv, Uv, smin, smax, nmin, nmax, h, kind);
+        const bool need = kind == RK_KEPT && ((is_fin(Uv) && nmin <= 1) || (is_fin(Lv) && nmax <= 1));
+        C.lneed[t] = need;
+    }
+    block_add(removed, &C.st->rows_removed);
+}
+
+__global__ void __launch_bounds__(kBlock) k_prop_long_tighten(Ctx C) {
+    const Chunk ch = C.A.chunks[blockIdx.x];
+    if (!C.lneed[ch.lidx]) return;
+    const int32_t i = ch.seg;
+    const double Lv = C.L[i], Uv = C.U[i];
+    const double2 act = C.act[i];
+    const int2 ni = C.ninf[i];
+    const bool up_row = is_fin(Uv) && ni.x <= 1, lo_row = is_fin(Lv) && ni.y <= 1;
+    for (int32_t k = ch.begin + threadIdx.x; k < ch.end; k += kBlock)
+        tighten_entry(C, C.A.idx[k], C.A.val[k], Lv, Uv, up_row, lo_row, act.x, act.y, ni.x, ni.y);
+}
+
+// ------------------------------------------------- S3' finalise + S4 fixing
+__global__ void __launch_bounds__(kBlock) k_colfin(Ctx C) {
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t changed = 0, fixed = 0;
+    if (j < C.n) {
+        const unsigned long long el = C.cand_l[j], eu = C.cand_u[j];
+        const bool has = el != kEncNegInf || eu != kEncPosInf;
+        uint8_t kind = CK_KEPT;
+        if (has || C.round == 1) {
+            if (has) {
+                C.cand_l[j] = kEncNegInf;
+                C.cand_u[j] = kEncPosInf;
+            }
+            const double2 b = C.lu[j];
+            double nl = b.x, nu = b.y;
+            if (has) {
+                const double dl = dec_dbl(el), du = dec_dbl(eu);
+                if (dl > nl) nl = dl;
+                if (du < nu) nu = du;
+            }
+            bool bad = false;
+            if (is_fin(nl) && is_fin(nu)) {
+                const double d = C.feas_tol * fmax(1.0, fmax(fabs(nl), fabs(nu)));
+                if (nl - nu > d) {
+                    bad = true;
+                } else if (nl != nu && fabs(nl - nu) <= d) {
+                    const double mid = 0.5 * (nl + nu);
+                    nl = mid;
+                    nu = mid;
+                }
+            }
+            const int32_t lp = lp_of_col(C, j);
+            if (bad) {
+                atomicMin(&C.verdict[lp * V_SLOTS + V_S3_COL], C.cmap[j]);
+            } else {
+                if (nl != b.x || nu != b.y) {
+                    C.lu[j] = make_double2(nl, nu);
+                    changed = 1;
+                    C.lp_changed[lp] = 1;
+                }
+                if (nl == nu) {
+                    kind = CK_FIXED;
+                    fixed = 1;
+                    C.fixv[j] = nl;
+                    const int32_t o = C.cmap[j];
+                    C.rec_ck[o] = CK_FIXED;
+                    C.rec_cr[o] = lp_round(C, lp);
+                    C.rec_cv[o] = nl;
+                    C.lp_changed[lp] = 1;
+                }
+            }
+        }
+        C.ckind[j] = kind;
+    }
+    block_add(changed, &C.st->bounds_changed);
+    block_add(fixed, &C.st->cols_fixed);
+}
+
+// ------------------------------------------------------------ S5 parallel rows
+// pass 0: rows kept by S2 with >= 2 entries; later passes: rows left
+// unmatched by the previous pass (rwork == 2).  Inserts each taking part
+// into the hash table and elects the leader of its key: the first equality
+// row, else the first row (Sec. 3.2), by atomicMin on (is_ineq, row).
+__global__ void __launch_bounds__(kBlock) k_s5_insert(Ctx C, int pass) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t part = 0;
+    if (i < C.m) {
+        bool take;
+        if (pass == 0) take = C.rkind[i] == RK_KEPT && C.A.ptr[i + 1] - C.A.ptr[i] >= 2;
+        else take = C.rwork[i] == 2;
+        int32_t slot = -1;
+        if (take) {
+            unsigned long long key = C.hrow[i];
+            if (key == 0) key = 1;
+            const uint32_t cap = (uint32_t)C.tcap;
+            uint32_t sl = (uint32_t)(key ^ (key >> 32)) & (cap - 1u);
+            for (uint32_t probe = 0; probe < cap; probe++) {
+                const unsigned long long prev = atomicCAS(&C.tkey[sl], 0ULL, key);
+                if (prev == 0ULL || prev == key) {
+                    slot = (int32_t)sl;
+                    break;
+                }
+                sl = (sl + 1u) & (cap - 1u);
+            }
+            if (slot < 0) {
+                atomicOr(&C.st->err, 1);
+                take = false;
+            } else {
+                const double Lv = C.L[i], Uv = C.U[i];
+                const bool eq = is_fin(Lv) && Lv == Uv;
+                const unsigned long long code = ((unsigned long long)(eq ? 0u : 1u) << 32) | (uint32_t)i;
+                atomicMin(&C.tlead[slot], code);
+                part = 1;
+            }
+        }
+        C.rslot[i] = take ? slot : -1;
+        C.rwork[i] = take ? 1 : 0;
+    }
+    block_add(part, &C.st->participants);
+}
+
+// merge a parallel follower i (row = lam * leader) into its leader li
+__device__ __forceinline__ void s5_accept(const Ctx &C, int32_t i, int32_t li, double lam) {
+    C.rkind[i] = RK_PARALLEL;
+    const int32_t o = C.rmap[i];
+    const int32_t lp = lp_of_row(C, i);
+    C.rec_rk[o] = RK_PARALLEL;
+    C.rec_rr[o] = lp_round(C, lp);
+    C.rec_ra[o] = C.rmap[li];
+    C.rec_rv[o] = lam;
+    C.lp_changed[lp] = 1;
+    const double Lj = C.L[i], Uj = C.U[i];
+    double lo, hi;
+    if (!is_neg(lam)) {
+        lo = is_fin(Lj) ? Lj / lam : ninf_();
+        hi = is_fin(Uj) ? Uj / lam : pinf();
+    } else {
+        lo = is_fin(Uj) ? Uj / lam : ninf_();
+        hi = is_fin(Lj) ? Lj / lam : pinf();
+    }
+    if (is_fin(lo)) atomic_max_dbl(&C.mL[li], lo);
+    if (is_fin(hi)) atomic_min_dbl(&C.mU[li], hi);
+    C.hasf[li] = 1;
+}
+
+template <int W>
+__device__ __forceinline__ void match_group(const Ctx &C, int32_t i, bool valid, int32_t &removed,
+                                            int32_t &unmatched) {
+    const unsigned mask = group_mask<W>();
+    const int lane = threadIdx.x & (W - 1);
+    bool act = valid && C.rwork[i] == 1;
+    int32_t li = -1;
+    if (act) {
+        li = (int32_t)(uint32_t)(C.tlead[C.rslot[i]] & 0xffffffffULL);
+        if (li == i) act = false;  // the leader itself
+    }
+    // every lane of a group sees the same `act`
+    int32_t bi = 0, bl = 0, len = 0;
+    bool ok = false;
+    double lam = 0.0;
+    if (act) {
+        bi = C.A.ptr[i];
+        bl = C.A.ptr[li];
+        len = C.A.ptr[i + 1] - bi;
+        ok = (C.A.ptr[li + 1] - bl) == len;
+        lam = C.A.val[bi] / C.A.val[bl];
+    }
+    if (ok) {
+        for (int32_t k = lane; k < len; k += W) {
+            const double ai = C.A.val[bi + k], al = C.A.val[bl + k];
+            const double la = lam * al;
+            const bool same = C.A.idx[bi + k] == C.A.idx[bl + k] &&
+                              fabs(ai - la) <= C.par_tol * fmax(fabs(ai), fabs(la));
+            if (!same) ok = false;
+        }
+    }
+    // all lanes of the group agree on `ok`
+    const unsigned bal = __ballot_sync(mask, !ok);
+    const unsigned mine = group_bits<W>(bal);
+    ok = act && mine == 0u;
+    if (valid && lane == 0) {
+        if (ok) {
+            s5_accept(C, i, li, lam);
+            C.rwork[i] = 0;
+            removed++;
+        } else if (act) {
+            C.rwork[i] = 2;
+            unmatched++;
+        } else {
+            C.rwork[i] = 0;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_s5_match_groups(Ctx C, GroupGrid g) {
+    const int c = grid_class(g, blockIdx.x);
+    const int32_t lb = blockIdx.x - g.blk_start[c];
+    int32_t removed = 0, unmatched = 0;
+    const int W = 1 << c;
+    const int32_t pos = C.A.cls_start[c] + lb * (kBlock / W) + threadIdx.x / W;
+    const bool valid = pos < C.A.cls_start[c + 1];
+    const int32_t i = valid ? C.A.order[pos] : 0;
+    switch (c) {
+        case 0: match_group<1>(C, i, valid, removed, unmatched); break;
+        case 1: match_group<2>(C, i, valid, removed, unmatched); break;
+        case 2: match_group<4>(C, i, valid, removed, unmatched); break;
+        case 3: match_group<8>(C, i, valid, removed, unmatched); break;
+        case 4: match_group<16>(C, i, valid, removed, unmatched); break;
+        default: match_group<32>(C, i, valid, removed, unmatched); break;
+    }
+    block_add(removed, &C.st->rows_removed);
+    block_add(unmatched, &C.st->unmatched);
+}
+
+// long rows: one block per row of class 6 (parallel long rows are rare)
+__global__ void __launch_bounds__(kBlock) k_s5_match_long(Ctx C) {
+    const int32_t t = blockIdx.x;
+    const int32_t i = C.A.order[C.A.cls_start[6] + t];
+    bool act = C.rwork[i] == 1;
+    int32_t li = -1;
+    if (act) {
+        li = (int32_t)(uint32_t)(C.tlead[C.rslot[i]] & 0xffffffffULL);
+        if (li == i) act = false;
+    }
+    int32_t bi = 0, bl = 0, len = 0;
+    bool ok = false;
+    double lam = 0.0;
+    if (act) {
+        bi = C.A.ptr[i];
+        bl = C.A.ptr[li];
+        len = C.A.ptr[i + 1] - bi;
+        ok = (C.A.ptr[li + 1] - bl) == len;
+        lam = C.A.val[bi] / C.A.val[bl];
+    }
+    if (ok) {
+        for (int32_t k = threadIdx.x; k < len; k += kBlock) {
+            const double ai = C.A.val[bi + k], al = C.A.val[bl + k];
+            const double la = lam * al;
+            if (!(C.A.idx[bi + k] == C.A.idx[bl + k] && fabs(ai - la) <= C.par_tol * fmax(fabs(ai), fabs(la))))
+                ok = false;
+        }
+    }
+    ok = __syncthreads_and(ok) != 0;
+    int32_t removed = 0, unmatched = 0;
+    if (threadIdx.x == 0) {
+        if (act && ok) {
+            s5_accept(C, i, li, lam);
+            C.rwork[i] = 0;
+            removed = 1;
+        } else if (act) {
+            C.rwork[i] = 2;
+            unmatched = 1;
+        } else {
+            C.rwork[i] = 0;
+        }
+    }
+    block_add(removed, &C.st->rows_removed);
+    block_add(unmatched, &C.st->unmatched);
+}
+
+// leaders take the followers' sides: L = max(L, merged), U = min(U, merged);
+// crossing by more than the tolerance is infeasible, nearly equal sides snap
+__global__ void __launch_bounds__(kBlock) k_s5_leader(Ctx C) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C.m || !C.hasf[i]) return;
+    C.hasf[i] = 0;
+    const unsigned long long eL = C.mL[i], eU = C.mU[i];
+    C.mL[i] = kEncNegInf;
+    C.mU[i] = kEncPosInf;
+    double nL = C.L[i], nU = C.U[i];
+    const double mL = dec_dbl(eL), mU = dec_dbl(eU);
+    if (mL > nL) nL = mL;
+    if (mU < nU) nU = mU;
+    if (is_fin(nL) && is_fin(nU)) {
+        const double d = C.feas_tol * fmax(1.0, fmax(fabs(nL), fabs(nU)));
+        if (nL - nU > d) {
+            atomicMin(&C.verdict[lp_of_row(C, i) * V_SLOTS + V_S5_ROW], C.rmap[i]);
+            return;
+        }
+        if (nL != nU && fabs(nL - nU) <= d) {
+            const double mid = 0.5 * (nL + nU);
+            nL = mid;
+            nU = mid;
+        }
+    }
+    C.L[i] = nL;
+    C.U[i] = nU;
+}
+
+inline unsigned blocks_for(int64_t cnt, int threads) {
+    return (unsigned)((cnt + threads - 1) / threads > 0 ? (cnt + threads - 1) / threads : 1);
+}
+
+}  // namespace
+
+void launch_prop(const Ctx &C, cudaStream_t s) {
+    const GroupGrid g = group_grid(C.A);
+    if (g.blk_start[6] > 0) k_prop_groups<<<g.blk_start[6], kBlock, 0, s>>>(C, g);
+    const int32_t nlong = C.A.cls_start[7] - C.A.cls_start[6];
+    if (nlong > 0 && C.A.nchunks > 0) {
+        k_prop_long_partial<<<C.A.nchunks, kBlock, 0, s>>>(C, C.ch_hash);
+        k_prop_long_combine<<<blocks_for(nlong, kBlock), kBlock, 0, s>>>(C, C.ch_hash);
+        k_prop_long_tighten<<<C.A.nchunks, kBlock, 0, s>>>(C);
+    }
+}
+
+void launch_colfin(const Ctx &C, cudaStream_t s) {
+    if (C.n > 0) k_colfin<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C);
+}
+
+void launch_s5_pass(const Ctx &C, int pass, cudaStream_t s) {
+    if (C.m == 0) return;
+    k_s5_insert<<<blocks_for(C.m, kBlock), kBlock, 0, s>>>(C, pass);
+    const GroupGrid g = group_grid(C.A);
+    if (g.blk_start[6] > 0) k_s5_match_groups<<<g.blk_start[6], kBlock, 0, s>>>(C, g);
+    const int32_t nlong = C.A.cls_start[7] - C.A.cls_start[6];
+    if (nlong > 0) k_s5_match_long<<<nlong, kBlock, 0, s>>>(C);
+}
+
+void launch_s5_leader(const Ctx &C, cudaStream_t s) {
+    if (C.m > 0) k_s5_leader<<<blocks_for(C.m, kBlock), kBlock, 0, s>>>(C);
+}
+
+}  // namespace lpp

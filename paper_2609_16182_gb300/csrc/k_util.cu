@@ -1,0 +1,490 @@
+// k_util.cu -- scans, class binning of segments, stable transpose (A -> A^T)
+// and the input checks of ingest (S0).
+#include <algorithm>
+
+#include "lpp_launch.h"
+
+namespace lpp {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kPerThread = kScanTile / kScanThreads;  // 8
+
+__device__ __forceinline__ int32_t block_sum_i32(int32_t v, int32_t *s_w) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int32_t t = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_w[w];
+    return t;  // valid in thread 0
+}
+
+// exclusive scan of the per-thread values of one block; returns the block total
+__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t &excl, int32_t *s_w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t acc = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            const int32_t t = s_w[w];
+            s_w[w] = acc;
+            acc += t;
+        }
+        s_w[32] = acc;
+    }
+    __syncthreads();
+    excl = s_w[warp] + x - v;
+    const int32_t total = s_w[32];
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t *in, int64_t cnt, int32_t *tsum) {
+    __shared__ int32_t s_w[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int32_t v = 0;
+    for (int t = threadIdx.x; t < kScanTile; t += kScanThreads) {
+        const int64_t k = base + t;
+        if (k < cnt) v += in[k];
+    }
+    const int32_t tot = block_sum_i32(v, s_w);
+    if (threadIdx.x == 0) tsum[blockIdx.x] = tot;
+}
+
+// one block: exclusive scan of tsum[0..ntiles) in place, tsum[ntiles] = out[cnt] = total
+__global__ void __launch_bounds__(1024) k_scan_top(int32_t *tsum, int32_t ntiles, int32_t *out, int64_t cnt) {
+    __shared__ int32_t s_w[33];
+    int32_t carry = 0;
+    for (int32_t b = 0; b < ntiles; b += 1024) {
+        const int32_t k = b + threadIdx.x;
+        const int32_t v = k < ntiles ? tsum[k] : 0;
+        int32_t ex;
+        const int32_t tot = block_excl_scan(v, ex, s_w);
+        if (k < ntiles) tsum[k] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        tsum[ntiles] = carry;
+        out[cnt] = carry;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const int32_t *in, int32_t *out, int64_t cnt,
+                                                            const int32_t *tsum) {
+    __shared__ int32_t s_w[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kPerThread;
+    int32_t v[kPerThread];
+    int32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < kPerThread; q++) {
+        const int64_t k = base + q;
+        v[q] = k < cnt ? in[k] : 0;
+        s += v[q];
+    }
+    int32_t ex;
+    block_excl_scan(s, ex, s_w);
+    int32_t run = tsum[blockIdx.x] + ex;
+#pragma unroll
+    for (int q = 0; q < kPerThread; q++) {
+        const int64_t k = base + q;
+        if (k < cnt) out[k] = run;
+        run += v[q];
+    }
+}
+
+// --------------------------------------------------------------- binning
+__global__ void __launch_bounds__(kScanThreads) k_bin_hist(const int32_t *ptr, int32_t cnt, int32_t *hist,
+                                                           int32_t ntiles) {
+    __shared__ int32_t s_h[kNumClass];
+    if (threadIdx.x < kNumClass) s_h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    for (int t = threadIdx.x; t < kScanTile; t += kScanThreads) {
+        const int64_t sg = base + t;
+        if (sg < cnt) atomicAdd(&s_h[seg_class(ptr[sg + 1] - ptr[sg])], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumClass) hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = s_h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_bin_scatter(const int32_t *ptr, int32_t cnt, const int32_t *off,
+                                                              int32_t ntiles, int32_t *order) {
+    __shared__ int32_t s_run[kNumClass];
+    __shared__ int32_t s_w[kScanThreads / 32][kNumClass];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    if (threadIdx.x < kNumClass) s_run[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    for (int r = 0; r < kPerThread; r++) {
+        const int64_t sg = base + (int64_t)r * kScanThreads + threadIdx.x;
+        const bool valid = sg < cnt;
+        const int c = valid ? seg_class(ptr[sg + 1] - ptr[sg]) : kNumClass;
+        int rank = 0;
+#pragma unroll
+        for (int k = 0; k < kNumClass; k++) {
+            const unsigned bal = __ballot_sync(0xffffffffu, c == k);
+            if (c == k) rank = __popc(bal & lt);
+            if (lane == 0) s_w[warp][k] = __popc(bal);
+        }
+        __syncthreads();
+        if (valid) {
+            int32_t pre = s_run[c];
+            for (int w = 0; w < warp; w++) pre += s_w[w][c];
+            order[off[(int64_t)c * ntiles + blockIdx.x] + pre + rank] = (int32_t)sg;
+        }
+        __syncthreads();
+        if (threadIdx.x < kNumClass) {
+            int32_t t = 0;
+            for (int w = 0; w < kScanThreads / 32; w++) t += s_w[w][threadIdx.x];
+            s_run[threadIdx.x] += t;
+        }
+        __syncthreads();
+    }
+}
+
+// class sizes from the scanned histogram
+__global__ void k_bin_finish(const int32_t *off, int32_t ntiles, int32_t *cls_out) {
+    if (threadIdx.x < kNumClass)
+        cls_out[threadIdx.x] =
+            off[(int64_t)(threadIdx.x + 1) * ntiles] - off[(int64_t)threadIdx.x * ntiles];
+}
+
+// chunk counts of the long segments (t < long count), zero beyond
+__global__ void k_chunk_count(const int32_t *ptr, const int32_t *order, const int32_t *off, int32_t ntiles,
+                              const int32_t *cls, int32_t cap_long, int32_t *nch) {
+    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cap_long) return;
+    const int32_t nlong = cls[6];
+    int32_t v = 0;
+    if (t < nlong) {
+        const int32_t sg = order[off[(int64_t)6 * ntiles] + t];
+        const int32_t len = ptr[sg + 1] - ptr[sg];
+        v = (len + kChunk - 1) / kChunk;
+    }
+    nch[t] = v;
+}
+
+__global__ void k_chunk_fill(const int32_t *ptr, const int32_t *order, const int32_t *off, int32_t ntiles,
+                             const int32_t *cls, int32_t cap_long, const int32_t *lfirst, Chunk *chunks) {
+    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cap_long || t >= cls[6]) return;
+    const int32_t sg = order[off[(int64_t)6 * ntiles] + t];
+    const int32_t b = ptr[sg], e = ptr[sg + 1];
+    int32_t q = lfirst[t];
+    for (int32_t k = b; k < e; k += kChunk, q++) {
+        Chunk ch;
+        ch.seg = sg;
+        ch.begin = k;
+        ch.end = min(e, k + kChunk);
+        ch.lidx = t;
+        chunks[q] = ch;
+    }
+}
+
+__global__ void k_copy_i32(const int32_t *src, int32_t *dst) { *dst = *src; }
+
+// ----------------------------------------------------------- input checks
+enum : int32_t { ERR_PTR = 1, ERR_COL = 2, ERR_VAL = 4, ERR_ORDER = 8, ERR_VEC = 16 };
+
+__global__ void k_check_ptr(const int32_t *ptr, int32_t m, int64_t nnz, int32_t *err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > m) return;
+    const int32_t p = ptr[i];
+    bool bad = p < 0 || (int64_t)p > nnz;
+    if (i == 0) bad |= p != 0;
+    if (i == m) bad |= (int64_t)p != nnz;
+    if (i < m) bad |= ptr[i + 1] < p;
+    if (bad) atomicOr(err, ERR_PTR);
+}
+
+// mark[p] += 1 for every row boundary p = ptr[i], 1 <= i < m
+__global__ void k_mark_rows(const int32_t *ptr, int32_t m, int64_t nnz, int32_t *mark) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1;
+    if (i >= m) return;
+    const int32_t p = ptr[i];
+    if (p >= 0 && (int64_t)p < nnz) atomicAdd(&mark[p], 1);
+}
+
+__global__ void k_check_entries(const int32_t *idx, const double *val, const int32_t *row_of, int64_t nnz,
+                                int32_t n, int32_t *err) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nnz) return;
+    const int32_t j = idx[k];
+    const double a = val[k];
+    int32_t e = 0;
+    if (j < 0 || j >= n) e |= ERR_COL;
+    if (!is_fin(a) || a == 0.0) e |= ERR_VAL;
+    if (k > 0 && row_of[k] == row_of[k - 1] && idx[k - 1] >= j) e |= ERR_ORDER;
+    if (e) atomicOr(err, e);
+}
+
+__device__ __forceinline__ double norm_inf(double x, double huge) {
+    if (x >= huge) return __longlong_as_double(0x7ff0000000000000LL);
+    if (x <= -huge) return __longlong_as_double((long long)0xfff0000000000000ULL);
+    return x;
+}
+
+__global__ void k_ingest_rows(const double *lhs, const double *rhs, int32_t m, double huge, double *L, double *U,
+                              int32_t *err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const double l = lhs[i], u = rhs[i];
+    if (isnan(l) || isnan(u)) atomicOr(err, ERR_VEC);
+    const double nl = norm_inf(l, huge), nu = norm_inf(u, huge);
+    if ((!is_fin(nl) && !is_neg(nl)) || (!is_fin(nu) && is_neg(nu))) atomicOr(err, ERR_VEC);
+    L[i] = nl;
+    U[i] = nu;
+}
+
+__global__ void k_ingest_cols(const double *lb, const double *ub, const double *c, int32_t n, double huge,
+                              double2 *lu, double *cc, int32_t *err) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double l = lb[j], u = ub[j], cj = c[j];
+    if (isnan(l) || isnan(u) || !is_fin(cj)) atomicOr(err, ERR_VEC);
+    const double nl = norm_inf(l, huge), nu = norm_inf(u, huge);
+    if ((!is_fin(nl) && !is_neg(nl)) || (!is_fin(nu) && is_neg(nu))) atomicOr(err, ERR_VEC);
+    lu[j] = make_double2(nl, nu);
+    cc[j] = cj;
+}
+
+// ------------------------------------------------------ stable transpose
+__global__ void __launch_bounds__(kScanThreads) k_radix_hist(const uint32_t *keys, int64_t cnt, int shift,
+                                                             int32_t *hist, int32_t ntiles) {
+    __shared__ int32_t s_h[256];
+    s_h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    for (int t = threadIdx.x; t < kScanTile; t += kScanThreads) {
+        const int64_t k = base + t;
+        if (k < cnt) atomicAdd(&s_h[(keys[k] >> shift) & 255u], 1);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = s_h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_radix_scatter(const uint32_t *kin, const int32_t *vin,
+                                                                int64_t cnt, int shift, const int32_t *off,
+                                                                int32_t ntiles, uint32_t *kout, int32_t *vout) {
+    __shared__ int32_t s_run[256];
+    __shared__ int32_t s_tot[256];
+    __shared__ int32_t s_w[kScanThreads / 32][256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    s_run[threadIdx.x] = 0;
+    for (int w = 0; w < kScanThreads / 32; w++) s_w[w][threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    for (int r = 0; r < kPerThread; r++) {
+        const int64_t k = base + (int64_t)r * kScanThreads + threadIdx.x;
+        const bool valid = k < cnt;
+        const uint32_t key = valid ? kin[k] : 0u;
+        const int32_t v = valid ? vin[k] : 0;
+        const int d = valid ? (int)((key >> shift) & 255u) : 256;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) s_w[warp][d] = __popc(peers);
+        __syncthreads();
+        {
+            int32_t acc = 0;
+            for (int w = 0; w < kScanThreads / 32; w++) {
+                const int32_t t = s_w[w][threadIdx.x];
+                s_w[w][threadIdx.x] = acc;
+                acc += t;
+            }
+            s_tot[threadIdx.x] = acc;
+        }
+        __syncthreads();
+        if (valid) {
+            const int32_t pos = off[(int64_t)d * ntiles + blockIdx.x] + s_run[d] + s_w[warp][d] + rank;
+            kout[pos] = key;
+            vout[pos] = v;
+        }
+        __syncthreads();
+        s_run[threadIdx.x] += s_tot[threadIdx.x];
+        for (int w = 0; w < kScanThreads / 32; w++) s_w[w][threadIdx.x] = 0;
+        __syncthreads();
+    }
+}
+
+__global__ void k_count_cols(const int32_t *idx, int64_t nnz, int32_t *colcnt) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nnz) atomicAdd(&colcnt[idx[k]], 1);
+}
+
+__global__ void k_gather_t(const int32_t *perm, const int32_t *row_of, const double *val, int64_t nnz,
+                           int32_t *tidx, double *tval) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nnz) return;
+    const int32_t e = perm[p];
+    tidx[p] = row_of[e];
+    tval[p] = val[e];
+}
+
+__global__ void k_copy_keys(const int32_t *idx, int64_t nnz, uint32_t *keys, int32_t *vals) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nnz) return;
+    keys[k] = (uint32_t)idx[k];
+    vals[k] = (int32_t)k;
+}
+
+__global__ void k_iota(int32_t *a, int32_t cnt, int32_t base) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < cnt) a[k] = base + (int32_t)k;
+}
+
+__global__ void k_fill_u64(unsigned long long *a, int64_t cnt, unsigned long long v) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < cnt) a[k] = v;
+}
+
+inline unsigned blocks_for(int64_t cnt, int threads) {
+    return (unsigned)std::max<int64_t>(1, (cnt + threads - 1) / threads);
+}
+
+}  // namespace
+
+// ================================================================= host side
+size_t scan_tmp_elems(int64_t cnt) { return (size_t)((cnt + kScanTile - 1) / kScanTile) + 1; }
+
+void scan_excl(const int32_t *in, int32_t *out, int64_t cnt, int32_t *tmp, cudaStream_t s) {
+    const int32_t ntiles = (int32_t)((cnt + kScanTile - 1) / kScanTile);
+    if (ntiles > 0) k_scan_reduce<<<ntiles, kScanThreads, 0, s>>>(in, cnt, tmp);
+    k_scan_top<<<1, 1024, 0, s>>>(tmp, ntiles, out, cnt);
+    if (ntiles > 0) k_scan_down<<<ntiles, kScanThreads, 0, s>>>(in, out, cnt, tmp);
+}
+
+size_t sched_tile_hist_elems(int64_t cnt) {
+    return (size_t)kNumClass * (size_t)((cnt + kScanTile - 1) / kScanTile) + 1;
+}
+
+int32_t sched_cap_long(int64_t nnz) { return (int32_t)std::max<int64_t>(1, nnz / kLongMin); }
+
+void build_schedule(const int32_t *ptr, int32_t cnt, int64_t nnz, const SchedBufs &b, int32_t *cls_out,
+                    int32_t *nchunk_out, cudaStream_t s) {
+    const int32_t ntiles = (int32_t)((cnt + kScanTile - 1) / kScanTile);
+    if (ntiles > 0) k_bin_hist<<<ntiles, kScanThreads, 0, s>>>(ptr, cnt, b.tile_hist, ntiles);
+    scan_excl(b.tile_hist, b.tile_hist, (int64_t)kNumClass * ntiles, b.tmp, s);
+    if (ntiles > 0) {
+        k_bin_scatter<<<ntiles, kScanThreads, 0, s>>>(ptr, cnt, b.tile_hist, ntiles, b.order);
+        k_bin_finish<<<1, 32, 0, s>>>(b.tile_hist, ntiles, cls_out);
+    } else {
+        cudaMemsetAsync(cls_out, 0, sizeof(int32_t) * kNumClass, s);
+    }
+    // chunks of the long segments: at most nnz / kLongMin of them
+    const int32_t cap_long = sched_cap_long(nnz);
+    k_chunk_count<<<blocks_for(cap_long, 256), 256, 0, s>>>(ptr, b.order, b.tile_hist, ntiles, cls_out, cap_long,
+                                                             b.nch);
+    scan_excl(b.nch, b.lfirst, cap_long, b.tmp, s);
+    k_chunk_fill<<<blocks_for(cap_long, 256), 256, 0, s>>>(ptr, b.order, b.tile_hist, ntiles, cls_out, cap_long,
+                                                            b.lfirst, b.chunks);
+    k_copy_i32<<<1, 1, 0, s>>>(b.lfirst + cap_long, nchunk_out);
+}
+
+void segmat_from_counts(SegMat &M, const int32_t cls[kNumClass], int32_t nchunks) {
+    M.cls_start[0] = 0;
+    for (int c = 0; c < kNumClass; c++) M.cls_start[c + 1] = M.cls_start[c] + cls[c];
+    M.nchunks = nchunks;
+}
+
+GroupGrid group_grid(const SegMat &M) {
+    GroupGrid g;
+    int32_t acc = 0;
+    for (int c = 0; c < 6; c++) {
+        g.blk_start[c] = acc;
+        const int32_t per = kBlock >> c;
+        const int32_t cnt = M.cls_start[c + 1] - M.cls_start[c];
+        acc += (cnt + per - 1) / per;
+    }
+    g.blk_start[6] = acc;
+    return g;
+}
+
+void check_csr(const int32_t *ptr, const int32_t *idx, const double *val, int32_t m, int32_t n, int64_t nnz,
+               int32_t *row_of, int32_t *tmp, int32_t *err, cudaStream_t s) {
+    k_check_ptr<<<blocks_for((int64_t)m + 1, 256), 256, 0, s>>>(ptr, m, nnz, err);
+    // row_of: mark boundaries, then an inclusive scan (exclusive scan shifted by one)
+    cudaMemsetAsync(row_of, 0, sizeof(int32_t) * (size_t)(nnz + 1), s);
+    if (m > 1) k_mark_rows<<<blocks_for((int64_t)m - 1, 256), 256, 0, s>>>(ptr, m, nnz, row_of);
+    scan_excl(row_of, row_of, nnz, tmp, s);  // row_of[k+1] = rows whose start is <= k ... see caller
+    if (nnz > 0) k_check_entries<<<blocks_for(nnz, 256), 256, 0, s>>>(idx, val, row_of + 1, nnz, n, err);
+}
+
+void ingest_vectors(const double *lhs, const double *rhs, const double *lb, const double *ub, const double *c,
+                    int32_t m, int32_t n, double huge, double *L, double *U, double2 *lu, double *cc, int32_t *err,
+                    cudaStream_t s) {
+    if (m > 0) k_ingest_rows<<<blocks_for(m, 256), 256, 0, s>>>(lhs, rhs, m, huge, L, U, err);
+    if (n > 0) k_ingest_cols<<<blocks_for(n, 256), 256, 0, s>>>(lb, ub, c, n, huge, lu, cc, err);
+}
+
+size_t transpose_hist_elems(int64_t nnz) { return (size_t)256 * (size_t)((nnz + kScanTile - 1) / kScanTile) + 1; }
+
+void transpose(const int32_t *ptr, const int32_t *idx, const double *val, const int32_t *row_of, int32_t m,
+               int32_t n, int64_t nnz, const TransposeBufs &b, int32_t *tptr, int32_t *tidx, double *tval,
+               int32_t *colcnt, cudaStream_t s) {
+    (void)ptr;
+    (void)m;
+    // column pointers: counts then a scan
+    cudaMemsetAsync(colcnt, 0, sizeof(int32_t) * (size_t)(n + 1), s);
+    if (nnz > 0) k_count_cols<<<blocks_for(nnz, 256), 256, 0, s>>>(idx, nnz, colcnt);
+    scan_excl(colcnt, tptr, n, b.tmp, s);
+    if (nnz == 0) return;
+    // stable LSD radix sort of the entries by column (entries come row by row)
+    k_copy_keys<<<blocks_for(nnz, 256), 256, 0, s>>>(idx, nnz, b.k0, b.v0);
+    int bits = 0;
+    while (bits < 31 && ((int64_t)1 << bits) < (int64_t)n) bits++;
+    const int passes = (bits + 7) / 8;
+    const int32_t ntiles = (int32_t)((nnz + kScanTile - 1) / kScanTile);
+    uint32_t *kin = b.k0, *kout = b.k1;
+    int32_t *vin = b.v0, *vout = b.v1;
+    for (int p = 0; p < passes; p++) {
+        k_radix_hist<<<ntiles, kScanThreads, 0, s>>>(kin, nnz, 8 * p, b.hist, ntiles);
+        scan_excl(b.hist, b.hist, (int64_t)256 * ntiles, b.tmp, s);
+        k_radix_scatter<<<ntiles, kScanThreads, 0, s>>>(kin, vin, nnz, 8 * p, b.hist, ntiles, kout, vout);
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    k_gather_t<<<blocks_for(nnz, 256), 256, 0, s>>>(vin, row_of, val, nnz, tidx, tval);
+}
+
+void iota(int32_t *a, int32_t cnt, int32_t base, cudaStream_t s) {
+    if (cnt > 0) k_iota<<<blocks_for(cnt, 256), 256, 0, s>>>(a, cnt, base);
+}
+
+void fill_u64(unsigned long long *a, int64_t cnt, unsigned long long v, cudaStream_t s) {
+    if (cnt > 0) k_fill_u64<<<blocks_for(cnt, 256), 256, 0, s>>>(a, cnt, v);
+}
+
+}  // namespace lpp
+
+namespace lpp {
+namespace {
+__global__ void k_fill_i32(int32_t *a, int64_t cnt, int32_t v) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < cnt) a[k] = v;
+}
+__global__ void k_split_lu(const double2 *lu, int32_t n, double *lb, double *ub) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double2 b = lu[j];
+    lb[j] = b.x;
+    ub[j] = b.y;
+}
+}  // namespace
+void fill_i32(int32_t *a, int64_t cnt, int32_t v, cudaStream_t s) {
+    if (cnt > 0) k_fill_i32<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(a, cnt, v);
+}
+void split_lu(const double2 *lu, int32_t n, double *lb, double *ub, cudaStream_t s) {
+    if (n > 0) k_split_lu<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(lu, n, lb, ub);
+}
+}  // namespace lpp

@@ -1,0 +1,582 @@
+// lpp_api.cu -- the C ABI of lpp.h: argument checks, engine runs, result objects.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+
+#include "lpp_engine.h"
+
+using namespace lpp;
+
+namespace {
+
+thread_local std::string g_err;
+
+lpp_status set_err(lpp_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+template <class F>
+lpp_status guarded(F &&f) {
+    try {
+        return f();
+    } catch (const StatusError &e) {
+        return set_err(e.st, e.what());
+    } catch (const CudaError &e) {
+        return set_err(LPP_ERR_CUDA, e.what());
+    } catch (const std::bad_alloc &) {
+        return set_err(LPP_ERR_OOM, "host allocation failed");
+    } catch (const std::exception &e) {
+        return set_err(LPP_ERR_CUDA, e.what());
+    }
+}
+
+void check_lp_shape(const lpp_lp *in) {
+    if (!in) throw StatusError(LPP_ERR_INVALID, "lp is NULL");
+    if (in->m < 0 || in->n < 0 || in->nnz < 0) throw StatusError(LPP_ERR_INVALID, "negative size");
+    if (in->nnz >= 2147483647LL) throw StatusError(LPP_ERR_INVALID, "nnz must be < 2^31");
+    if (!in->row_ptr) throw StatusError(LPP_ERR_INVALID, "row_ptr is NULL");
+    if (in->nnz > 0 && (!in->col_idx || !in->val)) throw StatusError(LPP_ERR_INVALID, "col_idx/val is NULL");
+    if (in->m > 0 && (!in->lhs || !in->rhs)) throw StatusError(LPP_ERR_INVALID, "lhs/rhs is NULL");
+    if (in->n > 0 && (!in->lb || !in->ub || !in->c)) throw StatusError(LPP_ERR_INVALID, "lb/ub/c is NULL");
+    if (in->nnz > 0 && in->n == 0) throw StatusError(LPP_ERR_INVALID, "entries but no columns");
+    if (in->m == 0 && in->nnz != 0) throw StatusError(LPP_ERR_INVALID, "entries but no rows");
+}
+
+lpp_opts resolve_opts(const lpp_opts *opts) {
+    lpp_opts o;
+    if (opts) o = *opts;
+    else lpp_opts_default(&o);
+    if (o.max_rounds < 0 || o.par_max_iter < 1 || !(o.feas_tol >= 0) || !(o.bound_tol >= 0) || !(o.huge > 0) ||
+        !(o.max_implied > 0) || !(o.par_tol >= 0))
+        throw StatusError(LPP_ERR_INVALID, "bad options");
+    return o;
+}
+
+__global__ void k_count_lp(const int32_t *lprow, const int32_t *rp, int32_t m, const int32_t *lpcol, int32_t n,
+                           int32_t *rows, int32_t *cols, int32_t *nnz) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) {
+        atomicAdd(&rows[lprow[t]], 1);
+        atomicAdd(&nnz[lprow[t]], rp[t + 1] - rp[t]);
+    }
+    if (t < n) atomicAdd(&cols[lpcol[t]], 1);
+}
+
+// arena -> per-LP local numbering: ptr arrays get one extra entry per LP
+__global__ void k_rebase_rows(const int32_t *rp, const int32_t *lprow, const int32_t *rmap, int32_t m,
+                              const int32_t *nnz_start, const int32_t *row_orig, int32_t *rp_out, int32_t *rmap_out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int32_t lp = lprow[i];
+    rp_out[i + lp] = rp[i] - nnz_start[lp];
+    rmap_out[i] = rmap[i] - row_orig[lp];
+}
+__global__ void k_rebase_cols(const int32_t *tp, const int32_t *lpcol, const int32_t *cmap, int32_t n,
+                              const int32_t *nnz_start, const int32_t *col_orig, int32_t *tp_out, int32_t *cmap_out) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int32_t lp = lpcol[j];
+    tp_out[j + lp] = tp[j] - nnz_start[lp];
+    cmap_out[j] = cmap[j] - col_orig[lp];
+}
+__global__ void k_ptr_tails(const int32_t *row_start, const int32_t *rows, const int32_t *col_start,
+                            const int32_t *cols, const int32_t *nnz, int32_t nlp, int32_t *rp_out, int32_t *tp_out) {
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nlp) return;
+    rp_out[row_start[k] + rows[k] + k] = nnz[k];
+    tp_out[col_start[k] + cols[k] + k] = nnz[k];
+}
+// entries: column index (CSR) / row index (CSC) made local to the LP
+__global__ void k_rebase_idx(int32_t *idx, const int32_t *ptr, const int32_t *lp_of_seg, int32_t segs,
+                             const int32_t *start) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= segs) return;
+    const int32_t d = start[lp_of_seg[i]];
+    for (int32_t k = ptr[i]; k < ptr[i + 1]; k++) idx[k] -= d;
+}
+
+unsigned nblk(int64_t cnt) { return (unsigned)((cnt + 255) / 256 > 0 ? (cnt + 255) / 256 : 1); }
+
+// Copies records, bounds and activities of the arena to the host.
+struct HostRecords {
+    std::vector<int32_t> rk, rr, ra, ck, cr, cmap, act_rmap;
+    std::vector<double> rv, cv, clb, cub, offset;
+    std::vector<double2> lu, act;
+    std::vector<int2> ninf;
+};
+
+HostRecords fetch_records(Engine &E) {
+    HostRecords h;
+    cudaStream_t s = E.s;
+    auto d2h = [&](void *dst, const void *src, size_t bytes) {
+        if (bytes) LPP_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+    };
+    h.rk.resize(E.m0); h.rr.resize(E.m0); h.ra.resize(E.m0); h.rv.resize(E.m0);
+    h.ck.resize(E.n0); h.cr.resize(E.n0); h.cv.resize(E.n0);
+    h.lu.resize(E.n); h.cmap.resize(E.n); h.offset.resize(E.nlp);
+    h.act.resize(E.act_m); h.ninf.resize(E.act_m); h.act_rmap.resize(E.act_m);
+    d2h(h.rk.data(), E.rec_rk, 4 * (size_t)E.m0);
+    d2h(h.rr.data(), E.rec_rr, 4 * (size_t)E.m0);
+    d2h(h.ra.data(), E.rec_ra, 4 * (size_t)E.m0);
+    d2h(h.rv.data(), E.rec_rv, 8 * (size_t)E.m0);
+    d2h(h.ck.data(), E.rec_ck, 4 * (size_t)E.n0);
+    d2h(h.cr.data(), E.rec_cr, 4 * (size_t)E.n0);
+    d2h(h.cv.data(), E.rec_cv, 8 * (size_t)E.n0);
+    d2h(h.lu.data(), E.lu[E.cur], 16 * (size_t)E.n);
+    d2h(h.cmap.data(), E.cmap[E.cur], 4 * (size_t)E.n);
+    d2h(h.offset.data(), E.K.offset, 8 * (size_t)E.nlp);
+    d2h(h.act.data(), E.act, 16 * (size_t)E.act_m);
+    d2h(h.ninf.data(), E.ninf, 8 * (size_t)E.act_m);
+    d2h(h.act_rmap.data(), E.rmap[E.act_buf], 4 * (size_t)E.act_m);
+    LPP_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
+
+// postsolve record of LP k of the arena (rows [r0, r0+m), columns [c0, c0+n))
+lpp_postsolve *make_postsolve(Engine &E, const HostRecords &h, int32_t k, int32_t m_red, int32_t n_red,
+                              int64_t nnz_red, const int32_t *cmap_local) {
+    auto *P = new lpp_postsolve();
+    const Member &mm = E.mem[k];
+    const int32_t r0 = mm.row_off, c0 = mm.col_off;
+    P->row_kind.assign(h.rk.begin() + r0, h.rk.begin() + r0 + mm.m);
+    P->row_round.assign(h.rr.begin() + r0, h.rr.begin() + r0 + mm.m);
+    P->row_aux.resize(mm.m);
+    P->row_val.assign(h.rv.begin() + r0, h.rv.begin() + r0 + mm.m);
+    for (int32_t i = 0; i < mm.m; i++) {
+        const int32_t a = h.ra[r0 + i];
+        const int32_t kd = P->row_kind[i];
+        P->row_aux[i] = a < 0 ? -1 : (kd == LPP_ROW_SINGLETON ? a - c0 : a - r0);
+    }
+    P->col_kind.assign(h.ck.begin() + c0, h.ck.begin() + c0 + mm.n);
+    P->col_round.assign(h.cr.begin() + c0, h.cr.begin() + c0 + mm.n);
+    P->col_val.assign(h.cv.begin() + c0, h.cv.begin() + c0 + mm.n);
+    P->col_lb.assign(mm.n, NAN);
+    P->col_ub.assign(mm.n, NAN);
+    for (int32_t j = 0; j < E.n; j++) {
+        const int32_t o = h.cmap[j] - c0;
+        if (o >= 0 && o < mm.n) {
+            P->col_lb[o] = h.lu[j].x;
+            P->col_ub[o] = h.lu[j].y;
+        }
+    }
+    for (int32_t j = 0; j < mm.n; j++)
+        if (P->col_kind[j] != LPP_COL_KEPT) P->col_lb[j] = P->col_ub[j] = P->col_val[j];
+    P->act_min.assign(mm.m, NAN);
+    P->act_max.assign(mm.m, NAN);
+    P->ninf_min.assign(mm.m, -1);
+    P->ninf_max.assign(mm.m, -1);
+    for (int32_t i = 0; i < E.act_m; i++) {
+        const int32_t o = h.act_rmap[i] - r0;
+        if (o >= 0 && o < mm.m) {
+            P->act_min[o] = h.act[i].x;
+            P->act_max[o] = h.act[i].y;
+            P->ninf_min[o] = h.ninf[i].x;
+            P->ninf_max[o] = h.ninf[i].y;
+        }
+    }
+    P->col_map.assign(cmap_local, cmap_local + n_red);
+    lpp_info &I = P->info;
+    I.status = E.lp_status[k];
+    I.where = E.lp_where[k];
+    I.index = E.lp_index[k] < 0 ? -1 : E.lp_index[k] - (I.where == LPP_WHERE_ROW ? r0 : c0);
+    I.round = E.lp_round[k];
+    I.rounds = E.lp_rounds[k];
+    I.m = mm.m;
+    I.n = mm.n;
+    I.nnz = mm.nnz;
+    I.m_red = m_red;
+    I.n_red = n_red;
+    I.nnz_red = nnz_red;
+    I.obj_offset = h.offset[k];
+    I.presolve_ms = E.loop_ms;
+    I.nnz_processed = E.nnz_processed;
+    P->r_nnz = E.r_nnz;
+    P->r_rows = E.r_rows;
+    P->r_cols = E.r_cols;
+    P->r_bounds = E.r_bounds;
+    P->r_ms = E.r_ms;
+    if (E.o.timing) {
+        std::vector<lpp_kernel_stat> ks(F_NUM);
+        for (int f = 0; f < F_NUM; f++) {
+            std::memset(&ks[f], 0, sizeof(lpp_kernel_stat));
+            std::snprintf(ks[f].name, sizeof ks[f].name, "%s", fam_name(f));
+        }
+        for (auto &mk : E.marks) {
+            float ms = 0.f;
+            LPP_CUDA(cudaEventElapsedTime(&ms, mk.a, mk.b));
+            ks[mk.fam].launches++;
+            ks[mk.fam].ms += ms;
+            ks[mk.fam].bytes += mk.bytes;
+        }
+        P->kstats = ks;
+    }
+    return P;
+}
+
+template <class T>
+const T *host_copy(std::vector<T> &h, const T *d, size_t cnt) {
+    if (h.size() != cnt) {
+        h.resize(cnt);
+        if (cnt) LPP_CUDA(cudaMemcpy(h.data(), d, sizeof(T) * cnt, cudaMemcpyDeviceToHost));
+    }
+    return h.data();
+}
+}  // namespace
+
+extern "C" {
+
+void lpp_opts_default(lpp_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->feas_tol = 1e-9;
+    o->bound_tol = 1e-6;
+    o->huge = 1e20;
+    o->max_implied = 1e10;
+    o->par_tol = 1e-12;
+    o->max_rounds = 20;
+    o->dual_reductions = 1;
+    o->par_max_iter = 16;
+    o->timing = 0;
+    o->device = 0;
+    o->stream = nullptr;
+}
+
+const char *lpp_last_error(void) { return g_err.c_str(); }
+
+lpp_status lpp_presolve(const lpp_lp *in, const lpp_opts *opts, lpp_reduced **out, lpp_postsolve **rec) {
+    return guarded([&]() -> lpp_status {
+        if (!out || !rec) throw StatusError(LPP_ERR_INVALID, "out/rec is NULL");
+        *out = nullptr;
+        *rec = nullptr;
+        check_lp_shape(in);
+        const lpp_opts o = resolve_opts(opts);
+        auto E = std::make_unique<Engine>();
+        Member mm{in->m, in->n, in->nnz, 0, 0, 0, in->obj_offset};
+        E->setup(o, 1, {mm});
+        E->ingest_plain(*in);
+        E->prepare();
+        E->run();
+        HostRecords h = fetch_records(*E);
+        // the reduced LP takes the current buffers
+        auto *R = new lpp_reduced();
+        const int c = E->cur;
+        R->m = E->m;
+        R->n = E->n;
+        R->nnz = E->nnz;
+        R->obj_offset = h.offset[0];
+        R->rp = E->rp[c];
+        R->ci = E->ci[c];
+        R->rv = E->rv[c];
+        R->tp = E->tp[c];
+        R->ti = E->ti[c];
+        R->tv = E->tv[c];
+        R->L = E->L[c];
+        R->U = E->U[c];
+        R->c = E->c[c];
+        R->rmap = E->rmap[c];
+        R->cmap = E->cmap[c];
+        for (void *p : {(void *)R->rp, (void *)R->ci, (void *)R->rv, (void *)R->tp, (void *)R->ti, (void *)R->tv,
+                        (void *)R->L, (void *)R->U, (void *)R->c, (void *)R->rmap, (void *)R->cmap}) {
+            E->pool.forget(p);
+            R->owned.push_back(p);
+        }
+        R->lb = E->pool.alloc<double>(R->n);
+        R->ub = E->pool.alloc<double>(R->n);
+        E->pool.forget(R->lb);
+        E->pool.forget(R->ub);
+        R->owned.push_back(R->lb);
+        R->owned.push_back(R->ub);
+        split_lu(E->lu[c], R->n, R->lb, R->ub, E->s);
+        LPP_CUDA(cudaStreamSynchronize(E->s));
+        lpp_postsolve *P = make_postsolve(*E, h, 0, R->m, R->n, R->nnz, h.cmap.data());
+        *out = R;
+        *rec = P;
+        return (lpp_status)P->info.status;
+    });
+}
+
+lpp_status lpp_presolve_batch(const lpp_lp *ins, int32_t count, const lpp_opts *opts, lpp_reduced **outs,
+                              lpp_postsolve **recs, lpp_status *per_lp) {
+    return guarded([&]() -> lpp_status {
+        if (count < 0 || (count > 0 && (!ins || !outs || !recs || !per_lp)))
+            throw StatusError(LPP_ERR_INVALID, "bad batch arguments");
+        if (count == 0) return LPP_OK;
+        for (int32_t k = 0; k < count; k++) {
+            outs[k] = nullptr;
+            recs[k] = nullptr;
+            per_lp[k] = LPP_ERR_INVALID;
+        }
+        const lpp_opts o = resolve_opts(opts);
+        std::vector<Member> mem(count);
+        int64_t ro = 0, co = 0, zo = 0;
+        for (int32_t k = 0; k < count; k++) {
+            check_lp_shape(&ins[k]);
+            mem[k] = Member{ins[k].m, ins[k].n, ins[k].nnz, (int32_t)ro, (int32_t)co, zo, ins[k].obj_offset};
+            ro += ins[k].m;
+            co += ins[k].n;
+            zo += ins[k].nnz;
+            if (ro >= 2147483647LL || co >= 2147483647LL || zo >= 2147483647LL)
+                throw StatusError(LPP_ERR_INVALID, "batch too large for int32 indices");
+        }
+        auto E = std::make_unique<Engine>();
+        E->setup(o, count, mem);
+        E->ingest_batch(ins, count);
+        E->prepare();
+        E->run();
+        HostRecords h = fetch_records(*E);
+        // per-LP sizes of the reduced arena
+        cudaStream_t s = E->s;
+        const int c = E->cur;
+        int32_t *cnt = E->pool.alloc<int32_t>(3 * (size_t)count);
+        LPP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * 3 * (size_t)count, s));
+        k_count_lp<<<nblk(std::max(E->m, E->n)), 256, 0, s>>>(E->lprow[c], E->rp[c], E->m, E->lpcol[c], E->n, cnt,
+                                                                cnt + count, cnt + 2 * count);
+        std::vector<int32_t> hc(3 * (size_t)count);
+        LPP_CUDA(cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * hc.size(), cudaMemcpyDeviceToHost, s));
+        LPP_CUDA(cudaStreamSynchronize(s));
+        // tables: row/col/nnz starts (reduced) and original offsets
+        std::vector<int32_t> tab(5 * (size_t)count);
+        int32_t rs = 0, cs = 0, zs = 0;
+        for (int32_t k = 0; k < count; k++) {
+            tab[k] = rs;
+            tab[count + k] = cs;
+            tab[2 * count + k] = zs;
+            tab[3 * count + k] = mem[k].row_off;
+            tab[4 * count + k] = mem[k].col_off;
+            rs += hc[k];
+            cs += hc[count + k];
+            zs += hc[2 * count + k];
+        }
+        int32_t *dtab = E->pool.alloc<int32_t>(tab.size());
+        LPP_CUDA(cudaMemcpyAsync(dtab, tab.data(), sizeof(int32_t) * tab.size(), cudaMemcpyHostToDevice, s));
+        const int32_t *row_start = dtab, *col_start = dtab + count, *nnz_start = dtab + 2 * count;
+        const int32_t *row_orig = dtab + 3 * count, *col_orig = dtab + 4 * count;
+        int32_t *rows = cnt, *cols = cnt + count, *nnzs = cnt + 2 * count;
+        // shared storage of all reduced LPs
+        auto store = std::make_shared<SharedStore>();
+        int32_t *rp_out = E->pool.alloc<int32_t>((size_t)E->m + count);
+        int32_t *tp_out = E->pool.alloc<int32_t>((size_t)E->n + count);
+        int32_t *rmap_out = E->pool.alloc<int32_t>(E->m);
+        int32_t *cmap_out = E->pool.alloc<int32_t>(E->n);
+        double *lb = E->pool.alloc<double>(E->n), *ub = E->pool.alloc<double>(E->n);
+        if (E->m > 0)
+            k_rebase_rows<<<nblk(E->m), 256, 0, s>>>(E->rp[c], E->lprow[c], E->rmap[c], E->m, nnz_start, row_orig,
+                                                     rp_out, rmap_out);
+        if (E->n > 0)
+            k_rebase_cols<<<nblk(E->n), 256, 0, s>>>(E->tp[c], E->lpcol[c], E->cmap[c], E->n, nnz_start, col_orig,
+                                                     tp_out, cmap_out);
+        k_ptr_tails<<<nblk(count), 256, 0, s>>>(row_start, rows, col_start, cols, nnzs, count, rp_out, tp_out);
+        if (E->m > 0) k_rebase_idx<<<nblk(E->m), 256, 0, s>>>(E->ci[c], E->rp[c], E->lprow[c], E->m, col_start);
+        if (E->n > 0) k_rebase_idx<<<nblk(E->n), 256, 0, s>>>(E->ti[c], E->tp[c], E->lpcol[c], E->n, row_start);
+        split_lu(E->lu[c], E->n, lb, ub, s);
+        LPP_CUDA(cudaGetLastError());
+        std::vector<int32_t> cmap_h(E->n);
+        LPP_CUDA(cudaMemcpyAsync(cmap_h.data(), cmap_out, sizeof(int32_t) * (size_t)E->n, cudaMemcpyDeviceToHost, s));
+        LPP_CUDA(cudaStreamSynchronize(s));
+        for (void *p : {(void *)rp_out, (void *)tp_out, (void *)rmap_out, (void *)cmap_out, (void *)lb, (void *)ub,
+                        (void *)E->ci[c], (void *)E->rv[c], (void *)E->ti[c], (void *)E->tv[c], (void *)E->L[c],
+                        (void *)E->U[c], (void *)E->c[c]}) {
+            E->pool.forget(p);
+            store->ptrs.push_back(p);
+        }
+        for (int32_t k = 0; k < count; k++) {
+            auto *R = new lpp_reduced();
+            const int32_t r0 = tab[k], c0 = tab[count + k], z0 = tab[2 * count + k];
+            R->m = hc[k];
+            R->n = hc[count + k];
+            R->nnz = hc[2 * count + k];
+            R->obj_offset = h.offset[k];
+            R->rp = rp_out + r0 + k;
+            R->tp = tp_out + c0 + k;
+            R->ci = E->ci[c] + z0;
+            R->rv = E->rv[c] + z0;
+            R->ti = E->ti[c] + z0;
+            R->tv = E->tv[c] + z0;
+            R->L = E->L[c] + r0;
+            R->U = E->U[c] + r0;
+            R->c = E->c[c] + c0;
+            R->lb = lb + c0;
+            R->ub = ub + c0;
+            R->rmap = rmap_out + r0;
+            R->cmap = cmap_out + c0;
+            R->shared = store;
+            outs[k] = R;
+            recs[k] = make_postsolve(*E, h, k, R->m, R->n, R->nnz, cmap_h.data() + c0);
+            per_lp[k] = (lpp_status)recs[k]->info.status;
+        }
+        return LPP_OK;
+    });
+}
+
+lpp_status lpp_reduced_view(lpp_reduced *R, lpp_lp *v, int32_t on_device) {
+    return guarded([&]() -> lpp_status {
+        if (!R || !v) throw StatusError(LPP_ERR_INVALID, "NULL argument");
+        std::memset(v, 0, sizeof *v);
+        v->m = R->m;
+        v->n = R->n;
+        v->nnz = R->nnz;
+        v->obj_offset = R->obj_offset;
+        if (on_device) {
+            v->row_ptr = R->rp;
+            v->col_idx = R->ci;
+            v->val = R->rv;
+            v->c = R->c;
+            v->lhs = R->L;
+            v->rhs = R->U;
+            v->lb = R->lb;
+            v->ub = R->ub;
+            v->on_device = 1;
+            return LPP_OK;
+        }
+        if (R->h_rp.empty()) {
+            R->h_rp.resize((size_t)R->m + 1);
+            R->h_ci.resize((size_t)R->nnz);
+            R->h_rv.resize((size_t)R->nnz);
+            R->h_c.resize(R->n);
+            R->h_L.resize(R->m);
+            R->h_U.resize(R->m);
+            R->h_lb.resize(R->n);
+            R->h_ub.resize(R->n);
+            auto d2h = [](void *dst, const void *src, size_t bytes) {
+                if (bytes) LPP_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+            };
+            d2h(R->h_rp.data(), R->rp, 4 * ((size_t)R->m + 1));
+            d2h(R->h_ci.data(), R->ci, 4 * (size_t)R->nnz);
+            d2h(R->h_rv.data(), R->rv, 8 * (size_t)R->nnz);
+            d2h(R->h_c.data(), R->c, 8 * (size_t)R->n);
+            d2h(R->h_L.data(), R->L, 8 * (size_t)R->m);
+            d2h(R->h_U.data(), R->U, 8 * (size_t)R->m);
+            d2h(R->h_lb.data(), R->lb, 8 * (size_t)R->n);
+            d2h(R->h_ub.data(), R->ub, 8 * (size_t)R->n);
+        }
+        v->row_ptr = R->h_rp.data();
+        v->col_idx = R->h_ci.data();
+        v->val = R->h_rv.data();
+        v->c = R->h_c.data();
+        v->lhs = R->h_L.data();
+        v->rhs = R->h_U.data();
+        v->lb = R->h_lb.data();
+        v->ub = R->h_ub.data();
+        v->on_device = 0;
+        return LPP_OK;
+    });
+}
+
+lpp_status lpp_reduced_csc(lpp_reduced *R, const int32_t **col_ptr, const int32_t **row_idx, const double **val,
+                           int32_t on_device) {
+    return guarded([&]() -> lpp_status {
+        if (!R) throw StatusError(LPP_ERR_INVALID, "NULL reduced");
+        if (on_device) {
+            if (col_ptr) *col_ptr = R->tp;
+            if (row_idx) *row_idx = R->ti;
+            if (val) *val = R->tv;
+        } else {
+            if (col_ptr) *col_ptr = host_copy(R->h_tp, R->tp, (size_t)R->n + 1);
+            if (row_idx) *row_idx = host_copy(R->h_ti, R->ti, (size_t)R->nnz);
+            if (val) *val = host_copy(R->h_tv, R->tv, (size_t)R->nnz);
+        }
+        return LPP_OK;
+    });
+}
+
+lpp_status lpp_reduced_maps(lpp_reduced *R, const int32_t **row_map, const int32_t **col_map, int32_t on_device) {
+    return guarded([&]() -> lpp_status {
+        if (!R) throw StatusError(LPP_ERR_INVALID, "NULL reduced");
+        if (on_device) {
+            if (row_map) *row_map = R->rmap;
+            if (col_map) *col_map = R->cmap;
+        } else {
+            if (row_map) *row_map = host_copy(R->h_rmap, R->rmap, (size_t)R->m);
+            if (col_map) *col_map = host_copy(R->h_cmap, R->cmap, (size_t)R->n);
+        }
+        return LPP_OK;
+    });
+}
+
+lpp_status lpp_result_info(const lpp_postsolve *P, lpp_info *info) {
+    if (!P || !info) return set_err(LPP_ERR_INVALID, "NULL argument");
+    *info = P->info;
+    return LPP_OK;
+}
+
+lpp_status lpp_result_rows(const lpp_postsolve *P, int32_t *kind, int32_t *round, int32_t *aux, double *val) {
+    if (!P) return set_err(LPP_ERR_INVALID, "NULL record");
+    const size_t m = P->row_kind.size();
+    if (kind && m) std::memcpy(kind, P->row_kind.data(), 4 * m);
+    if (round && m) std::memcpy(round, P->row_round.data(), 4 * m);
+    if (aux && m) std::memcpy(aux, P->row_aux.data(), 4 * m);
+    if (val && m) std::memcpy(val, P->row_val.data(), 8 * m);
+    return LPP_OK;
+}
+
+lpp_status lpp_result_cols(const lpp_postsolve *P, int32_t *kind, int32_t *round, double *val, double *lb,
+                           double *ub) {
+    if (!P) return set_err(LPP_ERR_INVALID, "NULL record");
+    const size_t n = P->col_kind.size();
+    if (kind && n) std::memcpy(kind, P->col_kind.data(), 4 * n);
+    if (round && n) std::memcpy(round, P->col_round.data(), 4 * n);
+    if (val && n) std::memcpy(val, P->col_val.data(), 8 * n);
+    if (lb && n) std::memcpy(lb, P->col_lb.data(), 8 * n);
+    if (ub && n) std::memcpy(ub, P->col_ub.data(), 8 * n);
+    return LPP_OK;
+}
+
+lpp_status lpp_result_activity(const lpp_postsolve *P, double *act_min, double *act_max, int32_t *ninf_min,
+                               int32_t *ninf_max) {
+    if (!P) return set_err(LPP_ERR_INVALID, "NULL record");
+    const size_t m = P->act_min.size();
+    if (act_min && m) std::memcpy(act_min, P->act_min.data(), 8 * m);
+    if (act_max && m) std::memcpy(act_max, P->act_max.data(), 8 * m);
+    if (ninf_min && m) std::memcpy(ninf_min, P->ninf_min.data(), 4 * m);
+    if (ninf_max && m) std::memcpy(ninf_max, P->ninf_max.data(), 4 * m);
+    return LPP_OK;
+}
+
+lpp_status lpp_result_rounds(const lpp_postsolve *P, int32_t cap, int64_t *nnz, int32_t *rows_removed,
+                             int32_t *cols_fixed, int32_t *bounds_changed, float *ms, int32_t *rounds) {
+    if (!P || cap < 0) return set_err(LPP_ERR_INVALID, "bad argument");
+    const int32_t R = (int32_t)P->r_nnz.size();
+    if (rounds) *rounds = R;
+    for (int32_t r = 0; r < R && r < cap; r++) {
+        if (nnz) nnz[r] = P->r_nnz[r];
+        if (rows_removed) rows_removed[r] = P->r_rows[r];
+        if (cols_fixed) cols_fixed[r] = P->r_cols[r];
+        if (bounds_changed) bounds_changed[r] = P->r_bounds[r];
+        if (ms) ms[r] = P->r_ms[r];
+    }
+    return LPP_OK;
+}
+
+lpp_status lpp_result_kernels(const lpp_postsolve *P, int32_t cap, lpp_kernel_stat *stats, int32_t *count) {
+    if (!P || cap < 0) return set_err(LPP_ERR_INVALID, "bad argument");
+    const int32_t K = (int32_t)P->kstats.size();
+    if (count) *count = K;
+    for (int32_t k = 0; k < K && k < cap && stats; k++) stats[k] = P->kstats[k];
+    return LPP_OK;
+}
+
+lpp_status lpp_postsolve_primal(const lpp_postsolve *P, const double *x_red, double *x_orig) {
+    if (!P || !x_orig || (!x_red && !P->col_map.empty())) return set_err(LPP_ERR_INVALID, "NULL argument");
+    const size_t n = P->col_kind.size();
+    for (size_t j = 0; j < n; j++) x_orig[j] = P->col_kind[j] != LPP_COL_KEPT ? P->col_val[j] : NAN;
+    for (size_t k = 0; k < P->col_map.size(); k++) {
+        const int32_t j = P->col_map[k];
+        if (j < 0 || (size_t)j >= n) return set_err(LPP_ERR_INVALID, "corrupt column map");
+        x_orig[j] = x_red[k];
+    }
+    return LPP_OK;
+}
+
+void lpp_free_reduced(lpp_reduced *R) {
+    if (!R) return;
+    for (void *p : R->owned) cudaFree(p);
+    delete R;
+}
+
+void lpp_free_postsolve(lpp_postsolve *P) { delete P; }
+
+}  // extern "C"

@@ -1,27 +1,29 @@
 // lpp_dev.cuh -- device-side types and helpers shared by the library's kernels.
 //
-// Layout in device memory (one LP, or one arena of many LPs in batch mode):
+// Layout in device memory (one LP, or one arena holding many LPs back to back
+// as one block-diagonal LP in batch and serving mode):
 //   CSR  ptr int32[m+1], idx int32[nnz], val f64[nnz]          (rows of A)
 //   CSC  ptr int32[n+1], idx int32[nnz], val f64[nnz]          (rows of A^T)
-//   rows L, U f64[m]   (lhs, rhs)      cols lu double2[n] (lb, ub), c f64[n]
-//   maps rmap int32[m], cmap int32[n]  (current -> original index)
-// Both matrices and all vectors are double-buffered: compaction (S7) writes
-// the next buffer and the driver swaps.
+//   rows L, U f64[m] (lhs, rhs), rmap int32[m], lp_row int32[m] (arena only)
+//   cols lu double2[n] (lb, ub), c f64[n], cmap int32[n], lp_col int32[n]
+// rmap / cmap map a current index to its original index.  Matrices and
+// vectors are double-buffered: compaction (S7) writes the other buffer.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
 
 namespace lpp {
 
-constexpr int kBlock = 256;         // threads per block of every segment kernel
+constexpr int kBlock = 256;         // threads per block of the segment kernels
 constexpr int kLongMin = 4097;      // segments longer than 4096 entries are chunked
 constexpr int kChunk = 4096;        // entries per chunk of a long segment
 constexpr int kNumClass = 7;        // 0..5: groups of 1<<c lanes per segment, 6: chunked
-constexpr int kNone = 0x7fffffff;   // "no index" in atomicMin slots
+constexpr int kNone = 0x7fffffff;   // empty slot of an atomicMin index
+constexpr int kScanTile = 2048;     // elements per tile of the device-wide scans
 
-// segment class by length: lanes per segment W = 1 << class for class <= 5.
-// The summation order inside a segment depends only on its length, so every
-// row gives the same bits whatever else is in the launch (batch == alone).
+// Segment class by length: W = 1 << class lanes per segment for class <= 5,
+// chunks of kChunk entries for class 6.  A segment's summation order depends
+// only on its own length, never on its neighbours in the launch.
 __host__ __device__ __forceinline__ int seg_class(int len) {
     if (len <= 4) return 0;
     if (len <= 8) return 1;
@@ -32,71 +34,149 @@ __host__ __device__ __forceinline__ int seg_class(int len) {
     return 6;
 }
 
-// row record kinds (the values of lpp.h)
+// row record kinds (values of lpp.h)
 enum : uint8_t { RK_KEPT = 0, RK_EMPTY = 1, RK_REDUNDANT = 2, RK_SINGLETON = 3, RK_PARALLEL = 4 };
-// per-row work flags
-enum : uint8_t { RF_UNMATCHED = 1, RF_LEADER = 2 };
 // column kinds
 enum : uint8_t { CK_KEPT = 0, CK_FIXED = 1, CK_EMPTY = 2 };
+// verdict slots per LP, in step order
+enum { V_S2_ROW = 0, V_S3_COL = 1, V_S5_ROW = 2, V_S6_COL = 3, V_SLOTS = 4 };
 
-// Device status word of a round.  Verdict slots hold the smallest current
-// index that proved infeasibility / unboundedness in that step (kNone = none).
+// Global counters of a round (block-aggregated atomics).
 struct DevStatus {
-    int32_t bad_row_s2, bad_col_s3, bad_row_s5, bad_col_s6;
-    int32_t verdict;           // nonzero once any verdict slot is set
-    int32_t err;               // internal error bits (bounded waits, checks)
     int32_t rows_removed, cols_fixed, bounds_changed, unmatched;
-    int32_t m_new, n_new, nnz_new, nnz_new_csc;
-    int32_t cls_r[kNumClass];  // class sizes of the rows of the next round
-    int32_t cls_c[kNumClass];  // class sizes of the columns of the next round
+    int32_t participants, long_tighten, err, pad0;
+    int32_t cls_r[kNumClass];  // class sizes of the rows after compaction
+    int32_t cls_c[kNumClass];  // class sizes of the columns after compaction
     int32_t nchunk_r, nchunk_c;
-    int32_t participants;      // rows taking part in S5
-    int32_t pad;
-    double offset_delta;       // objective constant gained this round
+    int32_t m_new, n_new, nnz_new, nnz_new_t;
 };
 
-// one chunk of a long segment: [begin, end) of segment `seg`, which is the
-// `lidx`-th long segment; chunks of one segment are consecutive.
+// one chunk of a long segment: entries [begin, end) of segment `seg`, the
+// `lidx`-th long segment of its matrix; chunks of a segment are consecutive
 struct Chunk {
     int32_t seg, begin, end, lidx;
 };
 
-// A segmented matrix (CSR of A, or of A^T) plus its schedule.
+// A segmented matrix (CSR of A, or CSR of A^T) with its schedule.
 struct SegMat {
     const int32_t *ptr;
     const int32_t *idx;
     const double *val;
-    const int32_t *order;      // segment ids grouped by class (stable)
+    const int32_t *order;      // segment ids grouped by class, stable within a class
     const Chunk *chunks;       // chunks of the long segments
-    const int32_t *lfirst;     // [long count + 1] first chunk of each long segment
-    int32_t cnt;               // number of segments
-    int32_t cls_start[kNumClass + 1];
+    const int32_t *lfirst;     // [long + 1] first chunk of each long segment
+    int32_t cnt;               // segments
     int32_t nchunks;
+    int32_t cls_start[kNumClass + 1];
 };
 
-// ------------------------------------------------------------------ encodings
-// Order-preserving map of a double to uint64 (for atomicMin / atomicMax):
-// x < y  <=>  enc(x) < enc(y) for all non-NaN x, y.
+// Everything a round kernel touches (passed by value).
+struct Ctx {
+    SegMat A;   // CSR of A
+    SegMat T;   // CSR of A^T
+    int32_t m, n, nlp, round;
+    // rows
+    double *L, *U;
+    const int32_t *rmap, *lp_row;
+    // columns
+    double2 *lu;
+    const double *c;
+    const int32_t *cmap, *lp_col;
+    // row work
+    double2 *act;
+    int2 *ninf;
+    uint8_t *rkind;
+    uint8_t *rwork;                 // S5: 1 = take part in this pass
+    unsigned long long *hrow;       // S5 key hash
+    int32_t *rslot;
+    unsigned long long *mL, *mU;    // S5 merged sides (ordered encoding)
+    uint8_t *hasf;
+    // column work
+    unsigned long long *cand_l, *cand_u;  // accepted implied bounds (ordered encoding)
+    uint8_t *ckind;
+    double *fixv;
+    // S5 table
+    unsigned long long *tkey, *tlead;
+    int32_t tcap;
+    // long segments
+    double2 *ch_act;
+    int2 *ch_ninf;
+    unsigned long long *ch_hash;
+    uint8_t *lneed;
+    // records, indexed by original (arena) index
+    int32_t *rec_rk, *rec_rr, *rec_ra;
+    double *rec_rv;
+    int32_t *rec_ck, *rec_cr;
+    double *rec_cv;
+    // per LP
+    int32_t *verdict;               // [nlp][V_SLOTS] smallest original index
+    uint8_t *lp_changed;            // [nlp]
+    DevStatus *st;
+    double feas_tol, bound_tol, max_implied, par_tol;
+    int32_t dual;
+};
+
+// Compaction work (S6, S7) beyond Ctx.
+struct CompactCtx {
+    int32_t *r_keep, *r_len, *r_pos, *r_off;   // keep flag, new length, new index, new offset
+    int32_t *c_keep, *c_len, *c_pos, *c_off;
+    double *shift;                             // per row: sum of a_ij * v_j over fixed j
+    int32_t *chr_cnt, *chr_off;                // per CSR chunk: kept entries, offset in segment
+    double *chr_shift;
+    int32_t *cht_cnt, *cht_off;                // per CSC chunk
+    double *contrib;                           // per column: c_j * v_j of fixed columns
+    double *offset;                            // [nlp] objective constant
+    double *offset_part;                       // two-level sum partials
+    int32_t *lp_first, *lp_last;               // [nlp] current column range of each LP
+    uint8_t *lp_dead;                          // [nlp] a verdict was reached
+    // next buffers
+    int32_t *rp2, *ci2;
+    double *rv2;
+    int32_t *cp2, *ri2;
+    double *cv2;
+    double *L2, *U2;
+    int32_t *rmap2, *lp_row2;
+    double2 *lu2;
+    double *c2;
+    int32_t *cmap2, *lp_col2;
+};
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+// finite test and sign test on the bit pattern (integer pipes, not FP64)
+__device__ __forceinline__ bool is_fin(double x) {
+    return (dbits(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool is_neg(double x) { return dbits(x) < 0; }
+// max(1, |x|) with the comparison done on the bit pattern
+__device__ __forceinline__ double max1abs(double x) {
+    const long long b = dbits(x) & 0x7fffffffffffffffLL;
+    return b > 0x3ff0000000000000LL ? __longlong_as_double(b) : 1.0;
+}
+
+// Order-preserving map of a double to uint64: x < y <=> enc(x) < enc(y)
+// for all non-NaN x, y (used by atomicMin / atomicMax on doubles).
 __device__ __forceinline__ unsigned long long enc_dbl(double x) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long b = (unsigned long long)dbits(x);
     return (b & 0x8000000000000000ULL) ? ~b : (b | 0x8000000000000000ULL);
 }
 __device__ __forceinline__ double dec_dbl(unsigned long long e) {
-    unsigned long long b = (e & 0x8000000000000000ULL) ? (e & 0x7fffffffffffffffULL) : ~e;
+    const unsigned long long b = (e & 0x8000000000000000ULL) ? (e & 0x7fffffffffffffffULL) : ~e;
     return __longlong_as_double((long long)b);
 }
-__device__ __forceinline__ bool is_fin(double x) { return fabs(x) < __longlong_as_double(0x7ff0000000000000LL); }
+constexpr unsigned long long kEncNegInf = 0x000fffffffffffffULL;  // enc(-inf)
+constexpr unsigned long long kEncPosInf = 0xfff0000000000000ULL;  // enc(+inf)
 
 __device__ __forceinline__ void atomic_min_dbl(unsigned long long *p, double v) {
-    unsigned long long e = enc_dbl(v);
+    const unsigned long long e = enc_dbl(v);
     if (e < *((volatile unsigned long long *)p)) atomicMin(p, e);
 }
 __device__ __forceinline__ void atomic_max_dbl(unsigned long long *p, double v) {
-    unsigned long long e = enc_dbl(v);
+    const unsigned long long e = enc_dbl(v);
     if (e > *((volatile unsigned long long *)p)) atomicMax(p, e);
 }
 
-// 64-bit mixer (the finaliser of SplitMix64, Steele et al. 2014)
+// 64-bit mixer: the output function of SplitMix64 (Steele, Lea, Flood 2014)
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     z += 0x9e3779b97f4a7c15ULL;
     z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
@@ -104,28 +184,52 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
-// normalised coefficient rounded to qbits mantissa bits (round to nearest on
-// the bit pattern), the coefficient part of the parallel-row key (Sec. 3.2)
-__device__ __forceinline__ unsigned long long quantise(double x, int qbits) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    int drop = 52 - qbits;
-    if (drop <= 0) return b;
-    b += 1ULL << (drop - 1);
-    return b & ~((1ULL << drop) - 1ULL);
+// ------------------------------------------------------------- lane groups
+// bits [0, W) set
+template <int W>
+__device__ __forceinline__ unsigned low_bits() {
+    if constexpr (W == 32) return 0xffffffffu;
+    else return (1u << W) - 1u;
 }
-
-// --------------------------------------------------------------- lane groups
+// the lanes of this thread's group of W lanes
 template <int W>
 __device__ __forceinline__ unsigned group_mask() {
-    if (W == 32) return 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    return ((1u << W) - 1u) << (lane & ~(W - 1));
+    return low_bits<W>() << ((threadIdx.x & 31) & ~(W - 1));
 }
+// bits of `bal` (a warp ballot) that belong to this thread's group, shifted to 0
+template <int W>
+__device__ __forceinline__ unsigned group_bits(unsigned bal) {
+    return (bal >> ((threadIdx.x & 31) & ~(W - 1))) & low_bits<W>();
+}
+// xor butterfly: every lane of the group ends with the same bits (a + b == b + a)
 template <int W, typename T>
 __device__ __forceinline__ T group_sum(T v, unsigned mask) {
 #pragma unroll
     for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, W);
     return v;
+}
+
+// block-aggregated counter: one atomic per block
+__device__ __forceinline__ void block_add(int32_t v, int32_t *dst) {
+    __shared__ int32_t s_acc;
+    if (threadIdx.x == 0) s_acc = 0;
+    __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_acc, v);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_acc) atomicAdd(dst, s_acc);
+}
+
+// Which class / block-in-class a block of a group launch serves.
+struct GroupGrid {
+    int32_t blk_start[7];  // first block of classes 0..5, [6] = total blocks
+};
+__device__ __forceinline__ int grid_class(const GroupGrid &g, int b) {
+    int c = 0;
+#pragma unroll
+    for (int k = 1; k < 6; k++) c += b >= g.blk_start[k];
+    return c;
 }
 
 }  // namespace lpp

@@ -1,0 +1,609 @@
+// lpp_engine.cu -- device state and the round loop (S0 .. S8) of the presolve.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+#include "lpp_engine.h"
+
+namespace lpp {
+
+void cuda_check(cudaError_t e, const char *expr, const char *file, int line) {
+    if (e == cudaSuccess) return;
+    char buf[512];
+    std::snprintf(buf, sizeof buf, "%s failed: %s (%s:%d)", expr, cudaGetErrorString(e), file, line);
+    if (e == cudaErrorMemoryAllocation) throw StatusError(LPP_ERR_OOM, buf);
+    throw CudaError(e, buf);
+}
+
+void DevPool::forget(void *p) {
+    auto it = std::find(ptrs.begin(), ptrs.end(), p);
+    if (it != ptrs.end()) ptrs.erase(it);
+}
+void DevPool::release() {
+    for (void *p : ptrs) cudaFreeAsync(p, s);
+    ptrs.clear();
+}
+
+namespace {
+
+int32_t pow2_at_least(int64_t v) {
+    int64_t p = 2;
+    while (p < v) p <<= 1;
+    return (int32_t)p;
+}
+
+// batch ingest from device inputs: one block row per LP copies and rebases
+struct SrcDesc {
+    const int32_t *rp, *ci;
+    const double *v, *c, *lhs, *rhs, *lb, *ub;
+    int32_t m, n;
+    int64_t nnz;
+    int32_t row_off, col_off;
+    int64_t nnz_off;
+};
+
+__global__ void k_gather_lps(const SrcDesc *d, int32_t *rp, int32_t *ci, double *v, double *lhs, double *rhs,
+                             double *lb, double *ub, double *c, int32_t *lprow, int32_t *lpcol, int32_t *err) {
+    const SrcDesc D = d[blockIdx.y];
+    const int32_t k = blockIdx.y;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = t0; i < D.m; i += step) {
+        const int32_t p = D.rp[i];
+        if (p < 0 || p > D.nnz) atomicOr(err, 1);
+        rp[D.row_off + i] = (int32_t)(D.nnz_off + p);
+        lhs[D.row_off + i] = D.lhs[i];
+        rhs[D.row_off + i] = D.rhs[i];
+        lprow[D.row_off + i] = k;
+    }
+    if (t0 == 0 && (D.rp[0] != 0 || D.rp[D.m] != D.nnz)) atomicOr(err, 1);
+    for (int64_t j = t0; j < D.n; j += step) {
+        lb[D.col_off + j] = D.lb[j];
+        ub[D.col_off + j] = D.ub[j];
+        c[D.col_off + j] = D.c[j];
+        lpcol[D.col_off + j] = k;
+    }
+    for (int64_t e = t0; e < D.nnz; e += step) {
+        const int32_t j = D.ci[e];
+        if (j < 0 || j >= D.n) atomicOr(err, 2);
+        ci[D.nnz_off + e] = D.col_off + j;
+        v[D.nnz_off + e] = D.v[e];
+    }
+}
+
+__global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
+__global__ void k_sizes(const CompactCtx K, int32_t m, int32_t n, DevStatus *st) {
+    st->m_new = K.r_pos[m];
+    st->nnz_new = K.r_off[m];
+    st->n_new = K.c_pos[n];
+    st->nnz_new_t = K.c_off[n];
+}
+
+const char *kFamNames[F_NUM] = {"prop", "colfin", "s5", "compact_count", "scan", "compact_scatter", "schedule"};
+
+}  // namespace
+
+Engine::~Engine() {
+    for (auto &mk : marks) {
+        cudaEventDestroy(mk.a);
+        cudaEventDestroy(mk.b);
+    }
+    for (auto e : spare_events) cudaEventDestroy(e);
+    pool.release();
+    if (s) cudaStreamSynchronize(s);
+    if (st_h) cudaFreeHost(st_h);
+    if (verdict_h) cudaFreeHost(verdict_h);
+    if (changed_h) cudaFreeHost(changed_h);
+    if (own_stream && s) cudaStreamDestroy(s);
+}
+
+void Engine::tbegin(int fam, double bytes) {
+    if (!o.timing) return;
+    Tmark mk;
+    mk.fam = fam;
+    mk.bytes = bytes;
+    LPP_CUDA(cudaEventCreate(&mk.a));
+    LPP_CUDA(cudaEventCreate(&mk.b));
+    LPP_CUDA(cudaEventRecord(mk.a, s));
+    marks.push_back(mk);
+}
+void Engine::tend() {
+    if (!o.timing) return;
+    LPP_CUDA(cudaEventRecord(marks.back().b, s));
+}
+
+void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member> &members) {
+    o = opts;
+    nlp = nlp_;
+    mem = members;
+    m0 = n0 = 0;
+    nnz0 = 0;
+    for (const Member &x : mem) {
+        m0 += x.m;
+        n0 += x.n;
+        nnz0 += x.nnz;
+    }
+    if (nnz0 >= 2147483647LL) throw StatusError(LPP_ERR_INVALID, "nnz must be < 2^31");
+    LPP_CUDA(cudaSetDevice(o.device));
+    if (o.stream) {
+        s = static_cast<cudaStream_t>(o.stream);
+    } else {
+        LPP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        own_stream = true;
+    }
+    pool.s = s;
+    LPP_CUDA(cudaMallocHost(&st_h, sizeof(DevStatus)));
+    LPP_CUDA(cudaMallocHost(&verdict_h, sizeof(int32_t) * (size_t)nlp * V_SLOTS));
+    LPP_CUDA(cudaMallocHost(&changed_h, (size_t)nlp));
+    const bool arena = nlp > 1;
+    for (int b = 0; b < 2; b++) {
+        rp[b] = pool.alloc<int32_t>(m0 + 1);
+        ci[b] = pool.alloc<int32_t>(nnz0);
+        rv[b] = pool.alloc<double>(nnz0);
+        tp[b] = pool.alloc<int32_t>(n0 + 1);
+        ti[b] = pool.alloc<int32_t>(nnz0);
+        tv[b] = pool.alloc<double>(nnz0);
+        L[b] = pool.alloc<double>(m0);
+        U[b] = pool.alloc<double>(m0);
+        rmap[b] = pool.alloc<int32_t>(m0);
+        lu[b] = pool.alloc<double2>(n0);
+        c[b] = pool.alloc<double>(n0);
+        cmap[b] = pool.alloc<int32_t>(n0);
+        lprow[b] = arena ? pool.alloc<int32_t>(m0) : nullptr;
+        lpcol[b] = arena ? pool.alloc<int32_t>(n0) : nullptr;
+    }
+    cap_long_a = sched_cap_long(nnz0);
+    cap_long_t = cap_long_a;
+    const int64_t cap_chunk = nnz0 / kChunk + cap_long_a + 1;
+    const int64_t max_scan = std::max<int64_t>({nnz0 + 1, (int64_t)transpose_hist_elems(nnz0),
+                                                (int64_t)sched_tile_hist_elems(std::max(m0, n0)), m0 + 1, n0 + 1,
+                                                (int64_t)cap_long_a + 1});
+    scan_tmp = pool.alloc<int32_t>(scan_tmp_elems(max_scan));
+    for (int w = 0; w < 2; w++) {
+        SchedBufs &b = w == 0 ? sa : sb;
+        const int32_t cnt = w == 0 ? m0 : n0;
+        b.order = pool.alloc<int32_t>(cnt);
+        b.chunks = pool.alloc<Chunk>(cap_chunk);
+        b.lfirst = pool.alloc<int32_t>(cap_long_a + 1);
+        b.nch = pool.alloc<int32_t>(cap_long_a + 1);
+        b.tile_hist = pool.alloc<int32_t>(sched_tile_hist_elems(cnt));
+        b.tmp = scan_tmp;
+    }
+    act = pool.alloc<double2>(m0);
+    ninf = pool.alloc<int2>(m0);
+    rkind = pool.alloc<uint8_t>(m0);
+    rwork = pool.alloc<uint8_t>(m0);
+    hasf = pool.alloc<uint8_t>(m0);
+    hrow = pool.alloc<unsigned long long>(m0);
+    mL = pool.alloc<unsigned long long>(m0);
+    mU = pool.alloc<unsigned long long>(m0);
+    rslot = pool.alloc<int32_t>(m0);
+    cand_l = pool.alloc<unsigned long long>(n0);
+    cand_u = pool.alloc<unsigned long long>(n0);
+    ckind = pool.alloc<uint8_t>(n0);
+    fixv = pool.alloc<double>(n0);
+    tcap_max = pow2_at_least(2 * (int64_t)std::max(m0, 1));
+    tkey = pool.alloc<unsigned long long>(tcap_max);
+    tlead = pool.alloc<unsigned long long>(tcap_max);
+    ch_act = pool.alloc<double2>(cap_chunk);
+    ch_ninf = pool.alloc<int2>(cap_chunk);
+    ch_hash = pool.alloc<unsigned long long>(cap_chunk);
+    lneed = pool.alloc<uint8_t>(cap_long_a + 1);
+    verdict = pool.alloc<int32_t>((size_t)nlp * V_SLOTS);
+    lp_changed = pool.alloc<uint8_t>(nlp);
+    lp_dead = pool.alloc<uint8_t>(nlp);
+    std::memset(&K, 0, sizeof K);
+    K.r_keep = pool.alloc<int32_t>(m0 + 1);
+    K.r_len = pool.alloc<int32_t>(m0 + 1);
+    K.r_pos = pool.alloc<int32_t>(m0 + 1);
+    K.r_off = pool.alloc<int32_t>(m0 + 1);
+    K.c_keep = pool.alloc<int32_t>(n0 + 1);
+    K.c_len = pool.alloc<int32_t>(n0 + 1);
+    K.c_pos = pool.alloc<int32_t>(n0 + 1);
+    K.c_off = pool.alloc<int32_t>(n0 + 1);
+    K.shift = pool.alloc<double>(m0);
+    K.chr_cnt = pool.alloc<int32_t>(cap_chunk);
+    K.chr_off = pool.alloc<int32_t>(cap_chunk);
+    K.chr_shift = pool.alloc<double>(cap_chunk);
+    K.cht_cnt = pool.alloc<int32_t>(cap_chunk);
+    K.cht_off = pool.alloc<int32_t>(cap_chunk);
+    K.contrib = pool.alloc<double>(n0);
+    K.offset = pool.alloc<double>(nlp);
+    K.offset_part = pool.alloc<double>(n0 / kScanTile + 2);
+    K.lp_first = pool.alloc<int32_t>(nlp);
+    K.lp_last = pool.alloc<int32_t>(nlp);
+    K.lp_dead = lp_dead;
+    rec_rk = pool.alloc<int32_t>(m0);
+    rec_rr = pool.alloc<int32_t>(m0);
+    rec_ra = pool.alloc<int32_t>(m0);
+    rec_rv = pool.alloc<double>(m0);
+    rec_ck = pool.alloc<int32_t>(n0);
+    rec_cr = pool.alloc<int32_t>(n0);
+    rec_cv = pool.alloc<double>(n0);
+    st = pool.alloc<DevStatus>(1);
+    LPP_CUDA(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
+}
+
+void Engine::ingest_plain(const lpp_lp &in) {
+    const cudaMemcpyKind kind = in.on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    LPP_CUDA(cudaMemcpyAsync(rp[0], in.row_ptr, sizeof(int32_t) * (size_t)(in.m + 1), kind, s));
+    if (in.nnz > 0) {
+        LPP_CUDA(cudaMemcpyAsync(ci[0], in.col_idx, sizeof(int32_t) * (size_t)in.nnz, kind, s));
+        LPP_CUDA(cudaMemcpyAsync(rv[0], in.val, sizeof(double) * (size_t)in.nnz, kind, s));
+    }
+    // vectors: staged in the second buffers, checked and normalised into the first
+    double *slhs = L[1], *srhs = U[1], *slb = reinterpret_cast<double *>(lu[1]), *sub = slb + n0, *sc = c[1];
+    if (in.m > 0) {
+        LPP_CUDA(cudaMemcpyAsync(slhs, in.lhs, sizeof(double) * (size_t)in.m, kind, s));
+        LPP_CUDA(cudaMemcpyAsync(srhs, in.rhs, sizeof(double) * (size_t)in.m, kind, s));
+    }
+    if (in.n > 0) {
+        LPP_CUDA(cudaMemcpyAsync(slb, in.lb, sizeof(double) * (size_t)in.n, kind, s));
+        LPP_CUDA(cudaMemcpyAsync(sub, in.ub, sizeof(double) * (size_t)in.n, kind, s));
+        LPP_CUDA(cudaMemcpyAsync(sc, in.c, sizeof(double) * (size_t)in.n, kind, s));
+    }
+    ingest_vectors(slhs, srhs, slb, sub, sc, m0, n0, o.huge, L[0], U[0], lu[0], c[0], &st->err, s);
+}
+
+void Engine::ingest_batch(const lpp_lp *ins, int32_t count) {
+    double *slhs = L[1], *srhs = U[1], *slb = reinterpret_cast<double *>(lu[1]), *sub = slb + n0, *sc = c[1];
+    const bool dev = ins[0].on_device != 0;
+    for (int32_t k = 0; k < count; k++)
+        if ((ins[k].on_device != 0) != dev) throw StatusError(LPP_ERR_INVALID, "batch mixes host and device inputs");
+    if (dev) {
+        std::vector<SrcDesc> d(count);
+        for (int32_t k = 0; k < count; k++) {
+            const lpp_lp &x = ins[k];
+            d[k] = SrcDesc{x.row_ptr, x.col_idx, x.val, x.c, x.lhs, x.rhs, x.lb, x.ub, x.m, x.n, x.nnz,
+                           mem[k].row_off, mem[k].col_off, mem[k].nnz_off};
+        }
+        SrcDesc *dd = pool.alloc<SrcDesc>(count);
+        LPP_CUDA(cudaMemcpyAsync(dd, d.data(), sizeof(SrcDesc) * count, cudaMemcpyHostToDevice, s));
+        // the host vector must outlive the copy
+        LPP_CUDA(cudaStreamSynchronize(s));
+        dim3 grid(8, (unsigned)count);
+        k_gather_lps<<<grid, 256, 0, s>>>(dd, rp[0], ci[0], rv[0], slhs, srhs, slb, sub, sc, lprow[0], lpcol[0],
+                                          &st->err);
+        LPP_CUDA(cudaGetLastError());
+    } else {
+        // pack on the host into pinned staging, then one copy per array
+        std::vector<int32_t> h_rp((size_t)m0 + 1), h_ci((size_t)nnz0), h_lr((size_t)m0), h_lc((size_t)n0);
+        std::vector<double> h_v((size_t)nnz0), h_l((size_t)m0), h_r((size_t)m0), h_lb((size_t)n0),
+            h_ub((size_t)n0), h_c((size_t)n0);
+        for (int32_t k = 0; k < count; k++) {
+            const lpp_lp &x = ins[k];
+            const Member &mm = mem[k];
+            if (x.m > 0 && (x.row_ptr[0] != 0 || x.row_ptr[x.m] != x.nnz))
+                throw StatusError(LPP_ERR_INVALID, "row_ptr does not match nnz");
+            for (int32_t i = 0; i < x.m; i++) {
+                h_rp[mm.row_off + i] = (int32_t)(mm.nnz_off + x.row_ptr[i]);
+                h_l[mm.row_off + i] = x.lhs[i];
+                h_r[mm.row_off + i] = x.rhs[i];
+                h_lr[mm.row_off + i] = k;
+            }
+            for (int32_t j = 0; j < x.n; j++) {
+                h_lb[mm.col_off + j] = x.lb[j];
+                h_ub[mm.col_off + j] = x.ub[j];
+                h_c[mm.col_off + j] = x.c[j];
+                h_lc[mm.col_off + j] = k;
+            }
+            for (int64_t e = 0; e < x.nnz; e++) {
+                const int32_t j = x.col_idx[e];
+                if (j < 0 || j >= x.n) throw StatusError(LPP_ERR_INVALID, "column index out of range");
+                h_ci[mm.nnz_off + e] = mm.col_off + j;
+                h_v[mm.nnz_off + e] = x.val[e];
+            }
+        }
+        h_rp[m0] = (int32_t)nnz0;
+        auto up = [&](void *dst, const void *src, size_t bytes) {
+            if (bytes) LPP_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+        };
+        up(rp[0], h_rp.data(), sizeof(int32_t) * h_rp.size());
+        up(ci[0], h_ci.data(), sizeof(int32_t) * h_ci.size());
+        up(rv[0], h_v.data(), sizeof(double) * h_v.size());
+        up(slhs, h_l.data(), sizeof(double) * h_l.size());
+        up(srhs, h_r.data(), sizeof(double) * h_r.size());
+        up(slb, h_lb.data(), sizeof(double) * h_lb.size());
+        up(sub, h_ub.data(), sizeof(double) * h_ub.size());
+        up(sc, h_c.data(), sizeof(double) * h_c.size());
+        up(lprow[0], h_lr.data(), sizeof(int32_t) * h_lr.size());
+        up(lpcol[0], h_lc.data(), sizeof(int32_t) * h_lc.size());
+        LPP_CUDA(cudaStreamSynchronize(s));  // pageable staging must outlive the copies
+    }
+    k_set_i32<<<1, 1, 0, s>>>(rp[0] + m0, (int32_t)nnz0);
+    ingest_vectors(slhs, srhs, slb, sub, sc, m0, n0, o.huge, L[0], U[0], lu[0], c[0], &st->err, s);
+}
+
+void Engine::prepare() {
+    // S0: checks, then A^T by a stable transpose
+    int32_t *row_of = pool.alloc<int32_t>(nnz0 + 1);
+    check_csr(rp[0], ci[0], rv[0], m0, n0, nnz0, row_of, scan_tmp, &st->err, s);
+    LPP_CUDA(cudaGetLastError());
+    read_status();
+    if (st_h->err) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf,
+                      "invalid LP (checks failed: %s%s%s%s%s)", (st_h->err & 1) ? "row_ptr " : "",
+                      (st_h->err & 2) ? "col_idx-range " : "", (st_h->err & 4) ? "val-not-finite-or-zero " : "",
+                      (st_h->err & 8) ? "col_idx-not-increasing " : "", (st_h->err & 16) ? "vectors" : "");
+        throw StatusError(LPP_ERR_INVALID, buf);
+    }
+    TransposeBufs tb;
+    tb.k0 = reinterpret_cast<uint32_t *>(ci[1]);
+    tb.k1 = reinterpret_cast<uint32_t *>(ti[1]);
+    tb.v0 = reinterpret_cast<int32_t *>(rv[1]);
+    tb.v1 = reinterpret_cast<int32_t *>(rv[1]) + nnz0;
+    tb.hist = pool.alloc<int32_t>(transpose_hist_elems(nnz0));
+    tb.tmp = scan_tmp;
+    transpose(rp[0], ci[0], rv[0], row_of + 1, m0, n0, nnz0, tb, tp[0], ti[0], tv[0], K.c_len, s);
+    LPP_CUDA(cudaGetLastError());
+    iota(rmap[0], m0, 0, s);
+    iota(cmap[0], n0, 0, s);
+    fill_u64(cand_l, n0, kEncNegInf, s);
+    fill_u64(cand_u, n0, kEncPosInf, s);
+    fill_u64(mL, m0, kEncNegInf, s);
+    fill_u64(mU, m0, kEncPosInf, s);
+    LPP_CUDA(cudaMemsetAsync(hasf, 0, (size_t)std::max(m0, 1), s));
+    LPP_CUDA(cudaMemsetAsync(rwork, 0, (size_t)std::max(m0, 1), s));
+    fill_i32(verdict, (int64_t)nlp * V_SLOTS, kNone, s);
+    LPP_CUDA(cudaMemsetAsync(rec_rk, 0, sizeof(int32_t) * (size_t)std::max(m0, 1), s));
+    LPP_CUDA(cudaMemsetAsync(rec_rr, 0, sizeof(int32_t) * (size_t)std::max(m0, 1), s));
+    fill_i32(rec_ra, m0, -1, s);
+    LPP_CUDA(cudaMemsetAsync(rec_rv, 0, sizeof(double) * (size_t)std::max(m0, 1), s));
+    LPP_CUDA(cudaMemsetAsync(rec_ck, 0, sizeof(int32_t) * (size_t)std::max(n0, 1), s));
+    LPP_CUDA(cudaMemsetAsync(rec_cr, 0, sizeof(int32_t) * (size_t)std::max(n0, 1), s));
+    LPP_CUDA(cudaMemsetAsync(rec_cv, 0, sizeof(double) * (size_t)std::max(n0, 1), s));
+    std::vector<double> offs(nlp);
+    for (int32_t k = 0; k < nlp; k++) offs[k] = mem[k].obj_offset;
+    LPP_CUDA(cudaMemcpyAsync(K.offset, offs.data(), sizeof(double) * nlp, cudaMemcpyHostToDevice, s));
+    m = m0;
+    n = n0;
+    nnz = nnz0;
+    cur = 0;
+    A.ptr = rp[0];
+    schedule_current();
+    LPP_CUDA(cudaStreamSynchronize(s));  // offs outlives its copy
+}
+
+void Engine::schedule_current() {
+    build_schedule(rp[cur], m, nnz, sa, st->cls_r, &st->nchunk_r, s);
+    build_schedule(tp[cur], n, nnz, sb, st->cls_c, &st->nchunk_c, s);
+    LPP_CUDA(cudaGetLastError());
+    read_status();
+    A.ptr = rp[cur];
+    A.idx = ci[cur];
+    A.val = rv[cur];
+    A.order = sa.order;
+    A.chunks = sa.chunks;
+    A.lfirst = sa.lfirst;
+    A.cnt = m;
+    segmat_from_counts(A, st_h->cls_r, st_h->nchunk_r);
+    T.ptr = tp[cur];
+    T.idx = ti[cur];
+    T.val = tv[cur];
+    T.order = sb.order;
+    T.chunks = sb.chunks;
+    T.lfirst = sb.lfirst;
+    T.cnt = n;
+    segmat_from_counts(T, st_h->cls_c, st_h->nchunk_c);
+    if (A.cls_start[kNumClass] != m || T.cls_start[kNumClass] != n)
+        throw StatusError(LPP_ERR_CUDA, "internal: schedule does not cover every segment");
+}
+
+void Engine::read_status() {
+    LPP_CUDA(cudaMemcpyAsync(st_h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    LPP_CUDA(cudaMemcpyAsync(verdict_h, verdict, sizeof(int32_t) * (size_t)nlp * V_SLOTS, cudaMemcpyDeviceToHost, s));
+    LPP_CUDA(cudaMemcpyAsync(changed_h, lp_changed, (size_t)nlp, cudaMemcpyDeviceToHost, s));
+    LPP_CUDA(cudaStreamSynchronize(s));
+}
+
+Ctx Engine::ctx(int32_t round) const {
+    Ctx C;
+    std::memset(&C, 0, sizeof C);
+    C.A = A;
+    C.T = T;
+    C.m = m;
+    C.n = n;
+    C.nlp = nlp;
+    C.round = round;
+    C.L = L[cur];
+    C.U = U[cur];
+    C.rmap = rmap[cur];
+    C.lp_row = lprow[cur];
+    C.lu = lu[cur];
+    C.c = c[cur];
+    C.cmap = cmap[cur];
+    C.lp_col = lpcol[cur];
+    C.act = act;
+    C.ninf = ninf;
+    C.rkind = rkind;
+    C.rwork = rwork;
+    C.hrow = hrow;
+    C.rslot = rslot;
+    C.mL = mL;
+    C.mU = mU;
+    C.hasf = hasf;
+    C.cand_l = cand_l;
+    C.cand_u = cand_u;
+    C.ckind = ckind;
+    C.fixv = fixv;
+    C.tkey = tkey;
+    C.tlead = tlead;
+    C.tcap = 2;
+    C.ch_act = ch_act;
+    C.ch_ninf = ch_ninf;
+    C.ch_hash = ch_hash;
+    C.lneed = lneed;
+    C.rec_rk = rec_rk;
+    C.rec_rr = rec_rr;
+    C.rec_ra = rec_ra;
+    C.rec_rv = rec_rv;
+    C.rec_ck = rec_ck;
+    C.rec_cr = rec_cr;
+    C.rec_cv = rec_cv;
+    C.verdict = verdict;
+    C.lp_changed = lp_changed;
+    C.st = st;
+    C.feas_tol = o.feas_tol;
+    C.bound_tol = o.bound_tol;
+    C.max_implied = o.max_implied;
+    C.par_tol = o.par_tol;
+    C.dual = o.dual_reductions;
+    return C;
+}
+
+void Engine::compact(int32_t round) {
+    const int nx = cur ^ 1;
+    K.rp2 = rp[nx];
+    K.ci2 = ci[nx];
+    K.rv2 = rv[nx];
+    K.cp2 = tp[nx];
+    K.ri2 = ti[nx];
+    K.cv2 = tv[nx];
+    K.L2 = L[nx];
+    K.U2 = U[nx];
+    K.rmap2 = rmap[nx];
+    K.lp_row2 = lprow[nx];
+    K.lu2 = lu[nx];
+    K.c2 = c[nx];
+    K.cmap2 = cmap[nx];
+    K.lp_col2 = lpcol[nx];
+    const Ctx C = ctx(round);
+    tbegin(F_COUNT, 4.0 * nnz * 2 + 8.0 * nnz + 24.0 * m + 40.0 * n);
+    launch_compact_counts(C, K, s);
+    tend();
+    tbegin(F_SCAN, 16.0 * (m + n) * 2);
+    scan_excl(K.r_keep, K.r_pos, m, scan_tmp, s);
+    scan_excl(K.r_len, K.r_off, m, scan_tmp, s);
+    scan_excl(K.c_keep, K.c_pos, n, scan_tmp, s);
+    scan_excl(K.c_len, K.c_off, n, scan_tmp, s);
+    tend();
+    launch_offset(C, K, s);
+    k_sizes<<<1, 1, 0, s>>>(K, m, n, st);
+    LPP_CUDA(cudaGetLastError());
+    read_status();
+    const int32_t m_new = st_h->m_new, n_new = st_h->n_new, nnz_new = st_h->nnz_new;
+    if (nnz_new != st_h->nnz_new_t || m_new < 0 || m_new > m || n_new < 0 || n_new > n || nnz_new > nnz)
+        throw StatusError(LPP_ERR_CUDA, "internal: compaction sizes disagree");
+    tbegin(F_SCATTER, 24.0 * nnz + 24.0 * nnz_new * 2 / 2 + 48.0 * (m + n));
+    launch_compact_scatter(C, K, m_new, n_new, s);
+    tend();
+    LPP_CUDA(cudaGetLastError());
+    cur = nx;
+    m = m_new;
+    n = n_new;
+    nnz = nnz_new;
+    tbegin(F_SCHED, 8.0 * (m + n));
+    schedule_current();
+    tend();
+}
+
+void Engine::run() {
+    const int32_t R = std::max(0, o.max_rounds);
+    lp_rounds.assign(nlp, 0);
+    lp_status.assign(nlp, LPP_OK);
+    lp_where.assign(nlp, LPP_WHERE_NONE);
+    lp_index.assign(nlp, -1);
+    lp_round.assign(nlp, 0);
+    lp_done.assign(nlp, 0);
+    std::vector<uint8_t> dropped(nlp, 0);
+    cudaEvent_t e0, e1, eloop;
+    LPP_CUDA(cudaEventCreate(&e0));
+    LPP_CUDA(cudaEventCreate(&e1));
+    LPP_CUDA(cudaEventCreate(&eloop));
+    spare_events.push_back(e0);
+    spare_events.push_back(e1);
+    spare_events.push_back(eloop);
+    LPP_CUDA(cudaEventRecord(eloop, s));
+    int32_t live = nlp;
+    for (int32_t r = 1; r <= R && live > 0; r++) {
+        act_m = m;
+        act_buf = cur;
+        r_nnz.push_back(nnz);
+        nnz_processed += nnz;
+        LPP_CUDA(cudaEventRecord(e0, s));
+        LPP_CUDA(cudaMemsetAsync(st, 0, 8 * sizeof(int32_t), s));
+        LPP_CUDA(cudaMemsetAsync(lp_changed, 0, (size_t)nlp, s));
+        Ctx C = ctx(r);
+        tbegin(F_PROP, 12.0 * nnz + 4.0 * (m + 1) + 16.0 * m + 16.0 * n + 33.0 * m);
+        launch_prop(C, s);
+        tend();
+        tbegin(F_COLFIN, 33.0 * n);
+        launch_colfin(C, s);
+        tend();
+        LPP_CUDA(cudaGetLastError());
+        // S5: leader passes
+        int32_t tcap = std::min(tcap_max, pow2_at_least(2 * (int64_t)std::max(m, 1)));
+        tbegin(F_S5, 16.0 * tcap + 12.0 * m);
+        LPP_CUDA(cudaMemsetAsync(tkey, 0, sizeof(unsigned long long) * tcap, s));
+        LPP_CUDA(cudaMemsetAsync(tlead, 0xff, sizeof(unsigned long long) * tcap, s));
+        C.tcap = tcap;
+        launch_s5_pass(C, 0, s);
+        tend();
+        LPP_CUDA(cudaGetLastError());
+        read_status();
+        for (int pass = 1; st_h->unmatched > 0 && pass < o.par_max_iter; pass++) {
+            tcap = std::min(tcap_max, pow2_at_least(2 * (int64_t)st_h->unmatched));
+            LPP_CUDA(cudaMemsetAsync(tkey, 0, sizeof(unsigned long long) * tcap, s));
+            LPP_CUDA(cudaMemsetAsync(tlead, 0xff, sizeof(unsigned long long) * tcap, s));
+            LPP_CUDA(cudaMemsetAsync(&st->unmatched, 0, sizeof(int32_t), s));
+            C.tcap = tcap;
+            launch_s5_pass(C, pass, s);
+            LPP_CUDA(cudaGetLastError());
+            read_status();
+        }
+        if (st_h->err) throw StatusError(LPP_ERR_CUDA, "internal: S5 hash table overflow");
+        launch_s5_leader(C, s);
+        LPP_CUDA(cudaGetLastError());
+        bool newly_dead = false;
+        for (int32_t k = 0; k < nlp; k++) {
+            if (dropped[k]) continue;
+            for (int v = 0; v < V_SLOTS; v++) newly_dead |= verdict_h[k * V_SLOTS + v] != kNone;
+        }
+        const bool structural = r == 1 || st_h->rows_removed > 0 || st_h->cols_fixed > 0 || newly_dead;
+        int32_t rows_removed = st_h->rows_removed, bounds = st_h->bounds_changed;
+        if (structural) compact(r);
+        LPP_CUDA(cudaEventRecord(e1, s));
+        read_status();
+        float ms = 0.f;
+        LPP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        r_ms.push_back(ms);
+        r_rows.push_back(rows_removed);
+        r_cols.push_back(st_h->cols_fixed);
+        r_bounds.push_back(bounds);
+        rounds = r;
+        for (int32_t k = 0; k < nlp; k++) {
+            if (lp_done[k]) {
+                if (structural && lp_status[k] != LPP_OK) dropped[k] = 1;
+                continue;
+            }
+            int v = 0;
+            while (v < V_SLOTS && verdict_h[k * V_SLOTS + v] == kNone) v++;
+            if (v < V_SLOTS) {
+                lp_status[k] = v == V_S6_COL ? LPP_UNBOUNDED : LPP_INFEASIBLE;
+                lp_where[k] = (v == V_S2_ROW || v == V_S5_ROW) ? LPP_WHERE_ROW : LPP_WHERE_COL;
+                lp_index[k] = verdict_h[k * V_SLOTS + v];
+                lp_round[k] = r;
+                lp_rounds[k] = r;
+                lp_done[k] = 1;
+                if (structural) dropped[k] = 1;
+                live--;
+            } else if (!changed_h[k]) {
+                lp_rounds[k] = r;
+                lp_done[k] = 1;
+                live--;
+            } else {
+                lp_rounds[k] = r;
+            }
+        }
+    }
+    float lms = 0.f;
+    LPP_CUDA(cudaEventRecord(e1, s));
+    LPP_CUDA(cudaEventSynchronize(e1));
+    LPP_CUDA(cudaEventElapsedTime(&lms, eloop, e1));
+    loop_ms = lms;
+}
+
+const char *fam_name(int f) { return kFamNames[f]; }
+
+}  // namespace lpp

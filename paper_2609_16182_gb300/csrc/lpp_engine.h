@@ -1,0 +1,176 @@
+// lpp_engine.h -- the presolve engine behind the C ABI (internal).
+//
+// One Engine owns the device state of an "arena": one LP (plain mode) or many
+// LPs laid out back to back as one block-diagonal LP (batch and serving).
+// Every kernel sees the arena as a single LP; per-LP bookkeeping (verdicts,
+// rounds, objective constant) uses lp_row / lp_col.  Because a row's or a
+// column's arithmetic never depends on its neighbours, an LP's result in an
+// arena equals its result alone.
+#pragma once
+#include <cstdint>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/lpp.h"
+#include "lpp_launch.h"
+
+namespace lpp {
+
+struct CudaError : std::runtime_error {
+    cudaError_t code;
+    CudaError(cudaError_t c, const std::string &what) : std::runtime_error(what), code(c) {}
+};
+struct StatusError : std::runtime_error {
+    lpp_status st;
+    StatusError(lpp_status s, const std::string &what) : std::runtime_error(what), st(s) {}
+};
+
+void cuda_check(cudaError_t e, const char *expr, const char *file, int line);
+#define LPP_CUDA(x) ::lpp::cuda_check((x), #x, __FILE__, __LINE__)
+
+// stream-ordered device allocations released together
+struct DevPool {
+    cudaStream_t s = nullptr;
+    std::vector<void *> ptrs;
+    template <class T>
+    T *alloc(size_t cnt) {
+        void *p = nullptr;
+        LPP_CUDA(cudaMallocAsync(&p, (cnt ? cnt : 1) * sizeof(T), s));
+        ptrs.push_back(p);
+        return static_cast<T *>(p);
+    }
+    void forget(void *p);  // ownership moves elsewhere
+    void release();
+    ~DevPool() { release(); }
+};
+
+// per-LP description of an arena member
+struct Member {
+    int32_t m, n;
+    int64_t nnz;
+    int32_t row_off, col_off;
+    int64_t nnz_off;
+    double obj_offset;
+};
+
+// Device buffers and host mirror of one arena.
+struct Engine {
+    lpp_opts o;
+    cudaStream_t s = nullptr;
+    bool own_stream = false;
+    DevPool pool;
+    int32_t nlp = 1;
+    std::vector<Member> mem;
+    int32_t m0 = 0, n0 = 0;
+    int64_t nnz0 = 0;
+    // current sizes
+    int32_t m = 0, n = 0;
+    int64_t nnz = 0;
+    int cur = 0;
+    // double buffers
+    int32_t *rp[2], *ci[2], *tp[2], *ti[2];
+    double *rv[2], *tv[2];
+    double *L[2], *U[2], *c[2];
+    double2 *lu[2];
+    int32_t *rmap[2], *cmap[2], *lprow[2], *lpcol[2];
+    // schedules
+    SchedBufs sa, sb;  // A (rows), T (columns)
+    int32_t cap_long_a, cap_long_t;
+    // work
+    double2 *act;
+    int2 *ninf;
+    uint8_t *rkind, *rwork, *hasf, *ckind, *lneed, *lp_changed, *lp_dead;
+    unsigned long long *hrow, *mL, *mU, *cand_l, *cand_u, *tkey, *tlead, *ch_hash;
+    int32_t *rslot, *verdict;
+    double *fixv;
+    double2 *ch_act;
+    int2 *ch_ninf;
+    int32_t tcap_max;
+    // compaction work
+    CompactCtx K;
+    int32_t *scan_tmp;
+    // records
+    int32_t *rec_rk, *rec_rr, *rec_ra, *rec_ck, *rec_cr;
+    double *rec_rv, *rec_cv;
+    DevStatus *st;
+    DevStatus *st_h = nullptr;  // pinned mirror
+    int32_t *verdict_h = nullptr;
+    uint8_t *changed_h = nullptr;
+    SegMat A, T;
+    // per-LP results
+    std::vector<int32_t> lp_rounds, lp_status, lp_where, lp_index, lp_round;
+    std::vector<uint8_t> lp_done;
+    // per-round statistics
+    std::vector<int64_t> r_nnz;
+    std::vector<int32_t> r_rows, r_cols, r_bounds;
+    std::vector<float> r_ms;
+    int32_t rounds = 0;
+    double loop_ms = 0.0;
+    int64_t nnz_processed = 0;
+    // activities of the last round: current-index arrays and the map valid then
+    int32_t act_m = 0, act_buf = 0;
+    // kernel timing
+    struct Tmark {
+        int fam;
+        cudaEvent_t a, b;
+        double bytes;
+    };
+    std::vector<Tmark> marks;
+    std::vector<cudaEvent_t> spare_events;
+
+    ~Engine();
+    void setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member> &members);
+    // ingest: the LPs' arrays are copied into the arena and checked
+    void ingest_plain(const lpp_lp &in);
+    void ingest_batch(const lpp_lp *ins, int32_t count);
+    void prepare();  // after ingest: transpose, schedules, work init
+    void run();      // the round loop
+    Ctx ctx(int32_t round) const;
+    void read_status();
+    void schedule_current();
+    void compact(int32_t round);
+    // timing helpers
+    void tbegin(int fam, double bytes);
+    void tend();
+};
+
+// Kernel families reported by lpp_result_kernels.
+enum Fam { F_PROP = 0, F_COLFIN, F_S5, F_COUNT, F_SCAN, F_SCATTER, F_SCHED, F_NUM };
+const char *fam_name(int f);
+
+// device allocations shared by the reduced LPs of one batch, freed with the last
+struct SharedStore {
+    std::vector<void *> ptrs;
+    ~SharedStore() {
+        for (void *p : ptrs) cudaFree(p);
+    }
+};
+
+}  // namespace lpp
+
+// Library objects behind the opaque C handles.
+struct lpp_reduced {
+    int32_t m = 0, n = 0;
+    int64_t nnz = 0;
+    double obj_offset = 0.0;
+    int32_t *rp = nullptr, *ci = nullptr, *tp = nullptr, *ti = nullptr, *rmap = nullptr, *cmap = nullptr;
+    double *rv = nullptr, *tv = nullptr, *L = nullptr, *U = nullptr, *lb = nullptr, *ub = nullptr, *c = nullptr;
+    std::vector<void *> owned;  // device allocations
+    std::shared_ptr<lpp::SharedStore> shared;  // batch: storage shared with the other LPs
+    // host copies made on demand by lpp_reduced_view(on_device = 0)
+    std::vector<int32_t> h_rp, h_ci, h_tp, h_ti, h_rmap, h_cmap;
+    std::vector<double> h_rv, h_c, h_L, h_U, h_lb, h_ub, h_tv;
+};
+
+struct lpp_postsolve {
+    lpp_info info{};
+    std::vector<int32_t> row_kind, row_round, row_aux, col_kind, col_round, col_map;
+    std::vector<double> row_val, col_val, col_lb, col_ub, act_min, act_max;
+    std::vector<int32_t> ninf_min, ninf_max;
+    std::vector<int64_t> r_nnz;
+    std::vector<int32_t> r_rows, r_cols, r_bounds;
+    std::vector<float> r_ms;
+    std::vector<lpp_kernel_stat> kstats;
+};

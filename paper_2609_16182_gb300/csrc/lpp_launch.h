@@ -1,0 +1,71 @@
+// lpp_launch.h -- host-side launchers of the library's kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "lpp_dev.cuh"
+
+namespace lpp {
+
+// ----------------------------------------------------------------- k_util.cu
+// Exclusive scan of in[0..cnt) into out[0..cnt], out[cnt] = total.  `tmp`
+// must hold scan_tmp_elems(cnt) int32 values.  in == out is allowed.
+size_t scan_tmp_elems(int64_t cnt);
+void scan_excl(const int32_t *in, int32_t *out, int64_t cnt, int32_t *tmp, cudaStream_t s);
+
+// Schedule (class lists + chunks) of a segmented matrix with ptr[cnt+1].
+struct SchedBufs {
+    int32_t *order;     // [cap_seg]
+    Chunk *chunks;      // [cap_chunk]
+    int32_t *lfirst;    // [cap_long + 1]
+    int32_t *tile_hist; // [7 * tiles + 1]
+    int32_t *tmp;       // scan temporary
+    int32_t *nch;       // [cap_long + 1]
+};
+size_t sched_tile_hist_elems(int64_t cnt);
+// most long segments a matrix with nnz entries can have (sizes lfirst, nch)
+int32_t sched_cap_long(int64_t nnz);
+// Builds the schedule and writes the class sizes to cls_out[7] and the chunk
+// count to *nchunk_out (device addresses inside DevStatus).  Chunks need at
+// most nnz / kChunk + cap_long entries.
+void build_schedule(const int32_t *ptr, int32_t cnt, int64_t nnz, const SchedBufs &b, int32_t *cls_out,
+                    int32_t *nchunk_out, cudaStream_t s);
+// Fill the host-side part of a SegMat from class sizes read back.
+void segmat_from_counts(SegMat &M, const int32_t cls[kNumClass], int32_t nchunks);
+GroupGrid group_grid(const SegMat &M);
+
+// Input checks: returns error bits in *err (device).  row_of[nnz] is filled.
+void check_csr(const int32_t *ptr, const int32_t *idx, const double *val, int32_t m, int32_t n, int64_t nnz,
+               int32_t *row_of, int32_t *tmp, int32_t *err, cudaStream_t s);
+// Vectors: normalise |v| >= huge to +-inf, check NaN / wrong-signed infinity,
+// interleave (lb, ub) into lu.
+void ingest_vectors(const double *lhs, const double *rhs, const double *lb, const double *ub, const double *c,
+                    int32_t m, int32_t n, double huge, double *L, double *U, double2 *lu, double *cc, int32_t *err,
+                    cudaStream_t s);
+// A^T in CSR form (stable: rows increasing inside each column).
+struct TransposeBufs {
+    uint32_t *k0, *k1;  // keys [nnz]
+    int32_t *v0, *v1;   // values [nnz]
+    int32_t *hist;      // [256 * tiles + 1]
+    int32_t *tmp;       // scan temporary
+};
+size_t transpose_hist_elems(int64_t nnz);
+void transpose(const int32_t *ptr, const int32_t *idx, const double *val, const int32_t *row_of, int32_t m,
+               int32_t n, int64_t nnz, const TransposeBufs &b, int32_t *tptr, int32_t *tidx, double *tval,
+               int32_t *colcnt, cudaStream_t s);
+void iota(int32_t *a, int32_t cnt, int32_t base, cudaStream_t s);
+void fill_u64(unsigned long long *a, int64_t cnt, unsigned long long v, cudaStream_t s);
+void fill_i32(int32_t *a, int64_t cnt, int32_t v, cudaStream_t s);
+void split_lu(const double2 *lu, int32_t n, double *lb, double *ub, cudaStream_t s);
+
+// ---------------------------------------------------------------- k_round.cu
+void launch_prop(const Ctx &C, cudaStream_t s);
+void launch_colfin(const Ctx &C, cudaStream_t s);
+void launch_s5_pass(const Ctx &C, int pass, cudaStream_t s);
+void launch_s5_leader(const Ctx &C, cudaStream_t s);
+
+// -------------------------------------------------------------- k_compact.cu
+void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s);
+void launch_compact_scatter(const Ctx &C, const CompactCtx &K, int32_t m_new, int32_t n_new, cudaStream_t s);
+void launch_offset(const Ctx &C, const CompactCtx &K, cudaStream_t s);
+
+}  // namespace lpp

@@ -1,0 +1,352 @@
+"""Python binding of liblpp.so (include/lpp.h): argument marshalling only.
+
+Every step of the presolve runs in the CUDA library; this module turns NumPy
+arrays or CUDA torch tensors into an ``lpp_lp`` and results back into NumPy.
+There is no fallback: if the shared library is missing or cannot be loaded,
+every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+OK, INFEASIBLE, UNBOUNDED = 0, 1, 2
+ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUDGET = -1, -2, -3, -4, -5
+ROW_KEPT, ROW_EMPTY, ROW_REDUNDANT, ROW_SINGLETON, ROW_PARALLEL = 0, 1, 2, 3, 4
+COL_KEPT, COL_FIXED, COL_EMPTY = 0, 1, 2
+WHERE_NONE, WHERE_ROW, WHERE_COL = 0, 1, 2
+
+
+class LppError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lpp status {status}: {msg}")
+        self.status = status
+
+
+class LpStruct(C.Structure):
+    _fields_ = [("m", C.c_int32), ("n", C.c_int32), ("nnz", C.c_int64),
+                ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("val", C.c_void_p),
+                ("c", C.c_void_p), ("lhs", C.c_void_p), ("rhs", C.c_void_p), ("lb", C.c_void_p),
+                ("ub", C.c_void_p), ("obj_offset", C.c_double), ("on_device", C.c_int32)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("feas_tol", C.c_double), ("bound_tol", C.c_double), ("huge", C.c_double),
+                ("max_implied", C.c_double), ("par_tol", C.c_double), ("max_rounds", C.c_int32),
+                ("dual_reductions", C.c_int32), ("par_max_iter", C.c_int32), ("timing", C.c_int32),
+                ("device", C.c_int32), ("stream", C.c_void_p)]
+
+
+class Info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("where", C.c_int32), ("index", C.c_int32), ("round", C.c_int32),
+                ("rounds", C.c_int32), ("m", C.c_int32), ("n", C.c_int32), ("m_red", C.c_int32),
+                ("n_red", C.c_int32), ("nnz", C.c_int64), ("nnz_red", C.c_int64), ("obj_offset", C.c_double),
+                ("presolve_ms", C.c_double), ("nnz_processed", C.c_int64)]
+
+
+class KernelStat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int32), ("ms", C.c_double), ("bytes", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("finished", C.c_int64), ("taken", C.c_int64),
+                ("ticks", C.c_int64), ("resident_bytes", C.c_int64), ("peak_resident_bytes", C.c_int64),
+                ("max_concurrent", C.c_int32)]
+
+
+# every symbol include/lpp.h declares
+SYMBOLS = ["lpp_opts_default", "lpp_presolve", "lpp_reduced_view", "lpp_reduced_csc", "lpp_reduced_maps",
+           "lpp_result_info", "lpp_result_rows", "lpp_result_cols", "lpp_result_activity", "lpp_result_rounds",
+           "lpp_result_kernels", "lpp_postsolve_primal", "lpp_free_reduced", "lpp_free_postsolve",
+           "lpp_last_error", "lpp_presolve_batch", "lpp_server_create", "lpp_server_submit", "lpp_server_take",
+           "lpp_server_stats_get", "lpp_server_destroy"]
+
+_lib = None
+P = C.c_void_p
+PP = C.POINTER(C.c_void_p)
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load liblpp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first (__graft_entry__.build())")
+    L = C.CDLL(path)
+    L.lpp_opts_default.argtypes = [C.POINTER(Opts)]
+    L.lpp_opts_default.restype = None
+    L.lpp_presolve.argtypes = [C.POINTER(LpStruct), C.POINTER(Opts), PP, PP]
+    L.lpp_presolve_batch.argtypes = [C.POINTER(LpStruct), C.c_int32, C.POINTER(Opts), PP, PP,
+                                     C.POINTER(C.c_int32)]
+    L.lpp_reduced_view.argtypes = [P, C.POINTER(LpStruct), C.c_int32]
+    L.lpp_reduced_csc.argtypes = [P, PP, PP, PP, C.c_int32]
+    L.lpp_reduced_maps.argtypes = [P, PP, PP, C.c_int32]
+    L.lpp_result_info.argtypes = [P, C.POINTER(Info)]
+    L.lpp_result_rows.argtypes = [P, P, P, P, P]
+    L.lpp_result_cols.argtypes = [P, P, P, P, P, P]
+    L.lpp_result_activity.argtypes = [P, P, P, P, P]
+    L.lpp_result_rounds.argtypes = [P, C.c_int32, P, P, P, P, P, C.POINTER(C.c_int32)]
+    L.lpp_result_kernels.argtypes = [P, C.c_int32, C.POINTER(KernelStat), C.POINTER(C.c_int32)]
+    L.lpp_postsolve_primal.argtypes = [P, P, P]
+    L.lpp_free_reduced.argtypes = [P]
+    L.lpp_free_reduced.restype = None
+    L.lpp_free_postsolve.argtypes = [P]
+    L.lpp_free_postsolve.restype = None
+    L.lpp_last_error.restype = C.c_char_p
+    L.lpp_server_create.argtypes = [C.c_size_t, C.POINTER(Opts), PP]
+    L.lpp_server_submit.argtypes = [P, C.POINTER(LpStruct), C.POINTER(C.c_uint64)]
+    L.lpp_server_take.argtypes = [P, C.c_uint64, C.c_int32, PP, PP]
+    L.lpp_server_stats_get.argtypes = [P, C.POINTER(ServerStats)]
+    L.lpp_server_destroy.argtypes = [P]
+    L.lpp_server_destroy.restype = None
+    for name in SYMBOLS:
+        if name not in ("lpp_opts_default", "lpp_free_reduced", "lpp_free_postsolve", "lpp_last_error",
+                        "lpp_server_destroy"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    return load().lpp_last_error().decode(errors="replace")
+
+
+def _check(st: int) -> int:
+    if st < 0:
+        raise LppError(st, last_error())
+    return st
+
+
+def opts(**kw) -> Opts:
+    o = Opts()
+    load().lpp_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def _is_torch_cuda(a) -> bool:
+    return type(a).__module__.startswith("torch") and getattr(a, "is_cuda", False)
+
+
+def lp_struct(lp, keep: list) -> LpStruct:
+    """lpp_lp from an object with row_ptr, col_idx, val, c, lhs, rhs, lb, ub
+    (NumPy arrays, or CUDA torch tensors for a device-resident LP)."""
+    names = ["row_ptr", "col_idx", "val", "c", "lhs", "rhs", "lb", "ub"]
+    arrs = {k: getattr(lp, k) for k in names}
+    dev = _is_torch_cuda(arrs["row_ptr"])
+    s = LpStruct()
+    if dev:
+        import torch
+        want = dict(row_ptr=torch.int32, col_idx=torch.int32)
+        for k in names:
+            t = arrs[k]
+            dt = want.get(k, torch.float64)
+            if t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
+                raise TypeError(f"{k} must be a contiguous CUDA tensor of {dt}")
+            keep.append(t)
+            setattr(s, k, t.data_ptr() if t.numel() else None)
+        s.m = int(arrs["lhs"].numel())
+        s.n = int(arrs["c"].numel())
+        s.nnz = int(arrs["col_idx"].numel())
+        s.on_device = 1
+    else:
+        conv = {}
+        for k in names:
+            dt = np.int32 if k in ("row_ptr", "col_idx") else np.float64
+            conv[k] = np.ascontiguousarray(arrs[k], dtype=dt)
+        keep.append(conv)
+        for k, a in conv.items():
+            setattr(s, k, a.ctypes.data if a.size else None)
+        s.m = int(conv["lhs"].size)
+        s.n = int(conv["c"].size)
+        s.nnz = int(conv["col_idx"].size)
+        s.on_device = 0
+    s.obj_offset = float(getattr(lp, "obj_offset", 0.0))
+    return s
+
+
+@dataclass
+class Reduced:
+    """Host copy of a reduced LP (CSR) plus its maps to the original indices."""
+    m: int
+    n: int
+    nnz: int
+    row_ptr: np.ndarray
+    col_idx: np.ndarray
+    val: np.ndarray
+    c: np.ndarray
+    lhs: np.ndarray
+    rhs: np.ndarray
+    lb: np.ndarray
+    ub: np.ndarray
+    obj_offset: float
+    row_map: np.ndarray
+    col_map: np.ndarray
+    csc_ptr: np.ndarray
+    csc_idx: np.ndarray
+    csc_val: np.ndarray
+
+
+class Result:
+    """Owns the C handles of one presolve; frees them when collected."""
+
+    def __init__(self, red, rec):
+        self._red = red
+        self._rec = rec
+        L = load()
+        info = Info()
+        _check(L.lpp_result_info(rec, C.byref(info)))
+        self.info = info
+        self.status = info.status
+        self.where = info.where
+        self.index = info.index
+        self.round = info.round
+        self.rounds = info.rounds
+        m, n = info.m, info.n
+        self.row_kind = np.zeros(m, np.int32)
+        self.row_round = np.zeros(m, np.int32)
+        self.row_aux = np.zeros(m, np.int32)
+        self.row_val = np.zeros(m)
+        _check(L.lpp_result_rows(rec, _p(self.row_kind), _p(self.row_round), _p(self.row_aux), _p(self.row_val)))
+        self.col_kind = np.zeros(n, np.int32)
+        self.col_round = np.zeros(n, np.int32)
+        self.col_val = np.zeros(n)
+        self.col_lb = np.zeros(n)
+        self.col_ub = np.zeros(n)
+        _check(L.lpp_result_cols(rec, _p(self.col_kind), _p(self.col_round), _p(self.col_val), _p(self.col_lb),
+                                 _p(self.col_ub)))
+        self.act_min = np.zeros(m)
+        self.act_max = np.zeros(m)
+        self.ninf_min = np.zeros(m, np.int32)
+        self.ninf_max = np.zeros(m, np.int32)
+        _check(L.lpp_result_activity(rec, _p(self.act_min), _p(self.act_max), _p(self.ninf_min),
+                                     _p(self.ninf_max)))
+        R = C.c_int32(0)
+        cap = 1024
+        self.round_nnz = np.zeros(cap, np.int64)
+        self.round_rows_removed = np.zeros(cap, np.int32)
+        self.round_cols_fixed = np.zeros(cap, np.int32)
+        self.round_bounds_changed = np.zeros(cap, np.int32)
+        self.round_ms = np.zeros(cap, np.float32)
+        _check(L.lpp_result_rounds(rec, cap, _p(self.round_nnz), _p(self.round_rows_removed),
+                                   _p(self.round_cols_fixed), _p(self.round_bounds_changed), _p(self.round_ms),
+                                   C.byref(R)))
+        k = min(R.value, cap)
+        for a in ("round_nnz", "round_rows_removed", "round_cols_fixed", "round_bounds_changed", "round_ms"):
+            setattr(self, a, getattr(self, a)[:k])
+        ks = (KernelStat * 32)()
+        cnt = C.c_int32(0)
+        _check(L.lpp_result_kernels(rec, 32, ks, C.byref(cnt)))
+        self.kernels = {ks[i].name.decode(): dict(launches=ks[i].launches, ms=ks[i].ms, bytes=ks[i].bytes)
+                        for i in range(cnt.value)}
+        self._reduced = None
+
+    @property
+    def presolve_ms(self) -> float:
+        return self.info.presolve_ms
+
+    def reduced(self) -> Reduced:
+        """Copies the reduced LP (and its CSC and maps) to the host."""
+        if self._reduced is not None:
+            return self._reduced
+        L = load()
+        v = LpStruct()
+        _check(L.lpp_reduced_view(self._red, C.byref(v), 0))
+        m, n, nnz = v.m, v.n, v.nnz
+
+        def arr(ptr, cnt, dt):
+            if cnt == 0 or not ptr:
+                return np.zeros(0, dt)
+            ct = C.c_int32 if dt == np.int32 else C.c_double
+            return np.ctypeslib.as_array(C.cast(ptr, C.POINTER(ct)), shape=(cnt,)).copy()
+
+        rp = arr(v.row_ptr, m + 1, np.int32) if m >= 0 else np.zeros(1, np.int32)
+        if m == 0:
+            rp = np.zeros(1, np.int32)
+        red = dict(m=m, n=n, nnz=nnz, row_ptr=rp, col_idx=arr(v.col_idx, nnz, np.int32), val=arr(v.val, nnz, float),
+                   c=arr(v.c, n, float), lhs=arr(v.lhs, m, float), rhs=arr(v.rhs, m, float),
+                   lb=arr(v.lb, n, float), ub=arr(v.ub, n, float), obj_offset=v.obj_offset)
+        rm, cm = C.c_void_p(), C.c_void_p()
+        _check(L.lpp_reduced_maps(self._red, C.byref(rm), C.byref(cm), 0))
+        tp, ti, tv = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        _check(L.lpp_reduced_csc(self._red, C.byref(tp), C.byref(ti), C.byref(tv), 0))
+        red["row_map"] = arr(rm.value, m, np.int32)
+        red["col_map"] = arr(cm.value, n, np.int32)
+        red["csc_ptr"] = arr(tp.value, n + 1, np.int32) if n > 0 else np.zeros(1, np.int32)
+        red["csc_idx"] = arr(ti.value, nnz, np.int32)
+        red["csc_val"] = arr(tv.value, nnz, float)
+        self._reduced = Reduced(**red)
+        return self._reduced
+
+    def device_view(self) -> LpStruct:
+        """The reduced LP as device pointers (valid while this Result lives)."""
+        v = LpStruct()
+        _check(load().lpp_reduced_view(self._red, C.byref(v), 1))
+        return v
+
+    def postsolve_primal(self, x_red: np.ndarray) -> np.ndarray:
+        x = np.zeros(self.info.n)
+        xr = np.ascontiguousarray(x_red, np.float64)
+        _check(load().lpp_postsolve_primal(self._rec, _p(xr), _p(x)))
+        return x
+
+    def close(self):
+        L = _lib
+        if L is not None:
+            if self._red:
+                L.lpp_free_reduced(self._red)
+            if self._rec:
+                L.lpp_free_postsolve(self._rec)
+        self._red = None
+        self._rec = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data if a.size else None
+
+
+def presolve(lp, options: Opts | None = None, **kw) -> Result:
+    """lpp_presolve on one LP (host NumPy arrays or CUDA torch tensors)."""
+    L = load()
+    o = options if options is not None else opts(**kw)
+    keep = []
+    s = lp_struct(lp, keep)
+    red, rec = C.c_void_p(), C.c_void_p()
+    _check(L.lpp_presolve(C.byref(s), C.byref(o), C.byref(red), C.byref(rec)))
+    return Result(red.value, rec.value)
+
+
+def presolve_batch(lps, options: Opts | None = None, **kw) -> list[Result]:
+    """lpp_presolve_batch on a list of LPs (all host or all device)."""
+    L = load()
+    o = options if options is not None else opts(**kw)
+    keep = []
+    cnt = len(lps)
+    arr = (LpStruct * max(cnt, 1))()
+    for k, lp in enumerate(lps):
+        arr[k] = lp_struct(lp, keep)
+    reds = (C.c_void_p * max(cnt, 1))()
+    recs = (C.c_void_p * max(cnt, 1))()
+    per = (C.c_int32 * max(cnt, 1))()
+    _check(L.lpp_presolve_batch(arr, cnt, C.byref(o), reds, recs, per))
+    return [Result(reds[k], recs[k]) for k in range(cnt)]

