@@ -258,6 +258,11 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     }
     for (j = 0; j < n0; j++) { out->col_kind[j] = LPPO_COL_KEPT; out->col_round[j] = 0; out->col_val[j] = 0.0; }
     out->where = LPPO_WHERE_NONE; out->index = -1; out->round = 0; out->rounds = 0;
+    for (i = 0; i < m0; i++) { /* no round executed yet: no row has activities */
+        out->ninf_min[i] = -1; out->ninf_max[i] = -1;
+        out->act_min[i] = NAN; out->act_max[i] = NAN;
+        out->act_scale_min[i] = NAN; out->act_scale_max[i] = NAN;
+    }
     au.min_ratio = INFINITY; au.n = 0; au.below = 0;
 
     for (r = 1; r <= o->max_rounds; r++) {

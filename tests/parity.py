@@ -26,7 +26,8 @@ def _close(g, o, scale=None, tol=TOL, what=""):
     s = np.maximum(1.0, np.abs(o))
     if scale is not None:
         s = np.maximum(s, np.where(np.isfinite(scale), np.abs(scale), 0.0))
-    ok |= fin & (np.abs(g - o) <= tol * s)
+    with np.errstate(invalid="ignore"):
+        ok |= fin & (np.abs(g - o) <= tol * s)
     if not ok.all():
         bad = np.flatnonzero(~ok)[:5]
         raise AssertionError(f"{what}: {np.count_nonzero(~ok)} mismatches, e.g. idx {bad}: gpu {g[bad]} oracle {o[bad]}")
