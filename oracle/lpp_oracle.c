@@ -304,7 +304,9 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
             kind[i] = LPPO_ROW_KEPT;
             if (isfin(L) && isfin(U)) {
                 double d = ft * dmax(1.0, dmax(fabs(L), fabs(U)));
-                audit(&au, (L - U) - d, s.ebL[i] + s.ebU[i]);
+                /* an equality row stays an exact equality on both sides (both
+                   sides are shifted by the same value), so L - U = 0 then */
+                if (L != U) audit(&au, (L - U) - d, s.ebL[i] + s.ebU[i]);
                 if (L - U > d) { bad = i; break; }
             }
             if (nmn[i] == 0 && isfin(U)) {
