@@ -219,6 +219,32 @@ lpp_status lpp_server_take(lpp_server *srv, uint64_t ticket, int32_t wait_ms, lp
 lpp_status lpp_server_stats_get(lpp_server *srv, lpp_server_stats *stats);
 void lpp_server_destroy(lpp_server *srv);
 
+/* Row activities of an LP already in device memory, computed without any
+ * device allocation.  The paper has no counterpart: this is for callers
+ * that cannot allocate device memory when they need activities, e.g. a GPU
+ * solver that reserved its whole memory budget up front and treats any later
+ * allocation as a failure, or a pipeline whose memory plan is fixed while it
+ * runs.  Computes, for every row i of the CSR (row_ptr[m+1], col_idx[nnz],
+ * val[nnz]) and bounds lb/ub[n] (|v| >= huge counts as infinite), what
+ * lpp_presolve's activity step computes: act_min[i] / act_max[i], the finite
+ * parts of the minimum / maximum of row i over the box, and ninf_min[i] /
+ * ninf_max[i], the numbers of infinite terms (Sec. 3.1).  All pointers are
+ * device pointers on the calling thread's current device; outputs [m] are
+ * allocated by the caller.  The CSR is not checked (it must be valid: the
+ * checks of lpp_presolve need scratch memory proportional to nnz).
+ * Scratch: one fixed array inside the library (4 MiB on every device that
+ * loads the library, held until the process exits) limits nnz to
+ * 268,435,456; larger inputs return LPP_ERR_INVALID with a message.  The
+ * first call on a device looks up that array's device address (set-up), so
+ * make it before any stream capture.  Every call shares the array: calls
+ * that overlap on the GPU (other streams, other threads) race; serialise
+ * them.  Runs asynchronously on `stream` (NULL = legacy default stream) and
+ * calls no allocation routine. */
+lpp_status lpp_row_activity_noalloc(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                                    const int32_t *col_idx, const double *val, const double *lb, const double *ub,
+                                    double huge, double *act_min, double *act_max, int32_t *ninf_min,
+                                    int32_t *ninf_max, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

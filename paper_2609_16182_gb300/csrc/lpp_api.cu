@@ -227,6 +227,8 @@ const T *host_copy(std::vector<T> &h, const T *d, size_t cnt) {
 }
 }  // namespace
 
+lpp_status lpp_noalloc_fail(lpp_status st, const char *msg) { return set_err(st, msg); }
+
 extern "C" {
 
 void lpp_opts_default(lpp_opts *o) {

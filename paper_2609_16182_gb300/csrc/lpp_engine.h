@@ -150,6 +150,9 @@ struct SharedStore {
 
 }  // namespace lpp
 
+// sets the message lpp_last_error() returns and passes the status through
+lpp_status lpp_noalloc_fail(lpp_status st, const char *msg);
+
 // Library objects behind the opaque C handles.
 struct lpp_reduced {
     int32_t m = 0, n = 0;

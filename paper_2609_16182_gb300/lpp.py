@@ -64,7 +64,7 @@ SYMBOLS = ["lpp_opts_default", "lpp_presolve", "lpp_reduced_view", "lpp_reduced_
            "lpp_result_info", "lpp_result_rows", "lpp_result_cols", "lpp_result_activity", "lpp_result_rounds",
            "lpp_result_kernels", "lpp_postsolve_primal", "lpp_free_reduced", "lpp_free_postsolve",
            "lpp_last_error", "lpp_presolve_batch", "lpp_server_create", "lpp_server_submit", "lpp_server_take",
-           "lpp_server_stats_get", "lpp_server_destroy"]
+           "lpp_server_stats_get", "lpp_server_destroy", "lpp_row_activity_noalloc"]
 
 _lib = None
 P = C.c_void_p
@@ -108,6 +108,8 @@ def load():
     L.lpp_server_submit.argtypes = [P, C.POINTER(LpStruct), C.POINTER(C.c_uint64)]
     L.lpp_server_take.argtypes = [P, C.c_uint64, C.c_int32, PP, PP]
     L.lpp_server_stats_get.argtypes = [P, C.POINTER(ServerStats)]
+    L.lpp_row_activity_noalloc.argtypes = [C.c_int32, C.c_int32, C.c_int64, P, P, P, P, P, C.c_double, P, P, P,
+                                           P, P]
     L.lpp_server_destroy.argtypes = [P]
     L.lpp_server_destroy.restype = None
     for name in SYMBOLS:
