@@ -151,6 +151,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the LP (profiling runs only)")
+    ap.add_argument("--profile", action="store_true",
+                    help="profiling run: W + K steps only (no timing pass, e2e or CPU baseline)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -200,6 +202,10 @@ def main():
         ev1.record(stream)
         barrier()
     ms_total = ev0.elapsed_time(ev1)
+    if args.profile:
+        print(json.dumps({"profile": True, "steps": args.steps, "ms_per_step": ms_total / max(1, args.steps),
+                          "nnz": lp.nnz}), flush=True)
+        return
     first = results[0]
     info = first.info
     round_ms = [float(x) for x in first.round_ms]
