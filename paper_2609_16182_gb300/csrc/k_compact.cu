@@ -427,10 +427,12 @@ __global__ void __launch_bounds__(kBlock) k_offset_tiles(const double *contrib, 
     s = block_sum_dbl(s);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
-__global__ void k_offset_final(const double *part, int32_t ntiles, double *offset) {
+// one block: thread t adds tiles t, t+256, ... in order, then the fixed-order block sum
+__global__ void __launch_bounds__(kBlock) k_offset_final(const double *part, int32_t ntiles, double *offset) {
     double s = 0.0;
-    for (int32_t t = 0; t < ntiles; t++) s += part[t];
-    offset[0] += s;
+    for (int32_t t = threadIdx.x; t < ntiles; t += kBlock) s += part[t];
+    s = block_sum_dbl(s);
+    if (threadIdx.x == 0) offset[0] += s;
 }
 // many LPs: column range of each LP, then one warp per LP
 __global__ void k_lp_ranges(const int32_t *lp_col, int32_t n, int32_t *first, int32_t *last) {
@@ -502,7 +504,7 @@ void launch_offset(const Ctx &C, const CompactCtx &K, cudaStream_t s) {
     if (C.nlp == 1) {
         const int32_t ntiles = (int32_t)((C.n + kScanTile - 1) / kScanTile);
         k_offset_tiles<<<ntiles, kBlock, 0, s>>>(K.contrib, C.n, K.offset_part);
-        k_offset_final<<<1, 1, 0, s>>>(K.offset_part, ntiles, K.offset);
+        k_offset_final<<<1, kBlock, 0, s>>>(K.offset_part, ntiles, K.offset);
     } else {
         cudaMemsetAsync(K.lp_first, 0, sizeof(int32_t) * (size_t)C.nlp, s);
         cudaMemsetAsync(K.lp_last, 0, sizeof(int32_t) * (size_t)C.nlp, s);

@@ -99,90 +99,66 @@ __global__ void k_rebase_idx(int32_t *idx, const int32_t *ptr, const int32_t *lp
     for (int32_t k = ptr[i]; k < ptr[i + 1]; k++) idx[k] -= d;
 }
 
-unsigned nblk(int64_t cnt) { return (unsigned)((cnt + 255) / 256 > 0 ? (cnt + 255) / 256 : 1); }
-
-// Copies records, bounds and activities of the arena to the host.
-struct HostRecords {
-    std::vector<int32_t> rk, rr, ra, ck, cr, cmap, act_rmap;
-    std::vector<double> rv, cv, clb, cub, offset;
-    std::vector<double2> lu, act;
-    std::vector<int2> ninf;
-};
-
-HostRecords fetch_records(Engine &E) {
-    HostRecords h;
-    cudaStream_t s = E.s;
-    auto d2h = [&](void *dst, const void *src, size_t bytes) {
-        if (bytes) LPP_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
-    };
-    h.rk.resize(E.m0); h.rr.resize(E.m0); h.ra.resize(E.m0); h.rv.resize(E.m0);
-    h.ck.resize(E.n0); h.cr.resize(E.n0); h.cv.resize(E.n0);
-    h.lu.resize(E.n); h.cmap.resize(E.n); h.offset.resize(E.nlp);
-    h.act.resize(E.act_m); h.ninf.resize(E.act_m); h.act_rmap.resize(E.act_m);
-    d2h(h.rk.data(), E.rec_rk, 4 * (size_t)E.m0);
-    d2h(h.rr.data(), E.rec_rr, 4 * (size_t)E.m0);
-    d2h(h.ra.data(), E.rec_ra, 4 * (size_t)E.m0);
-    d2h(h.rv.data(), E.rec_rv, 8 * (size_t)E.m0);
-    d2h(h.ck.data(), E.rec_ck, 4 * (size_t)E.n0);
-    d2h(h.cr.data(), E.rec_cr, 4 * (size_t)E.n0);
-    d2h(h.cv.data(), E.rec_cv, 8 * (size_t)E.n0);
-    d2h(h.lu.data(), E.lu[E.cur], 16 * (size_t)E.n);
-    d2h(h.cmap.data(), E.cmap[E.cur], 4 * (size_t)E.n);
-    d2h(h.offset.data(), E.K.offset, 8 * (size_t)E.nlp);
-    d2h(h.act.data(), E.act, 16 * (size_t)E.act_m);
-    d2h(h.ninf.data(), E.ninf, 8 * (size_t)E.act_m);
-    d2h(h.act_rmap.data(), E.rmap[E.act_buf], 4 * (size_t)E.act_m);
-    LPP_CUDA(cudaStreamSynchronize(s));
-    return h;
+__global__ void k_count_rows_lp(const int32_t *lprow, int32_t m, int32_t *rows) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) atomicAdd(&rows[lprow[t]], 1);
 }
 
-// postsolve record of LP k of the arena (rows [r0, r0+m), columns [c0, c0+n))
-lpp_postsolve *make_postsolve(Engine &E, const HostRecords &h, int32_t k, int32_t m_red, int32_t n_red,
-                              int64_t nnz_red, const int32_t *cmap_local) {
+unsigned nblk(int64_t cnt) { return (unsigned)((cnt + 255) / 256 > 0 ? (cnt + 255) / 256 : 1); }
+
+// Moves the record arrays of a finished run into a DeviceRecords object
+// (ownership leaves the engine's pool) together with copies of the final
+// bounds and column map and the last round's activities.
+std::shared_ptr<DeviceRecords> take_records(Engine &E) {
+    auto D = std::make_shared<DeviceRecords>();
+    D->m0 = E.m0;
+    D->n0 = E.n0;
+    D->n_final = E.n;
+    D->act_m = E.act_m;
+    D->rk = E.rec_rk;
+    D->rr = E.rec_rr;
+    D->ra = E.rec_ra;
+    D->rv = E.rec_rv;
+    D->ck = E.rec_ck;
+    D->cr = E.rec_cr;
+    D->cv = E.rec_cv;
+    D->lu = E.lu[E.cur];
+    D->act = E.act;
+    D->ninf = E.ninf;
+    for (void *p : {(void *)D->rk, (void *)D->rr, (void *)D->ra, (void *)D->rv, (void *)D->ck, (void *)D->cr,
+                    (void *)D->cv, (void *)D->lu, (void *)D->act, (void *)D->ninf}) {
+        E.pool.forget(p);
+        D->owned.push_back(p);
+    }
+    // maps may belong to the reduced LP: copy them
+    D->cmap = E.pool.alloc<int32_t>(E.n);
+    D->act_rmap = E.pool.alloc<int32_t>(E.act_m);
+    E.pool.forget(D->cmap);
+    E.pool.forget(D->act_rmap);
+    D->owned.push_back(D->cmap);
+    D->owned.push_back(D->act_rmap);
+    if (E.n) LPP_CUDA(cudaMemcpyAsync(D->cmap, E.cmap[E.cur], 4 * (size_t)E.n, cudaMemcpyDeviceToDevice, E.s));
+    if (E.act_m)
+        LPP_CUDA(cudaMemcpyAsync(D->act_rmap, E.rmap[E.act_buf], 4 * (size_t)E.act_m, cudaMemcpyDeviceToDevice, E.s));
+    return D;
+}
+
+// Postsolve record of LP k: verdict and counters now, the rest on first access.
+lpp_postsolve *make_postsolve(Engine &E, const std::shared_ptr<DeviceRecords> &D, int32_t k, int32_t m_red,
+                              int32_t n_red, int64_t nnz_red, double offset, int32_t cstart, int32_t astart,
+                              int32_t acnt) {
     auto *P = new lpp_postsolve();
     const Member &mm = E.mem[k];
-    const int32_t r0 = mm.row_off, c0 = mm.col_off;
-    P->row_kind.assign(h.rk.begin() + r0, h.rk.begin() + r0 + mm.m);
-    P->row_round.assign(h.rr.begin() + r0, h.rr.begin() + r0 + mm.m);
-    P->row_aux.resize(mm.m);
-    P->row_val.assign(h.rv.begin() + r0, h.rv.begin() + r0 + mm.m);
-    for (int32_t i = 0; i < mm.m; i++) {
-        const int32_t a = h.ra[r0 + i];
-        const int32_t kd = P->row_kind[i];
-        P->row_aux[i] = a < 0 ? -1 : (kd == LPP_ROW_SINGLETON ? a - c0 : a - r0);
-    }
-    P->col_kind.assign(h.ck.begin() + c0, h.ck.begin() + c0 + mm.n);
-    P->col_round.assign(h.cr.begin() + c0, h.cr.begin() + c0 + mm.n);
-    P->col_val.assign(h.cv.begin() + c0, h.cv.begin() + c0 + mm.n);
-    P->col_lb.assign(mm.n, NAN);
-    P->col_ub.assign(mm.n, NAN);
-    for (int32_t j = 0; j < E.n; j++) {
-        const int32_t o = h.cmap[j] - c0;
-        if (o >= 0 && o < mm.n) {
-            P->col_lb[o] = h.lu[j].x;
-            P->col_ub[o] = h.lu[j].y;
-        }
-    }
-    for (int32_t j = 0; j < mm.n; j++)
-        if (P->col_kind[j] != LPP_COL_KEPT) P->col_lb[j] = P->col_ub[j] = P->col_val[j];
-    P->act_min.assign(mm.m, NAN);
-    P->act_max.assign(mm.m, NAN);
-    P->ninf_min.assign(mm.m, -1);
-    P->ninf_max.assign(mm.m, -1);
-    for (int32_t i = 0; i < E.act_m; i++) {
-        const int32_t o = h.act_rmap[i] - r0;
-        if (o >= 0 && o < mm.m) {
-            P->act_min[o] = h.act[i].x;
-            P->act_max[o] = h.act[i].y;
-            P->ninf_min[o] = h.ninf[i].x;
-            P->ninf_max[o] = h.ninf[i].y;
-        }
-    }
-    P->col_map.assign(cmap_local, cmap_local + n_red);
+    P->dev = D;
+    P->r0 = mm.row_off;
+    P->c0 = mm.col_off;
+    P->cstart = cstart;
+    P->astart = astart;
+    P->acnt = acnt;
     lpp_info &I = P->info;
     I.status = E.lp_status[k];
     I.where = E.lp_where[k];
-    I.index = E.lp_index[k] < 0 ? -1 : E.lp_index[k] - (I.where == LPP_WHERE_ROW ? r0 : c0);
+    I.index = E.lp_index[k] < 0 ? -1 : E.lp_index[k] - (I.where == LPP_WHERE_ROW ? P->r0 : P->c0);
     I.round = E.lp_round[k];
     I.rounds = E.lp_rounds[k];
     I.m = mm.m;
@@ -191,7 +167,7 @@ lpp_postsolve *make_postsolve(Engine &E, const HostRecords &h, int32_t k, int32_
     I.m_red = m_red;
     I.n_red = n_red;
     I.nnz_red = nnz_red;
-    I.obj_offset = h.offset[k];
+    I.obj_offset = offset;
     I.presolve_ms = E.loop_ms;
     I.nnz_processed = E.nnz_processed;
     P->r_nnz = E.r_nnz;
@@ -218,6 +194,67 @@ lpp_postsolve *make_postsolve(Engine &E, const HostRecords &h, int32_t k, int32_
 }
 
 template <class T>
+void d2h_slice(std::vector<T> &h, const T *d, size_t off, size_t cnt) {
+    h.resize(cnt);
+    if (cnt) LPP_CUDA(cudaMemcpy(h.data(), d + off, sizeof(T) * cnt, cudaMemcpyDeviceToHost));
+}
+
+// host copies of this LP's records, bounds and activities
+void materialize(lpp_postsolve *P) {
+    if (P->host_ready) return;
+    const DeviceRecords &D = *P->dev;
+    const int32_t m = P->info.m, n = P->info.n, r0 = P->r0, c0 = P->c0;
+    d2h_slice(P->row_kind, D.rk, r0, m);
+    d2h_slice(P->row_round, D.rr, r0, m);
+    d2h_slice(P->row_aux, D.ra, r0, m);
+    d2h_slice(P->row_val, D.rv, r0, m);
+    d2h_slice(P->col_kind, D.ck, c0, n);
+    d2h_slice(P->col_round, D.cr, c0, n);
+    d2h_slice(P->col_val, D.cv, c0, n);
+    for (int32_t i = 0; i < m; i++) {
+        const int32_t a = P->row_aux[i];
+        if (a >= 0) P->row_aux[i] = P->row_kind[i] == LPP_ROW_SINGLETON ? a - c0 : a - r0;
+    }
+    std::vector<int32_t> cm;
+    std::vector<double2> lu;
+    d2h_slice(cm, D.cmap, P->cstart, P->info.n_red);
+    d2h_slice(lu, D.lu, P->cstart, P->info.n_red);
+    P->col_map.resize(cm.size());
+    P->col_lb.assign(n, NAN);
+    P->col_ub.assign(n, NAN);
+    for (size_t k = 0; k < cm.size(); k++) {
+        const int32_t o = cm[k] - c0;
+        P->col_map[k] = o;
+        if (o >= 0 && o < n) {
+            P->col_lb[o] = lu[k].x;
+            P->col_ub[o] = lu[k].y;
+        }
+    }
+    for (int32_t j = 0; j < n; j++)
+        if (P->col_kind[j] != LPP_COL_KEPT) P->col_lb[j] = P->col_ub[j] = P->col_val[j];
+    std::vector<double2> act;
+    std::vector<int2> ni;
+    std::vector<int32_t> am;
+    d2h_slice(act, D.act, P->astart, P->acnt);
+    d2h_slice(ni, D.ninf, P->astart, P->acnt);
+    d2h_slice(am, D.act_rmap, P->astart, P->acnt);
+    P->act_min.assign(m, NAN);
+    P->act_max.assign(m, NAN);
+    P->ninf_min.assign(m, -1);
+    P->ninf_max.assign(m, -1);
+    for (int32_t i = 0; i < P->acnt; i++) {
+        const int32_t o = am[i] - r0;
+        if (o >= 0 && o < m) {
+            P->act_min[o] = act[i].x;
+            P->act_max[o] = act[i].y;
+            P->ninf_min[o] = ni[i].x;
+            P->ninf_max[o] = ni[i].y;
+        }
+    }
+    P->host_ready = true;
+}
+
+template <class T>
 const T *host_copy(std::vector<T> &h, const T *d, size_t cnt) {
     if (h.size() != cnt) {
         h.resize(cnt);
@@ -225,6 +262,7 @@ const T *host_copy(std::vector<T> &h, const T *d, size_t cnt) {
     }
     return h.data();
 }
+
 }  // namespace
 
 lpp_status lpp_noalloc_fail(lpp_status st, const char *msg) { return set_err(st, msg); }
@@ -262,14 +300,15 @@ lpp_status lpp_presolve(const lpp_lp *in, const lpp_opts *opts, lpp_reduced **ou
         E->ingest_plain(*in);
         E->prepare();
         E->run();
-        HostRecords h = fetch_records(*E);
+        double offset = 0.0;
+        LPP_CUDA(cudaMemcpyAsync(&offset, E->K.offset, sizeof(double), cudaMemcpyDeviceToHost, E->s));
+        auto D = take_records(*E);
         // the reduced LP takes the current buffers
         auto *R = new lpp_reduced();
         const int c = E->cur;
         R->m = E->m;
         R->n = E->n;
         R->nnz = E->nnz;
-        R->obj_offset = h.offset[0];
         R->rp = E->rp[c];
         R->ci = E->ci[c];
         R->rv = E->rv[c];
@@ -292,9 +331,10 @@ lpp_status lpp_presolve(const lpp_lp *in, const lpp_opts *opts, lpp_reduced **ou
         E->pool.forget(R->ub);
         R->owned.push_back(R->lb);
         R->owned.push_back(R->ub);
-        split_lu(E->lu[c], R->n, R->lb, R->ub, E->s);
+        split_lu(D->lu, R->n, R->lb, R->ub, E->s);
         LPP_CUDA(cudaStreamSynchronize(E->s));
-        lpp_postsolve *P = make_postsolve(*E, h, 0, R->m, R->n, R->nnz, h.cmap.data());
+        R->obj_offset = offset;
+        lpp_postsolve *P = make_postsolve(*E, D, 0, R->m, R->n, R->nnz, offset, 0, 0, E->act_m);
         *out = R;
         *rec = P;
         return (lpp_status)P->info.status;
@@ -329,10 +369,18 @@ lpp_status lpp_presolve_batch(const lpp_lp *ins, int32_t count, const lpp_opts *
         E->ingest_batch(ins, count);
         E->prepare();
         E->run();
-        HostRecords h = fetch_records(*E);
-        // per-LP sizes of the reduced arena
         cudaStream_t s = E->s;
         const int c = E->cur;
+        std::vector<double> offs(count);
+        LPP_CUDA(cudaMemcpyAsync(offs.data(), E->K.offset, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
+        // rows of each LP in the numbering of the last round's start (activities)
+        int32_t *acnt = E->pool.alloc<int32_t>(count);
+        LPP_CUDA(cudaMemsetAsync(acnt, 0, sizeof(int32_t) * (size_t)count, s));
+        if (E->act_m > 0) k_count_rows_lp<<<nblk(E->act_m), 256, 0, s>>>(E->lprow[E->act_buf], E->act_m, acnt);
+        std::vector<int32_t> acnt_h(count);
+        LPP_CUDA(cudaMemcpyAsync(acnt_h.data(), acnt, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s));
+        auto D = take_records(*E);
+        // per-LP sizes of the reduced arena
         int32_t *cnt = E->pool.alloc<int32_t>(3 * (size_t)count);
         LPP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * 3 * (size_t)count, s));
         k_count_lp<<<nblk(std::max(E->m, E->n)), 256, 0, s>>>(E->lprow[c], E->rp[c], E->m, E->lpcol[c], E->n, cnt,
@@ -376,8 +424,6 @@ lpp_status lpp_presolve_batch(const lpp_lp *ins, int32_t count, const lpp_opts *
         if (E->n > 0) k_rebase_idx<<<nblk(E->n), 256, 0, s>>>(E->ti[c], E->tp[c], E->lpcol[c], E->n, row_start);
         split_lu(E->lu[c], E->n, lb, ub, s);
         LPP_CUDA(cudaGetLastError());
-        std::vector<int32_t> cmap_h(E->n);
-        LPP_CUDA(cudaMemcpyAsync(cmap_h.data(), cmap_out, sizeof(int32_t) * (size_t)E->n, cudaMemcpyDeviceToHost, s));
         LPP_CUDA(cudaStreamSynchronize(s));
         for (void *p : {(void *)rp_out, (void *)tp_out, (void *)rmap_out, (void *)cmap_out, (void *)lb, (void *)ub,
                         (void *)E->ci[c], (void *)E->rv[c], (void *)E->ti[c], (void *)E->tv[c], (void *)E->L[c],
@@ -385,13 +431,14 @@ lpp_status lpp_presolve_batch(const lpp_lp *ins, int32_t count, const lpp_opts *
             E->pool.forget(p);
             store->ptrs.push_back(p);
         }
+        int32_t astart = 0;
         for (int32_t k = 0; k < count; k++) {
             auto *R = new lpp_reduced();
             const int32_t r0 = tab[k], c0 = tab[count + k], z0 = tab[2 * count + k];
             R->m = hc[k];
             R->n = hc[count + k];
             R->nnz = hc[2 * count + k];
-            R->obj_offset = h.offset[k];
+            R->obj_offset = offs[k];
             R->rp = rp_out + r0 + k;
             R->tp = tp_out + c0 + k;
             R->ci = E->ci[c] + z0;
@@ -407,7 +454,8 @@ lpp_status lpp_presolve_batch(const lpp_lp *ins, int32_t count, const lpp_opts *
             R->cmap = cmap_out + c0;
             R->shared = store;
             outs[k] = R;
-            recs[k] = make_postsolve(*E, h, k, R->m, R->n, R->nnz, cmap_h.data() + c0);
+            recs[k] = make_postsolve(*E, D, k, R->m, R->n, R->nnz, offs[k], c0, astart, acnt_h[k]);
+            astart += acnt_h[k];
             per_lp[k] = (lpp_status)recs[k]->info.status;
         }
         return LPP_OK;
@@ -505,8 +553,11 @@ lpp_status lpp_result_info(const lpp_postsolve *P, lpp_info *info) {
     return LPP_OK;
 }
 
-lpp_status lpp_result_rows(const lpp_postsolve *P, int32_t *kind, int32_t *round, int32_t *aux, double *val) {
-    if (!P) return set_err(LPP_ERR_INVALID, "NULL record");
+lpp_status lpp_result_rows(const lpp_postsolve *Pc, int32_t *kind, int32_t *round, int32_t *aux, double *val) {
+    if (!Pc) return set_err(LPP_ERR_INVALID, "NULL record");
+    lpp_postsolve *P = const_cast<lpp_postsolve *>(Pc);
+    const lpp_status st = guarded([&]() -> lpp_status { materialize(P); return LPP_OK; });
+    if (st != LPP_OK) return st;
     const size_t m = P->row_kind.size();
     if (kind && m) std::memcpy(kind, P->row_kind.data(), 4 * m);
     if (round && m) std::memcpy(round, P->row_round.data(), 4 * m);
@@ -515,9 +566,12 @@ lpp_status lpp_result_rows(const lpp_postsolve *P, int32_t *kind, int32_t *round
     return LPP_OK;
 }
 
-lpp_status lpp_result_cols(const lpp_postsolve *P, int32_t *kind, int32_t *round, double *val, double *lb,
+lpp_status lpp_result_cols(const lpp_postsolve *Pc, int32_t *kind, int32_t *round, double *val, double *lb,
                            double *ub) {
-    if (!P) return set_err(LPP_ERR_INVALID, "NULL record");
+    if (!Pc) return set_err(LPP_ERR_INVALID, "NULL record");
+    lpp_postsolve *P = const_cast<lpp_postsolve *>(Pc);
+    const lpp_status st = guarded([&]() -> lpp_status { materialize(P); return LPP_OK; });
+    if (st != LPP_OK) return st;
     const size_t n = P->col_kind.size();
     if (kind && n) std::memcpy(kind, P->col_kind.data(), 4 * n);
     if (round && n) std::memcpy(round, P->col_round.data(), 4 * n);
@@ -527,9 +581,12 @@ lpp_status lpp_result_cols(const lpp_postsolve *P, int32_t *kind, int32_t *round
     return LPP_OK;
 }
 
-lpp_status lpp_result_activity(const lpp_postsolve *P, double *act_min, double *act_max, int32_t *ninf_min,
+lpp_status lpp_result_activity(const lpp_postsolve *Pc, double *act_min, double *act_max, int32_t *ninf_min,
                                int32_t *ninf_max) {
-    if (!P) return set_err(LPP_ERR_INVALID, "NULL record");
+    if (!Pc) return set_err(LPP_ERR_INVALID, "NULL record");
+    lpp_postsolve *P = const_cast<lpp_postsolve *>(Pc);
+    const lpp_status st = guarded([&]() -> lpp_status { materialize(P); return LPP_OK; });
+    if (st != LPP_OK) return st;
     const size_t m = P->act_min.size();
     if (act_min && m) std::memcpy(act_min, P->act_min.data(), 8 * m);
     if (act_max && m) std::memcpy(act_max, P->act_max.data(), 8 * m);
@@ -561,8 +618,12 @@ lpp_status lpp_result_kernels(const lpp_postsolve *P, int32_t cap, lpp_kernel_st
     return LPP_OK;
 }
 
-lpp_status lpp_postsolve_primal(const lpp_postsolve *P, const double *x_red, double *x_orig) {
-    if (!P || !x_orig || (!x_red && !P->col_map.empty())) return set_err(LPP_ERR_INVALID, "NULL argument");
+lpp_status lpp_postsolve_primal(const lpp_postsolve *Pc, const double *x_red, double *x_orig) {
+    if (!Pc || !x_orig) return set_err(LPP_ERR_INVALID, "NULL argument");
+    lpp_postsolve *P = const_cast<lpp_postsolve *>(Pc);
+    const lpp_status st = guarded([&]() -> lpp_status { materialize(P); return LPP_OK; });
+    if (st != LPP_OK) return st;
+    if (!x_red && !P->col_map.empty()) return set_err(LPP_ERR_INVALID, "NULL argument");
     const size_t n = P->col_kind.size();
     for (size_t j = 0; j < n; j++) x_orig[j] = P->col_kind[j] != LPP_COL_KEPT ? P->col_val[j] : NAN;
     for (size_t k = 0; k < P->col_map.size(); k++) {

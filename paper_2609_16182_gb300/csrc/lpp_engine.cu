@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "lpp_engine.h"
 
@@ -25,6 +26,72 @@ void DevPool::release() {
 }
 
 namespace {
+
+// Small pinned host buffers (status mirrors) are reused across presolves:
+// pinning memory costs far more than the rounds of a small LP.
+std::mutex g_pin_mu;
+std::vector<std::pair<size_t, void *>> g_pin_free;
+
+void *pinned_get(size_t bytes) {
+    bytes = std::max<size_t>(bytes, 64);
+    {
+        std::lock_guard<std::mutex> g(g_pin_mu);
+        for (size_t k = 0; k < g_pin_free.size(); k++)
+            if (g_pin_free[k].first >= bytes) {
+                void *p = g_pin_free[k].second;
+                g_pin_free.erase(g_pin_free.begin() + (long)k);
+                return p;
+            }
+    }
+    void *p = nullptr;
+    LPP_CUDA(cudaMallocHost(&p, bytes));
+    std::memset(p, 0, bytes);
+    return p;
+}
+
+// remembers a pinned buffer's capacity so it can be handed out again
+std::mutex g_cap_mu;
+std::vector<std::pair<void *, size_t>> g_pin_cap;
+
+void *pinned_get_sized(size_t bytes) {
+    bytes = std::max<size_t>(bytes, 64);
+    void *p = pinned_get(bytes);
+    std::lock_guard<std::mutex> g(g_cap_mu);
+    bool known = false;
+    for (auto &e : g_pin_cap)
+        if (e.first == p) known = true;
+    if (!known) g_pin_cap.emplace_back(p, bytes);
+    return p;
+}
+
+void pinned_put(void *p) {
+    if (!p) return;
+    size_t cap = 0;
+    {
+        std::lock_guard<std::mutex> g(g_cap_mu);
+        for (auto &e : g_pin_cap)
+            if (e.first == p) cap = e.second;
+    }
+    std::lock_guard<std::mutex> g(g_pin_mu);
+    g_pin_free.emplace_back(cap, p);
+}
+
+// Freed device memory stays in the device's default pool (stream-ordered
+// allocations are then reused by the next presolve instead of being mapped
+// again); set once per device.
+std::mutex g_pool_mu;
+bool g_pool_done[256] = {};
+
+void keep_pool_memory(int dev) {
+    std::lock_guard<std::mutex> g(g_pool_mu);
+    if (dev < 0 || dev >= 256 || g_pool_done[dev]) return;
+    cudaMemPool_t mp;
+    if (cudaDeviceGetDefaultMemPool(&mp, dev) == cudaSuccess) {
+        uint64_t thr = ~0ULL;
+        cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    g_pool_done[dev] = true;
+}
 
 int32_t pow2_at_least(int64_t v) {
     int64_t p = 2;
@@ -91,9 +158,9 @@ Engine::~Engine() {
     for (auto e : spare_events) cudaEventDestroy(e);
     pool.release();
     if (s) cudaStreamSynchronize(s);
-    if (st_h) cudaFreeHost(st_h);
-    if (verdict_h) cudaFreeHost(verdict_h);
-    if (changed_h) cudaFreeHost(changed_h);
+    pinned_put(st_h);
+    pinned_put(verdict_h);
+    pinned_put(changed_h);
     if (own_stream && s) cudaStreamDestroy(s);
 }
 
@@ -132,9 +199,10 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
         own_stream = true;
     }
     pool.s = s;
-    LPP_CUDA(cudaMallocHost(&st_h, sizeof(DevStatus)));
-    LPP_CUDA(cudaMallocHost(&verdict_h, sizeof(int32_t) * (size_t)nlp * V_SLOTS));
-    LPP_CUDA(cudaMallocHost(&changed_h, (size_t)nlp));
+    keep_pool_memory(o.device);
+    st_h = static_cast<DevStatus *>(pinned_get_sized(sizeof(DevStatus)));
+    verdict_h = static_cast<int32_t *>(pinned_get_sized(sizeof(int32_t) * (size_t)nlp * V_SLOTS));
+    changed_h = static_cast<uint8_t *>(pinned_get_sized((size_t)nlp));
     const bool arena = nlp > 1;
     for (int b = 0; b < 2; b++) {
         rp[b] = pool.alloc<int32_t>(m0 + 1);

@@ -167,8 +167,32 @@ struct lpp_reduced {
     std::vector<double> h_rv, h_c, h_L, h_U, h_lb, h_ub, h_tv;
 };
 
+namespace lpp {
+// Device-resident results of one engine run (all its LPs), shared by their
+// postsolve records; the host copies are made on first access.
+struct DeviceRecords {
+    int32_t m0 = 0, n0 = 0, n_final = 0, act_m = 0;
+    int32_t *rk = nullptr, *rr = nullptr, *ra = nullptr, *ck = nullptr, *cr = nullptr;
+    double *rv = nullptr, *cv = nullptr;
+    double2 *lu = nullptr;       // [n_final] final bounds of the kept columns (arena order)
+    int32_t *cmap = nullptr;     // [n_final] their original (arena) index
+    double2 *act = nullptr;      // [act_m] last round's activities (that round's numbering)
+    int2 *ninf = nullptr;
+    int32_t *act_rmap = nullptr;
+    std::vector<void *> owned;
+    ~DeviceRecords() {
+        for (void *p : owned) cudaFree(p);
+    }
+};
+}  // namespace lpp
+
 struct lpp_postsolve {
     lpp_info info{};
+    std::shared_ptr<lpp::DeviceRecords> dev;
+    int32_t r0 = 0, c0 = 0;          // first original row / column of this LP in the arena
+    int32_t cstart = 0;              // first kept column of this LP in the final arena
+    int32_t astart = 0, acnt = 0;    // this LP's rows in the last round's numbering
+    bool host_ready = false;
     std::vector<int32_t> row_kind, row_round, row_aux, col_kind, col_round, col_map;
     std::vector<double> row_val, col_val, col_lb, col_ub, act_min, act_max;
     std::vector<int32_t> ninf_min, ninf_max;

@@ -218,25 +218,6 @@ class Result:
         self.index = info.index
         self.round = info.round
         self.rounds = info.rounds
-        m, n = info.m, info.n
-        self.row_kind = np.zeros(m, np.int32)
-        self.row_round = np.zeros(m, np.int32)
-        self.row_aux = np.zeros(m, np.int32)
-        self.row_val = np.zeros(m)
-        _check(L.lpp_result_rows(rec, _p(self.row_kind), _p(self.row_round), _p(self.row_aux), _p(self.row_val)))
-        self.col_kind = np.zeros(n, np.int32)
-        self.col_round = np.zeros(n, np.int32)
-        self.col_val = np.zeros(n)
-        self.col_lb = np.zeros(n)
-        self.col_ub = np.zeros(n)
-        _check(L.lpp_result_cols(rec, _p(self.col_kind), _p(self.col_round), _p(self.col_val), _p(self.col_lb),
-                                 _p(self.col_ub)))
-        self.act_min = np.zeros(m)
-        self.act_max = np.zeros(m)
-        self.ninf_min = np.zeros(m, np.int32)
-        self.ninf_max = np.zeros(m, np.int32)
-        _check(L.lpp_result_activity(rec, _p(self.act_min), _p(self.act_max), _p(self.ninf_min),
-                                     _p(self.ninf_max)))
         R = C.c_int32(0)
         cap = 1024
         self.round_nnz = np.zeros(cap, np.int64)
@@ -256,6 +237,33 @@ class Result:
         self.kernels = {ks[i].name.decode(): dict(launches=ks[i].launches, ms=ks[i].ms, bytes=ks[i].bytes)
                         for i in range(cnt.value)}
         self._reduced = None
+        self._records = None
+
+    _RECORD_FIELDS = ("row_kind", "row_round", "row_aux", "row_val", "col_kind", "col_round", "col_val", "col_lb",
+                      "col_ub", "act_min", "act_max", "ninf_min", "ninf_max")
+
+    def __getattr__(self, name):
+        # per-row / per-column records are copied from the device on first use
+        if name in Result._RECORD_FIELDS:
+            if self._records is None:
+                self._records = self._load_records()
+            return self._records[name]
+        raise AttributeError(name)
+
+    def _load_records(self):
+        L = load()
+        rec = self._rec
+        m, n = self.info.m, self.info.n
+        r = dict(row_kind=np.zeros(m, np.int32), row_round=np.zeros(m, np.int32), row_aux=np.zeros(m, np.int32),
+                 row_val=np.zeros(m), col_kind=np.zeros(n, np.int32), col_round=np.zeros(n, np.int32),
+                 col_val=np.zeros(n), col_lb=np.zeros(n), col_ub=np.zeros(n), act_min=np.zeros(m),
+                 act_max=np.zeros(m), ninf_min=np.zeros(m, np.int32), ninf_max=np.zeros(m, np.int32))
+        _check(L.lpp_result_rows(rec, _p(r["row_kind"]), _p(r["row_round"]), _p(r["row_aux"]), _p(r["row_val"])))
+        _check(L.lpp_result_cols(rec, _p(r["col_kind"]), _p(r["col_round"]), _p(r["col_val"]), _p(r["col_lb"]),
+                                 _p(r["col_ub"])))
+        _check(L.lpp_result_activity(rec, _p(r["act_min"]), _p(r["act_max"]), _p(r["ninf_min"]),
+                                     _p(r["ninf_max"])))
+        return r
 
     @property
     def presolve_ms(self) -> float:
