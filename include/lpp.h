@@ -135,6 +135,7 @@ typedef struct lpp_kernel_stat {
     int32_t launches;
     double ms;            /* summed CUDA-event time of its launches               */
     double bytes;         /* algorithmic DRAM bytes of those launches             */
+    double fp64_ops;      /* algorithmic FP64 operations (activity FMAs), or 0   */
 } lpp_kernel_stat;
 
 void lpp_opts_default(lpp_opts *opts);

@@ -243,6 +243,12 @@ __global__ void __launch_bounds__(kBlock) k_rowvec(Ctx C, CompactCtx K) {
     K.rmap2[p] = C.rmap[i];
     if (C.lp_row) K.lp_row2[p] = C.lp_row[i];
     K.rp2[p] = K.r_off[i];
+    // a row that lost entries (fixed columns) changed: evaluate it next round
+    const bool lost = K.r_len[i] != C.A.ptr[i + 1] - C.A.ptr[i];
+    K.rdirty2[p] = (uint8_t)(C.rdnext[i] | lost);
+    K.act2[p] = C.act[i];
+    K.ninf2[p] = C.ninf[i];
+    K.hrow2[p] = C.hrow[i];
 }
 
 __global__ void __launch_bounds__(kBlock) k_colvec(Ctx C, CompactCtx K) {

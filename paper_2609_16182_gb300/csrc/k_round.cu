@@ -168,9 +168,16 @@ __device__ __forceinline__ unsigned long long len_hash(int32_t len) {
 
 // ------------------------------------------------------- S1 + S2 + S3 groups
 template <int W>
-__device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, int32_t &removed) {
+__device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, int32_t &removed, int32_t &evaluated) {
     const unsigned mask = group_mask<W>();
     const int lane = threadIdx.x & (W - 1);
+    // A row none of whose bounds, entries or sides changed since its last
+    // evaluation has the same activities and class (kept) and yields the same
+    // implied bounds, which were then already applied or rejected: skip it.
+    if (valid && !C.rdirty[i]) {
+        if (lane == 0) C.rkind[i] = RK_KEPT;
+        return;
+    }
     int32_t beg = 0, end = 0;
     if (valid) {
         beg = C.A.ptr[i];
@@ -200,6 +207,7 @@ __device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, 
     if (!valid) return;
     const int32_t len = end - beg;
     h += len_hash(len);
+    if (lane == 0) evaluated += len;
     const double Lv = C.L[i], Uv = C.U[i];
     uint8_t kind = RK_KEPT;
     if (lane == 0) removed += finish_row(C, i, beg, len, Lv, Uv, smin, smax, nmin, nmax, h, kind);
@@ -214,20 +222,21 @@ __device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, 
 __global__ void __launch_bounds__(kBlock) k_prop_groups(Ctx C, GroupGrid g) {
     const int c = grid_class(g, blockIdx.x);
     const int32_t lb = blockIdx.x - g.blk_start[c];
-    int32_t removed = 0;
+    int32_t removed = 0, evaluated = 0;
     const int W = 1 << c;
     const int32_t pos = C.A.cls_start[c] + lb * (kBlock / W) + threadIdx.x / W;
     const bool valid = pos < C.A.cls_start[c + 1];
     const int32_t i = valid ? C.A.order[pos] : 0;
     switch (c) {
-        case 0: prop_group<1>(C, i, valid, removed); break;
-        case 1: prop_group<2>(C, i, valid, removed); break;
-        case 2: prop_group<4>(C, i, valid, removed); break;
-        case 3: prop_group<8>(C, i, valid, removed); break;
-        case 4: prop_group<16>(C, i, valid, removed); break;
-        default: prop_group<32>(C, i, valid, removed); break;
+        case 0: prop_group<1>(C, i, valid, removed, evaluated); break;
+        case 1: prop_group<2>(C, i, valid, removed, evaluated); break;
+        case 2: prop_group<4>(C, i, valid, removed, evaluated); break;
+        case 3: prop_group<8>(C, i, valid, removed, evaluated); break;
+        case 4: prop_group<16>(C, i, valid, removed, evaluated); break;
+        default: prop_group<32>(C, i, valid, removed, evaluated); break;
     }
     block_add(removed, &C.st->rows_removed);
+    block_add(evaluated, &C.st->nnz_eval);
 }
 
 // fixed-order block reduction (warp butterflies, then warps in order)
@@ -250,6 +259,7 @@ __global__ void __launch_bounds__(kBlock) k_prop_long_partial(Ctx C, unsigned lo
     __shared__ int s_i[kBlock / 32];
     __shared__ unsigned long long s_h[kBlock / 32];
     const Chunk ch = C.A.chunks[blockIdx.x];
+    if (!C.rdirty[ch.seg]) return;  // block-uniform
     const bool neg0 = is_neg(C.A.val[C.A.ptr[ch.seg]]);
     double smin = 0.0, smax = 0.0;
     int nmin = 0, nmax = 0;
@@ -281,8 +291,11 @@ __global__ void __launch_bounds__(kBlock) k_prop_long_partial(Ctx C, unsigned lo
 __global__ void k_prop_long_combine(Ctx C, const unsigned long long *ch_hash) {
     const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t nlong = C.A.cls_start[7] - C.A.cls_start[6];
-    int32_t removed = 0;
-    if (t < nlong) {
+    int32_t removed = 0, evaluated = 0;
+    if (t < nlong && !C.rdirty[C.A.order[C.A.cls_start[6] + t]]) {
+        C.rkind[C.A.order[C.A.cls_start[6] + t]] = RK_KEPT;
+        C.lneed[t] = 0;
+    } else if (t < nlong) {
         const int32_t i = C.A.order[C.A.cls_start[6] + t];
         double smin = 0.0, smax = 0.0;
         int nmin = 0, nmax = 0;
@@ -301,10 +314,12 @@ __global__ void k_prop_long_combine(Ctx C, const unsigned long long *ch_hash) {
         const double Lv = C.L[i], Uv = C.U[i];
         uint8_t kind;
         removed = finish_row(C, i, beg, len, Lv, Uv, smin, smax, nmin, nmax, h, kind);
+        evaluated = len;
         const bool need = kind == RK_KEPT && ((is_fin(Uv) && nmin <= 1) || (is_fin(Lv) && nmax <= 1));
         C.lneed[t] = need;
     }
     block_add(removed, &C.st->rows_removed);
+    block_add(evaluated, &C.st->nnz_eval);
 }
 
 __global__ void __launch_bounds__(kBlock) k_prop_long_tighten(Ctx C) {
@@ -327,6 +342,7 @@ __global__ void __launch_bounds__(kBlock) k_colfin(Ctx C) {
         const unsigned long long el = C.cand_l[j], eu = C.cand_u[j];
         const bool has = el != kEncNegInf || eu != kEncPosInf;
         uint8_t kind = CK_KEPT;
+        uint8_t chg = 0;
         if (has || C.round == 1) {
             if (has) {
                 C.cand_l[j] = kEncNegInf;
@@ -357,6 +373,7 @@ __global__ void __launch_bounds__(kBlock) k_colfin(Ctx C) {
                 if (nl != b.x || nu != b.y) {
                     C.lu[j] = make_double2(nl, nu);
                     changed = 1;
+                    chg = 1;
                     C.lp_changed[lp] = 1;
                 }
                 if (nl == nu) {
@@ -372,6 +389,7 @@ __global__ void __launch_bounds__(kBlock) k_colfin(Ctx C) {
             }
         }
         C.ckind[j] = kind;
+        C.cchg[j] = chg;
     }
     block_add(changed, &C.st->bounds_changed);
     block_add(fixed, &C.st->cols_fixed);
@@ -584,8 +602,39 @@ __global__ void __launch_bounds__(kBlock) k_s5_leader(Ctx C) {
             nU = mid;
         }
     }
+    if (nL != C.L[i] || nU != C.U[i]) C.rdnext[i] = 1;
     C.L[i] = nL;
     C.U[i] = nU;
+}
+
+// rows of a column whose bounds changed must be re-evaluated next round
+template <int W>
+__device__ __forceinline__ void mark_group(const Ctx &C, int32_t j, bool valid) {
+    if (!valid || !C.cchg[j]) return;
+    const int lane = threadIdx.x & (W - 1);
+    for (int32_t k = C.T.ptr[j] + lane; k < C.T.ptr[j + 1]; k += W) C.rdnext[C.T.idx[k]] = 1;
+}
+
+__global__ void __launch_bounds__(kBlock) k_mark_groups(Ctx C, GroupGrid g) {
+    const int c = grid_class(g, blockIdx.x);
+    const int W = 1 << c;
+    const int32_t pos = C.T.cls_start[c] + (blockIdx.x - g.blk_start[c]) * (kBlock / W) + threadIdx.x / W;
+    const bool valid = pos < C.T.cls_start[c + 1];
+    const int32_t j = valid ? C.T.order[pos] : 0;
+    switch (c) {
+        case 0: mark_group<1>(C, j, valid); break;
+        case 1: mark_group<2>(C, j, valid); break;
+        case 2: mark_group<4>(C, j, valid); break;
+        case 3: mark_group<8>(C, j, valid); break;
+        case 4: mark_group<16>(C, j, valid); break;
+        default: mark_group<32>(C, j, valid); break;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_mark_long(Ctx C) {
+    const Chunk ch = C.T.chunks[blockIdx.x];
+    if (!C.cchg[ch.seg]) return;
+    for (int32_t k = ch.begin + threadIdx.x; k < ch.end; k += kBlock) C.rdnext[C.T.idx[k]] = 1;
 }
 
 inline unsigned blocks_for(int64_t cnt, int threads) {
@@ -607,6 +656,12 @@ void launch_prop(const Ctx &C, cudaStream_t s) {
 
 void launch_colfin(const Ctx &C, cudaStream_t s) {
     if (C.n > 0) k_colfin<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C);
+}
+
+void launch_mark_dirty(const Ctx &C, cudaStream_t s) {
+    const GroupGrid g = group_grid(C.T);
+    if (g.blk_start[6] > 0) k_mark_groups<<<g.blk_start[6], kBlock, 0, s>>>(C, g);
+    if (C.T.cls_start[7] > C.T.cls_start[6] && C.T.nchunks > 0) k_mark_long<<<C.T.nchunks, kBlock, 0, s>>>(C);
 }
 
 void launch_s5_pass(const Ctx &C, int pass, cudaStream_t s) {

@@ -123,8 +123,8 @@ std::shared_ptr<DeviceRecords> take_records(Engine &E) {
     D->cr = E.rec_cr;
     D->cv = E.rec_cv;
     D->lu = E.lu[E.cur];
-    D->act = E.act;
-    D->ninf = E.ninf;
+    D->act = E.act[E.act_buf];
+    D->ninf = E.ninf[E.act_buf];
     for (void *p : {(void *)D->rk, (void *)D->rr, (void *)D->ra, (void *)D->rv, (void *)D->ck, (void *)D->cr,
                     (void *)D->cv, (void *)D->lu, (void *)D->act, (void *)D->ninf}) {
         E.pool.forget(p);
@@ -187,6 +187,7 @@ lpp_postsolve *make_postsolve(Engine &E, const std::shared_ptr<DeviceRecords> &D
             ks[mk.fam].launches++;
             ks[mk.fam].ms += ms;
             ks[mk.fam].bytes += mk.bytes;
+            ks[mk.fam].fp64_ops += mk.ops;
         }
         P->kstats = ks;
     }

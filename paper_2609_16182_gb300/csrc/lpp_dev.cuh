@@ -44,7 +44,7 @@ enum { V_S2_ROW = 0, V_S3_COL = 1, V_S5_ROW = 2, V_S6_COL = 3, V_SLOTS = 4 };
 // Global counters of a round (block-aggregated atomics).
 struct DevStatus {
     int32_t rows_removed, cols_fixed, bounds_changed, unmatched;
-    int32_t participants, long_tighten, err, pad0;
+    int32_t participants, long_tighten, err, nnz_eval;  // nnz_eval: nonzeros of the rows S1 evaluated
     int32_t cls_r[kNumClass];  // class sizes of the rows after compaction
     int32_t cls_c[kNumClass];  // class sizes of the columns after compaction
     int32_t nchunk_r, nchunk_c;
@@ -82,6 +82,11 @@ struct Ctx {
     double2 *lu;
     const double *c;
     const int32_t *cmap, *lp_col;
+    // rows whose activities must be recomputed this round (1) and the flags
+    // being gathered for the next round; columns whose bounds changed
+    const uint8_t *rdirty;
+    uint8_t *rdnext;
+    uint8_t *cchg;
     // row work
     double2 *act;
     int2 *ninf;
@@ -139,6 +144,10 @@ struct CompactCtx {
     double2 *lu2;
     double *c2;
     int32_t *cmap2, *lp_col2;
+    uint8_t *rdirty2;                          // next round's dirty flags
+    double2 *act2;                             // carried results of clean rows
+    int2 *ninf2;
+    unsigned long long *hrow2;
 };
 
 // ------------------------------------------------------------------ helpers

@@ -169,6 +169,7 @@ void Engine::tbegin(int fam, double bytes) {
     Tmark mk;
     mk.fam = fam;
     mk.bytes = bytes;
+    mk.ops = 0.0;
     LPP_CUDA(cudaEventCreate(&mk.a));
     LPP_CUDA(cudaEventCreate(&mk.b));
     LPP_CUDA(cudaEventRecord(mk.a, s));
@@ -237,12 +238,17 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
         b.tile_hist = pool.alloc<int32_t>(sched_tile_hist_elems(cnt));
         b.tmp = scan_tmp;
     }
-    act = pool.alloc<double2>(m0);
-    ninf = pool.alloc<int2>(m0);
+    for (int b = 0; b < 2; b++) {
+        act[b] = pool.alloc<double2>(m0);
+        ninf[b] = pool.alloc<int2>(m0);
+        hrow[b] = pool.alloc<unsigned long long>(m0);
+        rdirty[b] = pool.alloc<uint8_t>(m0);
+    }
+    rdnext = pool.alloc<uint8_t>(m0);
+    cchg = pool.alloc<uint8_t>(n0);
     rkind = pool.alloc<uint8_t>(m0);
     rwork = pool.alloc<uint8_t>(m0);
     hasf = pool.alloc<uint8_t>(m0);
-    hrow = pool.alloc<unsigned long long>(m0);
     mL = pool.alloc<unsigned long long>(m0);
     mU = pool.alloc<unsigned long long>(m0);
     rslot = pool.alloc<int32_t>(m0);
@@ -412,6 +418,7 @@ void Engine::prepare() {
     fill_u64(mL, m0, kEncNegInf, s);
     fill_u64(mU, m0, kEncPosInf, s);
     LPP_CUDA(cudaMemsetAsync(hasf, 0, (size_t)std::max(m0, 1), s));
+    LPP_CUDA(cudaMemsetAsync(rdirty[0], 1, (size_t)std::max(m0, 1), s));  // round 1 evaluates every row
     LPP_CUDA(cudaMemsetAsync(rwork, 0, (size_t)std::max(m0, 1), s));
     fill_i32(verdict, (int64_t)nlp * V_SLOTS, kNone, s);
     LPP_CUDA(cudaMemsetAsync(rec_rk, 0, sizeof(int32_t) * (size_t)std::max(m0, 1), s));
@@ -482,11 +489,14 @@ Ctx Engine::ctx(int32_t round) const {
     C.c = c[cur];
     C.cmap = cmap[cur];
     C.lp_col = lpcol[cur];
-    C.act = act;
-    C.ninf = ninf;
+    C.act = act[cur];
+    C.ninf = ninf[cur];
+    C.rdirty = rdirty[cur];
+    C.rdnext = rdnext;
+    C.cchg = cchg;
     C.rkind = rkind;
     C.rwork = rwork;
-    C.hrow = hrow;
+    C.hrow = hrow[cur];
     C.rslot = rslot;
     C.mL = mL;
     C.mU = mU;
@@ -536,6 +546,10 @@ void Engine::compact(int32_t round) {
     K.c2 = c[nx];
     K.cmap2 = cmap[nx];
     K.lp_col2 = lpcol[nx];
+    K.rdirty2 = rdirty[nx];
+    K.act2 = act[nx];
+    K.ninf2 = ninf[nx];
+    K.hrow2 = hrow[nx];
     const Ctx C = ctx(round);
     tbegin(F_COUNT, 4.0 * nnz * 2 + 8.0 * nnz + 24.0 * m + 40.0 * n);
     launch_compact_counts(C, K, s);
@@ -592,12 +606,15 @@ void Engine::run() {
         LPP_CUDA(cudaEventRecord(e0, s));
         LPP_CUDA(cudaMemsetAsync(st, 0, 8 * sizeof(int32_t), s));
         LPP_CUDA(cudaMemsetAsync(lp_changed, 0, (size_t)nlp, s));
+        if (m > 0) LPP_CUDA(cudaMemsetAsync(rdnext, 0, (size_t)m, s));
         Ctx C = ctx(r);
-        tbegin(F_PROP, 12.0 * nnz + 4.0 * (m + 1) + 16.0 * m + 16.0 * n + 33.0 * m);
+        tbegin(F_PROP, 0.0);  // bytes and ops set once the evaluated nonzeros are known
+        const size_t prop_mark = marks.size();
         launch_prop(C, s);
         tend();
         tbegin(F_COLFIN, 33.0 * n);
         launch_colfin(C, s);
+        launch_mark_dirty(C, s);
         tend();
         LPP_CUDA(cudaGetLastError());
         // S5: leader passes
@@ -610,6 +627,14 @@ void Engine::run() {
         tend();
         LPP_CUDA(cudaGetLastError());
         read_status();
+        r_eval.push_back(st_h->nnz_eval);
+        if (o.timing && prop_mark > 0) {
+            // S1 algorithmic work: per evaluated nonzero its 12 bytes and two FMAs,
+            // per row ptr, sides, results (4 + 16 + 33 bytes), the bounds once
+            Tmark &pm = marks[prop_mark - 1];
+            pm.bytes = 12.0 * st_h->nnz_eval + 53.0 * m + 16.0 * n;
+            pm.ops = 2.0 * st_h->nnz_eval;
+        }
         for (int pass = 1; st_h->unmatched > 0 && pass < o.par_max_iter; pass++) {
             tcap = std::min(tcap_max, pow2_at_least(2 * (int64_t)st_h->unmatched));
             LPP_CUDA(cudaMemsetAsync(tkey, 0, sizeof(unsigned long long) * tcap, s));
@@ -631,6 +656,7 @@ void Engine::run() {
         const bool structural = r == 1 || st_h->rows_removed > 0 || st_h->cols_fixed > 0 || newly_dead;
         int32_t rows_removed = st_h->rows_removed, bounds = st_h->bounds_changed;
         if (structural) compact(r);
+        else std::swap(rdirty[cur], rdnext);  // same numbering: next round's flags
         LPP_CUDA(cudaEventRecord(e1, s));
         read_status();
         float ms = 0.f;

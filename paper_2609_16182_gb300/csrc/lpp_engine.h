@@ -78,11 +78,13 @@ struct Engine {
     // schedules
     SchedBufs sa, sb;  // A (rows), T (columns)
     int32_t cap_long_a, cap_long_t;
-    // work
-    double2 *act;
-    int2 *ninf;
+    // work (row results are double-buffered: clean rows carry them over)
+    double2 *act[2];
+    int2 *ninf[2];
+    unsigned long long *hrow[2];
+    uint8_t *rdirty[2], *rdnext, *cchg;
     uint8_t *rkind, *rwork, *hasf, *ckind, *lneed, *lp_changed, *lp_dead;
-    unsigned long long *hrow, *mL, *mU, *cand_l, *cand_u, *tkey, *tlead, *ch_hash;
+    unsigned long long *mL, *mU, *cand_l, *cand_u, *tkey, *tlead, *ch_hash;
     int32_t *rslot, *verdict;
     double *fixv;
     double2 *ch_act;
@@ -115,8 +117,9 @@ struct Engine {
     struct Tmark {
         int fam;
         cudaEvent_t a, b;
-        double bytes;
+        double bytes, ops;
     };
+    std::vector<int64_t> r_eval;  // nonzeros S1 evaluated per round
     std::vector<Tmark> marks;
     std::vector<cudaEvent_t> spare_events;
 

@@ -60,6 +60,7 @@ void split_lu(const double2 *lu, int32_t n, double *lb, double *ub, cudaStream_t
 // ---------------------------------------------------------------- k_round.cu
 void launch_prop(const Ctx &C, cudaStream_t s);
 void launch_colfin(const Ctx &C, cudaStream_t s);
+void launch_mark_dirty(const Ctx &C, cudaStream_t s);
 void launch_s5_pass(const Ctx &C, int pass, cudaStream_t s);
 void launch_s5_leader(const Ctx &C, cudaStream_t s);
 

@@ -50,7 +50,8 @@ class Info(C.Structure):
 
 
 class KernelStat(C.Structure):
-    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int32), ("ms", C.c_double), ("bytes", C.c_double)]
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int32), ("ms", C.c_double), ("bytes", C.c_double),
+                ("fp64_ops", C.c_double)]
 
 
 class ServerStats(C.Structure):
@@ -234,7 +235,8 @@ class Result:
         ks = (KernelStat * 32)()
         cnt = C.c_int32(0)
         _check(L.lpp_result_kernels(rec, 32, ks, C.byref(cnt)))
-        self.kernels = {ks[i].name.decode(): dict(launches=ks[i].launches, ms=ks[i].ms, bytes=ks[i].bytes)
+        self.kernels = {ks[i].name.decode(): dict(launches=ks[i].launches, ms=ks[i].ms, bytes=ks[i].bytes,
+                                                  fp64_ops=ks[i].fp64_ops)
                         for i in range(cnt.value)}
         self._reduced = None
         self._records = None
