@@ -498,3 +498,112 @@ def micro(seed: int, m: int = 5, n: int = 6, slack: float = 0.5) -> LP:
     rhs[empty] = np.maximum(rhs[empty], 0.0)
     c = _cost(rng, lb, ub)
     return _finish(m, n, ptr, cols, vals, c, lhs, rhs, lb, ub, dict(x0=x0, kinds=kinds), f"micro-{seed}")
+
+
+# ----------------------------------------------------- vectorised 200-row mix
+def _distinct_columns(rng, lengths, n, pool=None):
+    """Columns for rows of the given lengths, distinct inside each row, drawn
+    uniformly from `pool` (default: all n columns)."""
+    ptr = _ptr_from_lengths(lengths)
+    rows = _row_of_entry(ptr)
+    size = n if pool is None else len(pool)
+
+    def draw(k):
+        d = rng.integers(0, size, k)
+        return d if pool is None else pool[d]
+
+    cols = draw(int(ptr[-1]))
+    for _ in range(200):
+        key = rows * n + cols
+        order = np.argsort(key, kind="stable")
+        dup = np.flatnonzero(key[order][1:] == key[order][:-1])
+        if dup.size == 0:
+            break
+        redo = np.unique(order[dup + 1])
+        cols[redo] = draw(redo.size)
+    else:
+        raise RuntimeError("could not draw distinct columns")
+    return ptr, rows, cols
+
+
+def mix(seed: int, m: int = 200, n: int = 300, mean_len: float = 9.0, n_empty: int = 10,
+        n_single: int = 15, n_fixed: int = 20, n_redundant: int = 10, n_parallel: int = 8,
+        eq_frac: float = 0.5, inf_ub_frac: float = 0.1) -> LP:
+    """The recipe of ``tiny`` drawn with whole-array NumPy operations (for
+    large batches): base rows of length U{2..2*mean-2}, scaled copies, singleton
+    rows, redundant rows over finitely bounded columns, empty rows, fixed
+    columns, rows in random order."""
+    rng = np.random.default_rng(seed)
+    n_base = m - n_empty - n_single - n_redundant - n_parallel
+    assert n_base >= max(1, n_parallel) and n >= 8
+    lb = np.zeros(n)
+    ub = rng.uniform(1.0, 100.0, n)
+    ub[rng.random(n) < inf_ub_frac] = INF
+    fixed_cols = rng.choice(n, size=min(n_fixed, n), replace=False)
+    fv = rng.uniform(1.0, 10.0, len(fixed_cols))
+    lb[fixed_cols] = fv
+    ub[fixed_cols] = fv
+    x0 = _point_in_box(rng, lb, ub)
+    hi_len = max(3, int(round(2 * mean_len - 2)))
+    blen = np.minimum(rng.integers(2, hi_len + 1, n_base), n)
+    bptr, brows, bcols = _distinct_columns(rng, blen, n)
+    bvals = _draw_magnitudes(rng, bcols.size)
+    # scaled copies of random base rows
+    src = rng.choice(n_base, size=n_parallel, replace=False)
+    lam = rng.uniform(0.5, 4.0, n_parallel) * np.where(rng.random(n_parallel) < 0.5, -1.0, 1.0)
+    plen = blen[src]
+    pidx = np.concatenate([np.arange(bptr[s_], bptr[s_ + 1]) for s_ in src]) if n_parallel else np.zeros(0, int)
+    pcols = bcols[pidx]
+    pvals = bvals[pidx] * np.repeat(lam, plen)
+    # singleton rows
+    scols = rng.integers(0, n, n_single)
+    svals = _draw_magnitudes(rng, n_single)
+    # redundant rows over finitely bounded columns
+    finite = np.flatnonzero(np.isfinite(ub))
+    rlen = np.minimum(rng.integers(2, 6, n_redundant), len(finite))
+    _, rrows, rcols = _distinct_columns(rng, rlen, n, pool=finite)
+    rvals = _draw_magnitudes(rng, rcols.size)
+    lengths = np.concatenate([blen, plen, np.ones(n_single, np.int64), rlen, np.zeros(n_empty, np.int64)])
+    kinds = np.array(["base"] * n_base + ["parallel"] * n_parallel + ["singleton"] * n_single
+                     + ["redundant"] * n_redundant + ["empty"] * n_empty)
+    cols_all = np.concatenate([bcols, pcols, scols, rcols]).astype(np.int64)
+    vals_all = np.concatenate([bvals, pvals, svals, rvals])
+    row_all = np.repeat(np.arange(m), lengths)
+    perm = rng.permutation(m)
+    ptr, cols, vals = _sort_rows(perm[row_all], cols_all, vals_all, m)
+    kinds_new = np.empty(m, dtype=kinds.dtype)
+    kinds_new[perm] = kinds
+    ax = _dot_rows(ptr, cols, vals, x0, m)
+    eq = rng.random(m) < eq_frac
+    lhs, rhs = _sides_around(rng, ax, eq)
+    red = perm[n_base + n_parallel + n_single + np.arange(n_redundant)]
+    rows_sorted = _row_of_entry(ptr)
+    big = np.bincount(rows_sorted, weights=np.abs(vals) * np.maximum(np.abs(lb[cols]), np.abs(
+        np.where(np.isfinite(ub[cols]), ub[cols], 0.0))), minlength=m)
+    margin = 1.0 + rng.uniform(0.0, 1.0, m) * big
+    lhs[red] = np.where(rng.random(n_redundant) < 0.7, -big[red] - margin[red], -INF)
+    rhs[red] = big[red] + margin[red]
+    emp = perm[m - n_empty + np.arange(n_empty)]
+    eqz = rng.random(n_empty) < 0.3
+    lhs[emp] = np.where(eqz, 0.0, np.where(rng.random(n_empty) < 0.7, -rng.uniform(0, 5, n_empty), -INF))
+    rhs[emp] = np.where(eqz, 0.0, np.where(rng.random(n_empty) < 0.7, rng.uniform(0, 5, n_empty), INF))
+    c = _cost(rng, lb, ub)
+    planted = dict(empty=n_empty, singleton=n_single, fixed=len(fixed_cols), redundant=n_redundant,
+                   parallel=n_parallel, kinds=kinds_new)
+    return _finish(m, n, ptr, cols, vals, c, lhs, rhs, lb, ub, planted, f"mix-{seed}")
+
+
+def batch_mix(seed: int = 0, count: int = 4096, m_lo: int = 50, m_hi: int = 5000,
+              nnz_per_row: float = 6.0) -> list[LP]:
+    """The ragged batch with the vectorised generator: m log-uniform in
+    [m_lo, m_hi], n = 1.5 m, about ``nnz_per_row`` entries per row, the
+    planted mix scaled by m/200; LP k uses seed ``seed * 1_000_003 + k``."""
+    rng = np.random.default_rng(seed)
+    ms = np.exp(rng.uniform(np.log(m_lo), np.log(m_hi), count)).astype(np.int64)
+    out = []
+    for k, m in enumerate(ms):
+        f = m / 200.0
+        out.append(mix(seed * 1_000_003 + k, m=int(m), n=int(1.5 * m), mean_len=nnz_per_row,
+                       n_empty=max(1, int(10 * f)), n_single=max(1, int(15 * f)), n_fixed=max(1, int(20 * f)),
+                       n_redundant=max(1, int(10 * f)), n_parallel=max(1, int(8 * f))))
+    return out
