@@ -401,14 +401,14 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                     if (is_upper[t]) {
                         if (isfin(s.u[jj])) {
                             double thr = s.u[jj] - o->bound_tol * dmax(1.0, fabs(s.u[jj]));
-                            audit(&au, cv - thr, ebc[t] + s.ebu[jj]);
+                            audit(&au, cv - thr, ebc[t] + s.ebu[jj] + 2 * UROUND * fabs(thr));
                             if (!(cv < thr)) continue;
                         }
                         if (cv < nu[jj]) { nu[jj] = cv; ebnu[jj] = ebc[t]; }
                     } else {
                         if (isfin(s.l[jj])) {
                             double thr = s.l[jj] + o->bound_tol * dmax(1.0, fabs(s.l[jj]));
-                            audit(&au, cv - thr, ebc[t] + s.ebl[jj]);
+                            audit(&au, cv - thr, ebc[t] + s.ebl[jj] + 2 * UROUND * fabs(thr));
                             if (!(cv > thr)) continue;
                         }
                         if (cv > nl[jj]) { nl[jj] = cv; ebnl[jj] = ebc[t]; }
