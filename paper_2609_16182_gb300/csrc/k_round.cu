@@ -32,27 +32,28 @@ __device__ __forceinline__ int32_t lp_of_row(const Ctx &C, int32_t i) { return C
 __device__ __forceinline__ int32_t lp_of_col(const Ctx &C, int32_t j) { return C.lp_col ? C.lp_col[j] : 0; }
 
 // Implied upper bound x/a on column j (from a*x_j <= x with a > 0, or
-// a*x_j >= x with a < 0).  Accepted iff |x/a| <= max_implied and
-// (uold = +inf or x/a < uold - bound_tol*max(1,|uold|)).  Both tests are
-// decided exactly on the real quotient by the sign of one fused multiply-add.
+// a*x_j >= x with a < 0).  Accepted iff (uold = +inf or x/a < thr) and
+// |x/a| <= max_implied, thr = uold - bound_tol*max(1,|uold|) (one rounding).
+// Both tests are decided exactly on the real quotient by the sign of one
+// fused multiply-add; the cap is tested only for candidates that pass.
 __device__ __forceinline__ void try_upper(const Ctx &C, int32_t j, double x, double a, double uold) {
-    if (fma(-C.max_implied, fabs(a), fabs(x)) > 0.0) return;
     if (is_fin(uold)) {
-        const double thr = uold - C.bound_tol * max1abs(uold);
+        const double thr = fma(-C.bound_tol, max1abs(uold), uold);
         const double s = fma(-thr, a, x);
         if (is_neg(a) ? !(s > 0.0) : !(s < 0.0)) return;
     }
+    if (fma(-C.max_implied, fabs(a), fabs(x)) > 0.0) return;
     atomic_min_dbl(&C.cand_u[j], x / a);
 }
-// Implied lower bound x/a: accepted iff |x/a| <= max_implied and
-// (lold = -inf or x/a > lold + bound_tol*max(1,|lold|)).
+// Implied lower bound x/a: accepted iff (lold = -inf or x/a > thr) and
+// |x/a| <= max_implied, thr = lold + bound_tol*max(1,|lold|).
 __device__ __forceinline__ void try_lower(const Ctx &C, int32_t j, double x, double a, double lold) {
-    if (fma(-C.max_implied, fabs(a), fabs(x)) > 0.0) return;
     if (is_fin(lold)) {
-        const double thr = lold + C.bound_tol * max1abs(lold);
+        const double thr = fma(C.bound_tol, max1abs(lold), lold);
         const double s = fma(-thr, a, x);
         if (is_neg(a) ? !(s < 0.0) : !(s > 0.0)) return;
     }
+    if (fma(-C.max_implied, fabs(a), fabs(x)) > 0.0) return;
     atomic_max_dbl(&C.cand_l[j], x / a);
 }
 

@@ -11,101 +11,129 @@ namespace {
 constexpr int kScanThreads = 256;
 constexpr int kPerThread = kScanTile / kScanThreads;  // 8
 
-__device__ __forceinline__ int32_t block_sum_i32(int32_t v, int32_t *s_w) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
-    __syncthreads();
-    int32_t t = 0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_w[w];
-    return t;  // valid in thread 0
+struct Pair {
+    int32_t a, b;
+};
+__device__ __forceinline__ Pair operator+(Pair x, Pair y) { return Pair{x.a + y.a, x.b + y.b}; }
+__device__ __forceinline__ Pair operator-(Pair x, Pair y) { return Pair{x.a - y.a, x.b - y.b}; }
+__device__ __forceinline__ Pair shfl_up(Pair v, int o) {
+    return Pair{__shfl_up_sync(0xffffffffu, v.a, o), __shfl_up_sync(0xffffffffu, v.b, o)};
 }
+__device__ __forceinline__ int32_t shfl_up(int32_t v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+template <class T> __device__ __forceinline__ T zero_of();
+template <> __device__ __forceinline__ int32_t zero_of<int32_t>() { return 0; }
+template <> __device__ __forceinline__ Pair zero_of<Pair>() { return Pair{0, 0}; }
+
+// inputs of a scan: one array, or two arrays scanned together
+struct In1 {
+    const int32_t *a;
+    __device__ int32_t operator()(int64_t k) const { return a[k]; }
+};
+struct In2 {
+    const int32_t *a, *b;
+    __device__ Pair operator()(int64_t k) const { return Pair{a[k], b[k]}; }
+};
+struct Out1 {
+    int32_t *a;
+    __device__ void operator()(int64_t k, int32_t v) const { a[k] = v; }
+};
+struct Out2 {
+    int32_t *a, *b;
+    __device__ void operator()(int64_t k, Pair v) const {
+        a[k] = v.a;
+        b[k] = v.b;
+    }
+};
 
 // exclusive scan of the per-thread values of one block; returns the block total
-__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t &excl, int32_t *s_w) {
+template <class T>
+__device__ __forceinline__ T block_excl_scan(T v, T &excl, T *s_w) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t x = v;
+    T x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+        const T y = shfl_up(x, o);
+        if (lane >= o) x = x + y;
     }
     if (lane == 31) s_w[warp] = x;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int32_t acc = 0;
+        T acc = zero_of<T>();
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
-            const int32_t t = s_w[w];
+            const T t = s_w[w];
             s_w[w] = acc;
-            acc += t;
+            acc = acc + t;
         }
         s_w[32] = acc;
     }
     __syncthreads();
     excl = s_w[warp] + x - v;
-    const int32_t total = s_w[32];
+    const T total = s_w[32];
     __syncthreads();
     return total;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t *in, int64_t cnt, int32_t *tsum) {
-    __shared__ int32_t s_w[33];
+template <class T, class In>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(In in, int64_t cnt, T *tsum) {
+    __shared__ T s_w[33];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    int32_t v = 0;
+    T v = zero_of<T>();
     for (int t = threadIdx.x; t < kScanTile; t += kScanThreads) {
         const int64_t k = base + t;
-        if (k < cnt) v += in[k];
+        if (k < cnt) v = v + in(k);
     }
-    const int32_t tot = block_sum_i32(v, s_w);
+    T ex;
+    const T tot = block_excl_scan(v, ex, s_w);
     if (threadIdx.x == 0) tsum[blockIdx.x] = tot;
 }
 
 // one block: exclusive scan of tsum[0..ntiles) in place, tsum[ntiles] = out[cnt] = total
-__global__ void __launch_bounds__(1024) k_scan_top(int32_t *tsum, int32_t ntiles, int32_t *out, int64_t cnt) {
-    __shared__ int32_t s_w[33];
-    int32_t carry = 0;
+template <class T, class Out>
+__global__ void __launch_bounds__(1024) k_scan_top(T *tsum, int32_t ntiles, Out out, int64_t cnt) {
+    __shared__ T s_w[33];
+    T carry = zero_of<T>();
     for (int32_t b = 0; b < ntiles; b += 1024) {
         const int32_t k = b + threadIdx.x;
-        const int32_t v = k < ntiles ? tsum[k] : 0;
-        int32_t ex;
-        const int32_t tot = block_excl_scan(v, ex, s_w);
+        const T v = k < ntiles ? tsum[k] : zero_of<T>();
+        T ex;
+        const T tot = block_excl_scan(v, ex, s_w);
         if (k < ntiles) tsum[k] = carry + ex;
-        carry += tot;
+        carry = carry + tot;
     }
     if (threadIdx.x == 0) {
         tsum[ntiles] = carry;
-        out[cnt] = carry;
+        out(cnt, carry);
     }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(const int32_t *in, int32_t *out, int64_t cnt,
-                                                            const int32_t *tsum) {
-    __shared__ int32_t s_w[33];
+template <class T, class In, class Out>
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(In in, Out out, int64_t cnt, const T *tsum) {
+    __shared__ T s_w[33];
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kPerThread;
-    int32_t v[kPerThread];
-    int32_t s = 0;
+    T v[kPerThread];
+    T s = zero_of<T>();
 #pragma unroll
     for (int q = 0; q < kPerThread; q++) {
         const int64_t k = base + q;
-        v[q] = k < cnt ? in[k] : 0;
-        s += v[q];
+        v[q] = k < cnt ? in(k) : zero_of<T>();
+        s = s + v[q];
     }
-    int32_t ex;
+    T ex;
     block_excl_scan(s, ex, s_w);
-    int32_t run = tsum[blockIdx.x] + ex;
+    T run = tsum[blockIdx.x] + ex;
 #pragma unroll
     for (int q = 0; q < kPerThread; q++) {
         const int64_t k = base + q;
-        if (k < cnt) out[k] = run;
-        run += v[q];
+        if (k < cnt) out(k, run);
+        run = run + v[q];
     }
 }
 
 // --------------------------------------------------------------- binning
-__global__ void __launch_bounds__(kScanThreads) k_bin_hist(const int32_t *ptr, int32_t cnt, int32_t *hist,
-                                                           int32_t ntiles) {
+__global__ void __launch_bounds__(kScanThreads) k_bin_hist(const int32_t *ptr, const int32_t *cnt_dev,
+                                                           int32_t *hist, int32_t ntiles) {
     __shared__ int32_t s_h[kNumClass];
+    const int32_t cnt = *cnt_dev;
     if (threadIdx.x < kNumClass) s_h[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
@@ -117,9 +145,10 @@ __global__ void __launch_bounds__(kScanThreads) k_bin_hist(const int32_t *ptr, i
     if (threadIdx.x < kNumClass) hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = s_h[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_bin_scatter(const int32_t *ptr, int32_t cnt, const int32_t *off,
-                                                              int32_t ntiles, int32_t *order) {
+__global__ void __launch_bounds__(kScanThreads) k_bin_scatter(const int32_t *ptr, const int32_t *cnt_dev,
+                                                              const int32_t *off, int32_t ntiles, int32_t *order) {
     __shared__ int32_t s_run[kNumClass];
+    const int32_t cnt = *cnt_dev;
     __shared__ int32_t s_w[kScanThreads / 32][kNumClass];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -355,34 +384,41 @@ inline unsigned blocks_for(int64_t cnt, int threads) {
 }  // namespace
 
 // ================================================================= host side
-size_t scan_tmp_elems(int64_t cnt) { return (size_t)((cnt + kScanTile - 1) / kScanTile) + 1; }
+// int32 elements of scan temporary: room for pair tile sums
+size_t scan_tmp_elems(int64_t cnt) { return 2 * ((size_t)((cnt + kScanTile - 1) / kScanTile) + 1); }
 
 void scan_excl(const int32_t *in, int32_t *out, int64_t cnt, int32_t *tmp, cudaStream_t s) {
     const int32_t ntiles = (int32_t)((cnt + kScanTile - 1) / kScanTile);
-    if (ntiles > 0) k_scan_reduce<<<ntiles, kScanThreads, 0, s>>>(in, cnt, tmp);
-    k_scan_top<<<1, 1024, 0, s>>>(tmp, ntiles, out, cnt);
-    if (ntiles > 0) k_scan_down<<<ntiles, kScanThreads, 0, s>>>(in, out, cnt, tmp);
+    if (ntiles > 0) k_scan_reduce<int32_t><<<ntiles, kScanThreads, 0, s>>>(In1{in}, cnt, tmp);
+    k_scan_top<int32_t><<<1, 1024, 0, s>>>(tmp, ntiles, Out1{out}, cnt);
+    if (ntiles > 0) k_scan_down<int32_t><<<ntiles, kScanThreads, 0, s>>>(In1{in}, Out1{out}, cnt, tmp);
+}
+
+void scan_excl2(const int32_t *a, const int32_t *b, int32_t *oa, int32_t *ob, int64_t cnt, int32_t *tmp,
+                cudaStream_t s) {
+    const int32_t ntiles = (int32_t)((cnt + kScanTile - 1) / kScanTile);
+    Pair *t = reinterpret_cast<Pair *>(tmp);
+    if (ntiles > 0) k_scan_reduce<Pair><<<ntiles, kScanThreads, 0, s>>>(In2{a, b}, cnt, t);
+    k_scan_top<Pair><<<1, 1024, 0, s>>>(t, ntiles, Out2{oa, ob}, cnt);
+    if (ntiles > 0) k_scan_down<Pair><<<ntiles, kScanThreads, 0, s>>>(In2{a, b}, Out2{oa, ob}, cnt, t);
 }
 
 size_t sched_tile_hist_elems(int64_t cnt) {
-    return (size_t)kNumClass * (size_t)((cnt + kScanTile - 1) / kScanTile) + 1;
+    return (size_t)kNumClass * (size_t)std::max<int64_t>(1, (cnt + kScanTile - 1) / kScanTile) + 1;
 }
 
 int32_t sched_cap_long(int64_t nnz) { return (int32_t)std::max<int64_t>(1, nnz / kLongMin); }
 
-void build_schedule(const int32_t *ptr, int32_t cnt, int64_t nnz, const SchedBufs &b, int32_t *cls_out,
-                    int32_t *nchunk_out, cudaStream_t s) {
-    const int32_t ntiles = (int32_t)((cnt + kScanTile - 1) / kScanTile);
-    if (ntiles > 0) k_bin_hist<<<ntiles, kScanThreads, 0, s>>>(ptr, cnt, b.tile_hist, ntiles);
+void build_schedule(const int32_t *ptr, const int32_t *cnt_dev, int32_t cnt_max, int64_t nnz_max,
+                    const SchedBufs &b, int32_t *cls_out, int32_t *nchunk_out, cudaStream_t s) {
+    // tiles cover cnt_max segments; tiles past the actual count hold zeros
+    const int32_t ntiles = std::max<int32_t>(1, (int32_t)((cnt_max + kScanTile - 1) / kScanTile));
+    k_bin_hist<<<ntiles, kScanThreads, 0, s>>>(ptr, cnt_dev, b.tile_hist, ntiles);
     scan_excl(b.tile_hist, b.tile_hist, (int64_t)kNumClass * ntiles, b.tmp, s);
-    if (ntiles > 0) {
-        k_bin_scatter<<<ntiles, kScanThreads, 0, s>>>(ptr, cnt, b.tile_hist, ntiles, b.order);
-        k_bin_finish<<<1, 32, 0, s>>>(b.tile_hist, ntiles, cls_out);
-    } else {
-        cudaMemsetAsync(cls_out, 0, sizeof(int32_t) * kNumClass, s);
-    }
+    k_bin_scatter<<<ntiles, kScanThreads, 0, s>>>(ptr, cnt_dev, b.tile_hist, ntiles, b.order);
+    k_bin_finish<<<1, 32, 0, s>>>(b.tile_hist, ntiles, cls_out);
     // chunks of the long segments: at most nnz / kLongMin of them
-    const int32_t cap_long = sched_cap_long(nnz);
+    const int32_t cap_long = sched_cap_long(nnz_max);
     k_chunk_count<<<blocks_for(cap_long, 256), 256, 0, s>>>(ptr, b.order, b.tile_hist, ntiles, cls_out, cap_long,
                                                              b.nch);
     scan_excl(b.nch, b.lfirst, cap_long, b.tmp, s);

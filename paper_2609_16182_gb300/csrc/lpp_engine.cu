@@ -435,16 +435,23 @@ void Engine::prepare() {
     n = n0;
     nnz = nnz0;
     cur = 0;
-    A.ptr = rp[0];
+    k_set_i32<<<1, 1, 0, s>>>(&st->m_new, m0);
+    k_set_i32<<<1, 1, 0, s>>>(&st->n_new, n0);
     schedule_current();
-    LPP_CUDA(cudaStreamSynchronize(s));  // offs outlives its copy
+    read_status();  // also keeps offs alive until its copy is done
+    adopt_schedule();
 }
 
+// Launches the schedule builds of the current CSR and CSC; the segment
+// counts are read from st->m_new / st->n_new on the device (m, n bound them).
 void Engine::schedule_current() {
-    build_schedule(rp[cur], m, nnz, sa, st->cls_r, &st->nchunk_r, s);
-    build_schedule(tp[cur], n, nnz, sb, st->cls_c, &st->nchunk_c, s);
+    build_schedule(rp[cur], &st->m_new, m, nnz, sa, st->cls_r, &st->nchunk_r, s);
+    build_schedule(tp[cur], &st->n_new, n, nnz, sb, st->cls_c, &st->nchunk_c, s);
     LPP_CUDA(cudaGetLastError());
-    read_status();
+}
+
+// After read_status(): the host copies of the current schedules.
+void Engine::adopt_schedule() {
     A.ptr = rp[cur];
     A.idx = ci[cur];
     A.val = rv[cur];
@@ -555,26 +562,18 @@ void Engine::compact(int32_t round) {
     launch_compact_counts(C, K, s);
     tend();
     tbegin(F_SCAN, 16.0 * (m + n) * 2);
-    scan_excl(K.r_keep, K.r_pos, m, scan_tmp, s);
-    scan_excl(K.r_len, K.r_off, m, scan_tmp, s);
-    scan_excl(K.c_keep, K.c_pos, n, scan_tmp, s);
-    scan_excl(K.c_len, K.c_off, n, scan_tmp, s);
+    scan_excl2(K.r_keep, K.r_len, K.r_pos, K.r_off, m, scan_tmp, s);
+    scan_excl2(K.c_keep, K.c_len, K.c_pos, K.c_off, n, scan_tmp, s);
     tend();
     launch_offset(C, K, s);
     k_sizes<<<1, 1, 0, s>>>(K, m, n, st);
-    LPP_CUDA(cudaGetLastError());
-    read_status();
-    const int32_t m_new = st_h->m_new, n_new = st_h->n_new, nnz_new = st_h->nnz_new;
-    if (nnz_new != st_h->nnz_new_t || m_new < 0 || m_new > m || n_new < 0 || n_new > n || nnz_new > nnz)
-        throw StatusError(LPP_ERR_CUDA, "internal: compaction sizes disagree");
-    tbegin(F_SCATTER, 24.0 * nnz + 24.0 * nnz_new * 2 / 2 + 48.0 * (m + n));
-    launch_compact_scatter(C, K, m_new, n_new, s);
+    tbegin(F_SCATTER, 24.0 * nnz * 2 + 48.0 * (m + n));
+    launch_compact_scatter(C, K, 0, 0, s);
     tend();
     LPP_CUDA(cudaGetLastError());
+    // the next buffers become current; sizes and schedules are read back at
+    // the end of the round (one host sync per round)
     cur = nx;
-    m = m_new;
-    n = n_new;
-    nnz = nnz_new;
     tbegin(F_SCHED, 8.0 * (m + n));
     schedule_current();
     tend();
@@ -659,6 +658,15 @@ void Engine::run() {
         else std::swap(rdirty[cur], rdnext);  // same numbering: next round's flags
         LPP_CUDA(cudaEventRecord(e1, s));
         read_status();
+        if (structural) {
+            const int32_t m_new = st_h->m_new, n_new = st_h->n_new, nnz_new = st_h->nnz_new;
+            if (nnz_new != st_h->nnz_new_t || m_new < 0 || m_new > m || n_new < 0 || n_new > n || nnz_new > nnz)
+                throw StatusError(LPP_ERR_CUDA, "internal: compaction sizes disagree");
+            m = m_new;
+            n = n_new;
+            nnz = nnz_new;
+            adopt_schedule();
+        }
         float ms = 0.f;
         LPP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         r_ms.push_back(ms);

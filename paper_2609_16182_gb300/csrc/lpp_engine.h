@@ -133,6 +133,7 @@ struct Engine {
     Ctx ctx(int32_t round) const;
     void read_status();
     void schedule_current();
+    void adopt_schedule();
     void compact(int32_t round);
     // timing helpers
     void tbegin(int fam, double bytes);

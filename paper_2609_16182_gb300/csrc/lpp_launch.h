@@ -11,6 +11,9 @@ namespace lpp {
 // must hold scan_tmp_elems(cnt) int32 values.  in == out is allowed.
 size_t scan_tmp_elems(int64_t cnt);
 void scan_excl(const int32_t *in, int32_t *out, int64_t cnt, int32_t *tmp, cudaStream_t s);
+// two exclusive scans in one pass (oa[cnt], ob[cnt] = totals)
+void scan_excl2(const int32_t *a, const int32_t *b, int32_t *oa, int32_t *ob, int64_t cnt, int32_t *tmp,
+                cudaStream_t s);
 
 // Schedule (class lists + chunks) of a segmented matrix with ptr[cnt+1].
 struct SchedBufs {
@@ -27,8 +30,8 @@ int32_t sched_cap_long(int64_t nnz);
 // Builds the schedule and writes the class sizes to cls_out[7] and the chunk
 // count to *nchunk_out (device addresses inside DevStatus).  Chunks need at
 // most nnz / kChunk + cap_long entries.
-void build_schedule(const int32_t *ptr, int32_t cnt, int64_t nnz, const SchedBufs &b, int32_t *cls_out,
-                    int32_t *nchunk_out, cudaStream_t s);
+void build_schedule(const int32_t *ptr, const int32_t *cnt_dev, int32_t cnt_max, int64_t nnz_max,
+                    const SchedBufs &b, int32_t *cls_out, int32_t *nchunk_out, cudaStream_t s);
 // Fill the host-side part of a SegMat from class sizes read back.
 void segmat_from_counts(SegMat &M, const int32_t cls[kNumClass], int32_t nchunks);
 GroupGrid group_grid(const SegMat &M);
