@@ -49,7 +49,7 @@ def test_batch_members_equal_their_solo_runs_and_the_oracle():
         same_result(r, lpp.presolve(lp))
         o = oracle.presolve(lp)
         if o.audit_below_1e3 == 0:
-            compare(r, o, lp)
+            compare(r, o, lp, arena_stats=True)
 
 
 def test_infeasible_member_leaves_the_others_alone():
