@@ -21,13 +21,11 @@ namespace lpp {
 
 namespace {
 
-__device__ __forceinline__ int32_t lp_of_row(const Ctx &C, int32_t i) { return C.lp_row ? C.lp_row[i] : 0; }
-__device__ __forceinline__ int32_t lp_of_col(const Ctx &C, int32_t j) { return C.lp_col ? C.lp_col[j] : 0; }
 
 __global__ void k_lp_dead(Ctx C, CompactCtx K) {
     const int32_t lp = blockIdx.x * blockDim.x + threadIdx.x;
     if (lp >= C.nlp) return;
-    bool d = false;
+    bool d = K.lp_retired ? K.lp_retired[lp] != 0 : false;
     for (int v = 0; v < V_SLOTS; v++) d |= C.verdict[lp * V_SLOTS + v] != kNone;
     K.lp_dead[lp] = d;
 }
@@ -133,7 +131,7 @@ __global__ void __launch_bounds__(kBlock) k_colkeep(Ctx C, CompactCtx K) {
                 C.fixv[j] = v;
                 const int32_t o = C.cmap[j];
                 C.rec_ck[o] = CK_EMPTY;
-                C.rec_cr[o] = C.round;
+                C.rec_cr[o] = lp_round(C, lp);
                 C.rec_cv[o] = v;
                 C.lp_changed[lp] = 1;
                 fixed = 1;

@@ -28,8 +28,6 @@ namespace {
 __device__ __forceinline__ double pinf() { return __longlong_as_double(0x7ff0000000000000LL); }
 __device__ __forceinline__ double ninf_() { return __longlong_as_double((long long)0xfff0000000000000ULL); }
 
-__device__ __forceinline__ int32_t lp_of_row(const Ctx &C, int32_t i) { return C.lp_row ? C.lp_row[i] : 0; }
-__device__ __forceinline__ int32_t lp_of_col(const Ctx &C, int32_t j) { return C.lp_col ? C.lp_col[j] : 0; }
 
 // Implied upper bound x/a on column j (from a*x_j <= x with a > 0, or
 // a*x_j >= x with a < 0).  Accepted iff (uold = +inf or x/a < thr) and
@@ -110,10 +108,6 @@ __device__ __forceinline__ bool classify(const Ctx &C, double Lv, double Uv, int
     return true;
 }
 
-__device__ __forceinline__ int32_t lp_round(const Ctx &C, int32_t lp) {
-    (void)lp;
-    return C.round;
-}
 
 // writes the row's S1/S2 results and records; applies a singleton row as a bound
 __device__ __forceinline__ int32_t finish_row(const Ctx &C, int32_t i, int32_t beg, int32_t len, double Lv,
@@ -344,7 +338,8 @@ __global__ void __launch_bounds__(kBlock) k_colfin(Ctx C) {
         const bool has = el != kEncNegInf || eu != kEncPosInf;
         uint8_t kind = CK_KEPT;
         uint8_t chg = 0;
-        if (has || C.round == 1) {
+        const int32_t lpj = lp_of_col(C, j);
+        if (has || lp_round(C, lpj) == 1) {
             if (has) {
                 C.cand_l[j] = kEncNegInf;
                 C.cand_u[j] = kEncPosInf;
@@ -367,7 +362,7 @@ __global__ void __launch_bounds__(kBlock) k_colfin(Ctx C) {
                     nu = mid;
                 }
             }
-            const int32_t lp = lp_of_col(C, j);
+            const int32_t lp = lpj;
             if (bad) {
                 atomicMin(&C.verdict[lp * V_SLOTS + V_S3_COL], C.cmap[j]);
             } else {

@@ -114,6 +114,7 @@ struct Ctx {
     int32_t *rec_ck, *rec_cr;
     double *rec_cv;
     // per LP
+    const int32_t *lp_round0;       // arena round in which each LP joined (NULL: all in round 1)
     int32_t *verdict;               // [nlp][V_SLOTS] smallest original index
     uint8_t *lp_changed;            // [nlp]
     DevStatus *st;
@@ -133,7 +134,8 @@ struct CompactCtx {
     double *offset;                            // [nlp] objective constant
     double *offset_part;                       // two-level sum partials
     int32_t *lp_first, *lp_last;               // [nlp] current column range of each LP
-    uint8_t *lp_dead;                          // [nlp] a verdict was reached
+    uint8_t *lp_dead;                          // [nlp] a verdict was reached, or retired
+    const uint8_t *lp_retired;                 // [nlp] finished LPs leaving the arena (NULL: none)
     // next buffers
     int32_t *rp2, *ci2;
     double *rv2;
@@ -228,6 +230,13 @@ __device__ __forceinline__ void block_add(int32_t v, int32_t *dst) {
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_acc, v);
     __syncthreads();
     if (threadIdx.x == 0 && s_acc) atomicAdd(dst, s_acc);
+}
+
+__device__ __forceinline__ int32_t lp_of_row(const Ctx &C, int32_t i) { return C.lp_row ? C.lp_row[i] : 0; }
+__device__ __forceinline__ int32_t lp_of_col(const Ctx &C, int32_t j) { return C.lp_col ? C.lp_col[j] : 0; }
+// round number of an LP (1 in the arena round in which it joined)
+__device__ __forceinline__ int32_t lp_round(const Ctx &C, int32_t lp) {
+    return C.lp_round0 ? C.round - C.lp_round0[lp] + 1 : C.round;
 }
 
 // Which class / block-in-class a block of a group launch serves.

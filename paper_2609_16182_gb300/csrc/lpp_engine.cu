@@ -156,6 +156,8 @@ Engine::~Engine() {
         cudaEventDestroy(mk.b);
     }
     for (auto e : spare_events) cudaEventDestroy(e);
+    for (auto e : ev_round)
+        if (e) cudaEventDestroy(e);
     pool.release();
     if (s) cudaStreamSynchronize(s);
     pinned_put(st_h);
@@ -526,6 +528,7 @@ Ctx Engine::ctx(int32_t round) const {
     C.rec_ck = rec_ck;
     C.rec_cr = rec_cr;
     C.rec_cv = rec_cv;
+    C.lp_round0 = lp_round0_dev;
     C.verdict = verdict;
     C.lp_changed = lp_changed;
     C.st = st;
@@ -579,6 +582,93 @@ void Engine::compact(int32_t round) {
     tend();
 }
 
+// One round (S1 .. S8) over the whole arena.  first_round: some LP is in
+// its first round (S6 must then run on its input columns); force: compact even
+// if nothing was removed (to drop retired LPs).
+Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
+    StepOut out;
+    if (!ev_round[0]) {
+        LPP_CUDA(cudaEventCreate(&ev_round[0]));
+        LPP_CUDA(cudaEventCreate(&ev_round[1]));
+    }
+    act_m = m;
+    act_buf = cur;
+    r_nnz.push_back(nnz);
+    nnz_processed += nnz;
+    LPP_CUDA(cudaEventRecord(ev_round[0], s));
+    LPP_CUDA(cudaMemsetAsync(st, 0, 8 * sizeof(int32_t), s));
+    LPP_CUDA(cudaMemsetAsync(lp_changed, 0, (size_t)nlp, s));
+    if (m > 0) LPP_CUDA(cudaMemsetAsync(rdnext, 0, (size_t)m, s));
+    Ctx C = ctx(r);
+    tbegin(F_PROP, 0.0);  // bytes and ops set once the evaluated nonzeros are known
+    const size_t prop_mark = marks.size();
+    launch_prop(C, s);
+    tend();
+    tbegin(F_COLFIN, 33.0 * n);
+    launch_colfin(C, s);
+    launch_mark_dirty(C, s);
+    tend();
+    LPP_CUDA(cudaGetLastError());
+    // S5: leader passes
+    int32_t tcap = std::min(tcap_max, pow2_at_least(2 * (int64_t)std::max(m, 1)));
+    tbegin(F_S5, 16.0 * tcap + 12.0 * m);
+    LPP_CUDA(cudaMemsetAsync(tkey, 0, sizeof(unsigned long long) * tcap, s));
+    LPP_CUDA(cudaMemsetAsync(tlead, 0xff, sizeof(unsigned long long) * tcap, s));
+    C.tcap = tcap;
+    launch_s5_pass(C, 0, s);
+    tend();
+    LPP_CUDA(cudaGetLastError());
+    read_status();
+    r_eval.push_back(st_h->nnz_eval);
+    if (o.timing && prop_mark > 0) {
+        // S1 algorithmic work: per evaluated nonzero its 12 bytes and two FMAs,
+        // per row ptr, sides, results (4 + 16 + 33 bytes), the bounds once
+        Tmark &pm = marks[prop_mark - 1];
+        pm.bytes = 12.0 * st_h->nnz_eval + 53.0 * m + 16.0 * n;
+        pm.ops = 2.0 * st_h->nnz_eval;
+    }
+    for (int pass = 1; st_h->unmatched > 0 && pass < o.par_max_iter; pass++) {
+        tcap = std::min(tcap_max, pow2_at_least(2 * (int64_t)st_h->unmatched));
+        LPP_CUDA(cudaMemsetAsync(tkey, 0, sizeof(unsigned long long) * tcap, s));
+        LPP_CUDA(cudaMemsetAsync(tlead, 0xff, sizeof(unsigned long long) * tcap, s));
+        LPP_CUDA(cudaMemsetAsync(&st->unmatched, 0, sizeof(int32_t), s));
+        C.tcap = tcap;
+        launch_s5_pass(C, pass, s);
+        LPP_CUDA(cudaGetLastError());
+        read_status();
+    }
+    if (st_h->err) throw StatusError(LPP_ERR_CUDA, "internal: S5 hash table overflow");
+    launch_s5_leader(C, s);
+    LPP_CUDA(cudaGetLastError());
+    bool newly_dead = false;
+    for (int32_t k = 0; k < nlp; k++) {
+        if (lp_dropped[k]) continue;
+        for (int v = 0; v < V_SLOTS; v++) newly_dead |= verdict_h[k * V_SLOTS + v] != kNone;
+    }
+    out.structural = first_round || force || st_h->rows_removed > 0 || st_h->cols_fixed > 0 || newly_dead;
+    const int32_t rows_removed = st_h->rows_removed, bounds = st_h->bounds_changed;
+    if (out.structural) compact(r);
+    else std::swap(rdirty[cur], rdnext);  // same numbering: next round's flags
+    LPP_CUDA(cudaEventRecord(ev_round[1], s));
+    read_status();
+    if (out.structural) {
+        const int32_t m_new = st_h->m_new, n_new = st_h->n_new, nnz_new = st_h->nnz_new;
+        if (nnz_new != st_h->nnz_new_t || m_new < 0 || m_new > m || n_new < 0 || n_new > n || nnz_new > nnz)
+            throw StatusError(LPP_ERR_CUDA, "internal: compaction sizes disagree");
+        m = m_new;
+        n = n_new;
+        nnz = nnz_new;
+        adopt_schedule();
+    }
+    LPP_CUDA(cudaEventElapsedTime(&out.ms, ev_round[0], ev_round[1]));
+    r_ms.push_back(out.ms);
+    r_rows.push_back(rows_removed);
+    r_cols.push_back(st_h->cols_fixed);
+    r_bounds.push_back(bounds);
+    rounds = r;
+    return out;
+}
+
 void Engine::run() {
     const int32_t R = std::max(0, o.max_rounds);
     lp_rounds.assign(nlp, 0);
@@ -587,96 +677,19 @@ void Engine::run() {
     lp_index.assign(nlp, -1);
     lp_round.assign(nlp, 0);
     lp_done.assign(nlp, 0);
-    std::vector<uint8_t> dropped(nlp, 0);
-    cudaEvent_t e0, e1, eloop;
-    LPP_CUDA(cudaEventCreate(&e0));
-    LPP_CUDA(cudaEventCreate(&e1));
+    lp_dropped.assign(nlp, 0);
+    cudaEvent_t eloop, eend;
     LPP_CUDA(cudaEventCreate(&eloop));
-    spare_events.push_back(e0);
-    spare_events.push_back(e1);
+    LPP_CUDA(cudaEventCreate(&eend));
     spare_events.push_back(eloop);
+    spare_events.push_back(eend);
     LPP_CUDA(cudaEventRecord(eloop, s));
     int32_t live = nlp;
     for (int32_t r = 1; r <= R && live > 0; r++) {
-        act_m = m;
-        act_buf = cur;
-        r_nnz.push_back(nnz);
-        nnz_processed += nnz;
-        LPP_CUDA(cudaEventRecord(e0, s));
-        LPP_CUDA(cudaMemsetAsync(st, 0, 8 * sizeof(int32_t), s));
-        LPP_CUDA(cudaMemsetAsync(lp_changed, 0, (size_t)nlp, s));
-        if (m > 0) LPP_CUDA(cudaMemsetAsync(rdnext, 0, (size_t)m, s));
-        Ctx C = ctx(r);
-        tbegin(F_PROP, 0.0);  // bytes and ops set once the evaluated nonzeros are known
-        const size_t prop_mark = marks.size();
-        launch_prop(C, s);
-        tend();
-        tbegin(F_COLFIN, 33.0 * n);
-        launch_colfin(C, s);
-        launch_mark_dirty(C, s);
-        tend();
-        LPP_CUDA(cudaGetLastError());
-        // S5: leader passes
-        int32_t tcap = std::min(tcap_max, pow2_at_least(2 * (int64_t)std::max(m, 1)));
-        tbegin(F_S5, 16.0 * tcap + 12.0 * m);
-        LPP_CUDA(cudaMemsetAsync(tkey, 0, sizeof(unsigned long long) * tcap, s));
-        LPP_CUDA(cudaMemsetAsync(tlead, 0xff, sizeof(unsigned long long) * tcap, s));
-        C.tcap = tcap;
-        launch_s5_pass(C, 0, s);
-        tend();
-        LPP_CUDA(cudaGetLastError());
-        read_status();
-        r_eval.push_back(st_h->nnz_eval);
-        if (o.timing && prop_mark > 0) {
-            // S1 algorithmic work: per evaluated nonzero its 12 bytes and two FMAs,
-            // per row ptr, sides, results (4 + 16 + 33 bytes), the bounds once
-            Tmark &pm = marks[prop_mark - 1];
-            pm.bytes = 12.0 * st_h->nnz_eval + 53.0 * m + 16.0 * n;
-            pm.ops = 2.0 * st_h->nnz_eval;
-        }
-        for (int pass = 1; st_h->unmatched > 0 && pass < o.par_max_iter; pass++) {
-            tcap = std::min(tcap_max, pow2_at_least(2 * (int64_t)st_h->unmatched));
-            LPP_CUDA(cudaMemsetAsync(tkey, 0, sizeof(unsigned long long) * tcap, s));
-            LPP_CUDA(cudaMemsetAsync(tlead, 0xff, sizeof(unsigned long long) * tcap, s));
-            LPP_CUDA(cudaMemsetAsync(&st->unmatched, 0, sizeof(int32_t), s));
-            C.tcap = tcap;
-            launch_s5_pass(C, pass, s);
-            LPP_CUDA(cudaGetLastError());
-            read_status();
-        }
-        if (st_h->err) throw StatusError(LPP_ERR_CUDA, "internal: S5 hash table overflow");
-        launch_s5_leader(C, s);
-        LPP_CUDA(cudaGetLastError());
-        bool newly_dead = false;
-        for (int32_t k = 0; k < nlp; k++) {
-            if (dropped[k]) continue;
-            for (int v = 0; v < V_SLOTS; v++) newly_dead |= verdict_h[k * V_SLOTS + v] != kNone;
-        }
-        const bool structural = r == 1 || st_h->rows_removed > 0 || st_h->cols_fixed > 0 || newly_dead;
-        int32_t rows_removed = st_h->rows_removed, bounds = st_h->bounds_changed;
-        if (structural) compact(r);
-        else std::swap(rdirty[cur], rdnext);  // same numbering: next round's flags
-        LPP_CUDA(cudaEventRecord(e1, s));
-        read_status();
-        if (structural) {
-            const int32_t m_new = st_h->m_new, n_new = st_h->n_new, nnz_new = st_h->nnz_new;
-            if (nnz_new != st_h->nnz_new_t || m_new < 0 || m_new > m || n_new < 0 || n_new > n || nnz_new > nnz)
-                throw StatusError(LPP_ERR_CUDA, "internal: compaction sizes disagree");
-            m = m_new;
-            n = n_new;
-            nnz = nnz_new;
-            adopt_schedule();
-        }
-        float ms = 0.f;
-        LPP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        r_ms.push_back(ms);
-        r_rows.push_back(rows_removed);
-        r_cols.push_back(st_h->cols_fixed);
-        r_bounds.push_back(bounds);
-        rounds = r;
+        const StepOut so = step(r, r == 1, false);
         for (int32_t k = 0; k < nlp; k++) {
             if (lp_done[k]) {
-                if (structural && lp_status[k] != LPP_OK) dropped[k] = 1;
+                if (so.structural && lp_status[k] != LPP_OK) lp_dropped[k] = 1;
                 continue;
             }
             int v = 0;
@@ -688,7 +701,7 @@ void Engine::run() {
                 lp_round[k] = r;
                 lp_rounds[k] = r;
                 lp_done[k] = 1;
-                if (structural) dropped[k] = 1;
+                if (so.structural) lp_dropped[k] = 1;
                 live--;
             } else if (!changed_h[k]) {
                 lp_rounds[k] = r;
@@ -700,12 +713,17 @@ void Engine::run() {
         }
     }
     float lms = 0.f;
-    LPP_CUDA(cudaEventRecord(e1, s));
-    LPP_CUDA(cudaEventSynchronize(e1));
-    LPP_CUDA(cudaEventElapsedTime(&lms, eloop, e1));
+    LPP_CUDA(cudaEventRecord(eend, s));
+    LPP_CUDA(cudaEventSynchronize(eend));
+    LPP_CUDA(cudaEventElapsedTime(&lms, eloop, eend));
     loop_ms = lms;
 }
 
 const char *fam_name(int f) { return kFamNames[f]; }
+
+void Engine::k_sizes_set(int32_t m_, int32_t n_) {
+    k_set_i32<<<1, 1, 0, s>>>(&st->m_new, m_);
+    k_set_i32<<<1, 1, 0, s>>>(&st->n_new, n_);
+}
 
 }  // namespace lpp

@@ -130,6 +130,20 @@ struct Engine {
     void ingest_batch(const lpp_lp *ins, int32_t count);
     void prepare();  // after ingest: transpose, schedules, work init
     void run();      // the round loop
+    struct StepOut {
+        bool structural = false;
+        float ms = 0.f;
+    };
+    StepOut step(int32_t r, bool first_round, bool force);
+    // serving: an empty arena that LPs join and leave between rounds
+    int32_t *lp_round0_dev = nullptr;
+    uint8_t *lp_retired_dev = nullptr;
+    void init_empty();
+    void append(int32_t slot, const lpp_lp &in, int32_t rbase, int32_t cbase, int32_t round0);
+    void reschedule();
+    void k_sizes_set(int32_t m_, int32_t n_);
+    cudaEvent_t ev_round[2] = {nullptr, nullptr};
+    std::vector<uint8_t> lp_dropped;
     Ctx ctx(int32_t round) const;
     void read_status();
     void schedule_current();

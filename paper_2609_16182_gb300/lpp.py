@@ -362,3 +362,50 @@ def presolve_batch(lps, options: Opts | None = None, **kw) -> list[Result]:
     per = (C.c_int32 * max(cnt, 1))()
     _check(L.lpp_presolve_batch(arr, cnt, C.byref(o), reds, recs, per))
     return [Result(reds[k], recs[k]) for k in range(cnt)]
+
+
+class Server:
+    """lpp_server_*: a continuous-batching presolve server on one GPU."""
+
+    def __init__(self, hbm_budget: int, options: Opts | None = None, **kw):
+        L = load()
+        o = options if options is not None else opts(**kw)
+        h = C.c_void_p()
+        _check(L.lpp_server_create(C.c_size_t(int(hbm_budget)), C.byref(o), C.byref(h)))
+        self._h = h.value
+        self._keep = {}
+
+    def submit(self, lp) -> int:
+        keep = []
+        s = lp_struct(lp, keep)
+        t = C.c_uint64(0)
+        _check(load().lpp_server_submit(self._h, C.byref(s), C.byref(t)))
+        return t.value
+
+    def take(self, ticket: int, wait_ms: int = -1) -> Result:
+        red, rec = C.c_void_p(), C.c_void_p()
+        st = load().lpp_server_take(self._h, C.c_uint64(ticket), int(wait_ms), C.byref(red), C.byref(rec))
+        _check(st)
+        return Result(red.value, rec.value)
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(load().lpp_server_stats_get(self._h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            load().lpp_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
