@@ -113,7 +113,7 @@ __global__ void k_extract(ExtractArgs a) {
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t step = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = t0; i <= a.mr; i += step) {
-        a.o_rp[i] = a.rp[a.r0 + i] - a.z0;
+        a.o_rp[i] = a.rp[a.r0 + i] - a.rp[a.r0];
         if (i < a.mr) {
             a.o_L[i] = a.L[a.r0 + i];
             a.o_U[i] = a.U[a.r0 + i];
@@ -121,7 +121,7 @@ __global__ void k_extract(ExtractArgs a) {
         }
     }
     for (int64_t j = t0; j <= a.nc; j += step) {
-        a.o_tp[j] = a.tp[a.c0 + j] - a.z0;
+        a.o_tp[j] = a.tp[a.c0 + j] - a.tp[a.c0];
         if (j < a.nc) {
             const double2 b = a.lu[a.c0 + j];
             a.o_lb[j] = b.x;
