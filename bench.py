@@ -93,6 +93,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+def reduce_over_ranks(ms_total: float, nnz_proc: int, device, world_size: int):
+    """Whole-job throughput of independent replicas: the slowest rank's time
+    and the nonzeros of all ranks (weak scaling, no data-path collective)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_total], device=device, dtype=torch.float64)
+    tot = torch.tensor([float(nnz_proc)], device=device, dtype=torch.float64)
+    if world_size > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    return ms_max, float(tot.item()) / (ms_max / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -153,6 +167,91 @@ def batched_leg(lpp, synth, torch, dev, stream, count=4096):
                         "200-row LP scaled by m/200; device inputs; one batched call vs 4096 plain calls"}
 
 
+def serving_leg(lpp, synth, torch, dev, pool_size=24, requests=200, budget=120 << 30, seed=0):
+    """Poisson arrivals of skewed-like LPs (nnz log-uniform in [1e3, 1e6],
+    m = nnz/10, n = 1.5 m; requests draw from a pool of `pool_size` distinct
+    LPs), replayed in real time at 0.5x, 0.8x and 1.2x the serial capacity:
+    the continuous-batching server against a serial loop of lpp_presolve on
+    the same arrivals.  Latency = completion - arrival."""
+    import threading
+    rng = np.random.default_rng(seed)
+    nnz = np.exp(rng.uniform(np.log(1e3), np.log(1e6), pool_size)).astype(int)
+    pool = [synth.skewed_like(seed * 1_000_003 + k, int(z)) for k, z in enumerate(nnz)]
+    dpool = [synth.LP(m=lp.m, n=lp.n, **{k: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
+                                         for k, v in lp.arrays().items()}) for lp in pool]
+    # serial service time of each pool LP
+    for x in dpool[:4]:
+        lpp.presolve(x).close()
+    svc = []
+    for x in dpool:
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        lpp.presolve(x).close()
+        svc.append(time.perf_counter() - t0)
+    mean_svc = float(np.mean(svc))
+    out = {"pool": pool_size, "requests": requests, "budget_bytes": budget, "serial_capacity_lps": 1.0 / mean_svc,
+           "pool_nnz_mean": float(np.mean([lp.nnz for lp in pool])), "rates": []}
+
+    def pct(a, q):
+        return float(np.percentile(np.asarray(a) * 1e3, q))
+
+    srv = lpp.Server(budget)
+    try:
+        for f in (0.5, 0.8, 1.2):
+            lam = f / mean_svc
+            arr = np.cumsum(rng.exponential(1.0 / lam, requests))
+            pick = rng.integers(0, pool_size, requests)
+            # serial loop on the same arrivals
+            t0 = time.perf_counter()
+            lat_s, last = [], 0.0
+            for k in range(requests):
+                while time.perf_counter() - t0 < arr[k]:
+                    pass
+                lpp.presolve(dpool[pick[k]]).close()
+                last = time.perf_counter() - t0
+                lat_s.append(last - arr[k])
+            serial_span = last
+            # the server
+            tickets = [None] * requests
+            done_at = [0.0] * requests
+            t0 = time.perf_counter()
+
+            def submitter():
+                for k in range(requests):
+                    while time.perf_counter() - t0 < arr[k]:
+                        time.sleep(0.00005)
+                    tickets[k] = srv.submit(dpool[pick[k]])
+
+            th = threading.Thread(target=submitter)
+            th.start()
+            left = set(range(requests))
+            while left:
+                for k in list(left):
+                    if tickets[k] is None:
+                        continue
+                    try:
+                        r = srv.take(tickets[k], 0)
+                    except lpp.LppError as e:
+                        if e.status == lpp.ERR_TIMEOUT:
+                            continue
+                        raise
+                    done_at[k] = time.perf_counter() - t0
+                    r.close()
+                    left.discard(k)
+                time.sleep(0.0002)
+            th.join()
+            lat = [done_at[k] - arr[k] for k in range(requests)]
+            span = max(done_at)
+            out["rates"].append({"load": f, "arrival_lps": lam,
+                                 "served_lps": requests / span, "served_p50_ms": pct(lat, 50),
+                                 "served_p99_ms": pct(lat, 99), "serial_lps": requests / serial_span,
+                                 "serial_p50_ms": pct(lat_s, 50), "serial_p99_ms": pct(lat_s, 99)})
+        out["server_stats"] = srv.stats()
+    finally:
+        srv.close()
+    return out
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle as the reference arm."""
     ws, rank, _ = dist_env()
@@ -189,6 +288,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-presolve leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the LP (profiling runs only)")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: W + K steps only (no timing pass, e2e or CPU baseline)")
@@ -251,13 +351,7 @@ def main():
     round_nnz = [int(x) for x in first.round_nnz]
     for r in results:
         r.close()
-    t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-    tot = torch.tensor([float(nnz_proc)], device=dev, dtype=torch.float64)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    value = float(tot.item()) / (ms_max / 1e3)
+    ms_max, value = reduce_over_ranks(ms_total, nnz_proc, dev, ws)
 
     # per-kernel times: one more step with CUDA events around every launch family
     rt = lpp.presolve(d_lp, o_time)
@@ -315,6 +409,9 @@ def main():
     batched = None
     if not args.no_batch:
         batched = batched_leg(lpp, synth, torch, dev, stream)
+    serving = None
+    if not args.no_serve:
+        serving = serving_leg(lpp, synth, torch, dev)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": ws, "steps": args.steps,
@@ -330,7 +427,7 @@ def main():
                            "l2": "inputs larger than L2 (CSR alone ~245 MB > 129 MB)",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "e2e": e2e, "gpu_launches": None, "clocks": clk.summary(),
-                "batched": batched}
+                "batched": batched, "serving": serving}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

@@ -73,7 +73,7 @@ def test_server_device_inputs_infeasible_member_and_timeout():
 
 def test_server_rejects_what_cannot_fit():
     with lpp.Server(8 << 20) as srv:
-        big = synth.mix(1, m=3000, n=4500)
+        big = synth.mix(1, m=40_000, n=60_000)  # more rows than 8 MiB of arena holds
         with pytest.raises(lpp.LppError) as e:
             srv.submit(big)
         assert e.value.status == lpp.ERR_BUDGET
