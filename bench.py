@@ -328,6 +328,7 @@ def main():
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     nnz_proc = 0
+    launches = 0
     rounds = None
     results = []
     with ClockSampler(local) as clk:
@@ -336,6 +337,7 @@ def main():
         for _ in range(args.steps):
             r = lpp.presolve(d_lp, o_dev)
             nnz_proc += int(r.info.nnz_processed)
+            launches += int(r.info.launches)
             rounds = r.rounds
             results.append(r)
         ev1.record(stream)
@@ -426,7 +428,7 @@ def main():
                                        "nnz_ratio": info.nnz_red / max(1, info.nnz)},
                            "l2": "inputs larger than L2 (CSR alone ~245 MB > 129 MB)",
                            "parallelism": f"replicas x{ws}"},
-                "roofline": roofline, "e2e": e2e, "gpu_launches": None, "clocks": clk.summary(),
+                "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
                 "batched": batched, "serving": serving}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline()

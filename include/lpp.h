@@ -126,6 +126,7 @@ typedef struct lpp_info {
     double obj_offset;    /* constant to add to c_red^T x_red                             */
     double presolve_ms;   /* device time of the round loop (transfers excluded)          */
     int64_t nnz_processed;/* sum over rounds of the nonzeros present at the round start  */
+    int64_t launches;     /* kernels launched by the call (a batch: by the whole batch)   */
 } lpp_info;
 
 /* Time and traffic of one kernel family, summed over its launches

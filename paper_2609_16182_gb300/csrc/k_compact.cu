@@ -465,56 +465,56 @@ inline unsigned blocks_for(int64_t cnt, int threads) {
 }  // namespace
 
 void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s) {
-    k_lp_dead<<<blocks_for(C.nlp, 256), 256, 0, s>>>(C, K);
+    (k_lp_dead<<<blocks_for(C.nlp, 256), 256, 0, s>>>(C, K), note_launch());
     // 1. column counts over kept rows, then S6 and the column keep flags
     const GroupGrid gt = group_grid(C.T);
-    if (gt.blk_start[6] > 0) k_csc_count_groups<<<gt.blk_start[6], kBlock, 0, s>>>(C, K, gt);
+    if (gt.blk_start[6] > 0) (k_csc_count_groups<<<gt.blk_start[6], kBlock, 0, s>>>(C, K, gt), note_launch());
     const int32_t tlong = C.T.cls_start[7] - C.T.cls_start[6];
     if (tlong > 0 && C.T.nchunks > 0) {
-        k_csc_count_long<<<C.T.nchunks, kBlock, 0, s>>>(C, K);
-        k_long_prefix<<<blocks_for(tlong, 128), 128, 0, s>>>(C.T, K.cht_cnt, K.cht_off, K.c_len, nullptr, nullptr);
+        (k_csc_count_long<<<C.T.nchunks, kBlock, 0, s>>>(C, K), note_launch());
+        (k_long_prefix<<<blocks_for(tlong, 128), 128, 0, s>>>(C.T, K.cht_cnt, K.cht_off, K.c_len, nullptr, nullptr), note_launch());
     }
-    if (C.n > 0) k_colkeep<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C, K);
+    if (C.n > 0) (k_colkeep<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C, K), note_launch());
     // 2. row counts over kept columns and the side shifts
     const GroupGrid ga = group_grid(C.A);
-    if (ga.blk_start[6] > 0) k_csr_count_groups<<<ga.blk_start[6], kBlock, 0, s>>>(C, K, ga);
+    if (ga.blk_start[6] > 0) (k_csr_count_groups<<<ga.blk_start[6], kBlock, 0, s>>>(C, K, ga), note_launch());
     const int32_t along = C.A.cls_start[7] - C.A.cls_start[6];
     if (along > 0 && C.A.nchunks > 0) {
-        k_csr_count_long<<<C.A.nchunks, kBlock, 0, s>>>(C, K);
-        k_long_prefix<<<blocks_for(along, 128), 128, 0, s>>>(C.A, K.chr_cnt, K.chr_off, K.r_len, K.chr_shift,
-                                                               K.shift);
+        (k_csr_count_long<<<C.A.nchunks, kBlock, 0, s>>>(C, K), note_launch());
+        (k_long_prefix<<<blocks_for(along, 128), 128, 0, s>>>(C.A, K.chr_cnt, K.chr_off, K.r_len, K.chr_shift,
+                                                               K.shift), note_launch());
     }
 }
 
 void launch_compact_scatter(const Ctx &C, const CompactCtx &K, int32_t m_new, int32_t n_new, cudaStream_t s) {
     (void)m_new;
     (void)n_new;
-    k_zero_ptr<<<1, 1, 0, s>>>(K.rp2);
-    k_zero_ptr<<<1, 1, 0, s>>>(K.cp2);
-    if (C.m > 0) k_rowvec<<<blocks_for(C.m, kBlock), kBlock, 0, s>>>(C, K);
-    if (C.n > 0) k_colvec<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C, K);
+    (k_zero_ptr<<<1, 1, 0, s>>>(K.rp2), note_launch());
+    (k_zero_ptr<<<1, 1, 0, s>>>(K.cp2), note_launch());
+    if (C.m > 0) (k_rowvec<<<blocks_for(C.m, kBlock), kBlock, 0, s>>>(C, K), note_launch());
+    if (C.n > 0) (k_colvec<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C, K), note_launch());
     const GroupGrid ga = group_grid(C.A);
-    if (ga.blk_start[6] > 0) k_csr_scatter_groups<<<ga.blk_start[6], kBlock, 0, s>>>(C, K, ga);
+    if (ga.blk_start[6] > 0) (k_csr_scatter_groups<<<ga.blk_start[6], kBlock, 0, s>>>(C, K, ga), note_launch());
     if (C.A.cls_start[7] > C.A.cls_start[6] && C.A.nchunks > 0)
-        k_csr_scatter_long<<<C.A.nchunks, kBlock, 0, s>>>(C, K);
+        (k_csr_scatter_long<<<C.A.nchunks, kBlock, 0, s>>>(C, K), note_launch());
     const GroupGrid gt = group_grid(C.T);
-    if (gt.blk_start[6] > 0) k_csc_scatter_groups<<<gt.blk_start[6], kBlock, 0, s>>>(C, K, gt);
+    if (gt.blk_start[6] > 0) (k_csc_scatter_groups<<<gt.blk_start[6], kBlock, 0, s>>>(C, K, gt), note_launch());
     if (C.T.cls_start[7] > C.T.cls_start[6] && C.T.nchunks > 0)
-        k_csc_scatter_long<<<C.T.nchunks, kBlock, 0, s>>>(C, K);
+        (k_csc_scatter_long<<<C.T.nchunks, kBlock, 0, s>>>(C, K), note_launch());
 }
 
 void launch_offset(const Ctx &C, const CompactCtx &K, cudaStream_t s) {
     if (C.n == 0) return;
     if (C.nlp == 1) {
         const int32_t ntiles = (int32_t)((C.n + kScanTile - 1) / kScanTile);
-        k_offset_tiles<<<ntiles, kBlock, 0, s>>>(K.contrib, C.n, K.offset_part);
-        k_offset_final<<<1, kBlock, 0, s>>>(K.offset_part, ntiles, K.offset);
+        (k_offset_tiles<<<ntiles, kBlock, 0, s>>>(K.contrib, C.n, K.offset_part), note_launch());
+        (k_offset_final<<<1, kBlock, 0, s>>>(K.offset_part, ntiles, K.offset), note_launch());
     } else {
         cudaMemsetAsync(K.lp_first, 0, sizeof(int32_t) * (size_t)C.nlp, s);
         cudaMemsetAsync(K.lp_last, 0, sizeof(int32_t) * (size_t)C.nlp, s);
-        k_lp_ranges<<<blocks_for(C.n, 256), 256, 0, s>>>(C.lp_col, C.n, K.lp_first, K.lp_last);
-        k_offset_lps<<<blocks_for((int64_t)C.nlp * 32, 256), 256, 0, s>>>(K.contrib, K.lp_first, K.lp_last, C.nlp,
-                                                                           K.offset);
+        (k_lp_ranges<<<blocks_for(C.n, 256), 256, 0, s>>>(C.lp_col, C.n, K.lp_first, K.lp_last), note_launch());
+        (k_offset_lps<<<blocks_for((int64_t)C.nlp * 32, 256), 256, 0, s>>>(K.contrib, K.lp_first, K.lp_last, C.nlp,
+                                                                           K.offset), note_launch());
     }
 }
 

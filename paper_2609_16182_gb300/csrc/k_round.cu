@@ -641,36 +641,36 @@ inline unsigned blocks_for(int64_t cnt, int threads) {
 
 void launch_prop(const Ctx &C, cudaStream_t s) {
     const GroupGrid g = group_grid(C.A);
-    if (g.blk_start[6] > 0) k_prop_groups<<<g.blk_start[6], kBlock, 0, s>>>(C, g);
+    if (g.blk_start[6] > 0) (k_prop_groups<<<g.blk_start[6], kBlock, 0, s>>>(C, g), note_launch());
     const int32_t nlong = C.A.cls_start[7] - C.A.cls_start[6];
     if (nlong > 0 && C.A.nchunks > 0) {
-        k_prop_long_partial<<<C.A.nchunks, kBlock, 0, s>>>(C, C.ch_hash);
-        k_prop_long_combine<<<blocks_for(nlong, kBlock), kBlock, 0, s>>>(C, C.ch_hash);
-        k_prop_long_tighten<<<C.A.nchunks, kBlock, 0, s>>>(C);
+        (k_prop_long_partial<<<C.A.nchunks, kBlock, 0, s>>>(C, C.ch_hash), note_launch());
+        (k_prop_long_combine<<<blocks_for(nlong, kBlock), kBlock, 0, s>>>(C, C.ch_hash), note_launch());
+        (k_prop_long_tighten<<<C.A.nchunks, kBlock, 0, s>>>(C), note_launch());
     }
 }
 
 void launch_colfin(const Ctx &C, cudaStream_t s) {
-    if (C.n > 0) k_colfin<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C);
+    if (C.n > 0) (k_colfin<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C), note_launch());
 }
 
 void launch_mark_dirty(const Ctx &C, cudaStream_t s) {
     const GroupGrid g = group_grid(C.T);
-    if (g.blk_start[6] > 0) k_mark_groups<<<g.blk_start[6], kBlock, 0, s>>>(C, g);
-    if (C.T.cls_start[7] > C.T.cls_start[6] && C.T.nchunks > 0) k_mark_long<<<C.T.nchunks, kBlock, 0, s>>>(C);
+    if (g.blk_start[6] > 0) (k_mark_groups<<<g.blk_start[6], kBlock, 0, s>>>(C, g), note_launch());
+    if (C.T.cls_start[7] > C.T.cls_start[6] && C.T.nchunks > 0) (k_mark_long<<<C.T.nchunks, kBlock, 0, s>>>(C), note_launch());
 }
 
 void launch_s5_pass(const Ctx &C, int pass, cudaStream_t s) {
     if (C.m == 0) return;
-    k_s5_insert<<<blocks_for(C.m, kBlock), kBlock, 0, s>>>(C, pass);
+    (k_s5_insert<<<blocks_for(C.m, kBlock), kBlock, 0, s>>>(C, pass), note_launch());
     const GroupGrid g = group_grid(C.A);
-    if (g.blk_start[6] > 0) k_s5_match_groups<<<g.blk_start[6], kBlock, 0, s>>>(C, g);
+    if (g.blk_start[6] > 0) (k_s5_match_groups<<<g.blk_start[6], kBlock, 0, s>>>(C, g), note_launch());
     const int32_t nlong = C.A.cls_start[7] - C.A.cls_start[6];
-    if (nlong > 0) k_s5_match_long<<<nlong, kBlock, 0, s>>>(C);
+    if (nlong > 0) (k_s5_match_long<<<nlong, kBlock, 0, s>>>(C), note_launch());
 }
 
 void launch_s5_leader(const Ctx &C, cudaStream_t s) {
-    if (C.m > 0) k_s5_leader<<<blocks_for(C.m, kBlock), kBlock, 0, s>>>(C);
+    if (C.m > 0) (k_s5_leader<<<blocks_for(C.m, kBlock), kBlock, 0, s>>>(C), note_launch());
 }
 
 }  // namespace lpp

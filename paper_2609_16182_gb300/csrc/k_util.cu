@@ -1,10 +1,17 @@
 // k_util.cu -- scans, class binning of segments, stable transpose (A -> A^T)
 // and the input checks of ingest (S0).
 #include <algorithm>
+#include <atomic>
 
 #include "lpp_launch.h"
 
 namespace lpp {
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
@@ -389,18 +396,18 @@ size_t scan_tmp_elems(int64_t cnt) { return 2 * ((size_t)((cnt + kScanTile - 1) 
 
 void scan_excl(const int32_t *in, int32_t *out, int64_t cnt, int32_t *tmp, cudaStream_t s) {
     const int32_t ntiles = (int32_t)((cnt + kScanTile - 1) / kScanTile);
-    if (ntiles > 0) k_scan_reduce<int32_t><<<ntiles, kScanThreads, 0, s>>>(In1{in}, cnt, tmp);
-    k_scan_top<int32_t><<<1, 1024, 0, s>>>(tmp, ntiles, Out1{out}, cnt);
-    if (ntiles > 0) k_scan_down<int32_t><<<ntiles, kScanThreads, 0, s>>>(In1{in}, Out1{out}, cnt, tmp);
+    if (ntiles > 0) (k_scan_reduce<int32_t><<<ntiles, kScanThreads, 0, s>>>(In1{in}, cnt, tmp), note_launch());
+    (k_scan_top<int32_t><<<1, 1024, 0, s>>>(tmp, ntiles, Out1{out}, cnt), note_launch());
+    if (ntiles > 0) (k_scan_down<int32_t><<<ntiles, kScanThreads, 0, s>>>(In1{in}, Out1{out}, cnt, tmp), note_launch());
 }
 
 void scan_excl2(const int32_t *a, const int32_t *b, int32_t *oa, int32_t *ob, int64_t cnt, int32_t *tmp,
                 cudaStream_t s) {
     const int32_t ntiles = (int32_t)((cnt + kScanTile - 1) / kScanTile);
     Pair *t = reinterpret_cast<Pair *>(tmp);
-    if (ntiles > 0) k_scan_reduce<Pair><<<ntiles, kScanThreads, 0, s>>>(In2{a, b}, cnt, t);
-    k_scan_top<Pair><<<1, 1024, 0, s>>>(t, ntiles, Out2{oa, ob}, cnt);
-    if (ntiles > 0) k_scan_down<Pair><<<ntiles, kScanThreads, 0, s>>>(In2{a, b}, Out2{oa, ob}, cnt, t);
+    if (ntiles > 0) (k_scan_reduce<Pair><<<ntiles, kScanThreads, 0, s>>>(In2{a, b}, cnt, t), note_launch());
+    (k_scan_top<Pair><<<1, 1024, 0, s>>>(t, ntiles, Out2{oa, ob}, cnt), note_launch());
+    if (ntiles > 0) (k_scan_down<Pair><<<ntiles, kScanThreads, 0, s>>>(In2{a, b}, Out2{oa, ob}, cnt, t), note_launch());
 }
 
 size_t sched_tile_hist_elems(int64_t cnt) {
@@ -413,18 +420,18 @@ void build_schedule(const int32_t *ptr, const int32_t *cnt_dev, int32_t cnt_max,
                     const SchedBufs &b, int32_t *cls_out, int32_t *nchunk_out, cudaStream_t s) {
     // tiles cover cnt_max segments; tiles past the actual count hold zeros
     const int32_t ntiles = std::max<int32_t>(1, (int32_t)((cnt_max + kScanTile - 1) / kScanTile));
-    k_bin_hist<<<ntiles, kScanThreads, 0, s>>>(ptr, cnt_dev, b.tile_hist, ntiles);
+    (k_bin_hist<<<ntiles, kScanThreads, 0, s>>>(ptr, cnt_dev, b.tile_hist, ntiles), note_launch());
     scan_excl(b.tile_hist, b.tile_hist, (int64_t)kNumClass * ntiles, b.tmp, s);
-    k_bin_scatter<<<ntiles, kScanThreads, 0, s>>>(ptr, cnt_dev, b.tile_hist, ntiles, b.order);
-    k_bin_finish<<<1, 32, 0, s>>>(b.tile_hist, ntiles, cls_out);
+    (k_bin_scatter<<<ntiles, kScanThreads, 0, s>>>(ptr, cnt_dev, b.tile_hist, ntiles, b.order), note_launch());
+    (k_bin_finish<<<1, 32, 0, s>>>(b.tile_hist, ntiles, cls_out), note_launch());
     // chunks of the long segments: at most nnz / kLongMin of them
     const int32_t cap_long = sched_cap_long(nnz_max);
-    k_chunk_count<<<blocks_for(cap_long, 256), 256, 0, s>>>(ptr, b.order, b.tile_hist, ntiles, cls_out, cap_long,
-                                                             b.nch);
+    (k_chunk_count<<<blocks_for(cap_long, 256), 256, 0, s>>>(ptr, b.order, b.tile_hist, ntiles, cls_out, cap_long,
+                                                             b.nch), note_launch());
     scan_excl(b.nch, b.lfirst, cap_long, b.tmp, s);
-    k_chunk_fill<<<blocks_for(cap_long, 256), 256, 0, s>>>(ptr, b.order, b.tile_hist, ntiles, cls_out, cap_long,
-                                                            b.lfirst, b.chunks);
-    k_copy_i32<<<1, 1, 0, s>>>(b.lfirst + cap_long, nchunk_out);
+    (k_chunk_fill<<<blocks_for(cap_long, 256), 256, 0, s>>>(ptr, b.order, b.tile_hist, ntiles, cls_out, cap_long,
+                                                            b.lfirst, b.chunks), note_launch());
+    (k_copy_i32<<<1, 1, 0, s>>>(b.lfirst + cap_long, nchunk_out), note_launch());
 }
 
 void segmat_from_counts(SegMat &M, const int32_t cls[kNumClass], int32_t nchunks) {
@@ -448,19 +455,19 @@ GroupGrid group_grid(const SegMat &M) {
 
 void check_csr(const int32_t *ptr, const int32_t *idx, const double *val, int32_t m, int32_t n, int64_t nnz,
                int32_t *row_of, int32_t *tmp, int32_t *err, cudaStream_t s) {
-    k_check_ptr<<<blocks_for((int64_t)m + 1, 256), 256, 0, s>>>(ptr, m, nnz, err);
+    (k_check_ptr<<<blocks_for((int64_t)m + 1, 256), 256, 0, s>>>(ptr, m, nnz, err), note_launch());
     // row_of: mark boundaries, then an inclusive scan (exclusive scan shifted by one)
     cudaMemsetAsync(row_of, 0, sizeof(int32_t) * (size_t)(nnz + 1), s);
-    if (m > 1) k_mark_rows<<<blocks_for((int64_t)m - 1, 256), 256, 0, s>>>(ptr, m, nnz, row_of);
+    if (m > 1) (k_mark_rows<<<blocks_for((int64_t)m - 1, 256), 256, 0, s>>>(ptr, m, nnz, row_of), note_launch());
     scan_excl(row_of, row_of, nnz, tmp, s);  // row_of[k+1] = rows whose start is <= k ... see caller
-    if (nnz > 0) k_check_entries<<<blocks_for(nnz, 256), 256, 0, s>>>(idx, val, row_of + 1, nnz, n, err);
+    if (nnz > 0) (k_check_entries<<<blocks_for(nnz, 256), 256, 0, s>>>(idx, val, row_of + 1, nnz, n, err), note_launch());
 }
 
 void ingest_vectors(const double *lhs, const double *rhs, const double *lb, const double *ub, const double *c,
                     int32_t m, int32_t n, double huge, double *L, double *U, double2 *lu, double *cc, int32_t *err,
                     cudaStream_t s) {
-    if (m > 0) k_ingest_rows<<<blocks_for(m, 256), 256, 0, s>>>(lhs, rhs, m, huge, L, U, err);
-    if (n > 0) k_ingest_cols<<<blocks_for(n, 256), 256, 0, s>>>(lb, ub, c, n, huge, lu, cc, err);
+    if (m > 0) (k_ingest_rows<<<blocks_for(m, 256), 256, 0, s>>>(lhs, rhs, m, huge, L, U, err), note_launch());
+    if (n > 0) (k_ingest_cols<<<blocks_for(n, 256), 256, 0, s>>>(lb, ub, c, n, huge, lu, cc, err), note_launch());
 }
 
 size_t transpose_hist_elems(int64_t nnz) { return (size_t)256 * (size_t)((nnz + kScanTile - 1) / kScanTile) + 1; }
@@ -472,11 +479,11 @@ void transpose(const int32_t *ptr, const int32_t *idx, const double *val, const 
     (void)m;
     // column pointers: counts then a scan
     cudaMemsetAsync(colcnt, 0, sizeof(int32_t) * (size_t)(n + 1), s);
-    if (nnz > 0) k_count_cols<<<blocks_for(nnz, 256), 256, 0, s>>>(idx, nnz, colcnt);
+    if (nnz > 0) (k_count_cols<<<blocks_for(nnz, 256), 256, 0, s>>>(idx, nnz, colcnt), note_launch());
     scan_excl(colcnt, tptr, n, b.tmp, s);
     if (nnz == 0) return;
     // stable LSD radix sort of the entries by column (entries come row by row)
-    k_copy_keys<<<blocks_for(nnz, 256), 256, 0, s>>>(idx, nnz, b.k0, b.v0);
+    (k_copy_keys<<<blocks_for(nnz, 256), 256, 0, s>>>(idx, nnz, b.k0, b.v0), note_launch());
     int bits = 0;
     while (bits < 31 && ((int64_t)1 << bits) < (int64_t)n) bits++;
     const int passes = (bits + 7) / 8;
@@ -484,21 +491,21 @@ void transpose(const int32_t *ptr, const int32_t *idx, const double *val, const 
     uint32_t *kin = b.k0, *kout = b.k1;
     int32_t *vin = b.v0, *vout = b.v1;
     for (int p = 0; p < passes; p++) {
-        k_radix_hist<<<ntiles, kScanThreads, 0, s>>>(kin, nnz, 8 * p, b.hist, ntiles);
+        (k_radix_hist<<<ntiles, kScanThreads, 0, s>>>(kin, nnz, 8 * p, b.hist, ntiles), note_launch());
         scan_excl(b.hist, b.hist, (int64_t)256 * ntiles, b.tmp, s);
-        k_radix_scatter<<<ntiles, kScanThreads, 0, s>>>(kin, vin, nnz, 8 * p, b.hist, ntiles, kout, vout);
+        (k_radix_scatter<<<ntiles, kScanThreads, 0, s>>>(kin, vin, nnz, 8 * p, b.hist, ntiles, kout, vout), note_launch());
         std::swap(kin, kout);
         std::swap(vin, vout);
     }
-    k_gather_t<<<blocks_for(nnz, 256), 256, 0, s>>>(vin, row_of, val, nnz, tidx, tval);
+    (k_gather_t<<<blocks_for(nnz, 256), 256, 0, s>>>(vin, row_of, val, nnz, tidx, tval), note_launch());
 }
 
 void iota(int32_t *a, int32_t cnt, int32_t base, cudaStream_t s) {
-    if (cnt > 0) k_iota<<<blocks_for(cnt, 256), 256, 0, s>>>(a, cnt, base);
+    if (cnt > 0) (k_iota<<<blocks_for(cnt, 256), 256, 0, s>>>(a, cnt, base), note_launch());
 }
 
 void fill_u64(unsigned long long *a, int64_t cnt, unsigned long long v, cudaStream_t s) {
-    if (cnt > 0) k_fill_u64<<<blocks_for(cnt, 256), 256, 0, s>>>(a, cnt, v);
+    if (cnt > 0) (k_fill_u64<<<blocks_for(cnt, 256), 256, 0, s>>>(a, cnt, v), note_launch());
 }
 
 }  // namespace lpp
@@ -518,9 +525,9 @@ __global__ void k_split_lu(const double2 *lu, int32_t n, double *lb, double *ub)
 }
 }  // namespace
 void fill_i32(int32_t *a, int64_t cnt, int32_t v, cudaStream_t s) {
-    if (cnt > 0) k_fill_i32<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(a, cnt, v);
+    if (cnt > 0) (k_fill_i32<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(a, cnt, v), note_launch());
 }
 void split_lu(const double2 *lu, int32_t n, double *lb, double *ub, cudaStream_t s) {
-    if (n > 0) k_split_lu<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(lu, n, lb, ub);
+    if (n > 0) (k_split_lu<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(lu, n, lb, ub), note_launch());
 }
 }  // namespace lpp

@@ -170,6 +170,7 @@ lpp_postsolve *make_postsolve(Engine &E, const std::shared_ptr<DeviceRecords> &D
     I.obj_offset = offset;
     I.presolve_ms = E.loop_ms;
     I.nnz_processed = E.nnz_processed;
+    I.launches = launch_count() - E.launches0;
     P->r_nnz = E.r_nnz;
     P->r_rows = E.r_rows;
     P->r_cols = E.r_cols;
@@ -377,15 +378,15 @@ lpp_status lpp_presolve_batch(const lpp_lp *ins, int32_t count, const lpp_opts *
         // rows of each LP in the numbering of the last round's start (activities)
         int32_t *acnt = E->pool.alloc<int32_t>(count);
         LPP_CUDA(cudaMemsetAsync(acnt, 0, sizeof(int32_t) * (size_t)count, s));
-        if (E->act_m > 0) k_count_rows_lp<<<nblk(E->act_m), 256, 0, s>>>(E->lprow[E->act_buf], E->act_m, acnt);
+        if (E->act_m > 0) (k_count_rows_lp<<<nblk(E->act_m), 256, 0, s>>>(E->lprow[E->act_buf], E->act_m, acnt), note_launch());
         std::vector<int32_t> acnt_h(count);
         LPP_CUDA(cudaMemcpyAsync(acnt_h.data(), acnt, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s));
         auto D = take_records(*E);
         // per-LP sizes of the reduced arena
         int32_t *cnt = E->pool.alloc<int32_t>(3 * (size_t)count);
         LPP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * 3 * (size_t)count, s));
-        k_count_lp<<<nblk(std::max(E->m, E->n)), 256, 0, s>>>(E->lprow[c], E->rp[c], E->m, E->lpcol[c], E->n, cnt,
-                                                                cnt + count, cnt + 2 * count);
+        (k_count_lp<<<nblk(std::max(E->m, E->n)), 256, 0, s>>>(E->lprow[c], E->rp[c], E->m, E->lpcol[c], E->n, cnt,
+                                                                cnt + count, cnt + 2 * count), note_launch());
         std::vector<int32_t> hc(3 * (size_t)count);
         LPP_CUDA(cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * hc.size(), cudaMemcpyDeviceToHost, s));
         LPP_CUDA(cudaStreamSynchronize(s));
@@ -415,14 +416,14 @@ lpp_status lpp_presolve_batch(const lpp_lp *ins, int32_t count, const lpp_opts *
         int32_t *cmap_out = E->pool.alloc<int32_t>(E->n);
         double *lb = E->pool.alloc<double>(E->n), *ub = E->pool.alloc<double>(E->n);
         if (E->m > 0)
-            k_rebase_rows<<<nblk(E->m), 256, 0, s>>>(E->rp[c], E->lprow[c], E->rmap[c], E->m, nnz_start, row_orig,
-                                                     rp_out, rmap_out);
+            (k_rebase_rows<<<nblk(E->m), 256, 0, s>>>(E->rp[c], E->lprow[c], E->rmap[c], E->m, nnz_start, row_orig,
+                                                     rp_out, rmap_out), note_launch());
         if (E->n > 0)
-            k_rebase_cols<<<nblk(E->n), 256, 0, s>>>(E->tp[c], E->lpcol[c], E->cmap[c], E->n, nnz_start, col_orig,
-                                                     tp_out, cmap_out);
-        k_ptr_tails<<<nblk(count), 256, 0, s>>>(row_start, rows, col_start, cols, nnzs, count, rp_out, tp_out);
-        if (E->m > 0) k_rebase_idx<<<nblk(E->m), 256, 0, s>>>(E->ci[c], E->rp[c], E->lprow[c], E->m, col_start);
-        if (E->n > 0) k_rebase_idx<<<nblk(E->n), 256, 0, s>>>(E->ti[c], E->tp[c], E->lpcol[c], E->n, row_start);
+            (k_rebase_cols<<<nblk(E->n), 256, 0, s>>>(E->tp[c], E->lpcol[c], E->cmap[c], E->n, nnz_start, col_orig,
+                                                     tp_out, cmap_out), note_launch());
+        (k_ptr_tails<<<nblk(count), 256, 0, s>>>(row_start, rows, col_start, cols, nnzs, count, rp_out, tp_out), note_launch());
+        if (E->m > 0) (k_rebase_idx<<<nblk(E->m), 256, 0, s>>>(E->ci[c], E->rp[c], E->lprow[c], E->m, col_start), note_launch());
+        if (E->n > 0) (k_rebase_idx<<<nblk(E->n), 256, 0, s>>>(E->ti[c], E->tp[c], E->lpcol[c], E->n, row_start), note_launch());
         split_lu(E->lu[c], E->n, lb, ub, s);
         LPP_CUDA(cudaGetLastError());
         LPP_CUDA(cudaStreamSynchronize(s));

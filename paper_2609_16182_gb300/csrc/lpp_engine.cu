@@ -186,6 +186,7 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
     o = opts;
     nlp = nlp_;
     mem = members;
+    launches0 = launch_count();
     m0 = n0 = 0;
     nnz0 = 0;
     for (const Member &x : mem) {
@@ -338,8 +339,8 @@ void Engine::ingest_batch(const lpp_lp *ins, int32_t count) {
         // the host vector must outlive the copy
         LPP_CUDA(cudaStreamSynchronize(s));
         dim3 grid(8, (unsigned)count);
-        k_gather_lps<<<grid, 256, 0, s>>>(dd, rp[0], ci[0], rv[0], slhs, srhs, slb, sub, sc, lprow[0], lpcol[0],
-                                          &st->err);
+        (k_gather_lps<<<grid, 256, 0, s>>>(dd, rp[0], ci[0], rv[0], slhs, srhs, slb, sub, sc, lprow[0], lpcol[0],
+                                          &st->err), note_launch());
         LPP_CUDA(cudaGetLastError());
     } else {
         // pack on the host into pinned staging, then one copy per array
@@ -386,7 +387,7 @@ void Engine::ingest_batch(const lpp_lp *ins, int32_t count) {
         up(lpcol[0], h_lc.data(), sizeof(int32_t) * h_lc.size());
         LPP_CUDA(cudaStreamSynchronize(s));  // pageable staging must outlive the copies
     }
-    k_set_i32<<<1, 1, 0, s>>>(rp[0] + m0, (int32_t)nnz0);
+    (k_set_i32<<<1, 1, 0, s>>>(rp[0] + m0, (int32_t)nnz0), note_launch());
     ingest_vectors(slhs, srhs, slb, sub, sc, m0, n0, o.huge, L[0], U[0], lu[0], c[0], &st->err, s);
 }
 
@@ -437,8 +438,8 @@ void Engine::prepare() {
     n = n0;
     nnz = nnz0;
     cur = 0;
-    k_set_i32<<<1, 1, 0, s>>>(&st->m_new, m0);
-    k_set_i32<<<1, 1, 0, s>>>(&st->n_new, n0);
+    (k_set_i32<<<1, 1, 0, s>>>(&st->m_new, m0), note_launch());
+    (k_set_i32<<<1, 1, 0, s>>>(&st->n_new, n0), note_launch());
     schedule_current();
     read_status();  // also keeps offs alive until its copy is done
     adopt_schedule();
@@ -569,7 +570,7 @@ void Engine::compact(int32_t round) {
     scan_excl2(K.c_keep, K.c_len, K.c_pos, K.c_off, n, scan_tmp, s);
     tend();
     launch_offset(C, K, s);
-    k_sizes<<<1, 1, 0, s>>>(K, m, n, st);
+    (k_sizes<<<1, 1, 0, s>>>(K, m, n, st), note_launch());
     tbegin(F_SCATTER, 24.0 * nnz * 2 + 48.0 * (m + n));
     launch_compact_scatter(C, K, 0, 0, s);
     tend();
@@ -722,8 +723,8 @@ void Engine::run() {
 const char *fam_name(int f) { return kFamNames[f]; }
 
 void Engine::k_sizes_set(int32_t m_, int32_t n_) {
-    k_set_i32<<<1, 1, 0, s>>>(&st->m_new, m_);
-    k_set_i32<<<1, 1, 0, s>>>(&st->n_new, n_);
+    (k_set_i32<<<1, 1, 0, s>>>(&st->m_new, m_), note_launch());
+    (k_set_i32<<<1, 1, 0, s>>>(&st->n_new, n_), note_launch());
 }
 
 }  // namespace lpp

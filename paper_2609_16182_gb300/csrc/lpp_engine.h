@@ -111,6 +111,7 @@ struct Engine {
     int32_t rounds = 0;
     double loop_ms = 0.0;
     int64_t nnz_processed = 0;
+    int64_t launches0 = 0;  // launch counter at setup
     // activities of the last round: current-index arrays and the map valid then
     int32_t act_m = 0, act_buf = 0;
     // kernel timing

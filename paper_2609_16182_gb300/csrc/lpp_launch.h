@@ -6,6 +6,10 @@
 
 namespace lpp {
 
+// number of kernels the library has launched in this process (all threads)
+void note_launch();
+int64_t launch_count();
+
 // ----------------------------------------------------------------- k_util.cu
 // Exclusive scan of in[0..cnt) into out[0..cnt], out[cnt] = total.  `tmp`
 // must hold scan_tmp_elems(cnt) int32 values.  in == out is allowed.

@@ -314,9 +314,9 @@ void Engine::append(int32_t slot, const lpp_lp &in, int32_t rbase, int32_t cbase
     a.rec_rv = rec_rv;
     a.rec_cv = rec_cv;
     a.a_rdirty = rdirty[cur];
-    k_append<<<grid_for(std::max<int64_t>({(int64_t)ml + 1, (int64_t)nl + 1, (int64_t)zl})), 256, 0, s>>>(a);
-    k_set_slot<<<1, 32, 0, s>>>(verdict, lp_round0_dev, lp_retired_dev, K.offset, nullptr, slot, round0,
-                                 in.obj_offset);
+    (k_append<<<grid_for(std::max<int64_t>({(int64_t)ml + 1, (int64_t)nl + 1, (int64_t)zl})), 256, 0, s>>>(a), note_launch());
+    (k_set_slot<<<1, 32, 0, s>>>(verdict, lp_round0_dev, lp_retired_dev, K.offset, nullptr, slot, round0,
+                                 in.obj_offset), note_launch());
     LPP_CUDA(cudaGetLastError());
     m += ml;
     n += nl;
@@ -475,7 +475,7 @@ void finish_slot(lpp_server *S, int32_t k, const std::vector<int32_t> &rng, cons
     D->act_rmap = a.o_armap = (int32_t *)own(4 * (size_t)na, D->owned);
     const int64_t span = std::max<int64_t>({(int64_t)mr + 1, (int64_t)nc + 1, (int64_t)nz, (int64_t)Z.m0,
                                             (int64_t)Z.n0, (int64_t)na});
-    k_extract<<<grid_for(span), 256, 0, E.s>>>(a);
+    (k_extract<<<grid_for(span), 256, 0, E.s>>>(a), note_launch());
     LPP_CUDA(cudaGetLastError());
     LPP_CUDA(cudaStreamSynchronize(E.s));
     R->m = mr;
@@ -550,10 +550,10 @@ bool tick(lpp_server *S, std::vector<std::pair<int32_t, lpp_server::Req *>> &adm
     // per-slot ranges now and at the round start, objective constants
     int32_t *dr = E.pool.alloc<int32_t>(8 * (size_t)nl);
     fill_i32(dr, 8 * (int64_t)nl, -1, E.s);
-    if (E.m > 0) k_bounds<<<(E.m + 255) / 256, 256, 0, E.s>>>(E.lprow[E.cur], E.m, dr, dr + nl);
-    if (E.n > 0) k_bounds<<<(E.n + 255) / 256, 256, 0, E.s>>>(E.lpcol[E.cur], E.n, dr + 2 * nl, dr + 3 * nl);
-    if (E.act_m > 0) k_bounds<<<(E.act_m + 255) / 256, 256, 0, E.s>>>(E.lprow[E.act_buf], E.act_m, dr + 6 * nl,
-                                                                        dr + 7 * nl);
+    if (E.m > 0) (k_bounds<<<(E.m + 255) / 256, 256, 0, E.s>>>(E.lprow[E.cur], E.m, dr, dr + nl), note_launch());
+    if (E.n > 0) (k_bounds<<<(E.n + 255) / 256, 256, 0, E.s>>>(E.lpcol[E.cur], E.n, dr + 2 * nl, dr + 3 * nl), note_launch());
+    if (E.act_m > 0) (k_bounds<<<(E.act_m + 255) / 256, 256, 0, E.s>>>(E.lprow[E.act_buf], E.act_m, dr + 6 * nl,
+                                                                        dr + 7 * nl), note_launch());
     std::vector<int32_t> h(8 * (size_t)nl), rp_h((size_t)E.m + 1);
     std::vector<double> offs(nl);
     LPP_CUDA(cudaMemcpyAsync(h.data(), dr, sizeof(int32_t) * h.size(), cudaMemcpyDeviceToHost, E.s));

@@ -46,7 +46,7 @@ class Info(C.Structure):
     _fields_ = [("status", C.c_int32), ("where", C.c_int32), ("index", C.c_int32), ("round", C.c_int32),
                 ("rounds", C.c_int32), ("m", C.c_int32), ("n", C.c_int32), ("m_red", C.c_int32),
                 ("n_red", C.c_int32), ("nnz", C.c_int64), ("nnz_red", C.c_int64), ("obj_offset", C.c_double),
-                ("presolve_ms", C.c_double), ("nnz_processed", C.c_int64)]
+                ("presolve_ms", C.c_double), ("nnz_processed", C.c_int64), ("launches", C.c_int64)]
 
 
 class KernelStat(C.Structure):
