@@ -386,12 +386,12 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                 /* a x_j <= U - rmin  and  a x_j >= L - rmax */
                 if (isfin(U) && rmin_ok) {
                     cand[nc] = (U - rmin) / a;
-                    ebc[nc] = (s.ebU[i] + eb_rmin) / fabs(a) + UROUND * fabs(cand[nc]);
+                    ebc[nc] = (s.ebU[i] + eb_rmin + UROUND * fabs(U - mna[i])) / fabs(a) + UROUND * fabs(cand[nc]);
                     is_upper[nc++] = a > 0;
                 }
                 if (isfin(L) && rmax_ok) {
                     cand[nc] = (L - rmax) / a;
-                    ebc[nc] = (s.ebL[i] + eb_rmax) / fabs(a) + UROUND * fabs(cand[nc]);
+                    ebc[nc] = (s.ebL[i] + eb_rmax + UROUND * fabs(L - mxa[i])) / fabs(a) + UROUND * fabs(cand[nc]);
                     is_upper[nc++] = a < 0;
                 }
                 for (t = 0; t < nc; t++) {
