@@ -29,6 +29,13 @@ __device__ __forceinline__ double pinf() { return __longlong_as_double(0x7ff0000
 __device__ __forceinline__ double ninf_() { return __longlong_as_double((long long)0xfff0000000000000ULL); }
 
 
+// exact sign tests of a double on its bit pattern (integer pipes):
+// s < 0 <=> negative and not -0;  s > 0 <=> positive bits, not +0
+__device__ __forceinline__ bool lt0(double s) {
+    return dbits(s) < 0 && dbits(s) != (long long)0x8000000000000000ULL;
+}
+__device__ __forceinline__ bool gt0(double s) { return dbits(s) > 0; }
+
 // Implied upper bound x/a on column j (from a*x_j <= x with a > 0, or
 // a*x_j >= x with a < 0).  Accepted iff (uold = +inf or x/a < thr) and
 // |x/a| <= max_implied, thr = uold - bound_tol*max(1,|uold|) (one rounding).
@@ -38,9 +45,9 @@ __device__ __forceinline__ void try_upper(const Ctx &C, int32_t j, double x, dou
     if (is_fin(uold)) {
         const double thr = fma(-C.bound_tol, max1abs(uold), uold);
         const double s = fma(-thr, a, x);
-        if (is_neg(a) ? !(s > 0.0) : !(s < 0.0)) return;
+        if (is_neg(a) ? !gt0(s) : !lt0(s)) return;
     }
-    if (fma(-C.max_implied, fabs(a), fabs(x)) > 0.0) return;
+    if (gt0(fma(-C.max_implied, fabs(a), fabs(x)))) return;
     atomic_min_dbl(&C.cand_u[j], x / a);
 }
 // Implied lower bound x/a: accepted iff (lold = -inf or x/a > thr) and
@@ -49,30 +56,30 @@ __device__ __forceinline__ void try_lower(const Ctx &C, int32_t j, double x, dou
     if (is_fin(lold)) {
         const double thr = fma(C.bound_tol, max1abs(lold), lold);
         const double s = fma(-thr, a, x);
-        if (is_neg(a) ? !(s < 0.0) : !(s > 0.0)) return;
+        if (is_neg(a) ? !lt0(s) : !gt0(s)) return;
     }
-    if (fma(-C.max_implied, fabs(a), fabs(x)) > 0.0) return;
+    if (gt0(fma(-C.max_implied, fabs(a), fabs(x)))) return;
     atomic_max_dbl(&C.cand_l[j], x / a);
 }
 
-// candidates of one entry (S3); smin/smax, nmin/nmax are the row's activities
-__device__ __forceinline__ void tighten_entry(const Ctx &C, int32_t j, double a, double Lv, double Uv, bool up_row,
-                                              bool lo_row, double smin, double smax, int nmin, int nmax) {
+// Candidates of one entry (S3).  dU = U - smin and dL = L - smax are the
+// row's slacks: U - (min activity of the other entries) = dU + a*bmin when
+// every term is finite, = dU when this entry is the one infinite term.
+__device__ __forceinline__ void tighten_entry(const Ctx &C, int32_t j, double a, bool up_row, bool lo_row,
+                                              double dU, double dL, int nmin, int nmax) {
     const double2 b = C.lu[j];
     const bool neg = is_neg(a);
     const double bmin = neg ? b.y : b.x, bmax = neg ? b.x : b.y;
     const bool fmn = is_fin(bmin), fmx = is_fin(bmax);
     if (up_row && (fmn ? nmin == 0 : nmin == 1)) {
         // a x_j <= U - (min activity of the other entries)
-        const double rmin = fmn ? fma(-a, bmin, smin) : smin;
-        const double x = Uv - rmin;
+        const double x = fmn ? fma(a, bmin, dU) : dU;
         if (!neg) try_upper(C, j, x, a, b.y);
         else try_lower(C, j, x, a, b.x);
     }
     if (lo_row && (fmx ? nmax == 0 : nmax == 1)) {
         // a x_j >= L - (max activity of the other entries)
-        const double rmax = fmx ? fma(-a, bmax, smax) : smax;
-        const double x = Lv - rmax;
+        const double x = fmx ? fma(a, bmax, dL) : dL;
         if (!neg) try_lower(C, j, x, a, b.x);
         else try_upper(C, j, x, a, b.y);
     }
@@ -210,8 +217,9 @@ __device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, 
     if (kind != RK_KEPT || len < 2) return;
     const bool up_row = is_fin(Uv) && nmin <= 1, lo_row = is_fin(Lv) && nmax <= 1;
     if (!up_row && !lo_row) return;
+    const double dU = Uv - smin, dL = Lv - smax;
     for (int32_t k = beg + lane; k < end; k += W)
-        tighten_entry(C, C.A.idx[k], C.A.val[k], Lv, Uv, up_row, lo_row, smin, smax, nmin, nmax);
+        tighten_entry(C, C.A.idx[k], C.A.val[k], up_row, lo_row, dU, dL, nmin, nmax);
 }
 
 __global__ void __launch_bounds__(kBlock) k_prop_groups(Ctx C, GroupGrid g) {
@@ -325,8 +333,9 @@ __global__ void __launch_bounds__(kBlock) k_prop_long_tighten(Ctx C) {
     const double2 act = C.act[i];
     const int2 ni = C.ninf[i];
     const bool up_row = is_fin(Uv) && ni.x <= 1, lo_row = is_fin(Lv) && ni.y <= 1;
+    const double dU = Uv - act.x, dL = Lv - act.y;
     for (int32_t k = ch.begin + threadIdx.x; k < ch.end; k += kBlock)
-        tighten_entry(C, C.A.idx[k], C.A.val[k], Lv, Uv, up_row, lo_row, act.x, act.y, ni.x, ni.y);
+        tighten_entry(C, C.A.idx[k], C.A.val[k], up_row, lo_row, dU, dL, ni.x, ni.y);
 }
 
 // ------------------------------------------------- S3' finalise + S4 fixing
