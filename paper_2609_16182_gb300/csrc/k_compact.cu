@@ -39,6 +39,14 @@ __device__ __forceinline__ int32_t group_count(const int32_t *idx, int32_t beg, 
     return group_sum<W>(c, group_mask<W>());
 }
 
+// The flat scatter's tile t starts at entry t * kFlatTile; the segment (or
+// chunk) [b, e) that holds that entry records itself.  Segments and chunks
+// are at most kFlatTile long, so each holds at most one tile start.
+__device__ __forceinline__ void mark_tile(int32_t *tile, int32_t b, int32_t e, int32_t seg) {
+    const int64_t t = ((int64_t)b + kFlatTile - 1) / kFlatTile;
+    if (t * kFlatTile < e) tile[t] = seg;
+}
+
 // ---------------------------------------------------------------- CSC count
 template <int W>
 __device__ __forceinline__ void csc_count_group(const Ctx &C, const CompactCtx &K, int32_t j, bool valid) {
@@ -49,7 +57,10 @@ __device__ __forceinline__ void csc_count_group(const Ctx &C, const CompactCtx &
     }
     const uint8_t *rk = C.rkind;
     const int32_t cnt = group_count<W>(C.T.idx, beg, end, [rk](int32_t r) { return rk[r] == RK_KEPT; });
-    if (valid && (threadIdx.x & (W - 1)) == 0) K.c_len[j] = cnt;
+    if (valid && (threadIdx.x & (W - 1)) == 0) {
+        K.c_len[j] = cnt;
+        mark_tile(K.tile_t, beg, end, j);
+    }
 }
 
 __global__ void __launch_bounds__(kBlock) k_csc_count_groups(Ctx C, CompactCtx K, GroupGrid g) {
@@ -86,7 +97,11 @@ __global__ void __launch_bounds__(kBlock) k_csc_count_long(Ctx C, CompactCtx K) 
     int32_t c = 0;
     for (int32_t k = ch.begin + threadIdx.x; k < ch.end; k += kBlock) c += C.rkind[C.T.idx[k]] == RK_KEPT;
     c = block_sum_int(c);
-    if (threadIdx.x == 0) K.cht_cnt[blockIdx.x] = c;
+    if (threadIdx.x == 0) {
+        K.cht_cnt[blockIdx.x] = c;
+        mark_tile(K.tile_t, ch.begin, ch.end, ch.seg);
+        if (ch.begin == C.T.ptr[ch.seg]) K.c_ch0[ch.seg] = blockIdx.x;
+    }
 }
 
 // per long segment: chunk offsets (prefix in chunk order) and the total
@@ -155,9 +170,11 @@ __device__ __forceinline__ void csr_count_group(const Ctx &C, const CompactCtx &
     bool keep = false;
     if (valid) {
         keep = C.rkind[i] == RK_KEPT && !K.lp_dead[lp_of_row(C, i)];
+        const int32_t pb = C.A.ptr[i], pe = C.A.ptr[i + 1];
+        if (lane == 0) mark_tile(K.tile_a, pb, pe, i);
         if (keep) {
-            beg = C.A.ptr[i];
-            end = C.A.ptr[i + 1];
+            beg = pb;
+            end = pe;
         }
     }
     int32_t cnt = 0;
@@ -223,7 +240,11 @@ __global__ void __launch_bounds__(kBlock) k_csr_count_long(Ctx C, CompactCtx K) 
     if (threadIdx.x == 0) {
         K.chr_cnt[blockIdx.x] = cnt;
         K.chr_shift[blockIdx.x] = sh;
-        if (ch.begin == C.A.ptr[i]) K.r_keep[i] = keep;  // first chunk writes the flag
+        mark_tile(K.tile_a, ch.begin, ch.end, i);
+        if (ch.begin == C.A.ptr[i]) {  // the first chunk writes the flag
+            K.r_keep[i] = keep;
+            K.r_ch0[i] = blockIdx.x;
+        }
     }
 }
 
@@ -266,157 +287,190 @@ __global__ void __launch_bounds__(kBlock) k_colvec(Ctx C, CompactCtx K) {
 __global__ void k_zero_ptr(int32_t *p) { p[0] = 0; }
 
 // ---------------------------------------------------------------- scatter
-// ordered compaction of the kept entries of one segment by a lane group
-template <int W, class Keep, class Emit>
-__device__ __forceinline__ void group_scatter(const int32_t *idx, int32_t beg, int32_t end, int32_t out0, Keep keep,
-                                              Emit emit) {
-    const unsigned mask = group_mask<W>();
-    const int lane = threadIdx.x & (W - 1);
-    int32_t base = out0;
-    for (int32_t k0 = beg; k0 < end; k0 += W) {
-        const int32_t k = k0 + lane;
-        const bool in = k < end;
-        const int32_t t = in ? idx[k] : 0;
-        const bool kp = in && keep(t);
-        const unsigned b = group_bits<W>(__ballot_sync(mask, kp));
-        if (kp) emit(k, t, base + __popc(b & ((1u << lane) - 1u)));
-        base += __popc(b);
-    }
-}
+// Flat ordered compaction of all entries.  Segments of at most kFlatTile
+// entries, and the chunks of the long ones, are the units.  Block t takes the
+// entries [t T, t T + T) of the matrix, T = kFlatTile, in three phases:
+//   1. blocked: each thread finds the segment of each of its 16 consecutive
+//      entries (a binary search between the segments of tile t and t + 1,
+//      then a walk) and records the in-tile position of the first entry of
+//      that unit, or -1 if the segment is dropped;
+//   2. striped (coalesced loads): keep flags = segment recorded and the other
+//      index kept; one ballot per warp and step, exclusive scan of the counts;
+//   3. striped: a kept entry x of unit s goes to
+//         off[s] + (kept entries of s before x),
+//      where the second term is scan(x) - scan(first in-tile entry of s) plus,
+//      for a unit that started in an earlier tile, len[s] minus its kept
+//      entries in this tile (it ends in this tile: it has at most T entries).
+struct FlatArgs {
+    const int32_t *ptr, *idx;
+    const double *val;
+    int32_t nnz, cnt, ntiles;
+    const int32_t *seg_keep, *seg_off, *seg_len;  // per segment: kept, new offset, kept entries
+    const int32_t *seg_ch0;                       // per long segment: its first chunk
+    const int32_t *ch_off, *ch_cnt;               // per chunk: kept entries of its segment before it, its own
+    const int32_t *oth_keep, *oth_pos;            // per index of the other dimension: kept, new index
+    const int32_t *tile_seg;                      // per tile: segment of its first entry
+    int32_t *out_idx;
+    double *out_val;
+};
 
-template <int W>
-__device__ __forceinline__ void csr_scatter_group(const Ctx &C, const CompactCtx &K, int32_t i, bool valid) {
-    int32_t beg = 0, end = 0, out0 = 0;
-    if (valid && K.r_keep[i]) {
-        beg = C.A.ptr[i];
-        end = C.A.ptr[i + 1];
-        out0 = K.r_off[i];
-    }
-    const int32_t *ck = K.c_keep;
-    const int32_t *cpos = K.c_pos;
-    const double *val = C.A.val;
-    int32_t *ci2 = K.ci2;
-    double *rv2 = K.rv2;
-    group_scatter<W>(C.A.idx, beg, end, out0, [ck](int32_t j) { return ck[j] != 0; },
-                     [=](int32_t k, int32_t j, int32_t p) {
-                         ci2[p] = cpos[j];
-                         rv2[p] = val[k];
-                     });
-}
+constexpr int kFlatPer = kFlatTile / kBlock;  // entries per thread
+constexpr int kFlatWords = kFlatTile / 32;    // ballot words per tile
 
-template <int W>
-__device__ __forceinline__ void csc_scatter_group(const Ctx &C, const CompactCtx &K, int32_t j, bool valid) {
-    int32_t beg = 0, end = 0, out0 = 0;
-    if (valid && K.c_keep[j]) {
-        beg = C.T.ptr[j];
-        end = C.T.ptr[j + 1];
-        out0 = K.c_off[j];
-    }
-    const int32_t *rk = K.r_keep;
-    const int32_t *rpos = K.r_pos;
-    const double *val = C.T.val;
-    int32_t *ri2 = K.ri2;
-    double *cv2 = K.cv2;
-    group_scatter<W>(C.T.idx, beg, end, out0, [rk](int32_t r) { return rk[r] != 0; },
-                     [=](int32_t k, int32_t r, int32_t p) {
-                         ri2[p] = rpos[r];
-                         cv2[p] = val[k];
-                     });
-}
+__global__ void __launch_bounds__(kBlock) k_scatter_flat(FlatArgs F) {
+    __shared__ int16_t s_start[kFlatTile];
+    __shared__ int32_t s_raw[kFlatTile];
+    __shared__ unsigned s_bal[kFlatWords + 1];
+    __shared__ int32_t s_cb[kFlatWords + 1];
+    __shared__ int32_t s_re;
+    __shared__ int32_t s_fp;
+    const int t = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t k0 = (int32_t)((int64_t)t * kFlatTile);
+    const int32_t len = F.nnz - k0 < kFlatTile ? F.nnz - k0 : kFlatTile;
 
-__global__ void __launch_bounds__(kBlock) k_csr_scatter_groups(Ctx C, CompactCtx K, GroupGrid g) {
-    const int c = grid_class(g, blockIdx.x);
-    const int W = 1 << c;
-    const int32_t pos = C.A.cls_start[c] + (blockIdx.x - g.blk_start[c]) * (kBlock / W) + threadIdx.x / W;
-    const bool valid = pos < C.A.cls_start[c + 1];
-    const int32_t i = valid ? C.A.order[pos] : 0;
-    switch (c) {
-        case 0: csr_scatter_group<1>(C, K, i, valid); break;
-        case 1: csr_scatter_group<2>(C, K, i, valid); break;
-        case 2: csr_scatter_group<4>(C, K, i, valid); break;
-        case 3: csr_scatter_group<8>(C, K, i, valid); break;
-        case 4: csr_scatter_group<16>(C, K, i, valid); break;
-        default: csr_scatter_group<32>(C, K, i, valid); break;
-    }
-}
-
-__global__ void __launch_bounds__(kBlock) k_csc_scatter_groups(Ctx C, CompactCtx K, GroupGrid g) {
-    const int c = grid_class(g, blockIdx.x);
-    const int W = 1 << c;
-    const int32_t pos = C.T.cls_start[c] + (blockIdx.x - g.blk_start[c]) * (kBlock / W) + threadIdx.x / W;
-    const bool valid = pos < C.T.cls_start[c + 1];
-    const int32_t j = valid ? C.T.order[pos] : 0;
-    switch (c) {
-        case 0: csc_scatter_group<1>(C, K, j, valid); break;
-        case 1: csc_scatter_group<2>(C, K, j, valid); break;
-        case 2: csc_scatter_group<4>(C, K, j, valid); break;
-        case 3: csc_scatter_group<8>(C, K, j, valid); break;
-        case 4: csc_scatter_group<16>(C, K, j, valid); break;
-        default: csc_scatter_group<32>(C, K, j, valid); break;
-    }
-}
-
-// ordered compaction of one chunk by a whole block
-template <class Keep, class Emit>
-__device__ __forceinline__ void block_scatter(const int32_t *idx, int32_t beg, int32_t end, int32_t out0, Keep keep,
-                                              Emit emit) {
-    __shared__ int32_t s_w[kBlock / 32 + 1];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t base = out0;
-    for (int32_t k0 = beg; k0 < end; k0 += kBlock) {
-        const int32_t k = k0 + threadIdx.x;
-        const bool in = k < end;
-        const int32_t t = in ? idx[k] : 0;
-        const bool kp = in && keep(t);
-        const unsigned b = __ballot_sync(0xffffffffu, kp);
-        if (lane == 0) s_w[warp] = __popc(b);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int32_t acc = 0;
-            for (int w = 0; w < kBlock / 32; w++) {
-                const int32_t v = s_w[w];
-                s_w[w] = acc;
-                acc += v;
-            }
-            s_w[kBlock / 32] = acc;
+    // 1. segment of each entry, blocked.  A long segment is taken as its
+    //    chunks of kChunk entries (consecutive chunk ids from seg_ch0), each
+    //    with its own offset and kept count from the count pass.
+    const int x0 = tid * kFlatPer;
+    if (tid == 0) s_fp = 0;
+    if (x0 < len) {
+        int32_t lo = F.tile_seg[t];
+        int32_t hi = t + 1 < F.ntiles ? F.tile_seg[t + 1] : F.cnt - 1;
+        const int32_t k = k0 + x0;
+        while (lo < hi) {  // largest segment r in [lo, hi] with ptr[r] <= k
+            const int32_t mid = lo + ((hi - lo + 1) >> 1);
+            if (__ldg(F.ptr + mid) <= k) lo = mid;
+            else hi = mid - 1;
         }
-        __syncthreads();
-        if (kp) emit(k, t, base + s_w[warp] + __popc(b & ((1u << lane) - 1u)));
-        base += s_w[kBlock / 32];
-        __syncthreads();
+        int32_t r = lo;
+        int32_t pb = __ldg(F.ptr + r), pe = __ldg(F.ptr + r + 1);
+        bool emit = F.seg_keep[r] != 0;
+        int32_t vb, ve, voff, vlen;  // the (virtual) segment of entry kk: [vb, ve), offset, kept entries
+        auto enter = [&](int32_t kk) {
+            if (pe - pb < kLongMin) {
+                vb = pb;
+                ve = pe;
+                voff = F.seg_off[r];
+                vlen = F.seg_len[r];
+            } else {
+                const int32_t q = (kk - pb) / kChunk;
+                const int32_t ch = F.seg_ch0[r] + q;
+                vb = pb + q * kChunk;
+                ve = min(vb + kChunk, pe);
+                voff = F.seg_off[r] + F.ch_off[ch];
+                vlen = F.ch_cnt[ch];
+            }
+        };
+        if (emit) enter(k);
+        else ve = pe;
+#pragma unroll 4
+        for (int e = 0; e < kFlatPer; e++) {
+            const int x = x0 + e;
+            if (x >= len) {
+                s_start[x] = -1;
+                continue;
+            }
+            const int32_t kk = k0 + x;
+            if (ve <= kk) {
+                if (pe <= kk) {  // next non-empty segment
+                    do {
+                        r++;
+                        pb = pe;
+                        pe = __ldg(F.ptr + r + 1);
+                    } while (pe <= kk);
+                    emit = F.seg_keep[r] != 0;
+                }
+                if (emit) enter(kk);  // the segment, or the next chunk of a long one
+                else ve = pe;
+            }
+            if (!emit) {
+                s_start[x] = -1;
+                continue;
+            }
+            const int32_t rs = vb - k0;
+            const int xs = rs > 0 ? rs : 0;
+            s_start[x] = (int16_t)xs;
+            if (x == xs) {
+                int32_t raw = voff;
+                if (rs < 0) {  // started in an earlier tile (only entry 0 of thread 0)
+                    raw += vlen;
+                    s_re = ve - k0;
+                    s_fp = 1;
+                }
+                s_raw[x] = raw;
+            }
+        }
+    } else {
+        for (int e = 0; e < kFlatPer; e++) s_start[x0 + e] = -1;
     }
-}
+    __syncthreads();
 
-__global__ void __launch_bounds__(kBlock) k_csr_scatter_long(Ctx C, CompactCtx K) {
-    const Chunk ch = C.A.chunks[blockIdx.x];
-    if (!K.r_keep[ch.seg]) return;
-    const int32_t out0 = K.r_off[ch.seg] + K.chr_off[blockIdx.x];
-    const int32_t *ck = K.c_keep;
-    const int32_t *cpos = K.c_pos;
-    const double *val = C.A.val;
-    int32_t *ci2 = K.ci2;
-    double *rv2 = K.rv2;
-    block_scatter(C.A.idx, ch.begin, ch.end, out0, [ck](int32_t j) { return ck[j] != 0; },
-                  [=](int32_t k, int32_t j, int32_t p) {
-                      ci2[p] = cpos[j];
-                      rv2[p] = val[k];
-                  });
-}
+    // 2. keep flags, striped
+    int32_t jr[kFlatPer];
+    double vr[kFlatPer];
+#pragma unroll
+    for (int i = 0; i < kFlatPer; i++) {
+        const int x = i * kBlock + tid;
+        jr[i] = -1;
+        vr[i] = 0.0;
+        if (x < len && s_start[x] >= 0) {
+            jr[i] = F.idx[k0 + x];
+            vr[i] = F.val[k0 + x];
+        }
+    }
+    unsigned bal[kFlatPer];
+#pragma unroll
+    for (int i = 0; i < kFlatPer; i++) {
+        const bool kp = jr[i] >= 0 && F.oth_keep[jr[i]] != 0;
+        bal[i] = __ballot_sync(0xffffffffu, kp);
+        if (lane == 0) s_bal[i * (kBlock / 32) + warp] = bal[i];
+    }
+    __syncthreads();
+    if (warp == 0) {  // exclusive scan of the ballot counts
+        constexpr int per = kFlatWords / 32;
+        int32_t c[per], tot = 0;
+#pragma unroll
+        for (int q = 0; q < per; q++) {
+            c[q] = __popc(s_bal[lane * per + q]);
+            tot += c[q];
+        }
+        int32_t inc = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        int32_t acc = inc - tot;
+#pragma unroll
+        for (int q = 0; q < per; q++) {
+            s_cb[lane * per + q] = acc;
+            acc += c[q];
+        }
+        if (lane == 31) {
+            s_cb[kFlatWords] = inc;
+            s_bal[kFlatWords] = 0u;
+        }
+    }
+    __syncthreads();
 
-__global__ void __launch_bounds__(kBlock) k_csc_scatter_long(Ctx C, CompactCtx K) {
-    const Chunk ch = C.T.chunks[blockIdx.x];
-    if (!K.c_keep[ch.seg]) return;
-    const int32_t out0 = K.c_off[ch.seg] + K.cht_off[blockIdx.x];
-    const int32_t *rk = K.r_keep;
-    const int32_t *rpos = K.r_pos;
-    const double *val = C.T.val;
-    int32_t *ri2 = K.ri2;
-    double *cv2 = K.cv2;
-    block_scatter(C.T.idx, ch.begin, ch.end, out0, [rk](int32_t r) { return rk[r] != 0; },
-                  [=](int32_t k, int32_t r, int32_t p) {
-                      ri2[p] = rpos[r];
-                      cv2[p] = val[k];
-                  });
+    // 3. positions and copies, striped
+    auto scan_at = [&](int y) {  // kept entries of the tile before position y (0 <= y <= T)
+        const int q = y >> 5;
+        return s_cb[q] + __popc(s_bal[q] & ((1u << (y & 31)) - 1u));
+    };
+    const int32_t fix = s_fp ? scan_at(s_re) : 0;
+#pragma unroll
+    for (int i = 0; i < kFlatPer; i++) {
+        if (!((bal[i] >> lane) & 1u)) continue;
+        const int x = i * kBlock + tid;
+        const int xs = s_start[x];
+        const int32_t here = s_cb[i * (kBlock / 32) + warp] + __popc(bal[i] & ((1u << lane) - 1u));
+        int32_t p = s_raw[xs] - scan_at(xs) + here;
+        if (xs == 0) p -= fix;
+        F.out_idx[p] = F.oth_pos[jr[i]];
+        F.out_val[p] = vr[i];
+    }
 }
 
 // ---------------------------------------------------------- objective constant
@@ -486,21 +540,20 @@ void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s) {
     }
 }
 
-void launch_compact_scatter(const Ctx &C, const CompactCtx &K, int32_t m_new, int32_t n_new, cudaStream_t s) {
-    (void)m_new;
-    (void)n_new;
+void launch_compact_scatter(const Ctx &C, const CompactCtx &K, int32_t nnz, cudaStream_t s) {
     (k_zero_ptr<<<1, 1, 0, s>>>(K.rp2), note_launch());
     (k_zero_ptr<<<1, 1, 0, s>>>(K.cp2), note_launch());
     if (C.m > 0) (k_rowvec<<<blocks_for(C.m, kBlock), kBlock, 0, s>>>(C, K), note_launch());
     if (C.n > 0) (k_colvec<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C, K), note_launch());
-    const GroupGrid ga = group_grid(C.A);
-    if (ga.blk_start[6] > 0) (k_csr_scatter_groups<<<ga.blk_start[6], kBlock, 0, s>>>(C, K, ga), note_launch());
-    if (C.A.cls_start[7] > C.A.cls_start[6] && C.A.nchunks > 0)
-        (k_csr_scatter_long<<<C.A.nchunks, kBlock, 0, s>>>(C, K), note_launch());
-    const GroupGrid gt = group_grid(C.T);
-    if (gt.blk_start[6] > 0) (k_csc_scatter_groups<<<gt.blk_start[6], kBlock, 0, s>>>(C, K, gt), note_launch());
-    if (C.T.cls_start[7] > C.T.cls_start[6] && C.T.nchunks > 0)
-        (k_csc_scatter_long<<<C.T.nchunks, kBlock, 0, s>>>(C, K), note_launch());
+    const int32_t ntiles = (int32_t)(((int64_t)nnz + kFlatTile - 1) / kFlatTile);
+    if (ntiles > 0) {
+        FlatArgs fa{C.A.ptr, C.A.idx, C.A.val, nnz, C.m, ntiles, K.r_keep, K.r_off, K.r_len, K.r_ch0,
+                    K.chr_off, K.chr_cnt, K.c_keep, K.c_pos, K.tile_a, K.ci2, K.rv2};
+        (k_scatter_flat<<<ntiles, kBlock, 0, s>>>(fa), note_launch());
+        FlatArgs ft{C.T.ptr, C.T.idx, C.T.val, nnz, C.n, ntiles, K.c_keep, K.c_off, K.c_len, K.c_ch0,
+                    K.cht_off, K.cht_cnt, K.r_keep, K.r_pos, K.tile_t, K.ri2, K.cv2};
+        (k_scatter_flat<<<ntiles, kBlock, 0, s>>>(ft), note_launch());
+    }
 }
 
 void launch_offset(const Ctx &C, const CompactCtx &K, cudaStream_t s) {

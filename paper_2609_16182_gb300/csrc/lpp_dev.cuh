@@ -20,6 +20,10 @@ constexpr int kChunk = 4096;        // entries per chunk of a long segment
 constexpr int kNumClass = 7;        // 0..5: groups of 1<<c lanes per segment, 6: chunked
 constexpr int kNone = 0x7fffffff;   // empty slot of an atomicMin index
 constexpr int kScanTile = 2048;     // elements per tile of the device-wide scans
+constexpr int kFlatTile = 4096;     // entries per tile of the flat compaction scatter
+// a segment the flat scatter copies (at most kFlatTile entries) then spans at
+// most two tiles, and a chunk of a long segment holds at most one tile start
+static_assert(kLongMin - 1 <= kFlatTile && kChunk <= kFlatTile, "flat tile too small");
 
 // Segment class by length: W = 1 << class lanes per segment for class <= 5,
 // chunks of kChunk entries for class 6.  A segment's summation order depends
@@ -136,6 +140,8 @@ struct CompactCtx {
     int32_t *lp_first, *lp_last;               // [nlp] current column range of each LP
     uint8_t *lp_dead;                          // [nlp] a verdict was reached, or retired
     const uint8_t *lp_retired;                 // [nlp] finished LPs leaving the arena (NULL: none)
+    int32_t *tile_a, *tile_t;                  // per flat tile: the CSR / CSC segment holding its first entry
+    int32_t *r_ch0, *c_ch0;                    // per long row / column: its first chunk
     // next buffers
     int32_t *rp2, *ci2;
     double *rv2;

@@ -290,6 +290,10 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
     K.lp_first = pool.alloc<int32_t>(nlp);
     K.lp_last = pool.alloc<int32_t>(nlp);
     K.lp_dead = lp_dead;
+    K.tile_a = pool.alloc<int32_t>(nnz0 / kFlatTile + 2);
+    K.tile_t = pool.alloc<int32_t>(nnz0 / kFlatTile + 2);
+    K.r_ch0 = pool.alloc<int32_t>(m0 + 1);
+    K.c_ch0 = pool.alloc<int32_t>(n0 + 1);
     rec_rk = pool.alloc<int32_t>(m0);
     rec_rr = pool.alloc<int32_t>(m0);
     rec_ra = pool.alloc<int32_t>(m0);
@@ -572,7 +576,7 @@ void Engine::compact(int32_t round) {
     launch_offset(C, K, s);
     (k_sizes<<<1, 1, 0, s>>>(K, m, n, st), note_launch());
     tbegin(F_SCATTER, 24.0 * nnz * 2 + 48.0 * (m + n));
-    launch_compact_scatter(C, K, 0, 0, s);
+    launch_compact_scatter(C, K, (int32_t)nnz, s);
     tend();
     LPP_CUDA(cudaGetLastError());
     // the next buffers become current; sizes and schedules are read back at

@@ -73,7 +73,7 @@ void launch_s5_leader(const Ctx &C, cudaStream_t s);
 
 // -------------------------------------------------------------- k_compact.cu
 void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s);
-void launch_compact_scatter(const Ctx &C, const CompactCtx &K, int32_t m_new, int32_t n_new, cudaStream_t s);
+void launch_compact_scatter(const Ctx &C, const CompactCtx &K, int32_t nnz, cudaStream_t s);
 void launch_offset(const Ctx &C, const CompactCtx &K, cudaStream_t s);
 
 }  // namespace lpp
