@@ -253,8 +253,9 @@ __global__ void __launch_bounds__(kBlock) k_rowvec(Ctx C, CompactCtx K) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= C.m) return;
     if (i == C.m - 1) K.rp2[K.r_pos[C.m]] = K.r_off[C.m];
-    if (!K.r_keep[i]) return;
     const int32_t p = K.r_pos[i];
+    K.r_new[i] = K.r_keep[i] ? p : -1;
+    if (!K.r_keep[i]) return;
     const double sh = K.shift[i];
     const double Lv = C.L[i], Uv = C.U[i];
     K.L2[p] = is_fin(Lv) ? Lv - sh : Lv;
@@ -274,8 +275,9 @@ __global__ void __launch_bounds__(kBlock) k_colvec(Ctx C, CompactCtx K) {
     const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= C.n) return;
     if (j == C.n - 1) K.cp2[K.c_pos[C.n]] = K.c_off[C.n];
-    if (!K.c_keep[j]) return;
     const int32_t p = K.c_pos[j];
+    K.c_new[j] = K.c_keep[j] ? p : -1;
+    if (!K.c_keep[j]) return;
     K.lu2[p] = C.lu[j];
     K.c2[p] = C.c[j];
     K.cmap2[p] = C.cmap[j];
@@ -288,14 +290,16 @@ __global__ void k_zero_ptr(int32_t *p) { p[0] = 0; }
 
 // ---------------------------------------------------------------- scatter
 // Flat ordered compaction of all entries.  Segments of at most kFlatTile
-// entries, and the chunks of the long ones, are the units.  Block t takes the
-// entries [t T, t T + T) of the matrix, T = kFlatTile, in three phases:
-//   1. blocked: each thread finds the segment of each of its 16 consecutive
-//      entries (a binary search between the segments of tile t and t + 1,
-//      then a walk) and records the in-tile position of the first entry of
-//      that unit, or -1 if the segment is dropped;
-//   2. striped (coalesced loads): keep flags = segment recorded and the other
-//      index kept; one ballot per warp and step, exclusive scan of the counts;
+// entries, and the chunks of kChunk entries of the long ones, are the units.
+// Block t takes the entries [t T, t T + T) of the matrix, T = kFlatTile:
+//   1. one thread per segment between the segments of the entries t T and
+//      (t + 1) T (coalesced, independent loads) marks the first in-tile entry
+//      of each of its units in the tile, with a keep bit and the unit's base;
+//      a block max-scan of the marks gives every entry the first in-tile
+//      entry of its unit, or -1 if its segment is dropped;
+//   2. striped (coalesced): keep = unit kept and the other index kept (one
+//      gather of its new index, -1 if dropped); one ballot per warp and
+//      step, exclusive scan of the counts;
 //   3. striped: a kept entry x of unit s goes to
 //         off[s] + (kept entries of s before x),
 //      where the second term is scan(x) - scan(first in-tile entry of s) plus,
@@ -308,7 +312,7 @@ struct FlatArgs {
     const int32_t *seg_keep, *seg_off, *seg_len;  // per segment: kept, new offset, kept entries
     const int32_t *seg_ch0;                       // per long segment: its first chunk
     const int32_t *ch_off, *ch_cnt;               // per chunk: kept entries of its segment before it, its own
-    const int32_t *oth_keep, *oth_pos;            // per index of the other dimension: kept, new index
+    const int32_t *oth_new;                       // per index of the other dimension: new index, -1 if dropped
     const int32_t *tile_seg;                      // per tile: segment of its first entry
     int32_t *out_idx;
     double *out_val;
@@ -318,10 +322,11 @@ constexpr int kFlatPer = kFlatTile / kBlock;  // entries per thread
 constexpr int kFlatWords = kFlatTile / 32;    // ballot words per tile
 
 __global__ void __launch_bounds__(kBlock) k_scatter_flat(FlatArgs F) {
-    __shared__ int16_t s_start[kFlatTile];
+    __shared__ __align__(16) int16_t s_start[kFlatTile];
     __shared__ int32_t s_raw[kFlatTile];
     __shared__ unsigned s_bal[kFlatWords + 1];
     __shared__ int32_t s_cb[kFlatWords + 1];
+    __shared__ int32_t s_wmax[kBlock / 32];
     __shared__ int32_t s_re;
     __shared__ int32_t s_fp;
     const int t = blockIdx.x;
@@ -329,102 +334,102 @@ __global__ void __launch_bounds__(kBlock) k_scatter_flat(FlatArgs F) {
     const int32_t k0 = (int32_t)((int64_t)t * kFlatTile);
     const int32_t len = F.nnz - k0 < kFlatTile ? F.nnz - k0 : kFlatTile;
 
-    // 1. segment of each entry, blocked.  A long segment is taken as its
-    //    chunks of kChunk entries (consecutive chunk ids from seg_ch0), each
-    //    with its own offset and kept count from the count pass.
-    const int x0 = tid * kFlatPer;
+    // 1a. no marks; 1b. one thread per segment marks its units
+    {
+        int4 *w = reinterpret_cast<int4 *>(s_start);
+        for (int q = tid; q < kFlatTile / 8; q += kBlock) w[q] = make_int4(-1, -1, -1, -1);
+    }
     if (tid == 0) s_fp = 0;
-    if (x0 < len) {
-        int32_t lo = F.tile_seg[t];
-        int32_t hi = t + 1 < F.ntiles ? F.tile_seg[t + 1] : F.cnt - 1;
-        const int32_t k = k0 + x0;
-        while (lo < hi) {  // largest segment r in [lo, hi] with ptr[r] <= k
-            const int32_t mid = lo + ((hi - lo + 1) >> 1);
-            if (__ldg(F.ptr + mid) <= k) lo = mid;
-            else hi = mid - 1;
+    __syncthreads();
+    const int32_t lo = F.tile_seg[t];
+    const int32_t hi = t + 1 < F.ntiles ? F.tile_seg[t + 1] : F.cnt - 1;
+    const int32_t k1 = k0 + len;
+    for (int32_t r = lo + tid; r <= hi; r += kBlock) {
+        const int32_t pb = __ldg(F.ptr + r), pe = __ldg(F.ptr + r + 1);
+        if (pe <= pb || pb >= k1) continue;  // empty, or after the tile
+        const bool emit = F.seg_keep[r] != 0;
+        // units of r that meet the tile: the segment, or chunks q0..q1
+        int32_t q0 = 0, q1 = 0;
+        const bool lng = pe - pb >= kLongMin;
+        if (lng) {
+            q0 = ((pb > k0 ? pb : k0) - pb) / kChunk;
+            q1 = ((pe < k1 ? pe : k1) - 1 - pb) / kChunk;
         }
-        int32_t r = lo;
-        int32_t pb = __ldg(F.ptr + r), pe = __ldg(F.ptr + r + 1);
-        bool emit = F.seg_keep[r] != 0;
-        int32_t vb, ve, voff, vlen;  // the (virtual) segment of entry kk: [vb, ve), offset, kept entries
-        auto enter = [&](int32_t kk) {
-            if (pe - pb < kLongMin) {
-                vb = pb;
-                ve = pe;
-                voff = F.seg_off[r];
-                vlen = F.seg_len[r];
-            } else {
-                const int32_t q = (kk - pb) / kChunk;
-                const int32_t ch = F.seg_ch0[r] + q;
-                vb = pb + q * kChunk;
-                ve = min(vb + kChunk, pe);
-                voff = F.seg_off[r] + F.ch_off[ch];
-                vlen = F.ch_cnt[ch];
-            }
-        };
-        if (emit) enter(k);
-        else ve = pe;
-#pragma unroll 4
-        for (int e = 0; e < kFlatPer; e++) {
-            const int x = x0 + e;
-            if (x >= len) {
-                s_start[x] = -1;
-                continue;
-            }
-            const int32_t kk = k0 + x;
-            if (ve <= kk) {
-                if (pe <= kk) {  // next non-empty segment
-                    do {
-                        r++;
-                        pb = pe;
-                        pe = __ldg(F.ptr + r + 1);
-                    } while (pe <= kk);
-                    emit = F.seg_keep[r] != 0;
+        for (int32_t q = q0; q <= q1; q++) {
+            const int32_t vb = pb + q * kChunk;
+            const int32_t ve = lng ? min(vb + kChunk, pe) : pe;
+            const int32_t xs = vb > k0 ? vb - k0 : 0;
+            s_start[xs] = (int16_t)(2 * xs + (emit ? 1 : 0));
+            if (emit) {
+                int32_t raw, ln;
+                if (lng) {
+                    const int32_t ch = F.seg_ch0[r] + q;
+                    raw = F.seg_off[r] + F.ch_off[ch];
+                    ln = F.ch_cnt[ch];
+                } else {
+                    raw = F.seg_off[r];
+                    ln = F.seg_len[r];
                 }
-                if (emit) enter(kk);  // the segment, or the next chunk of a long one
-                else ve = pe;
-            }
-            if (!emit) {
-                s_start[x] = -1;
-                continue;
-            }
-            const int32_t rs = vb - k0;
-            const int xs = rs > 0 ? rs : 0;
-            s_start[x] = (int16_t)xs;
-            if (x == xs) {
-                int32_t raw = voff;
-                if (rs < 0) {  // started in an earlier tile (only entry 0 of thread 0)
-                    raw += vlen;
+                if (vb < k0) {  // the unit holding entry k0
+                    raw += ln;
                     s_re = ve - k0;
                     s_fp = 1;
                 }
-                s_raw[x] = raw;
+                s_raw[xs] = raw;
             }
         }
-    } else {
-        for (int e = 0; e < kFlatPer; e++) s_start[x0 + e] = -1;
+    }
+    __syncthreads();
+    // 1c. inclusive max-scan of the marks (blocked, 16 per thread)
+    {
+        const int x0 = tid * kFlatPer;
+        int4 *w = reinterpret_cast<int4 *>(s_start + x0);
+        int4 a = w[0], b = w[1];
+        int16_t v[kFlatPer];
+        memcpy(v, &a, 16);
+        memcpy(v + 8, &b, 16);
+        int32_t run = -1;
+#pragma unroll
+        for (int e = 0; e < kFlatPer; e++) {
+            run = v[e] > run ? v[e] : run;
+        }
+        int32_t inc = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o && y > inc) inc = y;
+        }
+        if (lane == 31) s_wmax[warp] = inc;
+        int32_t prev = __shfl_up_sync(0xffffffffu, inc, 1);
+        if (lane == 0) prev = -1;
+        __syncthreads();
+        for (int q = 0; q < warp; q++) prev = s_wmax[q] > prev ? s_wmax[q] : prev;
+        run = prev;
+#pragma unroll
+        for (int e = 0; e < kFlatPer; e++) {
+            run = v[e] > run ? v[e] : run;
+            v[e] = (x0 + e < len && (run & 1)) ? (int16_t)(run >> 1) : (int16_t)-1;
+        }
+        memcpy(&a, v, 16);
+        memcpy(&b, v + 8, 16);
+        w[0] = a;
+        w[1] = b;
     }
     __syncthreads();
 
     // 2. keep flags, striped
-    int32_t jr[kFlatPer];
-    double vr[kFlatPer];
+    int32_t jn[kFlatPer];
 #pragma unroll
     for (int i = 0; i < kFlatPer; i++) {
         const int x = i * kBlock + tid;
-        jr[i] = -1;
-        vr[i] = 0.0;
-        if (x < len && s_start[x] >= 0) {
-            jr[i] = F.idx[k0 + x];
-            vr[i] = F.val[k0 + x];
-        }
+        jn[i] = -1;
+        if (x < len && s_start[x] >= 0) jn[i] = F.idx[k0 + x];
     }
-    unsigned bal[kFlatPer];
 #pragma unroll
     for (int i = 0; i < kFlatPer; i++) {
-        const bool kp = jr[i] >= 0 && F.oth_keep[jr[i]] != 0;
-        bal[i] = __ballot_sync(0xffffffffu, kp);
-        if (lane == 0) s_bal[i * (kBlock / 32) + warp] = bal[i];
+        if (jn[i] >= 0) jn[i] = F.oth_new[jn[i]];
+        const unsigned bal = __ballot_sync(0xffffffffu, jn[i] >= 0);
+        if (lane == 0) s_bal[i * (kBlock / 32) + warp] = bal;
     }
     __syncthreads();
     if (warp == 0) {  // exclusive scan of the ballot counts
@@ -462,14 +467,13 @@ __global__ void __launch_bounds__(kBlock) k_scatter_flat(FlatArgs F) {
     const int32_t fix = s_fp ? scan_at(s_re) : 0;
 #pragma unroll
     for (int i = 0; i < kFlatPer; i++) {
-        if (!((bal[i] >> lane) & 1u)) continue;
+        if (jn[i] < 0) continue;
         const int x = i * kBlock + tid;
         const int xs = s_start[x];
-        const int32_t here = s_cb[i * (kBlock / 32) + warp] + __popc(bal[i] & ((1u << lane) - 1u));
-        int32_t p = s_raw[xs] - scan_at(xs) + here;
+        int32_t p = s_raw[xs] - scan_at(xs) + scan_at(x);
         if (xs == 0) p -= fix;
-        F.out_idx[p] = F.oth_pos[jr[i]];
-        F.out_val[p] = vr[i];
+        F.out_idx[p] = jn[i];
+        F.out_val[p] = F.val[k0 + x];
     }
 }
 
@@ -548,10 +552,10 @@ void launch_compact_scatter(const Ctx &C, const CompactCtx &K, int32_t nnz, cuda
     const int32_t ntiles = (int32_t)(((int64_t)nnz + kFlatTile - 1) / kFlatTile);
     if (ntiles > 0) {
         FlatArgs fa{C.A.ptr, C.A.idx, C.A.val, nnz, C.m, ntiles, K.r_keep, K.r_off, K.r_len, K.r_ch0,
-                    K.chr_off, K.chr_cnt, K.c_keep, K.c_pos, K.tile_a, K.ci2, K.rv2};
+                    K.chr_off, K.chr_cnt, K.c_new, K.tile_a, K.ci2, K.rv2};
         (k_scatter_flat<<<ntiles, kBlock, 0, s>>>(fa), note_launch());
         FlatArgs ft{C.T.ptr, C.T.idx, C.T.val, nnz, C.n, ntiles, K.c_keep, K.c_off, K.c_len, K.c_ch0,
-                    K.cht_off, K.cht_cnt, K.r_keep, K.r_pos, K.tile_t, K.ri2, K.cv2};
+                    K.cht_off, K.cht_cnt, K.r_new, K.tile_t, K.ri2, K.cv2};
         (k_scatter_flat<<<ntiles, kBlock, 0, s>>>(ft), note_launch());
     }
 }

@@ -142,6 +142,7 @@ struct CompactCtx {
     const uint8_t *lp_retired;                 // [nlp] finished LPs leaving the arena (NULL: none)
     int32_t *tile_a, *tile_t;                  // per flat tile: the CSR / CSC segment holding its first entry
     int32_t *r_ch0, *c_ch0;                    // per long row / column: its first chunk
+    int32_t *r_new, *c_new;                    // new index, -1 if dropped
     // next buffers
     int32_t *rp2, *ci2;
     double *rv2;

@@ -294,6 +294,8 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
     K.tile_t = pool.alloc<int32_t>(nnz0 / kFlatTile + 2);
     K.r_ch0 = pool.alloc<int32_t>(m0 + 1);
     K.c_ch0 = pool.alloc<int32_t>(n0 + 1);
+    K.r_new = pool.alloc<int32_t>(m0 + 1);
+    K.c_new = pool.alloc<int32_t>(n0 + 1);
     rec_rk = pool.alloc<int32_t>(m0);
     rec_rr = pool.alloc<int32_t>(m0);
     rec_ra = pool.alloc<int32_t>(m0);
