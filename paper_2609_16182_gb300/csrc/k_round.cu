@@ -401,44 +401,39 @@ __global__ void __launch_bounds__(kBlock) k_colfin(Ctx C) {
 }
 
 // ------------------------------------------------------------ S5 parallel rows
-// pass 0: rows kept by S2 with >= 2 entries; later passes: rows left
-// unmatched by the previous pass (rwork == 2).  Inserts each taking part
-// into the hash table and elects the leader of its key: the first equality
-// row, else the first row (Sec. 3.2), by atomicMin on (is_ineq, row).
-__global__ void __launch_bounds__(kBlock) k_s5_insert(Ctx C, int pass) {
+// Inserts row i into the hash table of capacity cap (a power of two) and
+// elects the leader of its key: the first equality row, else the first row
+// (Sec. 3.2), by atomicMin on (is_ineq, row).  Returns the slot, -1 if the
+// table is full (an internal error: the capacity is at least twice the rows).
+__device__ __forceinline__ int32_t s5_insert_row(const Ctx &C, int32_t i, uint32_t cap) {
+    unsigned long long key = C.hrow[i];
+    if (key == 0) key = 1;
+    uint32_t sl = (uint32_t)(key ^ (key >> 32)) & (cap - 1u);
+    for (uint32_t probe = 0; probe < cap; probe++) {
+        const unsigned long long prev = atomicCAS(&C.tkey[sl], 0ULL, key);
+        if (prev == 0ULL || prev == key) {
+            const double Lv = C.L[i], Uv = C.U[i];
+            const bool eq = is_fin(Lv) && Lv == Uv;
+            const unsigned long long code = ((unsigned long long)(eq ? 0u : 1u) << 32) | (uint32_t)i;
+            atomicMin(&C.tlead[sl], code);
+            return (int32_t)sl;
+        }
+        sl = (sl + 1u) & (cap - 1u);
+    }
+    atomicOr(&C.st->err, 1);
+    return -1;
+}
+
+// first pass: rows kept by S2 with >= 2 entries take part
+__global__ void __launch_bounds__(kBlock) k_s5_insert(Ctx C) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     int32_t part = 0;
     if (i < C.m) {
-        bool take;
-        if (pass == 0) take = C.rkind[i] == RK_KEPT && C.A.ptr[i + 1] - C.A.ptr[i] >= 2;
-        else take = C.rwork[i] == 2;
         int32_t slot = -1;
-        if (take) {
-            unsigned long long key = C.hrow[i];
-            if (key == 0) key = 1;
-            const uint32_t cap = (uint32_t)C.tcap;
-            uint32_t sl = (uint32_t)(key ^ (key >> 32)) & (cap - 1u);
-            for (uint32_t probe = 0; probe < cap; probe++) {
-                const unsigned long long prev = atomicCAS(&C.tkey[sl], 0ULL, key);
-                if (prev == 0ULL || prev == key) {
-                    slot = (int32_t)sl;
-                    break;
-                }
-                sl = (sl + 1u) & (cap - 1u);
-            }
-            if (slot < 0) {
-                atomicOr(&C.st->err, 1);
-                take = false;
-            } else {
-                const double Lv = C.L[i], Uv = C.U[i];
-                const bool eq = is_fin(Lv) && Lv == Uv;
-                const unsigned long long code = ((unsigned long long)(eq ? 0u : 1u) << 32) | (uint32_t)i;
-                atomicMin(&C.tlead[slot], code);
-                part = 1;
-            }
-        }
-        C.rslot[i] = take ? slot : -1;
-        C.rwork[i] = take ? 1 : 0;
+        if (C.rkind[i] == RK_KEPT && C.A.ptr[i + 1] - C.A.ptr[i] >= 2) slot = s5_insert_row(C, i, (uint32_t)C.tcap);
+        C.rslot[i] = slot;
+        C.rwork[i] = slot >= 0 ? 1 : 0;
+        part = slot >= 0;
     }
     block_add(part, &C.st->participants);
 }
@@ -468,7 +463,7 @@ __device__ __forceinline__ void s5_accept(const Ctx &C, int32_t i, int32_t li, d
 }
 
 template <int W>
-__device__ __forceinline__ void match_group(const Ctx &C, int32_t i, bool valid, int32_t &removed,
+__device__ __forceinline__ bool match_group(const Ctx &C, int32_t i, bool valid, int32_t &removed,
                                             int32_t &unmatched) {
     const unsigned mask = group_mask<W>();
     const int lane = threadIdx.x & (W - 1);
@@ -514,6 +509,7 @@ __device__ __forceinline__ void match_group(const Ctx &C, int32_t i, bool valid,
             C.rwork[i] = 0;
         }
     }
+    return valid && lane == 0 && act && !ok;
 }
 
 __global__ void __launch_bounds__(kBlock) k_s5_match_groups(Ctx C, GroupGrid g) {
@@ -524,16 +520,18 @@ __global__ void __launch_bounds__(kBlock) k_s5_match_groups(Ctx C, GroupGrid g) 
     const int32_t pos = C.A.cls_start[c] + lb * (kBlock / W) + threadIdx.x / W;
     const bool valid = pos < C.A.cls_start[c + 1];
     const int32_t i = valid ? C.A.order[pos] : 0;
+    bool left;
     switch (c) {
-        case 0: match_group<1>(C, i, valid, removed, unmatched); break;
-        case 1: match_group<2>(C, i, valid, removed, unmatched); break;
-        case 2: match_group<4>(C, i, valid, removed, unmatched); break;
-        case 3: match_group<8>(C, i, valid, removed, unmatched); break;
-        case 4: match_group<16>(C, i, valid, removed, unmatched); break;
-        default: match_group<32>(C, i, valid, removed, unmatched); break;
+        case 0: left = match_group<1>(C, i, valid, removed, unmatched); break;
+        case 1: left = match_group<2>(C, i, valid, removed, unmatched); break;
+        case 2: left = match_group<4>(C, i, valid, removed, unmatched); break;
+        case 3: left = match_group<8>(C, i, valid, removed, unmatched); break;
+        case 4: left = match_group<16>(C, i, valid, removed, unmatched); break;
+        default: left = match_group<32>(C, i, valid, removed, unmatched); break;
     }
     block_add(removed, &C.st->rows_removed);
     block_add(unmatched, &C.st->unmatched);
+    block_append(left, i, C.s5_out_cnt, C.s5_out);
 }
 
 // long rows: one block per row of class 6 (parallel long rows are rare)
@@ -574,12 +572,91 @@ __global__ void __launch_bounds__(kBlock) k_s5_match_long(Ctx C) {
         } else if (act) {
             C.rwork[i] = 2;
             unmatched = 1;
+            C.s5_out[atomicAdd(C.s5_out_cnt, 1)] = i;
         } else {
             C.rwork[i] = 0;
         }
     }
     block_add(removed, &C.st->rows_removed);
     block_add(unmatched, &C.st->unmatched);
+}
+
+// Later passes run on the list of rows the previous pass left unmatched
+// (count *cnt, at most the launch's grid): insert, match against the new
+// leader (one warp per row; unmatched rows go to the next list), then clear
+// the slots used so that the table is empty for the next pass.  The table
+// capacity of a pass is the power of two >= 2 * count, at most C.tcap.
+__device__ __forceinline__ uint32_t s5_tail_cap(const Ctx &C, int32_t n) {
+    uint32_t cap = 1;
+    while (cap < 2u * (uint32_t)n && cap < (uint32_t)C.tcap) cap <<= 1;
+    return cap;
+}
+
+__global__ void __launch_bounds__(kBlock) k_s5_tail_insert(Ctx C, const int32_t *list, const int32_t *cnt) {
+    const int32_t n = *cnt;
+    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int32_t i = list[t];
+    C.rslot[i] = s5_insert_row(C, i, s5_tail_cap(C, n));
+}
+
+__global__ void __launch_bounds__(kBlock) k_s5_tail_match(Ctx C, const int32_t *list, const int32_t *cnt,
+                                                         int32_t *out, int32_t *out_cnt) {
+    const int32_t n = *cnt;
+    const int32_t t = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    int32_t removed = 0;
+    bool left = false;
+    int32_t i = -1;
+    if (t < n) {
+        i = list[t];
+        const int32_t sl = C.rslot[i];
+        int32_t li = -1;
+        bool act = sl >= 0;
+        if (act) {
+            li = (int32_t)(uint32_t)(C.tlead[sl] & 0xffffffffULL);
+            if (li == i) act = false;  // the leader itself
+        }
+        int32_t bi = 0, bl = 0, len = 0;
+        bool ok = false;
+        double lam = 0.0;
+        if (act) {
+            bi = C.A.ptr[i];
+            bl = C.A.ptr[li];
+            len = C.A.ptr[i + 1] - bi;
+            ok = (C.A.ptr[li + 1] - bl) == len;
+            lam = C.A.val[bi] / C.A.val[bl];
+        }
+        if (ok) {
+            for (int32_t k = lane; k < len; k += 32) {
+                const double ai = C.A.val[bi + k], al = C.A.val[bl + k];
+                const double la = lam * al;
+                if (!(C.A.idx[bi + k] == C.A.idx[bl + k] && fabs(ai - la) <= C.par_tol * fmax(fabs(ai), fabs(la))))
+                    ok = false;
+            }
+        }
+        ok = __all_sync(0xffffffffu, ok) != 0;  // the warp's lanes share t
+        if (lane == 0) {
+            if (act && ok) {
+                s5_accept(C, i, li, lam);
+                removed = 1;
+            } else if (act) {
+                left = true;
+            }
+        }
+    }
+    block_add(removed, &C.st->rows_removed);
+    block_append(left, i, out_cnt, out);
+}
+
+__global__ void __launch_bounds__(kBlock) k_s5_tail_clear(Ctx C, const int32_t *list, const int32_t *cnt) {
+    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= *cnt) return;
+    const int32_t sl = C.rslot[list[t]];
+    if (sl >= 0) {
+        C.tkey[sl] = 0ULL;
+        C.tlead[sl] = ~0ULL;
+    }
 }
 
 // leaders take the followers' sides: L = max(L, merged), U = min(U, merged);
@@ -669,13 +746,22 @@ void launch_mark_dirty(const Ctx &C, cudaStream_t s) {
     if (C.T.cls_start[7] > C.T.cls_start[6] && C.T.nchunks > 0) (k_mark_long<<<C.T.nchunks, kBlock, 0, s>>>(C), note_launch());
 }
 
-void launch_s5_pass(const Ctx &C, int pass, cudaStream_t s) {
+void launch_s5_pass(const Ctx &C, cudaStream_t s) {
     if (C.m == 0) return;
-    (k_s5_insert<<<blocks_for(C.m, kBlock), kBlock, 0, s>>>(C, pass), note_launch());
+    (k_s5_insert<<<blocks_for(C.m, kBlock), kBlock, 0, s>>>(C), note_launch());
     const GroupGrid g = group_grid(C.A);
     if (g.blk_start[6] > 0) (k_s5_match_groups<<<g.blk_start[6], kBlock, 0, s>>>(C, g), note_launch());
     const int32_t nlong = C.A.cls_start[7] - C.A.cls_start[6];
     if (nlong > 0) (k_s5_match_long<<<nlong, kBlock, 0, s>>>(C), note_launch());
+}
+
+void launch_s5_tail(const Ctx &C, const int32_t *list, const int32_t *cnt, int32_t *out, int32_t *out_cnt,
+                    int32_t max_rows, cudaStream_t s) {
+    if (max_rows <= 0) return;
+    (k_s5_tail_insert<<<blocks_for(max_rows, kBlock), kBlock, 0, s>>>(C, list, cnt), note_launch());
+    (k_s5_tail_match<<<blocks_for((int64_t)max_rows * 32, kBlock), kBlock, 0, s>>>(C, list, cnt, out, out_cnt),
+     note_launch());
+    (k_s5_tail_clear<<<blocks_for(max_rows, kBlock), kBlock, 0, s>>>(C, list, cnt), note_launch());
 }
 
 void launch_s5_leader(const Ctx &C, cudaStream_t s) {

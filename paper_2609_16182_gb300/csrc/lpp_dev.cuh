@@ -107,6 +107,7 @@ struct Ctx {
     // S5 table
     unsigned long long *tkey, *tlead;
     int32_t tcap;
+    int32_t *s5_out, *s5_out_cnt;   // rows the first pass leaves unmatched (list, count)
     // long segments
     double2 *ch_act;
     int2 *ch_ninf;
@@ -237,6 +238,20 @@ __device__ __forceinline__ void block_add(int32_t v, int32_t *dst) {
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_acc, v);
     __syncthreads();
     if (threadIdx.x == 0 && s_acc) atomicAdd(dst, s_acc);
+}
+
+// Appends `value` to list[*cnt ...] for each thread with `want`: one shared
+// atomic per thread, one global atomic per block.  Every thread of the block
+// must call it.  The order within the list is unspecified.
+__device__ __forceinline__ void block_append(bool want, int32_t value, int32_t *cnt, int32_t *list) {
+    __shared__ int32_t s_n, s_base;
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    const int32_t pos = want ? atomicAdd(&s_n, 1) : 0;
+    __syncthreads();
+    if (threadIdx.x == 0) s_base = s_n ? atomicAdd(cnt, s_n) : 0;
+    __syncthreads();
+    if (want) list[s_base + pos] = value;
 }
 
 __device__ __forceinline__ int32_t lp_of_row(const Ctx &C, int32_t i) { return C.lp_row ? C.lp_row[i] : 0; }

@@ -163,6 +163,7 @@ Engine::~Engine() {
     pinned_put(st_h);
     pinned_put(verdict_h);
     pinned_put(changed_h);
+    pinned_put(s5_left_h);
     if (own_stream && s) cudaStreamDestroy(s);
 }
 
@@ -207,6 +208,7 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
     st_h = static_cast<DevStatus *>(pinned_get_sized(sizeof(DevStatus)));
     verdict_h = static_cast<int32_t *>(pinned_get_sized(sizeof(int32_t) * (size_t)nlp * V_SLOTS));
     changed_h = static_cast<uint8_t *>(pinned_get_sized((size_t)nlp));
+    s5_left_h = static_cast<int32_t *>(pinned_get_sized(sizeof(int32_t)));
     const bool arena = nlp > 1;
     for (int b = 0; b < 2; b++) {
         rp[b] = pool.alloc<int32_t>(m0 + 1);
@@ -262,6 +264,9 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
     tcap_max = pow2_at_least(2 * (int64_t)std::max(m0, 1));
     tkey = pool.alloc<unsigned long long>(tcap_max);
     tlead = pool.alloc<unsigned long long>(tcap_max);
+    s5_list[0] = pool.alloc<int32_t>(m0);
+    s5_list[1] = pool.alloc<int32_t>(m0);
+    s5_cnt = pool.alloc<int32_t>((size_t)o.par_max_iter + 2);
     ch_act = pool.alloc<double2>(cap_chunk);
     ch_ninf = pool.alloc<int2>(cap_chunk);
     ch_hash = pool.alloc<unsigned long long>(cap_chunk);
@@ -622,7 +627,10 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     LPP_CUDA(cudaMemsetAsync(tkey, 0, sizeof(unsigned long long) * tcap, s));
     LPP_CUDA(cudaMemsetAsync(tlead, 0xff, sizeof(unsigned long long) * tcap, s));
     C.tcap = tcap;
-    launch_s5_pass(C, 0, s);
+    LPP_CUDA(cudaMemsetAsync(s5_cnt, 0, sizeof(int32_t) * (size_t)(o.par_max_iter + 2), s));
+    C.s5_out = s5_list[0];
+    C.s5_out_cnt = s5_cnt + 1;
+    launch_s5_pass(C, s);
     tend();
     LPP_CUDA(cudaGetLastError());
     read_status();
@@ -634,15 +642,26 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
         pm.bytes = 12.0 * st_h->nnz_eval + 53.0 * m + 16.0 * n;
         pm.ops = 2.0 * st_h->nnz_eval;
     }
-    for (int pass = 1; st_h->unmatched > 0 && pass < o.par_max_iter; pass++) {
-        tcap = std::min(tcap_max, pow2_at_least(2 * (int64_t)st_h->unmatched));
+    // later passes on the list of unmatched rows, without a host sync per
+    // pass: chunks of 2, 4, 8, ... passes, then one read of the list size
+    const int32_t n1 = st_h->unmatched;
+    if (n1 > 0 && o.par_max_iter > 1) {
+        tcap = std::min(tcap_max, pow2_at_least(2 * (int64_t)n1));
         LPP_CUDA(cudaMemsetAsync(tkey, 0, sizeof(unsigned long long) * tcap, s));
         LPP_CUDA(cudaMemsetAsync(tlead, 0xff, sizeof(unsigned long long) * tcap, s));
-        LPP_CUDA(cudaMemsetAsync(&st->unmatched, 0, sizeof(int32_t), s));
         C.tcap = tcap;
-        launch_s5_pass(C, pass, s);
-        LPP_CUDA(cudaGetLastError());
-        read_status();
+        int32_t chunk = 2;
+        for (int32_t pass = 1; pass < o.par_max_iter;) {
+            const int32_t end = std::min<int32_t>(pass + chunk, o.par_max_iter);
+            for (int32_t q = pass; q < end; q++)
+                launch_s5_tail(C, s5_list[(q - 1) & 1], s5_cnt + q, s5_list[q & 1], s5_cnt + q + 1, n1, s);
+            LPP_CUDA(cudaGetLastError());
+            LPP_CUDA(cudaMemcpyAsync(s5_left_h, s5_cnt + end, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            LPP_CUDA(cudaStreamSynchronize(s));
+            if (*s5_left_h == 0) break;
+            pass = end;
+            chunk *= 2;
+        }
     }
     if (st_h->err) throw StatusError(LPP_ERR_CUDA, "internal: S5 hash table overflow");
     launch_s5_leader(C, s);
@@ -658,6 +677,7 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     else std::swap(rdirty[cur], rdnext);  // same numbering: next round's flags
     LPP_CUDA(cudaEventRecord(ev_round[1], s));
     read_status();
+    if (st_h->err) throw StatusError(LPP_ERR_CUDA, "internal: S5 hash table overflow");
     if (out.structural) {
         const int32_t m_new = st_h->m_new, n_new = st_h->n_new, nnz_new = st_h->nnz_new;
         if (nnz_new != st_h->nnz_new_t || m_new < 0 || m_new > m || n_new < 0 || n_new > n || nnz_new > nnz)

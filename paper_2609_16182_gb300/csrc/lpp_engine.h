@@ -85,6 +85,7 @@ struct Engine {
     uint8_t *rdirty[2], *rdnext, *cchg;
     uint8_t *rkind, *rwork, *hasf, *ckind, *lneed, *lp_changed, *lp_dead;
     unsigned long long *mL, *mU, *cand_l, *cand_u, *tkey, *tlead, *ch_hash;
+    int32_t *s5_list[2] = {nullptr, nullptr}, *s5_cnt = nullptr;  // S5 lists of unmatched rows, their sizes per pass
     int32_t *rslot, *verdict;
     double *fixv;
     double2 *ch_act;
@@ -100,6 +101,7 @@ struct Engine {
     DevStatus *st_h = nullptr;  // pinned mirror
     int32_t *verdict_h = nullptr;
     uint8_t *changed_h = nullptr;
+    int32_t *s5_left_h = nullptr;  // rows still unmatched after a chunk of S5 passes
     SegMat A, T;
     // per-LP results
     std::vector<int32_t> lp_rounds, lp_status, lp_where, lp_index, lp_round;
