@@ -19,6 +19,9 @@
 // per-entry sign, finiteness and max(1,|x|) test runs on integer pipes, the
 // activity sums are fused multiply-adds, and an implied bound is divided out
 // only after an exact FMA sign test (x - thr*a) says it will be accepted.
+#include <algorithm>
+#include <cooperative_groups.h>
+
 #include "lpp_launch.h"
 
 namespace lpp {
@@ -28,6 +31,22 @@ namespace {
 __device__ __forceinline__ double pinf() { return __longlong_as_double(0x7ff0000000000000LL); }
 __device__ __forceinline__ double ninf_() { return __longlong_as_double((long long)0xfff0000000000000ULL); }
 
+
+namespace cg = cooperative_groups;
+
+// appends v to list[*cnt ...] with one atomic per group of converged threads
+__device__ __forceinline__ void coalesced_append(int32_t v, int32_t *cnt, int32_t *list) {
+    cg::coalesced_group g = cg::coalesced_threads();
+    int32_t base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(cnt, (int32_t)g.size());
+    base = g.shfl(base, 0);
+    list[base + (int32_t)g.thread_rank()] = v;
+}
+
+// column j received a candidate: list it once per round for S3'
+__device__ __forceinline__ void touch_col(const Ctx &C, int32_t j) {
+    if (C.ctouch[j] == 0u && atomicExch(&C.ctouch[j], 1u) == 0u) coalesced_append(j, C.tl_cnt, C.tl_list);
+}
 
 // exact sign tests of a double on its bit pattern (integer pipes):
 // s < 0 <=> negative and not -0;  s > 0 <=> positive bits, not +0
@@ -49,6 +68,7 @@ __device__ __forceinline__ void try_upper(const Ctx &C, int32_t j, double x, dou
     }
     if (gt0(fma(-C.max_implied, fabs(a), fabs(x)))) return;
     atomic_min_dbl(&C.cand_u[j], x / a);
+    touch_col(C, j);
 }
 // Implied lower bound x/a: accepted iff (lold = -inf or x/a > thr) and
 // |x/a| <= max_implied, thr = lold + bound_tol*max(1,|lold|).
@@ -60,6 +80,7 @@ __device__ __forceinline__ void try_lower(const Ctx &C, int32_t j, double x, dou
     }
     if (gt0(fma(-C.max_implied, fabs(a), fabs(x)))) return;
     atomic_max_dbl(&C.cand_l[j], x / a);
+    touch_col(C, j);
 }
 
 // Candidates of one entry (S3).  dU = U - smin and dL = L - smax are the
@@ -154,6 +175,7 @@ __device__ __forceinline__ int32_t finish_row(const Ctx &C, int32_t i, int32_t b
         }
         if (is_fin(cl)) atomic_max_dbl(&C.cand_l[j], cl);
         if (is_fin(cu)) atomic_min_dbl(&C.cand_u[j], cu);
+        if (is_fin(cl) || is_fin(cu)) touch_col(C, j);
     } else {
         C.rec_ra[o] = -1;
         C.rec_rv[o] = 0.0;
@@ -339,63 +361,81 @@ __global__ void __launch_bounds__(kBlock) k_prop_long_tighten(Ctx C) {
 }
 
 // ------------------------------------------------- S3' finalise + S4 fixing
+// S3' + S4 on column j: apply the accepted candidates, check and snap the
+// bounds, fix the column if l == u.  Returns (changed, fixed) through refs;
+// a changed short column is listed for the dirty-row marking.
+__device__ __forceinline__ void colfin_one(const Ctx &C, int32_t j, bool full, int32_t &changed, int32_t &fixed) {
+    const unsigned long long el = C.cand_l[j], eu = C.cand_u[j];
+    const bool has = el != kEncNegInf || eu != kEncPosInf;
+    uint8_t kind = CK_KEPT;
+    uint8_t chg = 0;
+    const int32_t lp = lp_of_col(C, j);
+    if (has || (full && lp_round(C, lp) == 1)) {
+        if (has) {
+            C.cand_l[j] = kEncNegInf;
+            C.cand_u[j] = kEncPosInf;
+        }
+        const double2 b = C.lu[j];
+        double nl = b.x, nu = b.y;
+        if (has) {
+            const double dl = dec_dbl(el), du = dec_dbl(eu);
+            if (dl > nl) nl = dl;
+            if (du < nu) nu = du;
+        }
+        bool bad = false;
+        if (is_fin(nl) && is_fin(nu)) {
+            const double d = C.feas_tol * fmax(1.0, fmax(fabs(nl), fabs(nu)));
+            if (nl - nu > d) {
+                bad = true;
+            } else if (nl != nu && fabs(nl - nu) <= d) {
+                const double mid = 0.5 * (nl + nu);
+                nl = mid;
+                nu = mid;
+            }
+        }
+        if (bad) {
+            atomicMin(&C.verdict[lp * V_SLOTS + V_S3_COL], C.cmap[j]);
+        } else {
+            if (nl != b.x || nu != b.y) {
+                C.lu[j] = make_double2(nl, nu);
+                changed = 1;
+                chg = 1;
+                C.lp_changed[lp] = 1;
+            }
+            if (nl == nu) {
+                kind = CK_FIXED;
+                fixed = 1;
+                C.fixv[j] = nl;
+                const int32_t o = C.cmap[j];
+                C.rec_ck[o] = CK_FIXED;
+                C.rec_cr[o] = lp_round(C, lp);
+                C.rec_cv[o] = nl;
+                C.lp_changed[lp] = 1;
+            }
+        }
+    }
+    C.ckind[j] = kind;
+    C.cchg[j] = chg;
+    C.ctouch[j] = 0u;
+    if (chg && C.T.ptr[j + 1] - C.T.ptr[j] < kLongMin) coalesced_append(j, C.cl_cnt, C.cl_list);
+}
+
+// every column (some LP in its first round)
 __global__ void __launch_bounds__(kBlock) k_colfin(Ctx C) {
     const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     int32_t changed = 0, fixed = 0;
-    if (j < C.n) {
-        const unsigned long long el = C.cand_l[j], eu = C.cand_u[j];
-        const bool has = el != kEncNegInf || eu != kEncPosInf;
-        uint8_t kind = CK_KEPT;
-        uint8_t chg = 0;
-        const int32_t lpj = lp_of_col(C, j);
-        if (has || lp_round(C, lpj) == 1) {
-            if (has) {
-                C.cand_l[j] = kEncNegInf;
-                C.cand_u[j] = kEncPosInf;
-            }
-            const double2 b = C.lu[j];
-            double nl = b.x, nu = b.y;
-            if (has) {
-                const double dl = dec_dbl(el), du = dec_dbl(eu);
-                if (dl > nl) nl = dl;
-                if (du < nu) nu = du;
-            }
-            bool bad = false;
-            if (is_fin(nl) && is_fin(nu)) {
-                const double d = C.feas_tol * fmax(1.0, fmax(fabs(nl), fabs(nu)));
-                if (nl - nu > d) {
-                    bad = true;
-                } else if (nl != nu && fabs(nl - nu) <= d) {
-                    const double mid = 0.5 * (nl + nu);
-                    nl = mid;
-                    nu = mid;
-                }
-            }
-            const int32_t lp = lpj;
-            if (bad) {
-                atomicMin(&C.verdict[lp * V_SLOTS + V_S3_COL], C.cmap[j]);
-            } else {
-                if (nl != b.x || nu != b.y) {
-                    C.lu[j] = make_double2(nl, nu);
-                    changed = 1;
-                    chg = 1;
-                    C.lp_changed[lp] = 1;
-                }
-                if (nl == nu) {
-                    kind = CK_FIXED;
-                    fixed = 1;
-                    C.fixv[j] = nl;
-                    const int32_t o = C.cmap[j];
-                    C.rec_ck[o] = CK_FIXED;
-                    C.rec_cr[o] = lp_round(C, lp);
-                    C.rec_cv[o] = nl;
-                    C.lp_changed[lp] = 1;
-                }
-            }
-        }
-        C.ckind[j] = kind;
-        C.cchg[j] = chg;
-    }
+    if (j < C.n) colfin_one(C, j, true, changed, fixed);
+    block_add(changed, &C.st->bounds_changed);
+    block_add(fixed, &C.st->cols_fixed);
+}
+
+// the columns that received a candidate (the others keep their bounds; their
+// kind and change flag were reset at the start of the round)
+__global__ void __launch_bounds__(kBlock) k_colfin_list(Ctx C) {
+    const int32_t cnt = *C.tl_cnt;
+    int32_t changed = 0, fixed = 0;
+    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x)
+        colfin_one(C, C.tl_list[t], false, changed, fixed);
     block_add(changed, &C.st->bounds_changed);
     block_add(fixed, &C.st->cols_fixed);
 }
@@ -690,26 +730,15 @@ __global__ void __launch_bounds__(kBlock) k_s5_leader(Ctx C) {
 }
 
 // rows of a column whose bounds changed must be re-evaluated next round
-template <int W>
-__device__ __forceinline__ void mark_group(const Ctx &C, int32_t j, bool valid) {
-    if (!valid || !C.cchg[j]) return;
-    const int lane = threadIdx.x & (W - 1);
-    for (int32_t k = C.T.ptr[j] + lane; k < C.T.ptr[j + 1]; k += W) C.rdnext[C.T.idx[k]] = 1;
-}
-
-__global__ void __launch_bounds__(kBlock) k_mark_groups(Ctx C, GroupGrid g) {
-    const int c = grid_class(g, blockIdx.x);
-    const int W = 1 << c;
-    const int32_t pos = C.T.cls_start[c] + (blockIdx.x - g.blk_start[c]) * (kBlock / W) + threadIdx.x / W;
-    const bool valid = pos < C.T.cls_start[c + 1];
-    const int32_t j = valid ? C.T.order[pos] : 0;
-    switch (c) {
-        case 0: mark_group<1>(C, j, valid); break;
-        case 1: mark_group<2>(C, j, valid); break;
-        case 2: mark_group<4>(C, j, valid); break;
-        case 3: mark_group<8>(C, j, valid); break;
-        case 4: mark_group<16>(C, j, valid); break;
-        default: mark_group<32>(C, j, valid); break;
+// rows of the changed short columns need their activities next round: one
+// warp per listed column
+__global__ void __launch_bounds__(kBlock) k_mark_list(Ctx C) {
+    const int32_t cnt = *C.cl_cnt;
+    const int lane = threadIdx.x & 31;
+    const int32_t nw = (int32_t)((gridDim.x * (int64_t)blockDim.x) >> 5);
+    for (int32_t t = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); t < cnt; t += nw) {
+        const int32_t j = C.cl_list[t];
+        for (int32_t k = C.T.ptr[j] + lane; k < C.T.ptr[j + 1]; k += 32) C.rdnext[C.T.idx[k]] = 1;
     }
 }
 
@@ -736,13 +765,16 @@ void launch_prop(const Ctx &C, cudaStream_t s) {
     }
 }
 
-void launch_colfin(const Ctx &C, cudaStream_t s) {
-    if (C.n > 0) (k_colfin<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C), note_launch());
+void launch_colfin(const Ctx &C, bool full, cudaStream_t s) {
+    if (C.n <= 0) return;
+    if (full) (k_colfin<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C), note_launch());
+    else (k_colfin_list<<<std::min<unsigned>(blocks_for(C.n, kBlock), 8u * 152u), kBlock, 0, s>>>(C), note_launch());
 }
 
 void launch_mark_dirty(const Ctx &C, cudaStream_t s) {
-    const GroupGrid g = group_grid(C.T);
-    if (g.blk_start[6] > 0) (k_mark_groups<<<g.blk_start[6], kBlock, 0, s>>>(C, g), note_launch());
+    if (C.n <= 0) return;
+    (k_mark_list<<<std::min<unsigned>(blocks_for((int64_t)C.n * 32, kBlock), 8u * 152u), kBlock, 0, s>>>(C),
+     note_launch());
     if (C.T.cls_start[7] > C.T.cls_start[6] && C.T.nchunks > 0) (k_mark_long<<<C.T.nchunks, kBlock, 0, s>>>(C), note_launch());
 }
 

@@ -102,6 +102,9 @@ struct Ctx {
     uint8_t *hasf;
     // column work
     unsigned long long *cand_l, *cand_u;  // accepted implied bounds (ordered encoding)
+    uint32_t *ctouch;                     // 1 once the column received a candidate this round
+    int32_t *tl_list, *tl_cnt;            // columns that received a candidate this round
+    int32_t *cl_list, *cl_cnt;            // columns whose bounds changed this round
     uint8_t *ckind;
     double *fixv;
     // S5 table

@@ -259,6 +259,10 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
     rslot = pool.alloc<int32_t>(m0);
     cand_l = pool.alloc<unsigned long long>(n0);
     cand_u = pool.alloc<unsigned long long>(n0);
+    ctouch = pool.alloc<uint32_t>(n0);
+    tl_list = pool.alloc<int32_t>(n0);
+    cl_list = pool.alloc<int32_t>(n0);
+    col_cnt = pool.alloc<int32_t>(2);
     ckind = pool.alloc<uint8_t>(n0);
     fixv = pool.alloc<double>(n0);
     tcap_max = pow2_at_least(2 * (int64_t)std::max(m0, 1));
@@ -429,6 +433,7 @@ void Engine::prepare() {
     iota(cmap[0], n0, 0, s);
     fill_u64(cand_l, n0, kEncNegInf, s);
     fill_u64(cand_u, n0, kEncPosInf, s);
+    LPP_CUDA(cudaMemsetAsync(ctouch, 0, sizeof(uint32_t) * (size_t)std::max(n0, 1), s));
     fill_u64(mL, m0, kEncNegInf, s);
     fill_u64(mU, m0, kEncPosInf, s);
     LPP_CUDA(cudaMemsetAsync(hasf, 0, (size_t)std::max(m0, 1), s));
@@ -524,6 +529,11 @@ Ctx Engine::ctx(int32_t round) const {
     C.hasf = hasf;
     C.cand_l = cand_l;
     C.cand_u = cand_u;
+    C.ctouch = ctouch;
+    C.tl_list = tl_list;
+    C.tl_cnt = col_cnt;
+    C.cl_list = cl_list;
+    C.cl_cnt = col_cnt + 1;
     C.ckind = ckind;
     C.fixv = fixv;
     C.tkey = tkey;
@@ -611,13 +621,20 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     LPP_CUDA(cudaMemsetAsync(st, 0, 8 * sizeof(int32_t), s));
     LPP_CUDA(cudaMemsetAsync(lp_changed, 0, (size_t)nlp, s));
     if (m > 0) LPP_CUDA(cudaMemsetAsync(rdnext, 0, (size_t)m, s));
+    // the column lists of S3' start empty; outside a first round only listed
+    // columns are finalised, the others keep kind KEPT and no change flag
+    LPP_CUDA(cudaMemsetAsync(col_cnt, 0, 2 * sizeof(int32_t), s));
+    if (!first_round && n > 0) {
+        LPP_CUDA(cudaMemsetAsync(ckind, 0, (size_t)n, s));
+        LPP_CUDA(cudaMemsetAsync(cchg, 0, (size_t)n, s));
+    }
     Ctx C = ctx(r);
     tbegin(F_PROP, 0.0);  // bytes and ops set once the evaluated nonzeros are known
     const size_t prop_mark = marks.size();
     launch_prop(C, s);
     tend();
     tbegin(F_COLFIN, 33.0 * n);
-    launch_colfin(C, s);
+    launch_colfin(C, first_round, s);
     launch_mark_dirty(C, s);
     tend();
     LPP_CUDA(cudaGetLastError());

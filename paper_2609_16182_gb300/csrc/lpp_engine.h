@@ -85,7 +85,9 @@ struct Engine {
     uint8_t *rdirty[2], *rdnext, *cchg;
     uint8_t *rkind, *rwork, *hasf, *ckind, *lneed, *lp_changed, *lp_dead;
     unsigned long long *mL, *mU, *cand_l, *cand_u, *tkey, *tlead, *ch_hash;
-    int32_t *s5_list[2] = {nullptr, nullptr}, *s5_cnt = nullptr;  // S5 lists of unmatched rows, their sizes per pass
+    int32_t *s5_list[2] = {nullptr, nullptr}, *s5_cnt = nullptr;
+    uint32_t *ctouch = nullptr;                                      // S3' column lists
+    int32_t *tl_list = nullptr, *cl_list = nullptr, *col_cnt = nullptr;  // S5 lists of unmatched rows, their sizes per pass
     int32_t *rslot, *verdict;
     double *fixv;
     double2 *ch_act;

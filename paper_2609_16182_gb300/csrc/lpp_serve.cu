@@ -206,6 +206,7 @@ double now_s() {
 void Engine::init_empty() {
     fill_u64(cand_l, n0, kEncNegInf, s);
     fill_u64(cand_u, n0, kEncPosInf, s);
+    LPP_CUDA(cudaMemsetAsync(ctouch, 0, sizeof(uint32_t) * (size_t)std::max(n0, 1), s));
     fill_u64(mL, m0, kEncNegInf, s);
     fill_u64(mU, m0, kEncPosInf, s);
     LPP_CUDA(cudaMemsetAsync(hasf, 0, (size_t)std::max(m0, 1), s));

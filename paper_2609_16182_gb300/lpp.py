@@ -219,38 +219,49 @@ class Result:
         self.index = info.index
         self.round = info.round
         self.rounds = info.rounds
-        R = C.c_int32(0)
-        cap = 1024
-        self.round_nnz = np.zeros(cap, np.int64)
-        self.round_rows_removed = np.zeros(cap, np.int32)
-        self.round_cols_fixed = np.zeros(cap, np.int32)
-        self.round_bounds_changed = np.zeros(cap, np.int32)
-        self.round_ms = np.zeros(cap, np.float32)
-        _check(L.lpp_result_rounds(rec, cap, _p(self.round_nnz), _p(self.round_rows_removed),
-                                   _p(self.round_cols_fixed), _p(self.round_bounds_changed), _p(self.round_ms),
-                                   C.byref(R)))
-        k = min(R.value, cap)
-        for a in ("round_nnz", "round_rows_removed", "round_cols_fixed", "round_bounds_changed", "round_ms"):
-            setattr(self, a, getattr(self, a)[:k])
-        ks = (KernelStat * 32)()
-        cnt = C.c_int32(0)
-        _check(L.lpp_result_kernels(rec, 32, ks, C.byref(cnt)))
-        self.kernels = {ks[i].name.decode(): dict(launches=ks[i].launches, ms=ks[i].ms, bytes=ks[i].bytes,
-                                                  fp64_ops=ks[i].fp64_ops)
-                        for i in range(cnt.value)}
+        self._rounds_data = None
+        self._kernels = None
         self._reduced = None
         self._records = None
 
     _RECORD_FIELDS = ("row_kind", "row_round", "row_aux", "row_val", "col_kind", "col_round", "col_val", "col_lb",
                       "col_ub", "act_min", "act_max", "ninf_min", "ninf_max")
+    _ROUND_FIELDS = ("round_nnz", "round_rows_removed", "round_cols_fixed", "round_bounds_changed", "round_ms")
 
     def __getattr__(self, name):
-        # per-row / per-column records are copied from the device on first use
+        # records, per-round counters and kernel statistics are fetched on first use
         if name in Result._RECORD_FIELDS:
             if self._records is None:
                 self._records = self._load_records()
             return self._records[name]
+        if name in Result._ROUND_FIELDS:
+            if self._rounds_data is None:
+                self._rounds_data = self._load_rounds()
+            return self._rounds_data[name]
+        if name == "kernels":
+            if self._kernels is None:
+                self._kernels = self._load_kernels()
+            return self._kernels
         raise AttributeError(name)
+
+    def _load_rounds(self):
+        L = load()
+        R = C.c_int32(0)
+        cap = 1024
+        out = dict(round_nnz=np.zeros(cap, np.int64), round_rows_removed=np.zeros(cap, np.int32),
+                   round_cols_fixed=np.zeros(cap, np.int32), round_bounds_changed=np.zeros(cap, np.int32),
+                   round_ms=np.zeros(cap, np.float32))
+        _check(L.lpp_result_rounds(self._rec, cap, *[_p(out[k]) for k in Result._ROUND_FIELDS], C.byref(R)))
+        k = min(R.value, cap)
+        return {a: v[:k] for a, v in out.items()}
+
+    def _load_kernels(self):
+        ks = (KernelStat * 32)()
+        cnt = C.c_int32(0)
+        _check(load().lpp_result_kernels(self._rec, 32, ks, C.byref(cnt)))
+        return {ks[i].name.decode(): dict(launches=ks[i].launches, ms=ks[i].ms, bytes=ks[i].bytes,
+                                          fp64_ops=ks[i].fp64_ops)
+                for i in range(cnt.value)}
 
     def _load_records(self):
         L = load()
