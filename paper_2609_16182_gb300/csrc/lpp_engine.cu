@@ -638,16 +638,21 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     launch_mark_dirty(C, s);
     tend();
     LPP_CUDA(cudaGetLastError());
-    // S5: leader passes
+    // S5: leader passes.  Skipped when the last S5 resolved every key group
+    // (no row left unmatched at the pass cap) and no row lost an entry since:
+    // its survivors are pairwise not parallel, so it would remove nothing.
+    const bool run_s5 = first_round || !s5_clean;
     int32_t tcap = std::min(tcap_max, pow2_at_least(2 * (int64_t)std::max(m, 1)));
-    tbegin(F_S5, 16.0 * tcap + 12.0 * m);
-    LPP_CUDA(cudaMemsetAsync(tkey, 0, sizeof(unsigned long long) * tcap, s));
-    LPP_CUDA(cudaMemsetAsync(tlead, 0xff, sizeof(unsigned long long) * tcap, s));
-    C.tcap = tcap;
-    LPP_CUDA(cudaMemsetAsync(s5_cnt, 0, sizeof(int32_t) * (size_t)(o.par_max_iter + 2), s));
-    C.s5_out = s5_list[0];
-    C.s5_out_cnt = s5_cnt + 1;
-    launch_s5_pass(C, s);
+    tbegin(F_S5, run_s5 ? 16.0 * tcap + 12.0 * m : 0.0);
+    if (run_s5) {
+        LPP_CUDA(cudaMemsetAsync(tkey, 0, sizeof(unsigned long long) * tcap, s));
+        LPP_CUDA(cudaMemsetAsync(tlead, 0xff, sizeof(unsigned long long) * tcap, s));
+        C.tcap = tcap;
+        LPP_CUDA(cudaMemsetAsync(s5_cnt, 0, sizeof(int32_t) * (size_t)(o.par_max_iter + 2), s));
+        C.s5_out = s5_list[0];
+        C.s5_out_cnt = s5_cnt + 1;
+        launch_s5_pass(C, s);
+    }
     tend();
     LPP_CUDA(cudaGetLastError());
     read_status();
@@ -661,8 +666,10 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     }
     // later passes on the list of unmatched rows, without a host sync per
     // pass: chunks of 2, 4, 8, ... passes, then one read of the list size
-    const int32_t n1 = st_h->unmatched;
+    const int32_t n1 = run_s5 ? st_h->unmatched : 0;
+    bool resolved = n1 == 0;
     if (n1 > 0 && o.par_max_iter > 1) {
+        tbegin(F_S5, 0.0);
         tcap = std::min(tcap_max, pow2_at_least(2 * (int64_t)n1));
         LPP_CUDA(cudaMemsetAsync(tkey, 0, sizeof(unsigned long long) * tcap, s));
         LPP_CUDA(cudaMemsetAsync(tlead, 0xff, sizeof(unsigned long long) * tcap, s));
@@ -675,13 +682,18 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
             LPP_CUDA(cudaGetLastError());
             LPP_CUDA(cudaMemcpyAsync(s5_left_h, s5_cnt + end, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
             LPP_CUDA(cudaStreamSynchronize(s));
-            if (*s5_left_h == 0) break;
+            if (*s5_left_h == 0) {
+                resolved = true;
+                break;
+            }
             pass = end;
             chunk *= 2;
         }
+        tend();
     }
+    if (run_s5) s5_clean = resolved;
     if (st_h->err) throw StatusError(LPP_ERR_CUDA, "internal: S5 hash table overflow");
-    launch_s5_leader(C, s);
+    if (run_s5) launch_s5_leader(C, s);
     LPP_CUDA(cudaGetLastError());
     bool newly_dead = false;
     for (int32_t k = 0; k < nlp; k++) {
@@ -695,6 +707,7 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     LPP_CUDA(cudaEventRecord(ev_round[1], s));
     read_status();
     if (st_h->err) throw StatusError(LPP_ERR_CUDA, "internal: S5 hash table overflow");
+    if (st_h->cols_fixed > 0) s5_clean = false;  // rows lost entries (S4 or S6 fixings)
     if (out.structural) {
         const int32_t m_new = st_h->m_new, n_new = st_h->n_new, nnz_new = st_h->nnz_new;
         if (nnz_new != st_h->nnz_new_t || m_new < 0 || m_new > m || n_new < 0 || n_new > n || nnz_new > nnz)
@@ -715,6 +728,7 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
 
 void Engine::run() {
     const int32_t R = std::max(0, o.max_rounds);
+    s5_clean = false;
     lp_rounds.assign(nlp, 0);
     lp_status.assign(nlp, LPP_OK);
     lp_where.assign(nlp, LPP_WHERE_NONE);

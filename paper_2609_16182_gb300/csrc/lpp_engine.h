@@ -86,6 +86,7 @@ struct Engine {
     uint8_t *rkind, *rwork, *hasf, *ckind, *lneed, *lp_changed, *lp_dead;
     unsigned long long *mL, *mU, *cand_l, *cand_u, *tkey, *tlead, *ch_hash;
     int32_t *s5_list[2] = {nullptr, nullptr}, *s5_cnt = nullptr;
+    bool s5_clean = false;  // the last S5 resolved every group and no row changed since
     uint32_t *ctouch = nullptr;                                      // S3' column lists
     int32_t *tl_list = nullptr, *cl_list = nullptr, *col_cnt = nullptr;  // S5 lists of unmatched rows, their sizes per pass
     int32_t *rslot, *verdict;
