@@ -60,7 +60,15 @@ __device__ __forceinline__ bool gt0(double s) { return dbits(s) > 0; }
 // |x/a| <= max_implied, thr = uold - bound_tol*max(1,|uold|) (one rounding).
 // Both tests are decided exactly on the real quotient by the sign of one
 // fused multiply-add; the cap is tested only for candidates that pass.
+// A candidate that cannot lower the column's current minimum cur (x/a >= cur,
+// again the sign of one FMA) is dropped first: it would not change the
+// result, and it skips the threshold test and the divide.
 __device__ __forceinline__ void try_upper(const Ctx &C, int32_t j, double x, double a, double uold) {
+    const unsigned long long ec = *((volatile unsigned long long *)&C.cand_u[j]);
+    if (ec != kEncPosInf) {
+        const double s = fma(-dec_dbl(ec), a, x);
+        if (is_neg(a) ? !gt0(s) : !lt0(s)) return;
+    }
     if (is_fin(uold)) {
         const double thr = fma(-C.bound_tol, max1abs(uold), uold);
         const double s = fma(-thr, a, x);
@@ -71,8 +79,14 @@ __device__ __forceinline__ void try_upper(const Ctx &C, int32_t j, double x, dou
     touch_col(C, j);
 }
 // Implied lower bound x/a: accepted iff (lold = -inf or x/a > thr) and
-// |x/a| <= max_implied, thr = lold + bound_tol*max(1,|lold|).
+// |x/a| <= max_implied, thr = lold + bound_tol*max(1,|lold|); a candidate
+// that cannot raise the current maximum is dropped first.
 __device__ __forceinline__ void try_lower(const Ctx &C, int32_t j, double x, double a, double lold) {
+    const unsigned long long ec = *((volatile unsigned long long *)&C.cand_l[j]);
+    if (ec != kEncNegInf) {
+        const double s = fma(-dec_dbl(ec), a, x);
+        if (is_neg(a) ? !lt0(s) : !gt0(s)) return;
+    }
     if (is_fin(lold)) {
         const double thr = fma(C.bound_tol, max1abs(lold), lold);
         const double s = fma(-thr, a, x);
