@@ -62,62 +62,151 @@ __device__ __forceinline__ bool gt0(double s) { return dbits(s) > 0; }
 // fused multiply-add; the cap is tested only for candidates that pass.
 // A candidate that cannot lower the column's current minimum cur (x/a >= cur,
 // again the sign of one FMA) is dropped first: it would not change the
-// result, and it skips the threshold test and the divide.
-__device__ __forceinline__ void try_upper(const Ctx &C, int32_t j, double x, double a, double uold) {
+// result, and it skips the threshold test and the divide.  pass_upper makes
+// the sign tests; apply_cand the cap, the divide and the atomic.
+__device__ __forceinline__ bool pass_upper(const Ctx &C, int32_t j, double x, double a, double uold) {
     const unsigned long long ec = *((volatile unsigned long long *)&C.cand_u[j]);
     if (ec != kEncPosInf) {
         const double s = fma(-dec_dbl(ec), a, x);
-        if (is_neg(a) ? !gt0(s) : !lt0(s)) return;
+        if (is_neg(a) ? !gt0(s) : !lt0(s)) return false;
     }
     if (is_fin(uold)) {
         const double thr = fma(-C.bound_tol, max1abs(uold), uold);
         const double s = fma(-thr, a, x);
-        if (is_neg(a) ? !gt0(s) : !lt0(s)) return;
+        if (is_neg(a) ? !gt0(s) : !lt0(s)) return false;
     }
-    if (gt0(fma(-C.max_implied, fabs(a), fabs(x)))) return;
-    atomic_min_dbl(&C.cand_u[j], x / a);
-    touch_col(C, j);
+    return true;
 }
 // Implied lower bound x/a: accepted iff (lold = -inf or x/a > thr) and
 // |x/a| <= max_implied, thr = lold + bound_tol*max(1,|lold|); a candidate
 // that cannot raise the current maximum is dropped first.
-__device__ __forceinline__ void try_lower(const Ctx &C, int32_t j, double x, double a, double lold) {
+__device__ __forceinline__ bool pass_lower(const Ctx &C, int32_t j, double x, double a, double lold) {
     const unsigned long long ec = *((volatile unsigned long long *)&C.cand_l[j]);
     if (ec != kEncNegInf) {
         const double s = fma(-dec_dbl(ec), a, x);
-        if (is_neg(a) ? !lt0(s) : !gt0(s)) return;
+        if (is_neg(a) ? !lt0(s) : !gt0(s)) return false;
     }
     if (is_fin(lold)) {
         const double thr = fma(C.bound_tol, max1abs(lold), lold);
         const double s = fma(-thr, a, x);
-        if (is_neg(a) ? !lt0(s) : !gt0(s)) return;
+        if (is_neg(a) ? !lt0(s) : !gt0(s)) return false;
     }
-    if (gt0(fma(-C.max_implied, fabs(a), fabs(x)))) return;
-    atomic_max_dbl(&C.cand_l[j], x / a);
+    return true;
+}
+
+// candidate kinds: implied bounds (capped) and singleton-row bounds (not)
+enum : int32_t { CQ_UPPER = 0, CQ_LOWER = 1, CQ_SING_UPPER = 2, CQ_SING_LOWER = 3 };
+
+// the value x/a enters column j's candidates
+__device__ __forceinline__ void apply_cand(const Ctx &C, int32_t j, double x, double a, int32_t kind) {
+    if (kind < CQ_SING_UPPER && gt0(fma(-C.max_implied, fabs(a), fabs(x)))) return;
+    const double v = x / a;
+    if (!is_fin(v)) return;
+    if (kind == CQ_UPPER || kind == CQ_SING_UPPER) atomic_min_dbl(&C.cand_u[j], v);
+    else atomic_max_dbl(&C.cand_l[j], v);
     touch_col(C, j);
 }
 
-// Candidates of one entry (S3).  dU = U - smin and dL = L - smax are the
-// row's slacks: U - (min activity of the other entries) = dU + a*bmin when
-// every term is finite, = dU when this entry is the one infinite term.
-__device__ __forceinline__ void tighten_entry(const Ctx &C, int32_t j, double a, bool up_row, bool lo_row,
-                                              double dU, double dL, int nmin, int nmax) {
+// Sign tests of the two implied bounds of one entry (S3).  dU = U - smin and
+// dL = L - smax are the row's slacks: U - (min activity of the other
+// entries) = dU + a*bmin when every term is finite, = dU when this entry is
+// the one infinite term.  w1 / w2: a candidate x1/a (x2/a) of kind k1 (k2)
+// passed and still needs the cap and the divide.
+__device__ __forceinline__ void tighten_tests(const Ctx &C, int32_t j, double a, bool up_row, bool lo_row, double dU,
+                                              double dL, int nmin, int nmax, bool &w1, double &x1, int32_t &k1,
+                                              bool &w2, double &x2, int32_t &k2) {
     const double2 b = C.lu[j];
     const bool neg = is_neg(a);
     const double bmin = neg ? b.y : b.x, bmax = neg ? b.x : b.y;
     const bool fmn = is_fin(bmin), fmx = is_fin(bmax);
     if (up_row && (fmn ? nmin == 0 : nmin == 1)) {
         // a x_j <= U - (min activity of the other entries)
-        const double x = fmn ? fma(a, bmin, dU) : dU;
-        if (!neg) try_upper(C, j, x, a, b.y);
-        else try_lower(C, j, x, a, b.x);
+        x1 = fmn ? fma(a, bmin, dU) : dU;
+        if (!neg) {
+            k1 = CQ_UPPER;
+            w1 = pass_upper(C, j, x1, a, b.y);
+        } else {
+            k1 = CQ_LOWER;
+            w1 = pass_lower(C, j, x1, a, b.x);
+        }
     }
     if (lo_row && (fmx ? nmax == 0 : nmax == 1)) {
         // a x_j >= L - (max activity of the other entries)
-        const double x = fmx ? fma(a, bmax, dL) : dL;
-        if (!neg) try_lower(C, j, x, a, b.x);
-        else try_upper(C, j, x, a, b.y);
+        x2 = fmx ? fma(a, bmax, dL) : dL;
+        if (!neg) {
+            k2 = CQ_LOWER;
+            w2 = pass_lower(C, j, x2, a, b.x);
+        } else {
+            k2 = CQ_UPPER;
+            w2 = pass_upper(C, j, x2, a, b.y);
+        }
     }
+}
+
+// one entry, candidates applied at once (long rows: few of them tighten)
+__device__ __forceinline__ void tighten_entry(const Ctx &C, int32_t j, double a, bool up_row, bool lo_row,
+                                              double dU, double dL, int nmin, int nmax) {
+    bool w1 = false, w2 = false;
+    double x1 = 0.0, x2 = 0.0;
+    int32_t k1 = 0, k2 = 0;
+    tighten_tests(C, j, a, up_row, lo_row, dU, dL, nmin, nmax, w1, x1, k1, w2, x2, k2);
+    if (w1) apply_cand(C, j, x1, a, k1);
+    if (w2) apply_cand(C, j, x2, a, k2);
+}
+
+// Per-warp queue of candidates that passed their sign tests.  The divide
+// (and the cap, the atomic) then runs 32 candidates at a time, one per lane,
+// instead of on the one or two lanes of a warp that produced a candidate in
+// a step: on GB300 an FP64 instruction costs the pipe the same however many
+// lanes are active.  Every lane of the warp must call cq_push / cq_flush.
+struct CandQueue {
+    double *x, *a;
+    int32_t *j, *kind;
+    int32_t n;  // items held, the same in every lane
+};
+constexpr int kQueueCap = 64;
+
+__device__ __forceinline__ void cq_push(const Ctx &C, CandQueue &q, bool want, double x, double a, int32_t j,
+                                        int32_t kind) {
+    const unsigned b = __ballot_sync(0xffffffffu, want);
+    if (b == 0u) return;
+    const int lane = threadIdx.x & 31;
+    if (want) {
+        const int32_t p = q.n + __popc(b & ((1u << lane) - 1u));
+        q.x[p] = x;
+        q.a[p] = a;
+        q.j[p] = j;
+        q.kind[p] = kind;
+    }
+    q.n += __popc(b);
+    if (q.n < 32) return;
+    __syncwarp();
+    apply_cand(C, q.j[lane], q.x[lane], q.a[lane], q.kind[lane]);
+    const int32_t rest = q.n - 32;
+    double rx = 0.0, ra = 0.0;
+    int32_t rj = 0, rk = 0;
+    if (lane < rest) {
+        rx = q.x[32 + lane];
+        ra = q.a[32 + lane];
+        rj = q.j[32 + lane];
+        rk = q.kind[32 + lane];
+    }
+    __syncwarp();
+    if (lane < rest) {
+        q.x[lane] = rx;
+        q.a[lane] = ra;
+        q.j[lane] = rj;
+        q.kind[lane] = rk;
+    }
+    __syncwarp();
+    q.n = rest;
+}
+
+__device__ __forceinline__ void cq_flush(const Ctx &C, CandQueue &q) {
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    if (lane < q.n) apply_cand(C, q.j[lane], q.x[lane], q.a[lane], q.kind[lane]);
+    q.n = 0;
 }
 
 // S2: class of a row from its activities, first match wins: infeasible
@@ -151,10 +240,11 @@ __device__ __forceinline__ bool classify(const Ctx &C, double Lv, double Uv, int
 }
 
 
-// writes the row's S1/S2 results and records; applies a singleton row as a bound
+// writes the row's S1/S2 results and records; a singleton row returns its
+// entry (sa, sj) for the caller to apply as bounds L/a, U/a
 __device__ __forceinline__ int32_t finish_row(const Ctx &C, int32_t i, int32_t beg, int32_t len, double Lv,
                                               double Uv, double smin, double smax, int nmin, int nmax,
-                                              unsigned long long h, uint8_t &kind) {
+                                              unsigned long long h, uint8_t &kind, double &sa, int32_t &sj) {
     const bool ok = classify(C, Lv, Uv, len, smin, smax, nmin, nmax, kind);
     C.act[i] = make_double2(smin, smax);
     C.ninf[i] = make_int2(nmin, nmax);
@@ -174,22 +264,10 @@ __device__ __forceinline__ int32_t finish_row(const Ctx &C, int32_t i, int32_t b
     C.lp_changed[lp] = 1;
     if (kind == RK_SINGLETON) {
         // L <= a x_j <= U becomes a bound on x_j, always applied (no threshold)
-        const double a = C.A.val[beg];
-        const int32_t j = C.A.idx[beg];
-        C.rec_ra[o] = C.cmap[j];
-        C.rec_rv[o] = a;
-        const bool Lf = is_fin(Lv), Uf = is_fin(Uv);
-        double cl, cu;
-        if (!is_neg(a)) {
-            cl = Lf ? Lv / a : ninf_();
-            cu = Uf ? Uv / a : pinf();
-        } else {
-            cl = Uf ? Uv / a : ninf_();
-            cu = Lf ? Lv / a : pinf();
-        }
-        if (is_fin(cl)) atomic_max_dbl(&C.cand_l[j], cl);
-        if (is_fin(cu)) atomic_min_dbl(&C.cand_u[j], cu);
-        if (is_fin(cl) || is_fin(cu)) touch_col(C, j);
+        sa = C.A.val[beg];
+        sj = C.A.idx[beg];
+        C.rec_ra[o] = C.cmap[sj];
+        C.rec_rv[o] = sa;
     } else {
         C.rec_ra[o] = -1;
         C.rec_rv[o] = 0.0;
@@ -206,18 +284,21 @@ __device__ __forceinline__ unsigned long long len_hash(int32_t len) {
 
 // ------------------------------------------------------- S1 + S2 + S3 groups
 template <int W>
-__device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, int32_t &removed, int32_t &evaluated) {
+__device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, int32_t &removed, int32_t &evaluated,
+                                           CandQueue &q) {
     const unsigned mask = group_mask<W>();
     const int lane = threadIdx.x & (W - 1);
     // A row none of whose bounds, entries or sides changed since its last
     // evaluation has the same activities and class (kept) and yields the same
-    // implied bounds, which were then already applied or rejected: skip it.
+    // implied bounds, which were then already applied or rejected: skip it
+    // (its lanes stay for the warp's queue steps).
+    bool act = valid;
     if (valid && !C.rdirty[i]) {
         if (lane == 0) C.rkind[i] = RK_KEPT;
-        return;
+        act = false;
     }
     int32_t beg = 0, end = 0;
-    if (valid) {
+    if (act) {
         beg = C.A.ptr[i];
         end = C.A.ptr[i + 1];
     }
@@ -242,23 +323,52 @@ __device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, 
     nmin = group_sum<W>(nmin, mask);
     nmax = group_sum<W>(nmax, mask);
     h = group_sum<W>(h, mask);
-    if (!valid) return;
     const int32_t len = end - beg;
-    h += len_hash(len);
-    if (lane == 0) evaluated += len;
-    const double Lv = C.L[i], Uv = C.U[i];
-    uint8_t kind = RK_KEPT;
-    if (lane == 0) removed += finish_row(C, i, beg, len, Lv, Uv, smin, smax, nmin, nmax, h, kind);
-    kind = (uint8_t)__shfl_sync(mask, (int)kind, 0, W);
-    if (kind != RK_KEPT || len < 2) return;
-    const bool up_row = is_fin(Uv) && nmin <= 1, lo_row = is_fin(Lv) && nmax <= 1;
-    if (!up_row && !lo_row) return;
-    const double dU = Uv - smin, dL = Lv - smax;
-    for (int32_t k = beg + lane; k < end; k += W)
-        tighten_entry(C, C.A.idx[k], C.A.val[k], up_row, lo_row, dU, dL, nmin, nmax);
+    bool up_row = false, lo_row = false;
+    double dU = 0.0, dL = 0.0, Lv = 0.0, Uv = 0.0, sa = 0.0;
+    int32_t sj = -1;
+    if (act) {
+        h += len_hash(len);
+        if (lane == 0) evaluated += len;
+        Lv = C.L[i];
+        Uv = C.U[i];
+        uint8_t kind = RK_KEPT;
+        if (lane == 0) removed += finish_row(C, i, beg, len, Lv, Uv, smin, smax, nmin, nmax, h, kind, sa, sj);
+        kind = (uint8_t)__shfl_sync(mask, (int)kind, 0, W);
+        if (kind == RK_KEPT && len >= 2) {
+            up_row = is_fin(Uv) && nmin <= 1;
+            lo_row = is_fin(Lv) && nmax <= 1;
+            dU = Uv - smin;
+            dL = Lv - smax;
+        }
+    }
+    // a singleton row's bounds L/a and U/a (a < 0 swaps them)
+    const bool sing = sj >= 0, sneg = is_neg(sa);
+    cq_push(C, q, sing && is_fin(Lv), Lv, sa, sj, sneg ? CQ_SING_UPPER : CQ_SING_LOWER);
+    cq_push(C, q, sing && is_fin(Uv), Uv, sa, sj, sneg ? CQ_SING_LOWER : CQ_SING_UPPER);
+    // S3 over the row's entries, in steps the whole warp takes together
+    const int32_t trips = (up_row || lo_row) && lane < len ? (len - lane + W - 1) / W : 0;
+    const int32_t T = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)trips);
+    for (int32_t it = 0; it < T; it++) {
+        bool w1 = false, w2 = false;
+        double x1 = 0.0, x2 = 0.0, a = 0.0;
+        int32_t j = 0, k1 = 0, k2 = 0;
+        if (it < trips) {
+            const int32_t k = beg + lane + it * W;
+            j = C.A.idx[k];
+            a = C.A.val[k];
+            tighten_tests(C, j, a, up_row, lo_row, dU, dL, nmin, nmax, w1, x1, k1, w2, x2, k2);
+        }
+        cq_push(C, q, w1, x1, a, j, k1);
+        cq_push(C, q, w2, x2, a, j, k2);
+    }
 }
 
 __global__ void __launch_bounds__(kBlock) k_prop_groups(Ctx C, GroupGrid g) {
+    __shared__ double s_qx[kBlock / 32][kQueueCap], s_qa[kBlock / 32][kQueueCap];
+    __shared__ int32_t s_qj[kBlock / 32][kQueueCap], s_qk[kBlock / 32][kQueueCap];
+    const int warp = threadIdx.x >> 5;
+    CandQueue q{s_qx[warp], s_qa[warp], s_qj[warp], s_qk[warp], 0};
     const int c = grid_class(g, blockIdx.x);
     const int32_t lb = blockIdx.x - g.blk_start[c];
     int32_t removed = 0, evaluated = 0;
@@ -267,13 +377,14 @@ __global__ void __launch_bounds__(kBlock) k_prop_groups(Ctx C, GroupGrid g) {
     const bool valid = pos < C.A.cls_start[c + 1];
     const int32_t i = valid ? C.A.order[pos] : 0;
     switch (c) {
-        case 0: prop_group<1>(C, i, valid, removed, evaluated); break;
-        case 1: prop_group<2>(C, i, valid, removed, evaluated); break;
-        case 2: prop_group<4>(C, i, valid, removed, evaluated); break;
-        case 3: prop_group<8>(C, i, valid, removed, evaluated); break;
-        case 4: prop_group<16>(C, i, valid, removed, evaluated); break;
-        default: prop_group<32>(C, i, valid, removed, evaluated); break;
+        case 0: prop_group<1>(C, i, valid, removed, evaluated, q); break;
+        case 1: prop_group<2>(C, i, valid, removed, evaluated, q); break;
+        case 2: prop_group<4>(C, i, valid, removed, evaluated, q); break;
+        case 3: prop_group<8>(C, i, valid, removed, evaluated, q); break;
+        case 4: prop_group<16>(C, i, valid, removed, evaluated, q); break;
+        default: prop_group<32>(C, i, valid, removed, evaluated, q); break;
     }
+    cq_flush(C, q);
     block_add(removed, &C.st->rows_removed);
     block_add(evaluated, &C.st->nnz_eval);
 }
@@ -352,7 +463,9 @@ __global__ void k_prop_long_combine(Ctx C, const unsigned long long *ch_hash) {
         h += len_hash(len);
         const double Lv = C.L[i], Uv = C.U[i];
         uint8_t kind;
-        removed = finish_row(C, i, beg, len, Lv, Uv, smin, smax, nmin, nmax, h, kind);
+        double sa = 0.0;
+        int32_t sj = -1;  // long rows are never singletons
+        removed = finish_row(C, i, beg, len, Lv, Uv, smin, smax, nmin, nmax, h, kind, sa, sj);
         evaluated = len;
         const bool need = kind == RK_KEPT && ((is_fin(Uv) && nmin <= 1) || (is_fin(Lv) && nmax <= 1));
         C.lneed[t] = need;
