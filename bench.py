@@ -330,7 +330,7 @@ def main():
     nnz_proc = 0
     launches = 0
     rounds = None
-    results = []
+    first = None
     with ClockSampler(local) as clk:
         barrier()
         ev0.record(stream)
@@ -339,7 +339,9 @@ def main():
             nnz_proc += int(r.info.nnz_processed)
             launches += int(r.info.launches)
             rounds = r.rounds
-            results.append(r)
+            if first is None:  # host-side copies: no device work
+                first = (r.info, [float(x) for x in r.round_ms], [int(x) for x in r.round_nnz])
+            r.close()  # the reduced LP is handed on and freed, as a caller would
         ev1.record(stream)
         barrier()
     ms_total = ev0.elapsed_time(ev1)
@@ -347,12 +349,7 @@ def main():
         print(json.dumps({"profile": True, "steps": args.steps, "ms_per_step": ms_total / max(1, args.steps),
                           "nnz": lp.nnz}), flush=True)
         return
-    first = results[0]
-    info = first.info
-    round_ms = [float(x) for x in first.round_ms]
-    round_nnz = [int(x) for x in first.round_nnz]
-    for r in results:
-        r.close()
+    info, round_ms, round_nnz = first
     ms_max, value = reduce_over_ranks(ms_total, nnz_proc, dev, ws)
 
     # per-kernel times: one more step with CUDA events around every launch family

@@ -364,6 +364,10 @@ __device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, 
     }
 }
 
+// Lanes per row in S1-S3: one thread per row up to 16 entries (the row's
+// classification then runs on every lane of the warp), else the class width.
+__host__ __device__ __forceinline__ int prop_lanes(int c) { return c <= 2 ? 1 : 1 << c; }
+
 __global__ void __launch_bounds__(kBlock) k_prop_groups(Ctx C, GroupGrid g) {
     __shared__ double s_qx[kBlock / 32][kQueueCap], s_qa[kBlock / 32][kQueueCap];
     __shared__ int32_t s_qj[kBlock / 32][kQueueCap], s_qk[kBlock / 32][kQueueCap];
@@ -372,14 +376,14 @@ __global__ void __launch_bounds__(kBlock) k_prop_groups(Ctx C, GroupGrid g) {
     const int c = grid_class(g, blockIdx.x);
     const int32_t lb = blockIdx.x - g.blk_start[c];
     int32_t removed = 0, evaluated = 0;
-    const int W = 1 << c;
+    const int W = prop_lanes(c);
     const int32_t pos = C.A.cls_start[c] + lb * (kBlock / W) + threadIdx.x / W;
     const bool valid = pos < C.A.cls_start[c + 1];
     const int32_t i = valid ? C.A.order[pos] : 0;
     switch (c) {
-        case 0: prop_group<1>(C, i, valid, removed, evaluated, q); break;
-        case 1: prop_group<2>(C, i, valid, removed, evaluated, q); break;
-        case 2: prop_group<4>(C, i, valid, removed, evaluated, q); break;
+        case 0:
+        case 1:
+        case 2: prop_group<1>(C, i, valid, removed, evaluated, q); break;
         case 3: prop_group<8>(C, i, valid, removed, evaluated, q); break;
         case 4: prop_group<16>(C, i, valid, removed, evaluated, q); break;
         default: prop_group<32>(C, i, valid, removed, evaluated, q); break;
@@ -882,7 +886,14 @@ inline unsigned blocks_for(int64_t cnt, int threads) {
 }  // namespace
 
 void launch_prop(const Ctx &C, cudaStream_t s) {
-    const GroupGrid g = group_grid(C.A);
+    GroupGrid g;  // blocks per class at prop_lanes(c) lanes per row
+    int32_t acc = 0;
+    for (int c = 0; c < 6; c++) {
+        g.blk_start[c] = acc;
+        const int32_t per = kBlock / prop_lanes(c);
+        acc += (C.A.cls_start[c + 1] - C.A.cls_start[c] + per - 1) / per;
+    }
+    g.blk_start[6] = acc;
     if (g.blk_start[6] > 0) (k_prop_groups<<<g.blk_start[6], kBlock, 0, s>>>(C, g), note_launch());
     const int32_t nlong = C.A.cls_start[7] - C.A.cls_start[6];
     if (nlong > 0 && C.A.nchunks > 0) {

@@ -299,9 +299,13 @@ lpp_status lpp_presolve(const lpp_lp *in, const lpp_opts *opts, lpp_reduced **ou
         auto E = std::make_unique<Engine>();
         Member mm{in->m, in->n, in->nnz, 0, 0, 0, in->obj_offset};
         E->setup(o, 1, {mm});
+        // ingest: checks, copies, CSC, schedules (bytes: the input once, the CSC written)
+        E->tbegin(F_INGEST, 24.0 * in->nnz + 48.0 * in->m + 40.0 * in->n);
         E->ingest_plain(*in);
         E->prepare();
+        E->tend();
         E->run();
+        E->tbegin(F_FINISH, 0.0);  // records and the reduced LP handed over
         double offset = 0.0;
         LPP_CUDA(cudaMemcpyAsync(&offset, E->K.offset, sizeof(double), cudaMemcpyDeviceToHost, E->s));
         auto D = take_records(*E);
@@ -334,6 +338,7 @@ lpp_status lpp_presolve(const lpp_lp *in, const lpp_opts *opts, lpp_reduced **ou
         R->owned.push_back(R->lb);
         R->owned.push_back(R->ub);
         split_lu(D->lu, R->n, R->lb, R->ub, E->s);
+        E->tend();
         LPP_CUDA(cudaStreamSynchronize(E->s));
         R->obj_offset = offset;
         lpp_postsolve *P = make_postsolve(*E, D, 0, R->m, R->n, R->nnz, offset, 0, 0, E->act_m);

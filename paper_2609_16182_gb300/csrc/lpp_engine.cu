@@ -146,7 +146,8 @@ __global__ void k_sizes(const CompactCtx K, int32_t m, int32_t n, DevStatus *st)
     st->nnz_new_t = K.c_off[n];
 }
 
-const char *kFamNames[F_NUM] = {"prop", "colfin", "s5", "compact_count", "scan", "compact_scatter", "schedule"};
+const char *kFamNames[F_NUM] = {"prop",     "colfin",   "s5",     "compact_count", "scan", "compact_scatter",
+                                "schedule", "ingest",   "finish"};
 
 }  // namespace
 

@@ -161,7 +161,7 @@ struct Engine {
 };
 
 // Kernel families reported by lpp_result_kernels.
-enum Fam { F_PROP = 0, F_COLFIN, F_S5, F_COUNT, F_SCAN, F_SCATTER, F_SCHED, F_NUM };
+enum Fam { F_PROP = 0, F_COLFIN, F_S5, F_COUNT, F_SCAN, F_SCATTER, F_SCHED, F_INGEST, F_FINISH, F_NUM };
 const char *fam_name(int f);
 
 // device allocations shared by the reduced LPs of one batch, freed with the last
