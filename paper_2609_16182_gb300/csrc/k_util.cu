@@ -296,13 +296,34 @@ __global__ void k_ingest_cols(const double *lb, const double *ub, const double *
 }
 
 // ------------------------------------------------------ stable transpose
+// LSD radix sort of the entries by column, 8 bits per pass, tiles of
+// kRadixTile keys.  Each warp owns a contiguous chunk of 512 keys of its tile
+// and ranks them with a running per-warp digit count; the tile is then sorted
+// stably in shared memory and written out digit run by digit run (coalesced).
+constexpr int kRadixTile = 4096;
+constexpr int kRadixWarps = kScanThreads / 32;
+constexpr int kRadixChunk = kRadixTile / kRadixWarps;  // 512 keys per warp
+constexpr int kRadixSteps = kRadixChunk / 32;          // 16
+
+// lanes of the warp holding the same 8-bit digit d (d = 256: none), from 9
+// independent full-warp ballots; every lane of the warp must call it
+__device__ __forceinline__ unsigned digit_peers(int d) {
+    unsigned m = __ballot_sync(0xffffffffu, d < 256);
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+        const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1);
+        m &= ((d >> b) & 1) ? bb : ~bb;
+    }
+    return d < 256 ? m : 0u;
+}
+
 __global__ void __launch_bounds__(kScanThreads) k_radix_hist(const uint32_t *keys, int64_t cnt, int shift,
                                                              int32_t *hist, int32_t ntiles) {
     __shared__ int32_t s_h[256];
     s_h[threadIdx.x] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    for (int t = threadIdx.x; t < kScanTile; t += kScanThreads) {
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    for (int t = threadIdx.x; t < kRadixTile; t += kScanThreads) {
         const int64_t k = base + t;
         if (k < cnt) atomicAdd(&s_h[(keys[k] >> shift) & 255u], 1);
     }
@@ -310,52 +331,84 @@ __global__ void __launch_bounds__(kScanThreads) k_radix_hist(const uint32_t *key
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = s_h[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_radix_scatter(const uint32_t *kin, const int32_t *vin,
-                                                                int64_t cnt, int shift, const int32_t *off,
-                                                                int32_t ntiles, uint32_t *kout, int32_t *vout) {
-    __shared__ int32_t s_run[256];
-    __shared__ int32_t s_tot[256];
-    __shared__ int32_t s_w[kScanThreads / 32][256];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    s_run[threadIdx.x] = 0;
-    for (int w = 0; w < kScanThreads / 32; w++) s_w[w][threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    for (int r = 0; r < kPerThread; r++) {
-        const int64_t k = base + (int64_t)r * kScanThreads + threadIdx.x;
-        const bool valid = k < cnt;
-        const uint32_t key = valid ? kin[k] : 0u;
-        const int32_t v = valid ? vin[k] : 0;
-        const int d = valid ? (int)((key >> shift) & 255u) : 256;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const int rank = __popc(peers & ((1u << lane) - 1u));
-        if (valid && rank == 0) s_w[warp][d] = __popc(peers);
-        __syncthreads();
-        {
-            int32_t acc = 0;
-            for (int w = 0; w < kScanThreads / 32; w++) {
-                const int32_t t = s_w[w][threadIdx.x];
-                s_w[w][threadIdx.x] = acc;
-                acc += t;
-            }
-            s_tot[threadIdx.x] = acc;
-        }
-        __syncthreads();
-        if (valid) {
-            const int32_t pos = off[(int64_t)d * ntiles + blockIdx.x] + s_run[d] + s_w[warp][d] + rank;
-            kout[pos] = key;
-            vout[pos] = v;
-        }
-        __syncthreads();
-        s_run[threadIdx.x] += s_tot[threadIdx.x];
-        for (int w = 0; w < kScanThreads / 32; w++) s_w[w][threadIdx.x] = 0;
-        __syncthreads();
-    }
-}
+struct RadixOut {
+    uint32_t *kout;
+    int32_t *vout;  // payload: the entry index
+};
 
-__global__ void k_count_cols(const int32_t *idx, int64_t nnz, int32_t *colcnt) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < nnz) atomicAdd(&colcnt[idx[k]], 1);
+// first: the payload is the entry index itself (vin unused)
+__global__ void __launch_bounds__(kScanThreads) k_radix_scatter(const uint32_t *kin, const int32_t *vin, bool first,
+                                                                int64_t cnt, int shift, const int32_t *off,
+                                                                int32_t ntiles, RadixOut o) {
+    __shared__ int32_t s_wh[kRadixWarps][256];
+    __shared__ int32_t s_dbase[256];
+    __shared__ int32_t s_goff[256];
+    __shared__ int32_t s_wsum[kRadixWarps];
+    __shared__ uint32_t s_k[kRadixTile];
+    __shared__ int32_t s_v[kRadixTile];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int w = 0; w < kRadixWarps; w++) s_wh[w][threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    int32_t rk[kRadixSteps];
+    int dg[kRadixSteps];
+#pragma unroll
+    for (int i = 0; i < kRadixSteps; i++) {  // all loads first
+        const int64_t k = base + warp * kRadixChunk + i * 32 + lane;
+        dg[i] = k < cnt ? (int)((kin[k] >> shift) & 255u) : 256;
+    }
+#pragma unroll
+    for (int i = 0; i < kRadixSteps; i++) {
+        const int d = dg[i];
+        const unsigned peers = digit_peers(d);
+        const int run = d < 256 ? s_wh[warp][d] : 0;
+        rk[i] = run + __popc(peers & ((1u << lane) - 1u));
+        __syncwarp();
+        if (d < 256 && lane == __ffs(peers) - 1) s_wh[warp][d] = run + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: warps in order, then the tile's digits in order
+    const int d0 = threadIdx.x;
+    int32_t tot = 0;
+    for (int w = 0; w < kRadixWarps; w++) {
+        const int32_t c = s_wh[w][d0];
+        s_wh[w][d0] = tot;
+        tot += c;
+    }
+    int32_t inc = tot;
+#pragma unroll
+    for (int o2 = 1; o2 < 32; o2 <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, inc, o2);
+        if (lane >= o2) inc += y;
+    }
+    if (lane == 31) s_wsum[warp] = inc;
+    s_goff[d0] = off[(int64_t)d0 * ntiles + blockIdx.x];
+    __syncthreads();
+    int32_t wpre = 0;
+    for (int w = 0; w < warp; w++) wpre += s_wsum[w];
+    s_dbase[d0] = wpre + inc - tot;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kRadixSteps; i++) {  // the keys again (L1/L2), now to their sorted slots
+        const int64_t k = base + warp * kRadixChunk + i * 32 + lane;
+        if (k < cnt) {
+            const uint32_t key = kin[k];
+            const int d = (int)((key >> shift) & 255u);
+            const int32_t p = s_dbase[d] + s_wh[warp][d] + rk[i];
+            s_k[p] = key;
+            s_v[p] = first ? (int32_t)k : vin[k];
+        }
+    }
+    __syncthreads();
+    const int32_t ntile = (int32_t)(cnt - base < kRadixTile ? cnt - base : kRadixTile);
+    for (int q = threadIdx.x; q < ntile; q += kScanThreads) {
+        const uint32_t kk = s_k[q];
+        const int d = (int)((kk >> shift) & 255u);
+        const int32_t g = s_goff[d] + (q - s_dbase[d]);
+        o.kout[g] = kk;
+        o.vout[g] = s_v[q];
+    }
 }
 
 __global__ void k_gather_t(const int32_t *perm, const int32_t *row_of, const double *val, int64_t nnz,
@@ -367,11 +420,16 @@ __global__ void k_gather_t(const int32_t *perm, const int32_t *row_of, const dou
     tval[p] = val[e];
 }
 
-__global__ void k_copy_keys(const int32_t *idx, int64_t nnz, uint32_t *keys, int32_t *vals) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nnz) return;
-    keys[k] = (uint32_t)idx[k];
-    vals[k] = (int32_t)k;
+// A^T row pointers from the sorted column keys: key[p] starts column j's
+// run at p for every j in (key[p-1], key[p]]; columns after the last key end at nnz
+__global__ void k_colptr_from_keys(const uint32_t *key, int64_t nnz, int32_t n, int32_t *tptr) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nnz) return;
+    const int32_t kp = (int32_t)key[p];
+    const int32_t kq = p == 0 ? -1 : (int32_t)key[p - 1];
+    for (int32_t j = kq + 1; j <= kp; j++) tptr[j] = (int32_t)p;
+    if (p == nnz - 1)
+        for (int32_t j = kp + 1; j <= n; j++) tptr[j] = (int32_t)nnz;
 }
 
 __global__ void k_iota(int32_t *a, int32_t cnt, int32_t base) {
@@ -470,34 +528,37 @@ void ingest_vectors(const double *lhs, const double *rhs, const double *lb, cons
     if (n > 0) (k_ingest_cols<<<blocks_for(n, 256), 256, 0, s>>>(lb, ub, c, n, huge, lu, cc, err), note_launch());
 }
 
-size_t transpose_hist_elems(int64_t nnz) { return (size_t)256 * (size_t)((nnz + kScanTile - 1) / kScanTile) + 1; }
+size_t transpose_hist_elems(int64_t nnz) { return (size_t)256 * (size_t)((nnz + kRadixTile - 1) / kRadixTile) + 1; }
 
 void transpose(const int32_t *ptr, const int32_t *idx, const double *val, const int32_t *row_of, int32_t m,
                int32_t n, int64_t nnz, const TransposeBufs &b, int32_t *tptr, int32_t *tidx, double *tval,
-               int32_t *colcnt, cudaStream_t s) {
+               cudaStream_t s) {
     (void)ptr;
     (void)m;
-    // column pointers: counts then a scan
-    cudaMemsetAsync(colcnt, 0, sizeof(int32_t) * (size_t)(n + 1), s);
-    if (nnz > 0) (k_count_cols<<<blocks_for(nnz, 256), 256, 0, s>>>(idx, nnz, colcnt), note_launch());
-    scan_excl(colcnt, tptr, n, b.tmp, s);
-    if (nnz == 0) return;
+    if (nnz == 0) {
+        cudaMemsetAsync(tptr, 0, sizeof(int32_t) * (size_t)(n + 1), s);
+        return;
+    }
     // stable LSD radix sort of the entries by column (entries come row by row)
-    (k_copy_keys<<<blocks_for(nnz, 256), 256, 0, s>>>(idx, nnz, b.k0, b.v0), note_launch());
     int bits = 0;
     while (bits < 31 && ((int64_t)1 << bits) < (int64_t)n) bits++;
-    const int passes = (bits + 7) / 8;
-    const int32_t ntiles = (int32_t)((nnz + kScanTile - 1) / kScanTile);
-    uint32_t *kin = b.k0, *kout = b.k1;
-    int32_t *vin = b.v0, *vout = b.v1;
+    const int passes = bits > 0 ? (bits + 7) / 8 : 1;
+    const int32_t ntiles = (int32_t)((nnz + kRadixTile - 1) / kRadixTile);
+    const uint32_t *kin = reinterpret_cast<const uint32_t *>(idx);
+    const int32_t *vin = nullptr;
+    uint32_t *kbuf[2] = {b.k0, b.k1};
+    int32_t *vbuf[2] = {b.v0, b.v1};
     for (int p = 0; p < passes; p++) {
         (k_radix_hist<<<ntiles, kScanThreads, 0, s>>>(kin, nnz, 8 * p, b.hist, ntiles), note_launch());
         scan_excl(b.hist, b.hist, (int64_t)256 * ntiles, b.tmp, s);
-        (k_radix_scatter<<<ntiles, kScanThreads, 0, s>>>(kin, vin, nnz, 8 * p, b.hist, ntiles, kout, vout), note_launch());
-        std::swap(kin, kout);
-        std::swap(vin, vout);
+        RadixOut o{kbuf[p & 1], vbuf[p & 1]};
+        (k_radix_scatter<<<ntiles, kScanThreads, 0, s>>>(kin, vin, p == 0, nnz, 8 * p, b.hist, ntiles, o),
+         note_launch());
+        kin = kbuf[p & 1];
+        vin = vbuf[p & 1];
     }
     (k_gather_t<<<blocks_for(nnz, 256), 256, 0, s>>>(vin, row_of, val, nnz, tidx, tval), note_launch());
+    (k_colptr_from_keys<<<blocks_for(nnz, 256), 256, 0, s>>>(kin, nnz, n, tptr), note_launch());
 }
 
 void iota(int32_t *a, int32_t cnt, int32_t base, cudaStream_t s) {

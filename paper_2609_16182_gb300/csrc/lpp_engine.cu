@@ -428,7 +428,7 @@ void Engine::prepare() {
     tb.v1 = reinterpret_cast<int32_t *>(rv[1]) + nnz0;
     tb.hist = pool.alloc<int32_t>(transpose_hist_elems(nnz0));
     tb.tmp = scan_tmp;
-    transpose(rp[0], ci[0], rv[0], row_of + 1, m0, n0, nnz0, tb, tp[0], ti[0], tv[0], K.c_len, s);
+    transpose(rp[0], ci[0], rv[0], row_of + 1, m0, n0, nnz0, tb, tp[0], ti[0], tv[0], s);
     LPP_CUDA(cudaGetLastError());
     iota(rmap[0], m0, 0, s);
     iota(cmap[0], n0, 0, s);

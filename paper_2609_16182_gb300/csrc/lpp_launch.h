@@ -52,13 +52,13 @@ void ingest_vectors(const double *lhs, const double *rhs, const double *lb, cons
 struct TransposeBufs {
     uint32_t *k0, *k1;  // keys [nnz]
     int32_t *v0, *v1;   // values [nnz]
-    int32_t *hist;      // [256 * tiles + 1]
+    int32_t *hist;      // [transpose_hist_elems(nnz)]
     int32_t *tmp;       // scan temporary
 };
 size_t transpose_hist_elems(int64_t nnz);
 void transpose(const int32_t *ptr, const int32_t *idx, const double *val, const int32_t *row_of, int32_t m,
                int32_t n, int64_t nnz, const TransposeBufs &b, int32_t *tptr, int32_t *tidx, double *tval,
-               int32_t *colcnt, cudaStream_t s);
+               cudaStream_t s);
 void iota(int32_t *a, int32_t cnt, int32_t base, cudaStream_t s);
 void fill_u64(unsigned long long *a, int64_t cnt, unsigned long long v, cudaStream_t s);
 void fill_i32(int32_t *a, int64_t cnt, int32_t v, cudaStream_t s);

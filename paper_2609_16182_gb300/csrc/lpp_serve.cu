@@ -278,9 +278,9 @@ void Engine::append(int32_t slot, const lpp_lp &in, int32_t rbase, int32_t cbase
     tb.v1 = tmp.alloc<int32_t>(zl);
     tb.hist = tmp.alloc<int32_t>(transpose_hist_elems(zl));
     tb.tmp = stmp;
-    int32_t *ttp = tmp.alloc<int32_t>((size_t)nl + 1), *tti = tmp.alloc<int32_t>(zl), *cnt = tmp.alloc<int32_t>(nl + 1);
+    int32_t *ttp = tmp.alloc<int32_t>((size_t)nl + 1), *tti = tmp.alloc<int32_t>(zl);
     double *ttv = tmp.alloc<double>(zl);
-    transpose(rp_in, ci_in, rv_in, row_of + 1, ml, nl, zl, tb, ttp, tti, ttv, cnt, s);
+    transpose(rp_in, ci_in, rv_in, row_of + 1, ml, nl, zl, tb, ttp, tti, ttv, s);
     AppendArgs a;
     a.rp = rp_in;
     a.ci = ci_in;

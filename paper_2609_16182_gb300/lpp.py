@@ -359,19 +359,33 @@ def presolve(lp, options: Opts | None = None, **kw) -> Result:
     return Result(red.value, rec.value)
 
 
+class PackedLPs:
+    """An lpp_lp array for lpp_presolve_batch, built once and reusable (it
+    keeps the arrays or tensors it points to alive)."""
+
+    def __init__(self, lps):
+        self.keep: list = []
+        self.count = len(lps)
+        self.arr = (LpStruct * max(self.count, 1))()
+        for k, lp in enumerate(lps):
+            self.arr[k] = lp_struct(lp, self.keep)
+
+
+def pack_lps(lps) -> PackedLPs:
+    return PackedLPs(lps)
+
+
 def presolve_batch(lps, options: Opts | None = None, **kw) -> list[Result]:
-    """lpp_presolve_batch on a list of LPs (all host or all device)."""
+    """lpp_presolve_batch on a list of LPs (all host or all device), or on a
+    PackedLPs built by pack_lps."""
     L = load()
     o = options if options is not None else opts(**kw)
-    keep = []
-    cnt = len(lps)
-    arr = (LpStruct * max(cnt, 1))()
-    for k, lp in enumerate(lps):
-        arr[k] = lp_struct(lp, keep)
+    packed = lps if isinstance(lps, PackedLPs) else PackedLPs(lps)
+    cnt = packed.count
     reds = (C.c_void_p * max(cnt, 1))()
     recs = (C.c_void_p * max(cnt, 1))()
     per = (C.c_int32 * max(cnt, 1))()
-    _check(L.lpp_presolve_batch(arr, cnt, C.byref(o), reds, recs, per))
+    _check(L.lpp_presolve_batch(packed.arr, cnt, C.byref(o), reds, recs, per))
     return [Result(reds[k], recs[k]) for k in range(cnt)]
 
 
