@@ -51,46 +51,56 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu: int):
+    def __init__(self, gpu: int, period_ms: int = 50):
         self.gpu = gpu
-        self.rows = []
-        self._stop = threading.Event()
+        self.period_ms = period_ms
+        self.rows = []  # (arrival time, fields)
+        self.t0 = None  # the timed region, set by the caller
+        self.t1 = None
+        self._p = None
         self._t = None
 
     def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
-                if out.returncode == 0 and out.stdout.strip():
-                    self.rows.append([x.strip() for x in out.stdout.strip().split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+        try:
+            self._p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                        "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
+                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            return
+        for line in self._p.stdout:
+            if line.strip():
+                self.rows.append((time.monotonic(), [x.strip() for x in line.strip().split(",")]))
 
     def __enter__(self):
         self._t = threading.Thread(target=self._run, daemon=True)
         self._t.start()
+        time.sleep(0.2)  # the sampler is running before the timed region starts
         return self
 
     def __exit__(self, *a):
-        self._stop.set()
+        if self._p is not None:
+            self._p.terminate()
+            try:
+                self._p.wait(timeout=5)
+            except Exception:
+                self._p.kill()
         if self._t:
             self._t.join(timeout=10)
 
     def summary(self):
-        if not self.rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        rows = [r for t, r in self.rows if self.t0 is None or (self.t0 <= t <= (self.t1 or t))]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = set()
-        for r in self.rows:
+        for r in rows:
             for k, nm in enumerate(names):
                 if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.rows)}
+                "reasons": sorted(reasons), "samples": len(rows)}
 
 
 def reduce_over_ranks(ms_total: float, nnz_proc: int, device, world_size: int):
@@ -137,13 +147,13 @@ def batched_leg(lpp, synth, torch, dev, stream, count=4096):
     d = [synth.LP(m=lp.m, n=lp.n, **{k: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
                                      for k, v in lp.arrays().items()}) for lp in lps]
     o = lpp.opts(stream=stream.cuda_stream)
-    warm = lpp.presolve_batch(d[:64], o)
-    for r in warm:
+    packed = lpp.pack_lps(d)  # the lpp_lp array a C caller would hold
+    for r in lpp.presolve_batch(packed, o):  # warm-up at full size (memory pool)
         r.close()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    res = lpp.presolve_batch(d, o)
+    res = lpp.presolve_batch(packed, o)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     batch_ms = e0.elapsed_time(e1)
@@ -283,7 +293,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -333,6 +343,7 @@ def main():
     first = None
     with ClockSampler(local) as clk:
         barrier()
+        clk.t0 = time.monotonic()
         ev0.record(stream)
         for _ in range(args.steps):
             r = lpp.presolve(d_lp, o_dev)
@@ -344,6 +355,7 @@ def main():
             r.close()  # the reduced LP is handed on and freed, as a caller would
         ev1.record(stream)
         barrier()
+        clk.t1 = time.monotonic()
     ms_total = ev0.elapsed_time(ev1)
     if args.profile:
         print(json.dumps({"profile": True, "steps": args.steps, "ms_per_step": ms_total / max(1, args.steps),
