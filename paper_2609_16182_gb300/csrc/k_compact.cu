@@ -104,22 +104,39 @@ __global__ void __launch_bounds__(kBlock) k_csc_count_long(Ctx C, CompactCtx K) 
     }
 }
 
-// per long segment: chunk offsets (prefix in chunk order) and the total
+// per long segment (one warp): chunk offsets (prefix in chunk order), the
+// total, and the sum of the chunks' side shifts (lane-strided, then a butterfly)
 __global__ void k_long_prefix(const SegMat M, const int32_t *ch_cnt, int32_t *ch_off, int32_t *len_out,
                               const double *ch_shift, double *shift_out) {
-    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t t = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     const int32_t nlong = M.cls_start[7] - M.cls_start[6];
-    if (t >= nlong) return;
-    int32_t acc = 0;
+    if (t >= nlong) return;  // the same t in the whole warp
+    const int32_t q1 = M.lfirst[t + 1];
+    int32_t carry = 0;
     double sh = 0.0;
-    for (int32_t q = M.lfirst[t]; q < M.lfirst[t + 1]; q++) {
-        ch_off[q] = acc;
-        acc += ch_cnt[q];
-        if (ch_shift) sh += ch_shift[q];
+    for (int32_t q0 = M.lfirst[t]; q0 < q1; q0 += 32) {
+        const int32_t q = q0 + lane;
+        const int32_t c = q < q1 ? ch_cnt[q] : 0;
+        int32_t inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (q < q1) {
+            ch_off[q] = carry + inc - c;
+            if (ch_shift) sh += ch_shift[q];
+        }
+        carry += __shfl_sync(0xffffffffu, inc, 31);
     }
-    const int32_t seg = M.order[M.cls_start[6] + t];
-    len_out[seg] = acc;
-    if (shift_out) shift_out[seg] = sh;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sh += __shfl_xor_sync(0xffffffffu, sh, o);
+    if (lane == 0) {
+        const int32_t seg = M.order[M.cls_start[6] + t];
+        len_out[seg] = carry;
+        if (shift_out) shift_out[seg] = sh;
+    }
 }
 
 // ------------------------------------------------------- S6 + column keep
@@ -530,7 +547,8 @@ void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s) {
     const int32_t tlong = C.T.cls_start[7] - C.T.cls_start[6];
     if (tlong > 0 && C.T.nchunks > 0) {
         (k_csc_count_long<<<C.T.nchunks, kBlock, 0, s>>>(C, K), note_launch());
-        (k_long_prefix<<<blocks_for(tlong, 128), 128, 0, s>>>(C.T, K.cht_cnt, K.cht_off, K.c_len, nullptr, nullptr), note_launch());
+        (k_long_prefix<<<blocks_for((int64_t)tlong * 32, 128), 128, 0, s>>>(C.T, K.cht_cnt, K.cht_off, K.c_len, nullptr,
+                                                                             nullptr), note_launch());
     }
     if (C.n > 0) (k_colkeep<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C, K), note_launch());
     // 2. row counts over kept columns and the side shifts
@@ -539,8 +557,8 @@ void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s) {
     const int32_t along = C.A.cls_start[7] - C.A.cls_start[6];
     if (along > 0 && C.A.nchunks > 0) {
         (k_csr_count_long<<<C.A.nchunks, kBlock, 0, s>>>(C, K), note_launch());
-        (k_long_prefix<<<blocks_for(along, 128), 128, 0, s>>>(C.A, K.chr_cnt, K.chr_off, K.r_len, K.chr_shift,
-                                                               K.shift), note_launch());
+        (k_long_prefix<<<blocks_for((int64_t)along * 32, 128), 128, 0, s>>>(C.A, K.chr_cnt, K.chr_off, K.r_len,
+                                                                             K.chr_shift, K.shift), note_launch());
     }
 }
 

@@ -442,37 +442,49 @@ __global__ void __launch_bounds__(kBlock) k_prop_long_partial(Ctx C, unsigned lo
     }
 }
 
-__global__ void k_prop_long_combine(Ctx C, const unsigned long long *ch_hash) {
-    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+// one warp per long row: the chunk partials, lane-strided then a butterfly
+__global__ void __launch_bounds__(kBlock) k_prop_long_combine(Ctx C, const unsigned long long *ch_hash) {
+    const int32_t t = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     const int32_t nlong = C.A.cls_start[7] - C.A.cls_start[6];
     int32_t removed = 0, evaluated = 0;
-    if (t < nlong && !C.rdirty[C.A.order[C.A.cls_start[6] + t]]) {
-        C.rkind[C.A.order[C.A.cls_start[6] + t]] = RK_KEPT;
-        C.lneed[t] = 0;
-    } else if (t < nlong) {
+    if (t < nlong) {  // the same t in the whole warp
         const int32_t i = C.A.order[C.A.cls_start[6] + t];
-        double smin = 0.0, smax = 0.0;
-        int nmin = 0, nmax = 0;
-        unsigned long long h = 0;
-        for (int32_t q = C.A.lfirst[t]; q < C.A.lfirst[t + 1]; q++) {
-            const double2 a = C.ch_act[q];
-            const int2 c = C.ch_ninf[q];
-            smin += a.x;
-            smax += a.y;
-            nmin += c.x;
-            nmax += c.y;
-            h += ch_hash[q];
+        if (!C.rdirty[i]) {
+            if (lane == 0) {
+                C.rkind[i] = RK_KEPT;
+                C.lneed[t] = 0;
+            }
+        } else {
+            double smin = 0.0, smax = 0.0;
+            int nmin = 0, nmax = 0;
+            unsigned long long h = 0;
+            for (int32_t q = C.A.lfirst[t] + lane; q < C.A.lfirst[t + 1]; q += 32) {
+                const double2 a = C.ch_act[q];
+                const int2 c = C.ch_ninf[q];
+                smin += a.x;
+                smax += a.y;
+                nmin += c.x;
+                nmax += c.y;
+                h += ch_hash[q];
+            }
+            smin = group_sum<32>(smin, 0xffffffffu);
+            smax = group_sum<32>(smax, 0xffffffffu);
+            nmin = group_sum<32>(nmin, 0xffffffffu);
+            nmax = group_sum<32>(nmax, 0xffffffffu);
+            h = group_sum<32>(h, 0xffffffffu);
+            if (lane == 0) {
+                const int32_t beg = C.A.ptr[i], len = C.A.ptr[i + 1] - beg;
+                h += len_hash(len);
+                const double Lv = C.L[i], Uv = C.U[i];
+                uint8_t kind;
+                double sa = 0.0;
+                int32_t sj = -1;  // long rows are never singletons
+                removed = finish_row(C, i, beg, len, Lv, Uv, smin, smax, nmin, nmax, h, kind, sa, sj);
+                evaluated = len;
+                C.lneed[t] = kind == RK_KEPT && ((is_fin(Uv) && nmin <= 1) || (is_fin(Lv) && nmax <= 1));
+            }
         }
-        const int32_t beg = C.A.ptr[i], len = C.A.ptr[i + 1] - beg;
-        h += len_hash(len);
-        const double Lv = C.L[i], Uv = C.U[i];
-        uint8_t kind;
-        double sa = 0.0;
-        int32_t sj = -1;  // long rows are never singletons
-        removed = finish_row(C, i, beg, len, Lv, Uv, smin, smax, nmin, nmax, h, kind, sa, sj);
-        evaluated = len;
-        const bool need = kind == RK_KEPT && ((is_fin(Uv) && nmin <= 1) || (is_fin(Lv) && nmax <= 1));
-        C.lneed[t] = need;
     }
     block_add(removed, &C.st->rows_removed);
     block_add(evaluated, &C.st->nnz_eval);
@@ -771,26 +783,25 @@ __global__ void __launch_bounds__(kBlock) k_s5_tail_insert(Ctx C, const int32_t 
     C.rslot[i] = s5_insert_row(C, i, s5_tail_cap(C, n));
 }
 
+// one thread per listed row; rows longer than 32 entries are checked by the
+// whole warp in turn
 __global__ void __launch_bounds__(kBlock) k_s5_tail_match(Ctx C, const int32_t *list, const int32_t *cnt,
                                                          int32_t *out, int32_t *out_cnt) {
     const int32_t n = *cnt;
-    const int32_t t = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     int32_t removed = 0;
-    bool left = false;
-    int32_t i = -1;
+    bool left = false, act = false, ok = false;
+    int32_t i = -1, li = -1, bi = 0, bl = 0, len = 0;
+    double lam = 0.0;
     if (t < n) {
         i = list[t];
         const int32_t sl = C.rslot[i];
-        int32_t li = -1;
-        bool act = sl >= 0;
+        act = sl >= 0;
         if (act) {
             li = (int32_t)(uint32_t)(C.tlead[sl] & 0xffffffffULL);
             if (li == i) act = false;  // the leader itself
         }
-        int32_t bi = 0, bl = 0, len = 0;
-        bool ok = false;
-        double lam = 0.0;
         if (act) {
             bi = C.A.ptr[i];
             bl = C.A.ptr[li];
@@ -798,23 +809,37 @@ __global__ void __launch_bounds__(kBlock) k_s5_tail_match(Ctx C, const int32_t *
             ok = (C.A.ptr[li + 1] - bl) == len;
             lam = C.A.val[bi] / C.A.val[bl];
         }
-        if (ok) {
-            for (int32_t k = lane; k < len; k += 32) {
-                const double ai = C.A.val[bi + k], al = C.A.val[bl + k];
-                const double la = lam * al;
-                if (!(C.A.idx[bi + k] == C.A.idx[bl + k] && fabs(ai - la) <= C.par_tol * fmax(fabs(ai), fabs(la))))
-                    ok = false;
+    }
+    if (ok && len <= 32) {
+        for (int32_t k = 0; k < len; k++) {
+            const double ai = C.A.val[bi + k], la = lam * C.A.val[bl + k];
+            if (!(C.A.idx[bi + k] == C.A.idx[bl + k] && fabs(ai - la) <= C.par_tol * fmax(fabs(ai), fabs(la)))) {
+                ok = false;
+                break;
             }
         }
-        ok = __all_sync(0xffffffffu, ok) != 0;  // the warp's lanes share t
-        if (lane == 0) {
-            if (act && ok) {
-                s5_accept(C, i, li, lam);
-                removed = 1;
-            } else if (act) {
-                left = true;
-            }
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, ok && len > 32);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1u;
+        const int32_t sbi = __shfl_sync(0xffffffffu, bi, src), sbl = __shfl_sync(0xffffffffu, bl, src);
+        const int32_t slen = __shfl_sync(0xffffffffu, len, src);
+        const double slam = __shfl_sync(0xffffffffu, lam, src);
+        bool sok = true;
+        for (int32_t k = lane; k < slen; k += 32) {
+            const double ai = C.A.val[sbi + k], la = slam * C.A.val[sbl + k];
+            if (!(C.A.idx[sbi + k] == C.A.idx[sbl + k] && fabs(ai - la) <= C.par_tol * fmax(fabs(ai), fabs(la))))
+                sok = false;
         }
+        sok = __all_sync(0xffffffffu, sok) != 0;
+        if (lane == src) ok = sok;
+    }
+    if (act && ok) {
+        s5_accept(C, i, li, lam);
+        removed = 1;
+    } else if (act) {
+        left = true;
     }
     block_add(removed, &C.st->rows_removed);
     block_append(left, i, out_cnt, out);
@@ -862,14 +887,29 @@ __global__ void __launch_bounds__(kBlock) k_s5_leader(Ctx C) {
 
 // rows of a column whose bounds changed must be re-evaluated next round
 // rows of the changed short columns need their activities next round: one
-// warp per listed column
+// thread per listed column; columns longer than 32 entries are walked by the
+// whole warp in turn
 __global__ void __launch_bounds__(kBlock) k_mark_list(Ctx C) {
     const int32_t cnt = *C.cl_cnt;
     const int lane = threadIdx.x & 31;
-    const int32_t nw = (int32_t)((gridDim.x * (int64_t)blockDim.x) >> 5);
-    for (int32_t t = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); t < cnt; t += nw) {
-        const int32_t j = C.cl_list[t];
-        for (int32_t k = C.T.ptr[j] + lane; k < C.T.ptr[j + 1]; k += 32) C.rdnext[C.T.idx[k]] = 1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < cnt; base += stride) {
+        const int64_t t = base + lane;
+        int32_t b = 0, e = 0;
+        if (t < cnt) {
+            const int32_t j = C.cl_list[t];
+            b = C.T.ptr[j];
+            e = C.T.ptr[j + 1];
+        }
+        if (e - b <= 32)
+            for (int32_t k = b; k < e; k++) C.rdnext[C.T.idx[k]] = 1;
+        unsigned todo = __ballot_sync(0xffffffffu, e - b > 32);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const int32_t sb = __shfl_sync(0xffffffffu, b, src), se = __shfl_sync(0xffffffffu, e, src);
+            for (int32_t k = sb + lane; k < se; k += 32) C.rdnext[C.T.idx[k]] = 1;
+        }
     }
 }
 
@@ -898,7 +938,7 @@ void launch_prop(const Ctx &C, cudaStream_t s) {
     const int32_t nlong = C.A.cls_start[7] - C.A.cls_start[6];
     if (nlong > 0 && C.A.nchunks > 0) {
         (k_prop_long_partial<<<C.A.nchunks, kBlock, 0, s>>>(C, C.ch_hash), note_launch());
-        (k_prop_long_combine<<<blocks_for(nlong, kBlock), kBlock, 0, s>>>(C, C.ch_hash), note_launch());
+        (k_prop_long_combine<<<blocks_for((int64_t)nlong * 32, kBlock), kBlock, 0, s>>>(C, C.ch_hash), note_launch());
         (k_prop_long_tighten<<<C.A.nchunks, kBlock, 0, s>>>(C), note_launch());
     }
 }
@@ -911,8 +951,7 @@ void launch_colfin(const Ctx &C, bool full, cudaStream_t s) {
 
 void launch_mark_dirty(const Ctx &C, cudaStream_t s) {
     if (C.n <= 0) return;
-    (k_mark_list<<<std::min<unsigned>(blocks_for((int64_t)C.n * 32, kBlock), 8u * 152u), kBlock, 0, s>>>(C),
-     note_launch());
+    (k_mark_list<<<std::min<unsigned>(blocks_for(C.n, kBlock), 8u * 152u), kBlock, 0, s>>>(C), note_launch());
     if (C.T.cls_start[7] > C.T.cls_start[6] && C.T.nchunks > 0) (k_mark_long<<<C.T.nchunks, kBlock, 0, s>>>(C), note_launch());
 }
 
@@ -929,8 +968,7 @@ void launch_s5_tail(const Ctx &C, const int32_t *list, const int32_t *cnt, int32
                     int32_t max_rows, cudaStream_t s) {
     if (max_rows <= 0) return;
     (k_s5_tail_insert<<<blocks_for(max_rows, kBlock), kBlock, 0, s>>>(C, list, cnt), note_launch());
-    (k_s5_tail_match<<<blocks_for((int64_t)max_rows * 32, kBlock), kBlock, 0, s>>>(C, list, cnt, out, out_cnt),
-     note_launch());
+    (k_s5_tail_match<<<blocks_for(max_rows, kBlock), kBlock, 0, s>>>(C, list, cnt, out, out_cnt), note_launch());
     (k_s5_tail_clear<<<blocks_for(max_rows, kBlock), kBlock, 0, s>>>(C, list, cnt), note_launch());
 }
 
