@@ -60,38 +60,34 @@ __device__ __forceinline__ bool gt0(double s) { return dbits(s) > 0; }
 // |x/a| <= max_implied, thr = uold - bound_tol*max(1,|uold|) (one rounding).
 // Both tests are decided exactly on the real quotient by the sign of one
 // fused multiply-add; the cap is tested only for candidates that pass.
-// A candidate that cannot lower the column's current minimum cur (x/a >= cur,
-// again the sign of one FMA) is dropped first: it would not change the
-// result, and it skips the threshold test and the divide.  pass_upper makes
-// the sign tests; apply_cand the cap, the divide and the atomic.
+// A candidate that cannot lower the column's current minimum cur (x/a >= cur)
+// would not change the result: it is dropped by the same test, made against
+// min(cur, thr), and skips the divide.  pass_upper makes the sign test;
+// apply_cand the cap, the divide and the atomic.
 __device__ __forceinline__ bool pass_upper(const Ctx &C, int32_t j, double x, double a, double uold) {
-    const unsigned long long ec = *((volatile unsigned long long *)&C.cand_u[j]);
-    if (ec != kEncPosInf) {
-        const double s = fma(-dec_dbl(ec), a, x);
-        if (is_neg(a) ? !gt0(s) : !lt0(s)) return false;
-    }
+    // x/a must lie below both cur and thr: one test against min(cur, thr),
+    // taken on the order-preserving encoding (integer pipes)
+    unsigned long long e = *((volatile unsigned long long *)&C.cand_u[j]);
     if (is_fin(uold)) {
-        const double thr = fma(-C.bound_tol, max1abs(uold), uold);
-        const double s = fma(-thr, a, x);
-        if (is_neg(a) ? !gt0(s) : !lt0(s)) return false;
+        const unsigned long long et = enc_dbl(fma(-C.bound_tol, max1abs(uold), uold));
+        e = et < e ? et : e;
     }
-    return true;
+    if (e == kEncPosInf) return true;
+    const double s = fma(-dec_dbl(e), a, x);
+    return is_neg(a) ? gt0(s) : lt0(s);
 }
 // Implied lower bound x/a: accepted iff (lold = -inf or x/a > thr) and
 // |x/a| <= max_implied, thr = lold + bound_tol*max(1,|lold|); a candidate
-// that cannot raise the current maximum is dropped first.
+// that cannot raise the current maximum is dropped with it.
 __device__ __forceinline__ bool pass_lower(const Ctx &C, int32_t j, double x, double a, double lold) {
-    const unsigned long long ec = *((volatile unsigned long long *)&C.cand_l[j]);
-    if (ec != kEncNegInf) {
-        const double s = fma(-dec_dbl(ec), a, x);
-        if (is_neg(a) ? !lt0(s) : !gt0(s)) return false;
-    }
+    unsigned long long e = *((volatile unsigned long long *)&C.cand_l[j]);
     if (is_fin(lold)) {
-        const double thr = fma(C.bound_tol, max1abs(lold), lold);
-        const double s = fma(-thr, a, x);
-        if (is_neg(a) ? !lt0(s) : !gt0(s)) return false;
+        const unsigned long long et = enc_dbl(fma(C.bound_tol, max1abs(lold), lold));
+        e = et > e ? et : e;
     }
-    return true;
+    if (e == kEncNegInf) return true;
+    const double s = fma(-dec_dbl(e), a, x);
+    return is_neg(a) ? lt0(s) : gt0(s);
 }
 
 // candidate kinds: implied bounds (capped) and singleton-row bounds (not)
@@ -507,7 +503,8 @@ __global__ void __launch_bounds__(kBlock) k_prop_long_tighten(Ctx C) {
 // S3' + S4 on column j: apply the accepted candidates, check and snap the
 // bounds, fix the column if l == u.  Returns (changed, fixed) through refs;
 // a changed short column is listed for the dirty-row marking.
-__device__ __forceinline__ void colfin_one(const Ctx &C, int32_t j, bool full, int32_t &changed, int32_t &fixed) {
+__device__ __forceinline__ void colfin_one(const Ctx &C, int32_t j, bool full, int32_t &changed, int32_t &fixed,
+                                           int32_t &chg_nnz) {
     const unsigned long long el = C.cand_l[j], eu = C.cand_u[j];
     const bool has = el != kEncNegInf || eu != kEncPosInf;
     uint8_t kind = CK_KEPT;
@@ -560,27 +557,33 @@ __device__ __forceinline__ void colfin_one(const Ctx &C, int32_t j, bool full, i
     C.ckind[j] = kind;
     C.cchg[j] = chg;
     C.ctouch[j] = 0u;
-    if (chg && C.T.ptr[j + 1] - C.T.ptr[j] < kLongMin) coalesced_append(j, C.cl_cnt, C.cl_list);
+    if (chg) {
+        const int32_t len = C.T.ptr[j + 1] - C.T.ptr[j];
+        if (len < kLongMin) coalesced_append(j, C.cl_cnt, C.cl_list);
+        chg_nnz += len;
+    }
 }
 
 // every column (some LP in its first round)
 __global__ void __launch_bounds__(kBlock) k_colfin(Ctx C) {
     const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    int32_t changed = 0, fixed = 0;
-    if (j < C.n) colfin_one(C, j, true, changed, fixed);
+    int32_t changed = 0, fixed = 0, chg_nnz = 0;
+    if (j < C.n) colfin_one(C, j, true, changed, fixed, chg_nnz);
     block_add(changed, &C.st->bounds_changed);
     block_add(fixed, &C.st->cols_fixed);
+    block_add(chg_nnz, C.cl_nnz);
 }
 
 // the columns that received a candidate (the others keep their bounds; their
 // kind and change flag were reset at the start of the round)
 __global__ void __launch_bounds__(kBlock) k_colfin_list(Ctx C) {
     const int32_t cnt = *C.tl_cnt;
-    int32_t changed = 0, fixed = 0;
+    int32_t changed = 0, fixed = 0, chg_nnz = 0;
     for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x)
-        colfin_one(C, C.tl_list[t], false, changed, fixed);
+        colfin_one(C, C.tl_list[t], false, changed, fixed, chg_nnz);
     block_add(changed, &C.st->bounds_changed);
     block_add(fixed, &C.st->cols_fixed);
+    block_add(chg_nnz, C.cl_nnz);
 }
 
 // ------------------------------------------------------------ S5 parallel rows
@@ -888,11 +891,17 @@ __global__ void __launch_bounds__(kBlock) k_s5_leader(Ctx C) {
 // rows of a column whose bounds changed must be re-evaluated next round
 // rows of the changed short columns need their activities next round: one
 // thread per listed column; columns longer than 32 entries are walked by the
-// whole warp in turn
-__global__ void __launch_bounds__(kBlock) k_mark_list(Ctx C) {
+// whole warp in turn.  When the changed columns hold at least half of the
+// nonzeros, every row is marked instead (re-evaluating a row whose inputs did
+// not change finds nothing new).
+__global__ void __launch_bounds__(kBlock) k_mark_list(Ctx C, int64_t nnz) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (2 * (int64_t)*C.cl_nnz >= nnz) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < C.m; i += stride) C.rdnext[i] = 1;
+        return;
+    }
     const int32_t cnt = *C.cl_cnt;
     const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < cnt; base += stride) {
         const int64_t t = base + lane;
         int32_t b = 0, e = 0;
@@ -913,9 +922,9 @@ __global__ void __launch_bounds__(kBlock) k_mark_list(Ctx C) {
     }
 }
 
-__global__ void __launch_bounds__(kBlock) k_mark_long(Ctx C) {
+__global__ void __launch_bounds__(kBlock) k_mark_long(Ctx C, int64_t nnz) {
     const Chunk ch = C.T.chunks[blockIdx.x];
-    if (!C.cchg[ch.seg]) return;
+    if (!C.cchg[ch.seg] || 2 * (int64_t)*C.cl_nnz >= nnz) return;
     for (int32_t k = ch.begin + threadIdx.x; k < ch.end; k += kBlock) C.rdnext[C.T.idx[k]] = 1;
 }
 
@@ -949,10 +958,11 @@ void launch_colfin(const Ctx &C, bool full, cudaStream_t s) {
     else (k_colfin_list<<<std::min<unsigned>(blocks_for(C.n, kBlock), 8u * 152u), kBlock, 0, s>>>(C), note_launch());
 }
 
-void launch_mark_dirty(const Ctx &C, cudaStream_t s) {
+void launch_mark_dirty(const Ctx &C, int64_t nnz, cudaStream_t s) {
     if (C.n <= 0) return;
-    (k_mark_list<<<std::min<unsigned>(blocks_for(C.n, kBlock), 8u * 152u), kBlock, 0, s>>>(C), note_launch());
-    if (C.T.cls_start[7] > C.T.cls_start[6] && C.T.nchunks > 0) (k_mark_long<<<C.T.nchunks, kBlock, 0, s>>>(C), note_launch());
+    (k_mark_list<<<std::min<unsigned>(blocks_for(std::max(C.n, C.m), kBlock), 8u * 152u), kBlock, 0, s>>>(C, nnz),
+     note_launch());
+    if (C.T.cls_start[7] > C.T.cls_start[6] && C.T.nchunks > 0) (k_mark_long<<<C.T.nchunks, kBlock, 0, s>>>(C, nnz), note_launch());
 }
 
 void launch_s5_pass(const Ctx &C, cudaStream_t s) {

@@ -105,6 +105,7 @@ struct Ctx {
     uint32_t *ctouch;                     // 1 once the column received a candidate this round
     int32_t *tl_list, *tl_cnt;            // columns that received a candidate this round
     int32_t *cl_list, *cl_cnt;            // columns whose bounds changed this round
+    int32_t *cl_nnz;                      // their entries
     uint8_t *ckind;
     double *fixv;
     // S5 table

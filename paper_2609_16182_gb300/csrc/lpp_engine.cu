@@ -263,7 +263,7 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
     ctouch = pool.alloc<uint32_t>(n0);
     tl_list = pool.alloc<int32_t>(n0);
     cl_list = pool.alloc<int32_t>(n0);
-    col_cnt = pool.alloc<int32_t>(2);
+    col_cnt = pool.alloc<int32_t>(3);
     ckind = pool.alloc<uint8_t>(n0);
     fixv = pool.alloc<double>(n0);
     tcap_max = pow2_at_least(2 * (int64_t)std::max(m0, 1));
@@ -535,6 +535,7 @@ Ctx Engine::ctx(int32_t round) const {
     C.tl_cnt = col_cnt;
     C.cl_list = cl_list;
     C.cl_cnt = col_cnt + 1;
+    C.cl_nnz = col_cnt + 2;
     C.ckind = ckind;
     C.fixv = fixv;
     C.tkey = tkey;
@@ -624,7 +625,7 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     if (m > 0) LPP_CUDA(cudaMemsetAsync(rdnext, 0, (size_t)m, s));
     // the column lists of S3' start empty; outside a first round only listed
     // columns are finalised, the others keep kind KEPT and no change flag
-    LPP_CUDA(cudaMemsetAsync(col_cnt, 0, 2 * sizeof(int32_t), s));
+    LPP_CUDA(cudaMemsetAsync(col_cnt, 0, 3 * sizeof(int32_t), s));
     if (!first_round && n > 0) {
         LPP_CUDA(cudaMemsetAsync(ckind, 0, (size_t)n, s));
         LPP_CUDA(cudaMemsetAsync(cchg, 0, (size_t)n, s));
@@ -636,7 +637,7 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     tend();
     tbegin(F_COLFIN, 33.0 * n);
     launch_colfin(C, first_round, s);
-    launch_mark_dirty(C, s);
+    launch_mark_dirty(C, nnz, s);
     tend();
     LPP_CUDA(cudaGetLastError());
     // S5: leader passes.  Skipped when the last S5 resolved every key group

@@ -67,7 +67,7 @@ void split_lu(const double2 *lu, int32_t n, double *lb, double *ub, cudaStream_t
 // ---------------------------------------------------------------- k_round.cu
 void launch_prop(const Ctx &C, cudaStream_t s);
 void launch_colfin(const Ctx &C, bool full, cudaStream_t s);  // full: every column, else the touched list
-void launch_mark_dirty(const Ctx &C, cudaStream_t s);
+void launch_mark_dirty(const Ctx &C, int64_t nnz, cudaStream_t s);
 void launch_s5_pass(const Ctx &C, cudaStream_t s);
 // one later S5 pass over list[0 .. *cnt), *cnt <= max_rows; unmatched rows are appended to out
 void launch_s5_tail(const Ctx &C, const int32_t *list, const int32_t *cnt, int32_t *out, int32_t *out_cnt,
