@@ -190,45 +190,64 @@ __global__ void __launch_bounds__(kScanThreads) k_bin_scatter(const int32_t *ptr
 }
 
 // class sizes from the scanned histogram
-__global__ void k_bin_finish(const int32_t *off, int32_t ntiles, int32_t *cls_out) {
+// one block: exclusive scan in place of the 7 x ntiles class-by-tile counts
+// (class-major), the total at a[cnt], and the class sizes
+__global__ void __launch_bounds__(1024) k_scan_small_cls(int32_t *a, int32_t cnt, int32_t ntiles, int32_t *cls_out) {
+    __shared__ int32_t s_w[33];
+    int32_t carry = 0;
+    for (int32_t b = 0; b < cnt; b += 1024) {
+        const int32_t k = b + threadIdx.x;
+        const int32_t v = k < cnt ? a[k] : 0;
+        int32_t ex;
+        const int32_t tot = block_excl_scan(v, ex, s_w);
+        if (k < cnt) a[k] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) a[cnt] = carry;
+    __syncthreads();
     if (threadIdx.x < kNumClass)
-        cls_out[threadIdx.x] =
-            off[(int64_t)(threadIdx.x + 1) * ntiles] - off[(int64_t)threadIdx.x * ntiles];
+        cls_out[threadIdx.x] = a[(int64_t)(threadIdx.x + 1) * ntiles] - a[(int64_t)threadIdx.x * ntiles];
 }
 
-// chunk counts of the long segments (t < long count), zero beyond
-__global__ void k_chunk_count(const int32_t *ptr, const int32_t *order, const int32_t *off, int32_t ntiles,
-                              const int32_t *cls, int32_t cap_long, int32_t *nch) {
-    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= cap_long) return;
-    const int32_t nlong = cls[6];
-    int32_t v = 0;
-    if (t < nlong) {
-        const int32_t sg = order[off[(int64_t)6 * ntiles] + t];
-        const int32_t len = ptr[sg + 1] - ptr[sg];
-        v = (len + kChunk - 1) / kChunk;
+// one block: the chunks of the long segments (class 6, in schedule order),
+// their first chunk (lfirst, with the total at lfirst[long count]) and the count
+__global__ void __launch_bounds__(1024) k_chunks(const int32_t *ptr, const int32_t *order, const int32_t *off,
+                                                 int32_t ntiles, const int32_t *cls, int32_t cap_long,
+                                                 int32_t *lfirst, Chunk *chunks, int32_t *nchunk_out) {
+    __shared__ int32_t s_w[33];
+    const int32_t nlong = min(cls[6], cap_long);
+    const int32_t *lo = order + off[(int64_t)6 * ntiles];
+    int32_t carry = 0;
+    for (int32_t b = 0; b < nlong; b += 1024) {
+        const int32_t t = b + threadIdx.x;
+        int32_t sg = 0, pb = 0, pe = 0, v = 0;
+        if (t < nlong) {
+            sg = lo[t];
+            pb = ptr[sg];
+            pe = ptr[sg + 1];
+            v = (pe - pb + kChunk - 1) / kChunk;
+        }
+        int32_t ex;
+        const int32_t tot = block_excl_scan(v, ex, s_w);
+        if (t < nlong) {
+            int32_t q = carry + ex;
+            lfirst[t] = q;
+            for (int32_t k = pb; k < pe; k += kChunk, q++) {
+                Chunk ch;
+                ch.seg = sg;
+                ch.begin = k;
+                ch.end = min(pe, k + kChunk);
+                ch.lidx = t;
+                chunks[q] = ch;
+            }
+        }
+        carry += tot;
     }
-    nch[t] = v;
-}
-
-__global__ void k_chunk_fill(const int32_t *ptr, const int32_t *order, const int32_t *off, int32_t ntiles,
-                             const int32_t *cls, int32_t cap_long, const int32_t *lfirst, Chunk *chunks) {
-    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= cap_long || t >= cls[6]) return;
-    const int32_t sg = order[off[(int64_t)6 * ntiles] + t];
-    const int32_t b = ptr[sg], e = ptr[sg + 1];
-    int32_t q = lfirst[t];
-    for (int32_t k = b; k < e; k += kChunk, q++) {
-        Chunk ch;
-        ch.seg = sg;
-        ch.begin = k;
-        ch.end = min(e, k + kChunk);
-        ch.lidx = t;
-        chunks[q] = ch;
+    if (threadIdx.x == 0) {
+        lfirst[nlong] = carry;
+        *nchunk_out = carry;
     }
 }
-
-__global__ void k_copy_i32(const int32_t *src, int32_t *dst) { *dst = *src; }
 
 // ----------------------------------------------------------- input checks
 enum : int32_t { ERR_PTR = 1, ERR_COL = 2, ERR_VAL = 4, ERR_ORDER = 8, ERR_VEC = 16 };
@@ -479,17 +498,12 @@ void build_schedule(const int32_t *ptr, const int32_t *cnt_dev, int32_t cnt_max,
     // tiles cover cnt_max segments; tiles past the actual count hold zeros
     const int32_t ntiles = std::max<int32_t>(1, (int32_t)((cnt_max + kScanTile - 1) / kScanTile));
     (k_bin_hist<<<ntiles, kScanThreads, 0, s>>>(ptr, cnt_dev, b.tile_hist, ntiles), note_launch());
-    scan_excl(b.tile_hist, b.tile_hist, (int64_t)kNumClass * ntiles, b.tmp, s);
+    (k_scan_small_cls<<<1, 1024, 0, s>>>(b.tile_hist, kNumClass * ntiles, ntiles, cls_out), note_launch());
     (k_bin_scatter<<<ntiles, kScanThreads, 0, s>>>(ptr, cnt_dev, b.tile_hist, ntiles, b.order), note_launch());
-    (k_bin_finish<<<1, 32, 0, s>>>(b.tile_hist, ntiles, cls_out), note_launch());
     // chunks of the long segments: at most nnz / kLongMin of them
     const int32_t cap_long = sched_cap_long(nnz_max);
-    (k_chunk_count<<<blocks_for(cap_long, 256), 256, 0, s>>>(ptr, b.order, b.tile_hist, ntiles, cls_out, cap_long,
-                                                             b.nch), note_launch());
-    scan_excl(b.nch, b.lfirst, cap_long, b.tmp, s);
-    (k_chunk_fill<<<blocks_for(cap_long, 256), 256, 0, s>>>(ptr, b.order, b.tile_hist, ntiles, cls_out, cap_long,
-                                                            b.lfirst, b.chunks), note_launch());
-    (k_copy_i32<<<1, 1, 0, s>>>(b.lfirst + cap_long, nchunk_out), note_launch());
+    (k_chunks<<<1, 1024, 0, s>>>(ptr, b.order, b.tile_hist, ntiles, cls_out, cap_long, b.lfirst, b.chunks,
+                                 nchunk_out), note_launch());
 }
 
 void segmat_from_counts(SegMat &M, const int32_t cls[kNumClass], int32_t nchunks) {
