@@ -351,7 +351,9 @@ def main():
             launches += int(r.info.launches)
             rounds = r.rounds
             if first is None:  # host-side copies: no device work
-                first = (r.info, [float(x) for x in r.round_ms], [int(x) for x in r.round_nnz])
+                first = (r.info, [float(x) for x in r.round_ms], [int(x) for x in r.round_nnz],
+                         [int(x) for x in r.round_rows_removed], [int(x) for x in r.round_cols_fixed],
+                         [int(x) for x in r.round_bounds_changed])
             r.close()  # the reduced LP is handed on and freed, as a caller would
         ev1.record(stream)
         barrier()
@@ -361,7 +363,7 @@ def main():
         print(json.dumps({"profile": True, "steps": args.steps, "ms_per_step": ms_total / max(1, args.steps),
                           "nnz": lp.nnz}), flush=True)
         return
-    info, round_ms, round_nnz = first
+    info, round_ms, round_nnz, round_rows, round_cols, round_bounds = first
     ms_max, value = reduce_over_ranks(ms_total, nnz_proc, dev, ws)
 
     # per-kernel times: one more step with CUDA events around every launch family
@@ -385,7 +387,8 @@ def main():
     roofline = {"bound": "alu", "kernel": "k_prop_groups + long-row chunks (S1+S2+S3 fused)",
                 "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
                 "peak_source": "FP64 unit count x clock: 2 DFMA/SM/clk (ncu peak_sustained), 152 SMs, 2.07 GHz",
-                "work": "2 FMA (4 flops) per nonzero of the rows S1 evaluates",
+                "work": "2 FMA per nonzero of the rows S1 evaluates (activities) + 2 FMA per entry side S3 tests "
+                        "(residual, sign test); 2 flops per FMA",
                 "traffic": traffic, "launches": pk["launches"], "avg_ms": pk["ms"] / max(1, pk["launches"]),
                 "hbm_view": {"achieved_GBps": hbm, "peak_GBps": peak_gbs, "frac": hbm / peak_gbs,
                              "peak_source": f"{peak_src} hbm_gbs"},
@@ -433,6 +436,8 @@ def main():
                            "rounds": rounds, "presolve_ms": info.presolve_ms,
                            "round_ms": round_ms, "round_nnz": round_nnz,
                            "nnz_per_s_per_round": [n_ / (m_ / 1e3) for n_, m_ in zip(round_nnz, round_ms)],
+                           "round_rows_removed": round_rows, "round_cols_fixed": round_cols,
+                           "round_bounds_changed": round_bounds,
                            "reduced": {"m": info.m_red, "n": info.n_red, "nnz": info.nnz_red,
                                        "nnz_ratio": info.nnz_red / max(1, info.nnz)},
                            "l2": "inputs larger than L2 (CSR alone ~245 MB > 129 MB)",

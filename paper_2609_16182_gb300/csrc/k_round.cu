@@ -110,13 +110,14 @@ __device__ __forceinline__ void apply_cand(const Ctx &C, int32_t j, double x, do
 // passed and still needs the cap and the divide.
 __device__ __forceinline__ void tighten_tests(const Ctx &C, int32_t j, double a, bool up_row, bool lo_row, double dU,
                                               double dL, int nmin, int nmax, bool &w1, double &x1, int32_t &k1,
-                                              bool &w2, double &x2, int32_t &k2) {
+                                              bool &w2, double &x2, int32_t &k2, int32_t &tested) {
     const double2 b = C.lu[j];
     const bool neg = is_neg(a);
     const double bmin = neg ? b.y : b.x, bmax = neg ? b.x : b.y;
     const bool fmn = is_fin(bmin), fmx = is_fin(bmax);
     if (up_row && (fmn ? nmin == 0 : nmin == 1)) {
         // a x_j <= U - (min activity of the other entries)
+        tested++;
         x1 = fmn ? fma(a, bmin, dU) : dU;
         if (!neg) {
             k1 = CQ_UPPER;
@@ -128,6 +129,7 @@ __device__ __forceinline__ void tighten_tests(const Ctx &C, int32_t j, double a,
     }
     if (lo_row && (fmx ? nmax == 0 : nmax == 1)) {
         // a x_j >= L - (max activity of the other entries)
+        tested++;
         x2 = fmx ? fma(a, bmax, dL) : dL;
         if (!neg) {
             k2 = CQ_LOWER;
@@ -141,11 +143,11 @@ __device__ __forceinline__ void tighten_tests(const Ctx &C, int32_t j, double a,
 
 // one entry, candidates applied at once (long rows: few of them tighten)
 __device__ __forceinline__ void tighten_entry(const Ctx &C, int32_t j, double a, bool up_row, bool lo_row,
-                                              double dU, double dL, int nmin, int nmax) {
+                                              double dU, double dL, int nmin, int nmax, int32_t &tested) {
     bool w1 = false, w2 = false;
     double x1 = 0.0, x2 = 0.0;
     int32_t k1 = 0, k2 = 0;
-    tighten_tests(C, j, a, up_row, lo_row, dU, dL, nmin, nmax, w1, x1, k1, w2, x2, k2);
+    tighten_tests(C, j, a, up_row, lo_row, dU, dL, nmin, nmax, w1, x1, k1, w2, x2, k2, tested);
     if (w1) apply_cand(C, j, x1, a, k1);
     if (w2) apply_cand(C, j, x2, a, k2);
 }
@@ -281,7 +283,7 @@ __device__ __forceinline__ unsigned long long len_hash(int32_t len) {
 // ------------------------------------------------------- S1 + S2 + S3 groups
 template <int W>
 __device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, int32_t &removed, int32_t &evaluated,
-                                           CandQueue &q) {
+                                           int32_t &tested, CandQueue &q) {
     const unsigned mask = group_mask<W>();
     const int lane = threadIdx.x & (W - 1);
     // A row none of whose bounds, entries or sides changed since its last
@@ -353,7 +355,7 @@ __device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, 
             const int32_t k = beg + lane + it * W;
             j = C.A.idx[k];
             a = C.A.val[k];
-            tighten_tests(C, j, a, up_row, lo_row, dU, dL, nmin, nmax, w1, x1, k1, w2, x2, k2);
+            tighten_tests(C, j, a, up_row, lo_row, dU, dL, nmin, nmax, w1, x1, k1, w2, x2, k2, tested);
         }
         cq_push(C, q, w1, x1, a, j, k1);
         cq_push(C, q, w2, x2, a, j, k2);
@@ -371,7 +373,7 @@ __global__ void __launch_bounds__(kBlock) k_prop_groups(Ctx C, GroupGrid g) {
     CandQueue q{s_qx[warp], s_qa[warp], s_qj[warp], s_qk[warp], 0};
     const int c = grid_class(g, blockIdx.x);
     const int32_t lb = blockIdx.x - g.blk_start[c];
-    int32_t removed = 0, evaluated = 0;
+    int32_t removed = 0, evaluated = 0, tested = 0;
     const int W = prop_lanes(c);
     const int32_t pos = C.A.cls_start[c] + lb * (kBlock / W) + threadIdx.x / W;
     const bool valid = pos < C.A.cls_start[c + 1];
@@ -379,14 +381,15 @@ __global__ void __launch_bounds__(kBlock) k_prop_groups(Ctx C, GroupGrid g) {
     switch (c) {
         case 0:
         case 1:
-        case 2: prop_group<1>(C, i, valid, removed, evaluated, q); break;
-        case 3: prop_group<8>(C, i, valid, removed, evaluated, q); break;
-        case 4: prop_group<16>(C, i, valid, removed, evaluated, q); break;
-        default: prop_group<32>(C, i, valid, removed, evaluated, q); break;
+        case 2: prop_group<1>(C, i, valid, removed, evaluated, tested, q); break;
+        case 3: prop_group<8>(C, i, valid, removed, evaluated, tested, q); break;
+        case 4: prop_group<16>(C, i, valid, removed, evaluated, tested, q); break;
+        default: prop_group<32>(C, i, valid, removed, evaluated, tested, q); break;
     }
     cq_flush(C, q);
     block_add(removed, &C.st->rows_removed);
     block_add(evaluated, &C.st->nnz_eval);
+    block_add(tested, &C.st->sides_tested);
 }
 
 // fixed-order block reduction (warp butterflies, then warps in order)
@@ -495,8 +498,10 @@ __global__ void __launch_bounds__(kBlock) k_prop_long_tighten(Ctx C) {
     const int2 ni = C.ninf[i];
     const bool up_row = is_fin(Uv) && ni.x <= 1, lo_row = is_fin(Lv) && ni.y <= 1;
     const double dU = Uv - act.x, dL = Lv - act.y;
+    int32_t tested = 0;
     for (int32_t k = ch.begin + threadIdx.x; k < ch.end; k += kBlock)
-        tighten_entry(C, C.A.idx[k], C.A.val[k], up_row, lo_row, dU, dL, ni.x, ni.y);
+        tighten_entry(C, C.A.idx[k], C.A.val[k], up_row, lo_row, dU, dL, ni.x, ni.y, tested);
+    block_add(tested, &C.st->sides_tested);  // the whole block returned above or reaches here
 }
 
 // ------------------------------------------------- S3' finalise + S4 fixing

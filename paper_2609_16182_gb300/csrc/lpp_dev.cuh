@@ -48,7 +48,8 @@ enum { V_S2_ROW = 0, V_S3_COL = 1, V_S5_ROW = 2, V_S6_COL = 3, V_SLOTS = 4 };
 // Global counters of a round (block-aggregated atomics).
 struct DevStatus {
     int32_t rows_removed, cols_fixed, bounds_changed, unmatched;
-    int32_t participants, long_tighten, err, nnz_eval;  // nnz_eval: nonzeros of the rows S1 evaluated
+    int32_t participants, sides_tested, err, nnz_eval;  // nnz_eval: nonzeros of the rows S1 evaluated;
+                                                         // sides_tested: entry sides S3 tested
     int32_t cls_r[kNumClass];  // class sizes of the rows after compaction
     int32_t cls_c[kNumClass];  // class sizes of the columns after compaction
     int32_t nchunk_r, nchunk_c;

@@ -660,11 +660,13 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     read_status();
     r_eval.push_back(st_h->nnz_eval);
     if (o.timing && prop_mark > 0) {
-        // S1 algorithmic work: per evaluated nonzero its 12 bytes and two FMAs,
-        // per row ptr, sides, results (4 + 16 + 33 bytes), the bounds once
+        // S1-S3 algorithmic work: per evaluated nonzero its 12 bytes and two
+        // FMAs (activities), per tested entry side two FMAs (the residual and
+        // the sign test); per row ptr, sides, results (4 + 16 + 33 bytes), the
+        // bounds once
         Tmark &pm = marks[prop_mark - 1];
         pm.bytes = 12.0 * st_h->nnz_eval + 53.0 * m + 16.0 * n;
-        pm.ops = 2.0 * st_h->nnz_eval;
+        pm.ops = 2.0 * st_h->nnz_eval + 2.0 * st_h->sides_tested;
     }
     // later passes on the list of unmatched rows, without a host sync per
     // pass: chunks of 2, 4, 8, ... passes, then one read of the list size
