@@ -418,8 +418,8 @@ __global__ void __launch_bounds__(kBlock) k_prop_long_partial(Ctx C, unsigned lo
     int nmin = 0, nmax = 0;
     unsigned long long h = 0;
     for (int32_t k = ch.begin + threadIdx.x; k < ch.end; k += kBlock) {
-        const int32_t j = C.A.idx[k];
-        const double a = C.A.val[k];
+        const int32_t j = __ldcs(C.A.idx + k);  // streamed once: evict first, keep the bounds cached
+        const double a = __ldcs(C.A.val + k);
         const double2 b = C.lu[j];
         const bool neg = is_neg(a);
         const double bmin = neg ? b.y : b.x, bmax = neg ? b.x : b.y;
