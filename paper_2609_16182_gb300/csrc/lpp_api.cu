@@ -256,13 +256,35 @@ void materialize(lpp_postsolve *P) {
     P->host_ready = true;
 }
 
-template <class T>
-const T *host_copy(std::vector<T> &h, const T *d, size_t cnt) {
-    if (h.size() != cnt) {
-        h.resize(cnt);
-        if (cnt) LPP_CUDA(cudaMemcpy(h.data(), d, sizeof(T) * cnt, cudaMemcpyDeviceToHost));
+// every array of a reduced LP copied to one pinned host block (async copies,
+// one synchronisation), on the first request for a host view
+void materialize_host(lpp_reduced *R) {
+    if (R->hblock) return;
+    const size_t m = (size_t)R->m, n = (size_t)R->n, z = (size_t)R->nnz;
+    struct Part {
+        void **dst;
+        const void *src;
+        size_t bytes;
+    };
+    const Part parts[] = {{(void **)&R->h_rp, R->rp, 4 * (m + 1)}, {(void **)&R->h_ci, R->ci, 4 * z},
+                          {(void **)&R->h_rv, R->rv, 8 * z},       {(void **)&R->h_c, R->c, 8 * n},
+                          {(void **)&R->h_L, R->L, 8 * m},         {(void **)&R->h_U, R->U, 8 * m},
+                          {(void **)&R->h_lb, R->lb, 8 * n},       {(void **)&R->h_ub, R->ub, 8 * n},
+                          {(void **)&R->h_tp, R->tp, 4 * (n + 1)}, {(void **)&R->h_ti, R->ti, 4 * z},
+                          {(void **)&R->h_tv, R->tv, 8 * z},       {(void **)&R->h_rmap, R->rmap, 4 * m},
+                          {(void **)&R->h_cmap, R->cmap, 4 * n}};
+    auto up = [](size_t b) { return (b + 63) & ~(size_t)63; };
+    size_t total = 0;
+    for (const Part &p : parts) total += up(p.bytes);
+    char *blk = static_cast<char *>(pinned_get_sized(total));
+    size_t off = 0;
+    for (const Part &p : parts) {
+        *p.dst = blk + off;
+        if (p.bytes && p.src) LPP_CUDA(cudaMemcpyAsync(blk + off, p.src, p.bytes, cudaMemcpyDeviceToHost, 0));
+        off += up(p.bytes);
     }
-    return h.data();
+    LPP_CUDA(cudaStreamSynchronize(0));
+    R->hblock = blk;
 }
 
 }  // namespace
@@ -489,35 +511,15 @@ lpp_status lpp_reduced_view(lpp_reduced *R, lpp_lp *v, int32_t on_device) {
             v->on_device = 1;
             return LPP_OK;
         }
-        if (R->h_rp.empty()) {
-            R->h_rp.resize((size_t)R->m + 1);
-            R->h_ci.resize((size_t)R->nnz);
-            R->h_rv.resize((size_t)R->nnz);
-            R->h_c.resize(R->n);
-            R->h_L.resize(R->m);
-            R->h_U.resize(R->m);
-            R->h_lb.resize(R->n);
-            R->h_ub.resize(R->n);
-            auto d2h = [](void *dst, const void *src, size_t bytes) {
-                if (bytes) LPP_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
-            };
-            d2h(R->h_rp.data(), R->rp, 4 * ((size_t)R->m + 1));
-            d2h(R->h_ci.data(), R->ci, 4 * (size_t)R->nnz);
-            d2h(R->h_rv.data(), R->rv, 8 * (size_t)R->nnz);
-            d2h(R->h_c.data(), R->c, 8 * (size_t)R->n);
-            d2h(R->h_L.data(), R->L, 8 * (size_t)R->m);
-            d2h(R->h_U.data(), R->U, 8 * (size_t)R->m);
-            d2h(R->h_lb.data(), R->lb, 8 * (size_t)R->n);
-            d2h(R->h_ub.data(), R->ub, 8 * (size_t)R->n);
-        }
-        v->row_ptr = R->h_rp.data();
-        v->col_idx = R->h_ci.data();
-        v->val = R->h_rv.data();
-        v->c = R->h_c.data();
-        v->lhs = R->h_L.data();
-        v->rhs = R->h_U.data();
-        v->lb = R->h_lb.data();
-        v->ub = R->h_ub.data();
+        materialize_host(R);
+        v->row_ptr = R->h_rp;
+        v->col_idx = R->h_ci;
+        v->val = R->h_rv;
+        v->c = R->h_c;
+        v->lhs = R->h_L;
+        v->rhs = R->h_U;
+        v->lb = R->h_lb;
+        v->ub = R->h_ub;
         v->on_device = 0;
         return LPP_OK;
     });
@@ -532,9 +534,10 @@ lpp_status lpp_reduced_csc(lpp_reduced *R, const int32_t **col_ptr, const int32_
             if (row_idx) *row_idx = R->ti;
             if (val) *val = R->tv;
         } else {
-            if (col_ptr) *col_ptr = host_copy(R->h_tp, R->tp, (size_t)R->n + 1);
-            if (row_idx) *row_idx = host_copy(R->h_ti, R->ti, (size_t)R->nnz);
-            if (val) *val = host_copy(R->h_tv, R->tv, (size_t)R->nnz);
+            materialize_host(R);
+            if (col_ptr) *col_ptr = R->h_tp;
+            if (row_idx) *row_idx = R->h_ti;
+            if (val) *val = R->h_tv;
         }
         return LPP_OK;
     });
@@ -547,8 +550,9 @@ lpp_status lpp_reduced_maps(lpp_reduced *R, const int32_t **row_map, const int32
             if (row_map) *row_map = R->rmap;
             if (col_map) *col_map = R->cmap;
         } else {
-            if (row_map) *row_map = host_copy(R->h_rmap, R->rmap, (size_t)R->m);
-            if (col_map) *col_map = host_copy(R->h_cmap, R->cmap, (size_t)R->n);
+            materialize_host(R);
+            if (row_map) *row_map = R->h_rmap;
+            if (col_map) *col_map = R->h_cmap;
         }
         return LPP_OK;
     });
@@ -643,6 +647,7 @@ lpp_status lpp_postsolve_primal(const lpp_postsolve *Pc, const double *x_red, do
 
 void lpp_free_reduced(lpp_reduced *R) {
     if (!R) return;
+    if (R->hblock) pinned_put(R->hblock);
     for (void *p : R->owned) cudaFree(p);
     delete R;
 }

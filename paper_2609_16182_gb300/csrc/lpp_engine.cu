@@ -25,14 +25,12 @@ void DevPool::release() {
     ptrs.clear();
 }
 
-namespace {
+// Pinned host buffers (status mirrors, host copies of reduced LPs) are reused
+// across presolves: pinning memory costs far more than the rounds of a small LP.
+static std::mutex g_pin_mu;
+static std::vector<std::pair<size_t, void *>> g_pin_free;
 
-// Small pinned host buffers (status mirrors) are reused across presolves:
-// pinning memory costs far more than the rounds of a small LP.
-std::mutex g_pin_mu;
-std::vector<std::pair<size_t, void *>> g_pin_free;
-
-void *pinned_get(size_t bytes) {
+static void *pinned_get(size_t bytes) {
     bytes = std::max<size_t>(bytes, 64);
     {
         std::lock_guard<std::mutex> g(g_pin_mu);
@@ -50,8 +48,8 @@ void *pinned_get(size_t bytes) {
 }
 
 // remembers a pinned buffer's capacity so it can be handed out again
-std::mutex g_cap_mu;
-std::vector<std::pair<void *, size_t>> g_pin_cap;
+static std::mutex g_cap_mu;
+static std::vector<std::pair<void *, size_t>> g_pin_cap;
 
 void *pinned_get_sized(size_t bytes) {
     bytes = std::max<size_t>(bytes, 64);
@@ -75,6 +73,8 @@ void pinned_put(void *p) {
     std::lock_guard<std::mutex> g(g_pin_mu);
     g_pin_free.emplace_back(cap, p);
 }
+
+namespace {
 
 // Freed device memory stays in the device's default pool (stream-ordered
 // allocations are then reused by the next presolve instead of being mapped

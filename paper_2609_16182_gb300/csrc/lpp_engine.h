@@ -177,6 +177,12 @@ struct SharedStore {
 // sets the message lpp_last_error() returns and passes the status through
 lpp_status lpp_noalloc_fail(lpp_status st, const char *msg);
 
+namespace lpp {
+// pinned host buffers from a process-wide cache (first fit by capacity)
+void *pinned_get_sized(size_t bytes);
+void pinned_put(void *p);
+}  // namespace lpp
+
 // Library objects behind the opaque C handles.
 struct lpp_reduced {
     int32_t m = 0, n = 0;
@@ -186,9 +192,12 @@ struct lpp_reduced {
     double *rv = nullptr, *tv = nullptr, *L = nullptr, *U = nullptr, *lb = nullptr, *ub = nullptr, *c = nullptr;
     std::vector<void *> owned;  // device allocations
     std::shared_ptr<lpp::SharedStore> shared;  // batch: storage shared with the other LPs
-    // host copies made on demand by lpp_reduced_view(on_device = 0)
-    std::vector<int32_t> h_rp, h_ci, h_tp, h_ti, h_rmap, h_cmap;
-    std::vector<double> h_rv, h_c, h_L, h_U, h_lb, h_ub, h_tv;
+    // host copies made on the first request for one (on_device = 0): every
+    // array at once, into one pinned block
+    void *hblock = nullptr;
+    int32_t *h_rp = nullptr, *h_ci = nullptr, *h_tp = nullptr, *h_ti = nullptr, *h_rmap = nullptr, *h_cmap = nullptr;
+    double *h_rv = nullptr, *h_c = nullptr, *h_L = nullptr, *h_U = nullptr, *h_lb = nullptr, *h_ub = nullptr,
+           *h_tv = nullptr;
 };
 
 namespace lpp {

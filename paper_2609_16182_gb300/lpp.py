@@ -282,8 +282,10 @@ class Result:
     def presolve_ms(self) -> float:
         return self.info.presolve_ms
 
-    def reduced(self) -> Reduced:
-        """Copies the reduced LP (and its CSC and maps) to the host."""
+    def reduced(self, copy: bool = True) -> Reduced:
+        """The reduced LP (and its CSC and maps) on the host.  The library
+        copies it once into pinned host memory it owns; copy=False returns
+        NumPy views of that memory, valid until close()."""
         if self._reduced is not None:
             return self._reduced
         L = load()
@@ -295,7 +297,8 @@ class Result:
             if cnt == 0 or not ptr:
                 return np.zeros(0, dt)
             ct = C.c_int32 if dt == np.int32 else C.c_double
-            return np.ctypeslib.as_array(C.cast(ptr, C.POINTER(ct)), shape=(cnt,)).copy()
+            a = np.ctypeslib.as_array(C.cast(ptr, C.POINTER(ct)), shape=(cnt,))
+            return a.copy() if copy else a
 
         rp = arr(v.row_ptr, m + 1, np.int32) if m >= 0 else np.zeros(1, np.int32)
         if m == 0:
@@ -312,8 +315,10 @@ class Result:
         red["csc_ptr"] = arr(tp.value, n + 1, np.int32) if n > 0 else np.zeros(1, np.int32)
         red["csc_idx"] = arr(ti.value, nnz, np.int32)
         red["csc_val"] = arr(tv.value, nnz, float)
-        self._reduced = Reduced(**red)
-        return self._reduced
+        out = Reduced(**red)
+        if copy:
+            self._reduced = out
+        return out
 
     def device_view(self) -> LpStruct:
         """The reduced LP as device pointers (valid while this Result lives)."""
