@@ -30,16 +30,24 @@ void DevPool::release() {
 static std::mutex g_pin_mu;
 static std::vector<std::pair<size_t, void *>> g_pin_free;
 
+// best fit among the free buffers, and none more than 4x (+ 1 MiB) the
+// request: a status mirror must not take the block a reduced LP needs next
 static void *pinned_get(size_t bytes) {
     bytes = std::max<size_t>(bytes, 64);
     {
         std::lock_guard<std::mutex> g(g_pin_mu);
-        for (size_t k = 0; k < g_pin_free.size(); k++)
-            if (g_pin_free[k].first >= bytes) {
-                void *p = g_pin_free[k].second;
-                g_pin_free.erase(g_pin_free.begin() + (long)k);
-                return p;
-            }
+        size_t best = g_pin_free.size();
+        for (size_t k = 0; k < g_pin_free.size(); k++) {
+            const size_t cap = g_pin_free[k].first;
+            if (cap >= bytes && cap <= 4 * bytes + (1u << 20) &&
+                (best == g_pin_free.size() || cap < g_pin_free[best].first))
+                best = k;
+        }
+        if (best < g_pin_free.size()) {
+            void *p = g_pin_free[best].second;
+            g_pin_free.erase(g_pin_free.begin() + (long)best);
+            return p;
+        }
     }
     void *p = nullptr;
     LPP_CUDA(cudaMallocHost(&p, bytes));
