@@ -263,24 +263,83 @@ __global__ void k_check_ptr(const int32_t *ptr, int32_t m, int64_t nnz, int32_t 
     if (bad) atomicOr(err, ERR_PTR);
 }
 
-// mark[p] += 1 for every row boundary p = ptr[i], 1 <= i < m
-__global__ void k_mark_rows(const int32_t *ptr, int32_t m, int64_t nnz, int32_t *mark) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1;
-    if (i >= m) return;
-    const int32_t p = ptr[i];
-    if (p >= 0 && (int64_t)p < nnz) atomicAdd(&mark[p], 1);
+// Row of every entry (row_of) and the entry checks, one tile of kRowTile
+// entries per block: the rows starting in the tile mark their first entry,
+// a block max-scan spreads the marks, then the entries are checked (column
+// in range, value finite and nonzero, columns increasing inside a row).
+// Searches and marks stay inside [0, m) and the tile even for a malformed
+// ptr, which k_check_ptr reports.
+constexpr int kRowTile = 4096;
+constexpr int kRowPer = kRowTile / kScanThreads;  // 16
+
+// largest r in [0, m - 1] with ptr[r] <= k (0 if none), for non-decreasing ptr
+__device__ __forceinline__ int32_t row_search(const int32_t *ptr, int32_t m, int64_t k) {
+    int32_t lo = 0, hi = m - 1;
+    while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo + 1) >> 1);
+        if ((int64_t)ptr[mid] <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
-__global__ void k_check_entries(const int32_t *idx, const double *val, const int32_t *row_of, int64_t nnz,
-                                int32_t n, int32_t *err) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nnz) return;
-    const int32_t j = idx[k];
-    const double a = val[k];
+__global__ void __launch_bounds__(kScanThreads) k_rows_check(const int32_t *ptr, const int32_t *idx, const double *val,
+                                                             int32_t m, int32_t n, int64_t nnz, int32_t *row_of,
+                                                             int32_t *err) {
+    __shared__ int32_t s_row[kRowTile];
+    __shared__ int32_t s_wmax[kScanThreads / 32];
+    __shared__ int32_t s_r[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t k0 = (int64_t)blockIdx.x * kRowTile;
+    const int32_t len = (int32_t)(nnz - k0 < kRowTile ? nnz - k0 : kRowTile);
+    for (int x = tid; x < kRowTile; x += kScanThreads) s_row[x] = -1;
+    if (tid < 2) s_r[tid] = row_search(ptr, m, tid == 0 ? k0 : k0 + len - 1);
+    __syncthreads();
+    const int32_t r0 = s_r[0], r1 = s_r[1];
+    for (int64_t r = (int64_t)r0 + tid; r <= r1; r += kScanThreads) {
+        int64_t x = (int64_t)ptr[r] - k0;
+        if (x < 0) x = 0;
+        if (x < len) atomicMax(&s_row[x], (int32_t)r);
+    }
+    __syncthreads();
+    {  // inclusive max-scan, 16 consecutive positions per thread
+        const int x0 = tid * kRowPer;
+        int32_t v[kRowPer], run = -1;
+#pragma unroll
+        for (int e = 0; e < kRowPer; e++) {
+            v[e] = s_row[x0 + e];
+            run = v[e] > run ? v[e] : run;
+        }
+        int32_t inc = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o && y > inc) inc = y;
+        }
+        if (lane == 31) s_wmax[warp] = inc;
+        int32_t prev = __shfl_up_sync(0xffffffffu, inc, 1);
+        if (lane == 0) prev = -1;
+        __syncthreads();
+        for (int w = 0; w < warp; w++) prev = s_wmax[w] > prev ? s_wmax[w] : prev;
+        run = prev;
+#pragma unroll
+        for (int e = 0; e < kRowPer; e++) {
+            run = v[e] > run ? v[e] : run;
+            s_row[x0 + e] = run < 0 ? r0 : run;
+        }
+    }
+    __syncthreads();
     int32_t e = 0;
-    if (j < 0 || j >= n) e |= ERR_COL;
-    if (!is_fin(a) || a == 0.0) e |= ERR_VAL;
-    if (k > 0 && row_of[k] == row_of[k - 1] && idx[k - 1] >= j) e |= ERR_ORDER;
+    for (int x = tid; x < len; x += kScanThreads) {
+        const int64_t k = k0 + x;
+        const int32_t r = s_row[x];
+        row_of[k] = r;
+        const int32_t j = idx[k];
+        const double a = val[k];
+        if (j < 0 || j >= n) e |= ERR_COL;
+        if (!is_fin(a) || a == 0.0) e |= ERR_VAL;
+        if (k > 0 && (int64_t)ptr[r] < k && idx[k - 1] >= j) e |= ERR_ORDER;  // k - 1 in the same row
+    }
     if (e) atomicOr(err, e);
 }
 
@@ -527,12 +586,13 @@ GroupGrid group_grid(const SegMat &M) {
 
 void check_csr(const int32_t *ptr, const int32_t *idx, const double *val, int32_t m, int32_t n, int64_t nnz,
                int32_t *row_of, int32_t *tmp, int32_t *err, cudaStream_t s) {
+    (void)tmp;
     (k_check_ptr<<<blocks_for((int64_t)m + 1, 256), 256, 0, s>>>(ptr, m, nnz, err), note_launch());
-    // row_of: mark boundaries, then an inclusive scan (exclusive scan shifted by one)
-    cudaMemsetAsync(row_of, 0, sizeof(int32_t) * (size_t)(nnz + 1), s);
-    if (m > 1) (k_mark_rows<<<blocks_for((int64_t)m - 1, 256), 256, 0, s>>>(ptr, m, nnz, row_of), note_launch());
-    scan_excl(row_of, row_of, nnz, tmp, s);  // row_of[k+1] = rows whose start is <= k ... see caller
-    if (nnz > 0) (k_check_entries<<<blocks_for(nnz, 256), 256, 0, s>>>(idx, val, row_of + 1, nnz, n, err), note_launch());
+    // row_of[0] is unused (callers read row_of + 1)
+    if (nnz > 0 && m > 0)
+        (k_rows_check<<<(unsigned)((nnz + kRowTile - 1) / kRowTile), kScanThreads, 0, s>>>(ptr, idx, val, m, n, nnz,
+                                                                                           row_of + 1, err),
+         note_launch());
 }
 
 void ingest_vectors(const double *lhs, const double *rhs, const double *lb, const double *ub, const double *c,
