@@ -210,24 +210,35 @@ __device__ __forceinline__ void cq_flush(const Ctx &C, CandQueue &q) {
 // S2: class of a row from its activities, first match wins: infeasible
 // sides, infeasible activity, empty, redundant, singleton.  Returns false if
 // the row proves the LP infeasible.
+// Order-preserving integer key of a non-NaN double (-0 and +0 equal): the
+// row tests compare keys on the integer pipes instead of the FP64 pipe.
+__device__ __forceinline__ long long dkey(double x) {
+    const long long b = dbits(x);
+    if ((b & 0x7fffffffffffffffLL) == 0) return 0;
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+
 __device__ __forceinline__ bool classify(const Ctx &C, double Lv, double Uv, int32_t len, double smin, double smax,
                                          int nmin, int nmax, uint8_t &kind) {
     const double ft = C.feas_tol;
     const bool Lf = is_fin(Lv), Uf = is_fin(Uv);
     kind = RK_KEPT;
+    const double mL = max1abs(Lv), mU = max1abs(Uv);  // >= 1: their bits order like their values
     if (Lf && Uf) {
-        const double d = ft * fmax(1.0, fmax(fabs(Lv), fabs(Uv)));
-        if (Lv - Uv > d) return false;
+        const double d = ft * (dbits(mL) > dbits(mU) ? mL : mU);
+        if (dkey(Lv - Uv) > dkey(d)) return false;
     }
-    if (nmin == 0 && Uf && smin > Uv + ft * max1abs(Uv)) return false;
-    if (nmax == 0 && Lf && smax < Lv - ft * max1abs(Lv)) return false;
+    const double uhi = Uv + ft * mU, llo = Lv - ft * mL;  // U + delta(U), L - delta(L)
+    const long long ksmin = dkey(smin), ksmax = dkey(smax);
+    if (nmin == 0 && Uf && ksmin > dkey(uhi)) return false;
+    if (nmax == 0 && Lf && ksmax < dkey(llo)) return false;
     if (len == 0) {
         kind = RK_EMPTY;
         return true;
     }
-    const bool lo_ok = !Lf || (nmin == 0 && smin >= Lv - ft * max1abs(Lv));
+    const bool lo_ok = !Lf || (nmin == 0 && ksmin >= dkey(llo));
     if (lo_ok) {
-        const bool hi_ok = !Uf || (nmax == 0 && smax <= Uv + ft * max1abs(Uv));
+        const bool hi_ok = !Uf || (nmax == 0 && ksmax <= dkey(uhi));
         if (hi_ok) {
             kind = RK_REDUNDANT;
             return true;
