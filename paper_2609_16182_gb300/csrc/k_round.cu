@@ -207,6 +207,94 @@ __device__ __forceinline__ void cq_flush(const Ctx &C, CandQueue &q) {
     q.n = 0;
 }
 
+// Per-warp queue of S3 tests: an entry side that qualifies (its row slack
+// finite, the other terms finite or it the one infinite term) is queued
+// with its coefficient a, the row slack, the bound of its own term and the
+// bound it would tighten; the residual, the threshold and the sign test (the
+// FP64 work) then run 32 tests at a time, and the passing candidates go on
+// to the candidate queue.  flags: the candidate kind, | 4 if the entry's own
+// term is finite (residual = slack + a * bnd, else the slack itself).
+struct TestQueue {
+    double *a, *slack, *bnd, *bold;
+    int32_t *j, *flags;
+    int32_t n;
+};
+
+__device__ __forceinline__ void tq_run(const Ctx &C, CandQueue &cq, bool have, double a, double slack, double bnd,
+                                       double bold, int32_t j, int32_t flags) {
+    bool w = false;
+    double x = 0.0;
+    const int32_t kind = flags & 3;
+    if (have) {
+        x = (flags & 4) ? fma(a, bnd, slack) : slack;
+        w = kind == CQ_UPPER ? pass_upper(C, j, x, a, bold) : pass_lower(C, j, x, a, bold);
+    }
+    cq_push(C, cq, w, x, a, j, kind);
+}
+
+__device__ __forceinline__ void tq_push(const Ctx &C, TestQueue &q, CandQueue &cq, bool want, double a, double slack,
+                                        double bnd, double bold, int32_t j, int32_t flags) {
+    const unsigned b = __ballot_sync(0xffffffffu, want);
+    if (b == 0u) return;
+    const int lane = threadIdx.x & 31;
+    if (want) {
+        const int32_t p = q.n + __popc(b & ((1u << lane) - 1u));
+        q.a[p] = a;
+        q.slack[p] = slack;
+        q.bnd[p] = bnd;
+        q.bold[p] = bold;
+        q.j[p] = j;
+        q.flags[p] = flags;
+    }
+    q.n += __popc(b);
+    if (q.n < 32) return;
+    __syncwarp();
+    const double ia = q.a[lane], isl = q.slack[lane], ibn = q.bnd[lane], ibo = q.bold[lane];
+    const int32_t ij = q.j[lane], ifl = q.flags[lane];
+    const int32_t rest = q.n - 32;
+    double ra = 0.0, rs = 0.0, rb = 0.0, ro = 0.0;
+    int32_t rj = 0, rf = 0;
+    if (lane < rest) {
+        ra = q.a[32 + lane];
+        rs = q.slack[32 + lane];
+        rb = q.bnd[32 + lane];
+        ro = q.bold[32 + lane];
+        rj = q.j[32 + lane];
+        rf = q.flags[32 + lane];
+    }
+    __syncwarp();
+    if (lane < rest) {
+        q.a[lane] = ra;
+        q.slack[lane] = rs;
+        q.bnd[lane] = rb;
+        q.bold[lane] = ro;
+        q.j[lane] = rj;
+        q.flags[lane] = rf;
+    }
+    __syncwarp();
+    q.n = rest;
+    tq_run(C, cq, true, ia, isl, ibn, ibo, ij, ifl);
+}
+
+__device__ __forceinline__ void tq_flush(const Ctx &C, TestQueue &q, CandQueue &cq) {
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    const bool have = lane < q.n;
+    double ia = 0.0, isl = 0.0, ibn = 0.0, ibo = 0.0;
+    int32_t ij = 0, ifl = 0;
+    if (have) {
+        ia = q.a[lane];
+        isl = q.slack[lane];
+        ibn = q.bnd[lane];
+        ibo = q.bold[lane];
+        ij = q.j[lane];
+        ifl = q.flags[lane];
+    }
+    __syncwarp();
+    q.n = 0;
+    tq_run(C, cq, have, ia, isl, ibn, ibo, ij, ifl);
+}
+
 // S2: class of a row from its activities, first match wins: infeasible
 // sides, infeasible activity, empty, redundant, singleton.  Returns false if
 // the row proves the LP infeasible.
@@ -294,7 +382,7 @@ __device__ __forceinline__ unsigned long long len_hash(int32_t len) {
 // ------------------------------------------------------- S1 + S2 + S3 groups
 template <int W>
 __device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, int32_t &removed, int32_t &evaluated,
-                                           int32_t &tested, CandQueue &q) {
+                                           int32_t &tested, CandQueue &q, TestQueue &tq) {
     const unsigned mask = group_mask<W>();
     const int lane = threadIdx.x & (W - 1);
     // A row none of whose bounds, entries or sides changed since its last
@@ -360,16 +448,32 @@ __device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, 
     const int32_t T = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)trips);
     for (int32_t it = 0; it < T; it++) {
         bool w1 = false, w2 = false;
-        double x1 = 0.0, x2 = 0.0, a = 0.0;
-        int32_t j = 0, k1 = 0, k2 = 0;
+        double a = 0.0, bn1 = 0.0, bn2 = 0.0, bo1 = 0.0, bo2 = 0.0;
+        int32_t j = 0, f1 = 0, f2 = 0;
         if (it < trips) {
             const int32_t k = beg + lane + it * W;
             j = C.A.idx[k];
             a = C.A.val[k];
-            tighten_tests(C, j, a, up_row, lo_row, dU, dL, nmin, nmax, w1, x1, k1, w2, x2, k2, tested);
+            const double2 b = C.lu[j];
+            const bool neg = is_neg(a);
+            const double bmin = neg ? b.y : b.x, bmax = neg ? b.x : b.y;
+            const bool fmn = is_fin(bmin), fmx = is_fin(bmax);
+            if (up_row && (fmn ? nmin == 0 : nmin == 1)) {  // a x_j <= U - (min activity of the others)
+                w1 = true;
+                bn1 = bmin;
+                bo1 = neg ? b.x : b.y;
+                f1 = (neg ? CQ_LOWER : CQ_UPPER) | (fmn ? 4 : 0);
+            }
+            if (lo_row && (fmx ? nmax == 0 : nmax == 1)) {  // a x_j >= L - (max activity of the others)
+                w2 = true;
+                bn2 = bmax;
+                bo2 = neg ? b.y : b.x;
+                f2 = (neg ? CQ_UPPER : CQ_LOWER) | (fmx ? 4 : 0);
+            }
+            tested += (w1 ? 1 : 0) + (w2 ? 1 : 0);
         }
-        cq_push(C, q, w1, x1, a, j, k1);
-        cq_push(C, q, w2, x2, a, j, k2);
+        tq_push(C, tq, q, w1, a, dU, bn1, bo1, j, f1);
+        tq_push(C, tq, q, w2, a, dL, bn2, bo2, j, f2);
     }
 }
 
@@ -380,8 +484,12 @@ __host__ __device__ __forceinline__ int prop_lanes(int c) { return c <= 2 ? 1 : 
 __global__ void __launch_bounds__(kBlock) k_prop_groups(Ctx C, GroupGrid g) {
     __shared__ double s_qx[kBlock / 32][kQueueCap], s_qa[kBlock / 32][kQueueCap];
     __shared__ int32_t s_qj[kBlock / 32][kQueueCap], s_qk[kBlock / 32][kQueueCap];
+    __shared__ double s_ta[kBlock / 32][kQueueCap], s_ts[kBlock / 32][kQueueCap], s_tb[kBlock / 32][kQueueCap],
+        s_to[kBlock / 32][kQueueCap];
+    __shared__ int32_t s_tj[kBlock / 32][kQueueCap], s_tf[kBlock / 32][kQueueCap];
     const int warp = threadIdx.x >> 5;
     CandQueue q{s_qx[warp], s_qa[warp], s_qj[warp], s_qk[warp], 0};
+    TestQueue tq{s_ta[warp], s_ts[warp], s_tb[warp], s_to[warp], s_tj[warp], s_tf[warp], 0};
     const int c = grid_class(g, blockIdx.x);
     const int32_t lb = blockIdx.x - g.blk_start[c];
     int32_t removed = 0, evaluated = 0, tested = 0;
@@ -392,11 +500,12 @@ __global__ void __launch_bounds__(kBlock) k_prop_groups(Ctx C, GroupGrid g) {
     switch (c) {
         case 0:
         case 1:
-        case 2: prop_group<1>(C, i, valid, removed, evaluated, tested, q); break;
-        case 3: prop_group<8>(C, i, valid, removed, evaluated, tested, q); break;
-        case 4: prop_group<16>(C, i, valid, removed, evaluated, tested, q); break;
-        default: prop_group<32>(C, i, valid, removed, evaluated, tested, q); break;
+        case 2: prop_group<1>(C, i, valid, removed, evaluated, tested, q, tq); break;
+        case 3: prop_group<8>(C, i, valid, removed, evaluated, tested, q, tq); break;
+        case 4: prop_group<16>(C, i, valid, removed, evaluated, tested, q, tq); break;
+        default: prop_group<32>(C, i, valid, removed, evaluated, tested, q, tq); break;
     }
+    tq_flush(C, tq, q);
     cq_flush(C, q);
     block_add(removed, &C.st->rows_removed);
     block_add(evaluated, &C.st->nnz_eval);
