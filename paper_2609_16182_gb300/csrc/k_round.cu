@@ -481,7 +481,7 @@ __device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, 
 // classification then runs on every lane of the warp), else the class width.
 __host__ __device__ __forceinline__ int prop_lanes(int c) { return c <= 2 ? 1 : 1 << c; }
 
-__global__ void __launch_bounds__(kBlock) k_prop_groups(Ctx C, GroupGrid g) {
+__global__ void __launch_bounds__(kBlock, 4) k_prop_groups(Ctx C, GroupGrid g) {
     __shared__ double s_qx[kBlock / 32][kQueueCap], s_qa[kBlock / 32][kQueueCap];
     __shared__ int32_t s_qj[kBlock / 32][kQueueCap], s_qk[kBlock / 32][kQueueCap];
     __shared__ double s_ta[kBlock / 32][kQueueCap], s_ts[kBlock / 32][kQueueCap], s_tb[kBlock / 32][kQueueCap],
