@@ -403,7 +403,8 @@ __device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, 
     double smin = 0.0, smax = 0.0;
     int nmin = 0, nmax = 0;
     unsigned long long h = 0;
-    for (int32_t k = beg + lane; k < end; k += W) {
+#pragma unroll 4
+    for (int32_t k = beg + lane; k < end; k += W) {  // unrolled: the bound gathers overlap (same order)
         const int32_t j = C.A.idx[k];
         const double a = C.A.val[k];
         const double2 b = C.lu[j];
@@ -537,6 +538,7 @@ __global__ void __launch_bounds__(kBlock) k_prop_long_partial(Ctx C, unsigned lo
     double smin = 0.0, smax = 0.0;
     int nmin = 0, nmax = 0;
     unsigned long long h = 0;
+#pragma unroll 4
     for (int32_t k = ch.begin + threadIdx.x; k < ch.end; k += kBlock) {
         const int32_t j = __ldcs(C.A.idx + k);  // streamed once: evict first, keep the bounds cached
         const double a = __ldcs(C.A.val + k);
