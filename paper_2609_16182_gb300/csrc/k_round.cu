@@ -1018,12 +1018,12 @@ __global__ void __launch_bounds__(kBlock) k_s5_leader(Ctx C) {
 // rows of a column whose bounds changed must be re-evaluated next round
 // rows of the changed short columns need their activities next round: one
 // thread per listed column; columns longer than 32 entries are walked by the
-// whole warp in turn.  When the changed columns hold at least half of the
+// whole warp in turn.  When the changed columns hold at least an eighth of the
 // nonzeros, every row is marked instead (re-evaluating a row whose inputs did
 // not change finds nothing new).
 __global__ void __launch_bounds__(kBlock) k_mark_list(Ctx C, int64_t nnz) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    if (2 * (int64_t)*C.cl_nnz >= nnz) {
+    if (8 * (int64_t)*C.cl_nnz >= nnz) {
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < C.m; i += stride) C.rdnext[i] = 1;
         return;
     }
@@ -1051,7 +1051,7 @@ __global__ void __launch_bounds__(kBlock) k_mark_list(Ctx C, int64_t nnz) {
 
 __global__ void __launch_bounds__(kBlock) k_mark_long(Ctx C, int64_t nnz) {
     const Chunk ch = C.T.chunks[blockIdx.x];
-    if (!C.cchg[ch.seg] || 2 * (int64_t)*C.cl_nnz >= nnz) return;
+    if (!C.cchg[ch.seg] || 8 * (int64_t)*C.cl_nnz >= nnz) return;
     for (int32_t k = ch.begin + threadIdx.x; k < ch.end; k += kBlock) C.rdnext[C.T.idx[k]] = 1;
 }
 
