@@ -256,35 +256,43 @@ void materialize(lpp_postsolve *P) {
     P->host_ready = true;
 }
 
-// every array of a reduced LP copied to one pinned host block (async copies,
-// one synchronisation), on the first request for a host view
-void materialize_host(lpp_reduced *R) {
-    if (R->hblock) return;
+// Host copies of a reduced LP live in one pinned block (from the pinned
+// cache, sized for every array); each group is copied on its first request
+// with async copies and one synchronisation: 0 = the LP (CSR, c, sides,
+// bounds), 1 = the index maps, 2 = the CSC.
+void materialize_host(lpp_reduced *R, int group) {
+    if (R->host_done & (1 << group)) return;
     const size_t m = (size_t)R->m, n = (size_t)R->n, z = (size_t)R->nnz;
     struct Part {
+        int group;
         void **dst;
         const void *src;
         size_t bytes;
     };
-    const Part parts[] = {{(void **)&R->h_rp, R->rp, 4 * (m + 1)}, {(void **)&R->h_ci, R->ci, 4 * z},
-                          {(void **)&R->h_rv, R->rv, 8 * z},       {(void **)&R->h_c, R->c, 8 * n},
-                          {(void **)&R->h_L, R->L, 8 * m},         {(void **)&R->h_U, R->U, 8 * m},
-                          {(void **)&R->h_lb, R->lb, 8 * n},       {(void **)&R->h_ub, R->ub, 8 * n},
-                          {(void **)&R->h_tp, R->tp, 4 * (n + 1)}, {(void **)&R->h_ti, R->ti, 4 * z},
-                          {(void **)&R->h_tv, R->tv, 8 * z},       {(void **)&R->h_rmap, R->rmap, 4 * m},
-                          {(void **)&R->h_cmap, R->cmap, 4 * n}};
+    const Part parts[] = {{0, (void **)&R->h_rp, R->rp, 4 * (m + 1)}, {0, (void **)&R->h_ci, R->ci, 4 * z},
+                          {0, (void **)&R->h_rv, R->rv, 8 * z},       {0, (void **)&R->h_c, R->c, 8 * n},
+                          {0, (void **)&R->h_L, R->L, 8 * m},         {0, (void **)&R->h_U, R->U, 8 * m},
+                          {0, (void **)&R->h_lb, R->lb, 8 * n},       {0, (void **)&R->h_ub, R->ub, 8 * n},
+                          {1, (void **)&R->h_rmap, R->rmap, 4 * m},   {1, (void **)&R->h_cmap, R->cmap, 4 * n},
+                          {2, (void **)&R->h_tp, R->tp, 4 * (n + 1)}, {2, (void **)&R->h_ti, R->ti, 4 * z},
+                          {2, (void **)&R->h_tv, R->tv, 8 * z}};
     auto up = [](size_t b) { return (b + 63) & ~(size_t)63; };
-    size_t total = 0;
-    for (const Part &p : parts) total += up(p.bytes);
-    char *blk = static_cast<char *>(pinned_get_sized(total));
+    if (!R->hblock) {
+        size_t total = 0;
+        for (const Part &p : parts) total += up(p.bytes);
+        R->hblock = pinned_get_sized(total);
+    }
+    char *blk = static_cast<char *>(R->hblock);
     size_t off = 0;
     for (const Part &p : parts) {
-        *p.dst = blk + off;
-        if (p.bytes && p.src) LPP_CUDA(cudaMemcpyAsync(blk + off, p.src, p.bytes, cudaMemcpyDeviceToHost, 0));
+        if (p.group == group) {
+            *p.dst = blk + off;
+            if (p.bytes && p.src) LPP_CUDA(cudaMemcpyAsync(blk + off, p.src, p.bytes, cudaMemcpyDeviceToHost, 0));
+        }
         off += up(p.bytes);
     }
     LPP_CUDA(cudaStreamSynchronize(0));
-    R->hblock = blk;
+    R->host_done |= 1 << group;
 }
 
 }  // namespace
@@ -511,7 +519,7 @@ lpp_status lpp_reduced_view(lpp_reduced *R, lpp_lp *v, int32_t on_device) {
             v->on_device = 1;
             return LPP_OK;
         }
-        materialize_host(R);
+        materialize_host(R, 0);
         v->row_ptr = R->h_rp;
         v->col_idx = R->h_ci;
         v->val = R->h_rv;
@@ -534,7 +542,7 @@ lpp_status lpp_reduced_csc(lpp_reduced *R, const int32_t **col_ptr, const int32_
             if (row_idx) *row_idx = R->ti;
             if (val) *val = R->tv;
         } else {
-            materialize_host(R);
+            materialize_host(R, 2);
             if (col_ptr) *col_ptr = R->h_tp;
             if (row_idx) *row_idx = R->h_ti;
             if (val) *val = R->h_tv;
@@ -550,7 +558,7 @@ lpp_status lpp_reduced_maps(lpp_reduced *R, const int32_t **row_map, const int32
             if (row_map) *row_map = R->rmap;
             if (col_map) *col_map = R->cmap;
         } else {
-            materialize_host(R);
+            materialize_host(R, 1);
             if (row_map) *row_map = R->h_rmap;
             if (col_map) *col_map = R->h_cmap;
         }

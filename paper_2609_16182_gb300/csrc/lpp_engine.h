@@ -192,9 +192,10 @@ struct lpp_reduced {
     double *rv = nullptr, *tv = nullptr, *L = nullptr, *U = nullptr, *lb = nullptr, *ub = nullptr, *c = nullptr;
     std::vector<void *> owned;  // device allocations
     std::shared_ptr<lpp::SharedStore> shared;  // batch: storage shared with the other LPs
-    // host copies made on the first request for one (on_device = 0): every
-    // array at once, into one pinned block
+    // host copies made on the first request for them (on_device = 0), into
+    // one pinned block
     void *hblock = nullptr;
+    int host_done = 0;  // groups copied: 1 = LP, 2 = maps, 4 = CSC
     int32_t *h_rp = nullptr, *h_ci = nullptr, *h_tp = nullptr, *h_ti = nullptr, *h_rmap = nullptr, *h_cmap = nullptr;
     double *h_rv = nullptr, *h_c = nullptr, *h_L = nullptr, *h_U = nullptr, *h_lb = nullptr, *h_ub = nullptr,
            *h_tv = nullptr;

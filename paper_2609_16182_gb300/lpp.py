@@ -199,9 +199,9 @@ class Reduced:
     obj_offset: float
     row_map: np.ndarray
     col_map: np.ndarray
-    csc_ptr: np.ndarray
-    csc_idx: np.ndarray
-    csc_val: np.ndarray
+    csc_ptr: np.ndarray | None  # None when fetched with csc=False
+    csc_idx: np.ndarray | None
+    csc_val: np.ndarray | None
 
 
 class Result:
@@ -282,10 +282,10 @@ class Result:
     def presolve_ms(self) -> float:
         return self.info.presolve_ms
 
-    def reduced(self, copy: bool = True) -> Reduced:
-        """The reduced LP (and its CSC and maps) on the host.  The library
-        copies it once into pinned host memory it owns; copy=False returns
-        NumPy views of that memory, valid until close()."""
+    def reduced(self, copy: bool = True, csc: bool = True) -> Reduced:
+        """The reduced LP, its maps and (csc=True) its CSC on the host.  The
+        library copies them once into pinned host memory it owns; copy=False
+        returns NumPy views of that memory, valid until close()."""
         if self._reduced is not None:
             return self._reduced
         L = load()
@@ -308,15 +308,18 @@ class Result:
                    lb=arr(v.lb, n, float), ub=arr(v.ub, n, float), obj_offset=v.obj_offset)
         rm, cm = C.c_void_p(), C.c_void_p()
         _check(L.lpp_reduced_maps(self._red, C.byref(rm), C.byref(cm), 0))
-        tp, ti, tv = C.c_void_p(), C.c_void_p(), C.c_void_p()
-        _check(L.lpp_reduced_csc(self._red, C.byref(tp), C.byref(ti), C.byref(tv), 0))
         red["row_map"] = arr(rm.value, m, np.int32)
         red["col_map"] = arr(cm.value, n, np.int32)
-        red["csc_ptr"] = arr(tp.value, n + 1, np.int32) if n > 0 else np.zeros(1, np.int32)
-        red["csc_idx"] = arr(ti.value, nnz, np.int32)
-        red["csc_val"] = arr(tv.value, nnz, float)
+        if csc:
+            tp, ti, tv = C.c_void_p(), C.c_void_p(), C.c_void_p()
+            _check(L.lpp_reduced_csc(self._red, C.byref(tp), C.byref(ti), C.byref(tv), 0))
+            red["csc_ptr"] = arr(tp.value, n + 1, np.int32) if n > 0 else np.zeros(1, np.int32)
+            red["csc_idx"] = arr(ti.value, nnz, np.int32)
+            red["csc_val"] = arr(tv.value, nnz, float)
+        else:
+            red["csc_ptr"] = red["csc_idx"] = red["csc_val"] = None
         out = Reduced(**red)
-        if copy:
+        if copy and csc:
             self._reduced = out
         return out
 
