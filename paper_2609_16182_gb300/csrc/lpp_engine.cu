@@ -167,6 +167,7 @@ Engine::~Engine() {
     for (auto e : spare_events) cudaEventDestroy(e);
     for (auto e : ev_round)
         if (e) cudaEventDestroy(e);
+    if (s2) cudaStreamSynchronize(s2);  // vector copies still in flight after an error
     pool.release();
     if (s) cudaStreamSynchronize(s);
     pinned_put(st_h);
@@ -174,6 +175,9 @@ Engine::~Engine() {
     pinned_put(changed_h);
     pinned_put(s5_left_h);
     if (own_stream && s) cudaStreamDestroy(s);
+    if (ev_mat) cudaEventDestroy(ev_mat);
+    if (ev_vec) cudaEventDestroy(ev_vec);
+    if (s2) cudaStreamDestroy(s2);
 }
 
 void Engine::tbegin(int fam, double bytes) {
@@ -332,18 +336,37 @@ void Engine::ingest_plain(const lpp_lp &in) {
         LPP_CUDA(cudaMemcpyAsync(ci[0], in.col_idx, sizeof(int32_t) * (size_t)in.nnz, kind, s));
         LPP_CUDA(cudaMemcpyAsync(rv[0], in.val, sizeof(double) * (size_t)in.nnz, kind, s));
     }
-    // vectors: staged in the second buffers, checked and normalised into the first
+    // vectors: staged in the second buffers, checked and normalised into the
+    // first.  From the host they are copied on a second stream after the
+    // matrix, while the matrix checks and the transpose run (prepare then
+    // checks them); device inputs are copied and checked at once.
     double *slhs = L[1], *srhs = U[1], *slb = reinterpret_cast<double *>(lu[1]), *sub = slb + n0, *sc = c[1];
+    cudaStream_t sv = s;
+    if (!in.on_device) {
+        if (!s2) {
+            LPP_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+            LPP_CUDA(cudaEventCreateWithFlags(&ev_mat, cudaEventDisableTiming));
+            LPP_CUDA(cudaEventCreateWithFlags(&ev_vec, cudaEventDisableTiming));
+        }
+        LPP_CUDA(cudaEventRecord(ev_mat, s));
+        LPP_CUDA(cudaStreamWaitEvent(s2, ev_mat, 0));
+        sv = s2;
+    }
     if (in.m > 0) {
-        LPP_CUDA(cudaMemcpyAsync(slhs, in.lhs, sizeof(double) * (size_t)in.m, kind, s));
-        LPP_CUDA(cudaMemcpyAsync(srhs, in.rhs, sizeof(double) * (size_t)in.m, kind, s));
+        LPP_CUDA(cudaMemcpyAsync(slhs, in.lhs, sizeof(double) * (size_t)in.m, kind, sv));
+        LPP_CUDA(cudaMemcpyAsync(srhs, in.rhs, sizeof(double) * (size_t)in.m, kind, sv));
     }
     if (in.n > 0) {
-        LPP_CUDA(cudaMemcpyAsync(slb, in.lb, sizeof(double) * (size_t)in.n, kind, s));
-        LPP_CUDA(cudaMemcpyAsync(sub, in.ub, sizeof(double) * (size_t)in.n, kind, s));
-        LPP_CUDA(cudaMemcpyAsync(sc, in.c, sizeof(double) * (size_t)in.n, kind, s));
+        LPP_CUDA(cudaMemcpyAsync(slb, in.lb, sizeof(double) * (size_t)in.n, kind, sv));
+        LPP_CUDA(cudaMemcpyAsync(sub, in.ub, sizeof(double) * (size_t)in.n, kind, sv));
+        LPP_CUDA(cudaMemcpyAsync(sc, in.c, sizeof(double) * (size_t)in.n, kind, sv));
     }
-    ingest_vectors(slhs, srhs, slb, sub, sc, m0, n0, o.huge, L[0], U[0], lu[0], c[0], &st->err, s);
+    if (sv == s) {
+        ingest_vectors(slhs, srhs, slb, sub, sc, m0, n0, o.huge, L[0], U[0], lu[0], c[0], &st->err, s);
+    } else {
+        LPP_CUDA(cudaEventRecord(ev_vec, s2));
+        vec_pending = true;
+    }
 }
 
 void Engine::ingest_batch(const lpp_lp *ins, int32_t count) {
@@ -438,6 +461,12 @@ void Engine::prepare() {
     tb.tmp = scan_tmp;
     transpose(rp[0], ci[0], rv[0], row_of + 1, m0, n0, nnz0, tb, tp[0], ti[0], tv[0], s);
     LPP_CUDA(cudaGetLastError());
+    if (vec_pending) {  // the vectors' copies overlapped the checks and the transpose
+        vec_pending = false;
+        LPP_CUDA(cudaStreamWaitEvent(s, ev_vec, 0));
+        double *slb = reinterpret_cast<double *>(lu[1]);
+        ingest_vectors(L[1], U[1], slb, slb + n0, c[1], m0, n0, o.huge, L[0], U[0], lu[0], c[0], &st->err, s);
+    }
     iota(rmap[0], m0, 0, s);
     iota(cmap[0], n0, 0, s);
     fill_u64(cand_l, n0, kEncNegInf, s);
@@ -467,6 +496,7 @@ void Engine::prepare() {
     (k_set_i32<<<1, 1, 0, s>>>(&st->n_new, n0), note_launch());
     schedule_current();
     read_status();  // also keeps offs alive until its copy is done
+    if (st_h->err) throw StatusError(LPP_ERR_INVALID, "invalid LP (checks failed: vectors)");
     adopt_schedule();
 }
 

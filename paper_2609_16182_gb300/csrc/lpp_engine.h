@@ -87,6 +87,9 @@ struct Engine {
     unsigned long long *mL, *mU, *cand_l, *cand_u, *tkey, *tlead, *ch_hash;
     int32_t *s5_list[2] = {nullptr, nullptr}, *s5_cnt = nullptr;
     bool s5_clean = false;  // the last S5 resolved every group and no row changed since
+    cudaStream_t s2 = nullptr;                   // host inputs: the vectors' copies
+    cudaEvent_t ev_mat = nullptr, ev_vec = nullptr;
+    bool vec_pending = false;                    // their check waits for the copies (prepare)
     uint32_t *ctouch = nullptr;                                      // S3' column lists
     int32_t *tl_list = nullptr, *cl_list = nullptr, *col_cnt = nullptr;  // S5 lists of unmatched rows, their sizes per pass
     int32_t *rslot, *verdict;
