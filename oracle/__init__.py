@@ -17,7 +17,7 @@ _SRC = os.path.join(_HERE, "lpp_oracle.c")
 _LIB = os.path.join(_HERE, "liblpp_oracle.so")
 
 ROW_KEPT, ROW_EMPTY, ROW_REDUNDANT, ROW_SINGLETON, ROW_PARALLEL = 0, 1, 2, 3, 4
-COL_KEPT, COL_FIXED, COL_EMPTY = 0, 1, 2
+COL_KEPT, COL_FIXED, COL_EMPTY, COL_PARALLEL = 0, 1, 2, 3
 OK, INFEASIBLE, UNBOUNDED, ERR_INVALID = 0, 1, 2, -1
 
 
@@ -42,7 +42,7 @@ class _LP(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("feas_tol", C.c_double), ("bound_tol", C.c_double), ("huge", C.c_double),
                 ("max_implied", C.c_double), ("par_tol", C.c_double), ("max_rounds", C.c_int32),
-                ("dual_reductions", C.c_int32), ("par_max_iter", C.c_int32)]
+                ("dual_reductions", C.c_int32), ("par_max_iter", C.c_int32), ("parallel_cols", C.c_int32)]
 
 
 _OUT_FIELDS = [
@@ -53,6 +53,7 @@ _OUT_FIELDS = [
     ("row_map", C.c_void_p), ("col_map", C.c_void_p), ("obj_offset", C.c_double),
     ("row_kind", C.c_void_p), ("row_round", C.c_void_p), ("row_aux", C.c_void_p), ("row_val", C.c_void_p),
     ("col_kind", C.c_void_p), ("col_round", C.c_void_p), ("col_val", C.c_void_p),
+    ("col_aux", C.c_void_p), ("col_pass", C.c_void_p), ("col_mrg", C.c_void_p),
     ("col_lb", C.c_void_p), ("col_ub", C.c_void_p),
     ("act_min", C.c_void_p), ("act_max", C.c_void_p), ("act_scale_min", C.c_void_p),
     ("act_scale_max", C.c_void_p), ("ninf_min", C.c_void_p), ("ninf_max", C.c_void_p),
@@ -79,8 +80,7 @@ def lib():
         _lib.lppo_activities.argtypes = [C.POINTER(_LP), C.c_double, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p]
         _lib.lppo_activities.restype = C.c_int
-        _lib.lppo_postsolve_primal.argtypes = [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
-                                               C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib.lppo_postsolve_primal.argtypes = [C.c_int32, C.c_int32] + [C.c_void_p] * 9
         _lib.lppo_postsolve_primal.restype = C.c_int
     return _lib
 
@@ -140,6 +140,9 @@ class Result:
     col_kind: np.ndarray
     col_round: np.ndarray
     col_val: np.ndarray
+    col_aux: np.ndarray    # parallel-column merges: leader (original index)
+    col_pass: np.ndarray   # the pass of the merge within its round
+    col_mrg: np.ndarray    # [n, 4]: lk, uk, lj, uj just before the merge
     col_lb: np.ndarray
     col_ub: np.ndarray
     act_min: np.ndarray
@@ -176,7 +179,8 @@ def presolve(lp, opts: Opts | None = None) -> Result:
                            ("lb", n, np.float64), ("ub", n, np.float64), ("row_map", m, np.int32),
                            ("col_map", n, np.int32), ("row_kind", m, np.int32), ("row_round", m, np.int32),
                            ("row_aux", m, np.int32), ("row_val", m, np.float64), ("col_kind", n, np.int32),
-                           ("col_round", n, np.int32), ("col_val", n, np.float64), ("col_lb", n, np.float64),
+                           ("col_round", n, np.int32), ("col_val", n, np.float64), ("col_aux", n, np.int32),
+                           ("col_pass", n, np.int32), ("col_mrg", 4 * n, np.float64), ("col_lb", n, np.float64),
                            ("col_ub", n, np.float64), ("act_min", m, np.float64), ("act_max", m, np.float64),
                            ("act_scale_min", m, np.float64), ("act_scale_max", m, np.float64),
                            ("ninf_min", m, np.int32), ("ninf_max", m, np.int32),
@@ -196,7 +200,8 @@ def presolve(lp, opts: Opts | None = None) -> Result:
         col_map=arr["col_map"][:nr].copy(), obj_offset=out.obj_offset,
         row_kind=arr["row_kind"][:m], row_round=arr["row_round"][:m], row_aux=arr["row_aux"][:m],
         row_val=arr["row_val"][:m], col_kind=arr["col_kind"][:n], col_round=arr["col_round"][:n],
-        col_val=arr["col_val"][:n], col_lb=arr["col_lb"][:n], col_ub=arr["col_ub"][:n],
+        col_val=arr["col_val"][:n], col_aux=arr["col_aux"][:n], col_pass=arr["col_pass"][:n],
+        col_mrg=arr["col_mrg"][:4 * n].reshape(n, 4), col_lb=arr["col_lb"][:n], col_ub=arr["col_ub"][:n],
         act_min=arr["act_min"][:m], act_max=arr["act_max"][:m], act_scale_min=arr["act_scale_min"][:m],
         act_scale_max=arr["act_scale_max"][:m], ninf_min=arr["ninf_min"][:m], ninf_max=arr["ninf_max"][:m],
         round_nnz=arr["round_nnz"][:rounds].copy(), round_rows_removed=arr["round_rows_removed"][:rounds].copy(),
@@ -224,7 +229,9 @@ def postsolve_primal(res: Result, x_red: np.ndarray) -> np.ndarray:
     n = len(res.col_kind)
     x = np.zeros(max(n, 1))
     xr = np.ascontiguousarray(x_red, np.float64)
+    mrg = np.ascontiguousarray(res.col_mrg, np.float64).reshape(-1)
     rc = lib().lppo_postsolve_primal(n, res.n_red, _ptr(res.col_map), _ptr(res.col_kind), _ptr(res.col_val),
+                                     _ptr(res.col_aux), _ptr(res.col_round), _ptr(res.col_pass), _ptr(mrg),
                                      _ptr(xr), x.ctypes.data)
     if rc < 0:
         raise ValueError("bad column map")
@@ -234,7 +241,7 @@ def postsolve_primal(res: Result, x_red: np.ndarray) -> np.ndarray:
 def records(res: Result):
     """Postsolve records in canonical order (round, step, original index).
     Steps: 0 = row removed in S2, 1 = column fixed in S4, 2 = row merged in
-    S5, 3 = column fixed in S6."""
+    S5, 3 = column merged in S5c, 4 = column fixed in S6."""
     recs = []
     for i in np.flatnonzero(res.row_kind != ROW_KEPT):
         k = int(res.row_kind[i])
@@ -242,7 +249,8 @@ def records(res: Result):
         recs.append((int(res.row_round[i]), step, int(i), "row", k, int(res.row_aux[i]), float(res.row_val[i])))
     for j in np.flatnonzero(res.col_kind != COL_KEPT):
         k = int(res.col_kind[j])
-        step = 1 if k == COL_FIXED else 3
-        recs.append((int(res.col_round[j]), step, int(j), "col", k, -1, float(res.col_val[j])))
+        step = {COL_FIXED: 1, COL_PARALLEL: 3}.get(k, 4)
+        aux = int(res.col_aux[j]) if k == COL_PARALLEL else -1
+        recs.append((int(res.col_round[j]), step, int(j), "col", k, aux, float(res.col_val[j])))
     recs.sort(key=lambda t: (t[0], t[1], t[2]))
     return recs

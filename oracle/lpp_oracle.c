@@ -55,6 +55,7 @@ void lppo_opts_default(lppo_opts *o)
     o->max_rounds = 20;
     o->dual_reductions = 1;
     o->par_max_iter = 16;
+    o->parallel_cols = 0;
 }
 
 /* ---------------------------------------------------------------- audit */
@@ -187,6 +188,33 @@ static int cmp_key(const void *pa, const void *pb)
     return a->row < b->row ? -1 : (a->row > b->row);
 }
 
+/* ------------------------------------------------------ S5c key ordering
+ * Key of a column for parallel-column grouping (the S5 key applied to the
+ * columns of [c; A]): its length, its row pattern, for each coefficient
+ * whether its sign differs from the first one's, and the sign of the cost
+ * relative to the first coefficient (-1, 0, +1).  A_:j = lam A_:k with
+ * c_j = lam c_k gives equal keys for any lam != 0. */
+typedef struct {
+    int32_t col, len, csign;
+    const int32_t *rows;
+    const uint64_t *q;
+} ckey_t;
+
+static int cmp_ckey(const void *pa, const void *pb)
+{
+    const ckey_t *a = (const ckey_t *)pa, *b = (const ckey_t *)pb;
+    int32_t k;
+    if (a->len != b->len) return a->len < b->len ? -1 : 1;
+    for (k = 0; k < a->len; k++)
+        if (a->rows[k] != b->rows[k]) return a->rows[k] < b->rows[k] ? -1 : 1;
+    for (k = 0; k < a->len; k++)
+        if (a->q[k] != b->q[k]) return a->q[k] < b->q[k] ? -1 : 1;
+    if (a->csign != b->csign) return a->csign < b->csign ? -1 : 1;
+    return a->col < b->col ? -1 : (a->col > b->col);
+}
+
+static int dsign(double x) { return (x > 0) - (x < 0); }
+
 /* ------------------------------------------------------------ the loop */
 typedef struct {
     int32_t m, n;
@@ -218,6 +246,10 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     uint64_t *qbuf = NULL;
     int32_t *nrp = NULL, *nci = NULL;
     double *nv = NULL;
+    int32_t *tcp = NULL, *tri = NULL, *tfill = NULL, *calive = NULL;  /* S5c */
+    double *tvl = NULL;
+    ckey_t *ckeys = NULL;
+    uint64_t *cqbuf = NULL;
 
     memset(&s, 0, sizeof s);
     if (!validate(lp)) return LPPO_ERR_INVALID;
@@ -252,11 +284,19 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     ALLOC(hasf, m0); ALLOC(alive, m0); ALLOC(nrow, m0); ALLOC(ncol, n0);
     ALLOC(keys, m0); ALLOC(qbuf, lp->nnz);
     ALLOC(nrp, m0 + 1); ALLOC(nci, lp->nnz); ALLOC(nv, lp->nnz);
+    ALLOC(tcp, n0 + 1); ALLOC(tri, lp->nnz); ALLOC(tvl, lp->nnz); ALLOC(tfill, n0); ALLOC(calive, n0);
+    ALLOC(ckeys, n0); ALLOC(cqbuf, lp->nnz);
 
     for (i = 0; i < m0; i++) {
         out->row_kind[i] = LPPO_ROW_KEPT; out->row_round[i] = 0; out->row_aux[i] = -1; out->row_val[i] = 0.0;
     }
-    for (j = 0; j < n0; j++) { out->col_kind[j] = LPPO_COL_KEPT; out->col_round[j] = 0; out->col_val[j] = 0.0; }
+    for (j = 0; j < n0; j++) {
+        out->col_kind[j] = LPPO_COL_KEPT; out->col_round[j] = 0; out->col_val[j] = 0.0;
+        if (out->col_aux) out->col_aux[j] = -1;
+        if (out->col_pass) out->col_pass[j] = 0;
+        if (out->col_mrg) { out->col_mrg[4 * j] = 0.0; out->col_mrg[4 * j + 1] = 0.0;
+                            out->col_mrg[4 * j + 2] = 0.0; out->col_mrg[4 * j + 3] = 0.0; }
+    }
     out->where = LPPO_WHERE_NONE; out->index = -1; out->round = 0; out->rounds = 0;
     for (i = 0; i < m0; i++) { /* no round executed yet: no row has activities */
         out->ninf_min[i] = -1; out->ninf_max[i] = -1;
@@ -567,6 +607,104 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
             }
         }
 
+        /* ---- S5c (opt-in): parallel columns, the S5 machinery on [c; A].
+               On the columns of the round-start matrix (the rows S2 and S5
+               removed this round included: columns parallel on every row are
+               parallel on the kept ones), not fixed in S4.  Columns with
+               equal keys form a group; in each pass the group's leader (its
+               first column) takes the first other column j parallel to it:
+               A_:j = lam A_:k and c_j = lam c_k, lam = a_j,first / a_k,first,
+               each entry and the cost within par_tol as in S5.  Then
+               y = x_k + lam x_j replaces x_k, with bounds
+                 lam > 0: [l_k + lam l_j, u_k + lam u_j],
+                 lam < 0: [l_k + lam u_j, u_k + lam l_j],
+               and column j leaves the LP (its entries without a side shift,
+               its cost without an objective constant).  A leader with no
+               parallel column leaves the group.  At most par_max_iter passes. */
+        if (o->parallel_cols) {
+            int32_t nk = 0;
+            int64_t qo = 0;
+            for (j = 0; j <= n; j++) tcp[j] = 0;
+            for (k = 0; k < nnz; k++) tcp[s.ci[k] + 1]++;
+            for (j = 0; j < n; j++) tcp[j + 1] += tcp[j];
+            for (j = 0; j < n; j++) tfill[j] = tcp[j];
+            for (i = 0; i < m; i++)
+                for (k = s.rp[i]; k < s.rp[i + 1]; k++) {
+                    int32_t jj = s.ci[k];
+                    tri[tfill[jj]] = i; tvl[tfill[jj]] = s.v[k]; tfill[jj]++;
+                }
+            for (j = 0; j < n; j++) {
+                int32_t len = tcp[j + 1] - tcp[j];
+                if (fixed[j] || len < 1) continue;
+                ckeys[nk].col = j; ckeys[nk].len = len;
+                ckeys[nk].rows = tri + tcp[j];
+                ckeys[nk].q = cqbuf + qo;
+                ckeys[nk].csign = dsign(s.c[j]) * dsign(tvl[tcp[j]]);
+                for (k = tcp[j]; k < tcp[j + 1]; k++) cqbuf[qo++] = rel_sign(tvl[k], tvl[tcp[j]]);
+                nk++;
+            }
+            qsort(ckeys, (size_t)nk, sizeof(ckey_t), cmp_ckey);
+            {
+                int32_t g0, g1;
+                for (g0 = 0; g0 < nk; g0 = g1) {
+                    ckey_t probe = ckeys[g0];
+                    int32_t gsz, it, t;
+                    for (g1 = g0 + 1; g1 < nk; g1++) {
+                        probe.col = ckeys[g1].col; /* compare keys only */
+                        if (cmp_ckey(&probe, &ckeys[g1]) != 0) break;
+                    }
+                    gsz = g1 - g0;
+                    if (gsz < 2) continue;
+                    for (t = 0; t < gsz; t++) calive[t] = 1;
+                    for (it = 0; it < o->par_max_iter; it++) {
+                        int32_t lead = -1, fol = -1, ck, cj, len, q;
+                        double lam = 0.0;
+                        for (t = 0; t < gsz && lead < 0; t++) if (calive[t]) lead = t;
+                        if (lead < 0) break;
+                        ck = ckeys[g0 + lead].col; len = ckeys[g0 + lead].len;
+                        for (t = lead + 1; t < gsz && fol < 0; t++) {
+                            const double *ak, *aj;
+                            int par = 1;
+                            double lc;
+                            if (!calive[t]) continue;
+                            cj = ckeys[g0 + t].col;
+                            ak = tvl + tcp[ck]; aj = tvl + tcp[cj];
+                            lam = aj[0] / ak[0];
+                            for (q = 0; q < len && par; q++) {
+                                double la = lam * ak[q];
+                                if (!(fabs(aj[q] - la) <= o->par_tol * dmax(fabs(aj[q]), fabs(la)))) par = 0;
+                            }
+                            lc = lam * s.c[ck];
+                            if (par && !(fabs(s.c[cj] - lc) <= o->par_tol * dmax(fabs(s.c[cj]), fabs(lc)))) par = 0;
+                            if (par) fol = t;
+                        }
+                        if (fol < 0) { calive[lead] = 0; continue; }
+                        cj = ckeys[g0 + fol].col;
+                        calive[fol] = 0;
+                        {
+                            const double lk = s.l[ck], uk = s.u[ck], lj = s.l[cj], uj = s.u[cj];
+                            double nlk, nuk;
+                            if (lam > 0) { nlk = lk + lam * lj; nuk = uk + lam * uj; }
+                            else { nlk = lk + lam * uj; nuk = uk + lam * lj; }
+                            out->col_kind[s.cmap[cj]] = LPPO_COL_PARALLEL; out->col_round[s.cmap[cj]] = r;
+                            out->col_val[s.cmap[cj]] = lam;
+                            if (out->col_aux) out->col_aux[s.cmap[cj]] = s.cmap[ck];
+                            if (out->col_pass) out->col_pass[s.cmap[cj]] = it;
+                            if (out->col_mrg) {
+                                out->col_mrg[4 * s.cmap[cj]] = lk; out->col_mrg[4 * s.cmap[cj] + 1] = uk;
+                                out->col_mrg[4 * s.cmap[cj] + 2] = lj; out->col_mrg[4 * s.cmap[cj] + 3] = uj;
+                            }
+                            s.l[ck] = nlk; s.u[ck] = nuk;
+                            s.ebl[ck] += fabs(lam) * s.ebl[cj] + UROUND * fabs(nlk);
+                            s.ebu[ck] += fabs(lam) * s.ebu[cj] + UROUND * fabs(nuk);
+                            fixed[cj] = 3; fixv[cj] = 0.0;
+                            nfixed++;
+                        }
+                    }
+                }
+            }
+        }
+
         /* ---- S6: a column with no entry left in a kept row is fixed at the
                bound its cost prefers (dual reduction) */
         if (o->dual_reductions) {
@@ -592,8 +730,8 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                 break;
             }
         }
-        for (j = 0; j < n; j++) /* objective constant, column order */
-            if (fixed[j]) s.offset += s.c[j] * fixv[j];
+        for (j = 0; j < n; j++) /* objective constant, column order (merged columns: none) */
+            if (fixed[j] && fixed[j] != 3) s.offset += s.c[j] * fixv[j];
 
         /* ---- S7: shift the sides of kept rows by their fixed columns, then
                drop removed rows and fixed columns, keeping relative order */
@@ -607,7 +745,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                 if (kind[i] != LPPO_ROW_KEPT) { nrow[i] = -1; continue; }
                 for (k = s.rp[i]; k < s.rp[i + 1]; k++) {
                     int32_t jj = s.ci[k];
-                    if (!fixed[jj]) continue;
+                    if (!fixed[jj] || fixed[jj] == 3) continue;  /* merged columns: no shift */
                     sh += s.v[k] * fixv[jj];
                     ssh += fabs(s.v[k] * fixv[jj]);
                     esh += fabs(s.v[k]) * s.ebl[jj];
@@ -667,7 +805,9 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     for (j = 0; j < n0; j++) { out->col_lb[j] = NAN; out->col_ub[j] = NAN; }
     for (j = 0; j < s.n; j++) { out->col_lb[s.cmap[j]] = s.l[j]; out->col_ub[s.cmap[j]] = s.u[j]; }
     for (j = 0; j < n0; j++)
-        if (out->col_kind[j] != LPPO_COL_KEPT) { out->col_lb[j] = out->col_val[j]; out->col_ub[j] = out->col_val[j]; }
+        if (out->col_kind[j] != LPPO_COL_KEPT && out->col_kind[j] != LPPO_COL_PARALLEL) {
+            out->col_lb[j] = out->col_val[j]; out->col_ub[j] = out->col_val[j];
+        }
     out->audit_min_ratio = au.min_ratio; out->audit_decisions = au.n; out->audit_below_1e3 = au.below;
 
     free(s.rp); free(s.ci); free(s.v); free(s.L); free(s.U); free(s.l); free(s.u); free(s.c);
@@ -676,6 +816,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     free(kind); free(fixed); free(colcnt); free(nl); free(nu); free(ebnl); free(ebnu); free(fixv);
     free(mL); free(mU); free(ebmL); free(ebmU); free(hasf); free(alive); free(nrow); free(ncol);
     free(keys); free(qbuf); free(nrp); free(nci); free(nv);
+    free(tcp); free(tri); free(tvl); free(tfill); free(calive); free(ckeys); free(cqbuf);
     return status;
 oom:
     free(s.rp); free(s.ci); free(s.v); free(s.L); free(s.U); free(s.l); free(s.u); free(s.c);
@@ -684,21 +825,62 @@ oom:
     free(kind); free(fixed); free(colcnt); free(nl); free(nu); free(ebnl); free(ebnu); free(fixv);
     free(mL); free(mU); free(ebmL); free(ebmU); free(hasf); free(alive); free(nrow); free(ncol);
     free(keys); free(qbuf); free(nrp); free(nci); free(nv);
+    free(tcp); free(tri); free(tvl); free(tfill); free(calive); free(ckeys); free(cqbuf);
     return LPPO_ERR_OOM;
 }
 
 /* Postsolve, primal part (Sec. 2.1, postsolver paragraph; Sec. 3.3): every
    kept column takes its reduced value, every fixed column its record value.
-   Row removals and bound changes need no primal postsolve step. */
+   A merged column j (leader k, y = x_k + lam x_j) is split again, merges
+   undone latest first: x_j is the lowest value in [lj, uj] that keeps
+   x_k = y - lam x_j in [lk, uk] (the highest if that is -inf, 0 if both
+   are infinite), with the bounds of the moment of the merge.  Row removals
+   and bound changes need no primal postsolve step. */
 int lppo_postsolve_primal(int32_t n_orig, int32_t n_red, const int32_t *col_map,
                           const int32_t *col_kind, const double *col_val,
-                          const double *x_red, double *x_orig)
+                          const int32_t *col_aux, const int32_t *col_round, const int32_t *col_pass,
+                          const double *col_mrg, const double *x_red, double *x_orig)
 {
-    int32_t j;
+    int32_t j, nm = 0, a, b;
+    int32_t *ord;
     for (j = 0; j < n_orig; j++) x_orig[j] = col_kind[j] != LPPO_COL_KEPT ? col_val[j] : NAN;
     for (j = 0; j < n_red; j++) {
         if (col_map[j] < 0 || col_map[j] >= n_orig) return LPPO_ERR_INVALID;
         x_orig[col_map[j]] = x_red[j];
     }
+    for (j = 0; j < n_orig; j++) if (col_kind[j] == LPPO_COL_PARALLEL) nm++;
+    if (nm == 0) return LPPO_OK;
+    if (!col_aux || !col_round || !col_pass || !col_mrg) return LPPO_ERR_INVALID;
+    ord = malloc(sizeof(int32_t) * (size_t)nm);
+    if (!ord) return LPPO_ERR_OOM;
+    nm = 0;
+    for (j = 0; j < n_orig; j++) if (col_kind[j] == LPPO_COL_PARALLEL) ord[nm++] = j;
+    /* latest merge first: (round, pass) descending, a plain insertion sort */
+    for (a = 1; a < nm; a++) {
+        int32_t x = ord[a];
+        for (b = a - 1; b >= 0; b--) {
+            int32_t y = ord[b];
+            int later = col_round[x] > col_round[y] || (col_round[x] == col_round[y] && col_pass[x] > col_pass[y]);
+            if (!later) break;
+            ord[b + 1] = y;
+        }
+        ord[b + 1] = x;
+    }
+    for (a = 0; a < nm; a++) {
+        const int32_t jj = ord[a], kk = col_aux[jj];
+        const double lam = col_val[jj], y = x_orig[kk];
+        const double lk = col_mrg[4 * jj], uk = col_mrg[4 * jj + 1], lj = col_mrg[4 * jj + 2], uj = col_mrg[4 * jj + 3];
+        double lo, hi, xj;
+        if (lam > 0) { lo = (y - uk) / lam; hi = (y - lk) / lam; }
+        else { lo = (y - lk) / lam; hi = (y - uk) / lam; }
+        if (lj > lo) lo = lj;
+        if (uj < hi) hi = uj;
+        if (lo > -INFINITY && lo < INFINITY) xj = lo;
+        else if (hi > -INFINITY && hi < INFINITY) xj = hi;
+        else xj = 0.0;
+        x_orig[jj] = xj;
+        x_orig[kk] = y - lam * xj;
+    }
+    free(ord);
     return LPPO_OK;
 }

@@ -42,6 +42,7 @@ extern "C" {
 #define LPPO_COL_KEPT       0
 #define LPPO_COL_FIXED      1   /* lb == ub after tightening (primal)        */
 #define LPPO_COL_EMPTY      2   /* no entry left, fixed by the cost (dual)    */
+#define LPPO_COL_PARALLEL   3   /* merged into a parallel column (opt-in)      */
 
 /* where an infeasible / unbounded verdict was found */
 #define LPPO_WHERE_NONE 0
@@ -67,6 +68,7 @@ typedef struct {
     int32_t max_rounds;    /* 20    */
     int32_t dual_reductions; /* 1   */
     int32_t par_max_iter;  /* 16    */
+    int32_t parallel_cols; /* 0: S5c (parallel columns) off */
 } lppo_opts;
 
 /* All arrays are allocated by the caller with the sizes given. */
@@ -84,6 +86,10 @@ typedef struct {
     int32_t *row_kind, *row_round, *row_aux;  double *row_val;
     /* per original column [n] */
     int32_t *col_kind, *col_round;  double *col_val;
+    /* parallel-column merges [n] (col_val = lambda): the leader's original
+       index, the pass within the round, and the bounds of the leader and of
+       the merged column just before the merge (lk, uk, lj, uj) [4n] */
+    int32_t *col_aux, *col_pass;  double *col_mrg;
     double  *col_lb, *col_ub;     /* final bounds (fixed columns: value) */
     /* activities of the last executed round, per original row [m]
        (rows not active at that round's start: ninf = -1)               */
@@ -106,10 +112,13 @@ int  lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out);
 int  lppo_activities(const lppo_lp *lp, double huge, double *act_min, double *act_max,
                      int32_t *ninf_min, int32_t *ninf_max);
 
-/* Primal postsolve (Sec. 2.1, postsolver paragraph): x_orig from x_red. */
+/* Primal postsolve (Sec. 2.1, postsolver paragraph): x_orig from x_red.
+   col_aux, col_round, col_pass, col_mrg (the merge records) may be NULL when
+   no column was merged. */
 int  lppo_postsolve_primal(int32_t n_orig, int32_t n_red, const int32_t *col_map,
                            const int32_t *col_kind, const double *col_val,
-                           const double *x_red, double *x_orig);
+                           const int32_t *col_aux, const int32_t *col_round, const int32_t *col_pass,
+                           const double *col_mrg, const double *x_red, double *x_orig);
 
 #ifdef __cplusplus
 }

@@ -500,6 +500,50 @@ def micro(seed: int, m: int = 5, n: int = 6, slack: float = 0.5) -> LP:
     return _finish(m, n, ptr, cols, vals, c, lhs, rhs, lb, ub, dict(x0=x0, kinds=kinds), f"micro-{seed}")
 
 
+# ------------------------------------------------------- parallel columns
+def parcols(seed: int, m: int = 200, n_base: int = 280, pairs: int = 10, per_col: int = 6,
+            slack: float = 2.0, eq_frac: float = 0.3) -> LP:
+    """An LP with planted parallel columns: `n_base` random columns (about
+    `per_col` entries each, values U[-10,10] without zero, finite bounds), then
+    `pairs` copies of distinct base columns scaled by lambda in
+    {-4, -2, -1/2, 1/2, 2, 4} (exact in binary) with costs scaled alike, so that
+    A_:copy = lambda A_:base and c_copy = lambda c_base hold exactly.  Sides
+    around A x0 for x0 in the box, `eq_frac` of them equalities."""
+    rng = np.random.default_rng(seed)
+    per = np.clip(rng.poisson(per_col, n_base), 2, m).astype(np.int64)
+    cols_rows = [np.sort(rng.choice(m, size=int(k), replace=False)) for k in per]
+    cols_vals = [_draw_magnitudes(rng, int(k), -10.0, 10.0) for k in per]
+    lb = -rng.uniform(0.0, 5.0, n_base + pairs)
+    ub = lb + rng.uniform(1.0, 10.0, n_base + pairs)
+    c = rng.normal(0.0, 1.0, n_base + pairs)
+    base = rng.choice(n_base, size=min(pairs, n_base), replace=False)
+    lams = rng.choice([-4.0, -2.0, -0.5, 0.5, 2.0, 4.0], size=len(base))
+    for t, (k, lam) in enumerate(zip(base, lams)):
+        cols_rows.append(cols_rows[k].copy())
+        cols_vals.append(cols_vals[k] * lam)
+        c[n_base + t] = lam * c[k]
+    n = n_base + len(base)
+    # column lists -> CSR (rows of each column are distinct; columns increase in a row)
+    rows = np.concatenate(cols_rows)
+    colid = np.concatenate([np.full(len(r), j, np.int64) for j, r in enumerate(cols_rows)])
+    vals = np.concatenate(cols_vals)
+    order = np.lexsort((colid, rows))
+    rows, colid, vals = rows[order], colid[order], vals[order]
+    ptr = _ptr_from_lengths(np.bincount(rows, minlength=m).astype(np.int64))
+    x0 = _point_in_box(rng, lb, ub)
+    ax = _dot_rows(ptr, colid, vals, x0, m)
+    lhs = ax - rng.uniform(0.0, slack, m)
+    rhs = ax + rng.uniform(0.0, slack, m)
+    eq = rng.random(m) < eq_frac
+    lhs[eq] = ax[eq]
+    rhs[eq] = ax[eq]
+    empty = np.diff(ptr) == 0
+    lhs[empty] = np.minimum(lhs[empty], 0.0)
+    rhs[empty] = np.maximum(rhs[empty], 0.0)
+    planted = dict(base=base, copies=np.arange(n_base, n), lam=lams, x0=x0)
+    return _finish(m, n, ptr, colid, vals, c, lhs, rhs, lb, ub, planted, f"parcols-{seed}")
+
+
 # ----------------------------------------------------- vectorised 200-row mix
 def _distinct_columns(rng, lengths, n, pool=None):
     """Columns for rows of the given lengths, distinct inside each row, drawn
