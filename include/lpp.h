@@ -19,6 +19,8 @@
  *   S3  activity-based bound tightening, Jacobi form (Sec. 3.1)
  *   S4  fixing of variables whose bounds meet (Sec. 2.1, "fixing a variable")
  *   S5  parallel rows by hashing plus a leader check (Sec. 3.2)
+ *   S5c parallel columns, the same machinery on the columns of [c; A]
+ *       (Sec. 3.2, parallel columns; only with opts.parallel_cols = 1)
  *   S6  empty columns fixed at the bound their cost prefers (dual rule)
  *   S7  compaction of the CSR and CSC matrices and of all row/column vectors
  * The reduced LP has the same form (Sec. 3.3) and stays in device memory; the
@@ -73,6 +75,7 @@ typedef enum lpp_status {
 #define LPP_COL_KEPT 0
 #define LPP_COL_FIXED 1       /* lb == ub: fixed at that value (primal)           */
 #define LPP_COL_EMPTY 2       /* no entry left: fixed at the cheaper bound (dual) */
+#define LPP_COL_PARALLEL 3    /* merged into a parallel leader column (S5c)       */
 /* Where a verdict was found. */
 #define LPP_WHERE_NONE 0
 #define LPP_WHERE_ROW 1
@@ -104,7 +107,9 @@ typedef struct lpp_opts {
     double par_tol;         /* [1e-12] relative tolerance of the parallel-row check          */
     int32_t max_rounds;     /* [20]    round cap                                             */
     int32_t dual_reductions;/* [1]     enable S6 (empty columns)                             */
-    int32_t par_max_iter;   /* [16]    leader passes per group of equal keys (S5)            */
+    int32_t par_max_iter;   /* [16]    leader passes per group of equal keys (S5, S5c)       */
+    int32_t parallel_cols;  /* [0]     1: merge parallel columns (S5c, Sec. 3.2); lpp_presolve
+                                       and lpp_presolve_batch only (a server rejects it)      */
     int32_t timing;         /* [0]     1: time every kernel launch with CUDA events           */
     int32_t device;         /* [0]     CUDA device ordinal                                   */
     void *stream;           /* [NULL]  cudaStream_t to run on; NULL: a library-owned stream  */
@@ -165,10 +170,22 @@ lpp_status lpp_result_info(const lpp_postsolve *rec, lpp_info *info);
  * its column; parallel: its leader row, original indices; else -1), value
  * (singleton: its coefficient; parallel: lambda with row = lambda * leader). */
 lpp_status lpp_result_rows(const lpp_postsolve *rec, int32_t *kind, int32_t *round, int32_t *aux, double *val);
-/* Per original column (host arrays of n): kind, round, fixed value, and the
- * final bounds (a fixed column reports its value as both bounds). */
+/* Per original column (host arrays of n): kind, round, value, and the final
+ * bounds.  A fixed or empty column reports its value as both bounds; a
+ * merged column (LPP_COL_PARALLEL) reports lambda as its value and NaN
+ * bounds (its range lives on in the leader's). */
 lpp_status lpp_result_cols(const lpp_postsolve *rec, int32_t *kind, int32_t *round, double *val, double *lb,
                            double *ub);
+/* Parallel-column merges (Sec. 3.2, parallel columns; opts.parallel_cols).
+ * A column j of kind LPP_COL_PARALLEL was merged into its leader k when
+ * A_:j = lambda A_:k and c_j = lambda c_k (lambda is its value in
+ * lpp_result_cols): x_k + lambda x_j became one column y in place of x_k.
+ * Per original column (host arrays of n, any pointer may be NULL): leader[j]
+ * = k (original index, -1 if j was not merged), pass[j] = the leader pass of
+ * its round (0-based; merges are undone latest (round, pass) first), and
+ * bounds[4j .. 4j+3] = l_k, u_k, l_j, u_j at the time of the merge (NaN if
+ * j was not merged). */
+lpp_status lpp_result_merges(const lpp_postsolve *rec, int32_t *leader, int32_t *pass, double *bounds);
 /* Activities of the last executed round per original row (host arrays of m);
  * rows not present at that round's start get NaN and -1. */
 lpp_status lpp_result_activity(const lpp_postsolve *rec, double *act_min, double *act_max, int32_t *ninf_min,
@@ -183,7 +200,10 @@ lpp_status lpp_result_kernels(const lpp_postsolve *rec, int32_t cap, lpp_kernel_
 
 /* Primal postsolve on the CPU (Sec. 2.1 postsolver; Sec. 3.3): x_red[n_red]
  * -> x_orig[n] (host arrays): kept columns take their reduced value, fixed
- * columns their recorded value. */
+ * columns their recorded value.  Merges are split latest first: with
+ * y = x_k + lambda x_j at hand, x_j is the lowest value of [l_j, u_j] that
+ * leaves y - lambda x_j inside [l_k, u_k] (the highest if that range has no
+ * finite low end, 0 if it has neither), and x_k = y - lambda x_j. */
 lpp_status lpp_postsolve_primal(const lpp_postsolve *rec, const double *x_red, double *x_orig);
 
 void lpp_free_reduced(lpp_reduced *red);

@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kBlock) k_colkeep(Ctx C, CompactCtx K) {
                 fixed = 1;
             }
         }
-        if (!dead && kind != CK_KEPT) contrib = C.c[j] * C.fixv[j];
+        if (!dead && kind != CK_KEPT && kind != CK_PARALLEL) contrib = C.c[j] * C.fixv[j];  // merged: none
         const bool keep = !dead && kind == CK_KEPT;
         K.c_keep[j] = keep;
         if (!keep) K.c_len[j] = 0;

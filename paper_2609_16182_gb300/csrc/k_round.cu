@@ -372,13 +372,6 @@ __device__ __forceinline__ int32_t finish_row(const Ctx &C, int32_t i, int32_t b
     return 1;
 }
 
-__device__ __forceinline__ unsigned long long entry_hash(int32_t j, bool flip) {
-    return mix64(((unsigned long long)(uint32_t)j << 1) | (unsigned long long)flip);
-}
-__device__ __forceinline__ unsigned long long len_hash(int32_t len) {
-    return mix64(0xa0761d6478bd642fULL ^ (unsigned long long)(uint32_t)len);
-}
-
 // ------------------------------------------------------- S1 + S2 + S3 groups
 template <int W>
 __device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, int32_t &removed, int32_t &evaluated,

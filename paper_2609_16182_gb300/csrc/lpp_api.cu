@@ -1,4 +1,5 @@
 // lpp_api.cu -- the C ABI of lpp.h: argument checks, engine runs, result objects.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -51,7 +52,7 @@ lpp_opts resolve_opts(const lpp_opts *opts) {
     if (opts) o = *opts;
     else lpp_opts_default(&o);
     if (o.max_rounds < 0 || o.par_max_iter < 1 || !(o.feas_tol >= 0) || !(o.bound_tol >= 0) || !(o.huge > 0) ||
-        !(o.max_implied > 0) || !(o.par_tol >= 0))
+        !(o.max_implied > 0) || !(o.par_tol >= 0) || (o.parallel_cols != 0 && o.parallel_cols != 1))
         throw StatusError(LPP_ERR_INVALID, "bad options");
     return o;
 }
@@ -122,11 +123,16 @@ std::shared_ptr<DeviceRecords> take_records(Engine &E) {
     D->ck = E.rec_ck;
     D->cr = E.rec_cr;
     D->cv = E.rec_cv;
+    D->ca = E.rec_ca;
+    D->cp = E.rec_cp;
+    D->cm = E.rec_cm;
     D->lu = E.lu[E.cur];
     D->act = E.act[E.act_buf];
     D->ninf = E.ninf[E.act_buf];
     for (void *p : {(void *)D->rk, (void *)D->rr, (void *)D->ra, (void *)D->rv, (void *)D->ck, (void *)D->cr,
-                    (void *)D->cv, (void *)D->lu, (void *)D->act, (void *)D->ninf}) {
+                    (void *)D->cv, (void *)D->lu, (void *)D->act, (void *)D->ninf, (void *)D->ca, (void *)D->cp,
+                    (void *)D->cm}) {
+        if (!p) continue;
         E.pool.forget(p);
         D->owned.push_back(p);
     }
@@ -233,7 +239,19 @@ void materialize(lpp_postsolve *P) {
         }
     }
     for (int32_t j = 0; j < n; j++)
-        if (P->col_kind[j] != LPP_COL_KEPT) P->col_lb[j] = P->col_ub[j] = P->col_val[j];
+        if (P->col_kind[j] != LPP_COL_KEPT && P->col_kind[j] != LPP_COL_PARALLEL)
+            P->col_lb[j] = P->col_ub[j] = P->col_val[j];
+    if (D.ca) {
+        d2h_slice(P->col_aux, D.ca, c0, n);
+        d2h_slice(P->col_pass, D.cp, c0, n);
+        d2h_slice(P->col_mrg, D.cm, 4 * (size_t)c0, 4 * (size_t)n);
+        for (int32_t j = 0; j < n; j++)
+            if (P->col_aux[j] >= 0) P->col_aux[j] -= c0;
+    } else {
+        P->col_aux.assign(n, -1);
+        P->col_pass.assign(n, 0);
+        P->col_mrg.assign(4 * (size_t)n, NAN);
+    }
     std::vector<double2> act;
     std::vector<int2> ni;
     std::vector<int32_t> am;
@@ -312,6 +330,7 @@ void lpp_opts_default(lpp_opts *o) {
     o->max_rounds = 20;
     o->dual_reductions = 1;
     o->par_max_iter = 16;
+    o->parallel_cols = 0;
     o->timing = 0;
     o->device = 0;
     o->stream = nullptr;
@@ -600,6 +619,18 @@ lpp_status lpp_result_cols(const lpp_postsolve *Pc, int32_t *kind, int32_t *roun
     return LPP_OK;
 }
 
+lpp_status lpp_result_merges(const lpp_postsolve *Pc, int32_t *leader, int32_t *pass, double *bounds) {
+    if (!Pc) return set_err(LPP_ERR_INVALID, "NULL record");
+    lpp_postsolve *P = const_cast<lpp_postsolve *>(Pc);
+    const lpp_status st = guarded([&]() -> lpp_status { materialize(P); return LPP_OK; });
+    if (st != LPP_OK) return st;
+    const size_t n = P->col_kind.size();
+    if (leader && n) std::memcpy(leader, P->col_aux.data(), 4 * n);
+    if (pass && n) std::memcpy(pass, P->col_pass.data(), 4 * n);
+    if (bounds && n) std::memcpy(bounds, P->col_mrg.data(), 32 * n);
+    return LPP_OK;
+}
+
 lpp_status lpp_result_activity(const lpp_postsolve *Pc, double *act_min, double *act_max, int32_t *ninf_min,
                                int32_t *ninf_max) {
     if (!Pc) return set_err(LPP_ERR_INVALID, "NULL record");
@@ -649,6 +680,28 @@ lpp_status lpp_postsolve_primal(const lpp_postsolve *Pc, const double *x_red, do
         const int32_t j = P->col_map[k];
         if (j < 0 || (size_t)j >= n) return set_err(LPP_ERR_INVALID, "corrupt column map");
         x_orig[j] = x_red[k];
+    }
+    // merges, latest (round, pass) first: y = x_k + lam x_j sits in x_orig[k]
+    std::vector<int32_t> ord;
+    for (size_t j = 0; j < n; j++)
+        if (P->col_kind[j] == LPP_COL_PARALLEL) ord.push_back((int32_t)j);
+    std::stable_sort(ord.begin(), ord.end(), [P](int32_t a, int32_t b) {
+        if (P->col_round[a] != P->col_round[b]) return P->col_round[a] > P->col_round[b];
+        return P->col_pass[a] > P->col_pass[b];
+    });
+    for (const int32_t j : ord) {
+        const int32_t k = P->col_aux[j];
+        if (k < 0 || (size_t)k >= n) return set_err(LPP_ERR_INVALID, "corrupt merge record");
+        const double lam = P->col_val[j], y = x_orig[k];
+        const double *b = &P->col_mrg[4 * (size_t)j];  // l_k, u_k, l_j, u_j
+        // the x_j that keep y - lam x_j inside [l_k, u_k], within [l_j, u_j]
+        double lo = lam > 0.0 ? (y - b[1]) / lam : (y - b[0]) / lam;
+        double hi = lam > 0.0 ? (y - b[0]) / lam : (y - b[1]) / lam;
+        if (b[2] > lo) lo = b[2];
+        if (b[3] < hi) hi = b[3];
+        const double xj = std::isfinite(lo) ? lo : (std::isfinite(hi) ? hi : 0.0);
+        x_orig[j] = xj;
+        x_orig[k] = y - lam * xj;
     }
     return LPP_OK;
 }

@@ -40,8 +40,8 @@ __host__ __device__ __forceinline__ int seg_class(int len) {
 
 // row record kinds (values of lpp.h)
 enum : uint8_t { RK_KEPT = 0, RK_EMPTY = 1, RK_REDUNDANT = 2, RK_SINGLETON = 3, RK_PARALLEL = 4 };
-// column kinds
-enum : uint8_t { CK_KEPT = 0, CK_FIXED = 1, CK_EMPTY = 2 };
+// column kinds (CK_PARALLEL: merged into a parallel leader column, S5c)
+enum : uint8_t { CK_KEPT = 0, CK_FIXED = 1, CK_EMPTY = 2, CK_PARALLEL = 3 };
 // verdict slots per LP, in step order
 enum { V_S2_ROW = 0, V_S3_COL = 1, V_S5_ROW = 2, V_S6_COL = 3, V_SLOTS = 4 };
 
@@ -113,6 +113,13 @@ struct Ctx {
     unsigned long long *tkey, *tlead;
     int32_t tcap;
     int32_t *s5_out, *s5_out_cnt;   // rows the first pass leaves unmatched (list, count)
+    // S5c (parallel columns, opt-in): key hash and slot per column, the
+    // column table (key, leader, first parallel follower) of capacity ctcap
+    unsigned long long *hcol;
+    int32_t *cslot;
+    unsigned long long *ctkey, *ctlead;
+    int32_t *ctfol;
+    int32_t ctcap;
     // long segments
     double2 *ch_act;
     int2 *ch_ninf;
@@ -123,6 +130,8 @@ struct Ctx {
     double *rec_rv;
     int32_t *rec_ck, *rec_cr;
     double *rec_cv;
+    int32_t *rec_ca, *rec_cp;       // S5c merges: leader (original index), pass
+    double *rec_cm;                 // [4 per column] l_k, u_k, l_j, u_j at the merge
     // per LP
     const int32_t *lp_round0;       // arena round in which each LP joined (NULL: all in round 1)
     int32_t *verdict;               // [nlp][V_SLOTS] smallest original index
@@ -206,6 +215,17 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
     z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
     return z ^ (z >> 31);
+}
+
+// Key hashes of S5 and S5c: a segment's key hash is the wrapping sum of one
+// mixed value per entry (its index and whether its sign differs from the
+// first entry's) plus one for the length, so any split of the segment into
+// parts sums to the same hash.
+__device__ __forceinline__ unsigned long long entry_hash(int32_t j, bool flip) {
+    return mix64(((unsigned long long)(uint32_t)j << 1) | (unsigned long long)flip);
+}
+__device__ __forceinline__ unsigned long long len_hash(int32_t len) {
+    return mix64(0xa0761d6478bd642fULL ^ (unsigned long long)(uint32_t)len);
 }
 
 // ------------------------------------------------------------- lane groups

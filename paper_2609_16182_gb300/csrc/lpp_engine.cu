@@ -155,7 +155,7 @@ __global__ void k_sizes(const CompactCtx K, int32_t m, int32_t n, DevStatus *st)
 }
 
 const char *kFamNames[F_NUM] = {"prop",     "colfin",   "s5",     "compact_count", "scan", "compact_scatter",
-                                "schedule", "ingest",   "finish"};
+                                "schedule", "ingest",   "finish", "s5c"};
 
 }  // namespace
 
@@ -325,6 +325,20 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
     rec_ck = pool.alloc<int32_t>(n0);
     rec_cr = pool.alloc<int32_t>(n0);
     rec_cv = pool.alloc<double>(n0);
+    if (o.parallel_cols) {
+        hcol = pool.alloc<unsigned long long>(n0);
+        cslot = pool.alloc<int32_t>(n0);
+        ctcap_max = pow2_at_least(2 * (int64_t)std::max(n0, 1));
+        ctkey = pool.alloc<unsigned long long>(ctcap_max);
+        ctlead = pool.alloc<unsigned long long>(ctcap_max);
+        ctfol = pool.alloc<int32_t>(ctcap_max);
+        pc_list[0] = pool.alloc<int32_t>(n0);
+        pc_list[1] = pool.alloc<int32_t>(n0);
+        pc_cnt = pool.alloc<int32_t>((size_t)o.par_max_iter + 2);
+        rec_ca = pool.alloc<int32_t>(n0);
+        rec_cp = pool.alloc<int32_t>(n0);
+        rec_cm = pool.alloc<double>(4 * (int64_t)n0);
+    }
     st = pool.alloc<DevStatus>(1);
     LPP_CUDA(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
 }
@@ -485,6 +499,15 @@ void Engine::prepare() {
     LPP_CUDA(cudaMemsetAsync(rec_ck, 0, sizeof(int32_t) * (size_t)std::max(n0, 1), s));
     LPP_CUDA(cudaMemsetAsync(rec_cr, 0, sizeof(int32_t) * (size_t)std::max(n0, 1), s));
     LPP_CUDA(cudaMemsetAsync(rec_cv, 0, sizeof(double) * (size_t)std::max(n0, 1), s));
+    if (o.parallel_cols) {
+        // an empty column table: no key, no leader, no follower
+        LPP_CUDA(cudaMemsetAsync(ctkey, 0, sizeof(unsigned long long) * (size_t)ctcap_max, s));
+        LPP_CUDA(cudaMemsetAsync(ctlead, 0xff, sizeof(unsigned long long) * (size_t)ctcap_max, s));
+        fill_i32(ctfol, ctcap_max, kNone, s);
+        fill_i32(rec_ca, n0, -1, s);
+        LPP_CUDA(cudaMemsetAsync(rec_cp, 0, sizeof(int32_t) * (size_t)std::max(n0, 1), s));
+        fill_u64(reinterpret_cast<unsigned long long *>(rec_cm), 4 * (int64_t)n0, 0x7ff8000000000000ULL, s);  // NaN
+    }
     std::vector<double> offs(nlp);
     for (int32_t k = 0; k < nlp; k++) offs[k] = mem[k].obj_offset;
     LPP_CUDA(cudaMemcpyAsync(K.offset, offs.data(), sizeof(double) * nlp, cudaMemcpyHostToDevice, s));
@@ -590,6 +613,15 @@ Ctx Engine::ctx(int32_t round) const {
     C.rec_ck = rec_ck;
     C.rec_cr = rec_cr;
     C.rec_cv = rec_cv;
+    C.rec_ca = rec_ca;
+    C.rec_cp = rec_cp;
+    C.rec_cm = rec_cm;
+    C.hcol = hcol;
+    C.cslot = cslot;
+    C.ctkey = ctkey;
+    C.ctlead = ctlead;
+    C.ctfol = ctfol;
+    C.ctcap = 2;
     C.lp_round0 = lp_round0_dev;
     C.verdict = verdict;
     C.lp_changed = lp_changed;
@@ -737,6 +769,11 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     if (st_h->err) throw StatusError(LPP_ERR_CUDA, "internal: S5 hash table overflow");
     if (run_s5) launch_s5_leader(C, s);
     LPP_CUDA(cudaGetLastError());
+    // S5c (opt-in) on the round-start columns.  Skipped while the last S5c
+    // resolved every key and no row has been removed since: only a removed
+    // row can make two columns parallel, and merges keep the leader's entries
+    // and cost.
+    if (o.parallel_cols && (first_round || !s5c_clean)) s5c_clean = run_s5c(C);
     bool newly_dead = false;
     for (int32_t k = 0; k < nlp; k++) {
         if (lp_dropped[k]) continue;
@@ -749,7 +786,8 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     LPP_CUDA(cudaEventRecord(ev_round[1], s));
     read_status();
     if (st_h->err) throw StatusError(LPP_ERR_CUDA, "internal: S5 hash table overflow");
-    if (st_h->cols_fixed > 0) s5_clean = false;  // rows lost entries (S4 or S6 fixings)
+    if (st_h->cols_fixed > 0) s5_clean = false;  // rows lost entries (S4 or S6 fixings, S5c merges)
+    if (rows_removed > 0) s5c_clean = false;
     if (out.structural) {
         const int32_t m_new = st_h->m_new, n_new = st_h->n_new, nnz_new = st_h->nnz_new;
         if (nnz_new != st_h->nnz_new_t || m_new < 0 || m_new > m || n_new < 0 || n_new > n || nnz_new > nnz)
@@ -768,9 +806,51 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     return out;
 }
 
+// S5c leader passes: the first over every unfixed column, later ones over
+// the columns still in play (chunks of 2, 4, 8, ... passes between reads of
+// the list size).  Refreshes st_h, whose column count then includes the
+// merges.  Returns true once every key is resolved within par_max_iter passes.
+bool Engine::run_s5c(const Ctx &C0) {
+    Ctx C = C0;
+    tbegin(F_S5C, 0.0);
+    LPP_CUDA(cudaMemsetAsync(pc_cnt, 0, sizeof(int32_t) * (size_t)(o.par_max_iter + 2), s));
+    C.ctcap = std::min(ctcap_max, pow2_at_least(2 * (int64_t)std::max(n, 1)));
+    launch_s5c_keys(C, pc_list[0], pc_cnt, s);
+    launch_s5c_pass(C, pc_list[0], pc_cnt, 0, pc_list[1], pc_cnt + 1, n, false, s);
+    LPP_CUDA(cudaGetLastError());
+    LPP_CUDA(cudaMemcpyAsync(s5_left_h, pc_cnt + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LPP_CUDA(cudaStreamSynchronize(s));
+    const int32_t n1 = *s5_left_h;
+    bool resolved = n1 == 0;
+    if (n1 > 0 && o.par_max_iter > 1) {
+        C.ctcap = std::min(ctcap_max, pow2_at_least(2 * (int64_t)n1));
+        int32_t chunk = 2;
+        for (int32_t pass = 1; pass < o.par_max_iter;) {
+            const int32_t end = std::min<int32_t>(pass + chunk, o.par_max_iter);
+            for (int32_t q = pass; q < end; q++)
+                launch_s5c_pass(C, pc_list[q & 1], pc_cnt + q, q, pc_list[(q + 1) & 1], pc_cnt + q + 1, n1, true, s);
+            LPP_CUDA(cudaGetLastError());
+            LPP_CUDA(cudaMemcpyAsync(s5_left_h, pc_cnt + end, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            LPP_CUDA(cudaStreamSynchronize(s));
+            if (*s5_left_h == 0) {
+                resolved = true;
+                break;
+            }
+            pass = end;
+            chunk *= 2;
+        }
+    }
+    tend();
+    LPP_CUDA(cudaMemcpyAsync(st_h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    LPP_CUDA(cudaStreamSynchronize(s));
+    if (st_h->err) throw StatusError(LPP_ERR_CUDA, "internal: S5c hash table overflow");
+    return resolved;
+}
+
 void Engine::run() {
     const int32_t R = std::max(0, o.max_rounds);
     s5_clean = false;
+    s5c_clean = false;
     lp_rounds.assign(nlp, 0);
     lp_status.assign(nlp, LPP_OK);
     lp_where.assign(nlp, LPP_WHERE_NONE);

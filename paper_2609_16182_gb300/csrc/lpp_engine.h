@@ -87,6 +87,12 @@ struct Engine {
     unsigned long long *mL, *mU, *cand_l, *cand_u, *tkey, *tlead, *ch_hash;
     int32_t *s5_list[2] = {nullptr, nullptr}, *s5_cnt = nullptr;
     bool s5_clean = false;  // the last S5 resolved every group and no row changed since
+    // S5c (opts.parallel_cols): column keys and slots, the column table, the
+    // lists of columns per pass and their sizes
+    unsigned long long *hcol = nullptr, *ctkey = nullptr, *ctlead = nullptr;
+    int32_t *cslot = nullptr, *ctfol = nullptr, *pc_list[2] = {nullptr, nullptr}, *pc_cnt = nullptr;
+    int32_t ctcap_max = 0;
+    bool s5c_clean = false;  // the last S5c resolved every key and its round removed no row
     cudaStream_t s2 = nullptr;                   // host inputs: the vectors' copies
     cudaEvent_t ev_mat = nullptr, ev_vec = nullptr;
     bool vec_pending = false;                    // their check waits for the copies (prepare)
@@ -103,6 +109,8 @@ struct Engine {
     // records
     int32_t *rec_rk, *rec_rr, *rec_ra, *rec_ck, *rec_cr;
     double *rec_rv, *rec_cv;
+    int32_t *rec_ca = nullptr, *rec_cp = nullptr;  // S5c merges (NULL unless opts.parallel_cols)
+    double *rec_cm = nullptr;
     DevStatus *st;
     DevStatus *st_h = nullptr;  // pinned mirror
     int32_t *verdict_h = nullptr;
@@ -158,13 +166,14 @@ struct Engine {
     void schedule_current();
     void adopt_schedule();
     void compact(int32_t round);
+    bool run_s5c(const Ctx &C0);  // S5c leader passes; true once every key is resolved
     // timing helpers
     void tbegin(int fam, double bytes);
     void tend();
 };
 
 // Kernel families reported by lpp_result_kernels.
-enum Fam { F_PROP = 0, F_COLFIN, F_S5, F_COUNT, F_SCAN, F_SCATTER, F_SCHED, F_INGEST, F_FINISH, F_NUM };
+enum Fam { F_PROP = 0, F_COLFIN, F_S5, F_COUNT, F_SCAN, F_SCATTER, F_SCHED, F_INGEST, F_FINISH, F_S5C, F_NUM };
 const char *fam_name(int f);
 
 // device allocations shared by the reduced LPs of one batch, freed with the last
@@ -211,6 +220,8 @@ struct DeviceRecords {
     int32_t m0 = 0, n0 = 0, n_final = 0, act_m = 0;
     int32_t *rk = nullptr, *rr = nullptr, *ra = nullptr, *ck = nullptr, *cr = nullptr;
     double *rv = nullptr, *cv = nullptr;
+    int32_t *ca = nullptr, *cp = nullptr;  // S5c merges: leader, pass (NULL without parallel_cols)
+    double *cm = nullptr;                  // [4 per column] bounds at the merge
     double2 *lu = nullptr;       // [n_final] final bounds of the kept columns (arena order)
     int32_t *cmap = nullptr;     // [n_final] their original (arena) index
     double2 *act = nullptr;      // [act_m] last round's activities (that round's numbering)
@@ -230,8 +241,8 @@ struct lpp_postsolve {
     int32_t cstart = 0;              // first kept column of this LP in the final arena
     int32_t astart = 0, acnt = 0;    // this LP's rows in the last round's numbering
     bool host_ready = false;
-    std::vector<int32_t> row_kind, row_round, row_aux, col_kind, col_round, col_map;
-    std::vector<double> row_val, col_val, col_lb, col_ub, act_min, act_max;
+    std::vector<int32_t> row_kind, row_round, row_aux, col_kind, col_round, col_map, col_aux, col_pass;
+    std::vector<double> row_val, col_val, col_lb, col_ub, act_min, act_max, col_mrg;
     std::vector<int32_t> ninf_min, ninf_max;
     std::vector<int64_t> r_nnz;
     std::vector<int32_t> r_rows, r_cols, r_bounds;

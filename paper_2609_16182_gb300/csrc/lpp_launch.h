@@ -74,6 +74,15 @@ void launch_s5_tail(const Ctx &C, const int32_t *list, const int32_t *cnt, int32
                     int32_t max_rows, cudaStream_t s);
 void launch_s5_leader(const Ctx &C, cudaStream_t s);
 
+// --------------------------------------------------------------- k_parcols.cu
+// S5c first pass: key hash of every column S4 left unfixed, inserted into the
+// column table (C.ctcap slots); participants are appended to list / *cnt
+void launch_s5c_keys(const Ctx &C, int32_t *list, int32_t *cnt, cudaStream_t s);
+// one S5c pass over list[0 .. *cnt), *cnt <= max_cols (insert: put the listed
+// columns into the empty table first); columns that stay go to out
+void launch_s5c_pass(const Ctx &C, const int32_t *list, const int32_t *cnt, int32_t pass, int32_t *out,
+                     int32_t *out_cnt, int32_t max_cols, bool insert, cudaStream_t s);
+
 // -------------------------------------------------------------- k_compact.cu
 void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s);
 void launch_compact_scatter(const Ctx &C, const CompactCtx &K, int32_t nnz, cudaStream_t s);

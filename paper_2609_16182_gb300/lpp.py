@@ -18,7 +18,7 @@ from . import _build
 OK, INFEASIBLE, UNBOUNDED = 0, 1, 2
 ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUDGET = -1, -2, -3, -4, -5
 ROW_KEPT, ROW_EMPTY, ROW_REDUNDANT, ROW_SINGLETON, ROW_PARALLEL = 0, 1, 2, 3, 4
-COL_KEPT, COL_FIXED, COL_EMPTY = 0, 1, 2
+COL_KEPT, COL_FIXED, COL_EMPTY, COL_PARALLEL = 0, 1, 2, 3
 WHERE_NONE, WHERE_ROW, WHERE_COL = 0, 1, 2
 
 
@@ -38,8 +38,8 @@ class LpStruct(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("feas_tol", C.c_double), ("bound_tol", C.c_double), ("huge", C.c_double),
                 ("max_implied", C.c_double), ("par_tol", C.c_double), ("max_rounds", C.c_int32),
-                ("dual_reductions", C.c_int32), ("par_max_iter", C.c_int32), ("timing", C.c_int32),
-                ("device", C.c_int32), ("stream", C.c_void_p)]
+                ("dual_reductions", C.c_int32), ("par_max_iter", C.c_int32), ("parallel_cols", C.c_int32),
+                ("timing", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p)]
 
 
 class Info(C.Structure):
@@ -63,7 +63,7 @@ class ServerStats(C.Structure):
 # every symbol include/lpp.h declares
 SYMBOLS = ["lpp_opts_default", "lpp_presolve", "lpp_reduced_view", "lpp_reduced_csc", "lpp_reduced_maps",
            "lpp_result_info", "lpp_result_rows", "lpp_result_cols", "lpp_result_activity", "lpp_result_rounds",
-           "lpp_result_kernels", "lpp_postsolve_primal", "lpp_free_reduced", "lpp_free_postsolve",
+           "lpp_result_kernels", "lpp_result_merges", "lpp_postsolve_primal", "lpp_free_reduced", "lpp_free_postsolve",
            "lpp_last_error", "lpp_presolve_batch", "lpp_server_create", "lpp_server_submit", "lpp_server_take",
            "lpp_server_stats_get", "lpp_server_destroy", "lpp_row_activity_noalloc"]
 
@@ -99,6 +99,7 @@ def load():
     L.lpp_result_activity.argtypes = [P, P, P, P, P]
     L.lpp_result_rounds.argtypes = [P, C.c_int32, P, P, P, P, P, C.POINTER(C.c_int32)]
     L.lpp_result_kernels.argtypes = [P, C.c_int32, C.POINTER(KernelStat), C.POINTER(C.c_int32)]
+    L.lpp_result_merges.argtypes = [P, P, P, P]
     L.lpp_postsolve_primal.argtypes = [P, P, P]
     L.lpp_free_reduced.argtypes = [P]
     L.lpp_free_reduced.restype = None
@@ -225,7 +226,7 @@ class Result:
         self._records = None
 
     _RECORD_FIELDS = ("row_kind", "row_round", "row_aux", "row_val", "col_kind", "col_round", "col_val", "col_lb",
-                      "col_ub", "act_min", "act_max", "ninf_min", "ninf_max")
+                      "col_ub", "act_min", "act_max", "ninf_min", "ninf_max", "col_aux", "col_pass", "col_mrg")
     _ROUND_FIELDS = ("round_nnz", "round_rows_removed", "round_cols_fixed", "round_bounds_changed", "round_ms")
 
     def __getattr__(self, name):
@@ -270,12 +271,14 @@ class Result:
         r = dict(row_kind=np.zeros(m, np.int32), row_round=np.zeros(m, np.int32), row_aux=np.zeros(m, np.int32),
                  row_val=np.zeros(m), col_kind=np.zeros(n, np.int32), col_round=np.zeros(n, np.int32),
                  col_val=np.zeros(n), col_lb=np.zeros(n), col_ub=np.zeros(n), act_min=np.zeros(m),
-                 act_max=np.zeros(m), ninf_min=np.zeros(m, np.int32), ninf_max=np.zeros(m, np.int32))
+                 act_max=np.zeros(m), ninf_min=np.zeros(m, np.int32), ninf_max=np.zeros(m, np.int32),
+                 col_aux=np.zeros(n, np.int32), col_pass=np.zeros(n, np.int32), col_mrg=np.zeros((n, 4)))
         _check(L.lpp_result_rows(rec, _p(r["row_kind"]), _p(r["row_round"]), _p(r["row_aux"]), _p(r["row_val"])))
         _check(L.lpp_result_cols(rec, _p(r["col_kind"]), _p(r["col_round"]), _p(r["col_val"]), _p(r["col_lb"]),
                                  _p(r["col_ub"])))
         _check(L.lpp_result_activity(rec, _p(r["act_min"]), _p(r["act_max"]), _p(r["ninf_min"]),
                                      _p(r["ninf_max"])))
+        _check(L.lpp_result_merges(rec, _p(r["col_aux"]), _p(r["col_pass"]), _p(r["col_mrg"])))
         return r
 
     @property

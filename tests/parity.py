@@ -1,11 +1,12 @@
 """GPU-vs-oracle comparison (the parity bar).
 
 Bit-exact: status, verdict location and round, round count, every record
-(kind, round, leader / column, singleton coefficient, parallel factor),
+(kind, round, leader / column, singleton coefficient, parallel factor; for
+merged parallel columns the leader, pass and factor),
 row and column maps, the reduced CSR / CSC structure and its coefficients
 and costs (copies of the input), the counts of infinite activity terms.
 Within tolerance: values that come out of a floating-point sum (activities,
-implied bounds, shifted sides, the objective constant):
+implied bounds, shifted sides, the objective constant, bounds at a merge):
 |gpu - oracle| <= tol * max(1, |oracle|, S), S the absolute scale of the
 sum that produced the value (for activities the oracle reports it).
 """
@@ -56,6 +57,12 @@ def compare(gpu, orc, lp, check_records=True, arena_stats=False):
         np.testing.assert_array_equal(gpu.row_aux, orc.row_aux, err_msg="row aux")
         np.testing.assert_array_equal(gpu.row_val, orc.row_val, err_msg="row values (singleton a, parallel lambda)")
         np.testing.assert_array_equal(gpu.col_round, orc.col_round, err_msg="column rounds")
+        # parallel-column merges: leader everywhere; pass and bounds of merged columns
+        np.testing.assert_array_equal(gpu.col_aux, orc.col_aux, err_msg="merge leaders")
+        merged = orc.col_kind == 3
+        np.testing.assert_array_equal(gpu.col_pass[merged], orc.col_pass[merged], err_msg="merge passes")
+        np.testing.assert_array_equal(gpu.col_val[merged], orc.col_val[merged], err_msg="merge lambda")
+        _close(gpu.col_mrg[merged], orc.col_mrg[merged], what="bounds at the merge")
     fixed = orc.col_kind != 0
     _close(gpu.col_val[fixed], orc.col_val[fixed], what="fixed values")
     _close(gpu.col_lb, orc.col_lb, what="final lower bounds")
