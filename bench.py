@@ -177,6 +177,41 @@ def batched_leg(lpp, synth, torch, dev, stream, count=4096):
                         "200-row LP scaled by m/200; device inputs; one batched call vs 4096 plain calls"}
 
 
+def parcols_leg(lpp, synth, torch, dev, stream, lp, steps=10):
+    """The benchmark LP with 1% of its columns copied and scaled (planted
+    parallel columns), presolved with the parallel-column step on and off:
+    throughput of each, the step's own time and the merges it made."""
+    q = synth.plant_parallel_cols(lp, 0, frac=0.01)
+    d = synth.LP(m=q.m, n=q.n, **{k: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
+                                  for k, v in q.arrays().items()})
+    out = {"workload": f"benchmark LP + {len(q.planted['par_copies'])} scaled column copies "
+                       f"(n = {q.n}, nnz = {q.nnz})"}
+    for on in (1, 0):
+        o = lpp.opts(stream=stream.cuda_stream, parallel_cols=on)
+        for _ in range(2):
+            lpp.presolve(d, o).close()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        proc = 0
+        e0.record(stream)
+        for _ in range(steps):
+            r = lpp.presolve(d, o)
+            proc += int(r.info.nnz_processed)
+            r.close()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        out["on" if on else "off"] = {"ms_per_step": ms, "nnz_per_s": proc / steps / (ms / 1e3)}
+    # outside the timed steps: the merges (host copies of the records) and the
+    # step's own time (events around its launches)
+    rt = lpp.presolve(d, lpp.opts(stream=stream.cuda_stream, parallel_cols=1, timing=1))
+    k = rt.kernels.get("s5c", {"ms": 0.0, "launches": 0})
+    out.update(merged=int(np.count_nonzero(rt.col_kind == lpp.COL_PARALLEL)), rounds=rt.rounds,
+               s5c_ms=k["ms"], s5c_rounds=k["launches"])
+    rt.close()
+    return out
+
+
 def serving_leg(lpp, synth, torch, dev, pool_size=24, requests=200, budget=120 << 30, seed=0):
     """Poisson arrivals of skewed-like LPs (nnz log-uniform in [1e3, 1e6],
     m = nnz/10, n = 1.5 m; requests draw from a pool of `pool_size` distinct
@@ -299,6 +334,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-presolve leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-parcols", action="store_true", help="skip the parallel-columns leg")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the LP (profiling runs only)")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: W + K steps only (no timing pass, e2e or CPU baseline)")
@@ -428,6 +464,9 @@ def main():
     serving = None
     if not args.no_serve:
         serving = serving_leg(lpp, synth, torch, dev)
+    parcols = None
+    if not args.no_parcols:
+        parcols = parcols_leg(lpp, synth, torch, dev, stream, lp)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": ws, "steps": args.steps,
@@ -445,7 +484,7 @@ def main():
                            "l2": "inputs larger than L2 (CSR alone ~245 MB > 129 MB)",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
-                "batched": batched, "serving": serving}
+                "batched": batched, "serving": serving, "parallel_cols": parcols}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

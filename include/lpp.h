@@ -179,12 +179,13 @@ lpp_status lpp_result_cols(const lpp_postsolve *rec, int32_t *kind, int32_t *rou
 /* Parallel-column merges (Sec. 3.2, parallel columns; opts.parallel_cols).
  * A column j of kind LPP_COL_PARALLEL was merged into its leader k when
  * A_:j = lambda A_:k and c_j = lambda c_k (lambda is its value in
- * lpp_result_cols): x_k + lambda x_j became one column y in place of x_k.
- * Per original column (host arrays of n, any pointer may be NULL): leader[j]
- * = k (original index, -1 if j was not merged), pass[j] = the leader pass of
- * its round (0-based; merges are undone latest (round, pass) first), and
- * bounds[4j .. 4j+3] = l_k, u_k, l_j, u_j at the time of the merge (NaN if
- * j was not merged). */
+ * lpp_result_cols): y + lambda x_j replaced the leader's column y (x_k, or
+ * x_k with the columns merged before j).  In a pass a leader takes all its
+ * parallel columns, in increasing column order.  Per original column (host
+ * arrays of n, any pointer may be NULL): leader[j] = k (original index, -1
+ * if j was not merged), pass[j] = the leader pass of its round (0-based), and
+ * bounds[4j .. 4j+3] = l_y, u_y, l_j, u_j just before the merge (NaN if j
+ * was not merged).  Merges are undone latest (round, pass, column) first. */
 lpp_status lpp_result_merges(const lpp_postsolve *rec, int32_t *leader, int32_t *pass, double *bounds);
 /* Activities of the last executed round per original row (host arrays of m);
  * rows not present at that round's start get NaN and -1. */
@@ -200,10 +201,10 @@ lpp_status lpp_result_kernels(const lpp_postsolve *rec, int32_t cap, lpp_kernel_
 
 /* Primal postsolve on the CPU (Sec. 2.1 postsolver; Sec. 3.3): x_red[n_red]
  * -> x_orig[n] (host arrays): kept columns take their reduced value, fixed
- * columns their recorded value.  Merges are split latest first: with
- * y = x_k + lambda x_j at hand, x_j is the lowest value of [l_j, u_j] that
- * leaves y - lambda x_j inside [l_k, u_k] (the highest if that range has no
- * finite low end, 0 if it has neither), and x_k = y - lambda x_j. */
+ * columns their recorded value.  Merges are split latest first: with the
+ * merged value v = y + lambda x_j at hand, x_j is the lowest value of
+ * [l_j, u_j] that leaves v - lambda x_j inside [l_y, u_y] (the highest if that
+ * range has no finite low end, 0 if it has neither), and y = v - lambda x_j. */
 lpp_status lpp_postsolve_primal(const lpp_postsolve *rec, const double *x_red, double *x_orig);
 
 void lpp_free_reduced(lpp_reduced *red);

@@ -142,7 +142,7 @@ class Result:
     col_val: np.ndarray
     col_aux: np.ndarray    # parallel-column merges: leader (original index)
     col_pass: np.ndarray   # the pass of the merge within its round
-    col_mrg: np.ndarray    # [n, 4]: lk, uk, lj, uj just before the merge
+    col_mrg: np.ndarray    # [n, 4]: the leader's bounds and the column's just before the merge
     col_lb: np.ndarray
     col_ub: np.ndarray
     act_min: np.ndarray

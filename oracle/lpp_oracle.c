@@ -611,16 +611,17 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                On the columns of the round-start matrix (the rows S2 and S5
                removed this round included: columns parallel on every row are
                parallel on the kept ones), not fixed in S4.  Columns with
-               equal keys form a group; in each pass the group's leader (its
-               first column) takes the first other column j parallel to it:
-               A_:j = lam A_:k and c_j = lam c_k, lam = a_j,first / a_k,first,
-               each entry and the cost within par_tol as in S5.  Then
-               y = x_k + lam x_j replaces x_k, with bounds
-                 lam > 0: [l_k + lam l_j, u_k + lam u_j],
-                 lam < 0: [l_k + lam u_j, u_k + lam l_j],
+               equal keys form a group, in column order.  Each pass, as in S5,
+               the group's first live column k leads and leaves the group, and
+               every live column j parallel to it (A_:j = lam A_:k and
+               c_j = lam c_k, lam = a_j,first / a_k,first, each entry and the
+               cost within par_tol) merges into it, one after the other in
+               column order: y = x_k + lam x_j replaces x_k, with bounds
+                 lam > 0: [l_y + lam l_j, u_y + lam u_j],
+                 lam < 0: [l_y + lam u_j, u_y + lam l_j],
                and column j leaves the LP (its entries without a side shift,
-               its cost without an objective constant).  A leader with no
-               parallel column leaves the group.  At most par_max_iter passes. */
+               its cost without an objective constant).  At most par_max_iter
+               passes, while two or more columns live. */
         if (o->parallel_cols) {
             int32_t nk = 0;
             int64_t qo = 0;
@@ -648,7 +649,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                 int32_t g0, g1;
                 for (g0 = 0; g0 < nk; g0 = g1) {
                     ckey_t probe = ckeys[g0];
-                    int32_t gsz, it, t;
+                    int32_t gsz, it, t, live;
                     for (g1 = g0 + 1; g1 < nk; g1++) {
                         probe.col = ckeys[g1].col; /* compare keys only */
                         if (cmp_ckey(&probe, &ckeys[g1]) != 0) break;
@@ -656,19 +657,23 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                     gsz = g1 - g0;
                     if (gsz < 2) continue;
                     for (t = 0; t < gsz; t++) calive[t] = 1;
-                    for (it = 0; it < o->par_max_iter; it++) {
-                        int32_t lead = -1, fol = -1, ck, cj, len, q;
-                        double lam = 0.0;
+                    live = gsz;
+                    for (it = 0; it < o->par_max_iter && live >= 2; it++) {
+                        int32_t lead = -1, ck, len, q, nm = 0;
+                        double ly, uy, ely, euy;
                         for (t = 0; t < gsz && lead < 0; t++) if (calive[t]) lead = t;
-                        if (lead < 0) break;
+                        calive[lead] = 0;
+                        live--;
                         ck = ckeys[g0 + lead].col; len = ckeys[g0 + lead].len;
-                        for (t = lead + 1; t < gsz && fol < 0; t++) {
-                            const double *ak, *aj;
+                        ly = s.l[ck]; uy = s.u[ck]; ely = s.ebl[ck]; euy = s.ebu[ck];
+                        for (t = lead + 1; t < gsz; t++) {
+                            const double *ak = tvl + tcp[ck], *aj;
+                            int32_t cj;
                             int par = 1;
-                            double lc;
+                            double lam, lc, lj, uj;
                             if (!calive[t]) continue;
                             cj = ckeys[g0 + t].col;
-                            ak = tvl + tcp[ck]; aj = tvl + tcp[cj];
+                            aj = tvl + tcp[cj];
                             lam = aj[0] / ak[0];
                             for (q = 0; q < len && par; q++) {
                                 double la = lam * ak[q];
@@ -676,30 +681,27 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                             }
                             lc = lam * s.c[ck];
                             if (par && !(fabs(s.c[cj] - lc) <= o->par_tol * dmax(fabs(s.c[cj]), fabs(lc)))) par = 0;
-                            if (par) fol = t;
-                        }
-                        if (fol < 0) { calive[lead] = 0; continue; }
-                        cj = ckeys[g0 + fol].col;
-                        calive[fol] = 0;
-                        {
-                            const double lk = s.l[ck], uk = s.u[ck], lj = s.l[cj], uj = s.u[cj];
-                            double nlk, nuk;
-                            if (lam > 0) { nlk = lk + lam * lj; nuk = uk + lam * uj; }
-                            else { nlk = lk + lam * uj; nuk = uk + lam * lj; }
+                            if (!par) continue;
+                            calive[t] = 0;
+                            live--;
+                            lj = s.l[cj]; uj = s.u[cj];
                             out->col_kind[s.cmap[cj]] = LPPO_COL_PARALLEL; out->col_round[s.cmap[cj]] = r;
                             out->col_val[s.cmap[cj]] = lam;
                             if (out->col_aux) out->col_aux[s.cmap[cj]] = s.cmap[ck];
                             if (out->col_pass) out->col_pass[s.cmap[cj]] = it;
                             if (out->col_mrg) {
-                                out->col_mrg[4 * s.cmap[cj]] = lk; out->col_mrg[4 * s.cmap[cj] + 1] = uk;
+                                out->col_mrg[4 * s.cmap[cj]] = ly; out->col_mrg[4 * s.cmap[cj] + 1] = uy;
                                 out->col_mrg[4 * s.cmap[cj] + 2] = lj; out->col_mrg[4 * s.cmap[cj] + 3] = uj;
                             }
-                            s.l[ck] = nlk; s.u[ck] = nuk;
-                            s.ebl[ck] += fabs(lam) * s.ebl[cj] + UROUND * fabs(nlk);
-                            s.ebu[ck] += fabs(lam) * s.ebu[cj] + UROUND * fabs(nuk);
+                            if (lam > 0) { ly = ly + lam * lj; uy = uy + lam * uj; }
+                            else { ly = ly + lam * uj; uy = uy + lam * lj; }
+                            ely += fabs(lam) * s.ebl[cj] + UROUND * fabs(ly);
+                            euy += fabs(lam) * s.ebu[cj] + UROUND * fabs(uy);
                             fixed[cj] = 3; fixv[cj] = 0.0;
                             nfixed++;
+                            nm++;
                         }
+                        if (nm > 0) { s.l[ck] = ly; s.u[ck] = uy; s.ebl[ck] = ely; s.ebu[ck] = euy; }
                     }
                 }
             }
@@ -855,12 +857,15 @@ int lppo_postsolve_primal(int32_t n_orig, int32_t n_red, const int32_t *col_map,
     if (!ord) return LPPO_ERR_OOM;
     nm = 0;
     for (j = 0; j < n_orig; j++) if (col_kind[j] == LPPO_COL_PARALLEL) ord[nm++] = j;
-    /* latest merge first: (round, pass) descending, a plain insertion sort */
+    /* latest merge first: (round, pass, column) descending (within a pass a
+       leader takes its columns in increasing order), a plain insertion sort */
     for (a = 1; a < nm; a++) {
         int32_t x = ord[a];
         for (b = a - 1; b >= 0; b--) {
             int32_t y = ord[b];
-            int later = col_round[x] > col_round[y] || (col_round[x] == col_round[y] && col_pass[x] > col_pass[y]);
+            int later = col_round[x] > col_round[y] ||
+                        (col_round[x] == col_round[y] && (col_pass[x] > col_pass[y] ||
+                                                          (col_pass[x] == col_pass[y] && x > y)));
             if (!later) break;
             ord[b + 1] = y;
         }

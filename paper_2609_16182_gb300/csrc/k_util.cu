@@ -635,6 +635,29 @@ void transpose(const int32_t *ptr, const int32_t *idx, const double *val, const 
     (k_colptr_from_keys<<<blocks_for(nnz, 256), 256, 0, s>>>(kin, nnz, n, tptr), note_launch());
 }
 
+void sort_pairs(const uint32_t *keys, const int32_t *vals, int64_t cnt, int bits, const TransposeBufs &b,
+                const uint32_t **kout, const int32_t **vout, cudaStream_t s) {
+    const uint32_t *kin = keys;
+    const int32_t *vin = vals;
+    if (cnt > 0) {
+        const int passes = bits > 8 ? (bits + 7) / 8 : 1;
+        const int32_t ntiles = (int32_t)((cnt + kRadixTile - 1) / kRadixTile);
+        uint32_t *kbuf[2] = {b.k0, b.k1};
+        int32_t *vbuf[2] = {b.v0, b.v1};
+        for (int p = 0; p < passes; p++) {
+            (k_radix_hist<<<ntiles, kScanThreads, 0, s>>>(kin, cnt, 8 * p, b.hist, ntiles), note_launch());
+            scan_excl(b.hist, b.hist, (int64_t)256 * ntiles, b.tmp, s);
+            RadixOut o{kbuf[p & 1], vbuf[p & 1]};
+            (k_radix_scatter<<<ntiles, kScanThreads, 0, s>>>(kin, vin, false, cnt, 8 * p, b.hist, ntiles, o),
+             note_launch());
+            kin = kbuf[p & 1];
+            vin = vbuf[p & 1];
+        }
+    }
+    *kout = kin;
+    *vout = vin;
+}
+
 void iota(int32_t *a, int32_t cnt, int32_t base, cudaStream_t s) {
     if (cnt > 0) (k_iota<<<blocks_for(cnt, 256), 256, 0, s>>>(a, cnt, base), note_launch());
 }

@@ -681,13 +681,15 @@ lpp_status lpp_postsolve_primal(const lpp_postsolve *Pc, const double *x_red, do
         if (j < 0 || (size_t)j >= n) return set_err(LPP_ERR_INVALID, "corrupt column map");
         x_orig[j] = x_red[k];
     }
-    // merges, latest (round, pass) first: y = x_k + lam x_j sits in x_orig[k]
+    // merges, latest (round, pass, column) first -- within a pass a leader
+    // takes its columns in increasing order: y = x_k + lam x_j sits in x_orig[k]
     std::vector<int32_t> ord;
     for (size_t j = 0; j < n; j++)
         if (P->col_kind[j] == LPP_COL_PARALLEL) ord.push_back((int32_t)j);
-    std::stable_sort(ord.begin(), ord.end(), [P](int32_t a, int32_t b) {
+    std::sort(ord.begin(), ord.end(), [P](int32_t a, int32_t b) {
         if (P->col_round[a] != P->col_round[b]) return P->col_round[a] > P->col_round[b];
-        return P->col_pass[a] > P->col_pass[b];
+        if (P->col_pass[a] != P->col_pass[b]) return P->col_pass[a] > P->col_pass[b];
+        return a > b;
     });
     for (const int32_t j : ord) {
         const int32_t k = P->col_aux[j];

@@ -113,13 +113,16 @@ struct Ctx {
     unsigned long long *tkey, *tlead;
     int32_t tcap;
     int32_t *s5_out, *s5_out_cnt;   // rows the first pass leaves unmatched (list, count)
-    // S5c (parallel columns, opt-in): key hash and slot per column, the
-    // column table (key, leader, first parallel follower) of capacity ctcap
-    unsigned long long *hcol;
+    // S5c (parallel columns, opt-in): slot per column in the column table
+    // (key, columns per key, a member changed) of capacity ctcap; per
+    // original column its key, its group's size and its length after its
+    // last S5c
     int32_t *cslot;
-    unsigned long long *ctkey, *ctlead;
-    int32_t *ctfol;
+    unsigned long long *ctkey;
+    int32_t *ctcnt, *ctnew;
     int32_t ctcap;
+    unsigned long long *pkey;
+    int32_t *pcnt, *plen;
     // long segments
     double2 *ch_act;
     int2 *ch_ninf;

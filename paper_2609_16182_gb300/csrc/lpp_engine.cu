@@ -326,15 +326,29 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
     rec_cr = pool.alloc<int32_t>(n0);
     rec_cv = pool.alloc<double>(n0);
     if (o.parallel_cols) {
-        hcol = pool.alloc<unsigned long long>(n0);
         cslot = pool.alloc<int32_t>(n0);
         ctcap_max = pow2_at_least(2 * (int64_t)std::max(n0, 1));
         ctkey = pool.alloc<unsigned long long>(ctcap_max);
-        ctlead = pool.alloc<unsigned long long>(ctcap_max);
-        ctfol = pool.alloc<int32_t>(ctcap_max);
-        pc_list[0] = pool.alloc<int32_t>(n0);
-        pc_list[1] = pool.alloc<int32_t>(n0);
-        pc_cnt = pool.alloc<int32_t>((size_t)o.par_max_iter + 2);
+        ctcnt = pool.alloc<int32_t>(ctcap_max);
+        ctnew = pool.alloc<int32_t>(ctcap_max);
+        pkey = pool.alloc<unsigned long long>(n0);
+        pcnt = pool.alloc<int32_t>(n0);
+        plen = pool.alloc<int32_t>(n0);
+        pc_cnt = pool.alloc<int32_t>(4);
+        pc_mem = pool.alloc<unsigned char>(s5c_mem_bytes() * (size_t)std::max(n0, 1));
+        pc_flags = pool.alloc<int32_t>(n0 + 1);
+        pc_pos = pool.alloc<int32_t>(n0 + 1);
+        pc_slot = pool.alloc<uint32_t>(n0);
+        pc_col = pool.alloc<int32_t>(n0);
+        pc_sort.k0 = pool.alloc<uint32_t>(n0);
+        pc_sort.k1 = pool.alloc<uint32_t>(n0);
+        pc_sort.v0 = pool.alloc<int32_t>(n0);
+        pc_sort.v1 = pool.alloc<int32_t>(n0);
+        pc_sort.hist = pool.alloc<int32_t>(transpose_hist_elems(n0));
+        pc_scan = pool.alloc<int32_t>(scan_tmp_elems(std::max<int64_t>(n0 + 1, transpose_hist_elems(n0))));
+        pc_sort.tmp = pc_scan;
+        pc_alive = pool.alloc<uint8_t>(n0);
+        pc_glist = pool.alloc<int2>(n0 / 2 + 1);  // groups on blocks: two columns or more each
         rec_ca = pool.alloc<int32_t>(n0);
         rec_cp = pool.alloc<int32_t>(n0);
         rec_cm = pool.alloc<double>(4 * (int64_t)n0);
@@ -500,10 +514,14 @@ void Engine::prepare() {
     LPP_CUDA(cudaMemsetAsync(rec_cr, 0, sizeof(int32_t) * (size_t)std::max(n0, 1), s));
     LPP_CUDA(cudaMemsetAsync(rec_cv, 0, sizeof(double) * (size_t)std::max(n0, 1), s));
     if (o.parallel_cols) {
-        // an empty column table: no key, no leader, no follower
+        // an empty column table: no key, no column
         LPP_CUDA(cudaMemsetAsync(ctkey, 0, sizeof(unsigned long long) * (size_t)ctcap_max, s));
-        LPP_CUDA(cudaMemsetAsync(ctlead, 0xff, sizeof(unsigned long long) * (size_t)ctcap_max, s));
-        fill_i32(ctfol, ctcap_max, kNone, s);
+        LPP_CUDA(cudaMemsetAsync(ctcnt, 0, sizeof(int32_t) * (size_t)ctcap_max, s));
+        LPP_CUDA(cudaMemsetAsync(ctnew, 0, sizeof(int32_t) * (size_t)ctcap_max, s));
+        // no column has been through S5c: key 0 is never a key, size 0 never a group's
+        LPP_CUDA(cudaMemsetAsync(pkey, 0, sizeof(unsigned long long) * (size_t)std::max(n0, 1), s));
+        LPP_CUDA(cudaMemsetAsync(pcnt, 0, sizeof(int32_t) * (size_t)std::max(n0, 1), s));
+        LPP_CUDA(cudaMemsetAsync(plen, 0, sizeof(int32_t) * (size_t)std::max(n0, 1), s));  // no key stored
         fill_i32(rec_ca, n0, -1, s);
         LPP_CUDA(cudaMemsetAsync(rec_cp, 0, sizeof(int32_t) * (size_t)std::max(n0, 1), s));
         fill_u64(reinterpret_cast<unsigned long long *>(rec_cm), 4 * (int64_t)n0, 0x7ff8000000000000ULL, s);  // NaN
@@ -616,11 +634,13 @@ Ctx Engine::ctx(int32_t round) const {
     C.rec_ca = rec_ca;
     C.rec_cp = rec_cp;
     C.rec_cm = rec_cm;
-    C.hcol = hcol;
     C.cslot = cslot;
     C.ctkey = ctkey;
-    C.ctlead = ctlead;
-    C.ctfol = ctfol;
+    C.ctcnt = ctcnt;
+    C.ctnew = ctnew;
+    C.pkey = pkey;
+    C.pcnt = pcnt;
+    C.plen = plen;
     C.ctcap = 2;
     C.lp_round0 = lp_round0_dev;
     C.verdict = verdict;
@@ -769,11 +789,14 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     if (st_h->err) throw StatusError(LPP_ERR_CUDA, "internal: S5 hash table overflow");
     if (run_s5) launch_s5_leader(C, s);
     LPP_CUDA(cudaGetLastError());
-    // S5c (opt-in) on the round-start columns.  Skipped while the last S5c
-    // resolved every key and no row has been removed since: only a removed
-    // row can make two columns parallel, and merges keep the leader's entries
-    // and cost.
-    if (o.parallel_cols && (first_round || !s5c_clean)) s5c_clean = run_s5c(C);
+    // S5c (opt-in) on the round-start columns.  Skipped when no row was
+    // removed and no column fixed or merged since the last S5c and S4 fixed
+    // none this round: every group is then the one the last S5c left, with
+    // the same leaders and no parallel pair.
+    if (o.parallel_cols && (first_round || s5c_dirty || st_h->cols_fixed > 0)) {
+        run_s5c(C);
+        s5c_dirty = false;
+    }
     bool newly_dead = false;
     for (int32_t k = 0; k < nlp; k++) {
         if (lp_dropped[k]) continue;
@@ -787,7 +810,7 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     read_status();
     if (st_h->err) throw StatusError(LPP_ERR_CUDA, "internal: S5 hash table overflow");
     if (st_h->cols_fixed > 0) s5_clean = false;  // rows lost entries (S4 or S6 fixings, S5c merges)
-    if (rows_removed > 0) s5c_clean = false;
+    if (rows_removed > 0 || st_h->cols_fixed > 0) s5c_dirty = true;
     if (out.structural) {
         const int32_t m_new = st_h->m_new, n_new = st_h->n_new, nnz_new = st_h->nnz_new;
         if (nnz_new != st_h->nnz_new_t || m_new < 0 || m_new > m || n_new < 0 || n_new > n || nnz_new > nnz)
@@ -806,51 +829,45 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     return out;
 }
 
-// S5c leader passes: the first over every unfixed column, later ones over
-// the columns still in play (chunks of 2, 4, 8, ... passes between reads of
-// the list size).  Refreshes st_h, whose column count then includes the
-// merges.  Returns true once every key is resolved within par_max_iter passes.
-bool Engine::run_s5c(const Ctx &C0) {
+// S5c: keys into the column table, the columns of the changed groups in
+// column order, sorted by slot, then every such group's passes on the
+// device.  Two host reads: the number of grouped columns (sizes the sort),
+// then the status.  Refreshes st_h, whose column count then includes the
+// merges.
+void Engine::run_s5c(const Ctx &C0) {
     Ctx C = C0;
     tbegin(F_S5C, 0.0);
-    LPP_CUDA(cudaMemsetAsync(pc_cnt, 0, sizeof(int32_t) * (size_t)(o.par_max_iter + 2), s));
+    LPP_CUDA(cudaMemsetAsync(pc_cnt, 0, 4 * sizeof(int32_t), s));
     C.ctcap = std::min(ctcap_max, pow2_at_least(2 * (int64_t)std::max(n, 1)));
-    launch_s5c_keys(C, pc_list[0], pc_cnt, s);
-    launch_s5c_pass(C, pc_list[0], pc_cnt, 0, pc_list[1], pc_cnt + 1, n, false, s);
+    launch_s5c_keys(C, s);
+    launch_s5c_members(C, pc_flags, pc_pos, pc_scan, pc_slot, pc_col, s);
     LPP_CUDA(cudaGetLastError());
-    LPP_CUDA(cudaMemcpyAsync(s5_left_h, pc_cnt + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LPP_CUDA(cudaMemcpyAsync(s5_left_h, pc_pos + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     LPP_CUDA(cudaStreamSynchronize(s));
-    const int32_t n1 = *s5_left_h;
-    bool resolved = n1 == 0;
-    if (n1 > 0 && o.par_max_iter > 1) {
-        C.ctcap = std::min(ctcap_max, pow2_at_least(2 * (int64_t)n1));
-        int32_t chunk = 2;
-        for (int32_t pass = 1; pass < o.par_max_iter;) {
-            const int32_t end = std::min<int32_t>(pass + chunk, o.par_max_iter);
-            for (int32_t q = pass; q < end; q++)
-                launch_s5c_pass(C, pc_list[q & 1], pc_cnt + q, q, pc_list[(q + 1) & 1], pc_cnt + q + 1, n1, true, s);
-            LPP_CUDA(cudaGetLastError());
-            LPP_CUDA(cudaMemcpyAsync(s5_left_h, pc_cnt + end, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-            LPP_CUDA(cudaStreamSynchronize(s));
-            if (*s5_left_h == 0) {
-                resolved = true;
-                break;
-            }
-            pass = end;
-            chunk *= 2;
-        }
+    const int32_t F = n > 0 ? *s5_left_h : 0;
+    if (F > 0) {
+        int bits = 0;
+        while (((int64_t)1 << bits) < (int64_t)C.ctcap) bits++;
+        const uint32_t *ks = nullptr;
+        const int32_t *vs = nullptr;
+        sort_pairs(pc_slot, pc_col, F, bits, pc_sort, &ks, &vs, s);
+        launch_s5c_groups(C, ks, vs, F, pc_mem, pc_alive, pc_glist, pc_cnt, o.par_max_iter, s);
     }
+    // the table slots of this round, emptied for the next
+    LPP_CUDA(cudaMemsetAsync(ctkey, 0, sizeof(unsigned long long) * (size_t)C.ctcap, s));
+    LPP_CUDA(cudaMemsetAsync(ctcnt, 0, sizeof(int32_t) * (size_t)C.ctcap, s));
+    LPP_CUDA(cudaMemsetAsync(ctnew, 0, sizeof(int32_t) * (size_t)C.ctcap, s));
+    LPP_CUDA(cudaGetLastError());
     tend();
     LPP_CUDA(cudaMemcpyAsync(st_h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     LPP_CUDA(cudaStreamSynchronize(s));
     if (st_h->err) throw StatusError(LPP_ERR_CUDA, "internal: S5c hash table overflow");
-    return resolved;
 }
 
 void Engine::run() {
     const int32_t R = std::max(0, o.max_rounds);
     s5_clean = false;
-    s5c_clean = false;
+    s5c_dirty = true;
     lp_rounds.assign(nlp, 0);
     lp_status.assign(nlp, LPP_OK);
     lp_where.assign(nlp, LPP_WHERE_NONE);

@@ -87,12 +87,20 @@ struct Engine {
     unsigned long long *mL, *mU, *cand_l, *cand_u, *tkey, *tlead, *ch_hash;
     int32_t *s5_list[2] = {nullptr, nullptr}, *s5_cnt = nullptr;
     bool s5_clean = false;  // the last S5 resolved every group and no row changed since
-    // S5c (opts.parallel_cols): column keys and slots, the column table, the
-    // lists of columns per pass and their sizes
-    unsigned long long *hcol = nullptr, *ctkey = nullptr, *ctlead = nullptr;
-    int32_t *cslot = nullptr, *ctfol = nullptr, *pc_list[2] = {nullptr, nullptr}, *pc_cnt = nullptr;
+    // S5c (opts.parallel_cols): slots and the column table; flags, positions
+    // and the (slot, column) pairs of the grouped columns with their sort
+    // buffers; per-position cached data and live flags; the large groups
+    unsigned long long *ctkey = nullptr;
+    int32_t *cslot = nullptr, *ctcnt = nullptr, *ctnew = nullptr, *pc_cnt = nullptr, *pcnt = nullptr, *plen = nullptr;
+    unsigned long long *pkey = nullptr;
+    void *pc_mem = nullptr;
+    int32_t *pc_flags = nullptr, *pc_pos = nullptr, *pc_col = nullptr, *pc_scan = nullptr;
+    uint32_t *pc_slot = nullptr;
+    TransposeBufs pc_sort{};
+    uint8_t *pc_alive = nullptr;
+    int2 *pc_glist = nullptr;
     int32_t ctcap_max = 0;
-    bool s5c_clean = false;  // the last S5c resolved every key and its round removed no row
+    bool s5c_dirty = true;   // a row was removed or a column fixed or merged since the last S5c
     cudaStream_t s2 = nullptr;                   // host inputs: the vectors' copies
     cudaEvent_t ev_mat = nullptr, ev_vec = nullptr;
     bool vec_pending = false;                    // their check waits for the copies (prepare)
@@ -166,7 +174,7 @@ struct Engine {
     void schedule_current();
     void adopt_schedule();
     void compact(int32_t round);
-    bool run_s5c(const Ctx &C0);  // S5c leader passes; true once every key is resolved
+    void run_s5c(const Ctx &C0);  // S5c: keys, the changed groups, their leader passes
     // timing helpers
     void tbegin(int fam, double bytes);
     void tend();

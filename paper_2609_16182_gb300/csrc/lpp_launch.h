@@ -59,6 +59,12 @@ size_t transpose_hist_elems(int64_t nnz);
 void transpose(const int32_t *ptr, const int32_t *idx, const double *val, const int32_t *row_of, int32_t m,
                int32_t n, int64_t nnz, const TransposeBufs &b, int32_t *tptr, int32_t *tidx, double *tval,
                cudaStream_t s);
+// Stable LSD radix sort of cnt (key, value) pairs by the low `bits` bits of
+// the keys (8 bits per pass).  keys / vals are not written; the sorted pairs
+// end in b.k0/b.v0 or b.k1/b.v1, returned in *kout / *vout (the inputs
+// themselves when cnt == 0).  b.hist needs transpose_hist_elems(cnt) entries.
+void sort_pairs(const uint32_t *keys, const int32_t *vals, int64_t cnt, int bits, const TransposeBufs &b,
+                const uint32_t **kout, const int32_t **vout, cudaStream_t s);
 void iota(int32_t *a, int32_t cnt, int32_t base, cudaStream_t s);
 void fill_u64(unsigned long long *a, int64_t cnt, unsigned long long v, cudaStream_t s);
 void fill_i32(int32_t *a, int64_t cnt, int32_t v, cudaStream_t s);
@@ -75,13 +81,22 @@ void launch_s5_tail(const Ctx &C, const int32_t *list, const int32_t *cnt, int32
 void launch_s5_leader(const Ctx &C, cudaStream_t s);
 
 // --------------------------------------------------------------- k_parcols.cu
-// S5c first pass: key hash of every column S4 left unfixed, inserted into the
-// column table (C.ctcap slots); participants are appended to list / *cnt
-void launch_s5c_keys(const Ctx &C, int32_t *list, int32_t *cnt, cudaStream_t s);
-// one S5c pass over list[0 .. *cnt), *cnt <= max_cols (insert: put the listed
-// columns into the empty table first); columns that stay go to out
-void launch_s5c_pass(const Ctx &C, const int32_t *list, const int32_t *cnt, int32_t pass, int32_t *out,
-                     int32_t *out_cnt, int32_t max_cols, bool insert, cudaStream_t s);
+// S5c keys: the key hash of every column S4 left unfixed goes into the
+// column table (C.ctcap slots, empty before), which counts the columns per key
+void launch_s5c_keys(const Ctx &C, cudaStream_t s);
+// the columns of the groups that changed since their last S5c (a key or the
+// size) and have two or more columns, in column order: slot[p], col[p] for
+// p < pos[n] (flags, pos: n + 1 entries of scratch)
+void launch_s5c_members(const Ctx &C, int32_t *flags, int32_t *pos, int32_t *scan_tmp, uint32_t *slot, int32_t *col,
+                        cudaStream_t s);
+// bytes per grouped column of the launch_s5c_groups scratch `mem`
+size_t s5c_mem_bytes();
+// all leader passes of every group: F members sorted by slot (column order
+// within a slot), one warp per group of at most 256 columns, larger groups
+// listed in glist and run by thread blocks.  ctr[0]: groups left unresolved
+// at the pass cap, ctr[1]: large groups (both zero before).
+void launch_s5c_groups(const Ctx &C, const uint32_t *slot, const int32_t *col, int32_t F, void *mem, uint8_t *alive,
+                       int2 *glist, int32_t *ctr, int32_t max_iter, cudaStream_t s);
 
 // -------------------------------------------------------------- k_compact.cu
 void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s);

@@ -544,6 +544,39 @@ def parcols(seed: int, m: int = 200, n_base: int = 280, pairs: int = 10, per_col
     return _finish(m, n, ptr, colid, vals, c, lhs, rhs, lb, ub, planted, f"parcols-{seed}")
 
 
+def plant_parallel_cols(lp: LP, seed: int, frac: float = 0.01) -> LP:
+    """`lp` with scaled copies of a random `frac` of its non-empty columns
+    appended as new columns: A_:copy = lambda A_:base and c_copy = lambda c_base
+    exactly, lambda in {-4, -2, -1/2, 1/2, 2, 4}.  A copy's bounds are [-1, 1],
+    so x0 extended by zeros still satisfies the sides.  Vectorised, for LPs
+    of any size."""
+    rng = np.random.default_rng(seed)
+    rows = _row_of_entry(lp.row_ptr.astype(np.int64))
+    cols = lp.col_idx.astype(np.int64)
+    cnt = np.bincount(cols, minlength=lp.n)
+    nonempty = np.flatnonzero(cnt > 0)
+    p = min(len(nonempty), max(1, int(frac * lp.n)))
+    base = np.sort(rng.choice(nonempty, size=p, replace=False))
+    lams = rng.choice([-4.0, -2.0, -0.5, 0.5, 2.0, 4.0], size=p)
+    new_id = np.full(lp.n, -1, np.int64)
+    new_id[base] = lp.n + np.arange(p)
+    pick = new_id[cols] >= 0
+    lam_of = np.zeros(lp.n)
+    lam_of[base] = lams
+    r2 = np.concatenate([rows, rows[pick]])
+    c2 = np.concatenate([cols, new_id[cols[pick]]])
+    v2 = np.concatenate([lp.val, lp.val[pick] * lam_of[cols[pick]]])
+    ptr, cc, vv = _sort_rows(r2, c2, v2, lp.m)
+    n = lp.n + p
+    c = np.concatenate([lp.c, lams * lp.c[base]])
+    lb = np.concatenate([lp.lb, np.full(p, -1.0)])
+    ub = np.concatenate([lp.ub, np.full(p, 1.0)])
+    planted = dict(getattr(lp, "planted", None) or {})
+    planted.update(par_base=base, par_copies=np.arange(lp.n, n), par_lam=lams)
+    return _finish(lp.m, n, ptr, cc, vv, c, lp.lhs.copy(), lp.rhs.copy(), lb, ub, planted,
+                   f"{getattr(lp, 'name', 'lp')}+parcols")
+
+
 # ----------------------------------------------------- vectorised 200-row mix
 def _distinct_columns(rng, lengths, n, pool=None):
     """Columns for rows of the given lengths, distinct inside each row, drawn

@@ -29,6 +29,35 @@ def test_planted_copies_are_merged_into_their_base_with_the_planted_factor():
         assert lp.lb[b] <= lk <= uk <= lp.ub[b]
 
 
+def test_a_chain_of_merges_in_one_pass():
+    # columns 1, 2, 3 are copies of column 0 (factors 2, -1/2, 4): one pass
+    # merges all three into column 0 in column order, each record holding the
+    # leader's bounds before it; the final bounds are the interval sums
+    from lpmake import make
+    base = {0: 1.0, 1: -3.0}
+    lam = {1: 2.0, 2: -0.5, 3: 4.0}
+    rows = [{0: base[0], 1: lam[1] * base[0], 2: lam[2] * base[0], 3: lam[3] * base[0], 4: 1.0},
+            {0: base[1], 1: lam[1] * base[1], 2: lam[2] * base[1], 3: lam[3] * base[1], 4: -1.0}]
+    lb = [-1.0, 0.0, -2.0, 0.5, -1.0]
+    ub = [2.0, 1.0, 3.0, 1.0, 1.0]
+    c = [1.0, 2.0, -0.5, 4.0, 0.0]
+    # sides 1 inside each row's activity range: the rows stay (not redundant)
+    # and imply no bound (1 is below every row's span minus its largest term's)
+    lo_act = [sum(a * (lb[j] if a > 0 else ub[j]) for j, a in r.items()) for r in rows]
+    hi_act = [sum(a * (ub[j] if a > 0 else lb[j]) for j, a in r.items()) for r in rows]
+    lp = make(rows, [x + 1.0 for x in lo_act], [x - 1.0 for x in hi_act], lb, ub, c=c)
+    res = oracle.presolve(lp, oracle.default_opts(parallel_cols=1, max_rounds=1))
+    assert list(res.col_kind[:4]) == [0, 3, 3, 3]
+    ly, uy = lb[0], ub[0]
+    for j in (1, 2, 3):
+        assert res.col_aux[j] == 0 and res.col_pass[j] == 0 and res.col_val[j] == lam[j]
+        assert list(res.col_mrg[j]) == [ly, uy, lb[j], ub[j]]
+        ly, uy = (ly + lam[j] * lb[j], uy + lam[j] * ub[j]) if lam[j] > 0 else (ly + lam[j] * ub[j],
+                                                                                uy + lam[j] * lb[j])
+    k = int(np.flatnonzero(res.col_map == 0)[0])
+    assert (res.lb[k], res.ub[k]) == (ly, uy) == (-1.0 + 0.0 - 1.5 + 2.0, 2.0 + 2.0 + 1.0 + 4.0)
+
+
 def test_off_by_default():
     lp = synth.parcols(1)
     res = oracle.presolve(lp)
