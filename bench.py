@@ -338,6 +338,8 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the LP (profiling runs only)")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: W + K steps only (no timing pass, e2e or CPU baseline)")
+    ap.add_argument("--parallel-cols", action="store_true",
+                    help="with --profile: the LP with 1%% of its columns copied, parallel-column step on")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -356,10 +358,14 @@ def main():
     s = args.scale
     lp = synth.skewed(rank, m=int(2_000_000 * s), n=int(3_000_000 * s), target_nnz=int(20_000_000 * s),
                       row_cap=int(500_000 * s) if s < 1 else 500_000)
+    if args.parallel_cols:
+        if not args.profile:
+            raise SystemExit("--parallel-cols is a profiling option (use with --profile)")
+        lp = synth.plant_parallel_cols(lp, 0, frac=0.01)
     d_lp = synth.LP(m=lp.m, n=lp.n, **{k: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
                                         for k, v in lp.arrays().items()})
     stream = torch.cuda.current_stream(dev)
-    o_dev = lpp.opts(stream=stream.cuda_stream, timing=0)
+    o_dev = lpp.opts(stream=stream.cuda_stream, timing=0, parallel_cols=1 if args.parallel_cols else 0)
     o_time = lpp.opts(stream=stream.cuda_stream, timing=1)
 
     def barrier():
