@@ -16,8 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lpp_oracle.c")
 _LIB = os.path.join(_HERE, "liblpp_oracle.so")
 
-ROW_KEPT, ROW_EMPTY, ROW_REDUNDANT, ROW_SINGLETON, ROW_PARALLEL = 0, 1, 2, 3, 4
-COL_KEPT, COL_FIXED, COL_EMPTY, COL_PARALLEL = 0, 1, 2, 3
+ROW_KEPT, ROW_EMPTY, ROW_REDUNDANT, ROW_SINGLETON, ROW_PARALLEL, ROW_SUBST = 0, 1, 2, 3, 4, 5
+COL_KEPT, COL_FIXED, COL_EMPTY, COL_PARALLEL, COL_SUBST = 0, 1, 2, 3, 4
 OK, INFEASIBLE, UNBOUNDED, ERR_INVALID = 0, 1, 2, -1
 
 
@@ -42,7 +42,8 @@ class _LP(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("feas_tol", C.c_double), ("bound_tol", C.c_double), ("huge", C.c_double),
                 ("max_implied", C.c_double), ("par_tol", C.c_double), ("max_rounds", C.c_int32),
-                ("dual_reductions", C.c_int32), ("par_max_iter", C.c_int32), ("parallel_cols", C.c_int32)]
+                ("dual_reductions", C.c_int32), ("par_max_iter", C.c_int32), ("parallel_cols", C.c_int32),
+                ("col_singletons", C.c_int32)]
 
 
 _OUT_FIELDS = [
@@ -55,6 +56,8 @@ _OUT_FIELDS = [
     ("col_kind", C.c_void_p), ("col_round", C.c_void_p), ("col_val", C.c_void_p),
     ("col_aux", C.c_void_p), ("col_pass", C.c_void_p), ("col_mrg", C.c_void_p),
     ("col_lb", C.c_void_p), ("col_ub", C.c_void_p),
+    ("sub_beg", C.c_void_p), ("sub_len", C.c_void_p), ("sub_rhs", C.c_void_p), ("sub_col", C.c_void_p),
+    ("sub_val", C.c_void_p), ("sub_used", C.c_int64),
     ("act_min", C.c_void_p), ("act_max", C.c_void_p), ("act_scale_min", C.c_void_p),
     ("act_scale_max", C.c_void_p), ("ninf_min", C.c_void_p), ("ninf_max", C.c_void_p),
     ("round_nnz", C.c_void_p), ("round_rows_removed", C.c_void_p), ("round_cols_fixed", C.c_void_p),
@@ -80,7 +83,8 @@ def lib():
         _lib.lppo_activities.argtypes = [C.POINTER(_LP), C.c_double, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p]
         _lib.lppo_activities.restype = C.c_int
-        _lib.lppo_postsolve_primal.argtypes = [C.c_int32, C.c_int32] + [C.c_void_p] * 9
+        _lib.lppo_postsolve_primal.argtypes = ([C.c_int32, C.c_int32] + [C.c_void_p] * 7 + [C.c_int32]
+                                               + [C.c_void_p] * 11)
         _lib.lppo_postsolve_primal.restype = C.c_int
     return _lib
 
@@ -145,6 +149,11 @@ class Result:
     col_mrg: np.ndarray    # [n, 4]: the leader's bounds and the column's just before the merge
     col_lb: np.ndarray
     col_ub: np.ndarray
+    sub_beg: np.ndarray    # column-singleton substitutions, per original row: start in the store,
+    sub_len: np.ndarray    # entries, and the row's right-hand side b; the store holds the row's
+    sub_rhs: np.ndarray    # other columns (original indices) and coefficients
+    sub_col: np.ndarray
+    sub_val: np.ndarray
     act_min: np.ndarray
     act_max: np.ndarray
     act_scale_min: np.ndarray
@@ -181,7 +190,9 @@ def presolve(lp, opts: Opts | None = None) -> Result:
                            ("row_aux", m, np.int32), ("row_val", m, np.float64), ("col_kind", n, np.int32),
                            ("col_round", n, np.int32), ("col_val", n, np.float64), ("col_aux", n, np.int32),
                            ("col_pass", n, np.int32), ("col_mrg", 4 * n, np.float64), ("col_lb", n, np.float64),
-                           ("col_ub", n, np.float64), ("act_min", m, np.float64), ("act_max", m, np.float64),
+                           ("col_ub", n, np.float64), ("sub_beg", m, np.int64), ("sub_len", m, np.int32),
+                           ("sub_rhs", m, np.float64), ("sub_col", nnz, np.int32), ("sub_val", nnz, np.float64),
+                           ("act_min", m, np.float64), ("act_max", m, np.float64),
                            ("act_scale_min", m, np.float64), ("act_scale_max", m, np.float64),
                            ("ninf_min", m, np.int32), ("ninf_max", m, np.int32),
                            ("round_nnz", R, np.int64), ("round_rows_removed", R, np.int32),
@@ -202,6 +213,8 @@ def presolve(lp, opts: Opts | None = None) -> Result:
         row_val=arr["row_val"][:m], col_kind=arr["col_kind"][:n], col_round=arr["col_round"][:n],
         col_val=arr["col_val"][:n], col_aux=arr["col_aux"][:n], col_pass=arr["col_pass"][:n],
         col_mrg=arr["col_mrg"][:4 * n].reshape(n, 4), col_lb=arr["col_lb"][:n], col_ub=arr["col_ub"][:n],
+        sub_beg=arr["sub_beg"][:m], sub_len=arr["sub_len"][:m], sub_rhs=arr["sub_rhs"][:m],
+        sub_col=arr["sub_col"][:out.sub_used].copy(), sub_val=arr["sub_val"][:out.sub_used].copy(),
         act_min=arr["act_min"][:m], act_max=arr["act_max"][:m], act_scale_min=arr["act_scale_min"][:m],
         act_scale_max=arr["act_scale_max"][:m], ninf_min=arr["ninf_min"][:m], ninf_max=arr["ninf_max"][:m],
         round_nnz=arr["round_nnz"][:rounds].copy(), round_rows_removed=arr["round_rows_removed"][:rounds].copy(),
@@ -230,9 +243,14 @@ def postsolve_primal(res: Result, x_red: np.ndarray) -> np.ndarray:
     x = np.zeros(max(n, 1))
     xr = np.ascontiguousarray(x_red, np.float64)
     mrg = np.ascontiguousarray(res.col_mrg, np.float64).reshape(-1)
+    m = len(res.row_kind)
+    scol = np.ascontiguousarray(res.sub_col, np.int32) if len(res.sub_col) else np.zeros(1, np.int32)
+    sval = np.ascontiguousarray(res.sub_val, np.float64) if len(res.sub_val) else np.zeros(1)
     rc = lib().lppo_postsolve_primal(n, res.n_red, _ptr(res.col_map), _ptr(res.col_kind), _ptr(res.col_val),
                                      _ptr(res.col_aux), _ptr(res.col_round), _ptr(res.col_pass), _ptr(mrg),
-                                     _ptr(xr), x.ctypes.data)
+                                     m, _ptr(res.row_kind), _ptr(res.row_round), _ptr(res.row_aux),
+                                     _ptr(res.row_val), _ptr(res.sub_beg), _ptr(res.sub_len), _ptr(res.sub_rhs),
+                                     _ptr(scol), _ptr(sval), _ptr(xr), x.ctypes.data)
     if rc < 0:
         raise ValueError("bad column map")
     return x[:n]
@@ -241,15 +259,16 @@ def postsolve_primal(res: Result, x_red: np.ndarray) -> np.ndarray:
 def records(res: Result):
     """Postsolve records in canonical order (round, step, original index).
     Steps: 0 = row removed in S2, 1 = column fixed in S4, 2 = row merged in
-    S5, 3 = column merged in S5c, 4 = column fixed in S6."""
+    S5, 3 = column merged in S5c, 4 = row and column of a substitution in
+    S5d, 5 = column fixed in S6."""
     recs = []
     for i in np.flatnonzero(res.row_kind != ROW_KEPT):
         k = int(res.row_kind[i])
-        step = 2 if k == ROW_PARALLEL else 0
+        step = {ROW_PARALLEL: 2, ROW_SUBST: 4}.get(k, 0)
         recs.append((int(res.row_round[i]), step, int(i), "row", k, int(res.row_aux[i]), float(res.row_val[i])))
     for j in np.flatnonzero(res.col_kind != COL_KEPT):
         k = int(res.col_kind[j])
-        step = {COL_FIXED: 1, COL_PARALLEL: 3}.get(k, 4)
+        step = {COL_FIXED: 1, COL_PARALLEL: 3, COL_SUBST: 4}.get(k, 5)
         aux = int(res.col_aux[j]) if k == COL_PARALLEL else -1
         recs.append((int(res.col_round[j]), step, int(j), "col", k, aux, float(res.col_val[j])))
     recs.sort(key=lambda t: (t[0], t[1], t[2]))

@@ -56,6 +56,7 @@ void lppo_opts_default(lppo_opts *o)
     o->dual_reductions = 1;
     o->par_max_iter = 16;
     o->parallel_cols = 0;
+    o->col_singletons = 0;
 }
 
 /* ---------------------------------------------------------------- audit */
@@ -247,6 +248,8 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     int32_t *nrp = NULL, *nci = NULL;
     double *nv = NULL;
     int32_t *tcp = NULL, *tri = NULL, *tfill = NULL, *calive = NULL;  /* S5c */
+    int32_t *cs_cnt = NULL, *cs_row = NULL, *rcand = NULL, *cmin = NULL;  /* S5d */
+    int64_t sub_w = 0;
     double *tvl = NULL;
     ckey_t *ckeys = NULL;
     uint64_t *cqbuf = NULL;
@@ -286,9 +289,13 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     ALLOC(nrp, m0 + 1); ALLOC(nci, lp->nnz); ALLOC(nv, lp->nnz);
     ALLOC(tcp, n0 + 1); ALLOC(tri, lp->nnz); ALLOC(tvl, lp->nnz); ALLOC(tfill, n0); ALLOC(calive, n0);
     ALLOC(ckeys, n0); ALLOC(cqbuf, lp->nnz);
+    ALLOC(cs_cnt, n0); ALLOC(cs_row, n0); ALLOC(rcand, m0); ALLOC(cmin, n0);
 
     for (i = 0; i < m0; i++) {
         out->row_kind[i] = LPPO_ROW_KEPT; out->row_round[i] = 0; out->row_aux[i] = -1; out->row_val[i] = 0.0;
+        if (out->sub_beg) out->sub_beg[i] = 0;
+        if (out->sub_len) out->sub_len[i] = 0;
+        if (out->sub_rhs) out->sub_rhs[i] = 0.0;
     }
     for (j = 0; j < n0; j++) {
         out->col_kind[j] = LPPO_COL_KEPT; out->col_round[j] = 0; out->col_val[j] = 0.0;
@@ -707,6 +714,122 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
             }
         }
 
+        /* ---- S5d (opt-in): free column singletons (Sec. 3.2, column
+               singletons).  A column j with one entry in the round-start
+               matrix, unfixed and unmerged, whose row i is a kept equality
+               a_ij x_j + sum_k a_ik x_k = b, is row i's candidate (the
+               first such column of the row).  It is eliminated when it is
+               free or implied free: the range row i gives x_j under the
+               current bounds of the other columns,
+                 [(b - max rest) / a_ij, (b - min rest) / a_ij] (a_ij > 0;
+                 the ends swap for a_ij < 0),
+               lies within [l_j - d(l_j), u_j + d(u_j)] on each finite side
+               (d(x) = feas_tol max(1,|x|)).  Substitutions of one round touch
+               disjoint columns: a row is applied only when it is the first
+               eligible row in each of its columns; the others wait a round.
+               Applying row i: t = c_j / a_ij, c_k <- c_k - t a_ik for the
+               row's other columns, the constant c_j (b / a_ij) goes to the
+               objective (as for a fixed column with value b / a_ij), row i
+               and column j leave the LP, and the row's other entries and b
+               are stored for the postsolve, which sets
+               x_j = (b - sum_k a_ik x_k) / a_ij.  Columns merged in S5c are
+               part of their leader's column and are skipped in the row. */
+        if (o->col_singletons) {
+            for (j = 0; j < n; j++) { cs_cnt[j] = 0; cmin[j] = m; }
+            for (k = 0; k < nnz; k++) cs_cnt[s.ci[k]]++;
+            for (i = 0; i < m; i++) {
+                rcand[i] = -1;
+                for (k = s.rp[i]; k < s.rp[i + 1]; k++) if (cs_cnt[s.ci[k]] == 1) cs_row[s.ci[k]] = i;
+            }
+            for (j = 0; j < n; j++) {
+                if (fixed[j] || cs_cnt[j] != 1) continue;
+                i = cs_row[j];
+                if (kind[i] != LPPO_ROW_KEPT || !isfin(s.L[i]) || s.L[i] != s.U[i] || rcand[i] >= 0) continue;
+                rcand[i] = j;
+            }
+            /* eligibility (free or implied free), then the first row per column */
+            for (i = 0; i < m; i++) {
+                double a = 0.0, b = s.L[i], mnr = 0.0, mxr = 0.0, smn_ = 0.0, smx_ = 0.0, eb_mn = 0.0, eb_mx = 0.0;
+                double lo, hi, eblo, ebhi;
+                int32_t nmn_ = 0, nmx_ = 0, cnt_ = 0, ok = 1;
+                if (rcand[i] < 0) continue;
+                j = rcand[i];
+                for (k = s.rp[i]; k < s.rp[i + 1]; k++) {
+                    const int32_t kk = s.ci[k];
+                    const double ak = s.v[k];
+                    double bmn, bmx;
+                    if (kk == j) { a = ak; continue; }
+                    if (fixed[kk] == 3) continue;
+                    bmn = ak > 0 ? s.l[kk] : s.u[kk];
+                    bmx = ak > 0 ? s.u[kk] : s.l[kk];
+                    if (isfin(bmn)) { mnr = mnr + ak * bmn; smn_ += fabs(ak * bmn);
+                                      eb_mn += fabs(ak) * (ak > 0 ? s.ebl[kk] : s.ebu[kk]); }
+                    else nmn_++;
+                    if (isfin(bmx)) { mxr = mxr + ak * bmx; smx_ += fabs(ak * bmx);
+                                      eb_mx += fabs(ak) * (ak > 0 ? s.ebu[kk] : s.ebl[kk]); }
+                    else nmx_++;
+                    cnt_++;
+                }
+                eb_mn += sum_eb(cnt_, smn_);
+                eb_mx += sum_eb(cnt_, smx_);
+                /* a x_j = b - rest, rest in [mnr, mxr] */
+                if (a > 0) {
+                    lo = nmx_ == 0 ? (b - mxr) / a : -INFINITY; eblo = (s.ebL[i] + eb_mx) / fabs(a) + UROUND * fabs(lo);
+                    hi = nmn_ == 0 ? (b - mnr) / a : INFINITY;  ebhi = (s.ebL[i] + eb_mn) / fabs(a) + UROUND * fabs(hi);
+                } else {
+                    lo = nmn_ == 0 ? (b - mnr) / a : -INFINITY; eblo = (s.ebL[i] + eb_mn) / fabs(a) + UROUND * fabs(lo);
+                    hi = nmx_ == 0 ? (b - mxr) / a : INFINITY;  ebhi = (s.ebL[i] + eb_mx) / fabs(a) + UROUND * fabs(hi);
+                }
+                if (isfin(s.l[j])) {
+                    const double thr = s.l[j] - tol_at(ft, s.l[j]);
+                    if (isfin(lo)) audit(&au, lo - thr, eblo + s.ebl[j] + 2 * UROUND * fabs(thr));
+                    if (!(isfin(lo) && lo >= thr)) ok = 0;
+                }
+                if (isfin(s.u[j])) {
+                    const double thr = s.u[j] + tol_at(ft, s.u[j]);
+                    if (isfin(hi)) audit(&au, thr - hi, ebhi + s.ebu[j] + 2 * UROUND * fabs(thr));
+                    if (!(isfin(hi) && hi <= thr)) ok = 0;
+                }
+                if (!ok) { rcand[i] = -1; continue; }
+                for (k = s.rp[i]; k < s.rp[i + 1]; k++) {
+                    const int32_t kk = s.ci[k];
+                    if (kk != j && fixed[kk] != 3 && i < cmin[kk]) cmin[kk] = i;
+                }
+            }
+            for (i = 0; i < m; i++) {
+                double a = 0.0, t;
+                const double b = s.L[i];
+                int sel = 1;
+                if (rcand[i] < 0) continue;
+                j = rcand[i];
+                for (k = s.rp[i]; k < s.rp[i + 1]; k++) {
+                    const int32_t kk = s.ci[k];
+                    if (kk == j) { a = s.v[k]; continue; }
+                    if (fixed[kk] != 3 && cmin[kk] != i) sel = 0;
+                }
+                if (!sel) continue;
+                t = s.c[j] / a;
+                if (out->sub_beg) out->sub_beg[s.rmap[i]] = sub_w;
+                if (out->sub_rhs) out->sub_rhs[s.rmap[i]] = b;
+                for (k = s.rp[i]; k < s.rp[i + 1]; k++) {
+                    const int32_t kk = s.ci[k];
+                    if (kk == j || fixed[kk] == 3) continue;
+                    s.c[kk] = s.c[kk] - t * s.v[k];
+                    if (out->sub_col) { out->sub_col[sub_w] = s.cmap[kk]; out->sub_val[sub_w] = s.v[k]; }
+                    sub_w++;
+                }
+                if (out->sub_len) out->sub_len[s.rmap[i]] = (int32_t)(sub_w - (out->sub_beg ? out->sub_beg[s.rmap[i]] : 0));
+                kind[i] = LPPO_ROW_SUBST;
+                out->row_kind[s.rmap[i]] = LPPO_ROW_SUBST; out->row_round[s.rmap[i]] = r;
+                out->row_aux[s.rmap[i]] = s.cmap[j]; out->row_val[s.rmap[i]] = a;
+                removed++;
+                fixed[j] = 4; fixv[j] = b / a;
+                out->col_kind[s.cmap[j]] = LPPO_COL_SUBST; out->col_round[s.cmap[j]] = r;
+                out->col_val[s.cmap[j]] = fixv[j];
+                nfixed++;
+            }
+        }
+
         /* ---- S6: a column with no entry left in a kept row is fixed at the
                bound its cost prefers (dual reduction) */
         if (o->dual_reductions) {
@@ -795,6 +918,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     out->status = status;
     out->m_red = s.m; out->n_red = s.n; out->nnz_red = s.rp[s.m];
     out->obj_offset = s.offset;
+    out->sub_used = sub_w;
     memcpy(out->row_ptr, s.rp, sizeof(int32_t) * (size_t)(s.m + 1));
     if (s.rp[s.m] > 0) {
         memcpy(out->col_idx, s.ci, sizeof(int32_t) * (size_t)s.rp[s.m]);
@@ -819,6 +943,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     free(mL); free(mU); free(ebmL); free(ebmU); free(hasf); free(alive); free(nrow); free(ncol);
     free(keys); free(qbuf); free(nrp); free(nci); free(nv);
     free(tcp); free(tri); free(tvl); free(tfill); free(calive); free(ckeys); free(cqbuf);
+    free(cs_cnt); free(cs_row); free(rcand); free(cmin);
     return status;
 oom:
     free(s.rp); free(s.ci); free(s.v); free(s.L); free(s.U); free(s.l); free(s.u); free(s.c);
@@ -828,6 +953,7 @@ oom:
     free(mL); free(mU); free(ebmL); free(ebmU); free(hasf); free(alive); free(nrow); free(ncol);
     free(keys); free(qbuf); free(nrp); free(nci); free(nv);
     free(tcp); free(tri); free(tvl); free(tfill); free(calive); free(ckeys); free(cqbuf);
+    free(cs_cnt); free(cs_row); free(rcand); free(cmin);
     return LPPO_ERR_OOM;
 }
 
@@ -838,54 +964,81 @@ oom:
    x_k = y - lam x_j in [lk, uk] (the highest if that is -inf, 0 if both
    are infinite), with the bounds of the moment of the merge.  Row removals
    and bound changes need no primal postsolve step. */
+/* one merge (col >= 0) or substitution (row >= 0) to undo */
+typedef struct {
+    int32_t round, step, index;
+} pevent_t;
+
+static int later_first(const void *pa, const void *pb)
+{
+    const pevent_t *a = (const pevent_t *)pa, *b = (const pevent_t *)pb;
+    if (a->round != b->round) return a->round > b->round ? -1 : 1;
+    if (a->step != b->step) return a->step > b->step ? -1 : 1;
+    return a->index > b->index ? -1 : (a->index < b->index);
+}
+
 int lppo_postsolve_primal(int32_t n_orig, int32_t n_red, const int32_t *col_map,
                           const int32_t *col_kind, const double *col_val,
                           const int32_t *col_aux, const int32_t *col_round, const int32_t *col_pass,
-                          const double *col_mrg, const double *x_red, double *x_orig)
+                          const double *col_mrg, int32_t m_orig, const int32_t *row_kind,
+                          const int32_t *row_round, const int32_t *row_aux, const double *row_val,
+                          const int64_t *sub_beg, const int32_t *sub_len, const double *sub_rhs,
+                          const int32_t *sub_col, const double *sub_val,
+                          const double *x_red, double *x_orig)
 {
-    int32_t j, nm = 0, a, b;
-    int32_t *ord;
+    int32_t j, i, ne = 0, a;
+    pevent_t *ev;
     for (j = 0; j < n_orig; j++) x_orig[j] = col_kind[j] != LPPO_COL_KEPT ? col_val[j] : NAN;
     for (j = 0; j < n_red; j++) {
         if (col_map[j] < 0 || col_map[j] >= n_orig) return LPPO_ERR_INVALID;
         x_orig[col_map[j]] = x_red[j];
     }
-    for (j = 0; j < n_orig; j++) if (col_kind[j] == LPPO_COL_PARALLEL) nm++;
-    if (nm == 0) return LPPO_OK;
-    if (!col_aux || !col_round || !col_pass || !col_mrg) return LPPO_ERR_INVALID;
-    ord = malloc(sizeof(int32_t) * (size_t)nm);
-    if (!ord) return LPPO_ERR_OOM;
-    nm = 0;
-    for (j = 0; j < n_orig; j++) if (col_kind[j] == LPPO_COL_PARALLEL) ord[nm++] = j;
-    /* latest merge first: (round, pass, column) descending (within a pass a
-       leader takes its columns in increasing order), a plain insertion sort */
-    for (a = 1; a < nm; a++) {
-        int32_t x = ord[a];
-        for (b = a - 1; b >= 0; b--) {
-            int32_t y = ord[b];
-            int later = col_round[x] > col_round[y] ||
-                        (col_round[x] == col_round[y] && (col_pass[x] > col_pass[y] ||
-                                                          (col_pass[x] == col_pass[y] && x > y)));
-            if (!later) break;
-            ord[b + 1] = y;
+    for (j = 0; j < n_orig; j++) if (col_kind[j] == LPPO_COL_PARALLEL) ne++;
+    for (i = 0; i < m_orig && row_kind; i++) if (row_kind[i] == LPPO_ROW_SUBST) ne++;
+    if (ne == 0) return LPPO_OK;
+    ev = malloc(sizeof(pevent_t) * (size_t)ne);
+    if (!ev) return LPPO_ERR_OOM;
+    ne = 0;
+    for (j = 0; j < n_orig; j++)
+        if (col_kind[j] == LPPO_COL_PARALLEL) {
+            if (!col_aux || !col_round || !col_pass || !col_mrg) { free(ev); return LPPO_ERR_INVALID; }
+            ev[ne].round = col_round[j]; ev[ne].step = 0; ev[ne].index = j; ne++;
         }
-        ord[b + 1] = x;
+    for (i = 0; i < m_orig && row_kind; i++)
+        if (row_kind[i] == LPPO_ROW_SUBST) {
+            if (!row_round || !row_aux || !row_val || !sub_beg || !sub_len || !sub_rhs || !sub_col || !sub_val) {
+                free(ev); return LPPO_ERR_INVALID;
+            }
+            ev[ne].round = row_round[i]; ev[ne].step = 1; ev[ne].index = i; ne++;
+        }
+    /* latest first: round, then S5d (after S5c in a round), then index */
+    qsort(ev, (size_t)ne, sizeof(pevent_t), later_first);
+    for (a = 0; a < ne; a++) {
+        if (ev[a].step == 0) {
+            /* merge: v = y + lam x_j sits in x_orig[k] */
+            const int32_t jj = ev[a].index, kk = col_aux[jj];
+            const double lam = col_val[jj], y = x_orig[kk];
+            const double lk = col_mrg[4 * jj], uk = col_mrg[4 * jj + 1], lj = col_mrg[4 * jj + 2], uj = col_mrg[4 * jj + 3];
+            double lo, hi, xj;
+            if (lam > 0) { lo = (y - uk) / lam; hi = (y - lk) / lam; }
+            else { lo = (y - lk) / lam; hi = (y - uk) / lam; }
+            if (lj > lo) lo = lj;
+            if (uj < hi) hi = uj;
+            if (lo > -INFINITY && lo < INFINITY) xj = lo;
+            else if (hi > -INFINITY && hi < INFINITY) xj = hi;
+            else xj = 0.0;
+            x_orig[jj] = xj;
+            x_orig[kk] = y - lam * xj;
+        } else {
+            /* substitution: x_j = (b - sum_k a_k x_k) / a_j, in the stored order */
+            const int32_t ii = ev[a].index, jj = row_aux[ii];
+            double sum = 0.0;
+            int64_t q;
+            if (jj < 0 || jj >= n_orig) { free(ev); return LPPO_ERR_INVALID; }
+            for (q = sub_beg[ii]; q < sub_beg[ii] + sub_len[ii]; q++) sum = sum + sub_val[q] * x_orig[sub_col[q]];
+            x_orig[jj] = (sub_rhs[ii] - sum) / row_val[ii];
+        }
     }
-    for (a = 0; a < nm; a++) {
-        const int32_t jj = ord[a], kk = col_aux[jj];
-        const double lam = col_val[jj], y = x_orig[kk];
-        const double lk = col_mrg[4 * jj], uk = col_mrg[4 * jj + 1], lj = col_mrg[4 * jj + 2], uj = col_mrg[4 * jj + 3];
-        double lo, hi, xj;
-        if (lam > 0) { lo = (y - uk) / lam; hi = (y - lk) / lam; }
-        else { lo = (y - lk) / lam; hi = (y - uk) / lam; }
-        if (lj > lo) lo = lj;
-        if (uj < hi) hi = uj;
-        if (lo > -INFINITY && lo < INFINITY) xj = lo;
-        else if (hi > -INFINITY && hi < INFINITY) xj = hi;
-        else xj = 0.0;
-        x_orig[jj] = xj;
-        x_orig[kk] = y - lam * xj;
-    }
-    free(ord);
+    free(ev);
     return LPPO_OK;
 }

@@ -38,11 +38,13 @@ extern "C" {
 #define LPPO_ROW_REDUNDANT  2
 #define LPPO_ROW_SINGLETON  3
 #define LPPO_ROW_PARALLEL   4
+#define LPPO_ROW_SUBST      5   /* used to eliminate a column singleton (opt-in) */
 /* per-original-column record kinds */
 #define LPPO_COL_KEPT       0
 #define LPPO_COL_FIXED      1   /* lb == ub after tightening (primal)        */
 #define LPPO_COL_EMPTY      2   /* no entry left, fixed by the cost (dual)    */
 #define LPPO_COL_PARALLEL   3   /* merged into a parallel column (opt-in)      */
+#define LPPO_COL_SUBST      4   /* free column singleton, eliminated (opt-in)   */
 
 /* where an infeasible / unbounded verdict was found */
 #define LPPO_WHERE_NONE 0
@@ -69,6 +71,7 @@ typedef struct {
     int32_t dual_reductions; /* 1   */
     int32_t par_max_iter;  /* 16    */
     int32_t parallel_cols; /* 0: S5c (parallel columns) off */
+    int32_t col_singletons; /* 0: S5d (free column singletons) off */
 } lppo_opts;
 
 /* All arrays are allocated by the caller with the sizes given. */
@@ -91,6 +94,13 @@ typedef struct {
        the merged column just before the merge (lk, uk, lj, uj) [4n] */
     int32_t *col_aux, *col_pass;  double *col_mrg;
     double  *col_lb, *col_ub;     /* final bounds (fixed columns: value) */
+    /* column-singleton substitutions (may be NULL when the step is off):
+       per original row [m] the start and length of its entries in the store
+       and its right-hand side b; the store [nnz] holds the row's other
+       columns (original indices) and coefficients; sub_used = entries used */
+    int64_t *sub_beg;  int32_t *sub_len;  double *sub_rhs;
+    int32_t *sub_col;  double *sub_val;
+    int64_t  sub_used;
     /* activities of the last executed round, per original row [m]
        (rows not active at that round's start: ninf = -1)               */
     double  *act_min, *act_max, *act_scale_min, *act_scale_max;
@@ -113,12 +123,18 @@ int  lppo_activities(const lppo_lp *lp, double huge, double *act_min, double *ac
                      int32_t *ninf_min, int32_t *ninf_max);
 
 /* Primal postsolve (Sec. 2.1, postsolver paragraph): x_orig from x_red.
-   col_aux, col_round, col_pass, col_mrg (the merge records) may be NULL when
-   no column was merged. */
+   Fixed columns take their value; merges and substitutions are undone
+   latest first (round, then S5d before S5c, then index, all descending).
+   The merge records (col_aux, col_pass, col_mrg) and the substitution
+   records (row arrays and the store) may be NULL when none was made. */
 int  lppo_postsolve_primal(int32_t n_orig, int32_t n_red, const int32_t *col_map,
                            const int32_t *col_kind, const double *col_val,
                            const int32_t *col_aux, const int32_t *col_round, const int32_t *col_pass,
-                           const double *col_mrg, const double *x_red, double *x_orig);
+                           const double *col_mrg, int32_t m_orig, const int32_t *row_kind,
+                           const int32_t *row_round, const int32_t *row_aux, const double *row_val,
+                           const int64_t *sub_beg, const int32_t *sub_len, const double *sub_rhs,
+                           const int32_t *sub_col, const double *sub_val,
+                           const double *x_red, double *x_orig);
 
 #ifdef __cplusplus
 }

@@ -577,6 +577,32 @@ def plant_parallel_cols(lp: LP, seed: int, frac: float = 0.01) -> LP:
                    f"{getattr(lp, 'name', 'lp')}+parcols")
 
 
+def plant_col_singletons(lp: LP, seed: int, frac: float = 0.5, free_frac: float = 0.5, box: float = 50.0) -> LP:
+    """`lp` with a column singleton appended to a random `frac` of its
+    non-empty equality rows: one entry (U[-5, 5], |a| >= 0.01),
+    free with probability `free_frac`, else bounds [-box, box], cost N(0, 1).
+    x0 extended by zeros still satisfies the sides.  Vectorised."""
+    rng = np.random.default_rng(seed)
+    lens = np.diff(lp.row_ptr.astype(np.int64))
+    eq = np.isfinite(lp.lhs) & (lp.lhs == lp.rhs) & (lens >= 1)
+    cand = np.flatnonzero(eq)
+    p = min(len(cand), max(1, int(frac * len(cand)))) if len(cand) else 0
+    rows_new = np.sort(rng.choice(cand, size=p, replace=False)) if p else np.zeros(0, np.int64)
+    rows = _row_of_entry(lp.row_ptr.astype(np.int64))
+    r2 = np.concatenate([rows, rows_new])
+    c2 = np.concatenate([lp.col_idx.astype(np.int64), lp.n + np.arange(p)])
+    v2 = np.concatenate([lp.val, _draw_magnitudes(rng, p, -5.0, 5.0) if p else np.zeros(0)])
+    ptr, cc, vv = _sort_rows(r2, c2, v2, lp.m)
+    free = rng.random(p) < free_frac
+    lb = np.concatenate([lp.lb, np.where(free, -INF, -box)])
+    ub = np.concatenate([lp.ub, np.where(free, INF, box)])
+    c = np.concatenate([lp.c, rng.normal(0.0, 1.0, p)])
+    planted = dict(getattr(lp, "planted", None) or {})
+    planted.update(cs_rows=rows_new, cs_cols=lp.n + np.arange(p), cs_free=free)
+    return _finish(lp.m, lp.n + p, ptr, cc, vv, c, lp.lhs.copy(), lp.rhs.copy(), lb, ub, planted,
+                   f"{getattr(lp, 'name', 'lp')}+colsing")
+
+
 # ----------------------------------------------------- vectorised 200-row mix
 def _distinct_columns(rng, lengths, n, pool=None):
     """Columns for rows of the given lengths, distinct inside each row, drawn
