@@ -21,6 +21,8 @@
  *   S5  parallel rows by hashing plus a leader check (Sec. 3.2)
  *   S5c parallel columns, the same machinery on the columns of [c; A]
  *       (Sec. 3.2, parallel columns; only with opts.parallel_cols = 1)
+ *   S5d free column singletons eliminated through their equality row
+ *       (Sec. 3.2, column singletons; only with opts.col_singletons = 1)
  *   S6  empty columns fixed at the bound their cost prefers (dual rule)
  *   S7  compaction of the CSR and CSC matrices and of all row/column vectors
  * The reduced LP has the same form (Sec. 3.3) and stays in device memory; the
@@ -71,11 +73,13 @@ typedef enum lpp_status {
 #define LPP_ROW_REDUNDANT 2   /* activities lie inside the sides                  */
 #define LPP_ROW_SINGLETON 3   /* one entry: turned into a bound on that column    */
 #define LPP_ROW_PARALLEL 4    /* a multiple of a leader row, sides merged into it */
+#define LPP_ROW_SUBST 5       /* an equality row used to eliminate a column singleton */
 /* Per-original-column record kinds. */
 #define LPP_COL_KEPT 0
 #define LPP_COL_FIXED 1       /* lb == ub: fixed at that value (primal)           */
 #define LPP_COL_EMPTY 2       /* no entry left: fixed at the cheaper bound (dual) */
 #define LPP_COL_PARALLEL 3    /* merged into a parallel leader column (S5c)       */
+#define LPP_COL_SUBST 4       /* free column singleton eliminated (S5d)           */
 /* Where a verdict was found. */
 #define LPP_WHERE_NONE 0
 #define LPP_WHERE_ROW 1
@@ -110,6 +114,8 @@ typedef struct lpp_opts {
     int32_t par_max_iter;   /* [16]    leader passes per group of equal keys (S5, S5c)       */
     int32_t parallel_cols;  /* [0]     1: merge parallel columns (S5c, Sec. 3.2); lpp_presolve
                                        and lpp_presolve_batch only (a server rejects it)      */
+    int32_t col_singletons; /* [0]     1: eliminate free column singletons (S5d, Sec. 3.2);
+                                       lpp_presolve and lpp_presolve_batch only               */
     int32_t timing;         /* [0]     1: time every kernel launch with CUDA events           */
     int32_t device;         /* [0]     CUDA device ordinal                                   */
     void *stream;           /* [NULL]  cudaStream_t to run on; NULL: a library-owned stream  */
@@ -173,7 +179,9 @@ lpp_status lpp_result_rows(const lpp_postsolve *rec, int32_t *kind, int32_t *rou
 /* Per original column (host arrays of n): kind, round, value, and the final
  * bounds.  A fixed or empty column reports its value as both bounds; a
  * merged column (LPP_COL_PARALLEL) reports lambda as its value and NaN
- * bounds (its range lives on in the leader's). */
+ * bounds (its range lives on in the leader's); an eliminated singleton
+ * (LPP_COL_SUBST) reports b / a_ij as its value and NaN bounds (its value
+ * comes from the postsolve). */
 lpp_status lpp_result_cols(const lpp_postsolve *rec, int32_t *kind, int32_t *round, double *val, double *lb,
                            double *ub);
 /* Parallel-column merges (Sec. 3.2, parallel columns; opts.parallel_cols).
@@ -187,6 +195,18 @@ lpp_status lpp_result_cols(const lpp_postsolve *rec, int32_t *kind, int32_t *rou
  * bounds[4j .. 4j+3] = l_y, u_y, l_j, u_j just before the merge (NaN if j
  * was not merged).  Merges are undone latest (round, pass, column) first. */
 lpp_status lpp_result_merges(const lpp_postsolve *rec, int32_t *leader, int32_t *pass, double *bounds);
+/* Column-singleton substitutions (Sec. 3.2, column singletons;
+ * opts.col_singletons).  A row of kind LPP_ROW_SUBST, a_ij x_j + sum_k a_ik x_k
+ * = b, eliminated the column j in its aux (lpp_result_rows; the value is
+ * a_ij): x_j = (b - sum_k a_ik x_k) / a_ij, with the row's other columns as they
+ * stood then (columns merged into a leader excluded).  Per original row
+ * (host arrays of m, any pointer may be NULL): beg[i], len[i] = its entries
+ * in the store, rhs[i] = b (0 and 0 for other rows).  The store, col[] and
+ * val[] (original column indices and coefficients in row order), is written
+ * up to cap entries; *total receives its size.  Substitutions are undone in
+ * the postsolve latest first (round, then after the merges of their round). */
+lpp_status lpp_result_substitutions(const lpp_postsolve *rec, int64_t *beg, int32_t *len, double *rhs, int64_t cap,
+                                    int32_t *col, double *val, int64_t *total);
 /* Activities of the last executed round per original row (host arrays of m);
  * rows not present at that round's start get NaN and -1. */
 lpp_status lpp_result_activity(const lpp_postsolve *rec, double *act_min, double *act_max, int32_t *ninf_min,
@@ -201,7 +221,9 @@ lpp_status lpp_result_kernels(const lpp_postsolve *rec, int32_t cap, lpp_kernel_
 
 /* Primal postsolve on the CPU (Sec. 2.1 postsolver; Sec. 3.3): x_red[n_red]
  * -> x_orig[n] (host arrays): kept columns take their reduced value, fixed
- * columns their recorded value.  Merges are split latest first: with the
+ * columns their recorded value.  Merges and substitutions are undone latest
+ * first (round; in a round substitutions before merges; then index).  A
+ * substitution sets x_j = (b - sum_k a_ik x_k) / a_ij.  A merge: with the
  * merged value v = y + lambda x_j at hand, x_j is the lowest value of
  * [l_j, u_j] that leaves v - lambda x_j inside [l_y, u_y] (the highest if that
  * range has no finite low end, 0 if it has neither), and y = v - lambda x_j. */

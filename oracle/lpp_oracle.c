@@ -931,7 +931,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     for (j = 0; j < n0; j++) { out->col_lb[j] = NAN; out->col_ub[j] = NAN; }
     for (j = 0; j < s.n; j++) { out->col_lb[s.cmap[j]] = s.l[j]; out->col_ub[s.cmap[j]] = s.u[j]; }
     for (j = 0; j < n0; j++)
-        if (out->col_kind[j] != LPPO_COL_KEPT && out->col_kind[j] != LPPO_COL_PARALLEL) {
+        if (out->col_kind[j] == LPPO_COL_FIXED || out->col_kind[j] == LPPO_COL_EMPTY) {
             out->col_lb[j] = out->col_val[j]; out->col_ub[j] = out->col_val[j];
         }
     out->audit_min_ratio = au.min_ratio; out->audit_decisions = au.n; out->audit_below_1e3 = au.below;

@@ -28,8 +28,6 @@ namespace lpp {
 
 namespace {
 
-__device__ __forceinline__ double pinf() { return __longlong_as_double(0x7ff0000000000000LL); }
-__device__ __forceinline__ double ninf_() { return __longlong_as_double((long long)0xfff0000000000000ULL); }
 
 
 namespace cg = cooperative_groups;

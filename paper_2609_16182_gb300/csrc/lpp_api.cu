@@ -52,7 +52,8 @@ lpp_opts resolve_opts(const lpp_opts *opts) {
     if (opts) o = *opts;
     else lpp_opts_default(&o);
     if (o.max_rounds < 0 || o.par_max_iter < 1 || !(o.feas_tol >= 0) || !(o.bound_tol >= 0) || !(o.huge > 0) ||
-        !(o.max_implied > 0) || !(o.par_tol >= 0) || (o.parallel_cols != 0 && o.parallel_cols != 1))
+        !(o.max_implied > 0) || !(o.par_tol >= 0) || (o.parallel_cols != 0 && o.parallel_cols != 1) ||
+        (o.col_singletons != 0 && o.col_singletons != 1))
         throw StatusError(LPP_ERR_INVALID, "bad options");
     return o;
 }
@@ -126,12 +127,24 @@ std::shared_ptr<DeviceRecords> take_records(Engine &E) {
     D->ca = E.rec_ca;
     D->cp = E.rec_cp;
     D->cm = E.rec_cm;
+    D->sb = E.rec_sb;
+    D->sl = E.rec_sl;
+    D->srhs = E.rec_srhs;
+    D->scol = E.rec_scol;
+    D->sval = E.rec_sval;
+    if (E.sub_used) {
+        unsigned long long used = 0;
+        LPP_CUDA(cudaMemcpyAsync(&used, E.sub_used, sizeof used, cudaMemcpyDeviceToHost, E.s));
+        LPP_CUDA(cudaStreamSynchronize(E.s));
+        D->sub_used = (int64_t)used;
+    }
     D->lu = E.lu[E.cur];
     D->act = E.act[E.act_buf];
     D->ninf = E.ninf[E.act_buf];
     for (void *p : {(void *)D->rk, (void *)D->rr, (void *)D->ra, (void *)D->rv, (void *)D->ck, (void *)D->cr,
                     (void *)D->cv, (void *)D->lu, (void *)D->act, (void *)D->ninf, (void *)D->ca, (void *)D->cp,
-                    (void *)D->cm}) {
+                    (void *)D->cm, (void *)D->sb, (void *)D->sl, (void *)D->srhs, (void *)D->scol,
+                    (void *)D->sval}) {
         if (!p) continue;
         E.pool.forget(p);
         D->owned.push_back(p);
@@ -221,7 +234,8 @@ void materialize(lpp_postsolve *P) {
     d2h_slice(P->col_val, D.cv, c0, n);
     for (int32_t i = 0; i < m; i++) {
         const int32_t a = P->row_aux[i];
-        if (a >= 0) P->row_aux[i] = P->row_kind[i] == LPP_ROW_SINGLETON ? a - c0 : a - r0;
+        if (a >= 0)  // singleton and substitution rows name a column, parallel rows a row
+            P->row_aux[i] = (P->row_kind[i] == LPP_ROW_SINGLETON || P->row_kind[i] == LPP_ROW_SUBST) ? a - c0 : a - r0;
     }
     std::vector<int32_t> cm;
     std::vector<double2> lu;
@@ -239,7 +253,7 @@ void materialize(lpp_postsolve *P) {
         }
     }
     for (int32_t j = 0; j < n; j++)
-        if (P->col_kind[j] != LPP_COL_KEPT && P->col_kind[j] != LPP_COL_PARALLEL)
+        if (P->col_kind[j] == LPP_COL_FIXED || P->col_kind[j] == LPP_COL_EMPTY)
             P->col_lb[j] = P->col_ub[j] = P->col_val[j];
     if (D.ca) {
         d2h_slice(P->col_aux, D.ca, c0, n);
@@ -251,6 +265,39 @@ void materialize(lpp_postsolve *P) {
         P->col_aux.assign(n, -1);
         P->col_pass.assign(n, 0);
         P->col_mrg.assign(4 * (size_t)n, NAN);
+    }
+    // substitutions: this LP's rows and their entries, the store compacted to
+    // them (LP-local column indices)
+    P->sub_beg.assign(m, 0);
+    P->sub_len.assign(m, 0);
+    P->sub_rhs.assign(m, 0.0);
+    P->sub_col.clear();
+    P->sub_val.clear();
+    if (D.sb) {
+        DeviceRecords &DM = const_cast<DeviceRecords &>(D);
+        std::call_once(DM.store_once, [&DM]() {
+            d2h_slice(DM.h_scol, DM.scol, 0, (size_t)DM.sub_used);
+            d2h_slice(DM.h_sval, DM.sval, 0, (size_t)DM.sub_used);
+        });
+        std::vector<long long> sb;
+        std::vector<int32_t> sl;
+        d2h_slice(sb, D.sb, r0, m);
+        d2h_slice(sl, D.sl, r0, m);
+        d2h_slice(P->sub_rhs, D.srhs, r0, m);
+        for (int32_t i = 0; i < m; i++) {
+            if (P->row_kind[i] != LPP_ROW_SUBST) {
+                P->sub_rhs[i] = 0.0;
+                continue;
+            }
+            if (sb[i] < 0 || sl[i] < 0 || sb[i] + sl[i] > DM.sub_used)
+                throw StatusError(LPP_ERR_CUDA, "internal: substitution record out of range");
+            P->sub_beg[i] = (int64_t)P->sub_col.size();
+            P->sub_len[i] = sl[i];
+            for (long long q = sb[i]; q < sb[i] + sl[i]; q++) {
+                P->sub_col.push_back(DM.h_scol[(size_t)q] - c0);
+                P->sub_val.push_back(DM.h_sval[(size_t)q]);
+            }
+        }
     }
     std::vector<double2> act;
     std::vector<int2> ni;
@@ -331,6 +378,7 @@ void lpp_opts_default(lpp_opts *o) {
     o->dual_reductions = 1;
     o->par_max_iter = 16;
     o->parallel_cols = 0;
+    o->col_singletons = 0;
     o->timing = 0;
     o->device = 0;
     o->stream = nullptr;
@@ -631,6 +679,24 @@ lpp_status lpp_result_merges(const lpp_postsolve *Pc, int32_t *leader, int32_t *
     return LPP_OK;
 }
 
+lpp_status lpp_result_substitutions(const lpp_postsolve *Pc, int64_t *beg, int32_t *len, double *rhs, int64_t cap,
+                                    int32_t *col, double *val, int64_t *total) {
+    if (!Pc || cap < 0) return set_err(LPP_ERR_INVALID, "bad argument");
+    lpp_postsolve *P = const_cast<lpp_postsolve *>(Pc);
+    const lpp_status st = guarded([&]() -> lpp_status { materialize(P); return LPP_OK; });
+    if (st != LPP_OK) return st;
+    const size_t m = P->sub_beg.size();
+    const int64_t T = (int64_t)P->sub_col.size();
+    if (beg && m) std::memcpy(beg, P->sub_beg.data(), 8 * m);
+    if (len && m) std::memcpy(len, P->sub_len.data(), 4 * m);
+    if (rhs && m) std::memcpy(rhs, P->sub_rhs.data(), 8 * m);
+    const int64_t w = std::min(cap, T);
+    if (col && w) std::memcpy(col, P->sub_col.data(), 4 * (size_t)w);
+    if (val && w) std::memcpy(val, P->sub_val.data(), 8 * (size_t)w);
+    if (total) *total = T;
+    return LPP_OK;
+}
+
 lpp_status lpp_result_activity(const lpp_postsolve *Pc, double *act_min, double *act_max, int32_t *ninf_min,
                                int32_t *ninf_max) {
     if (!Pc) return set_err(LPP_ERR_INVALID, "NULL record");
@@ -681,29 +747,47 @@ lpp_status lpp_postsolve_primal(const lpp_postsolve *Pc, const double *x_red, do
         if (j < 0 || (size_t)j >= n) return set_err(LPP_ERR_INVALID, "corrupt column map");
         x_orig[j] = x_red[k];
     }
-    // merges, latest (round, pass, column) first -- within a pass a leader
-    // takes its columns in increasing order: y = x_k + lam x_j sits in x_orig[k]
-    std::vector<int32_t> ord;
+    // merges and substitutions, latest first: round, then substitutions
+    // before the merges of their round (S5d comes after S5c), then index
+    struct Ev {
+        int32_t round, step, index;
+    };
+    std::vector<Ev> ev;
     for (size_t j = 0; j < n; j++)
-        if (P->col_kind[j] == LPP_COL_PARALLEL) ord.push_back((int32_t)j);
-    std::sort(ord.begin(), ord.end(), [P](int32_t a, int32_t b) {
-        if (P->col_round[a] != P->col_round[b]) return P->col_round[a] > P->col_round[b];
-        if (P->col_pass[a] != P->col_pass[b]) return P->col_pass[a] > P->col_pass[b];
-        return a > b;
+        if (P->col_kind[j] == LPP_COL_PARALLEL) ev.push_back({P->col_round[j], 0, (int32_t)j});
+    for (size_t i = 0; i < P->row_kind.size(); i++)
+        if (P->row_kind[i] == LPP_ROW_SUBST) ev.push_back({P->row_round[i], 1, (int32_t)i});
+    std::sort(ev.begin(), ev.end(), [](const Ev &a, const Ev &b) {
+        if (a.round != b.round) return a.round > b.round;
+        if (a.step != b.step) return a.step > b.step;
+        return a.index > b.index;
     });
-    for (const int32_t j : ord) {
-        const int32_t k = P->col_aux[j];
-        if (k < 0 || (size_t)k >= n) return set_err(LPP_ERR_INVALID, "corrupt merge record");
-        const double lam = P->col_val[j], y = x_orig[k];
-        const double *b = &P->col_mrg[4 * (size_t)j];  // l_k, u_k, l_j, u_j
-        // the x_j that keep y - lam x_j inside [l_k, u_k], within [l_j, u_j]
-        double lo = lam > 0.0 ? (y - b[1]) / lam : (y - b[0]) / lam;
-        double hi = lam > 0.0 ? (y - b[0]) / lam : (y - b[1]) / lam;
-        if (b[2] > lo) lo = b[2];
-        if (b[3] < hi) hi = b[3];
-        const double xj = std::isfinite(lo) ? lo : (std::isfinite(hi) ? hi : 0.0);
-        x_orig[j] = xj;
-        x_orig[k] = y - lam * xj;
+    for (const Ev &e : ev) {
+        if (e.step == 0) {
+            const int32_t j = e.index, k = P->col_aux[j];
+            if (k < 0 || (size_t)k >= n) return set_err(LPP_ERR_INVALID, "corrupt merge record");
+            const double lam = P->col_val[j], y = x_orig[k];
+            const double *b = &P->col_mrg[4 * (size_t)j];  // l_y, u_y, l_j, u_j
+            // the x_j that keep y - lam x_j inside [l_y, u_y], within [l_j, u_j]
+            double lo = lam > 0.0 ? (y - b[1]) / lam : (y - b[0]) / lam;
+            double hi = lam > 0.0 ? (y - b[0]) / lam : (y - b[1]) / lam;
+            if (b[2] > lo) lo = b[2];
+            if (b[3] < hi) hi = b[3];
+            const double xj = std::isfinite(lo) ? lo : (std::isfinite(hi) ? hi : 0.0);
+            x_orig[j] = xj;
+            x_orig[k] = y - lam * xj;
+        } else {
+            // x_j = (b - sum_k a_ik x_k) / a_ij, the entries in row order
+            const int32_t i = e.index, j = P->row_aux[i];
+            if (j < 0 || (size_t)j >= n) return set_err(LPP_ERR_INVALID, "corrupt substitution record");
+            double sum = 0.0;
+            for (int64_t q = P->sub_beg[i]; q < P->sub_beg[i] + P->sub_len[i]; q++) {
+                const int32_t k = P->sub_col[(size_t)q];
+                if (k < 0 || (size_t)k >= n) return set_err(LPP_ERR_INVALID, "corrupt substitution record");
+                sum = sum + P->sub_val[(size_t)q] * x_orig[k];
+            }
+            x_orig[j] = (P->sub_rhs[i] - sum) / P->row_val[i];
+        }
     }
     return LPP_OK;
 }

@@ -39,9 +39,10 @@ __host__ __device__ __forceinline__ int seg_class(int len) {
 }
 
 // row record kinds (values of lpp.h)
-enum : uint8_t { RK_KEPT = 0, RK_EMPTY = 1, RK_REDUNDANT = 2, RK_SINGLETON = 3, RK_PARALLEL = 4 };
-// column kinds (CK_PARALLEL: merged into a parallel leader column, S5c)
-enum : uint8_t { CK_KEPT = 0, CK_FIXED = 1, CK_EMPTY = 2, CK_PARALLEL = 3 };
+enum : uint8_t { RK_KEPT = 0, RK_EMPTY = 1, RK_REDUNDANT = 2, RK_SINGLETON = 3, RK_PARALLEL = 4, RK_SUBST = 5 };
+// column kinds (CK_PARALLEL: merged into a parallel leader column, S5c;
+// CK_SUBST: a free column singleton eliminated through its row, S5d)
+enum : uint8_t { CK_KEPT = 0, CK_FIXED = 1, CK_EMPTY = 2, CK_PARALLEL = 3, CK_SUBST = 4 };
 // verdict slots per LP, in step order
 enum { V_S2_ROW = 0, V_S3_COL = 1, V_S5_ROW = 2, V_S6_COL = 3, V_SLOTS = 4 };
 
@@ -85,7 +86,7 @@ struct Ctx {
     const int32_t *rmap, *lp_row;
     // columns
     double2 *lu;
-    const double *c;
+    double *c;                      // written only by S5d (one product per column and round)
     const int32_t *cmap, *lp_col;
     // rows whose activities must be recomputed this round (1) and the flags
     // being gathered for the next round; columns whose bounds changed
@@ -135,6 +136,12 @@ struct Ctx {
     double *rec_cv;
     int32_t *rec_ca, *rec_cp;       // S5c merges: leader (original index), pass
     double *rec_cm;                 // [4 per column] l_k, u_k, l_j, u_j at the merge
+    long long *rec_sb;              // S5d substitutions, per original row: start in the store,
+    int32_t *rec_sl;                // entries, right-hand side; the store: columns (original
+    double *rec_srhs;               // indices) and coefficients, filled through sub_used
+    int32_t *rec_scol;
+    double *rec_sval;
+    unsigned long long *sub_used;
     // per LP
     const int32_t *lp_round0;       // arena round in which each LP joined (NULL: all in round 1)
     int32_t *verdict;               // [nlp][V_SLOTS] smallest original index
@@ -184,6 +191,8 @@ __device__ __forceinline__ bool is_fin(double x) {
     return (dbits(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
 }
 __device__ __forceinline__ bool is_neg(double x) { return dbits(x) < 0; }
+__device__ __forceinline__ double pinf() { return __longlong_as_double(0x7ff0000000000000LL); }
+__device__ __forceinline__ double ninf_() { return __longlong_as_double((long long)0xfff0000000000000ULL); }
 // max(1, |x|) with the comparison done on the bit pattern
 __device__ __forceinline__ double max1abs(double x) {
     const long long b = dbits(x) & 0x7fffffffffffffffLL;

@@ -155,7 +155,7 @@ __global__ void k_sizes(const CompactCtx K, int32_t m, int32_t n, DevStatus *st)
 }
 
 const char *kFamNames[F_NUM] = {"prop",     "colfin",   "s5",     "compact_count", "scan", "compact_scatter",
-                                "schedule", "ingest",   "finish", "s5c"};
+                                "schedule", "ingest",   "finish", "s5c", "s5d"};
 
 }  // namespace
 
@@ -353,6 +353,19 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
         rec_cp = pool.alloc<int32_t>(n0);
         rec_cm = pool.alloc<double>(4 * (int64_t)n0);
     }
+    if (o.col_singletons) {
+        cs_rcand = pool.alloc<int32_t>(m0);
+        cs_cmin = pool.alloc<int32_t>(n0);
+        cs_relig = pool.alloc<uint8_t>(m0);
+        cs_tasks = pool.alloc<int32_t>(m0);
+        cs_ntask = pool.alloc<int32_t>(1);
+        rec_sb = pool.alloc<long long>(m0);
+        rec_sl = pool.alloc<int32_t>(m0);
+        rec_srhs = pool.alloc<double>(m0);
+        rec_scol = pool.alloc<int32_t>(nnz0);  // each row is stored at most once
+        rec_sval = pool.alloc<double>(nnz0);
+        sub_used = pool.alloc<unsigned long long>(1);
+    }
     st = pool.alloc<DevStatus>(1);
     LPP_CUDA(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
 }
@@ -526,6 +539,12 @@ void Engine::prepare() {
         LPP_CUDA(cudaMemsetAsync(rec_cp, 0, sizeof(int32_t) * (size_t)std::max(n0, 1), s));
         fill_u64(reinterpret_cast<unsigned long long *>(rec_cm), 4 * (int64_t)n0, 0x7ff8000000000000ULL, s);  // NaN
     }
+    if (o.col_singletons) {
+        LPP_CUDA(cudaMemsetAsync(rec_sb, 0, sizeof(long long) * (size_t)std::max(m0, 1), s));
+        LPP_CUDA(cudaMemsetAsync(rec_sl, 0, sizeof(int32_t) * (size_t)std::max(m0, 1), s));
+        LPP_CUDA(cudaMemsetAsync(rec_srhs, 0, sizeof(double) * (size_t)std::max(m0, 1), s));
+        LPP_CUDA(cudaMemsetAsync(sub_used, 0, sizeof(unsigned long long), s));
+    }
     std::vector<double> offs(nlp);
     for (int32_t k = 0; k < nlp; k++) offs[k] = mem[k].obj_offset;
     LPP_CUDA(cudaMemcpyAsync(K.offset, offs.data(), sizeof(double) * nlp, cudaMemcpyHostToDevice, s));
@@ -634,6 +653,12 @@ Ctx Engine::ctx(int32_t round) const {
     C.rec_ca = rec_ca;
     C.rec_cp = rec_cp;
     C.rec_cm = rec_cm;
+    C.rec_sb = rec_sb;
+    C.rec_sl = rec_sl;
+    C.rec_srhs = rec_srhs;
+    C.rec_scol = rec_scol;
+    C.rec_sval = rec_sval;
+    C.sub_used = sub_used;
     C.cslot = cslot;
     C.ctkey = ctkey;
     C.ctcnt = ctcnt;
@@ -797,6 +822,8 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
         run_s5c(C);
         s5c_dirty = false;
     }
+    // S5d (opt-in) on the rows kept so far and the columns left
+    if (o.col_singletons) run_s5d(C);
     bool newly_dead = false;
     for (int32_t k = 0; k < nlp; k++) {
         if (lp_dropped[k]) continue;
@@ -862,6 +889,23 @@ void Engine::run_s5c(const Ctx &C0) {
     LPP_CUDA(cudaMemcpyAsync(st_h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     LPP_CUDA(cudaStreamSynchronize(s));
     if (st_h->err) throw StatusError(LPP_ERR_CUDA, "internal: S5c hash table overflow");
+}
+
+// S5d: the column-singleton kernels, then a read of the status (its counts
+// decide whether the round compacts)
+void Engine::run_s5d(const Ctx &C) {
+    tbegin(F_S5D, 0.0);
+    if (m > 0 && n > 0) {
+        fill_i32(cs_rcand, m, kNone, s);
+        fill_i32(cs_cmin, n, kNone, s);
+        LPP_CUDA(cudaMemsetAsync(cs_relig, 0, (size_t)m, s));
+        LPP_CUDA(cudaMemsetAsync(cs_ntask, 0, sizeof(int32_t), s));
+        launch_s5d(C, cs_rcand, cs_relig, cs_cmin, cs_tasks, cs_ntask, s);
+        LPP_CUDA(cudaGetLastError());
+    }
+    tend();
+    LPP_CUDA(cudaMemcpyAsync(st_h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    LPP_CUDA(cudaStreamSynchronize(s));
 }
 
 void Engine::run() {

@@ -9,6 +9,7 @@
 #pragma once
 #include <cstdint>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -101,6 +102,10 @@ struct Engine {
     int2 *pc_glist = nullptr;
     int32_t ctcap_max = 0;
     bool s5c_dirty = true;   // a row was removed or a column fixed or merged since the last S5c
+    // S5d (opts.col_singletons): candidate per row, eligibility per row, the
+    // first eligible row per column, the long rows deferred to block tasks
+    int32_t *cs_rcand = nullptr, *cs_cmin = nullptr, *cs_tasks = nullptr, *cs_ntask = nullptr;
+    uint8_t *cs_relig = nullptr;
     cudaStream_t s2 = nullptr;                   // host inputs: the vectors' copies
     cudaEvent_t ev_mat = nullptr, ev_vec = nullptr;
     bool vec_pending = false;                    // their check waits for the copies (prepare)
@@ -119,6 +124,10 @@ struct Engine {
     double *rec_rv, *rec_cv;
     int32_t *rec_ca = nullptr, *rec_cp = nullptr;  // S5c merges (NULL unless opts.parallel_cols)
     double *rec_cm = nullptr;
+    long long *rec_sb = nullptr;                   // S5d substitutions (NULL unless opts.col_singletons)
+    int32_t *rec_sl = nullptr, *rec_scol = nullptr;
+    double *rec_srhs = nullptr, *rec_sval = nullptr;
+    unsigned long long *sub_used = nullptr;
     DevStatus *st;
     DevStatus *st_h = nullptr;  // pinned mirror
     int32_t *verdict_h = nullptr;
@@ -175,13 +184,14 @@ struct Engine {
     void adopt_schedule();
     void compact(int32_t round);
     void run_s5c(const Ctx &C0);  // S5c: keys, the changed groups, their leader passes
+    void run_s5d(const Ctx &C);   // S5d: column singletons, then a status read
     // timing helpers
     void tbegin(int fam, double bytes);
     void tend();
 };
 
 // Kernel families reported by lpp_result_kernels.
-enum Fam { F_PROP = 0, F_COLFIN, F_S5, F_COUNT, F_SCAN, F_SCATTER, F_SCHED, F_INGEST, F_FINISH, F_S5C, F_NUM };
+enum Fam { F_PROP = 0, F_COLFIN, F_S5, F_COUNT, F_SCAN, F_SCATTER, F_SCHED, F_INGEST, F_FINISH, F_S5C, F_S5D, F_NUM };
 const char *fam_name(int f);
 
 // device allocations shared by the reduced LPs of one batch, freed with the last
@@ -230,6 +240,13 @@ struct DeviceRecords {
     double *rv = nullptr, *cv = nullptr;
     int32_t *ca = nullptr, *cp = nullptr;  // S5c merges: leader, pass (NULL without parallel_cols)
     double *cm = nullptr;                  // [4 per column] bounds at the merge
+    long long *sb = nullptr;               // S5d substitutions (NULL without col_singletons)
+    int32_t *sl = nullptr, *scol = nullptr;
+    double *srhs = nullptr, *sval = nullptr;
+    int64_t sub_used = 0;                  // entries in the store
+    std::once_flag store_once;             // the host copy of the store, made once
+    std::vector<int32_t> h_scol;
+    std::vector<double> h_sval;
     double2 *lu = nullptr;       // [n_final] final bounds of the kept columns (arena order)
     int32_t *cmap = nullptr;     // [n_final] their original (arena) index
     double2 *act = nullptr;      // [act_m] last round's activities (that round's numbering)
@@ -251,6 +268,9 @@ struct lpp_postsolve {
     bool host_ready = false;
     std::vector<int32_t> row_kind, row_round, row_aux, col_kind, col_round, col_map, col_aux, col_pass;
     std::vector<double> row_val, col_val, col_lb, col_ub, act_min, act_max, col_mrg;
+    std::vector<int64_t> sub_beg;                 // substitutions: per row, into sub_col / sub_val
+    std::vector<int32_t> sub_len, sub_col;
+    std::vector<double> sub_rhs, sub_val;
     std::vector<int32_t> ninf_min, ninf_max;
     std::vector<int64_t> r_nnz;
     std::vector<int32_t> r_rows, r_cols, r_bounds;

@@ -98,6 +98,14 @@ size_t s5c_mem_bytes();
 void launch_s5c_groups(const Ctx &C, const uint32_t *slot, const int32_t *col, int32_t F, void *mem, uint8_t *alive,
                        int2 *glist, int32_t *ctr, int32_t max_iter, cudaStream_t s);
 
+// --------------------------------------------------------------- k_colsing.cu
+// S5d on the current round: candidates (rcand per row, kNone before), the
+// eligibility test (relig per row, 0 before; long rows listed in tasks /
+// *ntask, 0 before), the first eligible row per column (cmin, kNone
+// before), then the substitutions
+void launch_s5d(const Ctx &C, int32_t *rcand, uint8_t *relig, int32_t *cmin, int32_t *tasks, int32_t *ntask,
+                cudaStream_t s);
+
 // -------------------------------------------------------------- k_compact.cu
 void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s);
 void launch_compact_scatter(const Ctx &C, const CompactCtx &K, int32_t nnz, cudaStream_t s);

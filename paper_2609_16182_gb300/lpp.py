@@ -17,8 +17,8 @@ from . import _build
 
 OK, INFEASIBLE, UNBOUNDED = 0, 1, 2
 ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUDGET = -1, -2, -3, -4, -5
-ROW_KEPT, ROW_EMPTY, ROW_REDUNDANT, ROW_SINGLETON, ROW_PARALLEL = 0, 1, 2, 3, 4
-COL_KEPT, COL_FIXED, COL_EMPTY, COL_PARALLEL = 0, 1, 2, 3
+ROW_KEPT, ROW_EMPTY, ROW_REDUNDANT, ROW_SINGLETON, ROW_PARALLEL, ROW_SUBST = 0, 1, 2, 3, 4, 5
+COL_KEPT, COL_FIXED, COL_EMPTY, COL_PARALLEL, COL_SUBST = 0, 1, 2, 3, 4
 WHERE_NONE, WHERE_ROW, WHERE_COL = 0, 1, 2
 
 
@@ -39,7 +39,8 @@ class Opts(C.Structure):
     _fields_ = [("feas_tol", C.c_double), ("bound_tol", C.c_double), ("huge", C.c_double),
                 ("max_implied", C.c_double), ("par_tol", C.c_double), ("max_rounds", C.c_int32),
                 ("dual_reductions", C.c_int32), ("par_max_iter", C.c_int32), ("parallel_cols", C.c_int32),
-                ("timing", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p)]
+                ("col_singletons", C.c_int32), ("timing", C.c_int32), ("device", C.c_int32),
+                ("stream", C.c_void_p)]
 
 
 class Info(C.Structure):
@@ -63,7 +64,7 @@ class ServerStats(C.Structure):
 # every symbol include/lpp.h declares
 SYMBOLS = ["lpp_opts_default", "lpp_presolve", "lpp_reduced_view", "lpp_reduced_csc", "lpp_reduced_maps",
            "lpp_result_info", "lpp_result_rows", "lpp_result_cols", "lpp_result_activity", "lpp_result_rounds",
-           "lpp_result_kernels", "lpp_result_merges", "lpp_postsolve_primal", "lpp_free_reduced", "lpp_free_postsolve",
+           "lpp_result_kernels", "lpp_result_merges", "lpp_result_substitutions", "lpp_postsolve_primal", "lpp_free_reduced", "lpp_free_postsolve",
            "lpp_last_error", "lpp_presolve_batch", "lpp_server_create", "lpp_server_submit", "lpp_server_take",
            "lpp_server_stats_get", "lpp_server_destroy", "lpp_row_activity_noalloc"]
 
@@ -100,6 +101,7 @@ def load():
     L.lpp_result_rounds.argtypes = [P, C.c_int32, P, P, P, P, P, C.POINTER(C.c_int32)]
     L.lpp_result_kernels.argtypes = [P, C.c_int32, C.POINTER(KernelStat), C.POINTER(C.c_int32)]
     L.lpp_result_merges.argtypes = [P, P, P, P]
+    L.lpp_result_substitutions.argtypes = [P, P, P, P, C.c_int64, P, P, C.POINTER(C.c_int64)]
     L.lpp_postsolve_primal.argtypes = [P, P, P]
     L.lpp_free_reduced.argtypes = [P]
     L.lpp_free_reduced.restype = None
@@ -226,7 +228,8 @@ class Result:
         self._records = None
 
     _RECORD_FIELDS = ("row_kind", "row_round", "row_aux", "row_val", "col_kind", "col_round", "col_val", "col_lb",
-                      "col_ub", "act_min", "act_max", "ninf_min", "ninf_max", "col_aux", "col_pass", "col_mrg")
+                      "col_ub", "act_min", "act_max", "ninf_min", "ninf_max", "col_aux", "col_pass", "col_mrg",
+                      "sub_beg", "sub_len", "sub_rhs", "sub_col", "sub_val")
     _ROUND_FIELDS = ("round_nnz", "round_rows_removed", "round_cols_fixed", "round_bounds_changed", "round_ms")
 
     def __getattr__(self, name):
@@ -279,6 +282,14 @@ class Result:
         _check(L.lpp_result_activity(rec, _p(r["act_min"]), _p(r["act_max"]), _p(r["ninf_min"]),
                                      _p(r["ninf_max"])))
         _check(L.lpp_result_merges(rec, _p(r["col_aux"]), _p(r["col_pass"]), _p(r["col_mrg"])))
+        r["sub_beg"], r["sub_len"], r["sub_rhs"] = np.zeros(m, np.int64), np.zeros(m, np.int32), np.zeros(m)
+        total = C.c_int64(0)
+        _check(L.lpp_result_substitutions(rec, _p(r["sub_beg"]), _p(r["sub_len"]), _p(r["sub_rhs"]), 0, None, None,
+                                          C.byref(total)))
+        r["sub_col"], r["sub_val"] = np.zeros(total.value, np.int32), np.zeros(total.value)
+        if total.value:
+            _check(L.lpp_result_substitutions(rec, None, None, None, total.value, _p(r["sub_col"]),
+                                              _p(r["sub_val"]), C.byref(total)))
         return r
 
     @property

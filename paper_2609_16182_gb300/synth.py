@@ -577,10 +577,14 @@ def plant_parallel_cols(lp: LP, seed: int, frac: float = 0.01) -> LP:
                    f"{getattr(lp, 'name', 'lp')}+parcols")
 
 
-def plant_col_singletons(lp: LP, seed: int, frac: float = 0.5, free_frac: float = 0.5, box: float = 50.0) -> LP:
+def plant_col_singletons(lp: LP, seed: int, frac: float = 0.5, free_frac: float = 0.5, box: float = 50.0,
+                         cost_scale: float = 1.0) -> LP:
     """`lp` with a column singleton appended to a random `frac` of its
     non-empty equality rows: one entry (U[-5, 5], |a| >= 0.01),
-    free with probability `free_frac`, else bounds [-box, box], cost N(0, 1).
+    free with probability `free_frac`, else bounds [-box, box], cost
+    cost_scale * N(0, 1) (a nonzero cost moves onto the row's other columns
+    when the singleton is eliminated; on LPs with infinite bounds that can
+    make the LP unbounded).
     x0 extended by zeros still satisfies the sides.  Vectorised."""
     rng = np.random.default_rng(seed)
     lens = np.diff(lp.row_ptr.astype(np.int64))
@@ -596,7 +600,7 @@ def plant_col_singletons(lp: LP, seed: int, frac: float = 0.5, free_frac: float 
     free = rng.random(p) < free_frac
     lb = np.concatenate([lp.lb, np.where(free, -INF, -box)])
     ub = np.concatenate([lp.ub, np.where(free, INF, box)])
-    c = np.concatenate([lp.c, rng.normal(0.0, 1.0, p)])
+    c = np.concatenate([lp.c, cost_scale * rng.normal(0.0, 1.0, p)])
     planted = dict(getattr(lp, "planted", None) or {})
     planted.update(cs_rows=rows_new, cs_cols=lp.n + np.arange(p), cs_free=free)
     return _finish(lp.m, lp.n + p, ptr, cc, vv, c, lp.lhs.copy(), lp.rhs.copy(), lb, ub, planted,
