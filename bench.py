@@ -212,6 +212,43 @@ def parcols_leg(lpp, synth, torch, dev, stream, lp, steps=10):
     return out
 
 
+def colsing_leg(lpp, synth, torch, dev, stream, lp, steps=10):
+    """The benchmark LP with a free column singleton (cost 0, so that the LP
+    stays bounded) in 30% of its equality rows, presolved with the
+    column-singleton step on and off: throughput of each, the step's own
+    time and the substitutions it made."""
+    q = synth.plant_col_singletons(lp, 0, frac=0.3, free_frac=1.0, cost_scale=0.0)
+    d = synth.LP(m=q.m, n=q.n, **{k: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
+                                  for k, v in q.arrays().items()})
+    out = {"workload": f"benchmark LP + {len(q.planted['cs_cols'])} free singleton columns in equality rows "
+                       f"(n = {q.n}, nnz = {q.nnz})"}
+    for on in (1, 0):
+        o = lpp.opts(stream=stream.cuda_stream, col_singletons=on)
+        for _ in range(2):
+            lpp.presolve(d, o).close()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        proc = 0
+        e0.record(stream)
+        for _ in range(steps):
+            r = lpp.presolve(d, o)
+            proc += int(r.info.nnz_processed)
+            r.close()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        out["on" if on else "off"] = {"ms_per_step": ms, "nnz_per_s": proc / steps / (ms / 1e3)}
+    # outside the timed steps: the substitutions (host copies of the records)
+    # and the step's own time (events around its launches)
+    rt = lpp.presolve(d, lpp.opts(stream=stream.cuda_stream, col_singletons=1, timing=1))
+    k = rt.kernels.get("s5d", {"ms": 0.0, "launches": 0})
+    sub = rt.row_kind == lpp.ROW_SUBST
+    out.update(substitutions=int(np.count_nonzero(sub)), rounds=rt.rounds, s5d_ms=k["ms"],
+               longest_row=int(np.diff(q.row_ptr)[sub].max()) if sub.any() else 0)
+    rt.close()
+    return out
+
+
 def serving_leg(lpp, synth, torch, dev, pool_size=24, requests=200, budget=120 << 30, seed=0):
     """Poisson arrivals of skewed-like LPs (nnz log-uniform in [1e3, 1e6],
     m = nnz/10, n = 1.5 m; requests draw from a pool of `pool_size` distinct
@@ -335,11 +372,14 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-presolve leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-parcols", action="store_true", help="skip the parallel-columns leg")
+    ap.add_argument("--no-colsing", action="store_true", help="skip the column-singletons leg")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the LP (profiling runs only)")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: W + K steps only (no timing pass, e2e or CPU baseline)")
     ap.add_argument("--parallel-cols", action="store_true",
                     help="with --profile: the LP with 1%% of its columns copied, parallel-column step on")
+    ap.add_argument("--col-singletons", action="store_true",
+                    help="with --profile: the LP with free singletons in 30%% of its equality rows, step on")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -358,14 +398,17 @@ def main():
     s = args.scale
     lp = synth.skewed(rank, m=int(2_000_000 * s), n=int(3_000_000 * s), target_nnz=int(20_000_000 * s),
                       row_cap=int(500_000 * s) if s < 1 else 500_000)
+    if (args.parallel_cols or args.col_singletons) and not args.profile:
+        raise SystemExit("--parallel-cols / --col-singletons are profiling options (use with --profile)")
     if args.parallel_cols:
-        if not args.profile:
-            raise SystemExit("--parallel-cols is a profiling option (use with --profile)")
         lp = synth.plant_parallel_cols(lp, 0, frac=0.01)
+    if args.col_singletons:
+        lp = synth.plant_col_singletons(lp, 0, frac=0.3, free_frac=1.0, cost_scale=0.0)
     d_lp = synth.LP(m=lp.m, n=lp.n, **{k: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
                                         for k, v in lp.arrays().items()})
     stream = torch.cuda.current_stream(dev)
-    o_dev = lpp.opts(stream=stream.cuda_stream, timing=0, parallel_cols=1 if args.parallel_cols else 0)
+    o_dev = lpp.opts(stream=stream.cuda_stream, timing=0, parallel_cols=1 if args.parallel_cols else 0,
+                     col_singletons=1 if args.col_singletons else 0)
     o_time = lpp.opts(stream=stream.cuda_stream, timing=1)
 
     def barrier():
@@ -473,6 +516,9 @@ def main():
     parcols = None
     if not args.no_parcols:
         parcols = parcols_leg(lpp, synth, torch, dev, stream, lp)
+    colsing = None
+    if not args.no_colsing:
+        colsing = colsing_leg(lpp, synth, torch, dev, stream, lp)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": ws, "steps": args.steps,
@@ -490,7 +536,7 @@ def main():
                            "l2": "inputs larger than L2 (CSR alone ~245 MB > 129 MB)",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
-                "batched": batched, "serving": serving, "parallel_cols": parcols}
+                "batched": batched, "serving": serving, "parallel_cols": parcols, "col_singletons": colsing}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

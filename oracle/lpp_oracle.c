@@ -724,9 +724,11 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                  [(b - max rest) / a_ij, (b - min rest) / a_ij] (a_ij > 0;
                  the ends swap for a_ij < 0),
                lies within [l_j - d(l_j), u_j + d(u_j)] on each finite side
-               (d(x) = feas_tol max(1,|x|)).  Substitutions of one round touch
-               disjoint columns: a row is applied only when it is the first
-               eligible row in each of its columns; the others wait a round.
+               (d(x) = feas_tol max(1,|x|)).  Substitutions of one round change
+               each cost at most once: a row whose column j has a nonzero cost
+               is applied only when it is the first such eligible row in each of
+               its columns (the others wait a round); a row whose column j has
+               cost 0 changes no cost and is always applied.
                Applying row i: t = c_j / a_ij, c_k <- c_k - t a_ik for the
                row's other columns, the constant c_j (b / a_ij) goes to the
                objective (as for a fixed column with value b / a_ij), row i
@@ -791,6 +793,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                     if (!(isfin(hi) && hi <= thr)) ok = 0;
                 }
                 if (!ok) { rcand[i] = -1; continue; }
+                if (s.c[j] == 0.0) continue;  /* changes no cost: no bid */
                 for (k = s.rp[i]; k < s.rp[i + 1]; k++) {
                     const int32_t kk = s.ci[k];
                     if (kk != j && fixed[kk] != 3 && i < cmin[kk]) cmin[kk] = i;
@@ -805,7 +808,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                 for (k = s.rp[i]; k < s.rp[i + 1]; k++) {
                     const int32_t kk = s.ci[k];
                     if (kk == j) { a = s.v[k]; continue; }
-                    if (fixed[kk] != 3 && cmin[kk] != i) sel = 0;
+                    if (s.c[j] != 0.0 && fixed[kk] != 3 && cmin[kk] != i) sel = 0;
                 }
                 if (!sel) continue;
                 t = s.c[j] / a;
@@ -814,7 +817,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                 for (k = s.rp[i]; k < s.rp[i + 1]; k++) {
                     const int32_t kk = s.ci[k];
                     if (kk == j || fixed[kk] == 3) continue;
-                    s.c[kk] = s.c[kk] - t * s.v[k];
+                    if (s.c[j] != 0.0) s.c[kk] = s.c[kk] - t * s.v[k];  /* cost 0: no cost changes */
                     if (out->sub_col) { out->sub_col[sub_w] = s.cmap[kk]; out->sub_val[sub_w] = s.v[k]; }
                     sub_w++;
                 }

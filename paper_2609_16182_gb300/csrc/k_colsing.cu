@@ -8,19 +8,23 @@
 // the other columns,
 //   [(b - max rest) / a_ij, (b - min rest) / a_ij]   (ends swapped if a_ij < 0),
 // lies within [l_j - d(l_j), u_j + d(u_j)] on each finite side, with
-// d(x) = feas_tol max(1, |x|).  Substitutions of one round touch disjoint
-// columns: a row applies only when it is the first eligible row in each of
-// its columns (atomicMin per column), so every cost changes by exactly one
-// product in a round.  Applying row i: t = c_j / a_ij, c_k <- c_k - t a_ik,
-// column j takes the value b / a_ij for the objective constant (as a fixed
-// column does), row i and column j leave the LP, and the row's other entries
-// and b are stored for the postsolve.  Columns merged in S5c are part of
+// d(x) = feas_tol max(1, |x|).  Substitutions of one round change each cost
+// at most once: a row whose column j has a nonzero cost applies only when it
+// is the first such eligible row in each of its columns (atomicMin per
+// column); a row whose column j costs 0 changes no cost (it writes none, so
+// it never races with a bidding row) and always applies.
+// Applying row i: t = c_j / a_ij, c_k <- c_k - t a_ik, column j takes the
+// value b / a_ij for the objective constant (as a fixed column does), row i
+// and column j leave the LP, and the row's other entries and b are stored
+// for the postsolve.  Columns merged in S5c are part of
 // their leader's column and are skipped.
 //
 // Rows of at most kShortRow entries run one per thread, summing in row
 // order; longer rows are deferred as tasks, one thread block each (the
 // paper's design for long rows), summing with a fixed-order block reduction
-// and storing the entries in row order through a block scan.
+// and storing the entries in row order through a block scan; rows of more
+// than 4096 entries are split into their 4096-entry chunks, one block each,
+// whose partial results one warp per row combines in chunk order.
 #include <algorithm>
 
 #include "lpp_launch.h"
@@ -91,6 +95,7 @@ __global__ void __launch_bounds__(kBlock) k_s5d_check(Ctx C, const int32_t *rcan
     const int32_t j = rcand[i];
     if (j == kNone) return;
     const int32_t beg = C.A.ptr[i], end = C.A.ptr[i + 1];
+    if (end - beg >= kLongMin) return;  // chunked
     if (end - beg > kShortRow) {
         tasks[atomicAdd(ntask, 1)] = i;
         return;
@@ -105,6 +110,7 @@ __global__ void __launch_bounds__(kBlock) k_s5d_check(Ctx C, const int32_t *rcan
     }
     if (!s5d_eligible(C, j, a, C.L[i], mnr, mxr, nmn, nmx)) return;
     relig[i] = 1;
+    if (C.c[j] == 0.0) return;  // changes no cost: no bid
     for (int32_t q = beg; q < end; q++) {
         const int32_t k = C.A.idx[q];
         if (!s5d_skip(C, k, j)) atomicMin(&cmin[k], i);
@@ -168,9 +174,11 @@ __global__ void __launch_bounds__(kTaskThreads) k_s5d_check_long(Ctx C, const in
         const bool ok = s5d_eligible(C, j, s_a, C.L[i], mnr, mxr, nmn, nmx);  // the same in every thread
         if (ok) {
             if (threadIdx.x == 0) relig[i] = 1;
-            for (int32_t q = beg + threadIdx.x; q < end; q += kTaskThreads) {
-                const int32_t k = C.A.idx[q];
-                if (!s5d_skip(C, k, j)) atomicMin(&cmin[k], i);
+            if (C.c[j] != 0.0) {  // changes a cost: bid
+                for (int32_t q = beg + threadIdx.x; q < end; q += kTaskThreads) {
+                    const int32_t k = C.A.idx[q];
+                    if (!s5d_skip(C, k, j)) atomicMin(&cmin[k], i);
+                }
             }
         }
         __syncthreads();
@@ -207,6 +215,7 @@ __global__ void __launch_bounds__(kBlock) k_s5d_apply(Ctx C, const int32_t *rcan
         const int32_t j = rcand[i];
         const int32_t beg = C.A.ptr[i], end = C.A.ptr[i + 1];
         if (end - beg <= kShortRow) {
+            const bool bids = C.c[j] != 0.0;
             bool sel = true;
             int32_t cnt = 0;
             double a = 0.0;
@@ -214,7 +223,7 @@ __global__ void __launch_bounds__(kBlock) k_s5d_apply(Ctx C, const int32_t *rcan
                 const int32_t k = C.A.idx[q];
                 if (k == j) a = C.A.val[q];
                 if (s5d_skip(C, k, j)) continue;
-                sel = sel && cmin[k] == i;
+                sel = sel && (!bids || cmin[k] == i);
                 cnt++;
             }
             if (sel) {
@@ -225,7 +234,7 @@ __global__ void __launch_bounds__(kBlock) k_s5d_apply(Ctx C, const int32_t *rcan
                     const int32_t k = C.A.idx[q];
                     if (s5d_skip(C, k, j)) continue;
                     const double ak = C.A.val[q];
-                    C.c[k] = C.c[k] - t * ak;
+                    if (bids) C.c[k] = C.c[k] - t * ak;  // a row that did not bid writes no cost
                     C.rec_scol[pos] = C.cmap[k];
                     C.rec_sval[pos] = ak;
                     pos++;
@@ -253,13 +262,14 @@ __global__ void __launch_bounds__(kTaskThreads) k_s5d_apply_long(Ctx C, const in
         if (!relig[i]) continue;  // the same in every thread
         const int32_t j = rcand[i];
         const int32_t beg = C.A.ptr[i], end = C.A.ptr[i + 1];
+        const bool bids = C.c[j] != 0.0;
         bool sel = true;
         int32_t cnt = 0;
         for (int32_t q = beg + threadIdx.x; q < end; q += kTaskThreads) {
             const int32_t k = C.A.idx[q];
             if (k == j) s_a = C.A.val[q];
             if (s5d_skip(C, k, j)) continue;
-            sel = sel && cmin[k] == i;
+            sel = sel && (!bids || cmin[k] == i);
             cnt++;
         }
         sel = __syncthreads_and(sel) != 0;
@@ -280,7 +290,7 @@ __global__ void __launch_bounds__(kTaskThreads) k_s5d_apply_long(Ctx C, const in
             const int32_t r = block_rank(keep, s_w, tot);
             if (keep) {
                 const double ak = C.A.val[q];
-                C.c[k] = C.c[k] - tj * ak;
+                if (bids) C.c[k] = C.c[k] - tj * ak;  // a row that did not bid writes no cost
                 C.rec_scol[base + r] = C.cmap[k];
                 C.rec_sval[base + r] = ak;
             }
@@ -294,6 +304,169 @@ __global__ void __launch_bounds__(kTaskThreads) k_s5d_apply_long(Ctx C, const in
     }
 }
 
+// ---------------------------------------------- rows of more than 4096 entries
+// per chunk of a candidate row: partial rest sums (ch_act, ch_ninf) and the
+// coefficient of the candidate column (cs_a)
+__global__ void __launch_bounds__(kTaskThreads) k_s5d_chunk_sums(Ctx C, const int32_t *rcand, double *cs_a) {
+    __shared__ double s_d[kTaskThreads / 32];
+    __shared__ int32_t s_i[kTaskThreads / 32];
+    const Chunk ch = C.A.chunks[blockIdx.x];
+    const int32_t i = ch.seg, j = rcand[i];
+    if (j == kNone) return;  // block-uniform
+    double mnr = 0.0, mxr = 0.0;
+    int32_t nmn = 0, nmx = 0;
+    for (int32_t q = ch.begin + threadIdx.x; q < ch.end; q += kTaskThreads) {
+        const int32_t k = C.A.idx[q];
+        if (k == j) cs_a[i] = C.A.val[q];
+        if (s5d_skip(C, k, j)) continue;
+        s5d_term(C, k, C.A.val[q], mnr, mxr, nmn, nmx);
+    }
+    mnr = block_sum_ordered(mnr, s_d);
+    mxr = block_sum_ordered(mxr, s_d);
+    nmn = block_sum_ordered(nmn, s_i);
+    nmx = block_sum_ordered(nmx, s_i);
+    if (threadIdx.x == 0) {
+        C.ch_act[blockIdx.x] = make_double2(mnr, mxr);
+        C.ch_ninf[blockIdx.x] = make_int2(nmn, nmx);
+    }
+}
+
+// one warp per long row: the chunk sums in chunk order, then the test
+__global__ void __launch_bounds__(kBlock) k_s5d_chunk_elig(Ctx C, const int32_t *rcand, const double *cs_a,
+                                                          uint8_t *relig) {
+    const int32_t t = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    const int32_t nlong = C.A.cls_start[7] - C.A.cls_start[6];
+    if (t >= nlong) return;  // the same t in the whole warp
+    const int32_t i = C.A.order[C.A.cls_start[6] + t], j = rcand[i];
+    if (j == kNone) return;
+    double mnr = 0.0, mxr = 0.0;
+    int32_t nmn = 0, nmx = 0;
+    for (int32_t q = C.A.lfirst[t] + lane; q < C.A.lfirst[t + 1]; q += 32) {
+        const double2 a = C.ch_act[q];
+        const int2 c = C.ch_ninf[q];
+        mnr += a.x;
+        mxr += a.y;
+        nmn += c.x;
+        nmx += c.y;
+    }
+    mnr = group_sum<32>(mnr, 0xffffffffu);
+    mxr = group_sum<32>(mxr, 0xffffffffu);
+    nmn = group_sum<32>(nmn, 0xffffffffu);
+    nmx = group_sum<32>(nmx, 0xffffffffu);
+    if (lane == 0 && s5d_eligible(C, j, cs_a[i], C.L[i], mnr, mxr, nmn, nmx)) relig[i] = 1;
+}
+
+// per chunk of an eligible row whose column costs something: the bids
+__global__ void __launch_bounds__(kTaskThreads) k_s5d_chunk_bid(Ctx C, const int32_t *rcand, const uint8_t *relig,
+                                                               int32_t *cmin) {
+    const Chunk ch = C.A.chunks[blockIdx.x];
+    const int32_t i = ch.seg;
+    if (!relig[i]) return;
+    const int32_t j = rcand[i];
+    if (C.c[j] == 0.0) return;
+    for (int32_t q = ch.begin + threadIdx.x; q < ch.end; q += kTaskThreads) {
+        const int32_t k = C.A.idx[q];
+        if (!s5d_skip(C, k, j)) atomicMin(&cmin[k], i);
+    }
+}
+
+// per chunk of an eligible row: does it win every column (ch_ninf.x) and how
+// many entries does it store (ch_ninf.y)
+__global__ void __launch_bounds__(kTaskThreads) k_s5d_chunk_sel(Ctx C, const int32_t *rcand, const uint8_t *relig,
+                                                               const int32_t *cmin) {
+    __shared__ int32_t s_w[kTaskThreads / 32];
+    const Chunk ch = C.A.chunks[blockIdx.x];
+    const int32_t i = ch.seg;
+    if (!relig[i]) return;
+    const int32_t j = rcand[i];
+    const bool bids = C.c[j] != 0.0;
+    bool sel = true;
+    int32_t cnt = 0;
+    for (int32_t q = ch.begin + threadIdx.x; q < ch.end; q += kTaskThreads) {
+        const int32_t k = C.A.idx[q];
+        if (s5d_skip(C, k, j)) continue;
+        sel = sel && (!bids || cmin[k] == i);
+        cnt++;
+    }
+    sel = __syncthreads_and(sel) != 0;
+    cnt = block_sum_ordered(cnt, s_w);
+    if (threadIdx.x == 0) C.ch_ninf[blockIdx.x] = make_int2(sel ? 1 : 0, cnt);
+}
+
+// one warp per long eligible row: selected when every chunk won; then the
+// store range (chunk bases in chunk order, in ch_hash) and the records
+__global__ void __launch_bounds__(kBlock) k_s5d_chunk_row(Ctx C, const int32_t *rcand, const double *cs_a,
+                                                         uint8_t *relig) {
+    const int32_t t = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    const int32_t nlong = C.A.cls_start[7] - C.A.cls_start[6];
+    int32_t applied = 0;
+    if (t < nlong) {  // the same t in the whole warp
+        const int32_t i = C.A.order[C.A.cls_start[6] + t];
+        if (relig[i]) {
+            const int32_t q0 = C.A.lfirst[t], q1 = C.A.lfirst[t + 1];
+            bool sel = true;
+            int32_t carry = 0;
+            for (int32_t b0 = q0; b0 < q1; b0 += 32) {
+                const int32_t q = b0 + lane;
+                const int2 v = q < q1 ? C.ch_ninf[q] : make_int2(1, 0);
+                sel = sel && v.x != 0;
+                int32_t inc = v.y;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += y;
+                }
+                if (q < q1) C.ch_hash[q] = (unsigned long long)(carry + inc - v.y);  // offset within the row
+                carry += __shfl_sync(0xffffffffu, inc, 31);
+            }
+            sel = __all_sync(0xffffffffu, sel) != 0;
+            if (sel) {
+                unsigned long long pos = 0;
+                if (lane == 0) {
+                    pos = atomicAdd(C.sub_used, (unsigned long long)carry);
+                    const int32_t j = rcand[i];
+                    s5d_record(C, i, j, cs_a[i], C.L[i], pos, carry);
+                    relig[i] = 2;  // applied: the chunks write their entries
+                }
+                pos = __shfl_sync(0xffffffffu, pos, 0);
+                for (int32_t q = q0 + lane; q < q1; q += 32) C.ch_hash[q] += pos;
+                applied = lane == 0;
+            }
+        }
+    }
+    block_add(applied, &C.st->rows_removed);
+    block_add(applied, &C.st->cols_fixed);
+}
+
+// per chunk of an applied row: cost updates and its entries at its base
+__global__ void __launch_bounds__(kTaskThreads) k_s5d_chunk_apply(Ctx C, const int32_t *rcand, const double *cs_a,
+                                                                 const uint8_t *relig) {
+    __shared__ int32_t s_w[kTaskThreads / 32];
+    const Chunk ch = C.A.chunks[blockIdx.x];
+    const int32_t i = ch.seg;
+    if (relig[i] != 2) return;
+    const int32_t j = rcand[i];
+    const bool bids = C.c[j] != 0.0;
+    const double tj = C.c[j] / cs_a[i];
+    unsigned long long base = C.ch_hash[blockIdx.x];
+    for (int32_t q0 = ch.begin; q0 < ch.end; q0 += kTaskThreads) {
+        const int32_t q = q0 + threadIdx.x;
+        const int32_t k = q < ch.end ? C.A.idx[q] : j;
+        const bool keep = q < ch.end && !s5d_skip(C, k, j);
+        int32_t tot;
+        const int32_t r = block_rank(keep, s_w, tot);
+        if (keep) {
+            const double ak = C.A.val[q];
+            if (bids) C.c[k] = C.c[k] - tj * ak;  // a row that did not bid writes no cost
+            C.rec_scol[base + r] = C.cmap[k];
+            C.rec_sval[base + r] = ak;
+        }
+        base += tot;
+    }
+}
+
 inline unsigned blocks_for(int64_t cnt, int threads) {
     return (unsigned)((cnt + threads - 1) / threads > 0 ? (cnt + threads - 1) / threads : 1);
 }
@@ -301,14 +474,27 @@ inline unsigned blocks_for(int64_t cnt, int threads) {
 }  // namespace
 
 void launch_s5d(const Ctx &C, int32_t *rcand, uint8_t *relig, int32_t *cmin, int32_t *tasks, int32_t *ntask,
-                cudaStream_t s) {
+                double *cs_a, cudaStream_t s) {
     if (C.n <= 0 || C.m <= 0) return;
     const int32_t task_grid = std::min<int32_t>(C.m, 2 * 152);
+    const int32_t nlong = C.A.cls_start[7] - C.A.cls_start[6];
+    const bool chunked = nlong > 0 && C.A.nchunks > 0;
+    const unsigned long_warps = blocks_for((int64_t)nlong * 32, kBlock);
     (k_s5d_detect<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C, rcand), note_launch());
     (k_s5d_check<<<blocks_for(C.m, kBlock), kBlock, 0, s>>>(C, rcand, relig, cmin, tasks, ntask), note_launch());
     (k_s5d_check_long<<<task_grid, kTaskThreads, 0, s>>>(C, rcand, relig, cmin, tasks, ntask), note_launch());
+    if (chunked) {
+        (k_s5d_chunk_sums<<<C.A.nchunks, kTaskThreads, 0, s>>>(C, rcand, cs_a), note_launch());
+        (k_s5d_chunk_elig<<<long_warps, kBlock, 0, s>>>(C, rcand, cs_a, relig), note_launch());
+        (k_s5d_chunk_bid<<<C.A.nchunks, kTaskThreads, 0, s>>>(C, rcand, relig, cmin), note_launch());
+    }
     (k_s5d_apply<<<blocks_for(C.m, kBlock), kBlock, 0, s>>>(C, rcand, relig, cmin), note_launch());
     (k_s5d_apply_long<<<task_grid, kTaskThreads, 0, s>>>(C, rcand, relig, cmin, tasks, ntask), note_launch());
+    if (chunked) {
+        (k_s5d_chunk_sel<<<C.A.nchunks, kTaskThreads, 0, s>>>(C, rcand, relig, cmin), note_launch());
+        (k_s5d_chunk_row<<<long_warps, kBlock, 0, s>>>(C, rcand, cs_a, relig), note_launch());
+        (k_s5d_chunk_apply<<<C.A.nchunks, kTaskThreads, 0, s>>>(C, rcand, cs_a, relig), note_launch());
+    }
 }
 
 }  // namespace lpp

@@ -359,6 +359,7 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
         cs_relig = pool.alloc<uint8_t>(m0);
         cs_tasks = pool.alloc<int32_t>(m0);
         cs_ntask = pool.alloc<int32_t>(1);
+        cs_a = pool.alloc<double>(m0);
         rec_sb = pool.alloc<long long>(m0);
         rec_sl = pool.alloc<int32_t>(m0);
         rec_srhs = pool.alloc<double>(m0);
@@ -900,7 +901,7 @@ void Engine::run_s5d(const Ctx &C) {
         fill_i32(cs_cmin, n, kNone, s);
         LPP_CUDA(cudaMemsetAsync(cs_relig, 0, (size_t)m, s));
         LPP_CUDA(cudaMemsetAsync(cs_ntask, 0, sizeof(int32_t), s));
-        launch_s5d(C, cs_rcand, cs_relig, cs_cmin, cs_tasks, cs_ntask, s);
+        launch_s5d(C, cs_rcand, cs_relig, cs_cmin, cs_tasks, cs_ntask, cs_a, s);
         LPP_CUDA(cudaGetLastError());
     }
     tend();

@@ -106,6 +106,7 @@ struct Engine {
     // first eligible row per column, the long rows deferred to block tasks
     int32_t *cs_rcand = nullptr, *cs_cmin = nullptr, *cs_tasks = nullptr, *cs_ntask = nullptr;
     uint8_t *cs_relig = nullptr;
+    double *cs_a = nullptr;  // per row: the candidate's coefficient (rows of more than 4096 entries)
     cudaStream_t s2 = nullptr;                   // host inputs: the vectors' copies
     cudaEvent_t ev_mat = nullptr, ev_vec = nullptr;
     bool vec_pending = false;                    // their check waits for the copies (prepare)

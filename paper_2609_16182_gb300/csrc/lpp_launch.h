@@ -100,11 +100,12 @@ void launch_s5c_groups(const Ctx &C, const uint32_t *slot, const int32_t *col, i
 
 // --------------------------------------------------------------- k_colsing.cu
 // S5d on the current round: candidates (rcand per row, kNone before), the
-// eligibility test (relig per row, 0 before; long rows listed in tasks /
-// *ntask, 0 before), the first eligible row per column (cmin, kNone
-// before), then the substitutions
+// eligibility test (relig per row, 0 before; rows of 65 to 4096 entries
+// listed in tasks / *ntask, 0 before; longer rows by chunks, their candidate's
+// coefficient in cs_a per row), the first bidding row per column (cmin,
+// kNone before), then the substitutions
 void launch_s5d(const Ctx &C, int32_t *rcand, uint8_t *relig, int32_t *cmin, int32_t *tasks, int32_t *ntask,
-                cudaStream_t s);
+                double *cs_a, cudaStream_t s);
 
 // -------------------------------------------------------------- k_compact.cu
 void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s);

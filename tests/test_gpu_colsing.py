@@ -6,6 +6,8 @@ candidate rows reach thousands of entries (the block tasks); the
 one-substitution-per-column rule over two rounds; the step together with
 parallel columns; a batch; and the postsolve.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -47,14 +49,31 @@ def test_tiny_planted(seed):
     assert np.count_nonzero(g.row_kind == lpp.ROW_SUBST) > 0
 
 
-@pytest.mark.parametrize("seed", range(2))
+@pytest.mark.parametrize("seed", [0, 1, 3])
 def test_skewed_planted_long_rows(seed):
+    # zero-cost singletons (the LP stays bounded): rows of 65..4096 entries run
+    # as block tasks, longer ones by chunks (seeds 1 and 3 substitute rows of
+    # 4605 and 7534 entries)
     lp = synth.plant_col_singletons(synth.skewed(seed, m=60_000, n=90_000, target_nnz=600_000, row_cap=20_000), seed,
                                     frac=0.3, free_frac=1.0, cost_scale=0.0)
     g, o = both(lp)
     compare(g, o, lp)
-    sub = np.flatnonzero(g.row_kind == lpp.ROW_SUBST)
-    assert np.any(np.diff(lp.row_ptr)[sub] > 64)  # rows handled as block tasks
+    lens = np.diff(lp.row_ptr)[g.row_kind == lpp.ROW_SUBST]
+    assert np.any(lens > 64)
+    if seed in (1, 3):
+        assert np.any(lens > 4096)
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_skewed_boxed_costly_singletons(seed):
+    # finite bounds everywhere (bounded LP) and singletons with costs: the
+    # substituted rows bid for their columns, long rows included (by chunks)
+    base = synth.skewed(seed, m=60_000, n=90_000, target_nnz=600_000, row_cap=20_000)
+    base = dataclasses.replace(base, lb=np.maximum(base.lb, -1e3), ub=np.minimum(base.ub, 1e3))
+    lp = synth.plant_col_singletons(base, seed, frac=0.3, free_frac=1.0, cost_scale=1.0)
+    g, o = both(lp)
+    compare(g, o, lp)
+    assert np.count_nonzero(g.row_kind == lpp.ROW_SUBST) > 1000
 
 
 def test_one_substitution_per_column_and_round():

@@ -57,6 +57,17 @@ def test_one_substitution_per_column_and_round():
     assert res.row_kind[1] == oracle.ROW_SUBST and res.row_round[1] == 2
 
 
+def test_zero_cost_singletons_do_not_wait():
+    # the same two rows with zero-cost singletons change no cost: both in round 1
+    lp = make([{0: 1.0, 1: 1.0, 2: 1.0}, {0: 1.0, 3: 2.0}, {0: 1.0, 1: -1.0}], [1.0, 2.0, -INF],
+              [1.0, 2.0, 1.0], [0.0, 0.0, -INF, -INF], [1.0, 1.0, INF, INF], c=[1.0, 1.0, 0.0, 0.0])
+    res = oracle.presolve(lp, opts())
+    assert list(res.row_kind[:2]) == [oracle.ROW_SUBST] * 2 and list(res.row_round[:2]) == [1, 1]
+    # x0, x1 kept their cost 1 (no update), so S6 later fixes both at lb = 0
+    assert list(res.col_kind[:2]) == [oracle.COL_EMPTY] * 2 and list(res.col_val[:2]) == [0.0, 0.0]
+    assert res.obj_offset == 0.0
+
+
 def test_off_by_default():
     lp = synth.plant_col_singletons(synth.tiny(1), 1)
     res = oracle.presolve(lp)
