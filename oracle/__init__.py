@@ -43,7 +43,7 @@ class Opts(C.Structure):
     _fields_ = [("feas_tol", C.c_double), ("bound_tol", C.c_double), ("huge", C.c_double),
                 ("max_implied", C.c_double), ("par_tol", C.c_double), ("max_rounds", C.c_int32),
                 ("dual_reductions", C.c_int32), ("par_max_iter", C.c_int32), ("parallel_cols", C.c_int32),
-                ("col_singletons", C.c_int32)]
+                ("col_singletons", C.c_int32), ("dual_fixing", C.c_int32)]
 
 
 _OUT_FIELDS = [

@@ -57,6 +57,7 @@ void lppo_opts_default(lppo_opts *o)
     o->par_max_iter = 16;
     o->parallel_cols = 0;
     o->col_singletons = 0;
+    o->dual_fixing = 0;
 }
 
 /* ---------------------------------------------------------------- audit */
@@ -249,6 +250,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     double *nv = NULL;
     int32_t *tcp = NULL, *tri = NULL, *tfill = NULL, *calive = NULL;  /* S5c */
     int32_t *cs_cnt = NULL, *cs_row = NULL, *rcand = NULL, *cmin = NULL;  /* S5d */
+    int32_t *dlock = NULL, *ulock = NULL;                                   /* S6 locks */
     int64_t sub_w = 0;
     double *tvl = NULL;
     ckey_t *ckeys = NULL;
@@ -290,6 +292,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     ALLOC(tcp, n0 + 1); ALLOC(tri, lp->nnz); ALLOC(tvl, lp->nnz); ALLOC(tfill, n0); ALLOC(calive, n0);
     ALLOC(ckeys, n0); ALLOC(cqbuf, lp->nnz);
     ALLOC(cs_cnt, n0); ALLOC(cs_row, n0); ALLOC(rcand, m0); ALLOC(cmin, n0);
+    ALLOC(dlock, n0); ALLOC(ulock, n0);
 
     for (i = 0; i < m0; i++) {
         out->row_kind[i] = LPPO_ROW_KEPT; out->row_round[i] = 0; out->row_aux[i] = -1; out->row_val[i] = 0.0;
@@ -834,19 +837,39 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
         }
 
         /* ---- S6: a column with no entry left in a kept row is fixed at the
-               bound its cost prefers (dual reduction) */
+               bound its cost prefers (dual reduction).  With dual_fixing, a
+               column is fixed so when no kept row locks it in that direction
+               (dual fixing, the locks of Sec. 3.2's dual explorers): a row
+               a_ij x_j + ... in [L_i, U_i] locks x_j downwards when a_ij > 0
+               and L_i is finite or a_ij < 0 and U_i is finite, upwards in the
+               mirrored cases.  Empty columns have no locks, so the rule
+               contains the empty-column one.  Choice: cost > 0 and no down
+               lock: lb; cost < 0 and no up lock: ub; cost 0: lb if finite and
+               not locked downwards, else ub if finite and not locked upwards,
+               else 0 when unlocked both ways.  An infinite choice with cost
+               != 0 means unbounded (or infeasible). */
         if (o->dual_reductions) {
-            for (j = 0; j < n; j++) colcnt[j] = 0;
+            for (j = 0; j < n; j++) { colcnt[j] = 0; dlock[j] = 0; ulock[j] = 0; }
             for (i = 0; i < m; i++) {
                 if (kind[i] != LPPO_ROW_KEPT) continue;
-                for (k = s.rp[i]; k < s.rp[i + 1]; k++) colcnt[s.ci[k]]++;
+                for (k = s.rp[i]; k < s.rp[i + 1]; k++) {
+                    const int32_t jj = s.ci[k];
+                    colcnt[jj]++;
+                    if (s.v[k] > 0) { dlock[jj] += isfin(s.L[i]); ulock[jj] += isfin(s.U[i]); }
+                    else { dlock[jj] += isfin(s.U[i]); ulock[jj] += isfin(s.L[i]); }
+                }
             }
             for (j = 0; j < n && bad < 0; j++) {
                 double v;
-                if (fixed[j] || colcnt[j] != 0) continue;
-                if (s.c[j] > 0) v = s.l[j];
-                else if (s.c[j] < 0) v = s.u[j];
-                else v = isfin(s.l[j]) ? s.l[j] : (isfin(s.u[j]) ? s.u[j] : 0.0);
+                int fix = 0;
+                if (fixed[j]) continue;
+                if (!o->dual_fixing && colcnt[j] != 0) continue;
+                if (s.c[j] > 0) { fix = dlock[j] == 0; v = s.l[j]; }
+                else if (s.c[j] < 0) { fix = ulock[j] == 0; v = s.u[j]; }
+                else if (dlock[j] == 0 && isfin(s.l[j])) { fix = 1; v = s.l[j]; }
+                else if (ulock[j] == 0 && isfin(s.u[j])) { fix = 1; v = s.u[j]; }
+                else { fix = dlock[j] == 0 && ulock[j] == 0; v = 0.0; }
+                if (!fix) continue;
                 if (!isfin(v)) { bad = j; break; }
                 fixed[j] = 2; fixv[j] = v;
                 out->col_kind[s.cmap[j]] = LPPO_COL_EMPTY; out->col_round[s.cmap[j]] = r;
@@ -946,7 +969,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     free(mL); free(mU); free(ebmL); free(ebmU); free(hasf); free(alive); free(nrow); free(ncol);
     free(keys); free(qbuf); free(nrp); free(nci); free(nv);
     free(tcp); free(tri); free(tvl); free(tfill); free(calive); free(ckeys); free(cqbuf);
-    free(cs_cnt); free(cs_row); free(rcand); free(cmin);
+    free(cs_cnt); free(cs_row); free(rcand); free(cmin); free(dlock); free(ulock);
     return status;
 oom:
     free(s.rp); free(s.ci); free(s.v); free(s.L); free(s.U); free(s.l); free(s.u); free(s.c);
@@ -956,7 +979,7 @@ oom:
     free(mL); free(mU); free(ebmL); free(ebmU); free(hasf); free(alive); free(nrow); free(ncol);
     free(keys); free(qbuf); free(nrp); free(nci); free(nv);
     free(tcp); free(tri); free(tvl); free(tfill); free(calive); free(ckeys); free(cqbuf);
-    free(cs_cnt); free(cs_row); free(rcand); free(cmin);
+    free(cs_cnt); free(cs_row); free(rcand); free(cmin); free(dlock); free(ulock);
     return LPPO_ERR_OOM;
 }
 

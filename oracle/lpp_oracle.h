@@ -72,6 +72,8 @@ typedef struct {
     int32_t par_max_iter;  /* 16    */
     int32_t parallel_cols; /* 0: S5c (parallel columns) off */
     int32_t col_singletons; /* 0: S5d (free column singletons) off */
+    int32_t dual_fixing;   /* 0: S6 fixes empty columns only; 1: every column without a lock
+                              in the direction its cost prefers (needs dual_reductions) */
 } lppo_opts;
 
 /* All arrays are allocated by the caller with the sizes given. */
