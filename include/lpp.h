@@ -23,7 +23,8 @@
  *       (Sec. 3.2, parallel columns; only with opts.parallel_cols = 1)
  *   S5d free column singletons eliminated through their equality row
  *       (Sec. 3.2, column singletons; only with opts.col_singletons = 1)
- *   S6  empty columns fixed at the bound their cost prefers (dual rule)
+ *   S6  empty columns fixed at the bound their cost prefers (dual rule); with
+ *       opts.dual_fixing every column no kept row locks in that direction
  *   S7  compaction of the CSR and CSC matrices and of all row/column vectors
  * The reduced LP has the same form (Sec. 3.3) and stays in device memory; the
  * postsolve record (Sec. 2.1, postsolver; Sec. 3.3) lives on the host.
@@ -77,7 +78,8 @@ typedef enum lpp_status {
 /* Per-original-column record kinds. */
 #define LPP_COL_KEPT 0
 #define LPP_COL_FIXED 1       /* lb == ub: fixed at that value (primal)           */
-#define LPP_COL_EMPTY 2       /* no entry left: fixed at the cheaper bound (dual) */
+#define LPP_COL_EMPTY 2       /* fixed at the cheaper bound (dual): no entry left, or
+                                 with opts.dual_fixing no lock in that direction  */
 #define LPP_COL_PARALLEL 3    /* merged into a parallel leader column (S5c)       */
 #define LPP_COL_SUBST 4       /* free column singleton eliminated (S5d)           */
 /* Where a verdict was found. */
@@ -116,6 +118,8 @@ typedef struct lpp_opts {
                                        and lpp_presolve_batch only (a server rejects it)      */
     int32_t col_singletons; /* [0]     1: eliminate free column singletons (S5d, Sec. 3.2);
                                        lpp_presolve and lpp_presolve_batch only               */
+    int32_t dual_fixing;    /* [0]     1: S6 fixes every column no kept row locks in the
+                                       direction its cost prefers (dual fixing by locks)      */
     int32_t timing;         /* [0]     1: time every kernel launch with CUDA events           */
     int32_t device;         /* [0]     CUDA device ordinal                                   */
     void *stream;           /* [NULL]  cudaStream_t to run on; NULL: a library-owned stream  */

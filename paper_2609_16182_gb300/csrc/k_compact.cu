@@ -139,6 +139,56 @@ __global__ void k_long_prefix(const SegMat M, const int32_t *ch_cnt, int32_t *ch
     }
 }
 
+// ------------------------------------------------- locks (dual fixing, S6)
+// A kept row a_ij x_j + ... in [L_i, U_i] locks x_j downwards when a_ij > 0
+// and L_i is finite or a_ij < 0 and U_i is finite, upwards in the mirrored
+// cases: bit 1 = down, bit 2 = up, OR-combined over the column.
+__device__ __forceinline__ int32_t entry_locks(const Ctx &C, int32_t i, double a) {
+    if (C.rkind[i] != RK_KEPT) return 0;
+    const int32_t fl = is_fin(C.L[i]), fu = is_fin(C.U[i]);
+    return is_neg(a) ? (fu | (fl << 1)) : (fl | (fu << 1));
+}
+
+template <int W>
+__device__ __forceinline__ void lock_group(const Ctx &C, const CompactCtx &K, int32_t j, bool valid) {
+    const unsigned mask = group_mask<W>();
+    const int lane = threadIdx.x & (W - 1);
+    int32_t beg = 0, end = 0, lk = 0;
+    if (valid) {
+        beg = C.T.ptr[j];
+        end = C.T.ptr[j + 1];
+    }
+    for (int32_t k = beg + lane; k < end; k += W) lk |= entry_locks(C, C.T.idx[k], C.T.val[k]);
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) lk |= __shfl_xor_sync(mask, lk, o, W);
+    if (valid && lane == 0) K.c_lock[j] = lk;
+}
+
+__global__ void __launch_bounds__(kBlock) k_locks_groups(Ctx C, CompactCtx K, GroupGrid g) {
+    const int c = grid_class(g, blockIdx.x);
+    const int W = 1 << c;
+    const int32_t pos = C.T.cls_start[c] + (blockIdx.x - g.blk_start[c]) * (kBlock / W) + threadIdx.x / W;
+    const bool valid = pos < C.T.cls_start[c + 1];
+    const int32_t j = valid ? C.T.order[pos] : 0;
+    switch (c) {
+        case 0: lock_group<1>(C, K, j, valid); break;
+        case 1: lock_group<2>(C, K, j, valid); break;
+        case 2: lock_group<4>(C, K, j, valid); break;
+        case 3: lock_group<8>(C, K, j, valid); break;
+        case 4: lock_group<16>(C, K, j, valid); break;
+        default: lock_group<32>(C, K, j, valid); break;
+    }
+}
+
+// long columns: one block per chunk, OR-ed into the column (zero before)
+__global__ void __launch_bounds__(kBlock) k_locks_long(Ctx C, CompactCtx K) {
+    const Chunk ch = C.T.chunks[blockIdx.x];
+    int32_t lk = 0;
+    for (int32_t k = ch.begin + threadIdx.x; k < ch.end; k += kBlock) lk |= entry_locks(C, C.T.idx[k], C.T.val[k]);
+    lk = __reduce_or_sync(0xffffffffu, (unsigned)lk);
+    if ((threadIdx.x & 31) == 0 && lk) atomicOr(&K.c_lock[ch.seg], lk);
+}
+
 // ------------------------------------------------------- S6 + column keep
 __global__ void __launch_bounds__(kBlock) k_colkeep(Ctx C, CompactCtx K) {
     const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -148,14 +198,23 @@ __global__ void __launch_bounds__(kBlock) k_colkeep(Ctx C, CompactCtx K) {
         const bool dead = K.lp_dead[lp];
         uint8_t kind = C.ckind[j];
         double contrib = 0.0;
-        if (!dead && kind == CK_KEPT && C.dual && K.c_len[j] == 0) {
+        if (!dead && kind == CK_KEPT && C.dual && (K.c_len[j] == 0 || C.dualfix)) {
+            // the bound the cost prefers, when no kept row locks the column in
+            // that direction (an empty column has no locks)
+            const int32_t lk = K.c_len[j] == 0 ? 0 : K.c_lock[j];
+            const bool dl = lk & 1, ul = lk & 2;
             const double2 b = C.lu[j];
             const double cj = C.c[j];
             double v;
-            if (cj > 0.0) v = b.x;
-            else if (cj < 0.0) v = b.y;
-            else v = is_fin(b.x) ? b.x : (is_fin(b.y) ? b.y : 0.0);
-            if (!is_fin(v)) {
+            bool fix;
+            if (cj > 0.0) { fix = !dl; v = b.x; }
+            else if (cj < 0.0) { fix = !ul; v = b.y; }
+            else if (!dl && is_fin(b.x)) { fix = true; v = b.x; }
+            else if (!ul && is_fin(b.y)) { fix = true; v = b.y; }
+            else { fix = !dl && !ul; v = 0.0; }
+            if (!fix) {
+                // locked: kept
+            } else if (!is_fin(v)) {
                 atomicMin(&C.verdict[lp * V_SLOTS + V_S6_COL], C.cmap[j]);
             } else {
                 kind = CK_EMPTY;
@@ -549,6 +608,11 @@ void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s) {
         (k_csc_count_long<<<C.T.nchunks, kBlock, 0, s>>>(C, K), note_launch());
         (k_long_prefix<<<blocks_for((int64_t)tlong * 32, 128), 128, 0, s>>>(C.T, K.cht_cnt, K.cht_off, K.c_len, nullptr,
                                                                              nullptr), note_launch());
+    }
+    if (C.dualfix && C.n > 0) {
+        cudaMemsetAsync(K.c_lock, 0, sizeof(int32_t) * (size_t)C.n, s);
+        if (gt.blk_start[6] > 0) (k_locks_groups<<<gt.blk_start[6], kBlock, 0, s>>>(C, K, gt), note_launch());
+        if (tlong > 0 && C.T.nchunks > 0) (k_locks_long<<<C.T.nchunks, kBlock, 0, s>>>(C, K), note_launch());
     }
     if (C.n > 0) (k_colkeep<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C, K), note_launch());
     // 2. row counts over kept columns and the side shifts

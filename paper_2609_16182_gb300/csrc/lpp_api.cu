@@ -53,7 +53,7 @@ lpp_opts resolve_opts(const lpp_opts *opts) {
     else lpp_opts_default(&o);
     if (o.max_rounds < 0 || o.par_max_iter < 1 || !(o.feas_tol >= 0) || !(o.bound_tol >= 0) || !(o.huge > 0) ||
         !(o.max_implied > 0) || !(o.par_tol >= 0) || (o.parallel_cols != 0 && o.parallel_cols != 1) ||
-        (o.col_singletons != 0 && o.col_singletons != 1))
+        (o.col_singletons != 0 && o.col_singletons != 1) || (o.dual_fixing != 0 && o.dual_fixing != 1))
         throw StatusError(LPP_ERR_INVALID, "bad options");
     return o;
 }
@@ -379,6 +379,7 @@ void lpp_opts_default(lpp_opts *o) {
     o->par_max_iter = 16;
     o->parallel_cols = 0;
     o->col_singletons = 0;
+    o->dual_fixing = 0;
     o->timing = 0;
     o->device = 0;
     o->stream = nullptr;

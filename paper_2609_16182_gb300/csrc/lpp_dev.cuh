@@ -149,6 +149,7 @@ struct Ctx {
     DevStatus *st;
     double feas_tol, bound_tol, max_implied, par_tol;
     int32_t dual;
+    int32_t dualfix;                // S6 by locks (opts.dual_fixing)
 };
 
 // Compaction work (S6, S7) beyond Ctx.
@@ -168,6 +169,7 @@ struct CompactCtx {
     int32_t *tile_a, *tile_t;                  // per flat tile: the CSR / CSC segment holding its first entry
     int32_t *r_ch0, *c_ch0;                    // per long row / column: its first chunk
     int32_t *r_new, *c_new;                    // new index, -1 if dropped
+    int32_t *c_lock;                           // per column: 1 locked down, 2 locked up (dual fixing)
     // next buffers
     int32_t *rp2, *ci2;
     double *rv2;

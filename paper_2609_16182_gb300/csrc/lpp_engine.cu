@@ -318,6 +318,7 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
     K.c_ch0 = pool.alloc<int32_t>(n0 + 1);
     K.r_new = pool.alloc<int32_t>(m0 + 1);
     K.c_new = pool.alloc<int32_t>(n0 + 1);
+    K.c_lock = o.dual_fixing ? pool.alloc<int32_t>(n0 + 1) : nullptr;
     rec_rk = pool.alloc<int32_t>(m0);
     rec_rr = pool.alloc<int32_t>(m0);
     rec_ra = pool.alloc<int32_t>(m0);
@@ -677,6 +678,7 @@ Ctx Engine::ctx(int32_t round) const {
     C.max_implied = o.max_implied;
     C.par_tol = o.par_tol;
     C.dual = o.dual_reductions;
+    C.dualfix = o.dual_fixing;
     return C;
 }
 
