@@ -177,76 +177,74 @@ def batched_leg(lpp, synth, torch, dev, stream, count=4096):
                         "200-row LP scaled by m/200; device inputs; one batched call vs 4096 plain calls"}
 
 
-def parcols_leg(lpp, synth, torch, dev, stream, lp, steps=10):
+def opt_in_leg(lpp, torch, dev, stream, q, workload, option, fam, count, steps=10):
+    """One opt-in presolve step on LP q, timed with the step on and off (CUDA
+    events, `steps` presolves each after two warm-ups); outside the timed
+    steps, one presolve with per-family events gives the step's own time
+    (family `fam`) and count(result) its reductions."""
+    d = synth_lp_to(q, torch, dev)
+    out = {"workload": workload}
+    for on in (1, 0):
+        o = lpp.opts(stream=stream.cuda_stream, **{option: on})
+        for _ in range(2):
+            lpp.presolve(d, o).close()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        proc = 0
+        e0.record(stream)
+        for _ in range(steps):
+            r = lpp.presolve(d, o)
+            proc += int(r.info.nnz_processed)
+            r.close()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        out["on" if on else "off"] = {"ms_per_step": ms, "nnz_per_s": proc / steps / (ms / 1e3)}
+    rt = lpp.presolve(d, lpp.opts(stream=stream.cuda_stream, timing=1, **{option: 1}))
+    k = rt.kernels.get(fam, {"ms": 0.0, "launches": 0})
+    out.update(count(rt), rounds=rt.rounds, step_family=fam, step_ms=k["ms"],
+               reduced_nnz=int(rt.info.nnz_red))
+    rt.close()
+    return out
+
+
+def synth_lp_to(q, torch, dev):
+    from paper_2609_16182_gb300 import synth
+    return synth.LP(m=q.m, n=q.n, **{k: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
+                                     for k, v in q.arrays().items()})
+
+
+def parcols_leg(lpp, synth, torch, dev, stream, lp):
     """The benchmark LP with 1% of its columns copied and scaled (planted
-    parallel columns), presolved with the parallel-column step on and off:
-    throughput of each, the step's own time and the merges it made."""
+    parallel columns), with the parallel-column step on and off."""
     q = synth.plant_parallel_cols(lp, 0, frac=0.01)
-    d = synth.LP(m=q.m, n=q.n, **{k: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
-                                  for k, v in q.arrays().items()})
-    out = {"workload": f"benchmark LP + {len(q.planted['par_copies'])} scaled column copies "
-                       f"(n = {q.n}, nnz = {q.nnz})"}
-    for on in (1, 0):
-        o = lpp.opts(stream=stream.cuda_stream, parallel_cols=on)
-        for _ in range(2):
-            lpp.presolve(d, o).close()
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        proc = 0
-        e0.record(stream)
-        for _ in range(steps):
-            r = lpp.presolve(d, o)
-            proc += int(r.info.nnz_processed)
-            r.close()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1) / steps
-        out["on" if on else "off"] = {"ms_per_step": ms, "nnz_per_s": proc / steps / (ms / 1e3)}
-    # outside the timed steps: the merges (host copies of the records) and the
-    # step's own time (events around its launches)
-    rt = lpp.presolve(d, lpp.opts(stream=stream.cuda_stream, parallel_cols=1, timing=1))
-    k = rt.kernels.get("s5c", {"ms": 0.0, "launches": 0})
-    out.update(merged=int(np.count_nonzero(rt.col_kind == lpp.COL_PARALLEL)), rounds=rt.rounds,
-               s5c_ms=k["ms"], s5c_rounds=k["launches"])
-    rt.close()
-    return out
+    return opt_in_leg(lpp, torch, dev, stream, q,
+                      f"benchmark LP + {len(q.planted['par_copies'])} scaled column copies (n = {q.n}, nnz = {q.nnz})",
+                      "parallel_cols", "s5c",
+                      lambda r: {"merged": int(np.count_nonzero(r.col_kind == lpp.COL_PARALLEL))})
 
 
-def colsing_leg(lpp, synth, torch, dev, stream, lp, steps=10):
+def colsing_leg(lpp, synth, torch, dev, stream, lp):
     """The benchmark LP with a free column singleton (cost 0, so that the LP
-    stays bounded) in 30% of its equality rows, presolved with the
-    column-singleton step on and off: throughput of each, the step's own
-    time and the substitutions it made."""
+    stays bounded) in 30% of its equality rows, with the column-singleton
+    step on and off."""
     q = synth.plant_col_singletons(lp, 0, frac=0.3, free_frac=1.0, cost_scale=0.0)
-    d = synth.LP(m=q.m, n=q.n, **{k: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
-                                  for k, v in q.arrays().items()})
-    out = {"workload": f"benchmark LP + {len(q.planted['cs_cols'])} free singleton columns in equality rows "
-                       f"(n = {q.n}, nnz = {q.nnz})"}
-    for on in (1, 0):
-        o = lpp.opts(stream=stream.cuda_stream, col_singletons=on)
-        for _ in range(2):
-            lpp.presolve(d, o).close()
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        proc = 0
-        e0.record(stream)
-        for _ in range(steps):
-            r = lpp.presolve(d, o)
-            proc += int(r.info.nnz_processed)
-            r.close()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1) / steps
-        out["on" if on else "off"] = {"ms_per_step": ms, "nnz_per_s": proc / steps / (ms / 1e3)}
-    # outside the timed steps: the substitutions (host copies of the records)
-    # and the step's own time (events around its launches)
-    rt = lpp.presolve(d, lpp.opts(stream=stream.cuda_stream, col_singletons=1, timing=1))
-    k = rt.kernels.get("s5d", {"ms": 0.0, "launches": 0})
-    sub = rt.row_kind == lpp.ROW_SUBST
-    out.update(substitutions=int(np.count_nonzero(sub)), rounds=rt.rounds, s5d_ms=k["ms"],
-               longest_row=int(np.diff(q.row_ptr)[sub].max()) if sub.any() else 0)
-    rt.close()
-    return out
+
+    def count(r):
+        sub = r.row_kind == lpp.ROW_SUBST
+        return {"substitutions": int(np.count_nonzero(sub)),
+                "longest_row": int(np.diff(q.row_ptr)[sub].max()) if sub.any() else 0}
+
+    return opt_in_leg(lpp, torch, dev, stream, q,
+                      f"benchmark LP + {len(q.planted['cs_cols'])} free singleton columns in equality rows "
+                      f"(n = {q.n}, nnz = {q.nnz})", "col_singletons", "s5d", count)
+
+
+def dualfix_leg(lpp, torch, dev, stream, lp):
+    """The benchmark LP itself with dual fixing by locks on and off (the
+    locks are counted in the compaction family)."""
+    return opt_in_leg(lpp, torch, dev, stream, lp, "benchmark LP", "dual_fixing", "compact_count",
+                      lambda r: {"dual_fixed": int(np.count_nonzero(r.col_kind == lpp.COL_EMPTY))})
 
 
 def serving_leg(lpp, synth, torch, dev, pool_size=24, requests=200, budget=120 << 30, seed=0):
@@ -373,6 +371,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-parcols", action="store_true", help="skip the parallel-columns leg")
     ap.add_argument("--no-colsing", action="store_true", help="skip the column-singletons leg")
+    ap.add_argument("--no-dualfix", action="store_true", help="skip the dual-fixing leg")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the LP (profiling runs only)")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: W + K steps only (no timing pass, e2e or CPU baseline)")
@@ -519,6 +518,9 @@ def main():
     colsing = None
     if not args.no_colsing:
         colsing = colsing_leg(lpp, synth, torch, dev, stream, lp)
+    dualfix = None
+    if not args.no_dualfix:
+        dualfix = dualfix_leg(lpp, torch, dev, stream, lp)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": ws, "steps": args.steps,
@@ -536,7 +538,8 @@ def main():
                            "l2": "inputs larger than L2 (CSR alone ~245 MB > 129 MB)",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
-                "batched": batched, "serving": serving, "parallel_cols": parcols, "col_singletons": colsing}
+                "batched": batched, "serving": serving, "parallel_cols": parcols, "col_singletons": colsing,
+                "dual_fixing": dualfix}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
