@@ -21,8 +21,9 @@
  *   S5  parallel rows by hashing plus a leader check (Sec. 3.2)
  *   S5c parallel columns, the same machinery on the columns of [c; A]
  *       (Sec. 3.2, parallel columns; only with opts.parallel_cols = 1)
- *   S5d free column singletons eliminated through their equality row
- *       (Sec. 3.2, column singletons; only with opts.col_singletons = 1)
+ *   S5d free column singletons eliminated through their row, read as the
+ *       equality at the side the column's cost selects (Sec. 3.2, column
+ *       singletons; only with opts.col_singletons = 1)
  *   S6  empty columns fixed at the bound their cost prefers (dual rule); with
  *       opts.dual_fixing every column no kept row locks in that direction
  *   S7  compaction of the CSR and CSC matrices and of all row/column vectors
@@ -200,10 +201,12 @@ lpp_status lpp_result_cols(const lpp_postsolve *rec, int32_t *kind, int32_t *rou
  * was not merged).  Merges are undone latest (round, pass, column) first. */
 lpp_status lpp_result_merges(const lpp_postsolve *rec, int32_t *leader, int32_t *pass, double *bounds);
 /* Column-singleton substitutions (Sec. 3.2, column singletons;
- * opts.col_singletons).  A row of kind LPP_ROW_SUBST, a_ij x_j + sum_k a_ik x_k
- * = b, eliminated the column j in its aux (lpp_result_rows; the value is
- * a_ij): x_j = (b - sum_k a_ik x_k) / a_ij, with the row's other columns as they
- * stood then (columns merged into a leader excluded).  Per original row
+ * opts.col_singletons).  A row of kind LPP_ROW_SUBST, read as the equality
+ * a_ij x_j + sum_k a_ik x_k = b at one of its sides (an equality's value, or
+ * the side the cost of column j pushes it to), eliminated the column j in its
+ * aux (lpp_result_rows; the value is a_ij): x_j = (b - sum_k a_ik x_k) / a_ij,
+ * with the row's other columns as they stood then (columns merged into a
+ * leader excluded).  Per original row
  * (host arrays of m, any pointer may be NULL): beg[i], len[i] = its entries
  * in the store, rhs[i] = b (0 and 0 for other rows).  The store, col[] and
  * val[] (original column indices and coefficients in row order), is written

@@ -217,6 +217,15 @@ static int cmp_ckey(const void *pa, const void *pb)
 
 static int dsign(double x) { return (x > 0) - (x < 0); }
 
+/* S5d: the side of row [L, U] that column j (cost c, coefficient a) is
+   substituted at: the one its cost pushes a x_j to, or L if finite (else U)
+   for c = 0; L = U for an equality */
+static double s5d_side(double L, double U, double c, double a)
+{
+    if (c != 0.0) return (c > 0) == (a > 0) ? L : U;
+    return isfin(L) ? L : U;
+}
+
 /* ------------------------------------------------------------ the loop */
 typedef struct {
     int32_t m, n;
@@ -250,6 +259,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     double *nv = NULL;
     int32_t *tcp = NULL, *tri = NULL, *tfill = NULL, *calive = NULL;  /* S5c */
     int32_t *cs_cnt = NULL, *cs_row = NULL, *rcand = NULL, *cmin = NULL;  /* S5d */
+    double *cs_val = NULL;
     int32_t *dlock = NULL, *ulock = NULL;                                   /* S6 locks */
     int64_t sub_w = 0;
     double *tvl = NULL;
@@ -291,7 +301,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     ALLOC(nrp, m0 + 1); ALLOC(nci, lp->nnz); ALLOC(nv, lp->nnz);
     ALLOC(tcp, n0 + 1); ALLOC(tri, lp->nnz); ALLOC(tvl, lp->nnz); ALLOC(tfill, n0); ALLOC(calive, n0);
     ALLOC(ckeys, n0); ALLOC(cqbuf, lp->nnz);
-    ALLOC(cs_cnt, n0); ALLOC(cs_row, n0); ALLOC(rcand, m0); ALLOC(cmin, n0);
+    ALLOC(cs_cnt, n0); ALLOC(cs_row, n0); ALLOC(rcand, m0); ALLOC(cmin, n0); ALLOC(cs_val, n0);
     ALLOC(dlock, n0); ALLOC(ulock, n0);
 
     for (i = 0; i < m0; i++) {
@@ -719,9 +729,13 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
 
         /* ---- S5d (opt-in): free column singletons (Sec. 3.2, column
                singletons).  A column j with one entry in the round-start
-               matrix, unfixed and unmerged, whose row i is a kept equality
-               a_ij x_j + sum_k a_ik x_k = b, is row i's candidate (the
-               first such column of the row).  It is eliminated when it is
+               matrix, unfixed and unmerged, in a kept row i with sides
+               [L_i, U_i] reads the row as the equality a_ij x_j + sum_k a_ik
+               x_k = b at one side: the side its cost pushes a_ij x_j to (L_i
+               when c_j a_ij > 0, U_i when c_j a_ij < 0; L_i = U_i for an
+               equality), for c_j = 0 the side L_i if finite, else U_i.  With
+               b finite it is a candidate of row i (the row's first such
+               column).  It is eliminated when it is
                free or implied free: the range row i gives x_j under the
                current bounds of the other columns,
                  [(b - max rest) / a_ij, (b - min rest) / a_ij] (a_ij > 0;
@@ -744,17 +758,19 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
             for (k = 0; k < nnz; k++) cs_cnt[s.ci[k]]++;
             for (i = 0; i < m; i++) {
                 rcand[i] = -1;
-                for (k = s.rp[i]; k < s.rp[i + 1]; k++) if (cs_cnt[s.ci[k]] == 1) cs_row[s.ci[k]] = i;
+                for (k = s.rp[i]; k < s.rp[i + 1]; k++)
+                    if (cs_cnt[s.ci[k]] == 1) { cs_row[s.ci[k]] = i; cs_val[s.ci[k]] = s.v[k]; }
             }
             for (j = 0; j < n; j++) {
                 if (fixed[j] || cs_cnt[j] != 1) continue;
                 i = cs_row[j];
-                if (kind[i] != LPPO_ROW_KEPT || !isfin(s.L[i]) || s.L[i] != s.U[i] || rcand[i] >= 0) continue;
+                if (kind[i] != LPPO_ROW_KEPT || rcand[i] >= 0) continue;
+                if (!isfin(s5d_side(s.L[i], s.U[i], s.c[j], cs_val[j]))) continue;
                 rcand[i] = j;
             }
             /* eligibility (free or implied free), then the first row per column */
             for (i = 0; i < m; i++) {
-                double a = 0.0, b = s.L[i], mnr = 0.0, mxr = 0.0, smn_ = 0.0, smx_ = 0.0, eb_mn = 0.0, eb_mx = 0.0;
+                double a = 0.0, b, ebb, mnr = 0.0, mxr = 0.0, smn_ = 0.0, smx_ = 0.0, eb_mn = 0.0, eb_mx = 0.0;
                 double lo, hi, eblo, ebhi;
                 int32_t nmn_ = 0, nmx_ = 0, cnt_ = 0, ok = 1;
                 if (rcand[i] < 0) continue;
@@ -777,13 +793,15 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                 }
                 eb_mn += sum_eb(cnt_, smn_);
                 eb_mx += sum_eb(cnt_, smx_);
+                b = s5d_side(s.L[i], s.U[i], s.c[j], a);
+                ebb = b == s.L[i] ? s.ebL[i] : s.ebU[i];
                 /* a x_j = b - rest, rest in [mnr, mxr] */
                 if (a > 0) {
-                    lo = nmx_ == 0 ? (b - mxr) / a : -INFINITY; eblo = (s.ebL[i] + eb_mx) / fabs(a) + UROUND * fabs(lo);
-                    hi = nmn_ == 0 ? (b - mnr) / a : INFINITY;  ebhi = (s.ebL[i] + eb_mn) / fabs(a) + UROUND * fabs(hi);
+                    lo = nmx_ == 0 ? (b - mxr) / a : -INFINITY; eblo = (ebb + eb_mx) / fabs(a) + UROUND * fabs(lo);
+                    hi = nmn_ == 0 ? (b - mnr) / a : INFINITY;  ebhi = (ebb + eb_mn) / fabs(a) + UROUND * fabs(hi);
                 } else {
-                    lo = nmn_ == 0 ? (b - mnr) / a : -INFINITY; eblo = (s.ebL[i] + eb_mn) / fabs(a) + UROUND * fabs(lo);
-                    hi = nmx_ == 0 ? (b - mxr) / a : INFINITY;  ebhi = (s.ebL[i] + eb_mx) / fabs(a) + UROUND * fabs(hi);
+                    lo = nmn_ == 0 ? (b - mnr) / a : -INFINITY; eblo = (ebb + eb_mn) / fabs(a) + UROUND * fabs(lo);
+                    hi = nmx_ == 0 ? (b - mxr) / a : INFINITY;  ebhi = (ebb + eb_mx) / fabs(a) + UROUND * fabs(hi);
                 }
                 if (isfin(s.l[j])) {
                     const double thr = s.l[j] - tol_at(ft, s.l[j]);
@@ -803,8 +821,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                 }
             }
             for (i = 0; i < m; i++) {
-                double a = 0.0, t;
-                const double b = s.L[i];
+                double a = 0.0, t, b;
                 int sel = 1;
                 if (rcand[i] < 0) continue;
                 j = rcand[i];
@@ -814,6 +831,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                     if (s.c[j] != 0.0 && fixed[kk] != 3 && cmin[kk] != i) sel = 0;
                 }
                 if (!sel) continue;
+                b = s5d_side(s.L[i], s.U[i], s.c[j], a);
                 t = s.c[j] / a;
                 if (out->sub_beg) out->sub_beg[s.rmap[i]] = sub_w;
                 if (out->sub_rhs) out->sub_rhs[s.rmap[i]] = b;
@@ -969,7 +987,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     free(mL); free(mU); free(ebmL); free(ebmU); free(hasf); free(alive); free(nrow); free(ncol);
     free(keys); free(qbuf); free(nrp); free(nci); free(nv);
     free(tcp); free(tri); free(tvl); free(tfill); free(calive); free(ckeys); free(cqbuf);
-    free(cs_cnt); free(cs_row); free(rcand); free(cmin); free(dlock); free(ulock);
+    free(cs_cnt); free(cs_row); free(rcand); free(cmin); free(cs_val); free(dlock); free(ulock);
     return status;
 oom:
     free(s.rp); free(s.ci); free(s.v); free(s.L); free(s.U); free(s.l); free(s.u); free(s.c);
@@ -979,7 +997,7 @@ oom:
     free(mL); free(mU); free(ebmL); free(ebmU); free(hasf); free(alive); free(nrow); free(ncol);
     free(keys); free(qbuf); free(nrp); free(nci); free(nv);
     free(tcp); free(tri); free(tvl); free(tfill); free(calive); free(ckeys); free(cqbuf);
-    free(cs_cnt); free(cs_row); free(rcand); free(cmin); free(dlock); free(ulock);
+    free(cs_cnt); free(cs_row); free(rcand); free(cmin); free(cs_val); free(dlock); free(ulock);
     return LPPO_ERR_OOM;
 }
 

@@ -2,8 +2,11 @@
 // opt-in).
 //
 // A column j with one entry in the round-start matrix, unfixed and unmerged,
-// whose row i is a kept equality a_ij x_j + sum_k a_ik x_k = b, is row i's
-// candidate (the smallest such column).  It is eliminated when it is free
+// in a kept row i with sides [L_i, U_i] reads the row as the equality
+// a_ij x_j + sum_k a_ik x_k = b at one side: the side its cost pushes a_ij x_j
+// to (L_i when c_j a_ij > 0, U_i when c_j a_ij < 0; L_i = U_i for an
+// equality), for c_j = 0 L_i if finite, else U_i.  With b finite it is a
+// candidate of row i, whose candidate is the smallest such column.  It is eliminated when it is free
 // or implied free: the range the row gives x_j under the current bounds of
 // the other columns,
 //   [(b - max rest) / a_ij, (b - min rest) / a_ij]   (ends swapped if a_ij < 0),
@@ -40,6 +43,13 @@ __device__ __forceinline__ bool s5d_skip(const Ctx &C, int32_t k, int32_t j) {
     return k == j || C.ckind[k] == CK_PARALLEL;
 }
 
+// the side b of row i that column j (coefficient a) is substituted at
+__device__ __forceinline__ double s5d_side(const Ctx &C, int32_t i, int32_t j, double a) {
+    const double cj = C.c[j];
+    if (cj != 0.0) return (cj > 0.0) == (a > 0.0) ? C.L[i] : C.U[i];
+    return is_fin(C.L[i]) ? C.L[i] : C.U[i];
+}
+
 // one column per thread: the singleton columns bid for their row
 __global__ void __launch_bounds__(kBlock) k_s5d_detect(Ctx C, int32_t *rcand) {
     const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -47,8 +57,7 @@ __global__ void __launch_bounds__(kBlock) k_s5d_detect(Ctx C, int32_t *rcand) {
     const int32_t b = C.T.ptr[j];
     if (C.T.ptr[j + 1] - b != 1 || C.ckind[j] != CK_KEPT) return;
     const int32_t i = C.T.idx[b];
-    const double L = C.L[i];
-    if (C.rkind[i] != RK_KEPT || !is_fin(L) || L != C.U[i]) return;
+    if (C.rkind[i] != RK_KEPT || !is_fin(s5d_side(C, i, j, C.T.val[b]))) return;
     atomicMin(&rcand[i], j);
 }
 
@@ -108,7 +117,7 @@ __global__ void __launch_bounds__(kBlock) k_s5d_check(Ctx C, const int32_t *rcan
         if (s5d_skip(C, k, j)) continue;
         s5d_term(C, k, C.A.val[q], mnr, mxr, nmn, nmx);
     }
-    if (!s5d_eligible(C, j, a, C.L[i], mnr, mxr, nmn, nmx)) return;
+    if (!s5d_eligible(C, j, a, s5d_side(C, i, j, a), mnr, mxr, nmn, nmx)) return;
     relig[i] = 1;
     if (C.c[j] == 0.0) return;  // changes no cost: no bid
     for (int32_t q = beg; q < end; q++) {
@@ -171,7 +180,7 @@ __global__ void __launch_bounds__(kTaskThreads) k_s5d_check_long(Ctx C, const in
         mxr = block_sum_ordered(mxr, s_d);
         nmn = block_sum_ordered(nmn, s_i);
         nmx = block_sum_ordered(nmx, s_i);
-        const bool ok = s5d_eligible(C, j, s_a, C.L[i], mnr, mxr, nmn, nmx);  // the same in every thread
+        const bool ok = s5d_eligible(C, j, s_a, s5d_side(C, i, j, s_a), mnr, mxr, nmn, nmx);  // block-uniform
         if (ok) {
             if (threadIdx.x == 0) relig[i] = 1;
             if (C.c[j] != 0.0) {  // changes a cost: bid
@@ -227,7 +236,7 @@ __global__ void __launch_bounds__(kBlock) k_s5d_apply(Ctx C, const int32_t *rcan
                 cnt++;
             }
             if (sel) {
-                const double b = C.L[i], t = C.c[j] / a;
+                const double b = s5d_side(C, i, j, a), t = C.c[j] / a;
                 unsigned long long pos = atomicAdd(C.sub_used, (unsigned long long)cnt);
                 s5d_record(C, i, j, a, b, pos, cnt);
                 for (int32_t q = beg; q < end; q++) {
@@ -275,7 +284,7 @@ __global__ void __launch_bounds__(kTaskThreads) k_s5d_apply_long(Ctx C, const in
         sel = __syncthreads_and(sel) != 0;
         cnt = block_sum_ordered(cnt, s_w);
         if (!sel) continue;
-        const double a = s_a, b = C.L[i], tj = C.c[j] / a;
+        const double a = s_a, b = s5d_side(C, i, j, a), tj = C.c[j] / a;
         if (threadIdx.x == 0) {
             s_pos = atomicAdd(C.sub_used, (unsigned long long)cnt);
             s5d_record(C, i, j, a, b, s_pos, cnt);
@@ -354,7 +363,7 @@ __global__ void __launch_bounds__(kBlock) k_s5d_chunk_elig(Ctx C, const int32_t 
     mxr = group_sum<32>(mxr, 0xffffffffu);
     nmn = group_sum<32>(nmn, 0xffffffffu);
     nmx = group_sum<32>(nmx, 0xffffffffu);
-    if (lane == 0 && s5d_eligible(C, j, cs_a[i], C.L[i], mnr, mxr, nmn, nmx)) relig[i] = 1;
+    if (lane == 0 && s5d_eligible(C, j, cs_a[i], s5d_side(C, i, j, cs_a[i]), mnr, mxr, nmn, nmx)) relig[i] = 1;
 }
 
 // per chunk of an eligible row whose column costs something: the bids
@@ -427,7 +436,7 @@ __global__ void __launch_bounds__(kBlock) k_s5d_chunk_row(Ctx C, const int32_t *
                 if (lane == 0) {
                     pos = atomicAdd(C.sub_used, (unsigned long long)carry);
                     const int32_t j = rcand[i];
-                    s5d_record(C, i, j, cs_a[i], C.L[i], pos, carry);
+                    s5d_record(C, i, j, cs_a[i], s5d_side(C, i, j, cs_a[i]), pos, carry);
                     relig[i] = 2;  // applied: the chunks write their entries
                 }
                 pos = __shfl_sync(0xffffffffu, pos, 0);

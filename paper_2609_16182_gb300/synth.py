@@ -578,9 +578,10 @@ def plant_parallel_cols(lp: LP, seed: int, frac: float = 0.01) -> LP:
 
 
 def plant_col_singletons(lp: LP, seed: int, frac: float = 0.5, free_frac: float = 0.5, box: float = 50.0,
-                         cost_scale: float = 1.0) -> LP:
+                         cost_scale: float = 1.0, rows: str = "eq") -> LP:
     """`lp` with a column singleton appended to a random `frac` of its
-    non-empty equality rows: one entry (U[-5, 5], |a| >= 0.01),
+    non-empty equality rows (rows="any": of its non-empty rows with a finite
+    side): one entry (U[-5, 5], |a| >= 0.01),
     free with probability `free_frac`, else bounds [-box, box], cost
     cost_scale * N(0, 1) (a nonzero cost moves onto the row's other columns
     when the singleton is eliminated; on LPs with infinite bounds that can
@@ -588,7 +589,10 @@ def plant_col_singletons(lp: LP, seed: int, frac: float = 0.5, free_frac: float 
     x0 extended by zeros still satisfies the sides.  Vectorised."""
     rng = np.random.default_rng(seed)
     lens = np.diff(lp.row_ptr.astype(np.int64))
-    eq = np.isfinite(lp.lhs) & (lp.lhs == lp.rhs) & (lens >= 1)
+    if rows == "eq":
+        eq = np.isfinite(lp.lhs) & (lp.lhs == lp.rhs) & (lens >= 1)
+    else:
+        eq = (np.isfinite(lp.lhs) | np.isfinite(lp.rhs)) & (lens >= 1)
     cand = np.flatnonzero(eq)
     p = min(len(cand), max(1, int(frac * len(cand)))) if len(cand) else 0
     rows_new = np.sort(rng.choice(cand, size=p, replace=False)) if p else np.zeros(0, np.int64)

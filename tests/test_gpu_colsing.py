@@ -32,16 +32,19 @@ def both(lp, **kw):
     return g, o
 
 
+@pytest.mark.parametrize("rows", ["eq", "any"])
 @pytest.mark.parametrize("seed", range(60))
-def test_micro_planted(seed):
-    lp = synth.plant_col_singletons(synth.micro(seed + 900), seed)
+def test_micro_planted(seed, rows):
+    # rows="any": singletons in inequality rows too (substituted at the side their cost selects)
+    lp = synth.plant_col_singletons(synth.micro(seed + 900), seed, rows=rows)
     g, o = both(lp)
     compare(g, o, lp)
 
 
+@pytest.mark.parametrize("rows", ["eq", "any"])
 @pytest.mark.parametrize("seed", range(6))
-def test_tiny_planted(seed):
-    lp = synth.plant_col_singletons(synth.tiny(seed), seed)
+def test_tiny_planted(seed, rows):
+    lp = synth.plant_col_singletons(synth.tiny(seed), seed, rows=rows)
     g, o = both(lp)
     if o.audit_below_1e3:
         pytest.skip("instance has a decision within 1000x of its error bound")
@@ -74,6 +77,15 @@ def test_skewed_boxed_costly_singletons(seed):
     g, o = both(lp)
     compare(g, o, lp)
     assert np.count_nonzero(g.row_kind == lpp.ROW_SUBST) > 1000
+
+
+def test_inequality_row_sides():
+    for c2, subst in ((-1.0, True), (1.0, False), (0.0, True)):
+        lp = make([{0: 1.0, 1: 1.0, 2: 1.0}, {0: 1.0, 1: 1.0}], [-INF, -INF], [4.0, 3.0],
+                  [0.0, 0.0, -INF], [2.0, 2.0, INF], c=[1.0, 2.0, c2])
+        g, o = both(lp, max_rounds=1)
+        compare(g, o, lp)
+        assert (g.row_kind[0] == lpp.ROW_SUBST) == subst
 
 
 def test_one_substitution_per_column_and_round():

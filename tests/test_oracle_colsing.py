@@ -47,6 +47,31 @@ def test_implied_free(lo, hi, eliminated):
     assert (res.col_kind[2] == oracle.COL_SUBST) == eliminated
 
 
+def test_inequality_rows_at_the_side_the_cost_selects():
+    # row 0: x0 + x1 + x2 <= 4 with x2 free and only there.  c2 = -1 pushes x2 (a = 1) up: the row
+    # is tight at 4 in an optimum, x2 = 4 - x0 - x1: costs 1 + 1 and 2 + 1, constant -4
+    lp = make([{0: 1.0, 1: 1.0, 2: 1.0}, {0: 1.0, 1: 1.0}], [-INF, -INF], [4.0, 3.0],
+              [0.0, 0.0, -INF], [2.0, 2.0, INF], c=[1.0, 2.0, -1.0])
+    res = oracle.presolve(lp, opts(max_rounds=1))
+    assert res.row_kind[0] == oracle.ROW_SUBST and res.sub_rhs[0] == 4.0
+    assert list(res.c) == [2.0, 3.0] and res.obj_offset == -4.0
+    # c2 = +1 pushes x2 down, to the side -inf: not a candidate
+    lp2 = make([{0: 1.0, 1: 1.0, 2: 1.0}, {0: 1.0, 1: 1.0}], [-INF, -INF], [4.0, 3.0],
+               [0.0, 0.0, -INF], [2.0, 2.0, INF], c=[1.0, 2.0, 1.0])
+    res2 = oracle.presolve(lp2, opts(max_rounds=1))
+    assert res2.row_kind[0] != oracle.ROW_SUBST
+    # cost 0: the finite side (rhs 4 here, the lhs being -inf)
+    lp3 = make([{0: 1.0, 1: 1.0, 2: 1.0}, {0: 1.0, 1: 1.0}], [-INF, -INF], [4.0, 3.0],
+               [0.0, 0.0, -INF], [2.0, 2.0, INF], c=[1.0, 2.0, 0.0])
+    res3 = oracle.presolve(lp3, opts(max_rounds=1))
+    assert res3.row_kind[0] == oracle.ROW_SUBST and res3.sub_rhs[0] == 4.0 and list(res3.c) == [1.0, 2.0]
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_any_row_optimum_kept_and_postsolve_optimal(seed):
+    test_optimum_kept_and_postsolve_optimal(seed, rows="any")
+
+
 def test_one_substitution_per_column_and_round():
     # rows 0 and 1 are equalities that share x0, each with a free singleton (x2, x3):
     # round 1 applies row 0 only, round 2 row 1
@@ -75,8 +100,8 @@ def test_off_by_default():
 
 
 @pytest.mark.parametrize("seed", range(60))
-def test_optimum_kept_and_postsolve_optimal(seed):
-    lp = synth.plant_col_singletons(synth.micro(seed + 900), seed)
+def test_optimum_kept_and_postsolve_optimal(seed, rows="eq"):
+    lp = synth.plant_col_singletons(synth.micro(seed + 900), seed, rows=rows)
     res = oracle.presolve(lp, opts())
     V = lp_vertices(lp)
     if len(V) == 0:
@@ -104,7 +129,7 @@ def test_optimum_kept_and_postsolve_optimal(seed):
 def test_reduced_optimum_matches_original_200_rows(seed):
     pytest.importorskip("scipy")
     from test_oracle_invariants import _linprog
-    lp = synth.plant_col_singletons(synth.tiny(seed), seed)
+    lp = synth.plant_col_singletons(synth.tiny(seed), seed, rows="any" if seed % 2 else "eq")
     res = oracle.presolve(lp, opts())
     assert res.status == oracle.OK
     assert np.count_nonzero(res.row_kind == oracle.ROW_SUBST) > 0
