@@ -16,8 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lpp_oracle.c")
 _LIB = os.path.join(_HERE, "liblpp_oracle.so")
 
-ROW_KEPT, ROW_EMPTY, ROW_REDUNDANT, ROW_SINGLETON, ROW_PARALLEL, ROW_SUBST = 0, 1, 2, 3, 4, 5
-COL_KEPT, COL_FIXED, COL_EMPTY, COL_PARALLEL, COL_SUBST = 0, 1, 2, 3, 4
+ROW_KEPT, ROW_EMPTY, ROW_REDUNDANT, ROW_SINGLETON, ROW_PARALLEL, ROW_SUBST, ROW_DOUBLETON = 0, 1, 2, 3, 4, 5, 6
+COL_KEPT, COL_FIXED, COL_EMPTY, COL_PARALLEL, COL_SUBST, COL_DOUBLETON = 0, 1, 2, 3, 4, 5
 OK, INFEASIBLE, UNBOUNDED, ERR_INVALID = 0, 1, 2, -1
 
 
@@ -43,7 +43,7 @@ class Opts(C.Structure):
     _fields_ = [("feas_tol", C.c_double), ("bound_tol", C.c_double), ("huge", C.c_double),
                 ("max_implied", C.c_double), ("par_tol", C.c_double), ("max_rounds", C.c_int32),
                 ("dual_reductions", C.c_int32), ("par_max_iter", C.c_int32), ("parallel_cols", C.c_int32),
-                ("col_singletons", C.c_int32), ("dual_fixing", C.c_int32)]
+                ("col_singletons", C.c_int32), ("dual_fixing", C.c_int32), ("doubletons", C.c_int32)]
 
 
 _OUT_FIELDS = [
@@ -260,15 +260,16 @@ def records(res: Result):
     """Postsolve records in canonical order (round, step, original index).
     Steps: 0 = row removed in S2, 1 = column fixed in S4, 2 = row merged in
     S5, 3 = column merged in S5c, 4 = row and column of a substitution in
-    S5d, 5 = column fixed in S6."""
+    S5d, 5 = row and column of a doubleton equation in S5e, 6 = column fixed
+    in S6."""
     recs = []
     for i in np.flatnonzero(res.row_kind != ROW_KEPT):
         k = int(res.row_kind[i])
-        step = {ROW_PARALLEL: 2, ROW_SUBST: 4}.get(k, 0)
+        step = {ROW_PARALLEL: 2, ROW_SUBST: 4, ROW_DOUBLETON: 5}.get(k, 0)
         recs.append((int(res.row_round[i]), step, int(i), "row", k, int(res.row_aux[i]), float(res.row_val[i])))
     for j in np.flatnonzero(res.col_kind != COL_KEPT):
         k = int(res.col_kind[j])
-        step = {COL_FIXED: 1, COL_PARALLEL: 3, COL_SUBST: 4}.get(k, 5)
+        step = {COL_FIXED: 1, COL_PARALLEL: 3, COL_SUBST: 4, COL_DOUBLETON: 5}.get(k, 6)
         aux = int(res.col_aux[j]) if k == COL_PARALLEL else -1
         recs.append((int(res.col_round[j]), step, int(j), "col", k, aux, float(res.col_val[j])))
     recs.sort(key=lambda t: (t[0], t[1], t[2]))

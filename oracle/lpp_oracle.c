@@ -58,6 +58,7 @@ void lppo_opts_default(lppo_opts *o)
     o->parallel_cols = 0;
     o->col_singletons = 0;
     o->dual_fixing = 0;
+    o->doubletons = 0;
 }
 
 /* ---------------------------------------------------------------- audit */
@@ -261,6 +262,8 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     int32_t *cs_cnt = NULL, *cs_row = NULL, *rcand = NULL, *cmin = NULL;  /* S5d */
     double *cs_val = NULL;
     int32_t *dlock = NULL, *ulock = NULL;                                   /* S6 locks */
+    int32_t *dminc = NULL, *dminr = NULL, *dk = NULL, *dmj = NULL, *dmk = NULL;  /* S5e */
+    double *dmd = NULL;
     int64_t sub_w = 0;
     double *tvl = NULL;
     ckey_t *ckeys = NULL;
@@ -303,6 +306,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     ALLOC(ckeys, n0); ALLOC(cqbuf, lp->nnz);
     ALLOC(cs_cnt, n0); ALLOC(cs_row, n0); ALLOC(rcand, m0); ALLOC(cmin, n0); ALLOC(cs_val, n0);
     ALLOC(dlock, n0); ALLOC(ulock, n0);
+    ALLOC(dminc, n0); ALLOC(dminr, m0); ALLOC(dk, m0); ALLOC(dmj, m0); ALLOC(dmk, m0); ALLOC(dmd, m0);
 
     for (i = 0; i < m0; i++) {
         out->row_kind[i] = LPPO_ROW_KEPT; out->row_round[i] = 0; out->row_aux[i] = -1; out->row_val[i] = 0.0;
@@ -854,6 +858,146 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
             }
         }
 
+        /* ---- S5e (opt-in): doubleton equations (Sec. 2.1, the doubleton-row
+               explorer).  A kept equality row i with two entries whose
+               columns are both unfixed, a x_j + b x_k = c, eliminates x_k,
+               the column with fewer entries in the round-start matrix (the
+               larger index on a tie): x_k = g - f x_j with f = a / b and
+               g = c / b.  Then
+                 x_j's bounds meet the range x_k's bounds give it,
+                   [(g - u_k) / f, (g - l_k) / f] (ends swapped for f < 0),
+                   crossing by more than the tolerance is infeasible, nearly
+                   equal bounds snap to their midpoint;
+                 c_j <- c_j - (c_k / b) a, and the constant c_k g goes to the
+                   objective (x_k takes the value g for the S7 offset sum);
+                 every other kept row r with x_k (coefficient a_rk) loses that
+                   entry and its sides a_rk g, and x_j's coefficient in r gains
+                   -(a_rk f): added to an existing entry (dropped when the sum
+                   is within par_tol of cancelling), else inserted;
+                 row i and column k leave the LP; the postsolve sets
+                   x_k = (c - a x_j) / b from a substitution record.
+               Doubletons of one round touch disjoint columns and rows: a row
+               applies only when it is the first candidate that claims each
+               of its two columns, itself and every row it changes. */
+        if (o->doubletons) {
+            int32_t napplied = 0;
+            for (j = 0; j <= n; j++) tcp[j] = 0;
+            for (k = 0; k < nnz; k++) tcp[s.ci[k] + 1]++;
+            for (j = 0; j < n; j++) tcp[j + 1] += tcp[j];
+            for (j = 0; j < n; j++) { tfill[j] = tcp[j]; dminc[j] = m; }
+            for (i = 0; i < m; i++)
+                for (k = s.rp[i]; k < s.rp[i + 1]; k++) {
+                    const int32_t jj = s.ci[k];
+                    tri[tfill[jj]] = i; tvl[tfill[jj]] = s.v[k]; tfill[jj]++;
+                }
+            for (i = 0; i < m; i++) { dminr[i] = m; dk[i] = -1; dmj[i] = -1; }
+            /* candidates and their claims */
+            for (i = 0; i < m; i++) {
+                int32_t c0, c1, kk, q;
+                if (kind[i] != LPPO_ROW_KEPT || s.rp[i + 1] - s.rp[i] != 2) continue;
+                if (!isfin(s.L[i]) || s.L[i] != s.U[i]) continue;
+                c0 = s.ci[s.rp[i]]; c1 = s.ci[s.rp[i] + 1];
+                if (fixed[c0] || fixed[c1]) continue;
+                kk = tcp[c1 + 1] - tcp[c1] <= tcp[c0 + 1] - tcp[c0] ? c1 : c0;
+                dk[i] = kk;
+                if (i < dminc[c0]) dminc[c0] = i;
+                if (i < dminc[c1]) dminc[c1] = i;
+                for (q = tcp[kk]; q < tcp[kk + 1]; q++) {
+                    const int32_t rr = tri[q];
+                    if ((rr == i || kind[rr] == LPPO_ROW_KEPT) && i < dminr[rr]) dminr[rr] = i;
+                }
+            }
+            /* apply, in row order, the rows first in every claim */
+            for (i = 0; i < m && bad < 0; i++) {
+                int32_t kk, jj, q, sel = 1;
+                double a, b, c, f, g, t, lo, hi, nl, nu;
+                if (dk[i] < 0) continue;
+                kk = dk[i];
+                jj = s.ci[s.rp[i]] == kk ? s.ci[s.rp[i] + 1] : s.ci[s.rp[i]];
+                a = s.ci[s.rp[i]] == jj ? s.v[s.rp[i]] : s.v[s.rp[i] + 1];
+                b = s.ci[s.rp[i]] == kk ? s.v[s.rp[i]] : s.v[s.rp[i] + 1];
+                c = s.L[i];
+                if (dminc[jj] != i || dminc[kk] != i || dminr[i] != i) sel = 0;
+                for (q = tcp[kk]; q < tcp[kk + 1] && sel; q++) {
+                    const int32_t rr = tri[q];
+                    if (rr != i && kind[rr] == LPPO_ROW_KEPT && dminr[rr] != i) sel = 0;
+                }
+                if (!sel) continue;
+                f = a / b; g = c / b;
+                if (f > 0) {
+                    lo = isfin(s.u[kk]) ? (g - s.u[kk]) / f : -INFINITY;
+                    hi = isfin(s.l[kk]) ? (g - s.l[kk]) / f : INFINITY;
+                } else {
+                    lo = isfin(s.l[kk]) ? (g - s.l[kk]) / f : -INFINITY;
+                    hi = isfin(s.u[kk]) ? (g - s.u[kk]) / f : INFINITY;
+                }
+                nl = lo > s.l[jj] ? lo : s.l[jj];
+                nu = hi < s.u[jj] ? hi : s.u[jj];
+                if (isfin(nl) && isfin(nu)) {
+                    const double d = ft * dmax(1.0, dmax(fabs(nl), fabs(nu)));
+                    if (nl - nu > d) { bad = jj; break; }
+                    if (nl > nu) nl = nu = 0.5 * (nl + nu);
+                }
+                if (nl != s.l[jj] || nu != s.u[jj]) bchanged++;
+                s.l[jj] = nl; s.u[jj] = nu;
+                t = s.c[kk] / b;
+                s.c[jj] = s.c[jj] - t * a;
+                /* the other rows of x_k: side shift now, coefficient change in the rebuild */
+                for (q = tcp[kk]; q < tcp[kk + 1]; q++) {
+                    const int32_t rr = tri[q];
+                    const double ark = tvl[q];
+                    if (rr == i || kind[rr] != LPPO_ROW_KEPT) continue;
+                    if (isfin(s.L[rr])) s.L[rr] = s.L[rr] - ark * g;
+                    if (isfin(s.U[rr])) s.U[rr] = s.U[rr] - ark * g;
+                    dmj[rr] = jj; dmk[rr] = kk; dmd[rr] = -(ark * f);
+                }
+                kind[i] = LPPO_ROW_DOUBLETON;
+                out->row_kind[s.rmap[i]] = LPPO_ROW_DOUBLETON; out->row_round[s.rmap[i]] = r;
+                out->row_aux[s.rmap[i]] = s.cmap[kk]; out->row_val[s.rmap[i]] = b;
+                if (out->sub_beg) out->sub_beg[s.rmap[i]] = sub_w;
+                if (out->sub_len) out->sub_len[s.rmap[i]] = 1;
+                if (out->sub_rhs) out->sub_rhs[s.rmap[i]] = c;
+                if (out->sub_col) { out->sub_col[sub_w] = s.cmap[jj]; out->sub_val[sub_w] = a; }
+                sub_w++;
+                removed++;
+                fixed[kk] = 5; fixv[kk] = g;
+                out->col_kind[s.cmap[kk]] = LPPO_COL_DOUBLETON; out->col_round[s.cmap[kk]] = r;
+                out->col_val[s.cmap[kk]] = g;
+                nfixed++;
+                napplied++;
+            }
+            if (bad >= 0) {
+                status = LPPO_INFEASIBLE; out->where = LPPO_WHERE_COL; out->index = s.cmap[bad]; out->round = r;
+                break;
+            }
+            /* the changed rows: x_k out, x_j's coefficient added or inserted */
+            if (napplied) {
+                int64_t w = 0;
+                for (i = 0; i < m; i++) {
+                    const int32_t jj = dmj[i], kk = dmk[i];
+                    int placed = jj < 0;
+                    nrp[i] = (int32_t)w;
+                    for (k = s.rp[i]; k < s.rp[i + 1]; k++) {
+                        const int32_t col = s.ci[k];
+                        if (jj >= 0 && col == kk) continue;
+                        if (!placed && col > jj) { nci[w] = jj; nv[w] = dmd[i]; w++; placed = 1; }
+                        if (jj >= 0 && col == jj) {
+                            const double v = s.v[k] + dmd[i];
+                            placed = 1;
+                            if (fabs(v) <= o->par_tol * dmax(fabs(s.v[k]), fabs(dmd[i]))) continue;
+                            nci[w] = jj; nv[w] = v; w++;
+                            continue;
+                        }
+                        nci[w] = col; nv[w] = s.v[k]; w++;
+                    }
+                    if (!placed) { nci[w] = jj; nv[w] = dmd[i]; w++; }
+                }
+                nrp[m] = (int32_t)w;
+                memcpy(s.rp, nrp, sizeof(int32_t) * (size_t)(m + 1));
+                if (w > 0) { memcpy(s.ci, nci, sizeof(int32_t) * (size_t)w); memcpy(s.v, nv, sizeof(double) * (size_t)w); }
+            }
+        }
+
         /* ---- S6: a column with no entry left in a kept row is fixed at the
                bound its cost prefers (dual reduction).  With dual_fixing, a
                column is fixed so when no kept row locks it in that direction
@@ -988,6 +1132,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     free(keys); free(qbuf); free(nrp); free(nci); free(nv);
     free(tcp); free(tri); free(tvl); free(tfill); free(calive); free(ckeys); free(cqbuf);
     free(cs_cnt); free(cs_row); free(rcand); free(cmin); free(cs_val); free(dlock); free(ulock);
+    free(dminc); free(dminr); free(dk); free(dmj); free(dmk); free(dmd);
     return status;
 oom:
     free(s.rp); free(s.ci); free(s.v); free(s.L); free(s.U); free(s.l); free(s.u); free(s.c);
@@ -998,6 +1143,7 @@ oom:
     free(keys); free(qbuf); free(nrp); free(nci); free(nv);
     free(tcp); free(tri); free(tvl); free(tfill); free(calive); free(ckeys); free(cqbuf);
     free(cs_cnt); free(cs_row); free(rcand); free(cmin); free(cs_val); free(dlock); free(ulock);
+    free(dminc); free(dminr); free(dk); free(dmj); free(dmk); free(dmd);
     return LPPO_ERR_OOM;
 }
 
@@ -1038,7 +1184,8 @@ int lppo_postsolve_primal(int32_t n_orig, int32_t n_red, const int32_t *col_map,
         x_orig[col_map[j]] = x_red[j];
     }
     for (j = 0; j < n_orig; j++) if (col_kind[j] == LPPO_COL_PARALLEL) ne++;
-    for (i = 0; i < m_orig && row_kind; i++) if (row_kind[i] == LPPO_ROW_SUBST) ne++;
+    for (i = 0; i < m_orig && row_kind; i++)
+        if (row_kind[i] == LPPO_ROW_SUBST || row_kind[i] == LPPO_ROW_DOUBLETON) ne++;
     if (ne == 0) return LPPO_OK;
     ev = malloc(sizeof(pevent_t) * (size_t)ne);
     if (!ev) return LPPO_ERR_OOM;
@@ -1049,13 +1196,13 @@ int lppo_postsolve_primal(int32_t n_orig, int32_t n_red, const int32_t *col_map,
             ev[ne].round = col_round[j]; ev[ne].step = 0; ev[ne].index = j; ne++;
         }
     for (i = 0; i < m_orig && row_kind; i++)
-        if (row_kind[i] == LPPO_ROW_SUBST) {
+        if (row_kind[i] == LPPO_ROW_SUBST || row_kind[i] == LPPO_ROW_DOUBLETON) {
             if (!row_round || !row_aux || !row_val || !sub_beg || !sub_len || !sub_rhs || !sub_col || !sub_val) {
                 free(ev); return LPPO_ERR_INVALID;
             }
-            ev[ne].round = row_round[i]; ev[ne].step = 1; ev[ne].index = i; ne++;
+            ev[ne].round = row_round[i]; ev[ne].step = row_kind[i] == LPPO_ROW_SUBST ? 1 : 2; ev[ne].index = i; ne++;
         }
-    /* latest first: round, then S5d (after S5c in a round), then index */
+    /* latest first: round, then S5e, S5d, S5c (their order in a round), then index */
     qsort(ev, (size_t)ne, sizeof(pevent_t), later_first);
     for (a = 0; a < ne; a++) {
         if (ev[a].step == 0) {

@@ -39,12 +39,14 @@ extern "C" {
 #define LPPO_ROW_SINGLETON  3
 #define LPPO_ROW_PARALLEL   4
 #define LPPO_ROW_SUBST      5   /* used to eliminate a column singleton (opt-in) */
+#define LPPO_ROW_DOUBLETON  6   /* doubleton equation used to eliminate a column (opt-in) */
 /* per-original-column record kinds */
 #define LPPO_COL_KEPT       0
 #define LPPO_COL_FIXED      1   /* lb == ub after tightening (primal)        */
 #define LPPO_COL_EMPTY      2   /* no entry left, fixed by the cost (dual)    */
 #define LPPO_COL_PARALLEL   3   /* merged into a parallel column (opt-in)      */
 #define LPPO_COL_SUBST      4   /* free column singleton, eliminated (opt-in)   */
+#define LPPO_COL_DOUBLETON  5   /* eliminated through a doubleton equation (opt-in) */
 
 /* where an infeasible / unbounded verdict was found */
 #define LPPO_WHERE_NONE 0
@@ -74,6 +76,7 @@ typedef struct {
     int32_t col_singletons; /* 0: S5d (free column singletons) off */
     int32_t dual_fixing;   /* 0: S6 fixes empty columns only; 1: every column without a lock
                               in the direction its cost prefers (needs dual_reductions) */
+    int32_t doubletons;    /* 0: S5e (doubleton equations) off */
 } lppo_opts;
 
 /* All arrays are allocated by the caller with the sizes given. */
@@ -126,7 +129,8 @@ int  lppo_activities(const lppo_lp *lp, double huge, double *act_min, double *ac
 
 /* Primal postsolve (Sec. 2.1, postsolver paragraph): x_orig from x_red.
    Fixed columns take their value; merges and substitutions are undone
-   latest first (round, then S5d before S5c, then index, all descending).
+   latest first (round, then S5e before S5d before S5c, then index, all
+   descending).  Doubleton rows use the substitution records.
    The merge records (col_aux, col_pass, col_mrg) and the substitution
    records (row arrays and the store) may be NULL when none was made. */
 int  lppo_postsolve_primal(int32_t n_orig, int32_t n_red, const int32_t *col_map,

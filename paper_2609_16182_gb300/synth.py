@@ -611,6 +611,38 @@ def plant_col_singletons(lp: LP, seed: int, frac: float = 0.5, free_frac: float 
                    f"{getattr(lp, 'name', 'lp')}+colsing")
 
 
+def plant_doubletons(lp: LP, seed: int, count: int = 2, point=None) -> LP:
+    """`lp` with `count` doubleton equations appended: a x_j + b x_k = c on two
+    random columns with finite bounds (a, b U[-5, 5] with |.| >= 0.01), c set by
+    `point` (a feasible point of lp keeps it feasible) or else by a point drawn
+    inside both columns' bounds."""
+    rng = np.random.default_rng(seed)
+    boxed = np.flatnonzero(np.isfinite(lp.lb) & np.isfinite(lp.ub))
+    if len(boxed) < 2 or count <= 0:
+        return lp
+    rows = _row_of_entry(lp.row_ptr.astype(np.int64))
+    r2, c2, v2 = [rows], [lp.col_idx.astype(np.int64)], [lp.val]
+    lhs, rhs = list(lp.lhs), list(lp.rhs)
+    for t in range(count):
+        j, k = np.sort(rng.choice(boxed, size=2, replace=False))
+        a, b = _draw_magnitudes(rng, 2, -5.0, 5.0)
+        v = lp.lb[[j, k]] + (lp.ub[[j, k]] - lp.lb[[j, k]]) * rng.random(2)
+        if point is not None:
+            v = np.asarray(point, float)[[j, k]]
+        c = a * v[0] + b * v[1]
+        r2.append(np.array([lp.m + t, lp.m + t]))
+        c2.append(np.array([j, k]))
+        v2.append(np.array([a, b]))
+        lhs.append(c)
+        rhs.append(c)
+    m = lp.m + count
+    ptr, cc, vv = _sort_rows(np.concatenate(r2), np.concatenate(c2), np.concatenate(v2), m)
+    planted = dict(getattr(lp, "planted", None) or {})
+    planted.update(doubleton_rows=np.arange(lp.m, m))
+    return _finish(m, lp.n, ptr, cc, vv, lp.c.copy(), np.array(lhs), np.array(rhs), lp.lb.copy(), lp.ub.copy(),
+                   planted, f"{getattr(lp, 'name', 'lp')}+doubletons")
+
+
 # ----------------------------------------------------- vectorised 200-row mix
 def _distinct_columns(rng, lengths, n, pool=None):
     """Columns for rows of the given lengths, distinct inside each row, drawn
