@@ -178,8 +178,10 @@ lpp_status lpp_reduced_maps(lpp_reduced *red, const int32_t **row_map, const int
 
 lpp_status lpp_result_info(const lpp_postsolve *rec, lpp_info *info);
 /* Per original row (host arrays of m): record kind, round, aux (singleton:
- * its column; parallel: its leader row, original indices; else -1), value
- * (singleton: its coefficient; parallel: lambda with row = lambda * leader). */
+ * its column; parallel: its leader row; substitution: the eliminated column;
+ * original indices; else -1), value (singleton: its coefficient; parallel:
+ * lambda with row = lambda * leader; substitution: the eliminated column's
+ * coefficient). */
 lpp_status lpp_result_rows(const lpp_postsolve *rec, int32_t *kind, int32_t *round, int32_t *aux, double *val);
 /* Per original column (host arrays of n): kind, round, value, and the final
  * bounds.  A fixed or empty column reports its value as both bounds; a
