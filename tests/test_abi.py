@@ -37,3 +37,46 @@ def test_options_defaults_through_the_abi():
     assert (o.max_rounds, o.dual_reductions, o.par_max_iter, o.timing, o.device) == (20, 1, 16, 0, 0)
     with pytest.raises(TypeError):
         lpp.opts(no_such_option=1)
+
+
+def struct_fields(path, name):
+    """Field names of `typedef struct { ... } name;` (or `typedef struct name {...} name;`), in order."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    m = re.search(r"typedef struct(?:\s+\w+)?\s*\{([^{}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        if not decl.strip():
+            continue
+        # the declarator of each comma-separated part is its last identifier
+        for part in decl.split(","):
+            ids = re.findall(r"[A-Za-z_]\w*", part)
+            if ids:
+                fields.append(ids[-1])
+    return fields
+
+
+def test_ctypes_mirrors_match_the_c_structs():
+    # the bindings pass these structs by pointer: a field missing or out of order corrupts memory
+    from paper_2609_16182_gb300 import lpp
+    import oracle
+    h = os.path.join(ROOT, "include", "lpp.h")
+    assert [f for f, _ in lpp.Opts._fields_] == struct_fields(h, "lpp_opts")
+    assert [f for f, _ in lpp.LpStruct._fields_] == struct_fields(h, "lpp_lp")
+    assert [f for f, _ in lpp.Info._fields_] == struct_fields(h, "lpp_info")
+    assert [f for f, _ in lpp.KernelStat._fields_] == struct_fields(h, "lpp_kernel_stat")
+    assert [f for f, _ in lpp.ServerStats._fields_] == struct_fields(h, "lpp_server_stats")
+    oh = os.path.join(ROOT, "oracle", "lpp_oracle.h")
+    assert [f for f, _ in oracle.Opts._fields_] == struct_fields(oh, "lppo_opts")
+    assert [f for f, _ in oracle._Out._fields_] == struct_fields(oh, "lppo_out")
+    assert [f for f, _ in oracle._LP._fields_] == struct_fields(oh, "lppo_lp")
+
+
+def test_opt_in_steps_default_off():
+    from paper_2609_16182_gb300 import lpp
+    import oracle
+    o = lpp.opts()
+    assert (o.parallel_cols, o.col_singletons, o.dual_fixing) == (0, 0, 0)
+    q = oracle.default_opts()
+    assert (q.parallel_cols, q.col_singletons, q.dual_fixing, q.doubletons) == (0, 0, 0, 0)
