@@ -19,6 +19,7 @@ _LIB = os.path.join(_HERE, "liblpp_oracle.so")
 ROW_KEPT, ROW_EMPTY, ROW_REDUNDANT, ROW_SINGLETON, ROW_PARALLEL, ROW_SUBST, ROW_DOUBLETON = 0, 1, 2, 3, 4, 5, 6
 COL_KEPT, COL_FIXED, COL_EMPTY, COL_PARALLEL, COL_SUBST, COL_DOUBLETON = 0, 1, 2, 3, 4, 5
 OK, INFEASIBLE, UNBOUNDED, ERR_INVALID = 0, 1, 2, -1
+WHERE_NONE, WHERE_ROW, WHERE_COL = 0, 1, 2
 
 
 def build(force: bool = False) -> str:

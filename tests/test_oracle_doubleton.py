@@ -56,6 +56,28 @@ def test_cancellation_drops_the_entry():
     assert res.row_kind[1] != oracle.ROW_KEPT or 0 not in row_of(res, 1)[0]
 
 
+def test_doubletons_sharing_a_column_wait_a_round():
+    # rows 0 and 1 are doubletons on x0 (x1 and x2 are eliminated, fewer entries): they claim x0 both,
+    # so row 0 applies in round 1 and row 1 in round 2
+    lp = make([{0: 1.0, 1: 1.0}, {0: 2.0, 2: 1.0}, {0: 1.0, 3: 1.0}, {0: 1.0, 3: -1.0}],
+              [1.0, 3.0, -INF, -INF], [1.0, 3.0, 5.0, 5.0],
+              [0.0, 0.0, 0.0, 0.0], [1.0, 1.0, 2.0, 2.0], c=[1.0, 1.0, 1.0, 1.0])
+    res = oracle.presolve(lp, opts(dual_reductions=0))
+    assert list(res.row_kind[:2]) == [oracle.ROW_DOUBLETON] * 2
+    assert list(res.row_round[:2]) == [1, 2]
+    assert list(res.col_kind[1:3]) == [oracle.COL_DOUBLETON] * 2
+
+
+def test_an_empty_bound_transfer_is_found_by_s2_first():
+    # x0 + x1 = 10 with x1 in [0, 1] would force x0 into [9, 10], but x0 <= 2.  A two-entry row's
+    # activity range is exactly the condition for the transferred range to meet x_j's bounds, so
+    # S2's activity test reports the row (round 1) before S5e runs
+    lp = make([{0: 1.0, 1: 1.0}, {0: 1.0, 2: 1.0}, {0: 1.0, 2: -1.0}], [10.0, -INF, -INF], [10.0, 50.0, 50.0],
+              [0.0, 0.0, 0.0], [2.0, 1.0, 1.0], c=[1.0, 1.0, 1.0])
+    res = oracle.presolve(lp, opts())
+    assert (res.status, res.where, res.index, res.round) == (oracle.INFEASIBLE, oracle.WHERE_ROW, 0, 1)
+
+
 def test_off_by_default():
     lp = synth.lprelax(1, m=600, n=1200, target_nnz=9_600, n_dense=1, dense_len=200)
     assert not np.any(oracle.presolve(lp).row_kind == oracle.ROW_DOUBLETON)
