@@ -907,8 +907,10 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                     if ((rr == i || kind[rr] == LPPO_ROW_KEPT) && i < dminr[rr]) dminr[rr] = i;
                 }
             }
-            /* apply, in row order, the rows first in every claim */
-            for (i = 0; i < m && bad < 0; i++) {
+            /* apply, in row order, the rows first in every claim; an empty
+               bound transfer makes the LP infeasible at the smallest original
+               column index among those of the round (as S3 reports) */
+            for (i = 0; i < m; i++) {
                 int32_t kk, jj, q, sel = 1;
                 double a, b, c, f, g, t, lo, hi, nl, nu;
                 if (dk[i] < 0) continue;
@@ -935,7 +937,10 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                 nu = hi < s.u[jj] ? hi : s.u[jj];
                 if (isfin(nl) && isfin(nu)) {
                     const double d = ft * dmax(1.0, dmax(fabs(nl), fabs(nu)));
-                    if (nl - nu > d) { bad = jj; break; }
+                    if (nl - nu > d) {
+                        if (bad < 0 || s.cmap[jj] < s.cmap[bad]) bad = jj;
+                        continue;
+                    }
                     if (nl > nu) nl = nu = 0.5 * (nl + nu);
                 }
                 if (nl != s.l[jj] || nu != s.u[jj]) bchanged++;

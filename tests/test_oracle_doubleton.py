@@ -78,6 +78,29 @@ def test_an_empty_bound_transfer_is_found_by_s2_first():
     assert (res.status, res.where, res.index, res.round) == (oracle.INFEASIBLE, oracle.WHERE_ROW, 0, 1)
 
 
+def test_empty_bound_transfer_after_tightening():
+    # x0 in [8.999995, 100]; row 0 (x0 + x1 = 10, x1 in [0, 1]) implies l0 >= 9, a gain below
+    # bound_tol * 9, which S3 rejects; row 1 tightens u0 to 8.999998 in the same round.  S5e maps
+    # x1's range onto x0, [9, 10], which misses [8.999995, 8.999998] by 2e-6 > feas_tol * 9:
+    # infeasible at column 0 in round 1.  Without S5e, S2 finds row 0 in round 2.
+    lp = make([{0: 1.0, 1: 1.0}, {0: 1.0, 2: 1.0}], [10.0, -INF], [10.0, 8.999998],
+              [8.999995, 0.0, 0.0], [100.0, 1.0, 1.0], c=[1.0, 1.0, 1.0])
+    res = oracle.presolve(lp, opts())
+    assert (res.status, res.where, res.index, res.round) == (oracle.INFEASIBLE, oracle.WHERE_COL, 0, 1)
+    res = oracle.presolve(lp, oracle.default_opts())
+    assert (res.status, res.where, res.index, res.round) == (oracle.INFEASIBLE, oracle.WHERE_ROW, 0, 2)
+
+
+def test_two_empty_transfers_report_the_smaller_column():
+    # the construction above twice: row 0 moves x3's range onto x2, row 1 x1's onto x0; both
+    # miss.  The verdict names the smaller original column (0), not the first row's (2)
+    lp = make([{2: 1.0, 3: 1.0}, {0: 1.0, 1: 1.0}, {2: 1.0, 4: 1.0}, {0: 1.0, 5: 1.0}],
+              [10.0, 10.0, -INF, -INF], [10.0, 10.0, 8.999998, 8.999998],
+              [8.999995, 0.0, 8.999995, 0.0, 0.0, 0.0], [100.0, 1.0, 100.0, 1.0, 1.0, 1.0], c=[1.0] * 6)
+    res = oracle.presolve(lp, opts())
+    assert (res.status, res.where, res.index, res.round) == (oracle.INFEASIBLE, oracle.WHERE_COL, 0, 1)
+
+
 def test_off_by_default():
     lp = synth.lprelax(1, m=600, n=1200, target_nnz=9_600, n_dense=1, dense_len=200)
     assert not np.any(oracle.presolve(lp).row_kind == oracle.ROW_DOUBLETON)
