@@ -24,6 +24,9 @@
  *   S5d free column singletons eliminated through their row, read as the
  *       equality at the side the column's cost selects (Sec. 3.2, column
  *       singletons; only with opts.col_singletons = 1)
+ *   S5e doubleton equations a x_j + b x_k = c: x_k = (c - a x_j) / b is
+ *       substituted into x_k's other rows and x_j takes over its bounds and
+ *       cost (Sec. 2.1, doubleton rows; opts.doubletons, not enabled yet)
  *   S6  empty columns fixed at the bound their cost prefers (dual rule); with
  *       opts.dual_fixing every column no kept row locks in that direction
  *   S7  compaction of the CSR and CSC matrices and of all row/column vectors
@@ -76,6 +79,7 @@ typedef enum lpp_status {
 #define LPP_ROW_SINGLETON 3   /* one entry: turned into a bound on that column    */
 #define LPP_ROW_PARALLEL 4    /* a multiple of a leader row, sides merged into it */
 #define LPP_ROW_SUBST 5       /* an equality row used to eliminate a column singleton */
+#define LPP_ROW_DOUBLETON 6   /* an equality a x_j + b x_k = c used to eliminate x_k  */
 /* Per-original-column record kinds. */
 #define LPP_COL_KEPT 0
 #define LPP_COL_FIXED 1       /* lb == ub: fixed at that value (primal)           */
@@ -83,6 +87,7 @@ typedef enum lpp_status {
                                  with opts.dual_fixing no lock in that direction  */
 #define LPP_COL_PARALLEL 3    /* merged into a parallel leader column (S5c)       */
 #define LPP_COL_SUBST 4       /* free column singleton eliminated (S5d)           */
+#define LPP_COL_DOUBLETON 5   /* eliminated through a doubleton equation (S5e)    */
 /* Where a verdict was found. */
 #define LPP_WHERE_NONE 0
 #define LPP_WHERE_ROW 1
@@ -121,6 +126,9 @@ typedef struct lpp_opts {
                                        lpp_presolve and lpp_presolve_batch only               */
     int32_t dual_fixing;    /* [0]     1: S6 fixes every column no kept row locks in the
                                        direction its cost prefers (dual fixing by locks)      */
+    int32_t doubletons;     /* [0]     1: eliminate a column of each doubleton equation (S5e,
+                                       Sec. 2.1); the device step is not enabled yet: any
+                                       call with 1 returns LPP_ERR_INVALID                    */
     int32_t timing;         /* [0]     1: time every kernel launch with CUDA events           */
     int32_t device;         /* [0]     CUDA device ordinal                                   */
     void *stream;           /* [NULL]  cudaStream_t to run on; NULL: a library-owned stream  */
@@ -178,17 +186,18 @@ lpp_status lpp_reduced_maps(lpp_reduced *red, const int32_t **row_map, const int
 
 lpp_status lpp_result_info(const lpp_postsolve *rec, lpp_info *info);
 /* Per original row (host arrays of m): record kind, round, aux (singleton:
- * its column; parallel: its leader row; substitution: the eliminated column;
- * original indices; else -1), value (singleton: its coefficient; parallel:
- * lambda with row = lambda * leader; substitution: the eliminated column's
- * coefficient). */
+ * its column; parallel: its leader row; substitution or doubleton: the
+ * eliminated column; original indices; else -1), value (singleton: its
+ * coefficient; parallel: lambda with row = lambda * leader; substitution or
+ * doubleton: the eliminated column's coefficient). */
 lpp_status lpp_result_rows(const lpp_postsolve *rec, int32_t *kind, int32_t *round, int32_t *aux, double *val);
 /* Per original column (host arrays of n): kind, round, value, and the final
  * bounds.  A fixed or empty column reports its value as both bounds; a
  * merged column (LPP_COL_PARALLEL) reports lambda as its value and NaN
  * bounds (its range lives on in the leader's); an eliminated singleton
  * (LPP_COL_SUBST) reports b / a_ij as its value and NaN bounds (its value
- * comes from the postsolve). */
+ * comes from the postsolve); so does a column eliminated through a
+ * doubleton (LPP_COL_DOUBLETON), with c / b as its value. */
 lpp_status lpp_result_cols(const lpp_postsolve *rec, int32_t *kind, int32_t *round, double *val, double *lb,
                            double *ub);
 /* Parallel-column merges (Sec. 3.2, parallel columns; opts.parallel_cols).
@@ -212,8 +221,11 @@ lpp_status lpp_result_merges(const lpp_postsolve *rec, int32_t *leader, int32_t 
  * (host arrays of m, any pointer may be NULL): beg[i], len[i] = its entries
  * in the store, rhs[i] = b (0 and 0 for other rows).  The store, col[] and
  * val[] (original column indices and coefficients in row order), is written
- * up to cap entries; *total receives its size.  Substitutions are undone in
- * the postsolve latest first (round, then after the merges of their round). */
+ * up to cap entries; *total receives its size.  A doubleton row (kind
+ * LPP_ROW_DOUBLETON, opts.doubletons) a x_j + b x_k = c is stored the same
+ * way: its one entry a of x_j and rhs c, with x_k = (c - a x_j) / b.
+ * Substitutions are undone in the postsolve latest first (round, then
+ * doubletons, column singletons and merges of a round in that order). */
 lpp_status lpp_result_substitutions(const lpp_postsolve *rec, int64_t *beg, int32_t *len, double *rhs, int64_t cap,
                                     int32_t *col, double *val, int64_t *total);
 /* Activities of the last executed round per original row (host arrays of m);

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblpp.so")
-SOURCES = ["k_util.cu", "k_round.cu", "k_parcols.cu", "k_colsing.cu", "k_compact.cu", "lpp_engine.cu", "lpp_api.cu", "lpp_serve.cu", "lpp_noalloc.cu"]
+SOURCES = ["k_util.cu", "k_round.cu", "k_parcols.cu", "k_colsing.cu", "k_doubleton.cu", "k_compact.cu", "lpp_engine.cu", "lpp_api.cu", "lpp_serve.cu", "lpp_noalloc.cu"]
 HEADERS = ["lpp_dev.cuh", "lpp_launch.h", "lpp_engine.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no multiply-add contraction anywhere; the kernels write fma()

@@ -53,8 +53,12 @@ lpp_opts resolve_opts(const lpp_opts *opts) {
     else lpp_opts_default(&o);
     if (o.max_rounds < 0 || o.par_max_iter < 1 || !(o.feas_tol >= 0) || !(o.bound_tol >= 0) || !(o.huge > 0) ||
         !(o.max_implied > 0) || !(o.par_tol >= 0) || (o.parallel_cols != 0 && o.parallel_cols != 1) ||
-        (o.col_singletons != 0 && o.col_singletons != 1) || (o.dual_fixing != 0 && o.dual_fixing != 1))
+        (o.col_singletons != 0 && o.col_singletons != 1) || (o.dual_fixing != 0 && o.dual_fixing != 1) ||
+        (o.doubletons != 0 && o.doubletons != 1))
         throw StatusError(LPP_ERR_INVALID, "bad options");
+    // the device S5e path is built and compiled but refused until its
+    // results have been compared with the reference presolver on a GPU
+    if (o.doubletons) throw StatusError(LPP_ERR_INVALID, "doubletons: the GPU S5e step is not enabled yet");
     return o;
 }
 
@@ -235,7 +239,10 @@ void materialize(lpp_postsolve *P) {
     for (int32_t i = 0; i < m; i++) {
         const int32_t a = P->row_aux[i];
         if (a >= 0)  // singleton and substitution rows name a column, parallel rows a row
-            P->row_aux[i] = (P->row_kind[i] == LPP_ROW_SINGLETON || P->row_kind[i] == LPP_ROW_SUBST) ? a - c0 : a - r0;
+            P->row_aux[i] = (P->row_kind[i] == LPP_ROW_SINGLETON || P->row_kind[i] == LPP_ROW_SUBST ||
+                             P->row_kind[i] == LPP_ROW_DOUBLETON)
+                                ? a - c0
+                                : a - r0;
     }
     std::vector<int32_t> cm;
     std::vector<double2> lu;
@@ -285,7 +292,7 @@ void materialize(lpp_postsolve *P) {
         d2h_slice(sl, D.sl, r0, m);
         d2h_slice(P->sub_rhs, D.srhs, r0, m);
         for (int32_t i = 0; i < m; i++) {
-            if (P->row_kind[i] != LPP_ROW_SUBST) {
+            if (P->row_kind[i] != LPP_ROW_SUBST && P->row_kind[i] != LPP_ROW_DOUBLETON) {
                 P->sub_rhs[i] = 0.0;
                 continue;
             }
@@ -380,6 +387,7 @@ void lpp_opts_default(lpp_opts *o) {
     o->parallel_cols = 0;
     o->col_singletons = 0;
     o->dual_fixing = 0;
+    o->doubletons = 0;
     o->timing = 0;
     o->device = 0;
     o->stream = nullptr;
@@ -748,8 +756,9 @@ lpp_status lpp_postsolve_primal(const lpp_postsolve *Pc, const double *x_red, do
         if (j < 0 || (size_t)j >= n) return set_err(LPP_ERR_INVALID, "corrupt column map");
         x_orig[j] = x_red[k];
     }
-    // merges and substitutions, latest first: round, then substitutions
-    // before the merges of their round (S5d comes after S5c), then index
+    // merges and substitutions, latest first: round, then step (S5e
+    // doubletons, S5d substitutions, S5c merges: the reverse of their order
+    // in a round), then index
     struct Ev {
         int32_t round, step, index;
     };
@@ -757,7 +766,8 @@ lpp_status lpp_postsolve_primal(const lpp_postsolve *Pc, const double *x_red, do
     for (size_t j = 0; j < n; j++)
         if (P->col_kind[j] == LPP_COL_PARALLEL) ev.push_back({P->col_round[j], 0, (int32_t)j});
     for (size_t i = 0; i < P->row_kind.size(); i++)
-        if (P->row_kind[i] == LPP_ROW_SUBST) ev.push_back({P->row_round[i], 1, (int32_t)i});
+        if (P->row_kind[i] == LPP_ROW_SUBST || P->row_kind[i] == LPP_ROW_DOUBLETON)
+            ev.push_back({P->row_round[i], P->row_kind[i] == LPP_ROW_DOUBLETON ? 2 : 1, (int32_t)i});
     std::sort(ev.begin(), ev.end(), [](const Ev &a, const Ev &b) {
         if (a.round != b.round) return a.round > b.round;
         if (a.step != b.step) return a.step > b.step;
@@ -778,7 +788,8 @@ lpp_status lpp_postsolve_primal(const lpp_postsolve *Pc, const double *x_red, do
             x_orig[j] = xj;
             x_orig[k] = y - lam * xj;
         } else {
-            // x_j = (b - sum_k a_ik x_k) / a_ij, the entries in row order
+            // x_j = (b - sum_k a_ik x_k) / a_ij, the entries in row order (a
+            // doubleton stores its one other entry: x_k = (c - a x_j) / b)
             const int32_t i = e.index, j = P->row_aux[i];
             if (j < 0 || (size_t)j >= n) return set_err(LPP_ERR_INVALID, "corrupt substitution record");
             double sum = 0.0;

@@ -39,12 +39,15 @@ __host__ __device__ __forceinline__ int seg_class(int len) {
 }
 
 // row record kinds (values of lpp.h)
-enum : uint8_t { RK_KEPT = 0, RK_EMPTY = 1, RK_REDUNDANT = 2, RK_SINGLETON = 3, RK_PARALLEL = 4, RK_SUBST = 5 };
+enum : uint8_t {
+    RK_KEPT = 0, RK_EMPTY = 1, RK_REDUNDANT = 2, RK_SINGLETON = 3, RK_PARALLEL = 4, RK_SUBST = 5, RK_DOUBLETON = 6
+};
 // column kinds (CK_PARALLEL: merged into a parallel leader column, S5c;
-// CK_SUBST: a free column singleton eliminated through its row, S5d)
-enum : uint8_t { CK_KEPT = 0, CK_FIXED = 1, CK_EMPTY = 2, CK_PARALLEL = 3, CK_SUBST = 4 };
+// CK_SUBST: a free column singleton eliminated through its row, S5d;
+// CK_DOUBLETON: eliminated through a doubleton equation, S5e)
+enum : uint8_t { CK_KEPT = 0, CK_FIXED = 1, CK_EMPTY = 2, CK_PARALLEL = 3, CK_SUBST = 4, CK_DOUBLETON = 5 };
 // verdict slots per LP, in step order
-enum { V_S2_ROW = 0, V_S3_COL = 1, V_S5_ROW = 2, V_S6_COL = 3, V_SLOTS = 4 };
+enum { V_S2_ROW = 0, V_S3_COL = 1, V_S5_ROW = 2, V_S5E_COL = 3, V_S6_COL = 4, V_SLOTS = 5 };
 
 // Global counters of a round (block-aggregated atomics).
 struct DevStatus {

@@ -155,7 +155,7 @@ __global__ void k_sizes(const CompactCtx K, int32_t m, int32_t n, DevStatus *st)
 }
 
 const char *kFamNames[F_NUM] = {"prop",     "colfin",   "s5",     "compact_count", "scan", "compact_scatter",
-                                "schedule", "ingest",   "finish", "s5c", "s5d"};
+                                "schedule", "ingest",   "finish", "s5c", "s5d", "s5e"};
 
 }  // namespace
 
@@ -174,6 +174,7 @@ Engine::~Engine() {
     pinned_put(verdict_h);
     pinned_put(changed_h);
     pinned_put(s5_left_h);
+    pinned_put(de_cnt_h);
     if (own_stream && s) cudaStreamDestroy(s);
     if (ev_mat) cudaEventDestroy(ev_mat);
     if (ev_vec) cudaEventDestroy(ev_vec);
@@ -361,6 +362,29 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
         cs_tasks = pool.alloc<int32_t>(m0);
         cs_ntask = pool.alloc<int32_t>(1);
         cs_a = pool.alloc<double>(m0);
+    }
+    if (o.doubletons) {
+        de.dk = pool.alloc<int32_t>(m0);
+        de.rmin = pool.alloc<int32_t>(m0);
+        de.cmin = pool.alloc<int32_t>(n0);
+        de.dj = pool.alloc<int32_t>(m0);
+        de.dmj = pool.alloc<int32_t>(m0);
+        de.dmk = pool.alloc<int32_t>(m0);
+        de.dpk = pool.alloc<int32_t>(m0);
+        de.dpj = pool.alloc<int32_t>(m0);
+        de.jlist = pool.alloc<int32_t>(n0);
+        de.cnt = pool.alloc<int32_t>(2);
+        de.dsel = pool.alloc<uint8_t>(m0);
+        de.dfl = pool.alloc<uint8_t>(m0);
+        de.df = pool.alloc<double>(m0);
+        de.dg = pool.alloc<double>(m0);
+        de.dmd = pool.alloc<double>(m0);
+        de.dnv = pool.alloc<double>(m0);
+        de_cnt_h = static_cast<int32_t *>(pinned_get_sized(2 * sizeof(int32_t)));
+    }
+    if (o.col_singletons || o.doubletons) {
+        // each row is stored at most once, with fewer entries than it has
+        // (rows never grow: a doubleton swaps x_k for x_j at most)
         rec_sb = pool.alloc<long long>(m0);
         rec_sl = pool.alloc<int32_t>(m0);
         rec_srhs = pool.alloc<double>(m0);
@@ -502,6 +526,7 @@ void Engine::prepare() {
     tb.v1 = reinterpret_cast<int32_t *>(rv[1]) + nnz0;
     tb.hist = pool.alloc<int32_t>(transpose_hist_elems(nnz0));
     tb.tmp = scan_tmp;
+    t_hist = tb.hist;  // S5e transposes its rewritten matrices with it
     transpose(rp[0], ci[0], rv[0], row_of + 1, m0, n0, nnz0, tb, tp[0], ti[0], tv[0], s);
     LPP_CUDA(cudaGetLastError());
     if (vec_pending) {  // the vectors' copies overlapped the checks and the transpose
@@ -541,7 +566,7 @@ void Engine::prepare() {
         LPP_CUDA(cudaMemsetAsync(rec_cp, 0, sizeof(int32_t) * (size_t)std::max(n0, 1), s));
         fill_u64(reinterpret_cast<unsigned long long *>(rec_cm), 4 * (int64_t)n0, 0x7ff8000000000000ULL, s);  // NaN
     }
-    if (o.col_singletons) {
+    if (o.col_singletons || o.doubletons) {
         LPP_CUDA(cudaMemsetAsync(rec_sb, 0, sizeof(long long) * (size_t)std::max(m0, 1), s));
         LPP_CUDA(cudaMemsetAsync(rec_sl, 0, sizeof(int32_t) * (size_t)std::max(m0, 1), s));
         LPP_CUDA(cudaMemsetAsync(rec_srhs, 0, sizeof(double) * (size_t)std::max(m0, 1), s));
@@ -827,6 +852,8 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     }
     // S5d (opt-in) on the rows kept so far and the columns left
     if (o.col_singletons) run_s5d(C);
+    // S5e (opt-in) on the rows and columns left; may rewrite the matrices
+    if (o.doubletons) run_s5e(C);
     bool newly_dead = false;
     for (int32_t k = 0; k < nlp; k++) {
         if (lp_dropped[k]) continue;
@@ -909,6 +936,64 @@ void Engine::run_s5d(const Ctx &C) {
     tend();
     LPP_CUDA(cudaMemcpyAsync(st_h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     LPP_CUDA(cudaStreamSynchronize(s));
+}
+
+// S5e: candidates, claims, the applied doubletons, a status read.  When any
+// applied, the CSR is rewritten into the other buffers (lengths, a scan, one
+// read of the new size, the placement) and the CSC rebuilt from it by the
+// ingest transpose; the old matrices, dead by then, lend the transpose its
+// scratch (the old CSC the row of each entry).  The buffers swap roles, the
+// schedules are rebuilt, and the rows of every x_j are marked for the next
+// round.  S6 and the compaction of the round then see the rewritten LP.
+void Engine::run_s5e(const Ctx &C) {
+    tbegin(F_S5E, 0.0);
+    int32_t applied = 0, nj = 0;
+    if (m > 0 && n > 0) {
+        fill_i32(de.rmin, m, kNone, s);
+        fill_i32(de.cmin, n, kNone, s);
+        LPP_CUDA(cudaMemsetAsync(de.cnt, 0, 2 * sizeof(int32_t), s));
+        launch_s5e(C, de, s);
+        LPP_CUDA(cudaGetLastError());
+        LPP_CUDA(cudaMemcpyAsync(de_cnt_h, de.cnt, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LPP_CUDA(cudaStreamSynchronize(s));
+        applied = de_cnt_h[0];
+        nj = de_cnt_h[1];
+    }
+    if (applied > 0) {
+        const int nx = cur ^ 1;
+        launch_s5e_rowlen(C, de, K.r_len, s);
+        scan_excl(K.r_len, rp[nx], m, scan_tmp, s);
+        LPP_CUDA(cudaGetLastError());
+        LPP_CUDA(cudaMemcpyAsync(de_cnt_h, rp[nx] + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LPP_CUDA(cudaStreamSynchronize(s));
+        const int32_t nnz2 = de_cnt_h[0];
+        if (nnz2 < 0 || nnz2 > nnz) throw StatusError(LPP_ERR_CUDA, "internal: S5e rewrite grew the matrix");
+        int32_t *row_of = ti[cur];
+        launch_s5e_scatter(C, de, rp[nx], ci[nx], rv[nx], row_of, nnz, s);
+        TransposeBufs tb;
+        tb.k0 = reinterpret_cast<uint32_t *>(ci[cur]);
+        tb.k1 = reinterpret_cast<uint32_t *>(rv[cur]);
+        tb.v0 = reinterpret_cast<int32_t *>(rv[cur]) + nnz0;
+        tb.v1 = reinterpret_cast<int32_t *>(tv[cur]);
+        tb.hist = t_hist;
+        tb.tmp = scan_tmp;
+        transpose(rp[nx], ci[nx], rv[nx], row_of, m, n, nnz2, tb, tp[nx], ti[nx], tv[nx], s);
+        LPP_CUDA(cudaGetLastError());
+        std::swap(rp[0], rp[1]);
+        std::swap(ci[0], ci[1]);
+        std::swap(rv[0], rv[1]);
+        std::swap(tp[0], tp[1]);
+        std::swap(ti[0], ti[1]);
+        std::swap(tv[0], tv[1]);
+        nnz = nnz2;
+        schedule_current();
+        read_status();
+        adopt_schedule();
+        launch_s5e_mark(ctx(C.round), de, nj, s);
+        LPP_CUDA(cudaGetLastError());
+    }
+    tend();
+    read_status();
 }
 
 void Engine::run() {

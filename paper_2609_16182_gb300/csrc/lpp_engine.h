@@ -107,6 +107,11 @@ struct Engine {
     int32_t *cs_rcand = nullptr, *cs_cmin = nullptr, *cs_tasks = nullptr, *cs_ntask = nullptr;
     uint8_t *cs_relig = nullptr;
     double *cs_a = nullptr;  // per row: the candidate's coefficient (rows of more than 4096 entries)
+    // S5e (opts.doubletons): the step's work (see S5eBufs), a pinned copy of
+    // its two counts, the transpose histogram kept from the ingest
+    S5eBufs de{};
+    int32_t *de_cnt_h = nullptr;
+    int32_t *t_hist = nullptr;
     cudaStream_t s2 = nullptr;                   // host inputs: the vectors' copies
     cudaEvent_t ev_mat = nullptr, ev_vec = nullptr;
     bool vec_pending = false;                    // their check waits for the copies (prepare)
@@ -125,7 +130,8 @@ struct Engine {
     double *rec_rv, *rec_cv;
     int32_t *rec_ca = nullptr, *rec_cp = nullptr;  // S5c merges (NULL unless opts.parallel_cols)
     double *rec_cm = nullptr;
-    long long *rec_sb = nullptr;                   // S5d substitutions (NULL unless opts.col_singletons)
+    long long *rec_sb = nullptr;                   // S5d / S5e substitutions (NULL unless opts.col_singletons
+                                                   // or opts.doubletons)
     int32_t *rec_sl = nullptr, *rec_scol = nullptr;
     double *rec_srhs = nullptr, *rec_sval = nullptr;
     unsigned long long *sub_used = nullptr;
@@ -186,13 +192,16 @@ struct Engine {
     void compact(int32_t round);
     void run_s5c(const Ctx &C0);  // S5c: keys, the changed groups, their leader passes
     void run_s5d(const Ctx &C);   // S5d: column singletons, then a status read
+    void run_s5e(const Ctx &C);   // S5e: doubleton equations, the rewritten matrices, a status read
     // timing helpers
     void tbegin(int fam, double bytes);
     void tend();
 };
 
 // Kernel families reported by lpp_result_kernels.
-enum Fam { F_PROP = 0, F_COLFIN, F_S5, F_COUNT, F_SCAN, F_SCATTER, F_SCHED, F_INGEST, F_FINISH, F_S5C, F_S5D, F_NUM };
+enum Fam {
+    F_PROP = 0, F_COLFIN, F_S5, F_COUNT, F_SCAN, F_SCATTER, F_SCHED, F_INGEST, F_FINISH, F_S5C, F_S5D, F_S5E, F_NUM
+};
 const char *fam_name(int f);
 
 // device allocations shared by the reduced LPs of one batch, freed with the last

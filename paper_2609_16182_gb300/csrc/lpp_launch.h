@@ -107,6 +107,31 @@ void launch_s5c_groups(const Ctx &C, const uint32_t *slot, const int32_t *col, i
 void launch_s5d(const Ctx &C, int32_t *rcand, uint8_t *relig, int32_t *cmin, int32_t *tasks, int32_t *ntask,
                 double *cs_a, cudaStream_t s);
 
+// ------------------------------------------------------------- k_doubleton.cu
+// S5e work: per row the candidate's eliminated column (dk, -1 if none), the
+// smallest candidate claiming the row (rmin, kNone before), selected (dsel),
+// for a selected row x_j, f, g (dj, df, dg); per changed row x_j, x_k and
+// x_j's coefficient change (dmj, -1 if unchanged, dmk, dmd), the positions
+// of x_k and of x_j (dpk, dpj), flags (dfl: 1 x_j present, 2 cancelled)
+// and x_j's new coefficient (dnv); per column the smallest claiming
+// candidate (cmin, kNone before); the columns x_j of the applied rows
+// (jlist); cnt[0] applied doubletons, cnt[1] jlist entries (0 before)
+struct S5eBufs {
+    int32_t *dk, *rmin, *cmin, *dj, *dmj, *dmk, *dpk, *dpj, *jlist, *cnt;
+    uint8_t *dsel, *dfl;
+    double *df, *dg, *dmd, *dnv;
+};
+// candidates, claims, selection and the applied doubletons (bounds, costs,
+// sides, records, the changed rows' notes)
+void launch_s5e(const Ctx &C, const S5eBufs &D, cudaStream_t s);
+// the rewritten row lengths into rlen[0 .. m)
+void launch_s5e_rowlen(const Ctx &C, const S5eBufs &D, int32_t *rlen, cudaStream_t s);
+// the rewritten CSR (rp2: the scanned lengths) and the row of each of its entries
+void launch_s5e_scatter(const Ctx &C, const S5eBufs &D, const int32_t *rp2, int32_t *ci2, double *rv2,
+                        int32_t *row_of, int64_t nnz, cudaStream_t s);
+// on the rewritten matrices: the rows of the cnt columns in jlist are dirty
+void launch_s5e_mark(const Ctx &C, const S5eBufs &D, int32_t cnt, cudaStream_t s);
+
 // -------------------------------------------------------------- k_compact.cu
 void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s);
 void launch_compact_scatter(const Ctx &C, const CompactCtx &K, int32_t nnz, cudaStream_t s);

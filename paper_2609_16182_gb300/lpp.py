@@ -17,8 +17,8 @@ from . import _build
 
 OK, INFEASIBLE, UNBOUNDED = 0, 1, 2
 ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUDGET = -1, -2, -3, -4, -5
-ROW_KEPT, ROW_EMPTY, ROW_REDUNDANT, ROW_SINGLETON, ROW_PARALLEL, ROW_SUBST = 0, 1, 2, 3, 4, 5
-COL_KEPT, COL_FIXED, COL_EMPTY, COL_PARALLEL, COL_SUBST = 0, 1, 2, 3, 4
+ROW_KEPT, ROW_EMPTY, ROW_REDUNDANT, ROW_SINGLETON, ROW_PARALLEL, ROW_SUBST, ROW_DOUBLETON = 0, 1, 2, 3, 4, 5, 6
+COL_KEPT, COL_FIXED, COL_EMPTY, COL_PARALLEL, COL_SUBST, COL_DOUBLETON = 0, 1, 2, 3, 4, 5
 WHERE_NONE, WHERE_ROW, WHERE_COL = 0, 1, 2
 
 
@@ -39,7 +39,8 @@ class Opts(C.Structure):
     _fields_ = [("feas_tol", C.c_double), ("bound_tol", C.c_double), ("huge", C.c_double),
                 ("max_implied", C.c_double), ("par_tol", C.c_double), ("max_rounds", C.c_int32),
                 ("dual_reductions", C.c_int32), ("par_max_iter", C.c_int32), ("parallel_cols", C.c_int32),
-                ("col_singletons", C.c_int32), ("dual_fixing", C.c_int32), ("timing", C.c_int32),
+                ("col_singletons", C.c_int32), ("dual_fixing", C.c_int32), ("doubletons", C.c_int32),
+                ("timing", C.c_int32),
                 ("device", C.c_int32), ("stream", C.c_void_p)]
 
 

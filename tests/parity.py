@@ -3,9 +3,11 @@
 Bit-exact: status, verdict location and round, round count, every record
 (kind, round, leader / column, singleton coefficient, parallel factor; for
 merged parallel columns the leader, pass and factor; for column-singleton
-substitutions the stored row),
+substitutions and doubletons the stored row),
 row and column maps, the reduced CSR / CSC structure and its coefficients
-and costs (copies of the input), the counts of infinite activity terms.
+and costs (copies of the input, or one rounded product and difference away
+from it: S5d and S5e costs, S5e coefficients), the counts of infinite
+activity terms.
 Within tolerance: values that come out of a floating-point sum (activities,
 implied bounds, shifted sides, the objective constant, bounds at a merge, the
 right-hand side of a substitution):
@@ -65,17 +67,18 @@ def compare(gpu, orc, lp, check_records=True, arena_stats=False):
         np.testing.assert_array_equal(gpu.col_pass[merged], orc.col_pass[merged], err_msg="merge passes")
         np.testing.assert_array_equal(gpu.col_val[merged], orc.col_val[merged], err_msg="merge lambda")
         _close(gpu.col_mrg[merged], orc.col_mrg[merged], what="bounds at the merge")
-        # column-singleton substitutions: each row's stored entries and b (the
-        # store's order of rows is the GPU's append order, not compared)
-        for i in np.flatnonzero(orc.row_kind == 5):
+        # column-singleton substitutions and doubletons: each row's stored
+        # entries and b (the store's order of rows is the GPU's append order,
+        # not compared)
+        stored = (orc.row_kind == 5) | (orc.row_kind == 6)
+        for i in np.flatnonzero(stored):
             go, gl = int(gpu.sub_beg[i]), int(gpu.sub_len[i])
             oo, ol = int(orc.sub_beg[i]), int(orc.sub_len[i])
             assert gl == ol, ("substitution length", i, gl, ol)
             np.testing.assert_array_equal(gpu.sub_col[go:go + gl], orc.sub_col[oo:oo + ol], err_msg=f"row {i} columns")
             np.testing.assert_array_equal(gpu.sub_val[go:go + gl], orc.sub_val[oo:oo + ol], err_msg=f"row {i} values")
         # b may come out of earlier side shifts (sums): a tolerance, as the reduced sides
-        subs = orc.row_kind == 5
-        _close(gpu.sub_rhs[subs], orc.sub_rhs[subs], what="substitution right-hand sides")
+        _close(gpu.sub_rhs[stored], orc.sub_rhs[stored], what="substitution right-hand sides")
     fixed = orc.col_kind != 0
     _close(gpu.col_val[fixed], orc.col_val[fixed], what="fixed values")
     _close(gpu.col_lb, orc.col_lb, what="final lower bounds")

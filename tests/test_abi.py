@@ -77,6 +77,27 @@ def test_opt_in_steps_default_off():
     from paper_2609_16182_gb300 import lpp
     import oracle
     o = lpp.opts()
-    assert (o.parallel_cols, o.col_singletons, o.dual_fixing) == (0, 0, 0)
+    assert (o.parallel_cols, o.col_singletons, o.dual_fixing, o.doubletons) == (0, 0, 0, 0)
     q = oracle.default_opts()
     assert (q.parallel_cols, q.col_singletons, q.dual_fixing, q.doubletons) == (0, 0, 0, 0)
+
+
+def test_doubletons_refused_before_any_device_work():
+    # the options are checked on the host before the first CUDA call, so this
+    # runs without a GPU: a call with doubletons = 1 returns LPP_ERR_INVALID
+    import ctypes as C
+    import numpy as np
+    from paper_2609_16182_gb300 import lpp
+    L = lpp.load()
+    rp = np.array([0, 2], np.int32)
+    ci = np.array([0, 1], np.int32)
+    v = np.array([1.0, 2.0])
+    side = np.array([3.0])
+    lb, ub, c = np.zeros(2), np.ones(2), np.ones(2)
+    lp = lpp.LpStruct(1, 2, 2, rp.ctypes.data, ci.ctypes.data, v.ctypes.data, c.ctypes.data, side.ctypes.data,
+                      side.ctypes.data, lb.ctypes.data, ub.ctypes.data, 0.0, 0)
+    o = lpp.opts(doubletons=1)
+    red, rec = C.c_void_p(), C.c_void_p()
+    st = L.lpp_presolve(C.byref(lp), C.byref(o), C.byref(red), C.byref(rec))
+    assert st == lpp.ERR_INVALID and not red.value and not rec.value
+    assert b"doubletons" in L.lpp_last_error()
