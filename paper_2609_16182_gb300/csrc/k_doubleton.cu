@@ -34,6 +34,7 @@
 #include <algorithm>
 
 #include "lpp_launch.h"
+#include "s5e_rewrite.cuh"
 
 namespace lpp {
 
@@ -81,17 +82,6 @@ __device__ __forceinline__ bool warp_any(bool own, int32_t b, int32_t e, int32_t
         if (lane == src) hit = any;
     }
     return hit;
-}
-
-// first position p in idx[0, len) with idx[p] >= key (idx increasing)
-__device__ __forceinline__ int32_t lower_pos(const int32_t *idx, int32_t len, int32_t key) {
-    int32_t lo = 0, hi = len;
-    while (lo < hi) {
-        const int32_t mid = lo + ((hi - lo) >> 1);
-        if (idx[mid] < key) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
 }
 
 // the other column of doubleton row i (entries at p, p + 1) than kk
@@ -252,23 +242,12 @@ __global__ void __launch_bounds__(kBlock) k_s5e_rowlen(Ctx C, S5eBufs D, int32_t
     const int32_t p = C.A.ptr[i], len = C.A.ptr[i + 1] - p, jj = D.dmj[i];
     int32_t nl = len;
     if (jj >= 0) {
-        const int32_t *idx = C.A.idx + p;
-        const int32_t pk = lower_pos(idx, len, D.dmk[i]);
-        const int32_t pj = lower_pos(idx, len, jj);
-        const bool found = pj < len && idx[pj] == jj;
-        const double dv = D.dmd[i];
-        double v = dv;
-        bool cancel = false;
-        if (found) {
-            const double old = C.A.val[p + pj];
-            v = old + dv;
-            cancel = fabs(v) <= C.par_tol * fmax(fabs(old), fabs(dv));
-        }
-        nl = len - 1 + (found ? (cancel ? -1 : 0) : 1);
-        D.dpk[i] = pk;
-        D.dpj[i] = pj;
-        D.dfl[i] = (uint8_t)((found ? 1 : 0) | (cancel ? 2 : 0));
-        D.dnv[i] = v;
+        const S5eNote t = s5e_note(C.A.idx + p, C.A.val + p, len, jj, D.dmk[i], D.dmd[i], C.par_tol);
+        nl = t.len_new;
+        D.dpk[i] = t.pk;
+        D.dpj[i] = t.pj;
+        D.dfl[i] = (uint8_t)((t.found ? 1 : 0) | (t.cancel ? 2 : 0));
+        D.dnv[i] = t.v;
     }
     rlen[i] = nl;
 }
@@ -296,22 +275,25 @@ __global__ void __launch_bounds__(kBlock) k_s5e_scatter(Ctx C, S5eBufs D, const 
     int32_t dest = base + q;
     const int32_t jj = D.dmj[i];
     if (jj >= 0) {
-        const int32_t pk = D.dpk[i], pj = D.dpj[i];
-        const bool found = D.dfl[i] & 1, cancel = D.dfl[i] & 2;
-        if (q == pk) {
-            if (!found) {
-                const int32_t at = base + pj - (pk < pj ? 1 : 0);
+        S5eNote t;
+        t.pk = D.dpk[i];
+        t.pj = D.dpj[i];
+        t.found = D.dfl[i] & 1;
+        t.cancel = D.dfl[i] & 2;
+        if (q == t.pk) {
+            if (!t.found) {
+                const int32_t at = base + s5e_insert_at(t);
                 ci2[at] = jj;
                 rv2[at] = D.dnv[i];
                 row_of[at] = i;
             }
             return;
         }
-        if (found && q == pj) {
-            if (cancel) return;
+        if (t.found && q == t.pj) {
+            if (t.cancel) return;
             v = D.dnv[i];
         }
-        dest = base + q - (q > pk ? 1 : 0) + (!found && q >= pj ? 1 : 0) - (found && cancel && q > pj ? 1 : 0);
+        dest = base + s5e_dest(t, q);
     }
     ci2[dest] = col;
     rv2[dest] = v;
