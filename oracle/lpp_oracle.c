@@ -912,7 +912,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                column index among those of the round (as S3 reports) */
             for (i = 0; i < m; i++) {
                 int32_t kk, jj, q, sel = 1;
-                double a, b, c, f, g, t, lo, hi, nl, nu;
+                double a, b, c, f, g, t, lo, hi, nl, nu, ebg, eblo, ebhi, ebnl, ebnu;
                 if (dk[i] < 0) continue;
                 kk = dk[i];
                 jj = s.ci[s.rp[i]] == kk ? s.ci[s.rp[i] + 1] : s.ci[s.rp[i]];
@@ -926,25 +926,37 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                 }
                 if (!sel) continue;
                 f = a / b; g = c / b;
-                if (f > 0) {
-                    lo = isfin(s.u[kk]) ? (g - s.u[kk]) / f : -INFINITY;
-                    hi = isfin(s.l[kk]) ? (g - s.l[kk]) / f : INFINITY;
-                } else {
-                    lo = isfin(s.l[kk]) ? (g - s.l[kk]) / f : -INFINITY;
-                    hi = isfin(s.u[kk]) ? (g - s.u[kk]) / f : INFINITY;
+                /* forward error bounds (audit): c carries its row's, the
+                   bounds theirs; a, b and f are exact copies on every path */
+                ebg = s.ebL[i] / fabs(b) + UROUND * fabs(g);
+                {
+                    const double bhi = f > 0 ? s.u[kk] : s.l[kk], blo = f > 0 ? s.l[kk] : s.u[kk];
+                    const double ebhi_k = f > 0 ? s.ebu[kk] : s.ebl[kk], eblo_k = f > 0 ? s.ebl[kk] : s.ebu[kk];
+                    lo = isfin(bhi) ? (g - bhi) / f : -INFINITY;
+                    hi = isfin(blo) ? (g - blo) / f : INFINITY;
+                    eblo = isfin(lo) ? (ebg + ebhi_k + UROUND * fabs(g - bhi)) / fabs(f) + UROUND * fabs(lo) : 0.0;
+                    ebhi = isfin(hi) ? (ebg + eblo_k + UROUND * fabs(g - blo)) / fabs(f) + UROUND * fabs(hi) : 0.0;
                 }
-                nl = lo > s.l[jj] ? lo : s.l[jj];
-                nu = hi < s.u[jj] ? hi : s.u[jj];
+                if (lo > s.l[jj]) { nl = lo; ebnl = eblo; } else { nl = s.l[jj]; ebnl = s.ebl[jj]; }
+                if (hi < s.u[jj]) { nu = hi; ebnu = ebhi; } else { nu = s.u[jj]; ebnu = s.ebu[jj]; }
+                /* finalised as S3' does: crossing by more than the tolerance is
+                   infeasible, bounds within it snap to their midpoint */
                 if (isfin(nl) && isfin(nu)) {
                     const double d = ft * dmax(1.0, dmax(fabs(nl), fabs(nu)));
+                    audit(&au, (nl - nu) - d, ebnl + ebnu);
                     if (nl - nu > d) {
                         if (bad < 0 || s.cmap[jj] < s.cmap[bad]) bad = jj;
                         continue;
                     }
-                    if (nl > nu) nl = nu = 0.5 * (nl + nu);
+                    audit(&au, fabs(nl - nu) - d, ebnl + ebnu);
+                    if (nl != nu && fabs(nl - nu) <= d) {
+                        const double mid = 0.5 * (nl + nu);
+                        const double e = dmax(ebnl, ebnu) + UROUND * fabs(mid);
+                        nl = nu = mid; ebnl = ebnu = e;
+                    }
                 }
                 if (nl != s.l[jj] || nu != s.u[jj]) bchanged++;
-                s.l[jj] = nl; s.u[jj] = nu;
+                s.l[jj] = nl; s.u[jj] = nu; s.ebl[jj] = ebnl; s.ebu[jj] = ebnu;
                 t = s.c[kk] / b;
                 s.c[jj] = s.c[jj] - t * a;
                 /* the other rows of x_k: side shift now, coefficient change in the rebuild */
@@ -952,8 +964,9 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                     const int32_t rr = tri[q];
                     const double ark = tvl[q];
                     if (rr == i || kind[rr] != LPPO_ROW_KEPT) continue;
-                    if (isfin(s.L[rr])) s.L[rr] = s.L[rr] - ark * g;
-                    if (isfin(s.U[rr])) s.U[rr] = s.U[rr] - ark * g;
+                    const double esh = fabs(ark) * ebg + UROUND * fabs(ark * g);
+                    if (isfin(s.L[rr])) { s.L[rr] = s.L[rr] - ark * g; s.ebL[rr] += esh + UROUND * fabs(s.L[rr]); }
+                    if (isfin(s.U[rr])) { s.U[rr] = s.U[rr] - ark * g; s.ebU[rr] += esh + UROUND * fabs(s.U[rr]); }
                     dmj[rr] = jj; dmk[rr] = kk; dmd[rr] = -(ark * f);
                 }
                 kind[i] = LPPO_ROW_DOUBLETON;

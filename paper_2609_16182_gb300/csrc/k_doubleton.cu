@@ -7,9 +7,10 @@
 // x_k = g - f x_j with f = a / b, g = c / b.  Then
 //   x_j's bounds meet the range x_k's bounds give it,
 //     [(g - u_k) / f, (g - l_k) / f]   (ends swapped for f < 0),
-//     crossing by more than d = feas_tol max(1, |l|, |u|) is infeasible
-//     (the smallest original column index of the round is reported),
-//     nearly equal bounds snap to their midpoint;
+//     finalised as S3' finalises bounds: crossing by more than
+//     d = feas_tol max(1, |l|, |u|) is infeasible (the smallest original
+//     column index of the round is reported), bounds within d of each
+//     other snap to their midpoint;
 //   c_j <- c_j - (c_k / b) a, and x_k takes the value g for the objective
 //     constant (as a fixed column does);
 //   every other kept row r of x_k (coefficient a_rk) loses that entry and
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(kBlock) k_s5e_apply(Ctx C, S5eBufs D) {
             if (nl - nu > d) {
                 atomicMin(&C.verdict[lp * V_SLOTS + V_S5E_COL], C.cmap[jj]);
                 sel = false;
-            } else if (nl > nu) {
+            } else if (nl != nu && fabs(nl - nu) <= d) {  // as S3' finalises: a symmetric snap
                 nl = nu = 0.5 * (nl + nu);
             }
         }

@@ -91,6 +91,17 @@ def test_empty_bound_transfer_after_tightening():
     assert (res.status, res.where, res.index, res.round) == (oracle.INFEASIBLE, oracle.WHERE_ROW, 0, 2)
 
 
+def test_transferred_bounds_within_tolerance_snap():
+    # x0 + x1 = 10, x1 in [0, 1] moves [9, 10] onto x0 in [9 - 4e-6, 9 + 5e-9] (S3 rejects row 0's
+    # l0 >= 9, a gain below bound_tol * 9): [9, 9 + 5e-9], 5e-9 apart, within feas_tol * 9.  As in
+    # S3', the bounds snap to their midpoint although they do not cross; x0 is fixed in round 2
+    lp = make([{0: 1.0, 1: 1.0}], [10.0], [10.0], [9.0 - 4e-6, 0.0], [9.0 + 5e-9, 1.0], c=[1.0, 1.0])
+    res = oracle.presolve(lp, opts(dual_reductions=0))
+    assert res.status == oracle.OK and res.row_kind[0] == oracle.ROW_DOUBLETON
+    assert list(res.col_kind) == [oracle.COL_FIXED, oracle.COL_DOUBLETON] and list(res.col_round) == [2, 1]
+    assert res.col_val[0] == 0.5 * (9.0 + (9.0 + 5e-9))
+
+
 def test_two_empty_transfers_report_the_smaller_column():
     # the construction above twice: row 0 moves x3's range onto x2, row 1 x1's onto x0; both
     # miss.  The verdict names the smaller original column (0), not the first row's (2)
