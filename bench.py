@@ -247,6 +247,28 @@ def dualfix_leg(lpp, torch, dev, stream, lp):
                       lambda r: {"dual_fixed": int(np.count_nonzero(r.col_kind == lpp.COL_EMPTY))})
 
 
+def doubleton_leg(lpp, synth, torch, dev, stream):
+    """The LP-relaxation workload (500k rows, 1M columns, 7.8M nonzeros,
+    4% doubleton equations, 10 dense columns) with the doubleton step on and
+    off.  While the library refuses the option, the leg reports why instead
+    (checked on a two-entry LP before the workload is generated)."""
+    tiny = synth.LP(m=1, n=2, row_ptr=np.array([0, 2], np.int32), col_idx=np.array([0, 1], np.int32),
+                    val=np.array([1.0, 1.0]), c=np.zeros(2), lhs=np.ones(1), rhs=np.ones(1),
+                    lb=np.zeros(2), ub=np.ones(2))
+    try:
+        lpp.presolve(tiny, doubletons=1).close()
+    except lpp.LppError as e:
+        return {"workload": "LP relaxation, 500k rows, 4% doubleton equations", "unavailable": str(e)}
+    q = synth.lprelax(0)
+
+    def count(r):
+        return {"doubletons": int(np.count_nonzero(r.row_kind == lpp.ROW_DOUBLETON))}
+
+    return opt_in_leg(lpp, torch, dev, stream, q,
+                      f"LP relaxation (m = {q.m}, n = {q.n}, nnz = {q.nnz}), 4% doubleton equations",
+                      "doubletons", "s5e", count)
+
+
 def serving_leg(lpp, synth, torch, dev, pool_size=24, requests=200, budget=120 << 30, seed=0):
     """Poisson arrivals of skewed-like LPs (nnz log-uniform in [1e3, 1e6],
     m = nnz/10, n = 1.5 m; requests draw from a pool of `pool_size` distinct
@@ -372,6 +394,7 @@ def main():
     ap.add_argument("--no-parcols", action="store_true", help="skip the parallel-columns leg")
     ap.add_argument("--no-colsing", action="store_true", help="skip the column-singletons leg")
     ap.add_argument("--no-dualfix", action="store_true", help="skip the dual-fixing leg")
+    ap.add_argument("--no-doubletons", action="store_true", help="skip the doubleton-equations leg")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the LP (profiling runs only)")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: W + K steps only (no timing pass, e2e or CPU baseline)")
@@ -521,6 +544,9 @@ def main():
     dualfix = None
     if not args.no_dualfix:
         dualfix = dualfix_leg(lpp, torch, dev, stream, lp)
+    doubletons = None
+    if not args.no_doubletons:
+        doubletons = doubleton_leg(lpp, synth, torch, dev, stream)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": ws, "steps": args.steps,
@@ -539,7 +565,7 @@ def main():
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
                 "batched": batched, "serving": serving, "parallel_cols": parcols, "col_singletons": colsing,
-                "dual_fixing": dualfix}
+                "dual_fixing": dualfix, "doubletons": doubletons}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
