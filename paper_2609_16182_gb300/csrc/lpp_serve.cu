@@ -22,6 +22,7 @@
 #include <unordered_map>
 
 #include "lpp_engine.h"
+#include "ranges.h"
 
 namespace lpp {
 
@@ -162,39 +163,6 @@ unsigned grid_for(int64_t cnt) {
     const int64_t b = (cnt + 255) / 256;
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
 }
-
-// first-fit allocator of index ranges (record space)
-struct Ranges {
-    std::vector<std::pair<int32_t, int32_t>> free_;  // (start, length), sorted
-    void init(int32_t cap) { free_.assign(1, {0, cap}); }
-    int32_t take(int32_t len) {
-        if (len == 0) return 0;
-        for (size_t k = 0; k < free_.size(); k++)
-            if (free_[k].second >= len) {
-                const int32_t s = free_[k].first;
-                free_[k].first += len;
-                free_[k].second -= len;
-                if (free_[k].second == 0) free_.erase(free_.begin() + (long)k);
-                return s;
-            }
-        return -1;
-    }
-    void give(int32_t s, int32_t len) {
-        if (len == 0) return;
-        auto it = free_.begin();
-        while (it != free_.end() && it->first < s) ++it;
-        it = free_.insert(it, {s, len});
-        // merge with neighbours
-        if (it + 1 != free_.end() && it->first + it->second == (it + 1)->first) {
-            it->second += (it + 1)->second;
-            free_.erase(it + 1);
-        }
-        if (it != free_.begin() && (it - 1)->first + (it - 1)->second == it->first) {
-            (it - 1)->second += it->second;
-            free_.erase(it);
-        }
-    }
-};
 
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
