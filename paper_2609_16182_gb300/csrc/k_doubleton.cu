@@ -27,15 +27,15 @@
 // GPU layout: one thread per row finds the candidates and claims; the
 // walks over x_k's column (claims, the check of the claims, the side
 // shifts) run on the owning thread for columns of at most 32 entries and on
-// the whole warp, in turn, for longer ones.  When a round applies any
+// the whole warp, in turn, for longer ones.  The work per row and per entry
+// is in s5e_logic.cuh, shared with a host build of the same steps.  When a round applies any
 // doubleton, the CSR is rewritten into the other buffer (each changed row's
 // new length by binary searches, a scan, one thread per entry placing it),
 // the CSC is rebuilt from it by the ingest transpose, and S6 and the
 // compaction then work on the rewritten matrices.
 #include <algorithm>
 
-#include "lpp_launch.h"
-#include "s5e_rewrite.cuh"
+#include "s5e_logic.cuh"
 
 namespace lpp {
 
@@ -85,220 +85,54 @@ __device__ __forceinline__ bool warp_any(bool own, int32_t b, int32_t e, int32_t
     return hit;
 }
 
-// the other column of doubleton row i (entries at p, p + 1) than kk
-__device__ __forceinline__ int32_t other_col(const Ctx &C, int32_t p, int32_t kk) {
-    return C.A.idx[p] == kk ? C.A.idx[p + 1] : C.A.idx[p];
-}
-
 // one thread per row: candidates, their column claims, and (by the walk of
-// x_k's column) their row claims; resets the row's note of a change
+// x_k's column) their row claims
 __global__ void __launch_bounds__(kBlock) k_s5e_detect(Ctx C, S5eBufs D) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    bool own = false;
-    int32_t b = 0, e = 0;
-    if (i < C.m) {
-        int32_t kk = -1;
-        const int32_t p = C.A.ptr[i];
-        D.dmj[i] = -1;
-        if (C.rkind[i] == RK_KEPT && C.A.ptr[i + 1] - p == 2) {
-            const double Lv = C.L[i];
-            const int32_t c0 = C.A.idx[p], c1 = C.A.idx[p + 1];
-            if (is_fin(Lv) && Lv == C.U[i] && C.ckind[c0] == CK_KEPT && C.ckind[c1] == CK_KEPT) {
-                const int32_t l0 = C.T.ptr[c0 + 1] - C.T.ptr[c0], l1 = C.T.ptr[c1 + 1] - C.T.ptr[c1];
-                kk = l1 <= l0 ? c1 : c0;
-                atomicMin(&D.cmin[c0], i);
-                atomicMin(&D.cmin[c1], i);
-                own = true;
-                b = C.T.ptr[kk];
-                e = C.T.ptr[kk + 1];
-            }
-        }
-        D.dk[i] = kk;
-    }
-    warp_walk(own, b, e, i, [&](int32_t src, int32_t k) {
-        const int32_t rr = C.T.idx[k];
-        if (rr == src || C.rkind[rr] == RK_KEPT) atomicMin(&D.rmin[rr], src);
-    });
+    const S5eWalk w = i < C.m ? s5e_detect_row(C, D, i) : S5eWalk{false, 0, 0};
+    warp_walk(w.own, w.b, w.e, i, [&](int32_t src, int32_t k) { s5e_claim_entry(C, D, src, k); });
 }
 
 // one thread per row: a candidate that holds both column claims, its own
 // row's and those of every kept row of x_k is selected (dsel)
 __global__ void __launch_bounds__(kBlock) k_s5e_select(Ctx C, S5eBufs D) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    bool own = false;
-    int32_t b = 0, e = 0;
-    if (i < C.m) {
-        const int32_t kk = D.dk[i];
-        if (kk >= 0) {
-            const int32_t jj = other_col(C, C.A.ptr[i], kk);
-            own = D.cmin[jj] == i && D.cmin[kk] == i && D.rmin[i] == i;
-            b = C.T.ptr[kk];
-            e = C.T.ptr[kk + 1];
-        }
-    }
-    const bool lost = warp_any(own, b, e, i, [&](int32_t src, int32_t k) {
-        const int32_t rr = C.T.idx[k];
-        return rr != src && C.rkind[rr] == RK_KEPT && D.rmin[rr] != src;
-    });
-    if (i < C.m) D.dsel[i] = (uint8_t)(own && !lost);
+    const S5eWalk w = i < C.m ? s5e_select_row(C, D, i) : S5eWalk{false, 0, 0};
+    const bool lost =
+        warp_any(w.own, w.b, w.e, i, [&](int32_t src, int32_t k) { return s5e_lost_entry(C, D, src, k); });
+    if (i < C.m) D.dsel[i] = (uint8_t)(w.own && !lost);
 }
 
 // one thread per selected row: the bound transfer (or the verdict), the
 // cost, the records; then the walk of x_k's column shifts the sides of its
-// other kept rows and notes their change (x_j, -(a_rk f)).  A row of x_k
-// other than i is claimed by i alone, so no other thread writes it or its
-// kind, and no selected row is one of them.
+// other kept rows and notes their change.  A row of x_k other than i is
+// claimed by i alone, so no other thread writes it or its kind, and no
+// selected row is one of them.
 __global__ void __launch_bounds__(kBlock) k_s5e_apply(Ctx C, S5eBufs D) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    bool sel = i < C.m && D.dsel[i];
-    int32_t b = 0, e = 0, applied = 0, changed = 0, jj = -1;
-    if (sel) {
-        const int32_t kk = D.dk[i], p = C.A.ptr[i];
-        const bool j_first = C.A.idx[p] != kk;
-        jj = j_first ? C.A.idx[p] : C.A.idx[p + 1];
-        const double a = j_first ? C.A.val[p] : C.A.val[p + 1];
-        const double bk = j_first ? C.A.val[p + 1] : C.A.val[p];
-        const double cv = C.L[i];
-        const double f = a / bk, g = cv / bk;
-        const double2 luj = C.lu[jj], luk = C.lu[kk];
-        double lo, hi;
-        if (f > 0.0) {
-            lo = is_fin(luk.y) ? (g - luk.y) / f : ninf_();
-            hi = is_fin(luk.x) ? (g - luk.x) / f : pinf();
-        } else {
-            lo = is_fin(luk.x) ? (g - luk.x) / f : ninf_();
-            hi = is_fin(luk.y) ? (g - luk.y) / f : pinf();
-        }
-        double nl = lo > luj.x ? lo : luj.x;
-        double nu = hi < luj.y ? hi : luj.y;
-        const int32_t lp = lp_of_row(C, i);
-        if (is_fin(nl) && is_fin(nu)) {
-            const double d = C.feas_tol * fmax(1.0, fmax(fabs(nl), fabs(nu)));
-            if (nl - nu > d) {
-                atomicMin(&C.verdict[lp * V_SLOTS + V_S5E_COL], C.cmap[jj]);
-                sel = false;
-            } else if (nl != nu && fabs(nl - nu) <= d) {  // as S3' finalises: a symmetric snap
-                nl = nu = 0.5 * (nl + nu);
-            }
-        }
-        if (sel) {
-            changed = nl != luj.x || nu != luj.y;
-            C.lu[jj] = make_double2(nl, nu);
-            const double t = C.c[kk] / bk;
-            C.c[jj] = C.c[jj] - t * a;
-            C.rkind[i] = RK_DOUBLETON;
-            C.ckind[kk] = CK_DOUBLETON;
-            C.fixv[kk] = g;
-            const int32_t oi = C.rmap[i], ok = C.cmap[kk], oj = C.cmap[jj], rd = lp_round(C, lp);
-            C.rec_rk[oi] = RK_DOUBLETON;
-            C.rec_rr[oi] = rd;
-            C.rec_ra[oi] = ok;
-            C.rec_rv[oi] = bk;
-            const unsigned long long pos = atomicAdd(C.sub_used, 1ULL);
-            C.rec_sb[oi] = (long long)pos;
-            C.rec_sl[oi] = 1;
-            C.rec_srhs[oi] = cv;
-            C.rec_scol[pos] = oj;
-            C.rec_sval[pos] = a;
-            C.rec_ck[ok] = CK_DOUBLETON;
-            C.rec_cr[ok] = rd;
-            C.rec_cv[ok] = g;
-            C.lp_changed[lp] = 1;
-            if (C.plen) C.plen[oj] = -1;  // x_j's entries change: its S5c key is recomputed
-            D.dj[i] = jj;
-            D.df[i] = f;
-            D.dg[i] = g;
-            b = C.T.ptr[kk];
-            e = C.T.ptr[kk + 1];
-            applied = 1;
-        }
-    }
+    S5eApplied r{S5eWalk{false, 0, 0}, 0, -1};
+    if (i < C.m && D.dsel[i]) r = s5e_apply_row(C, D, i);
     __syncwarp();  // the owners' dj, df, dg before the warp reads them
-    warp_walk(sel, b, e, i, [&](int32_t src, int32_t k) {
-        const int32_t rr = C.T.idx[k];
-        if (rr == src || C.rkind[rr] != RK_KEPT) return;
-        const double ark = C.T.val[k];
-        const double f = D.df[src], g = D.dg[src];
-        const double Lv = C.L[rr], Uv = C.U[rr];
-        if (is_fin(Lv)) C.L[rr] = Lv - ark * g;
-        if (is_fin(Uv)) C.U[rr] = Uv - ark * g;
-        D.dmj[rr] = D.dj[src];
-        D.dmk[rr] = D.dk[src];
-        D.dmd[rr] = -(ark * f);
-        C.rdnext[rr] = 1;
-    });
-    block_append(applied != 0, jj, &D.cnt[1], D.jlist);
+    warp_walk(r.w.own, r.w.b, r.w.e, i, [&](int32_t src, int32_t k) { s5e_shift_entry(C, D, src, k); });
+    const int32_t applied = r.w.own ? 1 : 0;
+    block_append(applied != 0, r.jj, &D.cnt[1], D.jlist);
     block_add(applied, &C.st->rows_removed);
     block_add(applied, &C.st->cols_fixed);
-    block_add(changed, &C.st->bounds_changed);
+    block_add(r.changed, &C.st->bounds_changed);
     block_add(applied, &D.cnt[0]);
 }
 
-// one thread per row: the rewritten length (x_k out; x_j's entry merged,
-// dropped when it cancels, or inserted) and, for a changed row, the
-// positions of x_k and of x_j (or where x_j goes), the flags and the value
+// one thread per row: the rewritten length and a changed row's note
 __global__ void __launch_bounds__(kBlock) k_s5e_rowlen(Ctx C, S5eBufs D, int32_t *rlen) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= C.m) return;
-    const int32_t p = C.A.ptr[i], len = C.A.ptr[i + 1] - p, jj = D.dmj[i];
-    int32_t nl = len;
-    if (jj >= 0) {
-        const S5eNote t = s5e_note(C.A.idx + p, C.A.val + p, len, jj, D.dmk[i], D.dmd[i], C.par_tol);
-        nl = t.len_new;
-        D.dpk[i] = t.pk;
-        D.dpj[i] = t.pj;
-        D.dfl[i] = (uint8_t)((t.found ? 1 : 0) | (t.cancel ? 2 : 0));
-        D.dnv[i] = t.v;
-    }
-    rlen[i] = nl;
+    if (i < C.m) rlen[i] = s5e_rowlen_row(C, D, i);
 }
 
 // one thread per entry of the current CSR: its place in the rewritten CSR
-// (rp2 the scanned new lengths).  In a changed row, with pk the position of
-// x_k and pj that of x_j (or where it goes), an entry at position q moves to
-//   rp2[i] + q - [q > pk] + [x_j inserted and q >= pj]
-//                         - [x_j cancelled and q > pj];
-// the thread of x_k's entry writes an inserted x_j at rp2[i] + pj - [pk < pj].
 __global__ void __launch_bounds__(kBlock) k_s5e_scatter(Ctx C, S5eBufs D, const int32_t *rp2, int32_t *ci2,
                                                        double *rv2, int32_t *row_of, int32_t nnz) {
     const int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nnz) return;
-    // the row of e: the last i with ptr[i] <= e
-    int32_t lo = 0, hi = C.m;
-    while (hi - lo > 1) {
-        const int32_t mid = lo + ((hi - lo) >> 1);
-        if (C.A.ptr[mid] <= e) lo = mid;
-        else hi = mid;
-    }
-    const int32_t i = lo, q = e - C.A.ptr[i], base = rp2[i];
-    int32_t col = C.A.idx[e];
-    double v = C.A.val[e];
-    int32_t dest = base + q;
-    const int32_t jj = D.dmj[i];
-    if (jj >= 0) {
-        S5eNote t;
-        t.pk = D.dpk[i];
-        t.pj = D.dpj[i];
-        t.found = D.dfl[i] & 1;
-        t.cancel = D.dfl[i] & 2;
-        if (q == t.pk) {
-            if (!t.found) {
-                const int32_t at = base + s5e_insert_at(t);
-                ci2[at] = jj;
-                rv2[at] = D.dnv[i];
-                row_of[at] = i;
-            }
-            return;
-        }
-        if (t.found && q == t.pj) {
-            if (t.cancel) return;
-            v = D.dnv[i];
-        }
-        dest = base + s5e_dest(t, q);
-    }
-    ci2[dest] = col;
-    rv2[dest] = v;
-    row_of[dest] = i;
+    if (e < nnz) s5e_place_entry(C, D, rp2, ci2, rv2, row_of, e);
 }
 
 // one thread per applied doubleton: the rows of x_j in the rewritten CSC
