@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kBlock) k_s5e_rowlen(Ctx C, S5eBufs D, int32_t
 __global__ void __launch_bounds__(kBlock) k_s5e_scatter(Ctx C, S5eBufs D, const int32_t *rp2, int32_t *ci2,
                                                        double *rv2, int32_t *row_of, int32_t nnz) {
     const int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < nnz) s5e_place_entry(C, D, rp2, ci2, rv2, row_of, e);
+    if (e < nnz && !s5e_place_entry(C, D, rp2, ci2, rv2, row_of, e)) atomicOr(&C.st->err, 2);
 }
 
 // one thread per applied doubleton: the rows of x_j in the rewritten CSC

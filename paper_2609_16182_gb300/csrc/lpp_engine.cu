@@ -988,6 +988,7 @@ void Engine::run_s5e(const Ctx &C) {
         nnz = nnz2;
         schedule_current();
         read_status();
+        if (st_h->err) throw StatusError(LPP_ERR_CUDA, "internal: S5e rewrite placed an entry outside its row");
         adopt_schedule();
         launch_s5e_mark(ctx(C.round), de, nj, s);
         LPP_CUDA(cudaGetLastError());

@@ -201,8 +201,10 @@ __host__ __device__ inline int32_t s5e_rowlen_row(const Ctx &C, const S5eBufs &D
 }
 
 // Entry e of the current CSR into the rewritten one (rp2: the scanned new
-// lengths); the entry of x_k in a changed row writes an inserted x_j
-__host__ __device__ inline void s5e_place_entry(const Ctx &C, const S5eBufs &D, const int32_t *rp2, int32_t *ci2,
+// lengths); the entry of x_k in a changed row writes an inserted x_j.  A
+// place outside the row's new range is not written and returns false (the
+// lengths and the notes disagree: an internal error the caller reports).
+__host__ __device__ inline bool s5e_place_entry(const Ctx &C, const S5eBufs &D, const int32_t *rp2, int32_t *ci2,
                                                 double *rv2, int32_t *row_of, int32_t e) {
     // the row of e: the last i with ptr[i] <= e
     int32_t lo = 0, hi = C.m;
@@ -225,21 +227,24 @@ __host__ __device__ inline void s5e_place_entry(const Ctx &C, const S5eBufs &D, 
         if (q == t.pk) {
             if (!t.found) {
                 const int32_t at = base + s5e_insert_at(t);
+                if (at < base || at >= rp2[i + 1]) return false;
                 ci2[at] = jj;
                 rv2[at] = D.dnv[i];
                 row_of[at] = i;
             }
-            return;
+            return true;
         }
         if (t.found && q == t.pj) {
-            if (t.cancel) return;
+            if (t.cancel) return true;
             v = D.dnv[i];
         }
         dest = base + s5e_dest(t, q);
     }
+    if (dest < base || dest >= rp2[i + 1]) return false;
     ci2[dest] = col;
     rv2[dest] = v;
     row_of[dest] = i;
+    return true;
 }
 
 }  // namespace lpp

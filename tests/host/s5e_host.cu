@@ -101,7 +101,8 @@ extern "C" int32_t s5e_host_round(int32_t m, int32_t n, int32_t round, const int
     rp2[0] = 0;
     for (int32_t i = 0; i < m; i++) rp2[i + 1] = rp2[i] + s5e_rowlen_row(C, D, i);
     if (rp2[m] > nnz) return -1;
-    for (int32_t e = 0; e < nnz; e++) s5e_place_entry(C, D, rp2, ci2, rv2, row_of.data(), e);
+    for (int32_t e = 0; e < nnz; e++)
+        if (!s5e_place_entry(C, D, rp2, ci2, rv2, row_of.data(), e)) return -3;  // outside its row
     for (int32_t i = 0; i < m; i++)
         for (int32_t q = rp2[i]; q < rp2[i + 1]; q++)
             if (row_of[(size_t)q] != i) return -2;  // a slot of row i not written by row i
