@@ -28,11 +28,11 @@
 // walks over x_k's column (claims, the check of the claims, the side
 // shifts) run on the owning thread for columns of at most 32 entries and on
 // the whole warp, in turn, for longer ones.  The work per row and per entry
-// is in s5e_logic.cuh, shared with a host build of the same steps.  When a round applies any
-// doubleton, the CSR is rewritten into the other buffer (each changed row's
-// new length by binary searches, a scan, one thread per entry placing it),
-// the CSC is rebuilt from it by the ingest transpose, and S6 and the
-// compaction then work on the rewritten matrices.
+// is in s5e_logic.cuh, shared with a host build of the same steps.  When a
+// round applies any doubleton, the CSR is rewritten into the other buffer
+// (each changed row's new length by binary searches, a scan, one thread per
+// entry placing it), the CSC is rebuilt from it by the ingest transpose, and
+// S6 and the compaction then work on the rewritten matrices.
 #include <algorithm>
 
 #include "s5e_logic.cuh"
