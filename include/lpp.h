@@ -88,7 +88,11 @@ typedef enum lpp_status {
 #define LPP_COL_PARALLEL 3    /* merged into a parallel leader column (S5c)       */
 #define LPP_COL_SUBST 4       /* free column singleton eliminated (S5d)           */
 #define LPP_COL_DOUBLETON 5   /* eliminated through a doubleton equation (S5e)    */
-/* Where a verdict was found. */
+/* Where a verdict was found.  Within a round the first step that finds one
+ * decides, in step order: S2 (a row's sides or activities), S3' (a column's
+ * bounds cross), S5 (merged parallel sides cross), S5e (a doubleton's bound
+ * transfer is empty), S6 (an unbounded fixing value: LPP_UNBOUNDED); each
+ * step reports its smallest original index. */
 #define LPP_WHERE_NONE 0
 #define LPP_WHERE_ROW 1
 #define LPP_WHERE_COL 2
