@@ -112,6 +112,25 @@ def test_two_empty_transfers_report_the_smaller_column():
     assert (res.status, res.where, res.index, res.round) == (oracle.INFEASIBLE, oracle.WHERE_COL, 0, 1)
 
 
+def test_steps_before_s5e_take_precedence():
+    # x0 + x1 = 2 with x1 a free, zero-cost column singleton: S5d (when on) eliminates x1 through
+    # row 0 first, so S5e finds no candidate; without S5d, S5e eliminates x1 (the shorter column)
+    lp = make([{0: 1.0, 1: 1.0}, {0: 1.0, 2: 1.0}], [2.0, -INF], [2.0, 3.0],
+              [0.0, -INF, 0.0], [5.0, INF, 5.0], c=[1.0, 0.0, 1.0])
+    res = oracle.presolve(lp, opts(max_rounds=1, dual_reductions=0))
+    assert (res.row_kind[0], res.col_kind[1]) == (oracle.ROW_DOUBLETON, oracle.COL_DOUBLETON)
+    res = oracle.presolve(lp, opts(col_singletons=1, max_rounds=1, dual_reductions=0))
+    assert (res.row_kind[0], res.col_kind[1]) == (oracle.ROW_SUBST, oracle.COL_SUBST)
+    # x1 = 2 x0 column-wise (rows 0 and 1, costs 1 and 2): S5c merges x1 into x0 before S5e,
+    # and row 0 then holds a merged column, which S5e does not take
+    lp = make([{0: 1.0, 1: 2.0}, {0: 1.0, 1: 2.0, 2: 1.0}], [3.0, -INF], [3.0, 9.0],
+              [0.0, 0.0, 0.0], [4.0, 4.0, 4.0], c=[1.0, 2.0, 1.0])
+    res = oracle.presolve(lp, opts(max_rounds=1, dual_reductions=0))
+    assert (res.row_kind[0], res.col_kind[1]) == (oracle.ROW_DOUBLETON, oracle.COL_DOUBLETON)
+    res = oracle.presolve(lp, opts(parallel_cols=1, max_rounds=1, dual_reductions=0))
+    assert (res.row_kind[0], res.col_kind[1]) == (oracle.ROW_KEPT, oracle.COL_PARALLEL)
+
+
 def test_off_by_default():
     lp = synth.lprelax(1, m=600, n=1200, target_nnz=9_600, n_dense=1, dense_len=200)
     assert not np.any(oracle.presolve(lp).row_kind == oracle.ROW_DOUBLETON)
