@@ -47,6 +47,26 @@ def test_hand_worked_elimination():
     assert list(x) == [2.0, 1.0, 0.0]
 
 
+def test_both_sides_of_a_changed_row_shift():
+    # the hand-worked LP with row 1 two-sided, -20 <= 3 x0 + 4 x1 + x2 <= 10: both sides lose 4 g = 8
+    lp = make([{0: 1.0, 1: 2.0}, {0: 3.0, 1: 4.0, 2: 1.0}, {0: 1.0, 2: -1.0}], [4.0, -20.0, -5.0], [4.0, 10.0, INF],
+              [0.0, 0.0, -1.0], [3.0, 1.5, 1.0], c=[1.0, 2.0, 3.0])
+    res = oracle.presolve(lp, opts(max_rounds=1, dual_reductions=0))
+    entries, lhs, rhs = row_of(res, 1)
+    assert entries == {0: 1.0, 2: 1.0} and (lhs, rhs) == (-28.0, 2.0)
+
+
+def test_doubletons_sharing_a_changed_row_wait_a_round():
+    # rows 0 and 1 eliminate x1 and x3 (the shorter columns); row 2 holds both, so both claim it:
+    # row 0 applies in round 1, row 1 in round 2
+    lp = make([{0: 1.0, 1: 1.0}, {2: 1.0, 3: 1.0}, {1: 1.0, 3: 1.0, 4: 1.0}, {0: 1.0, 2: 1.0}, {0: 1.0, 2: -1.0}],
+              [1.0, 1.0, -INF, -INF, -0.5], [1.0, 1.0, 2.0, 1.5, INF],
+              [0.0] * 5, [1.0] * 5, c=[1.0] * 5)
+    res = oracle.presolve(lp, opts(dual_reductions=0))
+    assert res.status == oracle.OK
+    assert list(res.row_kind[:2]) == [oracle.ROW_DOUBLETON] * 2 and list(res.row_round[:2]) == [1, 2]
+
+
 def test_cancellation_drops_the_entry():
     # row 1: 2 x0 + 4 x1 + x2 <= 10 -> (2 - 2) x0 + x2 <= 2: x0 leaves row 1
     lp = make([{0: 1.0, 1: 2.0}, {0: 2.0, 1: 4.0, 2: 1.0}, {0: 1.0, 2: -1.0}], [4.0, -INF, -5.0], [4.0, 10.0, INF],
@@ -96,10 +116,13 @@ def test_transferred_bounds_within_tolerance_snap():
     # l0 >= 9, a gain below bound_tol * 9): [9, 9 + 5e-9], 5e-9 apart, within feas_tol * 9.  As in
     # S3', the bounds snap to their midpoint although they do not cross; x0 is fixed in round 2
     lp = make([{0: 1.0, 1: 1.0}], [10.0], [10.0], [9.0 - 4e-6, 0.0], [9.0 + 5e-9, 1.0], c=[1.0, 1.0])
+    mid = 0.5 * (9.0 + (9.0 + 5e-9))
+    res = oracle.presolve(lp, opts(max_rounds=1, dual_reductions=0))
+    assert res.row_kind[0] == oracle.ROW_DOUBLETON and (res.lb[0], res.ub[0]) == (mid, mid)  # snapped in S5e
     res = oracle.presolve(lp, opts(dual_reductions=0))
     assert res.status == oracle.OK and res.row_kind[0] == oracle.ROW_DOUBLETON
     assert list(res.col_kind) == [oracle.COL_FIXED, oracle.COL_DOUBLETON] and list(res.col_round) == [2, 1]
-    assert res.col_val[0] == 0.5 * (9.0 + (9.0 + 5e-9))
+    assert res.col_val[0] == mid
 
 
 def test_two_empty_transfers_report_the_smaller_column():

@@ -1,0 +1,110 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of oracle/lpp_oracle.c (a flipped
+sign, swapped interval ends, a dropped test, the wrong eliminated column,
+...), builds it apart from the real oracle, and runs the pins of the step
+it touches against it: at least one of them must fail.  A control run of
+the unaltered source through the same harness passes.  No GPU needed."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "lpp_oracle.c")
+
+RULES = ["tests/test_oracle_rules.py"]
+S5E = ["tests/test_oracle_doubleton.py", "-k",
+       "hand_worked or both_sides or cancellation or empty or snap or sharing or steps_before"]
+S5D = ["tests/test_oracle_colsing.py", "-k",
+       "hand_worked or implied_free or inequality_rows or one_substitution or zero_cost"]
+S5C = ["tests/test_oracle_parcols.py"]
+DUALFIX = ["tests/test_oracle_dualfix.py", "-k", "hand_worked or unbounded"]
+POST = ["tests/test_oracle_colsing.py", "-k", "optimum_kept and 0"]
+
+# (name, text in the oracle, its replacement, pins to run)
+MUTANTS = [
+    ("activity: bounds of a negative coefficient swapped",
+     "double bmin = a > 0 ? l[j] : u[j];", "double bmin = a > 0 ? u[j] : l[j];", RULES),
+    ("S2: infeasible activity test dropped",
+     "if (mna[i] > U + tol_at(ft, U)) { bad = i; break; }", "if (0) { bad = i; break; }", RULES),
+    ("S3: residual takes the wrong sign",
+     "rmin = mna[i] - a * bmin;", "rmin = mna[i] + a * bmin;", RULES),
+    ("S3: acceptance threshold on the wrong side",
+     "double thr = s.u[jj] - o->bound_tol * dmax(1.0, fabs(s.u[jj]));",
+     "double thr = s.u[jj] + o->bound_tol * dmax(1.0, fabs(s.u[jj]));", RULES),
+    ("S5: merged sides of a negative factor not swapped",
+     "lo = isfin(s.U[fj]) ? s.U[fj] / lam : -INFINITY; eblo = s.ebU[fj] / fabs(lam);",
+     "lo = isfin(s.L[fj]) ? s.L[fj] / lam : -INFINITY; eblo = s.ebU[fj] / fabs(lam);", RULES),
+    ("S6: cost sign read backwards",
+     "if (s.c[j] > 0) { fix = dlock[j] == 0; v = s.l[j]; }",
+     "if (s.c[j] < 0) { fix = dlock[j] == 0; v = s.l[j]; }", RULES),
+    ("S7: side shift of fixed columns added instead of subtracted",
+     "if (isfin(s.L[i])) { s.L[i] = s.L[i] - sh;", "if (isfin(s.L[i])) { s.L[i] = s.L[i] + sh;", RULES),
+    ("S5c: merged bounds of a positive factor use the wrong ends",
+     "if (lam > 0) { ly = ly + lam * lj; uy = uy + lam * uj; }",
+     "if (lam > 0) { ly = ly + lam * uj; uy = uy + lam * lj; }", S5C),
+    ("S5d: substitution side chosen against the cost",
+     "if (c != 0.0) return (c > 0) == (a > 0) ? L : U;", "if (c != 0.0) return (c > 0) == (a > 0) ? U : L;", S5D),
+    ("dual fixing: locks of a negative coefficient not mirrored",
+     "else { dlock[jj] += isfin(s.U[i]); ulock[jj] += isfin(s.L[i]); }",
+     "else { dlock[jj] += isfin(s.L[i]); ulock[jj] += isfin(s.U[i]); }", DUALFIX),
+    ("S5e: the longer column eliminated",
+     "kk = tcp[c1 + 1] - tcp[c1] <= tcp[c0 + 1] - tcp[c0] ? c1 : c0;",
+     "kk = tcp[c1 + 1] - tcp[c1] <= tcp[c0 + 1] - tcp[c0] ? c0 : c1;", S5E),
+    ("S5e: side shift with the wrong sign",
+     "s.L[rr] = s.L[rr] - ark * g;", "s.L[rr] = s.L[rr] + ark * g;", S5E),
+    ("S5e: coefficient change with the wrong sign",
+     "dmd[rr] = -(ark * f);", "dmd[rr] = (ark * f);", S5E),
+    ("S5e: cost update with the wrong sign",
+     "s.c[jj] = s.c[jj] - t * a;", "s.c[jj] = s.c[jj] + t * a;", S5E),
+    ("S5e: claims of the changed rows ignored",
+     "if (rr != i && kind[rr] == LPPO_ROW_KEPT && dminr[rr] != i) sel = 0;", "if (0) sel = 0;", S5E),
+    ("S5e: bounds within the tolerance left apart",
+     "if (nl != nu && fabs(nl - nu) <= d) {", "if (nl > nu && fabs(nl - nu) <= d) {", S5E),
+    ("postsolve: a substituted column divided by the wrong coefficient",
+     "x_orig[jj] = (sub_rhs[ii] - sum) / row_val[ii];", "x_orig[jj] = (sub_rhs[ii] - sum) * row_val[ii];", POST),
+]
+
+
+def build(tmp, text):
+    src = os.path.join(tmp, "lpp_oracle.c")
+    shutil.copy(os.path.join(ROOT, "oracle", "lpp_oracle.h"), tmp)
+    with open(src, "w") as f:
+        f.write(text)
+    lib = os.path.join(tmp, "liblpp_oracle.so")
+    subprocess.run(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                    "-o", lib, src, "-lm"], check=True, capture_output=True)
+    return lib
+
+
+def run_pins(lib, pins):
+    env = dict(os.environ, LPPO_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
+                        *pins], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return r.returncode, r.stdout[-1500:]
+
+
+@pytest.fixture(scope="module")
+def source():
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not found")
+    with open(SRC) as f:
+        return f.read()
+
+
+def test_control_passes(source, tmp_path):
+    lib = build(str(tmp_path), source)
+    for pins in (RULES, S5E):
+        rc, out = run_pins(lib, pins)
+        assert rc == 0, out
+
+
+@pytest.mark.parametrize("name, old, new, pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(source, tmp_path, name, old, new, pins):
+    assert source.count(old) == 1, f"mutation site not unique or gone: {old!r}"
+    lib = build(str(tmp_path), source.replace(old, new))
+    rc, out = run_pins(lib, pins)
+    assert rc == 1, f"{name}: no pin failed (rc {rc})\n{out}"

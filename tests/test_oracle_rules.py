@@ -75,6 +75,21 @@ def test_infeasible_activity():
     assert r.status == oracle.INFEASIBLE and r.where == 1 and r.index == 0
 
 
+def test_infeasible_min_activity_is_a_row_verdict():
+    # x1 + x2 <= -1 with x >= 0: min activity 0 > -1, found by S2 at the row (S3 alone would find
+    # column 0's bounds crossing)
+    lp = make([{0: 1.0, 1: 1.0}], lhs=[-INF], rhs=[-1], lb=[0, 0], ub=[1, 1])
+    r = run(lp)
+    assert (r.status, r.where, r.index, r.round) == (oracle.INFEASIBLE, 1, 0, 1)
+
+
+def test_residual_activity_of_lower_bounds():
+    # x1 + x2 <= 10 with x1 >= 2, x2 >= 3: u1 <= 10 - 3 = 7 and u2 <= 10 - 2 = 8
+    lp = make([{0: 1.0, 1: 1.0}], lhs=[-INF], rhs=[10], lb=[2, 3], ub=[100, 100])
+    r = run(lp, max_rounds=1)
+    assert (r.ub[0], r.ub[1]) == (7.0, 8.0)
+
+
 def test_crossing_bounds_infeasible_column():
     # singletons x1 >= 5 and x1 <= 3 give l = 5 > u = 3
     lp = make([{0: 1.0}, {0: 1.0}], lhs=[5, -INF], rhs=[INF, 3], lb=[0], ub=[10])
@@ -141,6 +156,16 @@ def test_parallel_rows_inequality_leader_and_infeasible_pair():
     r = run(lp)
     assert r.status == oracle.OK and r.row_kind[1] == oracle.ROW_PARALLEL and r.row_val[1] == 2.0
     assert list(r.lhs) == [2.0] and list(r.rhs) == [3.0]
+
+
+def test_parallel_rows_negative_factor_swaps_the_sides():
+    # leader x1 + x2 <= 3, follower -2 x1 - 2 x2 <= -2 (lambda = -2): the follower says x1 + x2 >= 1,
+    # so the leader's sides become [1, 3]
+    lp = make([{0: 1.0, 1: 1.0}, {0: -2.0, 1: -2.0}], lhs=[-INF, -INF], rhs=[3, -2], lb=[-INF, -INF],
+              ub=[INF, INF])
+    r = run(lp)
+    assert r.row_kind[1] == oracle.ROW_PARALLEL and r.row_val[1] == -2.0
+    assert list(r.lhs) == [1.0] and list(r.rhs) == [3.0]
 
 
 def test_parallel_needs_same_pattern_and_ratio():
