@@ -37,12 +37,14 @@ def test_hand_worked_substitution():
     assert list(x) == [1.5, 0.5, 2 * 1.5 + 0.5 - 4]
 
 
+@pytest.mark.parametrize("sign", [1.0, -1.0])
 @pytest.mark.parametrize("lo,hi,eliminated", [(-100.0, 100.0, True), (-1.0, 1.0, False), (-INF, 3.0, True),
-                                              (-INF, 1.0, False)])
-def test_implied_free(lo, hi, eliminated):
-    # x2 = 2 x0 + x1 - 4 with x0, x1 in [0, 2]: the row implies x2 in [-4, 2]
-    lp = make([{0: 2.0, 1: 1.0, 2: -1.0}, {0: 1.0, 1: 1.0}], [4.0, -INF], [4.0, 3.0],
-              [0.0, 0.0, lo], [2.0, 2.0, hi], c=[1.0, 2.0, 3.0])
+                                              (-INF, 1.0, False), (-3.0, 5.0, False), (-5.0, 3.0, True)])
+def test_implied_free(lo, hi, eliminated, sign):
+    # x2 = 2 x0 + x1 - 4 with x0, x1 in [0, 2]: the row implies x2 in [-4, 2], whichever sign the
+    # row is written with (x2's coefficient -1, or +1 for the negated row)
+    lp = make([{0: 2.0 * sign, 1: 1.0 * sign, 2: -1.0 * sign}, {0: 1.0, 1: 1.0}], [4.0 * sign, -INF],
+              [4.0 * sign, 3.0], [0.0, 0.0, lo], [2.0, 2.0, hi], c=[1.0, 2.0, 3.0])
     res = oracle.presolve(lp, opts(max_rounds=1))
     assert (res.col_kind[2] == oracle.COL_SUBST) == eliminated
 

@@ -5,6 +5,7 @@ sign, swapped interval ends, a dropped test, the wrong eliminated column,
 ...), builds it apart from the real oracle, and runs the pins of the step
 it touches against it: at least one of them must fail.  A control run of
 the unaltered source through the same harness passes.  No GPU needed."""
+import concurrent.futures as cf
 import os
 import shutil
 import subprocess
@@ -64,6 +65,37 @@ MUTANTS = [
      "if (rr != i && kind[rr] == LPPO_ROW_KEPT && dminr[rr] != i) sel = 0;", "if (0) sel = 0;", S5E),
     ("S5e: bounds within the tolerance left apart",
      "if (nl != nu && fabs(nl - nu) <= d) {", "if (nl > nu && fabs(nl - nu) <= d) {", S5E),
+    ("S2: redundancy accepted one-sided (the upper side never checked)",
+     "hi_ok = mxa[i] <= U + tol_at(ft, U);", "hi_ok = 1;", RULES),
+    ("S2: an infinite lhs not treated as satisfied",
+     "if (L == -INFINITY) lo_ok = 1;", "if (L == -INFINITY) lo_ok = 0;", RULES),
+    ("S3': close bounds not snapped",
+     "if (lp_ != up_ && fabs(lp_ - up_) <= d) {", "if (0) {", RULES),
+    ("S4: a column fixed at its upper bound value taken from the wrong side",
+     "fixv[j] = s.l[j];\n            if (fixed[j]) {", "fixv[j] = s.u[j] + 1.0;\n            if (fixed[j]) {", RULES),
+    ("S6: a zero-cost column prefers its upper bound",
+     "else if (dlock[j] == 0 && isfin(s.l[j])) { fix = 1; v = s.l[j]; }",
+     "else if (dlock[j] == 0 && isfin(s.u[j])) { fix = 1; v = s.u[j]; }", RULES),
+    ("S5: the parallel factor inverted",
+     "lam = aj[0] / ai[0];", "lam = ai[0] / aj[0];", RULES),
+    ("S5c: cost test dropped",
+     "if (par && !(fabs(s.c[cj] - lc) <= o->par_tol * dmax(fabs(s.c[cj]), fabs(lc)))) par = 0;",
+     "if (0) par = 0;", S5C),
+    ("S5d: implied range of a positive coefficient from the wrong rest",
+     "lo = nmx_ == 0 ? (b - mxr) / a : -INFINITY; eblo = (ebb + eb_mx) / fabs(a) + UROUND * fabs(lo);\n"
+     "                    hi = nmn_ == 0 ? (b - mnr) / a : INFINITY;",
+     "lo = nmx_ == 0 ? (b - mnr) / a : -INFINITY; eblo = (ebb + eb_mx) / fabs(a) + UROUND * fabs(lo);\n"
+     "                    hi = nmn_ == 0 ? (b - mxr) / a : INFINITY;", S5D),
+    ("S5d: the other columns' costs not updated",
+     "if (s.c[j] != 0.0) s.c[kk] = s.c[kk] - t * s.v[k];", "if (0) s.c[kk] = s.c[kk] - t * s.v[k];", S5D),
+    ("S5e: cancellation never drops the entry",
+     "if (fabs(v) <= o->par_tol * dmax(fabs(s.v[k]), fabs(dmd[i]))) continue;",
+     "if (0) continue;", S5E),
+    ("S5e: a candidate's column claims ignored",
+     "if (dminc[jj] != i || dminc[kk] != i || dminr[i] != i) sel = 0;", "if (dminr[i] != i) sel = 0;", S5E),
+    ("postsolve: a merge undone with the wrong ends",
+     "if (lam > 0) { lo = (y - uk) / lam; hi = (y - lk) / lam; }",
+     "if (lam > 0) { lo = (y - lk) / lam; hi = (y - uk) / lam; }", S5C),
     ("postsolve: a substituted column divided by the wrong coefficient",
      "x_orig[jj] = (sub_rhs[ii] - sum) / row_val[ii];", "x_orig[jj] = (sub_rhs[ii] - sum) * row_val[ii];", POST),
 ]
@@ -95,16 +127,30 @@ def source():
         return f.read()
 
 
-def test_control_passes(source, tmp_path):
-    lib = build(str(tmp_path), source)
-    for pins in (RULES, S5E):
-        rc, out = run_pins(lib, pins)
-        assert rc == 0, out
+@pytest.fixture(scope="module")
+def outcomes(source, tmp_path_factory):
+    """Every mutant (and the control) built and run once, in parallel:
+    name -> (return code, output tail)."""
+    jobs = [("control", source, RULES + ["tests/test_oracle_doubleton.py"])]
+    for name, old, new, pins in MUTANTS:
+        assert source.count(old) == 1, f"mutation site not unique or gone: {old!r}"
+        jobs.append((name, source.replace(old, new), pins))
+
+    def one(job):
+        name, text, pins = job
+        lib = build(str(tmp_path_factory.mktemp("mutant")), text)
+        return name, run_pins(lib, pins)
+
+    with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+        return dict(ex.map(one, jobs))
 
 
-@pytest.mark.parametrize("name, old, new, pins", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_mutant_is_caught(source, tmp_path, name, old, new, pins):
-    assert source.count(old) == 1, f"mutation site not unique or gone: {old!r}"
-    lib = build(str(tmp_path), source.replace(old, new))
-    rc, out = run_pins(lib, pins)
+def test_control_passes(outcomes):
+    rc, out = outcomes["control"]
+    assert rc == 0, out
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+def test_mutant_is_caught(outcomes, name):
+    rc, out = outcomes[name]
     assert rc == 1, f"{name}: no pin failed (rc {rc})\n{out}"

@@ -77,6 +77,16 @@ def test_merged_bounds_are_the_closed_form():
     assert (res.lb[k], res.ub[k]) == (-1.0 - 2.0 * 3.0, 2.0 - 2.0 * 0.5)
 
 
+def test_costs_must_be_in_the_same_ratio():
+    # the closed-form LP with c1 = -2.5 instead of -2 = lam c0: the coefficients are parallel, the
+    # costs are not, so nothing merges
+    from lpmake import make
+    lp = make([{0: 1.0, 1: -2.0, 2: 1.0}, {0: 3.0, 1: -6.0, 2: -1.0}], [-8.0, -22.0], [2.9, 4.9],
+              [-1.0, 0.5, -2.0], [2.0, 3.0, 2.0], c=[1.0, -2.5, 0.5])
+    res = oracle.presolve(lp, oracle.default_opts(parallel_cols=1, max_rounds=1))
+    assert not np.any(res.col_kind == oracle.COL_PARALLEL)
+
+
 @pytest.mark.parametrize("seed", range(40))
 def test_optimum_kept_and_postsolve_optimal(seed):
     lp = synth.parcols(seed + 500, m=4, n_base=4, pairs=2, per_col=3, slack=1.0)
