@@ -96,6 +96,27 @@ MUTANTS = [
     ("postsolve: a merge undone with the wrong ends",
      "if (lam > 0) { lo = (y - uk) / lam; hi = (y - lk) / lam; }",
      "if (lam > 0) { lo = (y - lk) / lam; hi = (y - uk) / lam; }", S5C),
+    ("S1: an infinite min-activity term not counted",
+     "        else c_mn++;", "        else (void)c_mn;", RULES),
+    ("S2: a singleton row's bounds not mirrored for a negative coefficient",
+     "cl = isfin(U) ? U / a : -INFINITY;", "cl = isfin(L) ? L / a : -INFINITY;", RULES),
+    ("S3: the cap on implied bounds dropped",
+     "if (fabs(cv) > o->max_implied) continue;", "if (0) continue;", RULES),
+    ("S3: the one infinite term's own bound not implied",
+     "if (!isfin(bmin)) { rmin_ok = nmn[i] == 1;", "if (!isfin(bmin)) { rmin_ok = 0;", RULES),
+    ("S5: the leader is the first row even when an equality follows",
+     "if (alive[t] && isfin(s.L[rr]) && s.L[rr] == s.U[rr]) lead = t;", "if (0) lead = t;", RULES),
+    ("S5c: merged bounds of a negative factor use the wrong ends",
+     "else { ly = ly + lam * uj; uy = uy + lam * lj; }", "else { ly = ly + lam * lj; uy = uy + lam * uj; }", S5C),
+    ("S5d: the eliminated column's value inverted",
+     "fixed[j] = 4; fixv[j] = b / a;", "fixed[j] = 4; fixv[j] = a / b;", S5D),
+    ("S5e: g from the kept column's coefficient",
+     "f = a / b; g = c / b;", "f = a / b; g = c / a;", S5E),
+    ("S6: an infinite preferred bound not reported unbounded",
+     "if (!isfin(v)) { bad = j; break; }", "if (0) { bad = j; break; }", RULES),
+    ("objective constant: fixed columns' cost terms with the wrong sign",
+     "if (fixed[j] && fixed[j] != 3) s.offset += s.c[j] * fixv[j];",
+     "if (fixed[j] && fixed[j] != 3) s.offset -= s.c[j] * fixv[j];", RULES),
     ("postsolve: a substituted column divided by the wrong coefficient",
      "x_orig[jj] = (sub_rhs[ii] - sum) / row_val[ii];", "x_orig[jj] = (sub_rhs[ii] - sum) * row_val[ii];", POST),
 ]

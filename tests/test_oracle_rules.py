@@ -62,6 +62,7 @@ def test_singleton_rows_become_bounds():
     assert list(r.row_aux[:3]) == [0, 1, 2]
     assert list(r.row_val[:3]) == [2.0, -2.0, 4.0]
     assert r.col_ub[0] == 1.5 and r.col_ub[1] == 1.5
+    assert r.col_lb[0] == 0.0 and r.col_lb[1] == 0.0  # -2 x2 >= -3 bounds x2 above only
     assert r.col_lb[2] == -0.5 and r.col_ub[2] == 0.5
     # round 1: the last row has max activity 30 > 25; round 2: 1.5 + 1.5 + 0.5
     # = 3.5 <= 25 and lhs = -inf -> redundant
@@ -88,6 +89,14 @@ def test_residual_activity_of_lower_bounds():
     lp = make([{0: 1.0, 1: 1.0}], lhs=[-INF], rhs=[10], lb=[2, 3], ub=[100, 100])
     r = run(lp, max_rounds=1)
     assert (r.ub[0], r.ub[1]) == (7.0, 8.0)
+
+
+def test_the_one_infinite_term_gets_the_bound():
+    # x1 + x2 <= 5 with x1 in (-inf, 100], x2 in [1, 3]: x1 is the row's one infinite term of the min
+    # activity, so it alone gets u1 <= 5 - 1 = 4; x2's residual is infinite (no bound from this row)
+    lp = make([{0: 1.0, 1: 1.0}], lhs=[-INF], rhs=[5], lb=[-INF, 1], ub=[100, 3])
+    r = run(lp, max_rounds=1)
+    assert (r.ub[0], r.ub[1], r.lb[0]) == (4.0, 3.0, -INF)
 
 
 def test_crossing_bounds_infeasible_column():
