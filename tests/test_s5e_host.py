@@ -75,6 +75,18 @@ def random_state(seed, m=80, n=60):
             cols, vals = rows[r]
             if r != i and j in cols and k in cols and rng.random() < 0.5:
                 vals[cols.index(j)] = vals[cols.index(k)] * (a / b)
+    # plant transfers that end within the tolerance of x_j's upper bound (the snap)
+    for i in range(m):
+        if len(rows[i][0]) != 2 or L[i] != U[i] or rng.random() < 0.7:
+            continue
+        (c0, c1), (v0, v1) = rows[i]
+        (j, a), (k, b) = ((c0, v0), (c1, v1)) if clen[c1] <= clen[c0] else ((c1, v1), (c0, v0))
+        f, g = a / b, L[i] / b
+        bhi = ub[k] if f > 0 else lb[k]
+        if math.isfinite(bhi):
+            lo = (g - bhi) / f
+            if lo > lb[j]:
+                ub[j] = lo + 0.5e-9 * max(1.0, abs(lo))
     rp = np.zeros(m + 1, np.int32)
     rp[1:] = np.cumsum([len(r[0]) for r in rows])
     ci = np.array([c for r in rows for c in r[0]], np.int32)
@@ -106,7 +118,7 @@ def reference(st, rnd):
     L, U, lb, ub, c = (st[k].tolist() for k in ("L", "U", "lb", "ub", "c"))
     rmap, cmap = st["rmap"].tolist(), st["cmap"].tolist()
     out = dict(fixv={}, rec_row={}, rec_col={}, store={}, rdnext=set(), verdict=None, applied=0, changed=0,
-               cancelled=0, merged=0, inserted=0)
+               cancelled=0, merged=0, inserted=0, snapped=0)
     cand, cmin, rmin = {}, [NONE] * n, [NONE] * m
     for i in range(m):
         if rkind[i] != 0 or rp[i + 1] - rp[i] != 2 or not math.isfinite(L[i]) or L[i] != U[i]:
@@ -150,6 +162,7 @@ def reference(st, rnd):
                 continue
             if nl != nu and abs(nl - nu) <= d:
                 nl = nu = 0.5 * (nl + nu)
+                out["snapped"] += 1
         out["changed"] += nl != lb[jj] or nu != ub[jj]
         lb[jj], ub[jj] = nl, nu
         t = c[kk] / b
@@ -248,15 +261,16 @@ def check(L_, st, rnd=3):
 
 
 def test_random_round_states(lib):
-    tally = dict(applied=0, cancelled=0, merged=0, inserted=0, verdicts=0)
+    tally = dict(applied=0, cancelled=0, merged=0, inserted=0, snapped=0, verdicts=0)
     for seed in range(120):
         ref = check(lib, random_state(seed))
-        for k in ("applied", "cancelled", "merged", "inserted"):
+        for k in ("applied", "cancelled", "merged", "inserted", "snapped"):
             tally[k] += ref[k]
         tally["verdicts"] += ref["verdict"] is not None
     # the states exercise every branch
     assert tally["applied"] > 500 and tally["verdicts"] > 10, tally
     assert tally["cancelled"] > 20 and tally["merged"] > 20 and tally["inserted"] > 500, tally
+    assert tally["snapped"] > 20, tally
 
 
 def test_long_columns_and_ties(lib):
