@@ -157,13 +157,15 @@ def outcomes(source, tmp_path_factory):
         assert source.count(old) == 1, f"mutation site not unique or gone: {old!r}"
         jobs.append((name, source.replace(old, new), pins))
 
-    def one(job):
-        name, text, pins = job
-        lib = build(str(tmp_path_factory.mktemp("mutant")), text)
-        return name, run_pins(lib, pins)
+    # the directories are made here, before the threads: the factory is not thread-safe
+    dirs = [str(tmp_path_factory.mktemp("mutant")) for _ in jobs]
+
+    def one(job_dir):
+        (name, text, pins), d = job_dir
+        return name, run_pins(build(d, text), pins)
 
     with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
-        return dict(ex.map(one, jobs))
+        return dict(ex.map(one, zip(jobs, dirs)))
 
 
 def test_control_passes(outcomes):

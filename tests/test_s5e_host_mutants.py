@@ -85,12 +85,15 @@ def libs(tmp_path_factory):
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not found")
     jobs = [("control", None)] + [(m[0], m[1:]) for m in MUTANTS]
+    # the directories are made here, before the threads: the factory is not thread-safe
+    dirs = [str(tmp_path_factory.mktemp("s5e_mut")) for _ in jobs]
 
-    def one(job):
-        return job[0], build(str(tmp_path_factory.mktemp("s5e_mut")), job[1])
+    def one(job_dir):
+        (name, mutated), d = job_dir
+        return name, build(d, mutated)
 
     with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
-        return dict(ex.map(one, jobs))
+        return dict(ex.map(one, zip(jobs, dirs)))
 
 
 def test_control_passes(libs):
