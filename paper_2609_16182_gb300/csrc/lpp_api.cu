@@ -8,6 +8,7 @@
 #include <string>
 
 #include "lpp_engine.h"
+#include "postsolve.h"
 
 using namespace lpp;
 
@@ -748,59 +749,28 @@ lpp_status lpp_postsolve_primal(const lpp_postsolve *Pc, const double *x_red, do
     const lpp_status st = guarded([&]() -> lpp_status { materialize(P); return LPP_OK; });
     if (st != LPP_OK) return st;
     if (!x_red && !P->col_map.empty()) return set_err(LPP_ERR_INVALID, "NULL argument");
-    const size_t n = P->col_kind.size();
-    for (size_t j = 0; j < n; j++) x_orig[j] = P->col_kind[j] != LPP_COL_KEPT ? P->col_val[j] : NAN;
-    for (size_t k = 0; k < P->col_map.size(); k++) {
-        const int32_t j = P->col_map[k];
-        if (j < 0 || (size_t)j >= n) return set_err(LPP_ERR_INVALID, "corrupt column map");
-        x_orig[j] = x_red[k];
-    }
-    // merges and substitutions, latest first: round, then step (S5e
-    // doubletons, S5d substitutions, S5c merges: the reverse of their order
-    // in a round), then index
-    struct Ev {
-        int32_t round, step, index;
-    };
-    std::vector<Ev> ev;
-    for (size_t j = 0; j < n; j++)
-        if (P->col_kind[j] == LPP_COL_PARALLEL) ev.push_back({P->col_round[j], 0, (int32_t)j});
-    for (size_t i = 0; i < P->row_kind.size(); i++)
-        if (P->row_kind[i] == LPP_ROW_SUBST || P->row_kind[i] == LPP_ROW_DOUBLETON)
-            ev.push_back({P->row_round[i], P->row_kind[i] == LPP_ROW_DOUBLETON ? 2 : 1, (int32_t)i});
-    std::sort(ev.begin(), ev.end(), [](const Ev &a, const Ev &b) {
-        if (a.round != b.round) return a.round > b.round;
-        if (a.step != b.step) return a.step > b.step;
-        return a.index > b.index;
-    });
-    for (const Ev &e : ev) {
-        if (e.step == 0) {
-            const int32_t j = e.index, k = P->col_aux[j];
-            if (k < 0 || (size_t)k >= n) return set_err(LPP_ERR_INVALID, "corrupt merge record");
-            const double lam = P->col_val[j], y = x_orig[k];
-            const double *b = &P->col_mrg[4 * (size_t)j];  // l_y, u_y, l_j, u_j
-            // the x_j that keep y - lam x_j inside [l_y, u_y], within [l_j, u_j]
-            double lo = lam > 0.0 ? (y - b[1]) / lam : (y - b[0]) / lam;
-            double hi = lam > 0.0 ? (y - b[0]) / lam : (y - b[1]) / lam;
-            if (b[2] > lo) lo = b[2];
-            if (b[3] < hi) hi = b[3];
-            const double xj = std::isfinite(lo) ? lo : (std::isfinite(hi) ? hi : 0.0);
-            x_orig[j] = xj;
-            x_orig[k] = y - lam * xj;
-        } else {
-            // x_j = (b - sum_k a_ik x_k) / a_ij, the entries in row order (a
-            // doubleton stores its one other entry: x_k = (c - a x_j) / b)
-            const int32_t i = e.index, j = P->row_aux[i];
-            if (j < 0 || (size_t)j >= n) return set_err(LPP_ERR_INVALID, "corrupt substitution record");
-            double sum = 0.0;
-            for (int64_t q = P->sub_beg[i]; q < P->sub_beg[i] + P->sub_len[i]; q++) {
-                const int32_t k = P->sub_col[(size_t)q];
-                if (k < 0 || (size_t)k >= n) return set_err(LPP_ERR_INVALID, "corrupt substitution record");
-                sum = sum + P->sub_val[(size_t)q] * x_orig[k];
-            }
-            x_orig[j] = (P->sub_rhs[i] - sum) / P->row_val[i];
-        }
-    }
-    return LPP_OK;
+    PostsolveRecords R;
+    R.n = (int64_t)P->col_kind.size();
+    R.m = (int64_t)P->row_kind.size();
+    R.n_red = (int64_t)P->col_map.size();
+    R.col_kind = P->col_kind.data();
+    R.col_round = P->col_round.data();
+    R.col_aux = P->col_aux.data();
+    R.col_map = P->col_map.data();
+    R.col_val = P->col_val.data();
+    R.col_mrg = P->col_mrg.data();
+    R.row_kind = P->row_kind.data();
+    R.row_round = P->row_round.data();
+    R.row_aux = P->row_aux.data();
+    R.row_val = P->row_val.data();
+    R.sub_beg = P->sub_beg.data();
+    R.sub_len = P->sub_len.data();
+    R.sub_col = P->sub_col.data();
+    R.sub_rhs = P->sub_rhs.data();
+    R.sub_val = P->sub_val.data();
+    R.sub_size = (int64_t)P->sub_col.size();
+    const char *err = postsolve_primal(R, x_red, x_orig);
+    return err ? set_err(LPP_ERR_INVALID, err) : LPP_OK;
 }
 
 void lpp_free_reduced(lpp_reduced *R) {
