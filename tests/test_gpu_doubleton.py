@@ -56,9 +56,13 @@ def test_infeasible_transfer():
     compare(g, o, lp)
 
 
+@pytest.mark.parametrize("through_x0", [True, False])
 @pytest.mark.parametrize("seed", range(40))
-def test_micro_planted(seed):
-    lp = synth.plant_doubletons(synth.micro(seed + 2100), seed)
+def test_micro_planted(seed, through_x0):
+    # planted through the LP's feasible point (the LP stays feasible), or through a point of the
+    # columns' box (often infeasible: the verdict's location and round are compared)
+    base = synth.micro(seed + 2100)
+    lp = synth.plant_doubletons(base, seed, point=base.planted["x0"] if through_x0 else None)
     g, o = both(lp)
     compare(g, o, lp)
 
