@@ -26,7 +26,7 @@
  *       singletons; only with opts.col_singletons = 1)
  *   S5e doubleton equations a x_j + b x_k = c: x_k = (c - a x_j) / b is
  *       substituted into x_k's other rows and x_j takes over its bounds and
- *       cost (Sec. 2.1, doubleton rows; opts.doubletons, not enabled yet)
+ *       cost (Sec. 2.1, doubleton rows; only with opts.doubletons = 1)
  *   S6  empty columns fixed at the bound their cost prefers (dual rule); with
  *       opts.dual_fixing every column no kept row locks in that direction
  *   S7  compaction of the CSR and CSC matrices and of all row/column vectors
@@ -131,8 +131,7 @@ typedef struct lpp_opts {
     int32_t dual_fixing;    /* [0]     1: S6 fixes every column no kept row locks in the
                                        direction its cost prefers (dual fixing by locks)      */
     int32_t doubletons;     /* [0]     1: eliminate a column of each doubleton equation (S5e,
-                                       Sec. 2.1); the device step is not enabled yet: any
-                                       call with 1 returns LPP_ERR_INVALID                    */
+                                       Sec. 2.1); lpp_presolve and lpp_presolve_batch only    */
     int32_t timing;         /* [0]     1: time every kernel launch with CUDA events           */
     int32_t device;         /* [0]     CUDA device ordinal                                   */
     void *stream;           /* [NULL]  cudaStream_t to run on; NULL: a library-owned stream  */

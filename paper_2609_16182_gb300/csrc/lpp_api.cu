@@ -57,8 +57,6 @@ lpp_opts resolve_opts(const lpp_opts *opts) {
         (o.col_singletons != 0 && o.col_singletons != 1) || (o.dual_fixing != 0 && o.dual_fixing != 1) ||
         (o.doubletons != 0 && o.doubletons != 1))
         throw StatusError(LPP_ERR_INVALID, "bad options");
-    // S5e (doubleton equations) is compiled in but not enabled: refused
-    if (o.doubletons) throw StatusError(LPP_ERR_INVALID, "doubletons: the GPU S5e step is not enabled yet");
     return o;
 }
 

@@ -82,9 +82,9 @@ def test_opt_in_steps_default_off():
     assert (q.parallel_cols, q.col_singletons, q.dual_fixing, q.doubletons) == (0, 0, 0, 0)
 
 
-def test_doubletons_refused_before_any_device_work():
+def test_bad_opt_in_flags_refused_before_any_device_work():
     # the options are checked on the host before the first CUDA call, so this
-    # runs without a GPU: a call with doubletons = 1 returns LPP_ERR_INVALID
+    # runs without a GPU: an opt-in flag other than 0 or 1 returns LPP_ERR_INVALID
     import ctypes as C
     import numpy as np
     from paper_2609_16182_gb300 import lpp
@@ -96,8 +96,9 @@ def test_doubletons_refused_before_any_device_work():
     lb, ub, c = np.zeros(2), np.ones(2), np.ones(2)
     lp = lpp.LpStruct(1, 2, 2, rp.ctypes.data, ci.ctypes.data, v.ctypes.data, c.ctypes.data, side.ctypes.data,
                       side.ctypes.data, lb.ctypes.data, ub.ctypes.data, 0.0, 0)
-    o = lpp.opts(doubletons=1)
-    red, rec = C.c_void_p(), C.c_void_p()
-    st = L.lpp_presolve(C.byref(lp), C.byref(o), C.byref(red), C.byref(rec))
-    assert st == lpp.ERR_INVALID and not red.value and not rec.value
-    assert b"doubletons" in L.lpp_last_error()
+    for flag in ("doubletons", "parallel_cols", "col_singletons", "dual_fixing"):
+        o = lpp.opts(**{flag: 2})
+        red, rec = C.c_void_p(), C.c_void_p()
+        st = L.lpp_presolve(C.byref(lp), C.byref(o), C.byref(red), C.byref(rec))
+        assert st == lpp.ERR_INVALID and not red.value and not rec.value, flag
+        assert b"options" in L.lpp_last_error()

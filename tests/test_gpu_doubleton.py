@@ -2,8 +2,7 @@
 oracle: hand-worked rows, cancellation and insertion, an empty bound
 transfer, planted micro and 200-row LPs, long x_k columns of the
 LP-relaxation generator (warp walks), every opt-in step together, a batch,
-and the postsolve.  While the library refuses the option these tests are
-skipped (the refusal is checked on a two-entry LP, before any device work)."""
+and the postsolve."""
 import numpy as np
 import pytest
 
@@ -17,14 +16,6 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 from paper_2609_16182_gb300 import lpp  # noqa: E402
-
-_probe = synth.LP(m=1, n=2, row_ptr=np.array([0, 2], np.int32), col_idx=np.array([0, 1], np.int32),
-                  val=np.array([1.0, 1.0]), c=np.zeros(2), lhs=np.ones(1), rhs=np.ones(1), lb=np.zeros(2),
-                  ub=np.ones(2))
-try:
-    lpp.presolve(_probe, doubletons=1).close()
-except lpp.LppError as _e:
-    pytest.skip(f"the library refuses doubletons: {_e}", allow_module_level=True)
 
 
 def both(lp, **kw):
