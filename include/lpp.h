@@ -258,9 +258,10 @@ void lpp_free_postsolve(lpp_postsolve *rec);
 const char *lpp_last_error(void);
 
 /* Batched presolve: `count` independent LPs (all host or all device inputs)
- * presolved together in one device arena, each round one set of launches for
- * all LPs, the round sequence captured once in a CUDA graph and replayed.
- * Each LP gets the result it would get alone.  outs[k], recs[k], per_lp[k]
+ * presolved together in one device arena: each round is one set of kernel
+ * launches over all LPs, issued by the host, which reads the next round's
+ * launch geometry (sizes after compaction, length classes) back once per
+ * round.  Each LP gets the result it would get alone.  outs[k], recs[k], per_lp[k]
  * as for lpp_presolve.  Returns LPP_OK unless the batch itself failed. */
 lpp_status lpp_presolve_batch(const lpp_lp *ins, int32_t count, const lpp_opts *opts, lpp_reduced **outs,
                               lpp_postsolve **recs, lpp_status *per_lp);
@@ -297,18 +298,19 @@ void lpp_server_destroy(lpp_server *srv);
  * val[nnz]) and bounds lb/ub[n] (|v| >= huge counts as infinite), what
  * lpp_presolve's activity step computes: act_min[i] / act_max[i], the finite
  * parts of the minimum / maximum of row i over the box, and ninf_min[i] /
- * ninf_max[i], the numbers of infinite terms (Sec. 3.1).  All pointers are
- * device pointers on the calling thread's current device; outputs [m] are
- * allocated by the caller.  The CSR is not checked (it must be valid: the
- * checks of lpp_presolve need scratch memory proportional to nnz).
+ * ninf_max[i], the numbers of infinite terms.  All pointers are device
+ * pointers on the calling thread's current device; outputs [m] are allocated
+ * by the caller.  The CSR is not checked (it must be valid: the checks of
+ * lpp_presolve need scratch memory proportional to nnz).
  * Scratch: one fixed array inside the library (4 MiB on every device that
  * loads the library, held until the process exits) limits nnz to
  * 268,435,456; larger inputs return LPP_ERR_INVALID with a message.  The
- * first call on a device looks up that array's device address (set-up), so
- * make it before any stream capture.  Every call shares the array: calls
- * that overlap on the GPU (other streams, other threads) race; serialise
- * them.  Runs asynchronously on `stream` (NULL = legacy default stream) and
- * calls no allocation routine. */
+ * first call on a device looks up that array's device address and loads the
+ * entry point's three kernels (set-up), so make it before any stream
+ * capture.  Every call shares the array: calls that overlap on the GPU
+ * (other streams, other threads) race; serialise them.  Runs asynchronously
+ * on `stream` (NULL = legacy default stream) and calls no allocation
+ * routine. */
 lpp_status lpp_row_activity_noalloc(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
                                     const int32_t *col_idx, const double *val, const double *lb, const double *ub,
                                     double huge, double *act_min, double *act_max, int32_t *ninf_min,

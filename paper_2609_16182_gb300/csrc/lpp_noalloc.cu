@@ -206,12 +206,18 @@ extern "C" lpp_status lpp_row_activity_noalloc(int32_t m, int32_t n, int64_t nnz
     {
         std::lock_guard<std::mutex> g(g_na_mu);
         if (!g_na_ptr[dev]) {
-            // set-up, once per device, with that device current
-            e = cudaGetSymbolAddress(&g_na_ptr[dev], g_na_scratch);
-            if (e != cudaSuccess) {
-                g_na_ptr[dev] = nullptr;
-                return lpp_noalloc_fail(LPP_ERR_CUDA, cudaGetErrorString(e));
-            }
+            // set-up, once per device, with that device current: the array's
+            // address, and all three kernels loaded now (with lazy module
+            // loading a kernel is otherwise loaded at its first launch, which
+            // for the window kernels is the first call with nnz > 4096)
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_na_scratch);
+            cudaFuncAttributes fa;
+            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_na_short);
+            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_na_windows);
+            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_na_long);
+            if (e != cudaSuccess) return lpp_noalloc_fail(LPP_ERR_CUDA, cudaGetErrorString(e));
+            g_na_ptr[dev] = p;
         }
         scratch = g_na_ptr[dev];
     }
