@@ -17,6 +17,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "lpp_oracle.c")
 
 RULES = ["tests/test_oracle_rules.py"]
+S5P = ["tests/test_oracle_s5_passes.py"]
 S5E = ["tests/test_oracle_doubleton.py", "-k",
        "hand_worked or both_sides or cancellation or empty or snap or sharing or steps_before"]
 S5D = ["tests/test_oracle_colsing.py", "-k",
@@ -117,6 +118,18 @@ MUTANTS = [
     ("objective constant: fixed columns' cost terms with the wrong sign",
      "if (fixed[j] && fixed[j] != 3) s.offset += s.c[j] * fixv[j];",
      "if (fixed[j] && fixed[j] != 3) s.offset -= s.c[j] * fixv[j];", RULES),
+    ("S5: one leader pass per group and round",
+     "for (it = 0; it < o->par_max_iter; it++) {", "for (it = 0; it < 1; it++) {", S5P),
+    ("S5: the pass cap ignored",
+     "for (it = 0; it < o->par_max_iter; it++) {", "for (it = 0; it < 1000; it++) {", S5P),
+    ("S5: the leader not removed from its group",
+     "                    alive[lead] = 0;\n", "", S5P),
+    ("S5: a leader's lower side taken from its last follower, not the largest",
+     "if (lo > mL[li]) { mL[li] = lo;", "if (1) { mL[li] = lo;", S5P),
+    ("S5: a leader's upper side taken from its last follower, not the smallest",
+     "if (hi < mU[li]) { mU[li] = hi;", "if (1) { mU[li] = hi;", S5P),
+    ("S5: a group of two live rows not run",
+     "if (cnt < 2) break;", "if (cnt < 3) break;", S5P),
     ("postsolve: a substituted column divided by the wrong coefficient",
      "x_orig[jj] = (sub_rhs[ii] - sum) / row_val[ii];", "x_orig[jj] = (sub_rhs[ii] - sum) * row_val[ii];", POST),
 ]
@@ -152,7 +165,7 @@ def source():
 def outcomes(source, tmp_path_factory):
     """Every mutant (and the control) built and run once, in parallel:
     name -> (return code, output tail)."""
-    jobs = [("control", source, RULES + ["tests/test_oracle_doubleton.py"])]
+    jobs = [("control", source, RULES + S5P + ["tests/test_oracle_doubleton.py"])]
     for name, old, new, pins in MUTANTS:
         assert source.count(old) == 1, f"mutation site not unique or gone: {old!r}"
         jobs.append((name, source.replace(old, new), pins))
