@@ -67,7 +67,9 @@ _OUT_FIELDS = [
     ("act_scale_max", C.c_void_p), ("ninf_min", C.c_void_p), ("ninf_max", C.c_void_p),
     ("round_nnz", C.c_void_p), ("round_rows_removed", C.c_void_p), ("round_cols_fixed", C.c_void_p),
     ("round_bounds_changed", C.c_void_p),
+    ("s5_left", C.c_int64), ("s5_capped_groups", C.c_int64),
     ("audit_min_ratio", C.c_double), ("audit_decisions", C.c_int64), ("audit_below_1e3", C.c_int64),
+    ("audit_below_1", C.c_int64),
 ]
 
 
@@ -169,9 +171,12 @@ class Result:
     round_rows_removed: np.ndarray
     round_cols_fixed: np.ndarray
     round_bounds_changed: np.ndarray
+    s5_left: int
+    s5_capped_groups: int
     audit_min_ratio: float
     audit_decisions: int
     audit_below_1e3: int
+    audit_below_1: int
 
 
 def presolve(lp, opts: Opts | None = None) -> Result:
@@ -225,8 +230,9 @@ def presolve(lp, opts: Opts | None = None) -> Result:
         round_nnz=arr["round_nnz"][:rounds].copy(), round_rows_removed=arr["round_rows_removed"][:rounds].copy(),
         round_cols_fixed=arr["round_cols_fixed"][:rounds].copy(),
         round_bounds_changed=arr["round_bounds_changed"][:rounds].copy(),
+        s5_left=out.s5_left, s5_capped_groups=out.s5_capped_groups,
         audit_min_ratio=out.audit_min_ratio, audit_decisions=out.audit_decisions,
-        audit_below_1e3=out.audit_below_1e3)
+        audit_below_1e3=out.audit_below_1e3, audit_below_1=out.audit_below_1)
 
 
 def activities(lp, huge: float = 1e20):

@@ -64,7 +64,7 @@ void lppo_opts_default(lppo_opts *o)
 /* ---------------------------------------------------------------- audit */
 typedef struct {
     double min_ratio;
-    int64_t n, below;
+    int64_t n, below, below1;  /* decisions; within 1000x and within 1x of their error bound */
 } audit_t;
 
 static void audit(audit_t *a, double margin, double eb)
@@ -75,6 +75,7 @@ static void audit(audit_t *a, double margin, double eb)
     r = fabs(margin) / eb;
     if (r < a->min_ratio) a->min_ratio = r;
     if (r < 1e3) a->below++;
+    if (r < 1.0) a->below1++;
 }
 
 /* bound on the difference between two evaluations of a sum of `cnt`
@@ -252,6 +253,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     double *mna = NULL, *mxa = NULL, *smn = NULL, *smx = NULL, *ebmn = NULL, *ebmx = NULL;
     int32_t *nmn = NULL, *nmx = NULL, *kind = NULL, *fixed = NULL, *colcnt = NULL;
     double *nl = NULL, *nu = NULL, *ebnl = NULL, *ebnu = NULL, *fixv = NULL;
+    int32_t *srcl = NULL, *srcu = NULL; /* tie audit: the singleton row that set nl / nu, else -1 */
     double *mL = NULL, *mU = NULL, *ebmL = NULL, *ebmU = NULL;
     int32_t *hasf = NULL, *alive = NULL, *nrow = NULL, *ncol = NULL;
     pkey_t *keys = NULL;
@@ -298,6 +300,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     ALLOC(mna, m0); ALLOC(mxa, m0); ALLOC(smn, m0); ALLOC(smx, m0); ALLOC(ebmn, m0); ALLOC(ebmx, m0);
     ALLOC(nmn, m0); ALLOC(nmx, m0); ALLOC(kind, m0); ALLOC(fixed, n0); ALLOC(colcnt, n0);
     ALLOC(nl, n0); ALLOC(nu, n0); ALLOC(ebnl, n0); ALLOC(ebnu, n0); ALLOC(fixv, n0);
+    ALLOC(srcl, n0); ALLOC(srcu, n0);
     ALLOC(mL, m0); ALLOC(mU, m0); ALLOC(ebmL, m0); ALLOC(ebmU, m0);
     ALLOC(hasf, m0); ALLOC(alive, m0); ALLOC(nrow, m0); ALLOC(ncol, n0);
     ALLOC(keys, m0); ALLOC(qbuf, lp->nnz);
@@ -322,12 +325,13 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                             out->col_mrg[4 * j + 2] = 0.0; out->col_mrg[4 * j + 3] = 0.0; }
     }
     out->where = LPPO_WHERE_NONE; out->index = -1; out->round = 0; out->rounds = 0;
+    out->s5_left = 0; out->s5_capped_groups = 0;
     for (i = 0; i < m0; i++) { /* no round executed yet: no row has activities */
         out->ninf_min[i] = -1; out->ninf_max[i] = -1;
         out->act_min[i] = NAN; out->act_max[i] = NAN;
         out->act_scale_min[i] = NAN; out->act_scale_max[i] = NAN;
     }
-    au.min_ratio = INFINITY; au.n = 0; au.below = 0;
+    au.min_ratio = INFINITY; au.n = 0; au.below = 0; au.below1 = 0;
 
     for (r = 1; r <= o->max_rounds; r++) {
         const int32_t m = s.m, n = s.n;
@@ -420,7 +424,9 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
         /* ---- S3: implied bounds from residual activities (Sec. 3.1), Jacobi:
                every candidate is judged against the bounds of the round start
                and the accepted ones are combined by min / max. */
-        for (j = 0; j < n; j++) { nl[j] = s.l[j]; nu[j] = s.u[j]; ebnl[j] = s.ebl[j]; ebnu[j] = s.ebu[j]; }
+        for (j = 0; j < n; j++) {
+            nl[j] = s.l[j]; nu[j] = s.u[j]; ebnl[j] = s.ebl[j]; ebnu[j] = s.ebu[j]; srcl[j] = -1; srcu[j] = -1;
+        }
         for (i = 0; i < m; i++) {
             const double L = s.L[i], U = s.U[i];
             if (kind[i] != LPPO_ROW_KEPT || s.rp[i + 1] - s.rp[i] < 2) continue;
@@ -495,6 +501,13 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
             }
             if (isfin(cl) && isfin(s.l[j])) audit(&au, cl - s.l[j], ebcl + s.ebl[j]);
             if (isfin(cu) && isfin(s.u[j])) audit(&au, cu - s.u[j], ebcu + s.ebu[j]);
+            /* tie audit: the row is the source of nl / nu only if it wins the
+               max / min by more than the two values' error bounds (else
+               another evaluation may keep the other value: -2) */
+            if (cl > nl[j]) srcl[j] = isfin(nl[j]) && cl - nl[j] <= ebcl + ebnl[j] ? -2 : i;
+            else if (isfin(cl) && nl[j] - cl <= ebcl + ebnl[j]) srcl[j] = -2;
+            if (cu < nu[j]) srcu[j] = isfin(nu[j]) && nu[j] - cu <= ebcu + ebnu[j] ? -2 : i;
+            else if (isfin(cu) && cu - nu[j] <= ebcu + ebnu[j]) srcu[j] = -2;
             if (cl > nl[j]) { nl[j] = cl; ebnl[j] = ebcl; }
             if (cu < nu[j]) { nu[j] = cu; ebnu[j] = ebcu; }
         }
@@ -505,9 +518,13 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
             double lp_ = nl[j], up_ = nu[j];
             if (isfin(lp_) && isfin(up_)) {
                 double d = ft * dmax(1.0, dmax(fabs(lp_), fabs(up_)));
-                audit(&au, (lp_ - up_) - d, ebnl[j] + ebnu[j]);
+                /* both bounds from one singleton equality row (L == U, both
+                   divided by the same a): equal on every evaluation, so these
+                   two decisions are exact and not audited */
+                const int same = lp_ == up_ && srcl[j] >= 0 && srcl[j] == srcu[j];
+                if (!same) audit(&au, (lp_ - up_) - d, ebnl[j] + ebnu[j]);
                 if (lp_ - up_ > d) { bad = j; break; }
-                audit(&au, fabs(lp_ - up_) - d, ebnl[j] + ebnu[j]);
+                if (!same) audit(&au, fabs(lp_ - up_) - d, ebnl[j] + ebnu[j]);
                 if (lp_ != up_ && fabs(lp_ - up_) <= d) {
                     double mid = 0.5 * (lp_ + up_);
                     double e = dmax(ebnl[j], ebnu[j]) + UROUND * fabs(mid);
@@ -603,6 +620,12 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                         if (lo > mL[li]) { mL[li] = lo; ebmL[li] = eblo + UROUND * fabs(lo); }
                         if (hi < mU[li]) { mU[li] = hi; ebmU[li] = ebhi + UROUND * fabs(hi); }
                     }
+                }
+                if (it == o->par_max_iter) { /* the cap stopped the passes */
+                    int32_t left = 0;
+                    for (k = 0; k < gsz; k++) left += alive[k];
+                    out->s5_left += left;
+                    if (left >= 2) out->s5_capped_groups++;
                 }
             }
             /* merge the followers' sides into each leader, in row order */
@@ -1141,11 +1164,13 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
             out->col_lb[j] = out->col_val[j]; out->col_ub[j] = out->col_val[j];
         }
     out->audit_min_ratio = au.min_ratio; out->audit_decisions = au.n; out->audit_below_1e3 = au.below;
+    out->audit_below_1 = au.below1;
 
     free(s.rp); free(s.ci); free(s.v); free(s.L); free(s.U); free(s.l); free(s.u); free(s.c);
     free(s.rmap); free(s.cmap); free(s.ebL); free(s.ebU); free(s.ebl); free(s.ebu);
     free(mna); free(mxa); free(smn); free(smx); free(ebmn); free(ebmx); free(nmn); free(nmx);
     free(kind); free(fixed); free(colcnt); free(nl); free(nu); free(ebnl); free(ebnu); free(fixv);
+    free(srcl); free(srcu);
     free(mL); free(mU); free(ebmL); free(ebmU); free(hasf); free(alive); free(nrow); free(ncol);
     free(keys); free(qbuf); free(nrp); free(nci); free(nv);
     free(tcp); free(tri); free(tvl); free(tfill); free(calive); free(ckeys); free(cqbuf);
@@ -1157,6 +1182,7 @@ oom:
     free(s.rmap); free(s.cmap); free(s.ebL); free(s.ebU); free(s.ebl); free(s.ebu);
     free(mna); free(mxa); free(smn); free(smx); free(ebmn); free(ebmx); free(nmn); free(nmx);
     free(kind); free(fixed); free(colcnt); free(nl); free(nu); free(ebnl); free(ebnu); free(fixv);
+    free(srcl); free(srcu);
     free(mL); free(mU); free(ebmL); free(ebmU); free(hasf); free(alive); free(nrow); free(ncol);
     free(keys); free(qbuf); free(nrp); free(nci); free(nv);
     free(tcp); free(tri); free(tvl); free(tfill); free(calive); free(ckeys); free(cqbuf);

@@ -113,10 +113,18 @@ typedef struct {
     /* per-round counters [max_rounds] (may be NULL) */
     int64_t *round_nnz;
     int32_t *round_rows_removed, *round_cols_fixed, *round_bounds_changed;
-    /* tie audit: smallest margin / error-bound ratio over all decisions */
+    /* parallel rows: rows still live in their key group when the leader
+       passes stopped at par_max_iter (the last leader excluded), summed over
+       rounds, and the groups with two or more such rows */
+    int64_t  s5_left;
+    int64_t  s5_capped_groups;
+    /* tie audit: smallest margin / error-bound ratio over all decisions, the
+       decisions, those within 1000x of their error bound, and those within
+       it (only these could come out differently on another evaluation) */
     double   audit_min_ratio;
     int64_t  audit_decisions;
     int64_t  audit_below_1e3;
+    int64_t  audit_below_1;
 } lppo_out;
 
 void lppo_opts_default(lppo_opts *o);

@@ -75,6 +75,21 @@ def test_pass_cap_leaves_the_later_classes():
     assert list(r3.row_kind) == list(run(three_classes()).row_kind)
 
 
+def test_rows_left_at_the_cap_are_counted():
+    # no cap reached: nothing left
+    r = run(three_classes())
+    assert (r.s5_left, r.s5_capped_groups) == (0, 0)
+    # cap 3: the third pass matches the last pair, the group is empty at the cap
+    r = run(three_classes(), par_max_iter=3)
+    assert (r.s5_left, r.s5_capped_groups) == (0, 0)
+    # cap 2: rows 2 and 5 are live after the passes of round 1 and again of round 2
+    r = run(three_classes(), par_max_iter=2)
+    assert (r.s5_left, r.s5_capped_groups) == (4, 2)
+    # cap 1: rows 1, 2, 4, 5 in round 1, the same four in round 2
+    r = run(three_classes(), par_max_iter=1)
+    assert (r.s5_left, r.s5_capped_groups) == (8, 2)
+
+
 def test_equality_leads_first_in_every_pass():
     # row 5 is an equality: pass 1 is led by row 5 (the first equality), whose
     # follower is row 2 (lam = 2 / 1 = 2: [0 / 2, inf] = [0, inf]; the leader
