@@ -154,6 +154,9 @@ typedef struct lpp_info {
     double presolve_ms;   /* device time of the round loop (transfers excluded)          */
     int64_t nnz_processed;/* sum over rounds of the nonzeros present at the round start  */
     int64_t launches;     /* kernels launched by the call (a batch: by the whole batch)   */
+    int64_t s5_left;      /* rows of S5 key groups still unmatched when the leader passes
+                             stopped at opts.par_max_iter, summed over rounds (a batch:
+                             the whole batch's; a served LP: -1, not counted)             */
 } lpp_info;
 
 /* Time and traffic of one kernel family, summed over its launches

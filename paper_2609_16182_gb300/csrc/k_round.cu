@@ -619,8 +619,9 @@ __global__ void __launch_bounds__(kBlock) k_prop_long_tighten(Ctx C) {
 
 // ------------------------------------------------- S3' finalise + S4 fixing
 // S3' + S4 on column j: apply the accepted candidates, check and snap the
-// bounds, fix the column if l == u.  Returns (changed, fixed) through refs;
-// a changed short column is listed for the dirty-row marking.
+// bounds, fix the column if l == u.  Adds to the counts changed, fixed and
+// chg_nnz (a thread may finalise several columns); a changed short column is
+// listed for the dirty-row marking.
 __device__ __forceinline__ void colfin_one(const Ctx &C, int32_t j, bool full, int32_t &changed, int32_t &fixed,
                                            int32_t &chg_nnz) {
     const unsigned long long el = C.cand_l[j], eu = C.cand_u[j];
@@ -656,13 +657,13 @@ __device__ __forceinline__ void colfin_one(const Ctx &C, int32_t j, bool full, i
         } else {
             if (nl != b.x || nu != b.y) {
                 C.lu[j] = make_double2(nl, nu);
-                changed = 1;
+                changed++;
                 chg = 1;
                 C.lp_changed[lp] = 1;
             }
             if (nl == nu) {
                 kind = CK_FIXED;
-                fixed = 1;
+                fixed++;
                 C.fixv[j] = nl;
                 const int32_t o = C.cmap[j];
                 C.rec_ck[o] = CK_FIXED;

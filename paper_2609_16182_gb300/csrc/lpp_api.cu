@@ -192,6 +192,7 @@ lpp_postsolve *make_postsolve(Engine &E, const std::shared_ptr<DeviceRecords> &D
     I.presolve_ms = E.loop_ms;
     I.nnz_processed = E.nnz_processed;
     I.launches = launch_count() - E.launches0;
+    I.s5_left = E.s5_left;
     P->r_nnz = E.r_nnz;
     P->r_rows = E.r_rows;
     P->r_cols = E.r_cols;

@@ -828,6 +828,9 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
                 launch_s5_tail(C, s5_list[(q - 1) & 1], s5_cnt + q, s5_list[q & 1], s5_cnt + q + 1, n1, s);
             LPP_CUDA(cudaGetLastError());
             LPP_CUDA(cudaMemcpyAsync(s5_left_h, s5_cnt + end, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            // the status with the rows these passes removed (the round's
+            // removals decide whether it compacts)
+            LPP_CUDA(cudaMemcpyAsync(st_h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
             LPP_CUDA(cudaStreamSynchronize(s));
             if (*s5_left_h == 0) {
                 resolved = true;
@@ -839,6 +842,7 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
         tend();
     }
     if (run_s5) s5_clean = resolved;
+    if (run_s5 && !resolved) s5_left += o.par_max_iter > 1 ? *s5_left_h : n1;
     if (st_h->err) throw StatusError(LPP_ERR_CUDA, "internal: S5 hash table overflow");
     if (run_s5) launch_s5_leader(C, s);
     LPP_CUDA(cudaGetLastError());
@@ -1001,6 +1005,7 @@ void Engine::run() {
     const int32_t R = std::max(0, o.max_rounds);
     s5_clean = false;
     s5c_dirty = true;
+    s5_left = 0;
     lp_rounds.assign(nlp, 0);
     lp_status.assign(nlp, LPP_OK);
     lp_where.assign(nlp, LPP_WHERE_NONE);

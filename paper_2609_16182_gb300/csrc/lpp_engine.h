@@ -151,6 +151,7 @@ struct Engine {
     int32_t rounds = 0;
     double loop_ms = 0.0;
     int64_t nnz_processed = 0;
+    int64_t s5_left = 0;    // rows unmatched when the S5 leader passes stopped at the cap, summed over rounds
     int64_t launches0 = 0;  // launch counter at setup
     // activities of the last round: current-index arrays and the map valid then
     int32_t act_m = 0, act_buf = 0;

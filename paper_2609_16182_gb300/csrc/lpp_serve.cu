@@ -469,6 +469,7 @@ void finish_slot(lpp_server *S, int32_t k, const std::vector<int32_t> &rng, cons
     I.obj_offset = offs[k];
     I.presolve_ms = Z.ms;
     I.nnz_processed = Z.nnz_proc;
+    I.s5_left = -1;
     S->done[Z.ticket] = lpp_server::Done{(lpp_status)I.status, R, P};
 }
 

@@ -48,7 +48,8 @@ class Info(C.Structure):
     _fields_ = [("status", C.c_int32), ("where", C.c_int32), ("index", C.c_int32), ("round", C.c_int32),
                 ("rounds", C.c_int32), ("m", C.c_int32), ("n", C.c_int32), ("m_red", C.c_int32),
                 ("n_red", C.c_int32), ("nnz", C.c_int64), ("nnz_red", C.c_int64), ("obj_offset", C.c_double),
-                ("presolve_ms", C.c_double), ("nnz_processed", C.c_int64), ("launches", C.c_int64)]
+                ("presolve_ms", C.c_double), ("nnz_processed", C.c_int64), ("launches", C.c_int64),
+                ("s5_left", C.c_int64)]
 
 
 class KernelStat(C.Structure):
@@ -223,6 +224,7 @@ class Result:
         self.index = info.index
         self.round = info.round
         self.rounds = info.rounds
+        self.s5_left = info.s5_left
         self._rounds_data = None
         self._kernels = None
         self._reduced = None

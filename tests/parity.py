@@ -7,7 +7,8 @@ substitutions and doubletons the stored row),
 row and column maps, the reduced CSR / CSC structure and its coefficients
 and costs (copies of the input, or one rounded product and difference away
 from it: S5d and S5e costs, S5e coefficients), the counts of infinite
-activity terms.
+activity terms, the per-round counts of nonzeros and of removed rows and
+columns, the rows the parallel-row passes left unmatched at their cap.
 Within tolerance: values that come out of a floating-point sum (activities,
 implied bounds, shifted sides, the objective constant, bounds at a merge, the
 right-hand side of a substitution):
@@ -90,6 +91,10 @@ def compare(gpu, orc, lp, check_records=True, arena_stats=False):
     _close(gpu.act_max, orc.act_max, scale=orc.act_scale_max, what="max activity")
     if not arena_stats:
         np.testing.assert_array_equal(gpu.round_nnz, orc.round_nnz, err_msg="nnz per round")
+        np.testing.assert_array_equal(gpu.round_rows_removed, orc.round_rows_removed, err_msg="rows removed per round")
+        np.testing.assert_array_equal(gpu.round_cols_fixed, orc.round_cols_fixed, err_msg="columns removed per round")
+        # rows left unmatched when the parallel-row passes stopped at the cap
+        assert gpu.s5_left == orc.s5_left, ("S5 rows left at the pass cap", gpu.s5_left, orc.s5_left)
     red = gpu.reduced()
     assert (red.m, red.n, red.nnz) == (orc.m_red, orc.n_red, orc.nnz_red)
     np.testing.assert_array_equal(red.row_map, orc.row_map)

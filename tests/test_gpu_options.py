@@ -82,3 +82,16 @@ def test_parallel_rows_needing_many_passes(cap):
     compare(g, o, lp)
     if cap >= 10:  # one round resolves every group: each copy went into its base row
         assert np.count_nonzero(g.row_kind == lpp.ROW_PARALLEL) == 10
+
+
+@pytest.mark.parametrize("cap", [2, 16])
+def test_round_reduced_only_by_a_later_parallel_pass(cap):
+    # x = 2 is fixed in round 1; in round 2 the rows y + 2z, y + 3z, 2y + 6z
+    # form one key group whose first pass finds nothing and whose second
+    # pass merges 2y + 6z into y + 3z: the round's only reduction, which must
+    # still compact the matrix
+    lp = make([{0: 1, 1: 1, 2: 2}, {1: 1, 2: 3}, {0: 5, 1: 2, 2: 6}, {0: 1}],
+              [-INF, -INF, -20, 2], [12, 7, INF, 2], [0, -INF, -INF], [10, INF, INF])
+    g, o = both(lp, par_max_iter=cap)
+    assert o.row_kind[2] == lpp.ROW_PARALLEL and o.row_round[2] == 2
+    compare(g, o, lp)

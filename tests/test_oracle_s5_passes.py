@@ -144,3 +144,27 @@ def test_non_parallel_rows_of_one_key_stay():
               [INF] * 2)
     r = run(lp)
     assert np.all(r.row_kind == oracle.ROW_KEPT) and r.rounds == 1
+
+
+def later_pass_only_lp():
+    """Rows p = x + y + 2z, q = y + 3z, q' = 5x + 2y + 6z and the singleton
+    row x = 2 (x in [0, 10], y and z free).  Round 1 fixes x (S2, S3', S4);
+    p and q' share a key but are not parallel.  Round 2 sees p = y + 2z,
+    q = y + 3z, q' = 2y + 6z (sides shifted by the fixed x): one key group,
+    pass 1 led by p finds nothing, pass 2 led by q takes q' (lambda 2).  That
+    merge is the round's only reduction."""
+    return make([{0: 1, 1: 1, 2: 2}, {1: 1, 2: 3}, {0: 5, 1: 2, 2: 6}, {0: 1}],
+                [-INF, -INF, -20, 2], [12, 7, INF, 2], [0, -INF, -INF], [10, INF, INF])
+
+
+def test_a_later_pass_alone_reduces_a_round():
+    r = run(later_pass_only_lp())
+    assert r.status == oracle.OK
+    assert list(r.row_kind) == [oracle.ROW_KEPT, oracle.ROW_KEPT, oracle.ROW_PARALLEL, oracle.ROW_SINGLETON]
+    assert r.row_aux[2] == 1 and r.row_val[2] == 2.0 and r.row_round[2] == 2
+    assert r.col_kind[0] == oracle.COL_FIXED and r.col_val[0] == 2.0
+    # q' after the shift: 2y + 6z >= -20 - 5 * 2 = -30, divided by 2: q gets [-15, 7]
+    assert sides_of(r, 1) == (-15.0, 7.0)
+    assert sides_of(r, 0) == (-INF, 10.0)  # 12 - 1 * 2
+    assert list(r.round_rows_removed) == [1, 1, 0]
+    assert r.m_red == 2 and r.rounds == 3

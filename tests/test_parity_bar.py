@@ -116,6 +116,10 @@ def _round_nnz(g, o):
     g.round_nnz[0] += 1
 
 
+def _s5_left(g, o):
+    g.s5_left += 1
+
+
 def _red_val(g, o):
     g._red.val[0] = g._red.val[0] + ulp(g._red.val[0])
 
@@ -153,7 +157,7 @@ def _csc(g, o):
 
 
 CHANGES = [_kind, _round, _lam, _leader, _pass, _sub_entry, _sub_rhs, _fixed_value, _ninf, _act, _rounds,
-           _round_nnz, _red_val, _red_cost, _red_idx, _red_map, _red_side, _red_bound, _offset, _csc]
+           _round_nnz, _s5_left, _red_val, _red_cost, _red_idx, _red_map, _red_side, _red_bound, _offset, _csc]
 
 
 @pytest.mark.parametrize("change", CHANGES, ids=[f.__name__[1:] for f in CHANGES])
