@@ -2,14 +2,16 @@
 
 LPs submitted while others are resident join the arena at a round boundary;
 each result must equal the LP presolved alone (records, maps and reduced LP
-bit for bit, the objective constant within the parity tolerance).
+bit for bit, the objective constant within the parity tolerance) and match
+the oracle within the parity bar.
 """
 import time
 
 import numpy as np
 import pytest
 
-from parity import _close
+import oracle
+from parity import _close, compare
 from paper_2609_16182_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -49,8 +51,10 @@ def test_served_results_equal_solo_results_with_staggered_arrivals():
         st = srv.stats()
     assert st["submitted"] == len(lps) and st["finished"] == len(lps)
     assert st["max_concurrent"] >= 2
-    for a, b in zip(res, solo):
+    for a, b, lp in zip(res, solo, lps):
         same_result(a, b)
+        # the per-round counters of a served LP describe the shared arena
+        compare(a, oracle.presolve(lp), lp, arena_stats=True)
 
 
 def test_server_device_inputs_infeasible_member_and_timeout():
@@ -69,6 +73,8 @@ def test_server_device_inputs_infeasible_member_and_timeout():
         assert e.value.status == lpp.ERR_TIMEOUT
     assert rb.status == lpp.INFEASIBLE and rb.where == lpp.WHERE_ROW and rb.index == 0
     same_result(rg, lpp.presolve(good))
+    compare(rb, oracle.presolve(bad), bad, arena_stats=True)
+    compare(rg, oracle.presolve(good), good, arena_stats=True)
 
 
 def test_server_rejects_what_cannot_fit():
