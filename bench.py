@@ -117,6 +117,84 @@ def reduce_over_ranks(ms_total: float, nnz_proc: int, device, world_size: int):
     return ms_max, float(tot.item()) / (ms_max / 1e3)
 
 
+def round_sizes(m0, n0, rows_removed, cols_fixed):
+    """Rows and columns present at the start of each round, from the per-round
+    removal counters (every removed row or column leaves in that round's
+    compaction)."""
+    m, n = [m0], [n0]
+    for a, b in zip(rows_removed[:-1], cols_fixed[:-1]):
+        m.append(m[-1] - a)
+        n.append(n[-1] - b)
+    return m, n
+
+
+def prop_bytes(nnz, m, n):
+    """Algorithmic bytes of the activity and tightening steps of one round:
+    S1 reads the CSR (12 per entry), row_ptr (4 per row), the bounds (16 per
+    column) and writes activities and counts (24 per row); S3 reads the CSC
+    (12 per entry), col_ptr (4 per column), the activities and sides (40 per
+    row) and reads and writes the bounds (32 per column)."""
+    return 24 * nnz + 68 * m + 52 * n
+
+
+def round_bytes(nnz, nnz_next, m, n, compacted):
+    """Algorithmic bytes of one whole round: S1 + S3 as prop_bytes; the row
+    classes, fixings and empty columns 60 per row + 40 per column; parallel
+    rows 12 per surviving entry + 120 per row (keys and their sort passes);
+    compaction, in rounds that removed something, reads 24 per entry, writes
+    24 per surviving entry and rewrites the maps (8 per row and column)."""
+    b = prop_bytes(nnz, m, n) + 60 * m + 40 * n + 12 * nnz_next + 120 * m
+    if compacted:
+        b += 24 * nnz + 24 * nnz_next + 8 * (m + n)
+    return b
+
+
+def describe_rounds(info, first, peak_gbs):
+    """Per-round sizes, times, nnz/s and the HBM fraction of each whole round
+    (its algorithmic bytes / its time / the peak)."""
+    round_ms, round_nnz, round_rows, round_cols, round_bounds = first
+    m_r, n_r = round_sizes(info.m, info.n, round_rows, round_cols)
+    exact = info.status != 0 or (m_r[-1] - round_rows[-1] == info.m_red and n_r[-1] - round_cols[-1] == info.n_red)
+    nxt = list(round_nnz[1:]) + [info.nnz_red]
+    rb = [round_bytes(z, z2, a, b, ra > 0 or cb > 0)
+          for z, z2, a, b, ra, cb in zip(round_nnz, nxt, m_r, n_r, round_rows, round_cols)]
+    return {"rounds": len(round_ms), "presolve_ms": info.presolve_ms, "round_ms": round_ms, "round_nnz": round_nnz,
+            "round_m": m_r, "round_n": n_r, "round_sizes_exact": bool(exact),
+            "nnz_per_s_per_round": [n_ / (t / 1e3) for n_, t in zip(round_nnz, round_ms)],
+            "round_hbm_frac": [b / (t / 1e3) / 1e9 / peak_gbs for b, t in zip(rb, round_ms)],
+            "round_rows_removed": round_rows, "round_cols_fixed": round_cols, "round_bounds_changed": round_bounds,
+            "reduced": {"m": info.m_red, "n": info.n_red, "nnz": info.nnz_red,
+                        "nnz_ratio": info.nnz_red / max(1, info.nnz)},
+            "s5_rows_left_at_cap": int(info.s5_left)}
+
+
+def prop_roofline(kern, rounds, peak_gbs, peak_src, traffic):
+    """Roofline of the fused activity kernel family: its algorithmic bytes
+    (prop_bytes of each round's nnz, m, n) over its CUDA-event time, against
+    the measured HBM copy bandwidth; the FP64 view beside it."""
+    pk = kern.get("prop", {"ms": 0.0, "bytes": 0.0, "launches": 1, "fp64_ops": 0.0})
+    secs = pk["ms"] / 1e3
+    alg = sum(prop_bytes(z, a, b) for z, a, b in zip(rounds["round_nnz"], rounds["round_m"], rounds["round_n"]))
+    launches = max(1, pk["launches"])
+    achieved = alg / secs / 1e9 if secs > 0 else 0.0
+    # FP64 view: 2 DFMA per SM per clock x 152 SMs x 2.07 GHz x 2 flops = 1.26 TFLOP/s
+    fp64_peak = 2 * 152 * 2.070e9 * 2 / 1e12
+    fp64 = pk["fp64_ops"] * 2 / secs / 1e12 if secs > 0 else 0.0
+    return {"bound": "hbm", "kernel": "k_prop_groups + long-row chunks (S1+S2+S3 fused)",
+            "achieved": achieved, "peak": peak_gbs, "unit": "GB/s", "frac": achieved / peak_gbs,
+            "peak_source": f"{peak_src} hbm_gbs (copy bandwidth)",
+            "bytes_per_launch": alg / launches,
+            "bytes_basis": "per round 24 nnz + 68 m + 52 n (S1 + S3 algorithmic bytes), one launch per round",
+            "traffic": traffic, "launches": pk["launches"], "avg_ms": pk["ms"] / launches,
+            "fp64_view": {"achieved_TFLOPs": fp64, "peak_TFLOPs": fp64_peak, "frac": fp64 / fp64_peak,
+                          "work": "2 FMA per evaluated nonzero (activities) + 2 FMA per entry side S3 tests; "
+                                  "2 flops per FMA",
+                          "peak_source": "2 DFMA/SM/clk (ncu peak_sustained) x 152 SMs x 2.07 GHz"},
+            "kernel_families": {k: {"ms": v["ms"], "launches": v["launches"],
+                                    "GBps": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else None}
+                                for k, v in kern.items()}}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -247,19 +325,10 @@ def dualfix_leg(lpp, torch, dev, stream, lp):
                       lambda r: {"dual_fixed": int(np.count_nonzero(r.col_kind == lpp.COL_EMPTY))})
 
 
-def doubleton_leg(lpp, synth, torch, dev, stream):
+def doubleton_leg(lpp, synth, torch, dev, stream, q):
     """The LP-relaxation workload (500k rows, 1M columns, 7.8M nonzeros,
     4% doubleton equations, 10 dense columns) with the doubleton step on and
-    off.  While the library refuses the option, the leg reports why instead
-    (checked on a two-entry LP before the workload is generated)."""
-    tiny = synth.LP(m=1, n=2, row_ptr=np.array([0, 2], np.int32), col_idx=np.array([0, 1], np.int32),
-                    val=np.array([1.0, 1.0]), c=np.zeros(2), lhs=np.ones(1), rhs=np.ones(1),
-                    lb=np.zeros(2), ub=np.ones(2))
-    try:
-        lpp.presolve(tiny, doubletons=1).close()
-    except lpp.LppError as e:
-        return {"workload": "LP relaxation, 500k rows, 4% doubleton equations", "unavailable": str(e)}
-    q = synth.lprelax(0)
+    off."""
 
     def count(r):
         return {"doubletons": int(np.count_nonzero(r.row_kind == lpp.ROW_DOUBLETON))}
@@ -269,15 +338,53 @@ def doubleton_leg(lpp, synth, torch, dev, stream):
                       "doubletons", "s5e", count)
 
 
-def serving_leg(lpp, synth, torch, dev, pool_size=24, requests=200, budget=120 << 30, seed=0):
-    """Poisson arrivals of skewed-like LPs (nnz log-uniform in [1e3, 1e6],
+def lprelax_leg(lpp, synth, torch, dev, stream, q, peak_gbs, peak_src, steps=20, warmup=3):
+    """The LP-relaxation workload (m = 500k, n = 1M, 8M nonzeros, 10 dense
+    columns of 200k entries, 5% scaled row copies, 4% doubleton equations, 2%
+    loosened bounds) with the default steps: ms per presolve, nnz/s, per-round
+    sizes and times, and the activity kernel's roofline."""
+    d = synth_lp_to(q, torch, dev)
+    o = lpp.opts(stream=stream.cuda_stream)
+    for _ in range(warmup):
+        lpp.presolve(d, o).close()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    proc, first = 0, None
+    e0.record(stream)
+    for _ in range(steps):
+        r = lpp.presolve(d, o)
+        proc += int(r.info.nnz_processed)
+        if first is None:
+            first = (r.info, ([float(x) for x in r.round_ms], [int(x) for x in r.round_nnz],
+                              [int(x) for x in r.round_rows_removed], [int(x) for x in r.round_cols_fixed],
+                              [int(x) for x in r.round_bounds_changed]))
+        r.close()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    rounds_d = describe_rounds(first[0], first[1], peak_gbs)
+    rt = lpp.presolve(d, lpp.opts(stream=stream.cuda_stream, timing=1))
+    kern = rt.kernels
+    rt.close()
+    roof = prop_roofline(kern, rounds_d, peak_gbs, peak_src, None)
+    roof.pop("kernel_families")
+    return {"workload": f"LP relaxation (m = {q.m}, n = {q.n}, nnz = {q.nnz}): 10 dense columns of 200k, 5% "
+                        "scaled row copies, 4% doubleton equations, 2% loosened bounds; default steps",
+            "steps": steps, "ms_per_step": ms, "nnz_per_s": proc / steps / (ms / 1e3), **rounds_d,
+            "roofline": roof,
+            "kernel_families": {k: {"ms": v["ms"], "launches": v["launches"]} for k, v in kern.items()}}
+
+
+def serving_leg(lpp, synth, torch, dev, pool_size=16, requests=2000, nnz_hi=1e7, budget=120 << 30, seed=0):
+    """Poisson arrivals of skewed-like LPs (nnz log-uniform in [1e3, 1e7],
     m = nnz/10, n = 1.5 m; requests draw from a pool of `pool_size` distinct
-    LPs), replayed in real time at 0.5x, 0.8x and 1.2x the serial capacity:
-    the continuous-batching server against a serial loop of lpp_presolve on
-    the same arrivals.  Latency = completion - arrival."""
+    LPs, generated once before any timing), replayed in real time at 0.5x,
+    0.8x and 1.2x the serial capacity: the continuous-batching server against
+    a serial loop of lpp_presolve on the same arrivals.  Latency = completion
+    - arrival."""
     import threading
     rng = np.random.default_rng(seed)
-    nnz = np.exp(rng.uniform(np.log(1e3), np.log(1e6), pool_size)).astype(int)
+    nnz = np.exp(rng.uniform(np.log(1e3), np.log(nnz_hi), pool_size)).astype(int)
     pool = [synth.skewed_like(seed * 1_000_003 + k, int(z)) for k, z in enumerate(nnz)]
     dpool = [synth.LP(m=lp.m, n=lp.n, **{k: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
                                          for k, v in lp.arrays().items()}) for lp in pool]
@@ -292,7 +399,9 @@ def serving_leg(lpp, synth, torch, dev, pool_size=24, requests=200, budget=120 <
         svc.append(time.perf_counter() - t0)
     mean_svc = float(np.mean(svc))
     out = {"pool": pool_size, "requests": requests, "budget_bytes": budget, "serial_capacity_lps": 1.0 / mean_svc,
-           "pool_nnz_mean": float(np.mean([lp.nnz for lp in pool])), "rates": []}
+           "pool_nnz_mean": float(np.mean([lp.nnz for lp in pool])), "pool_nnz_max": int(max(lp.nnz for lp in pool)),
+           "workload": f"Poisson arrivals, {requests} requests per load, skewed-like LPs with nnz log-uniform in "
+                       f"[1e3, {nnz_hi:.0e}] (pool of {pool_size}), {budget >> 30} GB budget", "rates": []}
 
     def pct(a, q):
         return float(np.percentile(np.asarray(a) * 1e3, q))
@@ -395,6 +504,7 @@ def main():
     ap.add_argument("--no-colsing", action="store_true", help="skip the column-singletons leg")
     ap.add_argument("--no-dualfix", action="store_true", help="skip the dual-fixing leg")
     ap.add_argument("--no-doubletons", action="store_true", help="skip the doubleton-equations leg")
+    ap.add_argument("--no-lprelax", action="store_true", help="skip the LP-relaxation workload leg")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the LP (profiling runs only)")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: W + K steps only (no timing pass, e2e or CPU baseline)")
@@ -446,7 +556,6 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     nnz_proc = 0
     launches = 0
-    rounds = None
     first = None
     with ClockSampler(local) as clk:
         barrier()
@@ -456,11 +565,10 @@ def main():
             r = lpp.presolve(d_lp, o_dev)
             nnz_proc += int(r.info.nnz_processed)
             launches += int(r.info.launches)
-            rounds = r.rounds
             if first is None:  # host-side copies: no device work
-                first = (r.info, [float(x) for x in r.round_ms], [int(x) for x in r.round_nnz],
-                         [int(x) for x in r.round_rows_removed], [int(x) for x in r.round_cols_fixed],
-                         [int(x) for x in r.round_bounds_changed])
+                first = (r.info, ([float(x) for x in r.round_ms], [int(x) for x in r.round_nnz],
+                                  [int(x) for x in r.round_rows_removed], [int(x) for x in r.round_cols_fixed],
+                                  [int(x) for x in r.round_bounds_changed]))
             r.close()  # the reduced LP is handed on and freed, as a caller would
         ev1.record(stream)
         barrier()
@@ -470,38 +578,21 @@ def main():
         print(json.dumps({"profile": True, "steps": args.steps, "ms_per_step": ms_total / max(1, args.steps),
                           "nnz": lp.nnz}), flush=True)
         return
-    info, round_ms, round_nnz, round_rows, round_cols, round_bounds = first
+    info, per_round = first
     ms_max, value = reduce_over_ranks(ms_total, nnz_proc, dev, ws)
+    peak_gbs, peak_src = measured_peaks()
+    rounds_d = describe_rounds(info, per_round, peak_gbs)
 
     # per-kernel times: one more step with CUDA events around every launch family
     rt = lpp.presolve(d_lp, o_time)
     kern = rt.kernels
     rt.close()
-    peak_gbs, peak_src = measured_peaks()
-    pk = kern.get("prop", {"ms": 0.0, "bytes": 0.0, "launches": 1, "fp64_ops": 0.0})
     traffic_file = os.path.join(ROOT, "profiles", "prop_traffic.json")
     traffic = None
     if os.path.exists(traffic_file):
         with open(traffic_file) as f:
             traffic = json.load(f).get("bytes_per_launch")
-    # The fused activity kernel is FP64-pipe bound (ncu: FP64 pipe ~80% busy,
-    # DRAM ~6%): its roofline is the FP64 rate, 2 DFMA per SM per clock x 152
-    # SMs x 2.07 GHz x 2 flops = 1.26 TFLOP/s (unit counts and clock).
-    fp64_peak = 2 * 152 * 2.070e9 * 2 / 1e12
-    secs = pk["ms"] / 1e3
-    achieved = pk["fp64_ops"] * 2 / secs / 1e12 if secs > 0 else 0.0
-    hbm = pk["bytes"] / secs / 1e9 if secs > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": "k_prop_groups + long-row chunks (S1+S2+S3 fused)",
-                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                "peak_source": "FP64 unit count x clock: 2 DFMA/SM/clk (ncu peak_sustained), 152 SMs, 2.07 GHz",
-                "work": "2 FMA per nonzero of the rows S1 evaluates (activities) + 2 FMA per entry side S3 tests "
-                        "(residual, sign test); 2 flops per FMA",
-                "traffic": traffic, "launches": pk["launches"], "avg_ms": pk["ms"] / max(1, pk["launches"]),
-                "hbm_view": {"achieved_GBps": hbm, "peak_GBps": peak_gbs, "frac": hbm / peak_gbs,
-                             "peak_source": f"{peak_src} hbm_gbs"},
-                "kernel_families": {k: {"ms": v["ms"], "launches": v["launches"],
-                                        "GBps": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else None}
-                                    for k, v in kern.items()}}
+    roofline = prop_roofline(kern, rounds_d, peak_gbs, peak_src, traffic)
 
     # end to end: pinned host buffers, H2D + presolve + D2H of the reduced LP
     pinned = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in lp.arrays().items()}
@@ -544,28 +635,25 @@ def main():
     dualfix = None
     if not args.no_dualfix:
         dualfix = dualfix_leg(lpp, torch, dev, stream, lp)
-    doubletons = None
-    if not args.no_doubletons:
-        doubletons = doubleton_leg(lpp, synth, torch, dev, stream)
+    lprelax = doubletons = None
+    if not (args.no_lprelax and args.no_doubletons):
+        q = synth.lprelax(0)
+        if not args.no_lprelax:
+            lprelax = lprelax_leg(lpp, synth, torch, dev, stream, q, peak_gbs, peak_src)
+        if not args.no_doubletons:
+            doubletons = doubleton_leg(lpp, synth, torch, dev, stream, q)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD if s == 1 else f"{WORKLOAD} (scaled by {s})",
-                           "m": lp.m, "n": lp.n, "nnz": lp.nnz,
-                           "rounds": rounds, "presolve_ms": info.presolve_ms,
-                           "round_ms": round_ms, "round_nnz": round_nnz,
-                           "nnz_per_s_per_round": [n_ / (m_ / 1e3) for n_, m_ in zip(round_nnz, round_ms)],
-                           "round_rows_removed": round_rows, "round_cols_fixed": round_cols,
-                           "round_bounds_changed": round_bounds,
-                           "reduced": {"m": info.m_red, "n": info.n_red, "nnz": info.nnz_red,
-                                       "nnz_ratio": info.nnz_red / max(1, info.nnz)},
+                           "m": lp.m, "n": lp.n, "nnz": lp.nnz, **rounds_d,
                            "l2": "inputs larger than L2 (CSR alone ~245 MB > 129 MB)",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
                 "batched": batched, "serving": serving, "parallel_cols": parcols, "col_singletons": colsing,
-                "dual_fixing": dualfix, "doubletons": doubletons}
+                "dual_fixing": dualfix, "doubletons": doubletons, "lp_relaxation": lprelax}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
