@@ -15,12 +15,12 @@
 // then writes its entries from its own offset.
 #include <algorithm>
 
+#include "compact_dev.cuh"
 #include "lpp_launch.h"
 
 namespace lpp {
 
 namespace {
-
 
 __global__ void k_lp_dead(Ctx C, CompactCtx K) {
     const int32_t lp = blockIdx.x * blockDim.x + threadIdx.x;
@@ -139,16 +139,6 @@ __global__ void k_long_prefix(const SegMat M, const int32_t *ch_cnt, int32_t *ch
     }
 }
 
-// ------------------------------------------------- locks (dual fixing, S6)
-// A kept row a_ij x_j + ... in [L_i, U_i] locks x_j downwards when a_ij > 0
-// and L_i is finite or a_ij < 0 and U_i is finite, upwards in the mirrored
-// cases: bit 1 = down, bit 2 = up, OR-combined over the column.
-__device__ __forceinline__ int32_t entry_locks(const Ctx &C, int32_t i, double a) {
-    if (C.rkind[i] != RK_KEPT) return 0;
-    const int32_t fl = is_fin(C.L[i]), fu = is_fin(C.U[i]);
-    return is_neg(a) ? (fu | (fl << 1)) : (fl | (fu << 1));
-}
-
 template <int W>
 __device__ __forceinline__ void lock_group(const Ctx &C, const CompactCtx &K, int32_t j, bool valid) {
     const unsigned mask = group_mask<W>();
@@ -192,81 +182,15 @@ __global__ void __launch_bounds__(kBlock) k_locks_long(Ctx C, CompactCtx K) {
 // ------------------------------------------------------- S6 + column keep
 __global__ void __launch_bounds__(kBlock) k_colkeep(Ctx C, CompactCtx K) {
     const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    int32_t fixed = 0;
-    if (j < C.n) {
-        const int32_t lp = lp_of_col(C, j);
-        const bool dead = K.lp_dead[lp];
-        uint8_t kind = C.ckind[j];
-        double contrib = 0.0;
-        if (!dead && kind == CK_KEPT && C.dual && (K.c_len[j] == 0 || C.dualfix)) {
-            // the bound the cost prefers, when no kept row locks the column in
-            // that direction (an empty column has no locks)
-            const int32_t lk = K.c_len[j] == 0 ? 0 : K.c_lock[j];
-            const bool dl = lk & 1, ul = lk & 2;
-            const double2 b = C.lu[j];
-            const double cj = C.c[j];
-            double v;
-            bool fix;
-            if (cj > 0.0) { fix = !dl; v = b.x; }
-            else if (cj < 0.0) { fix = !ul; v = b.y; }
-            else if (!dl && is_fin(b.x)) { fix = true; v = b.x; }
-            else if (!ul && is_fin(b.y)) { fix = true; v = b.y; }
-            else { fix = !dl && !ul; v = 0.0; }
-            if (!fix) {
-                // locked: kept
-            } else if (!is_fin(v)) {
-                atomicMin(&C.verdict[lp * V_SLOTS + V_S6_COL], C.cmap[j]);
-            } else {
-                kind = CK_EMPTY;
-                C.ckind[j] = kind;
-                C.fixv[j] = v;
-                const int32_t o = C.cmap[j];
-                C.rec_ck[o] = CK_EMPTY;
-                C.rec_cr[o] = lp_round(C, lp);
-                C.rec_cv[o] = v;
-                C.lp_changed[lp] = 1;
-                fixed = 1;
-            }
-        }
-        if (!dead && kind != CK_KEPT && kind != CK_PARALLEL) contrib = C.c[j] * C.fixv[j];  // merged: none
-        const bool keep = !dead && kind == CK_KEPT;
-        K.c_keep[j] = keep;
-        if (!keep) K.c_len[j] = 0;
-        K.contrib[j] = contrib;
-    }
+    const int32_t fixed = j < C.n ? colkeep_one(C, K, j) : 0;
     block_add(fixed, &C.st->cols_fixed);
 }
 
 // --------------------------------------------------------------- CSR count
 template <int W>
 __device__ __forceinline__ void csr_count_group(const Ctx &C, const CompactCtx &K, int32_t i, bool valid) {
-    const unsigned mask = group_mask<W>();
-    const int lane = threadIdx.x & (W - 1);
-    int32_t beg = 0, end = 0;
-    bool keep = false;
-    if (valid) {
-        keep = C.rkind[i] == RK_KEPT && !K.lp_dead[lp_of_row(C, i)];
-        const int32_t pb = C.A.ptr[i], pe = C.A.ptr[i + 1];
-        if (lane == 0) mark_tile(K.tile_a, pb, pe, i);
-        if (keep) {
-            beg = pb;
-            end = pe;
-        }
-    }
-    int32_t cnt = 0;
-    double sh = 0.0;
-    for (int32_t k = beg + lane; k < end; k += W) {
-        const int32_t j = C.A.idx[k];
-        if (K.c_keep[j]) cnt++;
-        else sh = fma(C.A.val[k], C.fixv[j], sh);
-    }
-    cnt = group_sum<W>(cnt, mask);
-    sh = group_sum<W>(sh, mask);
-    if (valid && lane == 0) {
-        K.r_keep[i] = keep;
-        K.r_len[i] = cnt;
-        K.shift[i] = sh;
-    }
+    if (valid && (threadIdx.x & (W - 1)) == 0) mark_tile(K.tile_a, C.A.ptr[i], C.A.ptr[i + 1], i);
+    csr_count_row<W>(C, K, i, valid, valid && C.rkind[i] == RK_KEPT && !K.lp_dead[lp_of_row(C, i)]);
 }
 
 __global__ void __launch_bounds__(kBlock) k_csr_count_groups(Ctx C, CompactCtx K, GroupGrid g) {
