@@ -226,17 +226,41 @@ def batched_leg(lpp, synth, torch, dev, stream, count=4096):
                                      for k, v in lp.arrays().items()}) for lp in lps]
     o = lpp.opts(stream=stream.cuda_stream)
     packed = lpp.pack_lps(d)  # the lpp_lp array a C caller would hold
-    for r in lpp.presolve_batch(packed, o):  # warm-up at full size (memory pool)
-        r.close()
+    # warm-up at full size (memory pool); the first calls also let the
+    # library time each launch geometry of its persistent kernel once
+    for _ in range(8):
+        for r in lpp.presolve_batch(packed, o):
+            r.close()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
     e0.record(stream)
-    res = lpp.presolve_batch(packed, o)
+    for q in range(reps):
+        res = lpp.presolve_batch(packed, o)
+        if q < reps - 1:
+            for r in res:
+                r.close()
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    batch_ms = e0.elapsed_time(e1)
+    batch_ms = e0.elapsed_time(e1) / reps
+    kernel_ms = res[0].info.presolve_ms
     keys = [(r.status, r.info.m_red, r.info.n_red, r.info.nnz_red, r.rounds) for r in res]
+    recs = [(r.row_kind.copy(), r.col_kind.copy()) for r in res]
     for r in res:
+        r.close()
+    # the per-round launches over the arena, for comparison
+    o_arena = lpp.opts(stream=stream.cuda_stream, batch_persistent=0)
+    for r in lpp.presolve_batch(packed, o_arena):
+        r.close()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    res_a = lpp.presolve_batch(packed, o_arena)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    arena_ms = e0.elapsed_time(e1)
+    same_arena = all(np.array_equal(r.row_kind, a) and np.array_equal(r.col_kind, b)
+                     for r, (a, b) in zip(res_a, recs))
+    for r in res_a:
         r.close()
     e0.record(stream)
     plain = []
@@ -247,12 +271,17 @@ def batched_leg(lpp, synth, torch, dev, stream, count=4096):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     plain_ms = e0.elapsed_time(e1)
-    return {"lps": count, "nnz": int(sum(lp.nnz for lp in lps)), "batched_ms": batch_ms,
-            "batched_lps_per_s": count / (batch_ms / 1e3), "plain_ms": plain_ms,
+    nnz_all = int(sum(lp.nnz for lp in lps))
+    return {"lps": count, "nnz": nnz_all, "batched_ms": batch_ms,
+            "batched_lps_per_s": count / (batch_ms / 1e3), "batched_nnz_per_s": nnz_all / (batch_ms / 1e3),
+            "persistent_kernel_ms": kernel_ms, "host_reads_per_round": 0,
+            "per_round_launches_ms": arena_ms, "per_round_launches_lps_per_s": count / (arena_ms / 1e3),
+            "plain_ms": plain_ms,
             "plain_lps_per_s": count / (plain_ms / 1e3), "speedup": plain_ms / batch_ms,
-            "identical_results": keys == plain,
+            "identical_results": keys == plain and same_arena,
             "workload": "4096 LPs, m log-uniform in [50, 5000], n = 1.5 m, ~6 nnz/row, planted mix of the "
-                        "200-row LP scaled by m/200; device inputs; one batched call vs 4096 plain calls"}
+                        "200-row LP scaled by m/200; device inputs; one batched call (every round of each LP in one "
+                        "persistent kernel) vs the same call with per-round launches vs 4096 plain calls"}
 
 
 def opt_in_leg(lpp, torch, dev, stream, q, workload, option, fam, count, steps=10):
@@ -491,6 +520,28 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_batch(args):
+    """W + K calls of lpp_presolve_batch on the 4,096-LP workload (device
+    inputs), for a profiler: no timing, no other leg."""
+    import torch
+    from paper_2609_16182_gb300 import lpp, synth
+    dev = torch.device("cuda", 0)
+    lpp.load()
+    lps = synth.batch_mix(0, count=4096)
+    d = [synth.LP(m=lp.m, n=lp.n, **{k: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
+                                     for k, v in lp.arrays().items()}) for lp in lps]
+    packed = lpp.pack_lps(d)
+    o = lpp.opts(stream=torch.cuda.current_stream(dev).cuda_stream)
+    kernel_ms = []
+    for _ in range(args.warmup + args.steps):
+        res = lpp.presolve_batch(packed, o)
+        kernel_ms.append(res[0].info.presolve_ms)
+        for r in res:
+            r.close()
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"profile_batch": True, "calls": args.warmup + args.steps, "kernel_ms": kernel_ms}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -512,9 +563,13 @@ def main():
                     help="with --profile: the LP with 1%% of its columns copied, parallel-column step on")
     ap.add_argument("--col-singletons", action="store_true",
                     help="with --profile: the LP with free singletons in 30%% of its equality rows, step on")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="profiling run: W + K batched presolves of the 4,096-LP workload only")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_batch:
+        return profile_batch(args)
 
     import torch
     import torch.distributed as dist

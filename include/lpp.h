@@ -132,6 +132,12 @@ typedef struct lpp_opts {
                                        direction its cost prefers (dual fixing by locks)      */
     int32_t doubletons;     /* [0]     1: eliminate a column of each doubleton equation (S5e,
                                        Sec. 2.1); lpp_presolve and lpp_presolve_batch only    */
+    int32_t batch_persistent; /* [1]   lpp_presolve_batch: 1 runs every round of each LP in
+                                       one persistent kernel (a thread block per LP, no host
+                                       step between rounds) when every row and column has at
+                                       most 4096 entries and parallel_cols, col_singletons and
+                                       doubletons are 0; 0 (or an LP that does not qualify):
+                                       one set of kernel launches per round over all LPs      */
     int32_t timing;         /* [0]     1: time every kernel launch with CUDA events           */
     int32_t device;         /* [0]     CUDA device ordinal                                   */
     void *stream;           /* [NULL]  cudaStream_t to run on; NULL: a library-owned stream  */

@@ -12,8 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblpp.so")
-SOURCES = ["k_util.cu", "k_round.cu", "k_parcols.cu", "k_colsing.cu", "k_doubleton.cu", "k_compact.cu", "lpp_engine.cu", "lpp_api.cu", "lpp_serve.cu", "lpp_noalloc.cu"]
-HEADERS = ["lpp_dev.cuh", "lpp_launch.h", "lpp_engine.h", "s5e_rewrite.cuh", "s5e_logic.cuh", "ranges.h", "postsolve.h"]
+SOURCES = ["k_util.cu", "k_round.cu", "k_parcols.cu", "k_colsing.cu", "k_doubleton.cu", "k_compact.cu", "k_batch.cu", "lpp_engine.cu", "lpp_api.cu", "lpp_serve.cu", "lpp_noalloc.cu"]
+HEADERS = ["lpp_dev.cuh", "lpp_launch.h", "lpp_engine.h", "round_dev.cuh", "compact_dev.cuh", "s5e_rewrite.cuh", "s5e_logic.cuh", "ranges.h", "postsolve.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no multiply-add contraction anywhere; the kernels write fma()
 # explicitly where a fused multiply-add is meant.  The host compiler gets the

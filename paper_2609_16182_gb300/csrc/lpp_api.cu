@@ -3,7 +3,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -55,7 +57,7 @@ lpp_opts resolve_opts(const lpp_opts *opts) {
     if (o.max_rounds < 0 || o.par_max_iter < 1 || !(o.feas_tol >= 0) || !(o.bound_tol >= 0) || !(o.huge > 0) ||
         !(o.max_implied > 0) || !(o.par_tol >= 0) || (o.parallel_cols != 0 && o.parallel_cols != 1) ||
         (o.col_singletons != 0 && o.col_singletons != 1) || (o.dual_fixing != 0 && o.dual_fixing != 1) ||
-        (o.doubletons != 0 && o.doubletons != 1))
+        (o.doubletons != 0 && o.doubletons != 1) || (o.batch_persistent != 0 && o.batch_persistent != 1))
         throw StatusError(LPP_ERR_INVALID, "bad options");
     return o;
 }
@@ -366,6 +368,267 @@ void materialize_host(lpp_reduced *R, int group) {
     R->host_done |= 1 << group;
 }
 
+// ------------------------------------------------ batch: the persistent kernel
+// Launch geometry of the persistent batch kernel -- threads per block and
+// resident blocks per SM -- chosen per kind of batch (log2 of the LP count
+// and of the mean nonzeros per LP, dual fixing on or off) by measurement: the
+// first calls of a kind run each candidate once and record its kernel time,
+// later calls use the fastest.  Fewer resident blocks keep the LPs being
+// presolved inside L2; more hide more latency.  Every candidate gives the
+// same results (the lanes per row do not depend on it).
+struct FusedTuner {
+    static constexpr int kN = 6;
+    static constexpr int kThreads[kN] = {256, 256, 256, 512, 512, 128};
+    static constexpr int kPerSm[kN] = {1, 2, 4, 1, 2, 8};
+    struct Entry {
+        float ms[kN] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
+    };
+    std::mutex mu;
+    std::map<uint64_t, Entry> tab;
+    int pick(uint64_t key) {
+        std::lock_guard<std::mutex> g(mu);
+        Entry &e = tab[key];
+        int best = -1;
+        for (int c = 0; c < kN; c++) {
+            if (e.ms[c] < 0.f) return c;  // not tried yet
+            if (best < 0 || e.ms[c] < e.ms[best]) best = c;
+        }
+        return best;
+    }
+    void record(uint64_t key, int c, float ms) {
+        std::lock_guard<std::mutex> g(mu);
+        Entry &e = tab[key];
+        if (e.ms[c] < 0.f || ms < e.ms[c]) e.ms[c] = ms;
+    }
+};
+FusedTuner g_tuner;
+constexpr int FusedTuner::kThreads[FusedTuner::kN];
+constexpr int FusedTuner::kPerSm[FusedTuner::kN];
+
+uint64_t tuner_key(int32_t count, int64_t nnz, int32_t dualfix) {
+    int a = 0, b = 0;
+    while ((1LL << (a + 1)) <= count) a++;
+    const int64_t per = nnz / std::max<int32_t>(count, 1);
+    while ((1LL << (b + 1)) <= per) b++;
+    return ((uint64_t)a << 32) | ((uint64_t)b << 1) | (uint64_t)(dualfix != 0);
+}
+
+// Runs the batch in the persistent kernel when every LP qualifies (no row or
+// column beyond 4096 entries, none of the steps it does not carry); returns
+// false, with nothing done, otherwise.  E is prepared (ingested, checked,
+// transposed); the results are handed out as the per-round path does.
+bool batch_fused(Engine &E, const std::vector<Member> &mem, int32_t count, lpp_reduced **outs, lpp_postsolve **recs,
+                 lpp_status *per_lp) {
+    const lpp_opts &o = E.o;
+    if (!o.batch_persistent || o.parallel_cols || o.col_singletons || o.doubletons || o.timing || o.max_rounds <= 0)
+        return false;
+    if (E.A.cls_start[7] != E.A.cls_start[6] || E.T.cls_start[7] != E.T.cls_start[6]) return false;
+    cudaStream_t s = E.s;
+    const int32_t m0 = E.m0, n0 = E.n0;
+    const int64_t nnz0 = E.nnz0;
+    const int32_t R = std::max(0, o.max_rounds);
+    // per-LP table: ranges, S5 table region; the queue, largest LP first
+    std::vector<FusedLP> lps(count);
+    int64_t tab = 0;
+    for (int32_t k = 0; k < count; k++) {
+        const Member &mm = mem[k];
+        int64_t tcap = 2;
+        while (tcap < 2 * (int64_t)std::max(mm.m, 1)) tcap <<= 1;
+        lps[k] = FusedLP{mm.row_off, mm.col_off, (int32_t)mm.nnz_off, mm.m, mm.n, (int32_t)mm.nnz, (int32_t)tab,
+                         (int32_t)tcap};
+        tab += tcap;
+        if (tab >= 2147483647LL) return false;
+    }
+    std::vector<int32_t> queue(count);
+    for (int32_t k = 0; k < count; k++) queue[k] = k;
+    std::stable_sort(queue.begin(), queue.end(), [&](int32_t a, int32_t b) { return mem[a].nnz > mem[b].nnz; });
+    DevPool &P = E.pool;
+    FusedArgs F;
+    std::memset(&F, 0, sizeof F);
+    F.base = E.ctx(1);
+    F.K = E.K;
+    for (int b = 0; b < 2; b++) {
+        F.frp[b] = P.alloc<int32_t>((size_t)m0 + count + 1);
+        F.ftp[b] = P.alloc<int32_t>((size_t)n0 + count + 1);
+        F.ci[b] = E.ci[b];
+        F.ti[b] = E.ti[b];
+        F.rv[b] = E.rv[b];
+        F.tv[b] = E.tv[b];
+        F.L[b] = E.L[b];
+        F.U[b] = E.U[b];
+        F.c[b] = E.c[b];
+        F.lu[b] = E.lu[b];
+        F.rmap[b] = E.rmap[b];
+        F.cmap[b] = E.cmap[b];
+        F.list[b] = E.s5_list[b];
+    }
+    F.rp0 = E.rp[0];
+    F.tp0 = E.tp[0];
+    F.order = P.alloc<int32_t>(m0);
+    F.tkey = P.alloc<unsigned long long>((size_t)tab);
+    F.tlead = P.alloc<unsigned long long>((size_t)tab);
+    F.st = P.alloc<DevStatus>(count);
+    F.cnt = P.alloc<int32_t>(4 * (size_t)count);
+    F.dead = P.alloc<uint8_t>(count);
+    FusedLP *d_lps = P.alloc<FusedLP>(count);
+    int32_t *d_queue = P.alloc<int32_t>(count);
+    F.lps = d_lps;
+    F.queue = d_queue;
+    F.next = P.alloc<int32_t>(1);
+    F.count = count;
+    F.max_rounds = R;
+    F.par_max_iter = o.par_max_iter;
+    F.out = P.alloc<FusedOut>(count);
+    F.rstat = P.alloc<int32_t>(4 * (size_t)count * (size_t)R);
+    // outputs: moved to the reduced LPs' shared store and the records below
+    F.o_rp = P.alloc<int32_t>((size_t)m0 + count);
+    F.o_tp = P.alloc<int32_t>((size_t)n0 + count);
+    F.o_ci = P.alloc<int32_t>(nnz0);
+    F.o_ti = P.alloc<int32_t>(nnz0);
+    F.o_rv = P.alloc<double>(nnz0);
+    F.o_tv = P.alloc<double>(nnz0);
+    F.o_L = P.alloc<double>(m0);
+    F.o_U = P.alloc<double>(m0);
+    F.o_rmap = P.alloc<int32_t>(m0);
+    F.o_c = P.alloc<double>(n0);
+    F.o_lb = P.alloc<double>(n0);
+    F.o_ub = P.alloc<double>(n0);
+    F.o_cmap = P.alloc<int32_t>(n0);
+    F.o_fcmap = P.alloc<int32_t>(n0);
+    F.o_lu = P.alloc<double2>(n0);
+    F.o_act = P.alloc<double2>(m0);
+    F.o_ninf = P.alloc<int2>(m0);
+    F.o_armap = P.alloc<int32_t>(m0);
+    LPP_CUDA(cudaMemcpyAsync(d_lps, lps.data(), sizeof(FusedLP) * lps.size(), cudaMemcpyHostToDevice, s));
+    LPP_CUDA(cudaMemcpyAsync(d_queue, queue.data(), sizeof(int32_t) * queue.size(), cudaMemcpyHostToDevice, s));
+    LPP_CUDA(cudaMemsetAsync(F.tkey, 0, sizeof(unsigned long long) * (size_t)tab, s));
+    LPP_CUDA(cudaMemsetAsync(F.tlead, 0xff, sizeof(unsigned long long) * (size_t)tab, s));
+    LPP_CUDA(cudaMemsetAsync(F.dead, 0, (size_t)count, s));
+    LPP_CUDA(cudaMemsetAsync(F.next, 0, sizeof(int32_t), s));
+    LPP_CUDA(cudaMemsetAsync(F.rstat, 0, sizeof(int32_t) * 4 * (size_t)count * (size_t)R, s));
+    // launch geometry: the tuner's block size, as many blocks as stay resident
+    const uint64_t key = tuner_key(count, nnz0, o.dual_fixing);
+    const int cand = g_tuner.pick(key);
+    const int threads = FusedTuner::kThreads[cand];
+    int sms = 0;
+    LPP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device));
+    const int per_sm = std::max(1, std::min(FusedTuner::kPerSm[cand], batch_fused_blocks_per_sm(threads)));
+    const int blocks = (int)std::min<int64_t>(count, (int64_t)sms * per_sm);
+    cudaEvent_t e0, e1;
+    LPP_CUDA(cudaEventCreate(&e0));
+    LPP_CUDA(cudaEventCreate(&e1));
+    E.spare_events.push_back(e0);
+    E.spare_events.push_back(e1);
+    LPP_CUDA(cudaEventRecord(e0, s));
+    launch_batch_fused(F, threads, blocks, s);
+    LPP_CUDA(cudaGetLastError());
+    LPP_CUDA(cudaEventRecord(e1, s));
+    std::vector<FusedOut> out(count);
+    std::vector<int32_t> rstat(4 * (size_t)count * (size_t)R);
+    std::vector<double> offs(count);
+    LPP_CUDA(cudaMemcpyAsync(out.data(), F.out, sizeof(FusedOut) * out.size(), cudaMemcpyDeviceToHost, s));
+    LPP_CUDA(cudaMemcpyAsync(rstat.data(), F.rstat, sizeof(int32_t) * rstat.size(), cudaMemcpyDeviceToHost, s));
+    LPP_CUDA(cudaMemcpyAsync(offs.data(), E.K.offset, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
+    std::vector<DevStatus> sts(count);
+    LPP_CUDA(cudaMemcpyAsync(sts.data(), F.st, sizeof(DevStatus) * count, cudaMemcpyDeviceToHost, s));
+    LPP_CUDA(cudaStreamSynchronize(s));
+    for (auto &x : sts)
+        if (x.err) throw StatusError(LPP_ERR_CUDA, "internal: S5 hash table overflow (batch)");
+    float ms = 0.f;
+    LPP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    g_tuner.record(key, cand, ms);
+    E.loop_ms = ms;
+    // per-LP verdicts and counters for the records
+    E.lp_status.assign(count, LPP_OK);
+    E.lp_where.assign(count, LPP_WHERE_NONE);
+    E.lp_index.assign(count, -1);
+    E.lp_round.assign(count, 0);
+    E.lp_rounds.assign(count, 0);
+    int64_t proc = 0;
+    for (int32_t k = 0; k < count; k++) {
+        E.lp_status[k] = out[k].status;
+        E.lp_where[k] = out[k].where;
+        E.lp_index[k] = out[k].index;
+        E.lp_round[k] = out[k].round;
+        E.lp_rounds[k] = out[k].rounds;
+        for (int32_t r = 0; r < out[k].rounds; r++) proc += rstat[4 * ((size_t)k * R + r)];
+    }
+    E.nnz_processed = proc;
+    // records: the engine's record arrays, the fused outputs for bounds, maps
+    // and activities (each LP's at its own ranges)
+    auto D = std::make_shared<DeviceRecords>();
+    D->m0 = m0;
+    D->n0 = n0;
+    D->n_final = n0;
+    D->act_m = m0;
+    D->rk = E.rec_rk;
+    D->rr = E.rec_rr;
+    D->ra = E.rec_ra;
+    D->rv = E.rec_rv;
+    D->ck = E.rec_ck;
+    D->cr = E.rec_cr;
+    D->cv = E.rec_cv;
+    D->lu = F.o_lu;
+    D->cmap = F.o_fcmap;
+    D->act = F.o_act;
+    D->ninf = F.o_ninf;
+    D->act_rmap = F.o_armap;
+    for (void *p : {(void *)D->rk, (void *)D->rr, (void *)D->ra, (void *)D->rv, (void *)D->ck, (void *)D->cr,
+                    (void *)D->cv, (void *)D->lu, (void *)D->cmap, (void *)D->act, (void *)D->ninf,
+                    (void *)D->act_rmap}) {
+        P.forget(p);
+        D->owned.push_back(p);
+    }
+    auto store = std::make_shared<SharedStore>();
+    for (void *p : {(void *)F.o_rp, (void *)F.o_tp, (void *)F.o_ci, (void *)F.o_ti, (void *)F.o_rv, (void *)F.o_tv,
+                    (void *)F.o_L, (void *)F.o_U, (void *)F.o_rmap, (void *)F.o_c, (void *)F.o_lb, (void *)F.o_ub,
+                    (void *)F.o_cmap}) {
+        P.forget(p);
+        store->ptrs.push_back(p);
+    }
+    for (int32_t k = 0; k < count; k++) {
+        const FusedLP &L = lps[k];
+        auto *Rd = new lpp_reduced();
+        Rd->m = out[k].m;
+        Rd->n = out[k].n;
+        Rd->nnz = out[k].nnz;
+        Rd->obj_offset = offs[k];
+        Rd->rp = F.o_rp + L.row_off + k;
+        Rd->tp = F.o_tp + L.col_off + k;
+        Rd->ci = F.o_ci + L.nnz_off;
+        Rd->rv = F.o_rv + L.nnz_off;
+        Rd->ti = F.o_ti + L.nnz_off;
+        Rd->tv = F.o_tv + L.nnz_off;
+        Rd->L = F.o_L + L.row_off;
+        Rd->U = F.o_U + L.row_off;
+        Rd->c = F.o_c + L.col_off;
+        Rd->lb = F.o_lb + L.col_off;
+        Rd->ub = F.o_ub + L.col_off;
+        Rd->rmap = F.o_rmap + L.row_off;
+        Rd->cmap = F.o_cmap + L.col_off;
+        Rd->shared = store;
+        outs[k] = Rd;
+        lpp_postsolve *Pk = make_postsolve(E, D, k, Rd->m, Rd->n, Rd->nnz, offs[k], L.col_off, L.row_off, out[k].act_m);
+        const int32_t rk = out[k].rounds;
+        Pk->r_nnz.assign(rk, 0);
+        Pk->r_rows.assign(rk, 0);
+        Pk->r_cols.assign(rk, 0);
+        Pk->r_bounds.assign(rk, 0);
+        Pk->r_ms.assign(rk, 0.f);
+        for (int32_t r = 0; r < rk; r++) {
+            const int32_t *q = &rstat[4 * ((size_t)k * R + r)];
+            Pk->r_nnz[r] = q[0];
+            Pk->r_rows[r] = q[1];
+            Pk->r_cols[r] = q[2];
+            Pk->r_bounds[r] = q[3];
+        }
+        Pk->info.s5_left = out[k].s5_left;
+        recs[k] = Pk;
+        per_lp[k] = (lpp_status)Pk->info.status;
+    }
+    return true;
+}
+
 }  // namespace
 
 lpp_status lpp_noalloc_fail(lpp_status st, const char *msg) { return set_err(st, msg); }
@@ -387,6 +650,7 @@ void lpp_opts_default(lpp_opts *o) {
     o->col_singletons = 0;
     o->dual_fixing = 0;
     o->doubletons = 0;
+    o->batch_persistent = 1;
     o->timing = 0;
     o->device = 0;
     o->stream = nullptr;
@@ -480,6 +744,7 @@ lpp_status lpp_presolve_batch(const lpp_lp *ins, int32_t count, const lpp_opts *
         E->setup(o, count, mem);
         E->ingest_batch(ins, count);
         E->prepare();
+        if (batch_fused(*E, mem, count, outs, recs, per_lp)) return LPP_OK;
         E->run();
         cudaStream_t s = E->s;
         const int c = E->cur;

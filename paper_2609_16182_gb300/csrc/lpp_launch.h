@@ -132,6 +132,59 @@ void launch_s5e_scatter(const Ctx &C, const S5eBufs &D, const int32_t *rp2, int3
 // on the rewritten matrices: the rows of the cnt columns in jlist are dirty
 void launch_s5e_mark(const Ctx &C, const S5eBufs &D, int32_t cnt, cudaStream_t s);
 
+// ---------------------------------------------------------------- k_batch.cu
+// The persistent batch kernel: one thread block per LP at a time, every round
+// of the LP on the device (LPs whose rows and columns all have at most 4096
+// entries; options without parallel_cols, col_singletons and doubletons).
+struct FusedLP {
+    int32_t row_off, col_off, nnz_off;  // the LP's ranges in the arena
+    int32_t m, n, nnz;
+    int32_t tab_off, tcap;              // its S5 table: tcap slots (a power of two >= 2 m) from tab_off
+};
+
+// per LP result
+struct FusedOut {
+    int32_t status, where, index, round, rounds;
+    int32_t m, n, nnz;  // reduced sizes
+    int32_t act_m;      // rows at the start of the last round
+    int32_t pad;
+    long long s5_left;  // rows unmatched when the S5 passes stopped at the cap, over all rounds
+};
+
+struct FusedArgs {
+    Ctx base;         // arena arrays shared by all LPs (row / column work, records, options)
+    CompactCtx K;     // arena compaction work
+    int32_t *frp[2], *ftp[2];  // CSR / CSC pointers, LP k's at row_off + k / col_off + k (m + 1, n + 1 entries)
+    int32_t *ci[2], *ti[2];
+    double *rv[2], *tv[2], *L[2], *U[2], *c[2];
+    double2 *lu[2];
+    int32_t *rmap[2], *cmap[2];
+    const int32_t *rp0, *tp0;  // pointers of the ingested arena (one entry per row / column + 1)
+    int32_t *order;            // rows by length class
+    int32_t *list[2];          // S5 lists of unmatched rows
+    unsigned long long *tkey, *tlead;
+    DevStatus *st;             // per LP
+    int32_t *cnt;              // per LP: touched columns, changed columns, their entries
+    uint8_t *dead;             // per LP
+    const FusedLP *lps;
+    const int32_t *queue;      // LP order
+    int32_t *next;             // queue head
+    int32_t count, max_rounds, par_max_iter;
+    FusedOut *out;
+    int32_t *rstat;            // per LP and round: nonzeros, rows removed, columns fixed, bounds changed
+    // outputs (the LP's ranges; ptr arrays at row_off + k / col_off + k)
+    int32_t *o_rp, *o_ci, *o_tp, *o_ti, *o_rmap, *o_cmap, *o_fcmap, *o_armap;
+    double *o_rv, *o_tv, *o_L, *o_U, *o_c, *o_lb, *o_ub;
+    double2 *o_lu, *o_act;
+    int2 *o_ninf;
+};
+
+// dynamic shared memory and resident blocks per SM of a launch with `threads`
+// (128, 256 or 512) threads per block
+size_t batch_fused_smem(int threads);
+int batch_fused_blocks_per_sm(int threads);
+void launch_batch_fused(const FusedArgs &F, int threads, int blocks, cudaStream_t s);
+
 // -------------------------------------------------------------- k_compact.cu
 void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s);
 void launch_compact_scatter(const Ctx &C, const CompactCtx &K, int32_t nnz, cudaStream_t s);

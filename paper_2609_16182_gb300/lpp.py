@@ -40,7 +40,7 @@ class Opts(C.Structure):
                 ("max_implied", C.c_double), ("par_tol", C.c_double), ("max_rounds", C.c_int32),
                 ("dual_reductions", C.c_int32), ("par_max_iter", C.c_int32), ("parallel_cols", C.c_int32),
                 ("col_singletons", C.c_int32), ("dual_fixing", C.c_int32), ("doubletons", C.c_int32),
-                ("timing", C.c_int32),
+                ("batch_persistent", C.c_int32), ("timing", C.c_int32),
                 ("device", C.c_int32), ("stream", C.c_void_p)]
 
 

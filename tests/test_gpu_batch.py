@@ -79,3 +79,57 @@ def test_batch_with_long_rows_and_empty_members():
     res = lpp.presolve_batch(lps)
     for lp, r in zip(lps, res):
         same_result(r, lpp.presolve(lp))
+
+
+# ---------------------------------------------------------- persistent kernel
+# lpp_presolve_batch runs every round of each LP in one persistent kernel (a
+# thread block per LP) when every row and column has at most 4096 entries
+# and no step it does not carry is on; batch_persistent = 0 forces the
+# per-round launches over the arena.  Both must give every LP its solo result.
+
+def same_counters(a, b):
+    np.testing.assert_array_equal(a.round_nnz, b.round_nnz, err_msg="nnz per round")
+    np.testing.assert_array_equal(a.round_rows_removed, b.round_rows_removed, err_msg="rows removed per round")
+    np.testing.assert_array_equal(a.round_cols_fixed, b.round_cols_fixed, err_msg="columns removed per round")
+    np.testing.assert_array_equal(a.round_bounds_changed, b.round_bounds_changed, err_msg="bounds changed per round")
+    assert a.s5_left == b.s5_left
+
+
+@pytest.mark.parametrize("kw", [{}, {"dual_fixing": 1}, {"par_max_iter": 2}, {"max_rounds": 1}])
+def test_persistent_batch_equals_solo_and_per_round_batch(kw):
+    lps = synth.batch_mix(11, count=64, m_lo=50, m_hi=2000)
+    lps += [synth.tiny(s) for s in range(6)] + [synth.mix(3)]
+    fused = lpp.presolve_batch(lps, **kw)
+    arena = lpp.presolve_batch(lps, batch_persistent=0, **kw)
+    assert fused[0].info.launches < arena[0].info.launches  # the persistent kernel ran
+    for lp, f, a in zip(lps, fused, arena):
+        solo = lpp.presolve(lp, **kw)
+        same_result(f, solo)
+        same_result(a, solo)
+        if f.status == 0:
+            same_counters(f, solo)  # the persistent kernel counts per LP
+        o = oracle.presolve(lp, oracle.default_opts(**kw))
+        if o.audit_below_1 == 0:
+            compare(f, o, lp)
+
+
+def test_persistent_batch_parallel_rows_over_many_passes_and_verdicts():
+    from lpmake import INF, make
+    # key groups needing many leader passes, a later pass alone reducing a
+    # round, an infeasible member and an unbounded one
+    many = make([{0: 1.0, 1: float(k + 2)} for k in range(12)] + [{0: 2.0, 1: float(2 * (k + 2))} for k in range(12)],
+                [-INF] * 24, [float(10 + k) for k in range(24)], [-INF, -INF], [INF, INF])
+    later = make([{0: 1, 1: 1, 2: 2}, {1: 1, 2: 3}, {0: 5, 1: 2, 2: 6}, {0: 1}],
+                 [-INF, -INF, -20, 2], [12, 7, INF, 2], [0, -INF, -INF], [10, INF, INF])
+    bad = make([{0: 1.0, 1: 1.0}], lhs=[5], rhs=[INF], lb=[0, 0], ub=[1, 1])
+    unb = make([{0: 1.0}], lhs=[-INF], rhs=[1], lb=[0, 0], ub=[5, INF], c=[0.0, -1.0])
+    lps = [many, later, bad, unb, synth.mix(4)]
+    for cap in (1, 3, 16):
+        res = lpp.presolve_batch(lps, par_max_iter=cap)
+        for lp, r in zip(lps, res):
+            solo = lpp.presolve(lp, par_max_iter=cap)
+            same_result(r, solo)
+            if r.status == 0:
+                same_counters(r, solo)
+            compare(r, oracle.presolve(lp, oracle.default_opts(par_max_iter=cap)), lp)
+    assert res[2].status == lpp.INFEASIBLE and res[3].status == lpp.UNBOUNDED
