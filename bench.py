@@ -454,6 +454,7 @@ def serving_leg(lpp, synth, torch, dev, pool_size=16, requests=2000, nnz_hi=1e7,
             # the server
             tickets = [None] * requests
             done_at = [0.0] * requests
+            nsub = [0]
             t0 = time.perf_counter()
 
             def submitter():
@@ -461,24 +462,29 @@ def serving_leg(lpp, synth, torch, dev, pool_size=16, requests=2000, nnz_hi=1e7,
                     while time.perf_counter() - t0 < arr[k]:
                         time.sleep(0.00005)
                     tickets[k] = srv.submit(dpool[pick[k]])
+                    nsub[0] = k + 1
 
             th = threading.Thread(target=submitter)
             th.start()
-            left = set(range(requests))
-            while left:
-                for k in list(left):
-                    if tickets[k] is None:
-                        continue
+            # poll the submitted requests not yet taken (oldest first)
+            pending, nxt = [], 0
+            while nxt < requests or pending:
+                while nxt < nsub[0]:
+                    pending.append(nxt)
+                    nxt += 1
+                still = []
+                for k in pending:
                     try:
                         r = srv.take(tickets[k], 0)
                     except lpp.LppError as e:
                         if e.status == lpp.ERR_TIMEOUT:
+                            still.append(k)
                             continue
                         raise
                     done_at[k] = time.perf_counter() - t0
                     r.close()
-                    left.discard(k)
-                time.sleep(0.0002)
+                pending = still
+                time.sleep(0.00005)
             th.join()
             lat = [done_at[k] - arr[k] for k in range(requests)]
             span = max(done_at)

@@ -162,7 +162,7 @@ typedef struct lpp_info {
     int64_t launches;     /* kernels launched by the call (a batch: by the whole batch)   */
     int64_t s5_left;      /* rows of S5 key groups still unmatched when the leader passes
                              stopped at opts.par_max_iter, summed over rounds (a batch:
-                             the whole batch's; a served LP: -1, not counted)             */
+                             the whole batch's; an LP served in the shared arena: -1)     */
 } lpp_info;
 
 /* Time and traffic of one kernel family, summed over its launches
@@ -280,13 +280,17 @@ lpp_status lpp_presolve_batch(const lpp_lp *ins, int32_t count, const lpp_opts *
  * memory that resident LPs may hold.  submit copies the LP (host or device
  * input) into a queue and returns a ticket; a worker thread admits queued
  * LPs while they fit the budget, runs one presolve round over all resident
- * unfinished LPs per tick, and keeps finished LPs resident until taken.
+ * unfinished LPs per tick, and keeps finished LPs resident until taken.  When
+ * nothing is resident and at most two requests are queued, the oldest is
+ * presolved at once with its rounds back to back, as lpp_presolve would;
+ * requests arriving meanwhile wait for it, and a longer queue is batched.
  * take waits up to wait_ms (-1 = forever) for the ticket's result
  * (LPP_ERR_TIMEOUT if not ready) and hands over the reduced LP and record. */
 typedef struct lpp_server lpp_server;
 typedef struct lpp_server_stats {
     int64_t submitted, admitted, finished, taken;
     int64_t ticks;          /* batched rounds run                    */
+    int64_t solo;           /* requests presolved alone (they arrived at an idle server) */
     int64_t resident_bytes; /* device bytes held by resident LPs now */
     int64_t peak_resident_bytes;
     int32_t max_concurrent; /* most LPs resident in one tick         */

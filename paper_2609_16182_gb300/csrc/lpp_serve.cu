@@ -314,6 +314,8 @@ struct lpp_server {
     int64_t nnz_cap = 0;
     std::thread worker;
     std::mutex mu;
+    std::mutex submit_mu;                 // one device copy of a request at a time
+    cudaStream_t submit_stream = nullptr; // non-blocking: copies do not wait for the rounds
     std::condition_variable cv_work, cv_done;
     bool stop = false;
     std::string fatal;
@@ -348,8 +350,8 @@ struct lpp_server {
 
 namespace {
 
-void free_req(lpp_server::Req *q) {
-    if (q->dev) cudaFree(q->dev);
+void free_req(lpp_server::Req *q, cudaStream_t s) {
+    if (q->dev) cudaFreeAsync(q->dev, s);
     delete q;
 }
 
@@ -492,7 +494,7 @@ bool tick(lpp_server *S, std::vector<std::pair<int32_t, lpp_server::Req *>> &adm
             S->rec_cols.give(Z.cbase, Z.n0);
             Z = lpp_server::Slot();
         }
-        free_req(pr.second);
+        free_req(pr.second, E.s);
     }
     if (first) E.reschedule();
     bool any = false, retired = false;
@@ -583,11 +585,28 @@ bool tick(lpp_server *S, std::vector<std::pair<int32_t, lpp_server::Req *>> &adm
     return true;
 }
 
+// a request presolved alone on the worker's stream (lpp_presolve's engine)
+void run_solo(lpp_server *S, lpp_server::Req *q) {
+    lpp_opts o = S->o;
+    o.stream = S->E.s;
+    lpp_reduced *red = nullptr;
+    lpp_postsolve *rec = nullptr;
+    const lpp_status st = lpp_presolve(&q->lp, &o, &red, &rec);
+    const uint64_t ticket = q->ticket;
+    free_req(q, S->E.s);
+    std::lock_guard<std::mutex> g(S->mu);
+    S->done[ticket] = lpp_server::Done{st, red, rec};
+    S->stats.finished++;
+    S->stats.solo++;
+    S->cv_done.notify_all();
+}
+
 void worker_main(lpp_server *S) {
     try {
         LPP_CUDA(cudaSetDevice(S->o.device));
         while (true) {
             std::vector<std::pair<int32_t, lpp_server::Req *>> admit;
+            lpp_server::Req *solo = nullptr;
             {
                 std::unique_lock<std::mutex> lk(S->mu);
                 auto busy = [&] {
@@ -597,9 +616,17 @@ void worker_main(lpp_server *S) {
                 };
                 S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty() || busy(); });
                 if (S->stop) break;
+                // an idle server with one or two requests queued: presolve the
+                // oldest at once, rounds back to back, instead of one round
+                // per tick (a longer queue is batched)
+                if (!busy() && S->queue.size() <= 2) {
+                    solo = S->queue.front();
+                    S->queue.pop_front();
+                    S->stats.admitted++;
+                }
                 // admission, oldest first, while the arena and record space allow
                 int64_t m = S->E.m, n = S->E.n, z = S->E.nnz;
-                while (!S->queue.empty()) {
+                while (!solo && !S->queue.empty()) {
                     lpp_server::Req *q = S->queue.front();
                     const lpp_lp &lp = q->lp;
                     int32_t slot = -1;
@@ -632,6 +659,10 @@ void worker_main(lpp_server *S) {
                     admit.emplace_back(slot, q);
                     S->stats.admitted++;
                 }
+            }
+            if (solo) {
+                run_solo(S, solo);
+                continue;
             }
             const bool ran = tick(S, admit);
             std::lock_guard<std::mutex> g(S->mu);
@@ -691,6 +722,7 @@ lpp_status lpp_server_create(size_t hbm_budget, const lpp_opts *opts, lpp_server
         S->E.lp_index.assign(S->slots, -1);
         S->E.lp_round.assign(S->slots, 0);
         S->E.init_empty();
+        LPP_CUDA(cudaStreamCreateWithFlags(&S->submit_stream, cudaStreamNonBlocking));
         S->worker = std::thread(worker_main, S);
     } catch (const StatusError &e) {
         delete S;
@@ -733,16 +765,21 @@ lpp_status lpp_server_submit(lpp_server *S, const lpp_lp *lp, uint64_t *ticket) 
         q->lp.ub = d + z + 2 * m + n;
         q->lp.c = d + z + 2 * m + 2 * n;
     } else {
+        // the copy is made on the server's submit stream (which does not wait
+        // for the worker's rounds) from its stream-ordered memory pool
         const size_t ibytes = 4 * (m + 1 + z), doff = (ibytes + 7) / 8 * 8;
         const size_t bytes = doff + 8 * (z + 2 * m + 3 * n);
-        if (cudaMalloc(&q->dev, bytes) != cudaSuccess) {
+        std::lock_guard<std::mutex> sg(S->submit_mu);
+        cudaStream_t ss = S->submit_stream;
+        if (cudaMallocAsync(&q->dev, bytes, ss) != cudaSuccess) {
             delete q;
             return lpp_noalloc_fail(LPP_ERR_OOM, "device copy of the request failed");
         }
         char *p = static_cast<char *>(q->dev);
+        bool copy_ok = true;
         auto cp = [&](const void *src, size_t b) {
             void *dst = p;
-            if (b) cudaMemcpy(dst, src, b, cudaMemcpyDeviceToDevice);
+            if (b && cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToDevice, ss) != cudaSuccess) copy_ok = false;
             p += b;
             return dst;
         };
@@ -755,11 +792,16 @@ lpp_status lpp_server_submit(lpp_server *S, const lpp_lp *lp, uint64_t *ticket) 
         q->lp.lb = (const double *)cp(lp->lb, 8 * n);
         q->lp.ub = (const double *)cp(lp->ub, 8 * n);
         q->lp.c = (const double *)cp(lp->c, 8 * n);
+        if (!copy_ok || cudaStreamSynchronize(ss) != cudaSuccess) {
+            cudaFreeAsync(q->dev, ss);
+            delete q;
+            return lpp_noalloc_fail(LPP_ERR_CUDA, "device copy of the request failed");
+        }
     }
     {
         std::lock_guard<std::mutex> g(S->mu);
         if (S->stop) {
-            free_req(q);
+            free_req(q, S->submit_stream);
             return lpp_noalloc_fail(LPP_ERR_CUDA, S->fatal.empty() ? "server stopped" : S->fatal.c_str());
         }
         q->ticket = S->next_ticket++;
@@ -809,10 +851,14 @@ void lpp_server_destroy(lpp_server *S) {
     }
     S->cv_work.notify_all();
     if (S->worker.joinable()) S->worker.join();
-    for (auto *q : S->queue) free_req(q);
+    for (auto *q : S->queue) free_req(q, S->submit_stream);
     for (auto &kv : S->done) {
         lpp_free_reduced(kv.second.red);
         lpp_free_postsolve(kv.second.rec);
+    }
+    if (S->submit_stream) {
+        cudaStreamSynchronize(S->submit_stream);
+        cudaStreamDestroy(S->submit_stream);
     }
     delete S;
 }

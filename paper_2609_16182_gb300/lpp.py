@@ -59,7 +59,8 @@ class KernelStat(C.Structure):
 
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("finished", C.c_int64), ("taken", C.c_int64),
-                ("ticks", C.c_int64), ("resident_bytes", C.c_int64), ("peak_resident_bytes", C.c_int64),
+                ("ticks", C.c_int64), ("solo", C.c_int64), ("resident_bytes", C.c_int64),
+                ("peak_resident_bytes", C.c_int64),
                 ("max_concurrent", C.c_int32)]
 
 

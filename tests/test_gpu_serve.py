@@ -83,3 +83,14 @@ def test_server_rejects_what_cannot_fit():
         with pytest.raises(lpp.LppError) as e:
             srv.submit(big)
         assert e.value.status == lpp.ERR_BUDGET
+
+
+def test_a_request_to_an_idle_server_runs_at_once_and_equals_solo():
+    lp = synth.skewed(5, m=20_000, n=30_000, target_nnz=200_000, row_cap=6000)
+    solo = lpp.presolve(lp)
+    with lpp.Server(2 << 30) as srv:
+        r = srv.take(srv.submit(lp), 60_000)
+        st = srv.stats()
+    assert st["solo"] == 1 and st["ticks"] == 0
+    same_result(r, solo)
+    compare(r, oracle.presolve(lp), lp)
