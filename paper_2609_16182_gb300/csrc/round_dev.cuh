@@ -378,18 +378,36 @@ __device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, 
     double smin = 0.0, smax = 0.0;
     int nmin = 0, nmax = 0;
     unsigned long long h = 0;
-#pragma unroll 4
-    for (int32_t k = beg + lane; k < end; k += W) {  // unrolled: the bound gathers overlap (same order)
-        const int32_t j = C.A.idx[k];
-        const double a = C.A.val[k];
-        const double2 b = C.lu[j];
-        const bool neg = is_neg(a);
-        const double bmin = neg ? b.y : b.x, bmax = neg ? b.x : b.y;
-        if (is_fin(bmin)) smin = fma(a, bmin, smin);
-        else nmin++;
-        if (is_fin(bmax)) smax = fma(a, bmax, smax);
-        else nmax++;
-        h += entry_hash(j, neg != neg0);
+    // The lane's entries in steps of four, the tail of a step predicated: the
+    // four bound gathers of a step overlap, and a warp whose lanes hold rows of
+    // different lengths runs no separate remainder loop (which would issue
+    // its FP64 work a second time for the lanes still in it).  The sums take
+    // the entries in the same order as a plain loop.
+    for (int32_t k0 = beg + lane; k0 < end; k0 += 4 * W) {
+        int32_t jq[4];
+        double aq[4];
+        double2 bq[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int32_t k = k0 + q * W;
+            jq[q] = k < end ? C.A.idx[k] : 0;
+            aq[q] = k < end ? C.A.val[k] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) bq[q] = k0 + q * W < end ? C.lu[jq[q]] : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            if (k0 + q * W >= end) break;
+            const double a = aq[q];
+            const double2 b = bq[q];
+            const bool neg = is_neg(a);
+            const double bmin = neg ? b.y : b.x, bmax = neg ? b.x : b.y;
+            if (is_fin(bmin)) smin = fma(a, bmin, smin);
+            else nmin++;
+            if (is_fin(bmax)) smax = fma(a, bmax, smax);
+            else nmax++;
+            h += entry_hash(jq[q], neg != neg0);
+        }
     }
     smin = group_sum<W>(smin, mask);
     smax = group_sum<W>(smax, mask);
