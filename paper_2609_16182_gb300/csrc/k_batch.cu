@@ -130,6 +130,10 @@ __device__ void set_ctx(BlockState &S, const FusedArgs &F, const FusedLP &P) {
     C.U = F.U[b];
     C.rmap = F.rmap[b];
     C.lp_row = nullptr;
+    C.act = F.act[b];
+    C.ninf = F.ninf[b];
+    C.hrow = F.hrow[b];
+    C.rdirty = F.rdirty[b];
     C.lu = F.lu[b];
     C.c = F.c[b];
     C.cmap = F.cmap[b];
@@ -190,6 +194,7 @@ __global__ void __launch_bounds__(NT) k_batch_fused(FusedArgs F) {
         }
         int32_t status = LPP_OK, where = LPP_WHERE_NONE, vindex = -1, vround = 0, rounds = 0;
         long long s5_left = 0;
+        bool s5_clean = false;  // the last S5 resolved every group and no row changed since
         __syncthreads();
         for (int32_t r = 1; r <= F.max_rounds; r++) {
             if (tid == 0) {
@@ -212,6 +217,7 @@ __global__ void __launch_bounds__(NT) k_batch_fused(FusedArgs F) {
                     C.ckind[j] = CK_KEPT;
                     C.cchg[j] = 0;
                 }
+            for (int32_t i = r0 + tid; i < r0 + m; i += NT) C.rdnext[i] = 0;
             // rows by length class (one shared atomic per class and warp step)
             for (int32_t i0 = r0 + warp * 32; i0 < r0 + m; i0 += NT) {
                 const int32_t i = i0 + lane;
@@ -275,10 +281,25 @@ __global__ void __launch_bounds__(NT) k_batch_fused(FusedArgs F) {
             }
             changed = bsum<NT>(changed, S.w);
             fixed = bsum<NT>(fixed, S.w);
+            chg_nnz = bsum<NT>(chg_nnz, S.w);
+            // rows of columns whose bounds changed are evaluated next round
+            // (every row when those columns hold an eighth of the entries)
+            if (8 * (int64_t)chg_nnz >= nnz) {
+                for (int32_t i = r0 + tid; i < r0 + m; i += NT) C.rdnext[i] = 1;
+            } else {
+                const int32_t cc = C.cl_cnt[0];
+                for (int32_t t = tid; t < cc; t += NT) {
+                    const int32_t j = C.cl_list[t];
+                    for (int32_t e = C.T.ptr[j]; e < C.T.ptr[j + 1]; e++) C.rdnext[C.T.idx[e]] = 1;
+                }
+            }
 
             // S5, first pass: rows S2 kept with >= 2 entries, leaders elected in
-            // the LP's table, then every row against its leader (class width W)
-            for (int32_t i = r0 + tid; i < r0 + m; i += NT) {
+            // the LP's table, then every row against its leader (class width W).
+            // Skipped when the last S5 resolved every key group and no row lost
+            // an entry since (it would remove nothing).
+            const bool run_s5 = r == 1 || !s5_clean;
+            for (int32_t i = r0 + tid; i < r0 + m && run_s5; i += NT) {
                 int32_t slot = -1;
                 if (C.rkind[i] == RK_KEPT && C.A.ptr[i + 1] - C.A.ptr[i] >= 2) slot = s5_insert_row(C, i, (uint32_t)P.tcap);
                 C.rslot[i] = slot;
@@ -290,7 +311,7 @@ __global__ void __launch_bounds__(NT) k_batch_fused(FusedArgs F) {
             }
             __syncthreads();
             int32_t unmatched = 0;
-            for (int c = 0; c < 6; c++) {
+            for (int c = 0; c < 6 && run_s5; c++) {
                 const int W = 1 << c, per = 32 / W;
                 const int32_t b0 = S.cls[c], cnt = S.cls[c + 1] - b0;
                 const int32_t packets = (cnt + per - 1) / per;
@@ -312,7 +333,7 @@ __global__ void __launch_bounds__(NT) k_batch_fused(FusedArgs F) {
             }
             __syncthreads();
             // the table empty again
-            for (int32_t i = r0 + tid; i < r0 + m; i += NT) {
+            for (int32_t i = r0 + tid; i < r0 + m && run_s5; i += NT) {
                 const int32_t sl = C.rslot[i];
                 if (sl >= 0) {
                     C.tkey[sl] = 0ULL;
@@ -350,6 +371,7 @@ __global__ void __launch_bounds__(NT) k_batch_fused(FusedArgs F) {
             }
             // rows still unmatched at the pass cap (all passes ran)
             if (ncur > 0) s5_left += ncur;
+            if (run_s5) s5_clean = ncur == 0;
             for (int32_t i = r0 + tid; i < r0 + m; i += NT)
                 if (C.hasf[i]) s5_leader_one(C, i);
             removed += bsum<NT>(rem, S.w);
@@ -422,6 +444,14 @@ __global__ void __launch_bounds__(NT) k_batch_fused(FusedArgs F) {
                     F.U[nx][p] = is_fin(Uv) ? Uv - sh : Uv;
                     F.rmap[nx][p] = C.rmap[i];
                     rp2[p] = z0 + K.r_off[i];
+                    // a row that lost entries changed: evaluate it next round;
+                    // an unchanged row's S5 key is taken again when columns
+                    // were dropped (it hashes the renumbered column indices)
+                    const bool lost = K.r_len[i] != C.A.ptr[i + 1] - C.A.ptr[i];
+                    F.rdirty[nx][p] = (C.rdnext[i] | lost) ? 1 : (n2 != n ? 2 : 0);
+                    F.act[nx][p] = C.act[i];
+                    F.ninf[nx][p] = C.ninf[i];
+                    F.hrow[nx][p] = C.hrow[i];
                 }
                 for (int32_t j = c0 + tid; j < c0 + n; j += NT) {
                     const bool kp = K.c_keep[j] != 0;
@@ -503,7 +533,11 @@ __global__ void __launch_bounds__(NT) k_batch_fused(FusedArgs F) {
                     S.nnz = 0;
                     S.K.lp_dead[0] = 1;
                 }
+            } else {  // same numbering: the flags gathered this round
+                uint8_t *rd = F.rdirty[S.cur];
+                for (int32_t i = r0 + tid; i < r0 + m; i += NT) rd[i] = C.rdnext[i];
             }
+            if (fixed > 0) s5_clean = false;  // rows lost entries (S4 or S6 fixings)
             __syncthreads();
             // round end: counters, then the LP's verdict or convergence
             if (tid == 0) {
@@ -558,8 +592,8 @@ __global__ void __launch_bounds__(NT) k_batch_fused(FusedArgs F) {
             }
             const int32_t am = S.act_m, ab = S.act_buf;
             for (int32_t t = tid; t < am; t += NT) {
-                F.o_act[r0 + t] = F.base.act[r0 + t];
-                F.o_ninf[r0 + t] = F.base.ninf[r0 + t];
+                F.o_act[r0 + t] = F.act[ab][r0 + t];
+                F.o_ninf[r0 + t] = F.ninf[ab][r0 + t];
                 F.o_armap[r0 + t] = F.rmap[ab][r0 + t];
             }
             if (tid == 0) {

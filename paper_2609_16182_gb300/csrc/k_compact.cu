@@ -263,9 +263,11 @@ __global__ void __launch_bounds__(kBlock) k_rowvec(Ctx C, CompactCtx K) {
     K.rmap2[p] = C.rmap[i];
     if (C.lp_row) K.lp_row2[p] = C.lp_row[i];
     K.rp2[p] = K.r_off[i];
-    // a row that lost entries (fixed columns) changed: evaluate it next round
+    // a row that lost entries (fixed columns) changed: evaluate it next round;
+    // an unchanged row's S5 key is taken again when columns were dropped (the
+    // key hashes column indices, which the compaction renumbers)
     const bool lost = K.r_len[i] != C.A.ptr[i + 1] - C.A.ptr[i];
-    K.rdirty2[p] = (uint8_t)(C.rdnext[i] | lost);
+    K.rdirty2[p] = (C.rdnext[i] | lost) ? 1 : (K.c_pos[C.n] != C.n ? 2 : 0);
     K.act2[p] = C.act[i];
     K.ninf2[p] = C.ninf[i];
     K.hrow2[p] = C.hrow[i];

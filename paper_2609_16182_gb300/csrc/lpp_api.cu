@@ -461,6 +461,10 @@ bool batch_fused(Engine &E, const std::vector<Member> &mem, int32_t count, lpp_r
         F.rmap[b] = E.rmap[b];
         F.cmap[b] = E.cmap[b];
         F.list[b] = E.s5_list[b];
+        F.act[b] = E.act[b];
+        F.ninf[b] = E.ninf[b];
+        F.hrow[b] = E.hrow[b];
+        F.rdirty[b] = E.rdirty[b];
     }
     F.rp0 = E.rp[0];
     F.tp0 = E.tp[0];

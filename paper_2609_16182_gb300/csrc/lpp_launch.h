@@ -159,6 +159,10 @@ struct FusedArgs {
     double *rv[2], *tv[2], *L[2], *U[2], *c[2];
     double2 *lu[2];
     int32_t *rmap[2], *cmap[2];
+    double2 *act[2];           // row results, carried over for rows not re-evaluated
+    int2 *ninf[2];
+    unsigned long long *hrow[2];
+    uint8_t *rdirty[2];        // rows to evaluate this round (buffer 0: every row, round 1)
     const int32_t *rp0, *tp0;  // pointers of the ingested arena (one entry per row / column + 1)
     int32_t *order;            // rows by length class
     int32_t *list[2];          // S5 lists of unmatched rows

@@ -363,14 +363,14 @@ __device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, 
     // A row none of whose bounds, entries or sides changed since its last
     // evaluation has the same activities and class (kept) and yields the same
     // implied bounds, which were then already applied or rejected: skip it
-    // (its lanes stay for the warp's queue steps).
-    bool act = valid;
-    if (valid && !C.rdirty[i]) {
-        if (lane == 0) C.rkind[i] = RK_KEPT;
-        act = false;
-    }
+    // (its lanes stay for the warp's queue steps).  Flag 2: such a row whose
+    // columns were renumbered by a compaction since; only its S5 key, which
+    // hashes the column indices, is taken again (no bound gathers).
+    const uint8_t flag = valid ? C.rdirty[i] : 0;
+    const bool act = flag == 1, rehash = flag == 2;
+    if (valid && !act && lane == 0) C.rkind[i] = RK_KEPT;
     int32_t beg = 0, end = 0;
-    if (act) {
+    if (act || rehash) {
         beg = C.A.ptr[i];
         end = C.A.ptr[i + 1];
     }
@@ -394,7 +394,7 @@ __device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, 
             aq[q] = k < end ? C.A.val[k] : 0.0;
         }
 #pragma unroll
-        for (int q = 0; q < 4; q++) bq[q] = k0 + q * W < end ? C.lu[jq[q]] : make_double2(0.0, 0.0);
+        for (int q = 0; q < 4; q++) bq[q] = act && k0 + q * W < end ? C.lu[jq[q]] : make_double2(0.0, 0.0);
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             if (k0 + q * W >= end) break;
@@ -415,6 +415,7 @@ __device__ __forceinline__ void prop_group(const Ctx &C, int32_t i, bool valid, 
     nmax = group_sum<W>(nmax, mask);
     h = group_sum<W>(h, mask);
     const int32_t len = end - beg;
+    if (rehash && lane == 0) C.hrow[i] = h + len_hash(len);
     bool up_row = false, lo_row = false;
     double dU = 0.0, dL = 0.0, Lv = 0.0, Uv = 0.0, sa = 0.0;
     int32_t sj = -1;

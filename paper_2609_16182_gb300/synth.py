@@ -544,6 +544,63 @@ def parcols(seed: int, m: int = 200, n_base: int = 280, pairs: int = 10, per_col
     return _finish(m, n, ptr, colid, vals, c, lhs, rhs, lb, ub, planted, f"parcols-{seed}")
 
 
+def late_parallel(seed: int, pairs: int = 300, w_lo: int = 3, w_hi: int = 12, decoy_frac: float = 0.25) -> LP:
+    """Rows that become parallel only after a fixed column is dropped (Sec.
+    3.2 on the reduced matrix of a later round).  Columns 0..pairs-1 are fixed
+    (lb = ub = v_t), the others lie in [0, 5].  Pair t has a row A_t over w
+    fresh columns (|a| in [1.2, 2], random signs) with U_A leaving a margin of
+    at least one over every bound it could imply (so no bound moves and A_t
+    is unchanged after round 1), and a row B_t = lam A_t + e x_{f_t} whose side
+    is lam U_A + e v_t + delta (lam in {+-1/2, +-1, +-2, +-4}, |delta| <=
+    |lam|/2, the side on the matching end for lam < 0).  A `decoy_frac` of
+    the B_t have one coefficient scaled by 1.5: same pattern and signs, not
+    parallel.  Rows are shuffled; dropping the fixed columns renumbers every
+    other column."""
+    rng = np.random.default_rng(seed)
+    w = rng.integers(w_lo, w_hi + 1, pairs)
+    n = pairs + int(w.sum())
+    lb = np.zeros(n)
+    ub = np.full(n, 5.0)
+    v = rng.uniform(-2.0, 2.0, pairs)
+    lb[:pairs] = v
+    ub[:pairs] = v
+    rows, cols, vals, lhs, rhs = [], [], [], [], []
+    lams = rng.choice([-4.0, -2.0, -1.0, -0.5, 0.5, 1.0, 2.0, 4.0], pairs)
+    decoy = rng.random(pairs) < decoy_frac
+    nxt = pairs
+    for t in range(pairs):
+        S = np.arange(nxt, nxt + w[t])
+        nxt += w[t]
+        a = rng.uniform(1.2, 2.0, w[t]) * rng.choice([-1.0, 1.0], w[t])
+        minact = 5.0 * a[a < 0].sum()
+        UA = minact + max(10.0, 0.6 * 5.0 * np.abs(a).sum()) + 1.0
+        e = _draw_magnitudes(rng, 1, -3.0, 3.0)[0]
+        lam = lams[t]
+        b = lam * a
+        if decoy[t]:
+            b[rng.integers(w[t])] *= 1.5
+        side = lam * UA + e * v[t] + rng.uniform(-0.5, 0.5) * abs(lam)
+        rows.append((S, a, -INF, UA))
+        bl, bu = (-INF, side) if lam > 0 else (side, INF)
+        rows.append((np.concatenate(([t], S)), np.concatenate(([e], b)), bl, bu))
+    perm = rng.permutation(len(rows))
+    ptr = [0]
+    for q in perm:
+        S, a, lo, hi = rows[q]
+        cols.append(S)
+        vals.append(a)
+        lhs.append(lo)
+        rhs.append(hi)
+        ptr.append(ptr[-1] + len(S))
+    m = len(rows)
+    c = rng.uniform(-1.0, 1.0, n)
+    inv = np.empty(m, np.int64)
+    inv[perm] = np.arange(m)
+    planted = dict(a_row=inv[0::2], b_row=inv[1::2], lam=lams, decoy=decoy)
+    return _finish(m, n, np.array(ptr, np.int64), np.concatenate(cols), np.concatenate(vals), c,
+                   np.array(lhs), np.array(rhs), lb, ub, planted, f"late-parallel-{seed}")
+
+
 def plant_parallel_cols(lp: LP, seed: int, frac: float = 0.01) -> LP:
     """`lp` with scaled copies of a random `frac` of its non-empty columns
     appended as new columns: A_:copy = lambda A_:base and c_copy = lambda c_base

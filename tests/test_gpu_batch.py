@@ -133,3 +133,20 @@ def test_persistent_batch_parallel_rows_over_many_passes_and_verdicts():
                 same_counters(r, solo)
             compare(r, oracle.presolve(lp, oracle.default_opts(par_max_iter=cap)), lp)
     assert res[2].status == lpp.INFEASIBLE and res[3].status == lpp.UNBOUNDED
+
+
+def test_persistent_batch_with_empty_and_degenerate_members():
+    from lpmake import INF, make
+    lps = [make([], [], [], [], [], None, n=0),                      # nothing
+           make([], [], [], [0, -1], [1, 2], [1.0, -1.0]),           # columns only
+           make([{}, {}], [-1, 0], [1, 0], [], [], None, n=0),       # rows only, empty
+           make([{0: 1.0, 1: 2.0}], [3], [3], [1, 1], [1, 1], [1.0, 1.0]),  # every column fixed on input
+           synth.tiny(5), synth.mix(6)]
+    fused = lpp.presolve_batch(lps)
+    arena = lpp.presolve_batch(lps, batch_persistent=0)
+    assert fused[0].info.launches < arena[0].info.launches
+    for lp, f, a in zip(lps, fused, arena):
+        solo = lpp.presolve(lp)
+        same_result(f, solo)
+        same_result(a, solo)
+        compare(f, oracle.presolve(lp), lp)

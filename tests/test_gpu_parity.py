@@ -57,6 +57,8 @@ HAND = [
     ([{0: 1.0, 1: 1e-11}, {0: 1.0, 2: 1.0}], [-INF, -INF], [1, 1000], [0, 0, 0], [5, INF, 5], None),
     ([{0: 1.0, 1: -1.0}, {1: 1.0, 2: -1.0}, {2: 1.0, 3: -1.0}, {0: 1.0, 1: 1.0, 2: 1.0, 3: 1.0}], [-INF] * 4,
      [0, 0, 0, 100], [0, 0, 0, 0], [10, 20, 30, 1], None),
+    # B loses the fixed x0 in round 1 and is then 2 A (round 2 merges it)
+    ([{1: 1.0, 2: 1.0}, {0: 1.0, 1: 2.0, 2: 2.0}], [-INF, -INF], [6, 13], [0, 0, 0], [0, 5, 5], [1, 1, 1]),
 ]
 
 

@@ -168,3 +168,40 @@ def test_a_later_pass_alone_reduces_a_round():
     assert sides_of(r, 0) == (-INF, 10.0)  # 12 - 1 * 2
     assert list(r.round_rows_removed) == [1, 1, 0]
     assert r.m_red == 2 and r.rounds == 3
+
+
+# ------------------------------------- rows parallel only on the reduced matrix
+def test_rows_made_parallel_by_a_fixed_column_merge_in_round_two():
+    """A = x1 + x2 <= 6 and B = x0 + 2 x1 + 2 x2 <= 13 with x0 fixed at 0: B
+    loses x0 in round 1 (S4 fixes it, the compaction drops it and renumbers
+    x1, x2), so round 2 finds B = 2 A with B's side 13 - 0 = 13 -> 6.5; A keeps
+    min(6, 6.5) = 6.  Worked by hand: no bound moves (x_j <= 6, 6.5 > 5)."""
+    lp = make([{1: 1.0, 2: 1.0}, {0: 1.0, 1: 2.0, 2: 2.0}], lhs=[-INF, -INF], rhs=[6, 13],
+              lb=[0, 0, 0], ub=[0, 5, 5], c=[1, 1, 1])
+    r = run(lp)
+    assert list(r.col_kind) == [oracle.COL_FIXED, 0, 0] and list(r.col_round) == [1, 0, 0]
+    assert r.row_kind[1] == oracle.ROW_PARALLEL and r.row_round[1] == 2
+    assert r.row_aux[1] == 0 and r.row_val[1] == 2.0
+    assert r.row_kind[0] == 0 and sides_of(r, 0) == (-INF, 6.0)
+
+
+def test_late_parallel_recipe_every_planted_pair_merges_in_round_two():
+    """synth.late_parallel by construction: each non-decoy pair (A_t, B_t)
+    merges in round 2 (the lower row index leads, lam or 1/lam exactly: both
+    are powers of two or +-1), each decoy pair stays; no column bound moves,
+    only the fixed columns go."""
+    from paper_2609_16182_gb300 import synth
+    for seed in range(2):
+        lp = synth.late_parallel(seed, pairs=120)
+        P = lp.planted
+        r = run(lp)
+        assert r.status == 0
+        assert list(np.flatnonzero(r.col_kind != 0)) == list(range(120))
+        for t, (a, b) in enumerate(zip(P["a_row"], P["b_row"])):
+            if P["decoy"][t]:
+                assert r.row_kind[a] == 0 and r.row_kind[b] == 0
+                continue
+            lam = P["lam"][t]
+            lead, fol, lv = (a, b, lam) if a < b else (b, a, 1.0 / lam)
+            assert (r.row_kind[fol], r.row_aux[fol], r.row_round[fol]) == (oracle.ROW_PARALLEL, lead, 2)
+            assert r.row_val[fol] == lv and r.row_kind[lead] == 0
