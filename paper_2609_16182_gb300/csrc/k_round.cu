@@ -315,6 +315,51 @@ __global__ void __launch_bounds__(kBlock) k_s5_tail_clear(Ctx C, const int32_t *
     }
 }
 
+// All remaining later passes in one block, for a short list: the passes
+// above (insert, match, clear) separated by block barriers instead of
+// launches, with no host read between them.  Starts at pass p0 from list
+// lists[(p0 - 1) & 1] of cnt[p0] rows, runs passes p0 .. max_iter - 1 (fewer
+// once no row is left) and writes the rows left after the last one to
+// cnt[max_iter].  The next list of a pass is written in the order the rows
+// are left (unspecified, as in the launched form; the leaders of a pass do
+// not depend on it).
+constexpr int kTailBlock = 1024;
+__global__ void __launch_bounds__(kTailBlock) k_s5_tail_block(Ctx C, int32_t *l0, int32_t *l1, int32_t *cnt,
+                                                              int32_t p0, int32_t max_iter) {
+    __shared__ int32_t s_n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int32_t n = cnt[p0], from = (p0 - 1) & 1, rem = 0;
+    for (int32_t p = p0; p < max_iter && n > 0; p++) {
+        const int32_t *lst = from ? l1 : l0;
+        int32_t *nxt = from ? l0 : l1;
+        const uint32_t cap = s5_tail_cap(C, n);
+        for (int32_t t = tid; t < n; t += kTailBlock) C.rslot[lst[t]] = s5_insert_row(C, lst[t], cap);
+        if (tid == 0) s_n = 0;
+        __syncthreads();
+        for (int32_t tb = warp * 32; tb < n; tb += kTailBlock) {  // warp-uniform: every lane calls the match
+            int32_t rm, i;
+            bool left;
+            s5_tail_match_one(C, lst, n, tb + lane, rm, left, i);
+            rem += rm;
+            if (left) nxt[atomicAdd(&s_n, 1)] = i;
+        }
+        __syncthreads();
+        for (int32_t t = tid; t < n; t += kTailBlock) {
+            const int32_t sl = C.rslot[lst[t]];
+            if (sl >= 0) {
+                C.tkey[sl] = 0ULL;
+                C.tlead[sl] = ~0ULL;
+            }
+        }
+        __syncthreads();
+        n = s_n;
+        from ^= 1;
+        __syncthreads();  // every thread has read s_n before the next pass resets it
+    }
+    block_add(rem, &C.st->rows_removed);
+    if (tid == 0) cnt[max_iter] = n;
+}
+
 __global__ void __launch_bounds__(kBlock) k_s5_leader(Ctx C) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= C.m || !C.hasf[i]) return;
@@ -413,6 +458,11 @@ void launch_s5_tail(const Ctx &C, const int32_t *list, const int32_t *cnt, int32
     (k_s5_tail_insert<<<blocks_for(max_rows, kBlock), kBlock, 0, s>>>(C, list, cnt), note_launch());
     (k_s5_tail_match<<<blocks_for(max_rows, kBlock), kBlock, 0, s>>>(C, list, cnt, out, out_cnt), note_launch());
     (k_s5_tail_clear<<<blocks_for(max_rows, kBlock), kBlock, 0, s>>>(C, list, cnt), note_launch());
+}
+
+void launch_s5_tail_block(const Ctx &C, int32_t *l0, int32_t *l1, int32_t *cnt, int32_t p0, int32_t max_iter,
+                          cudaStream_t s) {
+    (k_s5_tail_block<<<1, kTailBlock, 0, s>>>(C, l0, l1, cnt, p0, max_iter), note_launch());
 }
 
 void launch_s5_leader(const Ctx &C, cudaStream_t s) {

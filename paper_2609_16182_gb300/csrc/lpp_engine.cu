@@ -821,8 +821,18 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
         LPP_CUDA(cudaMemsetAsync(tkey, 0, sizeof(unsigned long long) * tcap, s));
         LPP_CUDA(cudaMemsetAsync(tlead, 0xff, sizeof(unsigned long long) * tcap, s));
         C.tcap = tcap;
-        int32_t chunk = 2;
+        int32_t chunk = 2, left = n1;
         for (int32_t pass = 1; pass < o.par_max_iter;) {
+            if (left <= kTailBlockRows) {  // the remaining passes in one block, one read
+                launch_s5_tail_block(C, s5_list[0], s5_list[1], s5_cnt, pass, o.par_max_iter, s);
+                LPP_CUDA(cudaGetLastError());
+                LPP_CUDA(cudaMemcpyAsync(s5_left_h, s5_cnt + o.par_max_iter, sizeof(int32_t),
+                                         cudaMemcpyDeviceToHost, s));
+                LPP_CUDA(cudaMemcpyAsync(st_h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+                LPP_CUDA(cudaStreamSynchronize(s));
+                resolved = *s5_left_h == 0;
+                break;
+            }
             const int32_t end = std::min<int32_t>(pass + chunk, o.par_max_iter);
             for (int32_t q = pass; q < end; q++)
                 launch_s5_tail(C, s5_list[(q - 1) & 1], s5_cnt + q, s5_list[q & 1], s5_cnt + q + 1, n1, s);
@@ -836,6 +846,7 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
                 resolved = true;
                 break;
             }
+            left = *s5_left_h;
             pass = end;
             chunk *= 2;
         }

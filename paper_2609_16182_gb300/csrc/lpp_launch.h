@@ -78,6 +78,11 @@ void launch_s5_pass(const Ctx &C, cudaStream_t s);
 // one later S5 pass over list[0 .. *cnt), *cnt <= max_rows; unmatched rows are appended to out
 void launch_s5_tail(const Ctx &C, const int32_t *list, const int32_t *cnt, int32_t *out, int32_t *out_cnt,
                     int32_t max_rows, cudaStream_t s);
+// all remaining later S5 passes of a short list in one block (passes p0 ..
+// max_iter - 1; rows left after the last one in cnt[max_iter])
+void launch_s5_tail_block(const Ctx &C, int32_t *l0, int32_t *l1, int32_t *cnt, int32_t p0, int32_t max_iter,
+                          cudaStream_t s);
+constexpr int32_t kTailBlockRows = 4096;  // longest list the one-block form takes
 void launch_s5_leader(const Ctx &C, cudaStream_t s);
 
 // --------------------------------------------------------------- k_parcols.cu
