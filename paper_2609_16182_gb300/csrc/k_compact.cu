@@ -248,6 +248,63 @@ __global__ void __launch_bounds__(kBlock) k_csr_count_long(Ctx C, CompactCtx K) 
     }
 }
 
+// ------------------------------------- column counts with the input CSC kept
+// When T is the input's A^T (Ctx::t_orig) the entries per current column in
+// the kept rows are the previous counts less the entries of the rows this
+// round removed: their CSR entries, one atomic each (K.c_len holds the
+// previous counts on entry).
+template <int W>
+__device__ __forceinline__ void clen_dec_group(const Ctx &C, const CompactCtx &K, int32_t i, bool valid) {
+    const int lane = threadIdx.x & (W - 1);
+    int32_t beg = 0, end = 0;
+    if (valid && C.rkind[i] != RK_KEPT) {
+        beg = C.A.ptr[i];
+        end = C.A.ptr[i + 1];
+    }
+    for (int32_t k = beg + lane; k < end; k += W) atomicSub(&K.c_len[C.A.idx[k]], 1);
+}
+
+__global__ void __launch_bounds__(kBlock) k_clen_dec_groups(Ctx C, CompactCtx K, GroupGrid g) {
+    const int c = grid_class(g, blockIdx.x);
+    const int W = 1 << c;
+    const int32_t pos = C.A.cls_start[c] + (blockIdx.x - g.blk_start[c]) * (kBlock / W) + threadIdx.x / W;
+    const bool valid = pos < C.A.cls_start[c + 1];
+    const int32_t i = valid ? C.A.order[pos] : 0;
+    switch (c) {
+        case 0: clen_dec_group<1>(C, K, i, valid); break;
+        case 1: clen_dec_group<2>(C, K, i, valid); break;
+        case 2: clen_dec_group<4>(C, K, i, valid); break;
+        case 3: clen_dec_group<8>(C, K, i, valid); break;
+        case 4: clen_dec_group<16>(C, K, i, valid); break;
+        default: clen_dec_group<32>(C, K, i, valid); break;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_clen_dec_long(Ctx C, CompactCtx K) {
+    const Chunk ch = C.A.chunks[blockIdx.x];
+    if (C.rkind[ch.seg] == RK_KEPT) return;  // block-uniform
+    for (int32_t k = ch.begin + threadIdx.x; k < ch.end; k += kBlock) atomicSub(&K.c_len[C.A.idx[k]], 1);
+}
+
+// input rows / columns still in the LP, as a row kind (KEPT or not) and a
+// keep flag for the compaction of the input CSC into the result's
+__global__ void k_rows_left(const int32_t *rinv, int32_t m, uint8_t *rk) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) rk[i] = rinv[i] >= 0 ? (uint8_t)RK_KEPT : (uint8_t)RK_EMPTY;
+}
+__global__ void k_cols_left(const int32_t *cinv, int32_t n, int32_t *keep, int32_t *len) {
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    keep[j] = cinv[j] >= 0;
+    if (cinv[j] < 0) len[j] = 0;
+}
+// the result CSC's pointers from the kept input columns' offsets
+__global__ void k_cols_ptr(const CompactCtx K, int32_t n, int32_t *ptr) {
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j == 0) ptr[K.c_pos[n]] = K.c_off[n];
+    if (j < n && K.c_keep[j]) ptr[K.c_pos[j]] = K.c_off[j];
+}
+
 // ---------------------------------------------------------- vector gathers
 __global__ void __launch_bounds__(kBlock) k_rowvec(Ctx C, CompactCtx K) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -255,6 +312,7 @@ __global__ void __launch_bounds__(kBlock) k_rowvec(Ctx C, CompactCtx K) {
     if (i == C.m - 1) K.rp2[K.r_pos[C.m]] = K.r_off[C.m];
     const int32_t p = K.r_pos[i];
     K.r_new[i] = K.r_keep[i] ? p : -1;
+    if (K.rinv) K.rinv[C.rmap[i]] = K.r_keep[i] ? p : -1;
     if (!K.r_keep[i]) return;
     const double sh = K.shift[i];
     const double Lv = C.L[i], Uv = C.U[i];
@@ -276,15 +334,17 @@ __global__ void __launch_bounds__(kBlock) k_rowvec(Ctx C, CompactCtx K) {
 __global__ void __launch_bounds__(kBlock) k_colvec(Ctx C, CompactCtx K) {
     const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= C.n) return;
-    if (j == C.n - 1) K.cp2[K.c_pos[C.n]] = K.c_off[C.n];
+    if (K.cp2 && j == C.n - 1) K.cp2[K.c_pos[C.n]] = K.c_off[C.n];
     const int32_t p = K.c_pos[j];
     K.c_new[j] = K.c_keep[j] ? p : -1;
+    if (K.cinv) K.cinv[C.cmap[j]] = K.c_keep[j] ? p : -1;
     if (!K.c_keep[j]) return;
     K.lu2[p] = C.lu[j];
     K.c2[p] = C.c[j];
     K.cmap2[p] = C.cmap[j];
     if (C.lp_col) K.lp_col2[p] = C.lp_col[j];
-    K.cp2[p] = K.c_off[j];
+    if (K.cp2) K.cp2[p] = K.c_off[j];       // the compacted CSC
+    if (K.clen2) K.clen2[p] = K.c_len[j];   // the input CSC kept: entries per column
 }
 
 // empty matrices still need ptr[0] = 0
@@ -527,10 +587,17 @@ inline unsigned blocks_for(int64_t cnt, int threads) {
 void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s) {
     (k_lp_dead<<<blocks_for(C.nlp, 256), 256, 0, s>>>(C, K), note_launch());
     // 1. column counts over kept rows, then S6 and the column keep flags
+    const GroupGrid ga = group_grid(C.A);
+    const int32_t along = C.A.cls_start[7] - C.A.cls_start[6];
+    if (C.t_orig) {  // the previous counts less the removed rows' entries
+        if (C.n > 0) cudaMemcpyAsync(K.c_len, C.clen, sizeof(int32_t) * (size_t)C.n, cudaMemcpyDeviceToDevice, s);
+        if (ga.blk_start[6] > 0) (k_clen_dec_groups<<<ga.blk_start[6], kBlock, 0, s>>>(C, K, ga), note_launch());
+        if (along > 0 && C.A.nchunks > 0) (k_clen_dec_long<<<C.A.nchunks, kBlock, 0, s>>>(C, K), note_launch());
+    }
     const GroupGrid gt = group_grid(C.T);
-    if (gt.blk_start[6] > 0) (k_csc_count_groups<<<gt.blk_start[6], kBlock, 0, s>>>(C, K, gt), note_launch());
+    if (!C.t_orig && gt.blk_start[6] > 0) (k_csc_count_groups<<<gt.blk_start[6], kBlock, 0, s>>>(C, K, gt), note_launch());
     const int32_t tlong = C.T.cls_start[7] - C.T.cls_start[6];
-    if (tlong > 0 && C.T.nchunks > 0) {
+    if (!C.t_orig && tlong > 0 && C.T.nchunks > 0) {
         (k_csc_count_long<<<C.T.nchunks, kBlock, 0, s>>>(C, K), note_launch());
         (k_long_prefix<<<blocks_for((int64_t)tlong * 32, 128), 128, 0, s>>>(C.T, K.cht_cnt, K.cht_off, K.c_len, nullptr,
                                                                              nullptr), note_launch());
@@ -542,9 +609,7 @@ void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s) {
     }
     if (C.n > 0) (k_colkeep<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C, K), note_launch());
     // 2. row counts over kept columns and the side shifts
-    const GroupGrid ga = group_grid(C.A);
     if (ga.blk_start[6] > 0) (k_csr_count_groups<<<ga.blk_start[6], kBlock, 0, s>>>(C, K, ga), note_launch());
-    const int32_t along = C.A.cls_start[7] - C.A.cls_start[6];
     if (along > 0 && C.A.nchunks > 0) {
         (k_csr_count_long<<<C.A.nchunks, kBlock, 0, s>>>(C, K), note_launch());
         (k_long_prefix<<<blocks_for((int64_t)along * 32, 128), 128, 0, s>>>(C.A, K.chr_cnt, K.chr_off, K.r_len,
@@ -554,7 +619,7 @@ void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s) {
 
 void launch_compact_scatter(const Ctx &C, const CompactCtx &K, int32_t nnz, cudaStream_t s) {
     (k_zero_ptr<<<1, 1, 0, s>>>(K.rp2), note_launch());
-    (k_zero_ptr<<<1, 1, 0, s>>>(K.cp2), note_launch());
+    if (!C.t_orig) (k_zero_ptr<<<1, 1, 0, s>>>(K.cp2), note_launch());
     if (C.m > 0) (k_rowvec<<<blocks_for(C.m, kBlock), kBlock, 0, s>>>(C, K), note_launch());
     if (C.n > 0) (k_colvec<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C, K), note_launch());
     const int32_t ntiles = (int32_t)(((int64_t)nnz + kFlatTile - 1) / kFlatTile);
@@ -562,10 +627,45 @@ void launch_compact_scatter(const Ctx &C, const CompactCtx &K, int32_t nnz, cuda
         FlatArgs fa{C.A.ptr, C.A.idx, C.A.val, nnz, C.m, ntiles, K.r_keep, K.r_off, K.r_len, K.r_ch0,
                     K.chr_off, K.chr_cnt, K.c_new, K.tile_a, K.ci2, K.rv2};
         (k_scatter_flat<<<ntiles, kBlock, 0, s>>>(fa), note_launch());
-        FlatArgs ft{C.T.ptr, C.T.idx, C.T.val, nnz, C.n, ntiles, K.c_keep, K.c_off, K.c_len, K.c_ch0,
-                    K.cht_off, K.cht_cnt, K.r_new, K.tile_t, K.ri2, K.cv2};
+        if (!C.t_orig) {
+            FlatArgs ft{C.T.ptr, C.T.idx, C.T.val, nnz, C.n, ntiles, K.c_keep, K.c_off, K.c_len, K.c_ch0,
+                        K.cht_off, K.cht_cnt, K.r_new, K.tile_t, K.ri2, K.cv2};
+            (k_scatter_flat<<<ntiles, kBlock, 0, s>>>(ft), note_launch());
+        }
+    }
+}
+
+// The result's CSC from the input CSC C.T (input numbering, Ctx::t_orig):
+// C.rkind marks the input rows still in the LP, keep / len the input
+// columns still in it and their entries left; the one compaction of the
+// kept columns' kept entries, renumbered by rinv, into ptr / idx / val
+// (K.c_pos / c_off: the column scan, done by the caller between the two
+// calls).
+void launch_csc_from_input_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s) {
+    const GroupGrid gt = group_grid(C.T);
+    if (gt.blk_start[6] > 0) (k_csc_count_groups<<<gt.blk_start[6], kBlock, 0, s>>>(C, K, gt), note_launch());
+    const int32_t tlong = C.T.cls_start[7] - C.T.cls_start[6];
+    if (tlong > 0 && C.T.nchunks > 0) {
+        (k_csc_count_long<<<C.T.nchunks, kBlock, 0, s>>>(C, K), note_launch());
+        (k_long_prefix<<<blocks_for((int64_t)tlong * 32, 128), 128, 0, s>>>(C.T, K.cht_cnt, K.cht_off, K.c_len, nullptr,
+                                                                             nullptr), note_launch());
+    }
+    if (C.n > 0) (k_cols_left<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C.cinv, C.n, K.c_keep, K.c_len), note_launch());
+}
+
+void launch_csc_from_input_scatter(const Ctx &C, const CompactCtx &K, int64_t nnz, int32_t *ptr, int32_t *idx,
+                                   double *val, cudaStream_t s) {
+    (k_cols_ptr<<<blocks_for(std::max(C.n, 1), kBlock), kBlock, 0, s>>>(K, C.n, ptr), note_launch());
+    const int32_t ntiles = (int32_t)((nnz + kFlatTile - 1) / kFlatTile);
+    if (ntiles > 0) {
+        FlatArgs ft{C.T.ptr, C.T.idx, C.T.val, (int32_t)nnz, C.n, ntiles, K.c_keep, K.c_off, K.c_len, K.c_ch0,
+                    K.cht_off, K.cht_cnt, C.rinv, K.tile_t, idx, val};
         (k_scatter_flat<<<ntiles, kBlock, 0, s>>>(ft), note_launch());
     }
+}
+
+void launch_rows_left(const int32_t *rinv, int32_t m, uint8_t *rk, cudaStream_t s) {
+    if (m > 0) (k_rows_left<<<blocks_for(m, kBlock), kBlock, 0, s>>>(rinv, m, rk), note_launch());
 }
 
 void launch_offset(const Ctx &C, const CompactCtx &K, cudaStream_t s) {

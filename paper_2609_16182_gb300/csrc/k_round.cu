@@ -366,7 +366,13 @@ __global__ void __launch_bounds__(kBlock) k_s5_leader(Ctx C) {
     s5_leader_one(C, i);
 }
 
-// rows of a column whose bounds changed must be re-evaluated next round
+// row r of a T entry (an input row when T is not compacted: its current
+// index, none once it left) is evaluated next round
+__device__ __forceinline__ void mark_row_of(const Ctx &C, int32_t r) {
+    if (C.t_orig) r = C.rinv[r];
+    if (r >= 0) C.rdnext[r] = 1;
+}
+
 // rows of the changed short columns need their activities next round: one
 // thread per listed column; columns longer than 32 entries are walked by the
 // whole warp in turn.  When the changed columns hold at least an eighth of the
@@ -385,25 +391,27 @@ __global__ void __launch_bounds__(kBlock) k_mark_list(Ctx C, int64_t nnz) {
         int32_t b = 0, e = 0;
         if (t < cnt) {
             const int32_t j = C.cl_list[t];
-            b = C.T.ptr[j];
-            e = C.T.ptr[j + 1];
+            const int32_t jt = C.t_orig ? C.cmap[j] : j;
+            b = C.T.ptr[jt];
+            e = C.T.ptr[jt + 1];
         }
         if (e - b <= 32)
-            for (int32_t k = b; k < e; k++) C.rdnext[C.T.idx[k]] = 1;
+            for (int32_t k = b; k < e; k++) mark_row_of(C, C.T.idx[k]);
         unsigned todo = __ballot_sync(0xffffffffu, e - b > 32);
         while (todo) {
             const int src = __ffs(todo) - 1;
             todo &= todo - 1u;
             const int32_t sb = __shfl_sync(0xffffffffu, b, src), se = __shfl_sync(0xffffffffu, e, src);
-            for (int32_t k = sb + lane; k < se; k += 32) C.rdnext[C.T.idx[k]] = 1;
+            for (int32_t k = sb + lane; k < se; k += 32) mark_row_of(C, C.T.idx[k]);
         }
     }
 }
 
 __global__ void __launch_bounds__(kBlock) k_mark_long(Ctx C, int64_t nnz) {
     const Chunk ch = C.T.chunks[blockIdx.x];
-    if (!C.cchg[ch.seg] || 8 * (int64_t)*C.cl_nnz >= nnz) return;
-    for (int32_t k = ch.begin + threadIdx.x; k < ch.end; k += kBlock) C.rdnext[C.T.idx[k]] = 1;
+    const int32_t j = C.t_orig ? C.cinv[ch.seg] : ch.seg;
+    if (j < 0 || !C.cchg[j] || 8 * (int64_t)*C.cl_nnz >= nnz) return;
+    for (int32_t k = ch.begin + threadIdx.x; k < ch.end; k += kBlock) mark_row_of(C, C.T.idx[k]);
 }
 
 inline unsigned blocks_for(int64_t cnt, int threads) {

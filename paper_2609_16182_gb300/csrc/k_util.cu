@@ -510,6 +510,12 @@ __global__ void k_colptr_from_keys(const uint32_t *key, int64_t nnz, int32_t n, 
         for (int32_t j = kp + 1; j <= n; j++) tptr[j] = (int32_t)nnz;
 }
 
+// segment lengths from a pointer array
+__global__ void k_ptr_diff(const int32_t *ptr, int32_t cnt, int32_t *out) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cnt) out[i] = ptr[i + 1] - ptr[i];
+}
+
 __global__ void k_iota(int32_t *a, int32_t cnt, int32_t base) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < cnt) a[k] = base + (int32_t)k;
@@ -656,6 +662,10 @@ void sort_pairs(const uint32_t *keys, const int32_t *vals, int64_t cnt, int bits
     }
     *kout = kin;
     *vout = vin;
+}
+
+void ptr_diff(const int32_t *ptr, int32_t cnt, int32_t *out, cudaStream_t s) {
+    if (cnt > 0) (k_ptr_diff<<<blocks_for(cnt, 256), 256, 0, s>>>(ptr, cnt, out), note_launch());
 }
 
 void iota(int32_t *a, int32_t cnt, int32_t base, cudaStream_t s) {

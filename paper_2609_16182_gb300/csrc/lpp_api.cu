@@ -446,7 +446,10 @@ bool batch_fused(Engine &E, const std::vector<Member> &mem, int32_t count, lpp_r
     FusedArgs F;
     std::memset(&F, 0, sizeof F);
     F.base = E.ctx(1);
+    F.base.t_orig = 0;  // each block compacts its LP's CSC itself
+    F.base.rinv = F.base.cinv = F.base.clen = nullptr;
     F.K = E.K;
+    F.K.rinv = F.K.cinv = F.K.clen2 = nullptr;
     for (int b = 0; b < 2; b++) {
         F.frp[b] = P.alloc<int32_t>((size_t)m0 + count + 1);
         F.ftp[b] = P.alloc<int32_t>((size_t)n0 + count + 1);
@@ -671,6 +674,7 @@ lpp_status lpp_presolve(const lpp_lp *in, const lpp_opts *opts, lpp_reduced **ou
         const lpp_opts o = resolve_opts(opts);
         auto E = std::make_unique<Engine>();
         Member mm{in->m, in->n, in->nnz, 0, 0, 0, in->obj_offset};
+        E->lazy_req = true;  // the CSC is compacted once, at the end, when no step reads it
         E->setup(o, 1, {mm});
         // ingest: checks, copies, CSC, schedules (bytes: the input once, the CSC written)
         E->tbegin(F_INGEST, 24.0 * in->nnz + 48.0 * in->m + 40.0 * in->n);
@@ -745,6 +749,7 @@ lpp_status lpp_presolve_batch(const lpp_lp *ins, int32_t count, const lpp_opts *
                 throw StatusError(LPP_ERR_INVALID, "batch too large for int32 indices");
         }
         auto E = std::make_unique<Engine>();
+        E->lazy_req = true;  // the CSC is compacted once, at the end, when no step reads it
         E->setup(o, count, mem);
         E->ingest_batch(ins, count);
         E->prepare();

@@ -91,6 +91,12 @@ struct Ctx {
     double2 *lu;
     double *c;                      // written only by S5d (one product per column and round)
     const int32_t *cmap, *lp_col;
+    // t_orig: the CSC T is the input's A^T, never compacted (no step that
+    // reads columns' entries is on).  rinv / cinv map an input row / column
+    // to its current index (-1 once it left); clen: entries per current
+    // column in the current rows.
+    const int32_t *rinv, *cinv, *clen;
+    int32_t t_orig;
     // rows whose activities must be recomputed this round (1) and the flags
     // being gathered for the next round; columns whose bounds changed
     const uint8_t *rdirty;
@@ -187,6 +193,9 @@ struct CompactCtx {
     double2 *act2;                             // carried results of clean rows
     int2 *ninf2;
     unsigned long long *hrow2;
+    // CSC kept in the input's numbering (Ctx::t_orig): the input-to-current
+    // maps, updated in place, and the next entries-per-column counts
+    int32_t *rinv, *cinv, *clen2;
 };
 
 // ------------------------------------------------------------------ helpers

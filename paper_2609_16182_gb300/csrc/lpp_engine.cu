@@ -147,6 +147,11 @@ __global__ void k_gather_lps(const SrcDesc *d, int32_t *rp, int32_t *ci, double 
 }
 
 __global__ void k_set_i32(int32_t *p, int32_t v) { *p = v; }
+__global__ void k_csc_sizes(const CompactCtx K, int32_t n, DevStatus *st) {
+    st->n_new = K.c_pos[n];
+    st->nnz_new_t = K.c_off[n];
+}
+
 __global__ void k_sizes(const CompactCtx K, int32_t m, int32_t n, DevStatus *st) {
     st->m_new = K.r_pos[m];
     st->nnz_new = K.r_off[m];
@@ -265,6 +270,15 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
     }
     rdnext = pool.alloc<uint8_t>(m0);
     cchg = pool.alloc<uint8_t>(n0);
+    t_orig = lazy_req && !o.parallel_cols && !o.col_singletons && !o.dual_fixing && !o.doubletons;
+    t_fixed = false;
+    if (t_orig) {
+        rinv = pool.alloc<int32_t>(m0);
+        cinv = pool.alloc<int32_t>(n0);
+        clive[0] = pool.alloc<int32_t>(n0);
+        clive[1] = pool.alloc<int32_t>(n0);
+        rleft = pool.alloc<uint8_t>(m0);
+    }
     rkind = pool.alloc<uint8_t>(m0);
     rwork = pool.alloc<uint8_t>(m0);
     hasf = pool.alloc<uint8_t>(m0);
@@ -537,6 +551,11 @@ void Engine::prepare() {
     }
     iota(rmap[0], m0, 0, s);
     iota(cmap[0], n0, 0, s);
+    if (t_orig) {
+        iota(rinv, m0, 0, s);
+        iota(cinv, n0, 0, s);
+        ptr_diff(tp[0], n0, clive[0], s);
+    }
     fill_u64(cand_l, n0, kEncNegInf, s);
     fill_u64(cand_u, n0, kEncPosInf, s);
     LPP_CUDA(cudaMemsetAsync(ctouch, 0, sizeof(uint32_t) * (size_t)std::max(n0, 1), s));
@@ -585,13 +604,15 @@ void Engine::prepare() {
     read_status();  // also keeps offs alive until its copy is done
     if (st_h->err) throw StatusError(LPP_ERR_INVALID, "invalid LP (checks failed: vectors)");
     adopt_schedule();
+    t_fixed = t_orig;  // from here on T and its schedule stay the input's
 }
 
-// Launches the schedule builds of the current CSR and CSC; the segment
-// counts are read from st->m_new / st->n_new on the device (m, n bound them).
+// Launches the schedule builds of the current CSR and CSC (not of a CSC kept
+// as the input's); the segment counts are read from st->m_new / st->n_new on
+// the device (m, n bound them).
 void Engine::schedule_current() {
     build_schedule(rp[cur], &st->m_new, m, nnz, sa, st->cls_r, &st->nchunk_r, s);
-    build_schedule(tp[cur], &st->n_new, n, nnz, sb, st->cls_c, &st->nchunk_c, s);
+    if (!t_fixed) build_schedule(tp[cur], &st->n_new, n, nnz, sb, st->cls_c, &st->nchunk_c, s);
     LPP_CUDA(cudaGetLastError());
 }
 
@@ -605,6 +626,10 @@ void Engine::adopt_schedule() {
     A.lfirst = sa.lfirst;
     A.cnt = m;
     segmat_from_counts(A, st_h->cls_r, st_h->nchunk_r);
+    if (t_fixed) {
+        if (A.cls_start[kNumClass] != m) throw StatusError(LPP_ERR_CUDA, "internal: schedule does not cover every segment");
+        return;
+    }
     T.ptr = tp[cur];
     T.idx = ti[cur];
     T.val = tv[cur];
@@ -641,6 +666,10 @@ Ctx Engine::ctx(int32_t round) const {
     C.c = c[cur];
     C.cmap = cmap[cur];
     C.lp_col = lpcol[cur];
+    C.t_orig = t_orig ? 1 : 0;
+    C.rinv = rinv;
+    C.cinv = cinv;
+    C.clen = t_orig ? clive[cur] : nullptr;
     C.act = act[cur];
     C.ninf = ninf[cur];
     C.rdirty = rdirty[cur];
@@ -712,9 +741,12 @@ void Engine::compact(int32_t round) {
     K.rp2 = rp[nx];
     K.ci2 = ci[nx];
     K.rv2 = rv[nx];
-    K.cp2 = tp[nx];
-    K.ri2 = ti[nx];
-    K.cv2 = tv[nx];
+    K.cp2 = t_orig ? nullptr : tp[nx];
+    K.ri2 = t_orig ? nullptr : ti[nx];
+    K.cv2 = t_orig ? nullptr : tv[nx];
+    K.rinv = t_orig ? rinv : nullptr;
+    K.cinv = t_orig ? cinv : nullptr;
+    K.clen2 = t_orig ? clive[nx] : nullptr;
     K.L2 = L[nx];
     K.U2 = U[nx];
     K.rmap2 = rmap[nx];
@@ -1058,11 +1090,43 @@ void Engine::run() {
             }
         }
     }
+    if (t_orig) finish_csc();
     float lms = 0.f;
     LPP_CUDA(cudaEventRecord(eend, s));
     LPP_CUDA(cudaEventSynchronize(eend));
     LPP_CUDA(cudaEventElapsedTime(&lms, eloop, eend));
     loop_ms = lms;
+}
+
+// The result's CSC when the rounds kept the input's: one compaction of the
+// input CSC (slot 0) to the rows and columns still in the LP, renumbered,
+// into the other slot, which then becomes the current one.  Its sizes must
+// be the current CSR's.
+void Engine::finish_csc() {
+    tbegin(F_SCATTER, 24.0 * nnz0 + 12.0 * nnz + 16.0 * (m0 + n0));
+    launch_rows_left(rinv, m0, rleft, s);
+    Ctx C0 = ctx(rounds);
+    C0.rkind = rleft;
+    C0.m = m0;
+    C0.n = n0;
+    launch_csc_from_input_counts(C0, K, s);
+    scan_excl2(K.c_keep, K.c_len, K.c_pos, K.c_off, n0, scan_tmp, s);
+    const int o = 1;  // the slot not holding the input CSC
+    launch_csc_from_input_scatter(C0, K, nnz0, tp[o], ti[o], tv[o], s);
+    (k_csc_sizes<<<1, 1, 0, s>>>(K, n0, st), note_launch());
+    LPP_CUDA(cudaGetLastError());
+    tend();
+    read_status();
+    if (st_h->n_new != n || st_h->nnz_new_t != nnz)
+        throw StatusError(LPP_ERR_CUDA, "internal: result CSC sizes disagree with the CSR");
+    if (cur != o) {
+        std::swap(tp[0], tp[1]);
+        std::swap(ti[0], ti[1]);
+        std::swap(tv[0], tv[1]);
+    }
+    T.ptr = tp[cur];
+    T.idx = ti[cur];
+    T.val = tv[cur];
 }
 
 const char *fam_name(int f) { return kFamNames[f]; }

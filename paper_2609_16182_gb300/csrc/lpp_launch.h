@@ -66,6 +66,7 @@ void transpose(const int32_t *ptr, const int32_t *idx, const double *val, const 
 void sort_pairs(const uint32_t *keys, const int32_t *vals, int64_t cnt, int bits, const TransposeBufs &b,
                 const uint32_t **kout, const int32_t **vout, cudaStream_t s);
 void iota(int32_t *a, int32_t cnt, int32_t base, cudaStream_t s);
+void ptr_diff(const int32_t *ptr, int32_t cnt, int32_t *out, cudaStream_t s);  // out[i] = ptr[i+1] - ptr[i]
 void fill_u64(unsigned long long *a, int64_t cnt, unsigned long long v, cudaStream_t s);
 void fill_i32(int32_t *a, int64_t cnt, int32_t v, cudaStream_t s);
 void split_lu(const double2 *lu, int32_t n, double *lb, double *ub, cudaStream_t s);
@@ -197,6 +198,12 @@ void launch_batch_fused(const FusedArgs &F, int threads, int blocks, cudaStream_
 // -------------------------------------------------------------- k_compact.cu
 void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s);
 void launch_compact_scatter(const Ctx &C, const CompactCtx &K, int32_t nnz, cudaStream_t s);
+// the result's CSC from the input CSC when it was not compacted (Ctx::t_orig):
+// counts and keep flags, then (after the caller's column scan) the scatter
+void launch_rows_left(const int32_t *rinv, int32_t m, uint8_t *rk, cudaStream_t s);
+void launch_csc_from_input_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s);
+void launch_csc_from_input_scatter(const Ctx &C, const CompactCtx &K, int64_t nnz, int32_t *ptr, int32_t *idx,
+                                   double *val, cudaStream_t s);
 void launch_offset(const Ctx &C, const CompactCtx &K, cudaStream_t s);
 
 }  // namespace lpp

@@ -536,9 +536,13 @@ __device__ __forceinline__ void colfin_one(const Ctx &C, int32_t j, bool full, i
     C.cchg[j] = chg;
     C.ctouch[j] = 0u;
     if (chg) {
-        const int32_t len = C.T.ptr[j + 1] - C.T.ptr[j];
+        // the column's segment in T (input numbering when T is not compacted)
+        // decides list or chunks for the dirty-row marking; its current
+        // entries count towards the marking threshold
+        const int32_t jt = C.t_orig ? C.cmap[j] : j;
+        const int32_t len = C.T.ptr[jt + 1] - C.T.ptr[jt];
         if (len < kLongMin) coalesced_append(j, C.cl_cnt, C.cl_list);
-        chg_nnz += len;
+        chg_nnz += C.t_orig ? C.clen[j] : len;
     }
 }
 
