@@ -31,24 +31,67 @@ template <class T> __device__ __forceinline__ T zero_of();
 template <> __device__ __forceinline__ int32_t zero_of<int32_t>() { return 0; }
 template <> __device__ __forceinline__ Pair zero_of<Pair>() { return Pair{0, 0}; }
 
+// eight consecutive ints from a[k] (zero past cnt): two 16-byte loads when
+// all eight are in range and a + k is 16-byte aligned, else one at a time
+__device__ __forceinline__ void load8(const int32_t *a, int64_t k, int64_t cnt, int32_t *v) {
+    if (k + 8 <= cnt && (reinterpret_cast<uintptr_t>(a + k) & 15u) == 0) {
+        const int4 x = *reinterpret_cast<const int4 *>(a + k), y = *reinterpret_cast<const int4 *>(a + k + 4);
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+        v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; q++) v[q] = k + q < cnt ? a[k + q] : 0;
+    }
+}
+// eight consecutive ints to a[k] (those before cnt), the same way
+__device__ __forceinline__ void store8(int32_t *a, int64_t k, int64_t cnt, const int32_t *v) {
+    if (k + 8 <= cnt && (reinterpret_cast<uintptr_t>(a + k) & 15u) == 0) {
+        *reinterpret_cast<int4 *>(a + k) = make_int4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<int4 *>(a + k + 4) = make_int4(v[4], v[5], v[6], v[7]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+            if (k + q < cnt) a[k + q] = v[q];
+    }
+}
+
 // inputs of a scan: one array, or two arrays scanned together
 struct In1 {
     const int32_t *a;
     __device__ int32_t operator()(int64_t k) const { return a[k]; }
+    __device__ void get8(int64_t k, int64_t cnt, int32_t *v) const { load8(a, k, cnt, v); }
 };
 struct In2 {
     const int32_t *a, *b;
     __device__ Pair operator()(int64_t k) const { return Pair{a[k], b[k]}; }
+    __device__ void get8(int64_t k, int64_t cnt, Pair *v) const {
+        int32_t x[8], y[8];
+        load8(a, k, cnt, x);
+        load8(b, k, cnt, y);
+#pragma unroll
+        for (int q = 0; q < 8; q++) v[q] = Pair{x[q], y[q]};
+    }
 };
 struct Out1 {
     int32_t *a;
     __device__ void operator()(int64_t k, int32_t v) const { a[k] = v; }
+    __device__ void put8(int64_t k, int64_t cnt, const int32_t *v) const { store8(a, k, cnt, v); }
 };
 struct Out2 {
     int32_t *a, *b;
     __device__ void operator()(int64_t k, Pair v) const {
         a[k] = v.a;
         b[k] = v.b;
+    }
+    __device__ void put8(int64_t k, int64_t cnt, const Pair *v) const {
+        int32_t x[8], y[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            x[q] = v[q].a;
+            y[q] = v[q].b;
+        }
+        store8(a, k, cnt, x);
+        store8(b, k, cnt, y);
     }
 };
 
@@ -116,24 +159,23 @@ __global__ void __launch_bounds__(1024) k_scan_top(T *tsum, int32_t ntiles, Out 
 template <class T, class In, class Out>
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(In in, Out out, int64_t cnt, const T *tsum) {
     __shared__ T s_w[33];
+    static_assert(kPerThread == 8, "the scan's thread step is eight values");
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kPerThread;
     T v[kPerThread];
+    in.get8(base, cnt, v);
     T s = zero_of<T>();
 #pragma unroll
-    for (int q = 0; q < kPerThread; q++) {
-        const int64_t k = base + q;
-        v[q] = k < cnt ? in(k) : zero_of<T>();
-        s = s + v[q];
-    }
+    for (int q = 0; q < kPerThread; q++) s = s + v[q];
     T ex;
     block_excl_scan(s, ex, s_w);
     T run = tsum[blockIdx.x] + ex;
+    T o[kPerThread];
 #pragma unroll
     for (int q = 0; q < kPerThread; q++) {
-        const int64_t k = base + q;
-        if (k < cnt) out(k, run);
+        o[q] = run;
         run = run + v[q];
     }
+    out.put8(base, cnt, o);
 }
 
 // --------------------------------------------------------------- binning
