@@ -360,6 +360,87 @@ __global__ void __launch_bounds__(kTailBlock) k_s5_tail_block(Ctx C, int32_t *l0
     if (tid == 0) cnt[max_iter] = n;
 }
 
+// All remaining later passes of a long list in one cooperative launch (every
+// block resident): the passes of the launched form, separated by grid
+// barriers.  Mutable data (lists, slots, leaders, counts) is read at L2.  A
+// barrier that waits too long (it cannot, with every block resident) sets
+// st->err bit 4 and the kernel returns.  Same starting point and result
+// slot as k_s5_tail_block.
+constexpr long long kBarSpins = 1LL << 22;
+__device__ bool grid_barrier(unsigned *bar, int32_t *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        volatile int32_t *verr = err;
+        const unsigned g = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            for (long long spins = 0; *gen == g; spins++) {
+                if (spins > kBarSpins || (*verr & 4)) {
+                    atomicOr(err, 4);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kBlock) k_s5_tail_grid(Ctx C, int32_t *l0, int32_t *l1, int32_t *cnt, int32_t p0,
+                                                        int32_t max_iter, unsigned *bar) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gstride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gwarp = gtid >> 5;
+    int32_t n = __ldcg(cnt + p0), from = (p0 - 1) & 1, rem = 0;
+    bool ok = true;
+    int32_t p = p0;
+    for (; p < max_iter && n > 0 && ok; p++) {
+        const int32_t *lst = from ? l1 : l0;
+        int32_t *nxt = from ? l0 : l1;
+        const uint32_t cap = s5_tail_cap(C, n);
+        for (int64_t t = gtid; t < n; t += gstride) {
+            const int32_t i = __ldcg(lst + t);
+            C.rslot[i] = s5_insert_row(C, i, cap);
+        }
+        if (!(ok = grid_barrier(bar, &C.st->err))) break;
+        for (int64_t tb = gwarp * 32; tb < n; tb += gstride) {  // warp-uniform: every lane calls the match
+            int32_t rm, i;
+            bool left;
+            s5_tail_match_one(C, lst, n, (int32_t)(tb + lane), rm, left, i);
+            rem += rm;
+            const unsigned want = __ballot_sync(0xffffffffu, left);
+            int32_t base = 0;
+            if (lane == 0 && want) base = atomicAdd(cnt + p + 1, __popc(want));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (left) nxt[base + __popc(want & ((1u << lane) - 1u))] = i;
+        }
+        if (!(ok = grid_barrier(bar, &C.st->err))) break;
+        for (int64_t t = gtid; t < n; t += gstride) {
+            const int32_t sl = __ldcg(C.rslot + __ldcg(lst + t));
+            if (sl >= 0) {
+                C.tkey[sl] = 0ULL;
+                C.tlead[sl] = ~0ULL;
+            }
+        }
+        if (!(ok = grid_barrier(bar, &C.st->err))) break;
+        n = __ldcg(cnt + p + 1);
+        from ^= 1;
+    }
+    block_add(rem, &C.st->rows_removed);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ok) cnt[max_iter] = n;
+}
+
 __global__ void __launch_bounds__(kBlock) k_s5_leader(Ctx C) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= C.m || !C.hasf[i]) return;
@@ -471,6 +552,32 @@ void launch_s5_tail(const Ctx &C, const int32_t *list, const int32_t *cnt, int32
 void launch_s5_tail_block(const Ctx &C, int32_t *l0, int32_t *l1, int32_t *cnt, int32_t p0, int32_t max_iter,
                           cudaStream_t s) {
     (k_s5_tail_block<<<1, kTailBlock, 0, s>>>(C, l0, l1, cnt, p0, max_iter), note_launch());
+}
+
+// cooperative launch of k_s5_tail_grid, at most one block per SM and
+// resident block slot, no more than the first list needs; false if the
+// device cannot take a cooperative launch (the caller then launches passes)
+bool launch_s5_tail_grid(const Ctx &C, int32_t *l0, int32_t *l1, int32_t *cnt, int32_t p0, int32_t max_iter,
+                         int32_t rows, unsigned *bar, cudaStream_t s) {
+    static int per_sm = -1, sms = 0;
+    if (per_sm < 0) {
+        int dev = 0, coop = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int nb = 0;
+        if (coop) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_s5_tail_grid, kBlock, 0);
+        per_sm = coop ? nb : 0;
+    }
+    if (per_sm <= 0 || sms <= 0) return false;
+    const int64_t want = std::max<int64_t>(1, ((int64_t)rows + kBlock - 1) / kBlock);
+    const unsigned grid = (unsigned)std::min<int64_t>(want, (int64_t)per_sm * sms);
+    Ctx Cv = C;
+    void *args[] = {&Cv, &l0, &l1, &cnt, &p0, &max_iter, &bar};
+    if (cudaLaunchCooperativeKernel((const void *)k_s5_tail_grid, dim3(grid), dim3(kBlock), args, 0, s) != cudaSuccess)
+        return false;
+    note_launch();
+    return true;
 }
 
 void launch_s5_leader(const Ctx &C, cudaStream_t s) {

@@ -199,7 +199,14 @@ struct CompactCtx {
 };
 
 // ------------------------------------------------------------------ helpers
-__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+// The bit pattern of a double through an opaque move: on a plain bitcast the
+// compiler turns tests such as "exponent bits all set" or "all but the sign
+// bit zero" back into FP64 comparisons, which run on the scarce FP64 pipe.
+__device__ __forceinline__ long long dbits(double x) {
+    long long r;
+    asm("mov.b64 %0, %1;" : "=l"(r) : "d"(x));
+    return r;
+}
 // finite test and sign test on the bit pattern (integer pipes, not FP64)
 __device__ __forceinline__ bool is_fin(double x) {
     return (dbits(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;

@@ -299,6 +299,8 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
     s5_list[0] = pool.alloc<int32_t>(m0);
     s5_list[1] = pool.alloc<int32_t>(m0);
     s5_cnt = pool.alloc<int32_t>((size_t)o.par_max_iter + 2);
+    s5_bar = pool.alloc<unsigned>(2);
+    LPP_CUDA(cudaMemsetAsync(s5_bar, 0, 2 * sizeof(unsigned), s));
     ch_act = pool.alloc<double2>(cap_chunk);
     ch_ninf = pool.alloc<int2>(cap_chunk);
     ch_hash = pool.alloc<unsigned long long>(cap_chunk);
@@ -865,6 +867,18 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
                 resolved = *s5_left_h == 0;
                 break;
             }
+            if (launch_s5_tail_grid(C, s5_list[0], s5_list[1], s5_cnt, pass, o.par_max_iter, left, s5_bar, s)) {
+                // the remaining passes in one cooperative launch, one read
+                LPP_CUDA(cudaGetLastError());
+                LPP_CUDA(cudaMemcpyAsync(s5_left_h, s5_cnt + o.par_max_iter, sizeof(int32_t),
+                                         cudaMemcpyDeviceToHost, s));
+                LPP_CUDA(cudaMemcpyAsync(st_h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+                LPP_CUDA(cudaStreamSynchronize(s));
+                if (st_h->err & 4) throw StatusError(LPP_ERR_CUDA, "internal: S5 pass barrier timed out");
+                resolved = *s5_left_h == 0;
+                break;
+            }
+            cudaGetLastError();  // no cooperative launch: launched passes
             const int32_t end = std::min<int32_t>(pass + chunk, o.par_max_iter);
             for (int32_t q = pass; q < end; q++)
                 launch_s5_tail(C, s5_list[(q - 1) & 1], s5_cnt + q, s5_list[q & 1], s5_cnt + q + 1, n1, s);

@@ -87,6 +87,7 @@ struct Engine {
     uint8_t *rkind, *rwork, *hasf, *ckind, *lneed, *lp_changed, *lp_dead;
     unsigned long long *mL, *mU, *cand_l, *cand_u, *tkey, *tlead, *ch_hash;
     int32_t *s5_list[2] = {nullptr, nullptr}, *s5_cnt = nullptr;
+    unsigned *s5_bar = nullptr;  // grid barrier of the cooperative S5 passes (two words)
     bool s5_clean = false;  // the last S5 resolved every group and no row changed since
     // S5c (opts.parallel_cols): slots and the column table; flags, positions
     // and the (slot, column) pairs of the grouped columns with their sort

@@ -84,6 +84,11 @@ void launch_s5_tail(const Ctx &C, const int32_t *list, const int32_t *cnt, int32
 void launch_s5_tail_block(const Ctx &C, int32_t *l0, int32_t *l1, int32_t *cnt, int32_t p0, int32_t max_iter,
                           cudaStream_t s);
 constexpr int32_t kTailBlockRows = 4096;  // longest list the one-block form takes
+// all remaining later S5 passes of a longer list in one cooperative launch
+// with grid barriers (bar: two zeroed words kept by the caller); false if
+// the launch is not possible
+bool launch_s5_tail_grid(const Ctx &C, int32_t *l0, int32_t *l1, int32_t *cnt, int32_t p0, int32_t max_iter,
+                         int32_t rows, unsigned *bar, cudaStream_t s);
 void launch_s5_leader(const Ctx &C, cudaStream_t s);
 
 // --------------------------------------------------------------- k_parcols.cu

@@ -665,11 +665,13 @@ __device__ __forceinline__ void s5_tail_match_one(const Ctx &C, const int32_t *l
     int32_t li = -1, bi = 0, bl = 0, len = 0;
     double lam = 0.0;
     if (t < n) {
-        i = list[t];
-        const int32_t sl = C.rslot[i];
+        // the list, the slots and the leaders change from pass to pass, also
+        // within one launch (grid-wide passes): read at L2, never from L1
+        i = __ldcg(list + t);
+        const int32_t sl = __ldcg(C.rslot + i);
         act = sl >= 0;
         if (act) {
-            li = (int32_t)(uint32_t)(C.tlead[sl] & 0xffffffffULL);
+            li = (int32_t)(uint32_t)(__ldcg(C.tlead + sl) & 0xffffffffULL);
             if (li == i) act = false;  // the leader itself
         }
         if (act) {
