@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 
 #include "lpp_engine.h"
@@ -18,11 +19,53 @@ void cuda_check(cudaError_t e, const char *expr, const char *file, int line) {
 
 void DevPool::forget(void *p) {
     auto it = std::find(ptrs.begin(), ptrs.end(), p);
-    if (it != ptrs.end()) ptrs.erase(it);
+    if (it != ptrs.end()) {
+        sizes.erase(sizes.begin() + (it - ptrs.begin()));
+        ptrs.erase(it);
+    }
 }
 void DevPool::release() {
-    for (void *p : ptrs) cudaFreeAsync(p, s);
+    if (ptrs.empty()) return;
+    const bool done = cache && cudaStreamSynchronize(s) == cudaSuccess;
+    for (size_t k = 0; k < ptrs.size(); k++) {
+        if (done) dev_cache_put(ptrs[k], sizes[k], s);
+        else cudaFreeAsync(ptrs[k], s);
+    }
     ptrs.clear();
+    sizes.clear();
+}
+
+namespace {
+std::mutex g_dev_mu;
+std::multimap<std::pair<int, size_t>, void *> g_dev_free;
+size_t g_dev_free_bytes = 0;
+constexpr size_t kDevCacheMax = size_t(16) << 30;  // beyond this, released blocks are freed
+}  // namespace
+
+void *dev_cache_take(size_t bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> g(g_dev_mu);
+    auto it = g_dev_free.find({dev, bytes});
+    if (it == g_dev_free.end()) return nullptr;
+    void *p = it->second;
+    g_dev_free.erase(it);
+    g_dev_free_bytes -= bytes;
+    return p;
+}
+
+void dev_cache_put(void *p, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    bool keep = cudaGetDevice(&dev) == cudaSuccess;
+    {
+        std::lock_guard<std::mutex> g(g_dev_mu);
+        keep = keep && g_dev_free_bytes + bytes <= kDevCacheMax;
+        if (keep) {
+            g_dev_free.emplace(std::make_pair(dev, bytes), p);
+            g_dev_free_bytes += bytes;
+        }
+    }
+    if (!keep) cudaFreeAsync(p, s);
 }
 
 // Pinned host buffers (status mirrors, host copies of reduced LPs) are reused

@@ -31,15 +31,27 @@ struct StatusError : std::runtime_error {
 void cuda_check(cudaError_t e, const char *expr, const char *file, int line);
 #define LPP_CUDA(x) ::lpp::cuda_check((x), #x, __FILE__, __LINE__)
 
-// stream-ordered device allocations released together
+// A process-wide cache of device blocks that finished presolves released,
+// by device and exact size: a presolve makes some seventy allocations, and
+// the next presolve of an LP of the same sizes takes them back without a
+// call into the allocator.  take: such a block, or nullptr.
+void *dev_cache_take(size_t bytes);
+void dev_cache_put(void *p, size_t bytes, cudaStream_t s);
+
+// stream-ordered device allocations released together (to the cache, once
+// the stream's work on them is done)
 struct DevPool {
     cudaStream_t s = nullptr;
+    bool cache = true;  // false: released stream-ordered, without a wait
     std::vector<void *> ptrs;
+    std::vector<size_t> sizes;
     template <class T>
     T *alloc(size_t cnt) {
-        void *p = nullptr;
-        LPP_CUDA(cudaMallocAsync(&p, (cnt ? cnt : 1) * sizeof(T), s));
+        const size_t bytes = (cnt ? cnt : 1) * sizeof(T);
+        void *p = dev_cache_take(bytes);
+        if (!p) LPP_CUDA(cudaMallocAsync(&p, bytes, s));
         ptrs.push_back(p);
+        sizes.push_back(bytes);
         return static_cast<T *>(p);
     }
     void forget(void *p);  // ownership moves elsewhere

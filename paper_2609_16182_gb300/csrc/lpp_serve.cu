@@ -200,8 +200,9 @@ void Engine::init_empty() {
 
 void Engine::append(int32_t slot, const lpp_lp &in, int32_t rbase, int32_t cbase, int32_t round0) {
     const int32_t ml = in.m, nl = in.n, zl = (int32_t)in.nnz;
-    DevPool tmp;
+    DevPool tmp;  // staging of a host request: freed stream-ordered
     tmp.s = s;
+    tmp.cache = false;
     const int32_t *rp_in = in.row_ptr, *ci_in = in.col_idx;
     const double *rv_in = in.val;
     const double *lhs = in.lhs, *rhs = in.rhs, *lb = in.lb, *ub = in.ub, *cc = in.c;
