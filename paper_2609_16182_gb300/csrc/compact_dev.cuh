@@ -83,10 +83,20 @@ __device__ __forceinline__ void csr_count_row(const Ctx &C, const CompactCtx &K,
     }
     int32_t cnt = 0;
     double sh = 0.0;
-    for (int32_t k = beg + lane; k < end; k += W) {
-        const int32_t j = C.A.idx[k];
-        if (K.c_keep[j]) cnt++;
-        else sh = fma(C.A.val[k], C.fixv[j], sh);
+    // four entries per lane and step: their indices, then their keep flags,
+    // in flight together; the shift takes the entries in order
+    for (int32_t k0 = beg + lane; k0 < end; k0 += 4 * W) {
+        int32_t jq[4], kq[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) jq[q] = k0 + q * W < end ? C.A.idx[k0 + q * W] : 0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) kq[q] = k0 + q * W < end ? K.c_keep[jq[q]] : 1;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            if (k0 + q * W >= end) break;
+            if (kq[q]) cnt++;
+            else sh = fma(C.A.val[k0 + q * W], C.fixv[jq[q]], sh);
+        }
     }
     cnt = group_sum<W>(cnt, mask);
     sh = group_sum<W>(sh, mask);

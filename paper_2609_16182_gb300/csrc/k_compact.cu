@@ -228,11 +228,19 @@ __global__ void __launch_bounds__(kBlock) k_csr_count_long(Ctx C, CompactCtx K) 
     const bool keep = C.rkind[i] == RK_KEPT && !K.lp_dead[lp_of_row(C, i)];
     int32_t cnt = 0;
     double sh = 0.0;
-    if (keep) {
-        for (int32_t k = ch.begin + threadIdx.x; k < ch.end; k += kBlock) {
-            const int32_t j = C.A.idx[k];
-            if (K.c_keep[j]) cnt++;
-            else sh = fma(C.A.val[k], C.fixv[j], sh);
+    if (keep) {  // eight entries per thread and step in flight; the shift in entry order
+        for (int32_t k0 = ch.begin + threadIdx.x; k0 < ch.end; k0 += 8 * kBlock) {
+            int32_t jq[8], kq[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) jq[q] = k0 + q * kBlock < ch.end ? C.A.idx[k0 + q * kBlock] : 0;
+#pragma unroll
+            for (int q = 0; q < 8; q++) kq[q] = k0 + q * kBlock < ch.end ? K.c_keep[jq[q]] : 1;
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                if (k0 + q * kBlock >= ch.end) break;
+                if (kq[q]) cnt++;
+                else sh = fma(C.A.val[k0 + q * kBlock], C.fixv[jq[q]], sh);
+            }
         }
     }
     cnt = block_sum_int(cnt);
