@@ -180,9 +180,27 @@ __global__ void __launch_bounds__(kBlock) k_locks_long(Ctx C, CompactCtx K) {
 }
 
 // ------------------------------------------------------- S6 + column keep
+// With the input CSC kept (Ctx::t_orig) the columns also stay in place: a
+// column that left in an earlier round (cinv < 0) is skipped, the others
+// keep their index (c_new = j), and one that leaves now gets cinv = -1.
 __global__ void __launch_bounds__(kBlock) k_colkeep(Ctx C, CompactCtx K) {
     const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int32_t fixed = j < C.n ? colkeep_one(C, K, j) : 0;
+    int32_t fixed = 0;
+    if (j < C.n) {
+        if (C.t_orig && C.cinv[j] < 0) {
+            K.c_keep[j] = 0;
+            K.c_len[j] = 0;
+            K.contrib[j] = 0.0;
+            K.c_new[j] = -1;
+        } else {
+            fixed = colkeep_one(C, K, j);
+            if (C.t_orig) {
+                const bool kp = K.c_keep[j] != 0;
+                K.c_new[j] = kp ? j : -1;
+                if (!kp) K.cinv[j] = -1;
+            }
+        }
+    }
     block_add(fixed, &C.st->cols_fixed);
 }
 
@@ -294,6 +312,31 @@ __global__ void __launch_bounds__(kBlock) k_clen_dec_long(Ctx C, CompactCtx K) {
     for (int32_t k = ch.begin + threadIdx.x; k < ch.end; k += kBlock) atomicSub(&K.c_len[C.A.idx[k]], 1);
 }
 
+// ------------------------------------- the columns' one compaction (t_orig)
+// keep flag of each column slot: still in the LP
+__global__ void k_cols_alive(const int32_t *cinv, int32_t n, int32_t *keep) {
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) keep[j] = cinv[j] >= 0;
+}
+// the kept columns' vectors to their compacted positions; cinv then maps
+// an input column to its final index
+__global__ void k_cols_final(const Ctx C, const CompactCtx K, int32_t n, int32_t *cinv) {
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    if (!K.c_keep[j]) return;  // cinv already -1
+    const int32_t p = K.c_pos[j];
+    K.lu2[p] = C.lu[j];
+    K.c2[p] = C.c[j];
+    K.cmap2[p] = C.cmap[j];
+    if (C.lp_col) K.lp_col2[p] = C.lp_col[j];
+    cinv[C.cmap[j]] = p;
+}
+// the CSR's column indices renumbered in place
+__global__ void k_idx_renumber(int32_t *idx, int64_t nnz, const int32_t *pos) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nnz) idx[k] = pos[idx[k]];
+}
+
 // input rows / columns still in the LP, as a row kind (KEPT or not) and a
 // keep flag for the compaction of the input CSC into the result's
 __global__ void k_rows_left(const int32_t *rinv, int32_t m, uint8_t *rk) {
@@ -333,7 +376,7 @@ __global__ void __launch_bounds__(kBlock) k_rowvec(Ctx C, CompactCtx K) {
     // an unchanged row's S5 key is taken again when columns were dropped (the
     // key hashes column indices, which the compaction renumbers)
     const bool lost = K.r_len[i] != C.A.ptr[i + 1] - C.A.ptr[i];
-    K.rdirty2[p] = (C.rdnext[i] | lost) ? 1 : (K.c_pos[C.n] != C.n ? 2 : 0);
+    K.rdirty2[p] = (C.rdnext[i] | lost) ? 1 : (!C.t_orig && K.c_pos[C.n] != C.n ? 2 : 0);
     K.act2[p] = C.act[i];
     K.ninf2[p] = C.ninf[i];
     K.hrow2[p] = C.hrow[i];
@@ -342,17 +385,15 @@ __global__ void __launch_bounds__(kBlock) k_rowvec(Ctx C, CompactCtx K) {
 __global__ void __launch_bounds__(kBlock) k_colvec(Ctx C, CompactCtx K) {
     const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= C.n) return;
-    if (K.cp2 && j == C.n - 1) K.cp2[K.c_pos[C.n]] = K.c_off[C.n];
+    if (j == C.n - 1) K.cp2[K.c_pos[C.n]] = K.c_off[C.n];
     const int32_t p = K.c_pos[j];
     K.c_new[j] = K.c_keep[j] ? p : -1;
-    if (K.cinv) K.cinv[C.cmap[j]] = K.c_keep[j] ? p : -1;
     if (!K.c_keep[j]) return;
     K.lu2[p] = C.lu[j];
     K.c2[p] = C.c[j];
     K.cmap2[p] = C.cmap[j];
     if (C.lp_col) K.lp_col2[p] = C.lp_col[j];
-    if (K.cp2) K.cp2[p] = K.c_off[j];       // the compacted CSC
-    if (K.clen2) K.clen2[p] = K.c_len[j];   // the input CSC kept: entries per column
+    K.cp2[p] = K.c_off[j];
 }
 
 // empty matrices still need ptr[0] = 0
@@ -598,7 +639,8 @@ void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s) {
     const GroupGrid ga = group_grid(C.A);
     const int32_t along = C.A.cls_start[7] - C.A.cls_start[6];
     if (C.t_orig) {  // the previous counts less the removed rows' entries
-        if (C.n > 0) cudaMemcpyAsync(K.c_len, C.clen, sizeof(int32_t) * (size_t)C.n, cudaMemcpyDeviceToDevice, s);
+        if (C.n > 0 && K.c_len != C.clen)
+            cudaMemcpyAsync(K.c_len, C.clen, sizeof(int32_t) * (size_t)C.n, cudaMemcpyDeviceToDevice, s);
         if (ga.blk_start[6] > 0) (k_clen_dec_groups<<<ga.blk_start[6], kBlock, 0, s>>>(C, K, ga), note_launch());
         if (along > 0 && C.A.nchunks > 0) (k_clen_dec_long<<<C.A.nchunks, kBlock, 0, s>>>(C, K), note_launch());
     }
@@ -629,7 +671,7 @@ void launch_compact_scatter(const Ctx &C, const CompactCtx &K, int32_t nnz, cuda
     (k_zero_ptr<<<1, 1, 0, s>>>(K.rp2), note_launch());
     if (!C.t_orig) (k_zero_ptr<<<1, 1, 0, s>>>(K.cp2), note_launch());
     if (C.m > 0) (k_rowvec<<<blocks_for(C.m, kBlock), kBlock, 0, s>>>(C, K), note_launch());
-    if (C.n > 0) (k_colvec<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C, K), note_launch());
+    if (C.n > 0 && !C.t_orig) (k_colvec<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C, K), note_launch());
     const int32_t ntiles = (int32_t)(((int64_t)nnz + kFlatTile - 1) / kFlatTile);
     if (ntiles > 0) {
         FlatArgs fa{C.A.ptr, C.A.idx, C.A.val, nnz, C.m, ntiles, K.r_keep, K.r_off, K.r_len, K.r_ch0,
@@ -670,6 +712,15 @@ void launch_csc_from_input_scatter(const Ctx &C, const CompactCtx &K, int64_t nn
                     K.cht_off, K.cht_cnt, C.rinv, K.tile_t, idx, val};
         (k_scatter_flat<<<ntiles, kBlock, 0, s>>>(ft), note_launch());
     }
+}
+
+void launch_cols_alive(const int32_t *cinv, int32_t n, int32_t *keep, cudaStream_t s) {
+    if (n > 0) (k_cols_alive<<<blocks_for(n, kBlock), kBlock, 0, s>>>(cinv, n, keep), note_launch());
+}
+void launch_cols_final(const Ctx &C, const CompactCtx &K, int32_t n, int32_t *cinv, int32_t *idx, int64_t nnz,
+                       cudaStream_t s) {
+    if (n > 0) (k_cols_final<<<blocks_for(n, kBlock), kBlock, 0, s>>>(C, K, n, cinv), note_launch());
+    if (nnz > 0) (k_idx_renumber<<<blocks_for(nnz, kBlock), kBlock, 0, s>>>(idx, nnz, K.c_pos), note_launch());
 }
 
 void launch_rows_left(const int32_t *rinv, int32_t m, uint8_t *rk, cudaStream_t s) {

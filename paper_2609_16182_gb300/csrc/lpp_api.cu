@@ -449,7 +449,7 @@ bool batch_fused(Engine &E, const std::vector<Member> &mem, int32_t count, lpp_r
     F.base.t_orig = 0;  // each block compacts its LP's CSC itself
     F.base.rinv = F.base.cinv = F.base.clen = nullptr;
     F.K = E.K;
-    F.K.rinv = F.K.cinv = F.K.clen2 = nullptr;
+    F.K.rinv = F.K.cinv = nullptr;
     for (int b = 0; b < 2; b++) {
         F.frp[b] = P.alloc<int32_t>((size_t)m0 + count + 1);
         F.ftp[b] = P.alloc<int32_t>((size_t)n0 + count + 1);

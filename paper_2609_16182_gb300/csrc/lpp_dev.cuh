@@ -91,10 +91,11 @@ struct Ctx {
     double2 *lu;
     double *c;                      // written only by S5d (one product per column and round)
     const int32_t *cmap, *lp_col;
-    // t_orig: the CSC T is the input's A^T, never compacted (no step that
-    // reads columns' entries is on).  rinv / cinv map an input row / column
-    // to its current index (-1 once it left); clen: entries per current
-    // column in the current rows.
+    // t_orig: the CSC T is the input's A^T, never compacted, and the columns
+    // stay in their input slots (no step that reads columns' entries is on).
+    // rinv maps an input row to its current index, cinv an input column to
+    // its slot (-1 once either left); clen: entries per column in the
+    // current rows.
     const int32_t *rinv, *cinv, *clen;
     int32_t t_orig;
     // rows whose activities must be recomputed this round (1) and the flags
@@ -193,9 +194,9 @@ struct CompactCtx {
     double2 *act2;                             // carried results of clean rows
     int2 *ninf2;
     unsigned long long *hrow2;
-    // CSC kept in the input's numbering (Ctx::t_orig): the input-to-current
-    // maps, updated in place, and the next entries-per-column counts
-    int32_t *rinv, *cinv, *clen2;
+    // CSC kept in the input's numbering and columns kept in place
+    // (Ctx::t_orig): the input-to-current maps, updated in place
+    int32_t *rinv, *cinv;
 };
 
 // ------------------------------------------------------------------ helpers

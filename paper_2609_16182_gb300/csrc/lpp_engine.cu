@@ -195,11 +195,12 @@ __global__ void k_csc_sizes(const CompactCtx K, int32_t n, DevStatus *st) {
     st->nnz_new_t = K.c_off[n];
 }
 
-__global__ void k_sizes(const CompactCtx K, int32_t m, int32_t n, DevStatus *st) {
+// cols_in_place: the column slots stay (n), the CSC is not compacted
+__global__ void k_sizes(const CompactCtx K, int32_t m, int32_t n, int32_t cols_in_place, DevStatus *st) {
     st->m_new = K.r_pos[m];
     st->nnz_new = K.r_off[m];
-    st->n_new = K.c_pos[n];
-    st->nnz_new_t = K.c_off[n];
+    st->n_new = cols_in_place ? n : K.c_pos[n];
+    st->nnz_new_t = cols_in_place ? K.r_off[m] : K.c_off[n];
 }
 
 const char *kFamNames[F_NUM] = {"prop",     "colfin",   "s5",     "compact_count", "scan", "compact_scatter",
@@ -318,8 +319,7 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
     if (t_orig) {
         rinv = pool.alloc<int32_t>(m0);
         cinv = pool.alloc<int32_t>(n0);
-        clive[0] = pool.alloc<int32_t>(n0);
-        clive[1] = pool.alloc<int32_t>(n0);
+        clive = pool.alloc<int32_t>(n0);
         rleft = pool.alloc<uint8_t>(m0);
     }
     rkind = pool.alloc<uint8_t>(m0);
@@ -599,7 +599,7 @@ void Engine::prepare() {
     if (t_orig) {
         iota(rinv, m0, 0, s);
         iota(cinv, n0, 0, s);
-        ptr_diff(tp[0], n0, clive[0], s);
+        ptr_diff(tp[0], n0, clive, s);
     }
     fill_u64(cand_l, n0, kEncNegInf, s);
     fill_u64(cand_u, n0, kEncPosInf, s);
@@ -714,7 +714,7 @@ Ctx Engine::ctx(int32_t round) const {
     C.t_orig = t_orig ? 1 : 0;
     C.rinv = rinv;
     C.cinv = cinv;
-    C.clen = t_orig ? clive[cur] : nullptr;
+    C.clen = t_orig ? clive : nullptr;
     C.act = act[cur];
     C.ninf = ninf[cur];
     C.rdirty = rdirty[cur];
@@ -791,7 +791,6 @@ void Engine::compact(int32_t round) {
     K.cv2 = t_orig ? nullptr : tv[nx];
     K.rinv = t_orig ? rinv : nullptr;
     K.cinv = t_orig ? cinv : nullptr;
-    K.clen2 = t_orig ? clive[nx] : nullptr;
     K.L2 = L[nx];
     K.U2 = U[nx];
     K.rmap2 = rmap[nx];
@@ -805,21 +804,33 @@ void Engine::compact(int32_t round) {
     K.ninf2 = ninf[nx];
     K.hrow2 = hrow[nx];
     const Ctx C = ctx(round);
+    // columns kept in place (t_orig): their counts are updated in place, no
+    // column scan, no column vectors moved; the slots of the columns that
+    // leave are marked (cinv) and dropped once, at the end
+    int32_t *own_clen = K.c_len;
+    if (t_orig) K.c_len = clive;
     tbegin(F_COUNT, 4.0 * nnz * 2 + 8.0 * nnz + 24.0 * m + 40.0 * n);
     launch_compact_counts(C, K, s);
     tend();
-    tbegin(F_SCAN, 16.0 * (m + n) * 2);
+    tbegin(F_SCAN, 16.0 * (m + (t_orig ? 0 : n)) * 2);
     scan_excl2(K.r_keep, K.r_len, K.r_pos, K.r_off, m, scan_tmp, s);
-    scan_excl2(K.c_keep, K.c_len, K.c_pos, K.c_off, n, scan_tmp, s);
+    if (!t_orig) scan_excl2(K.c_keep, K.c_len, K.c_pos, K.c_off, n, scan_tmp, s);
     tend();
     launch_offset(C, K, s);
-    (k_sizes<<<1, 1, 0, s>>>(K, m, n, st), note_launch());
+    (k_sizes<<<1, 1, 0, s>>>(K, m, n, t_orig ? 1 : 0, st), note_launch());
     tbegin(F_SCATTER, 24.0 * nnz * 2 + 48.0 * (m + n));
     launch_compact_scatter(C, K, (int32_t)nnz, s);
     tend();
     LPP_CUDA(cudaGetLastError());
+    K.c_len = own_clen;
     // the next buffers become current; sizes and schedules are read back at
     // the end of the round (one host sync per round)
+    if (t_orig) {  // the column vectors stay where they are: they move with cur
+        std::swap(lu[cur], lu[nx]);
+        std::swap(c[cur], c[nx]);
+        std::swap(cmap[cur], cmap[nx]);
+        std::swap(lpcol[cur], lpcol[nx]);
+    }
     cur = nx;
     tbegin(F_SCHED, 8.0 * (m + n));
     schedule_current();
@@ -1147,12 +1158,43 @@ void Engine::run() {
             }
         }
     }
-    if (t_orig) finish_csc();
+    if (t_orig) {
+        finish_cols();
+        finish_csc();
+    }
     float lms = 0.f;
     LPP_CUDA(cudaEventRecord(eend, s));
     LPP_CUDA(cudaEventSynchronize(eend));
     LPP_CUDA(cudaEventElapsedTime(&lms, eloop, eend));
     loop_ms = lms;
+}
+
+// The columns' one compaction when the rounds kept them in place: the
+// slots still in the LP, in order, into the other buffers (which then become
+// the current ones), the CSR's column indices renumbered, cinv to the final
+// indices.
+void Engine::finish_cols() {
+    tbegin(F_SCATTER, 4.0 * nnz * 2 + 72.0 * n);
+    launch_cols_alive(cinv, n, K.c_keep, s);
+    scan_excl(K.c_keep, K.c_pos, n, scan_tmp, s);
+    const int nx = cur ^ 1;
+    K.lu2 = lu[nx];
+    K.c2 = c[nx];
+    K.cmap2 = cmap[nx];
+    K.lp_col2 = lpcol[nx];
+    const Ctx C = ctx(rounds);
+    launch_cols_final(C, K, n, cinv, ci[cur], nnz, s);
+    (k_csc_sizes<<<1, 1, 0, s>>>(K, n, st), note_launch());  // n_new: the columns left
+    LPP_CUDA(cudaGetLastError());
+    tend();
+    read_status();
+    const int32_t n_new = st_h->n_new;
+    if (n_new < 0 || n_new > n) throw StatusError(LPP_ERR_CUDA, "internal: column compaction size");
+    std::swap(lu[cur], lu[nx]);
+    std::swap(c[cur], c[nx]);
+    std::swap(cmap[cur], cmap[nx]);
+    std::swap(lpcol[cur], lpcol[nx]);
+    n = n_new;
 }
 
 // The result's CSC when the rounds kept the input's: one compaction of the

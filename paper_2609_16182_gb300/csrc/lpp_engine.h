@@ -135,15 +135,17 @@ struct Engine {
     double2 *ch_act;
     int2 *ch_ninf;
     int32_t tcap_max;
-    // The CSC kept as the input's A^T instead of compacted each round (set
-    // by setup when lazy_req and no step that reads columns' entries is on):
-    // input-to-current row / column maps, entries per current column in the
-    // current rows (double-buffered like the columns), and at the end the
-    // input rows still in the LP (the result's CSC is compacted once).
+    // The CSC kept as the input's A^T and the columns kept in place instead
+    // of compacted each round (set by setup when lazy_req and no step that
+    // reads columns' entries is on): input-to-current row map, column map
+    // (the slot itself while the column is in the LP, -1 once it left),
+    // entries per column in the current rows, and at the end the input rows
+    // still in the LP (columns and CSC are compacted once, at the end).
     bool lazy_req = false, t_orig = false, t_fixed = false;
-    int32_t *rinv = nullptr, *cinv = nullptr, *clive[2] = {nullptr, nullptr};
+    int32_t *rinv = nullptr, *cinv = nullptr, *clive = nullptr;
     uint8_t *rleft = nullptr;
-    void finish_csc();  // the result's CSC from the input's (t_orig)
+    void finish_cols();  // the columns' one compaction (t_orig)
+    void finish_csc();   // the result's CSC from the input's (t_orig)
     // compaction work
     CompactCtx K;
     int32_t *scan_tmp;

@@ -206,6 +206,12 @@ void launch_compact_scatter(const Ctx &C, const CompactCtx &K, int32_t nnz, cuda
 // the result's CSC from the input CSC when it was not compacted (Ctx::t_orig):
 // counts and keep flags, then (after the caller's column scan) the scatter
 void launch_rows_left(const int32_t *rinv, int32_t m, uint8_t *rk, cudaStream_t s);
+// columns kept in place (Ctx::t_orig): their keep flags, then (after the
+// caller's scan of them into K.c_pos) their vectors to K.lu2 / c2 / cmap2 /
+// lp_col2, cinv to final indices and the CSR's column indices renumbered
+void launch_cols_alive(const int32_t *cinv, int32_t n, int32_t *keep, cudaStream_t s);
+void launch_cols_final(const Ctx &C, const CompactCtx &K, int32_t n, int32_t *cinv, int32_t *idx, int64_t nnz,
+                       cudaStream_t s);
 void launch_csc_from_input_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s);
 void launch_csc_from_input_scatter(const Ctx &C, const CompactCtx &K, int64_t nnz, int32_t *ptr, int32_t *idx,
                                    double *val, cudaStream_t s);
