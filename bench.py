@@ -229,8 +229,7 @@ def batched_leg(lpp, synth, torch, dev, stream, count=4096):
     # warm-up at full size (memory pool); the first calls also let the
     # library time each launch geometry of its persistent kernel once
     for _ in range(8):
-        for r in lpp.presolve_batch(packed, o):
-            r.close()
+        lpp.presolve_batch(packed, o).close()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = 5
@@ -238,20 +237,17 @@ def batched_leg(lpp, synth, torch, dev, stream, count=4096):
     for q in range(reps):
         res = lpp.presolve_batch(packed, o)
         if q < reps - 1:
-            for r in res:
-                r.close()
+            res.close()  # every handle of the batch in one call
     e1.record(stream)
     torch.cuda.synchronize(dev)
     batch_ms = e0.elapsed_time(e1) / reps
     kernel_ms = res[0].info.presolve_ms
     keys = [(r.status, r.info.m_red, r.info.n_red, r.info.nnz_red, r.rounds) for r in res]
     recs = [(r.row_kind.copy(), r.col_kind.copy()) for r in res]
-    for r in res:
-        r.close()
+    res.close()
     # the per-round launches over the arena, for comparison
     o_arena = lpp.opts(stream=stream.cuda_stream, batch_persistent=0)
-    for r in lpp.presolve_batch(packed, o_arena):
-        r.close()
+    lpp.presolve_batch(packed, o_arena).close()
     torch.cuda.synchronize(dev)
     e0.record(stream)
     res_a = lpp.presolve_batch(packed, o_arena)
@@ -260,8 +256,7 @@ def batched_leg(lpp, synth, torch, dev, stream, count=4096):
     arena_ms = e0.elapsed_time(e1)
     same_arena = all(np.array_equal(r.row_kind, a) and np.array_equal(r.col_kind, b)
                      for r, (a, b) in zip(res_a, recs))
-    for r in res_a:
-        r.close()
+    res_a.close()
     e0.record(stream)
     plain = []
     for x in d:
@@ -542,8 +537,7 @@ def profile_batch(args):
     for _ in range(args.warmup + args.steps):
         res = lpp.presolve_batch(packed, o)
         kernel_ms.append(res[0].info.presolve_ms)
-        for r in res:
-            r.close()
+        res.close()
     torch.cuda.synchronize(dev)
     print(json.dumps({"profile_batch": True, "calls": args.warmup + args.steps, "kernel_ms": kernel_ms}), flush=True)
 

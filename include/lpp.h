@@ -264,6 +264,10 @@ lpp_status lpp_postsolve_primal(const lpp_postsolve *rec, const double *x_red, d
 
 void lpp_free_reduced(lpp_reduced *red);
 void lpp_free_postsolve(lpp_postsolve *rec);
+/* Frees reds[k] and recs[k] for k < count (NULL entries are skipped), as
+ * lpp_free_reduced / lpp_free_postsolve would one by one: the handles of a
+ * batch in one call. */
+void lpp_free_results(lpp_reduced *const *reds, lpp_postsolve *const *recs, int32_t count);
 const char *lpp_last_error(void);
 
 /* Batched presolve: `count` independent LPs (all host or all device inputs)

@@ -1055,4 +1055,11 @@ void lpp_free_reduced(lpp_reduced *R) {
 
 void lpp_free_postsolve(lpp_postsolve *P) { delete P; }
 
+void lpp_free_results(lpp_reduced *const *reds, lpp_postsolve *const *recs, int32_t count) {
+    for (int32_t k = 0; k < count; k++) {
+        if (reds) lpp_free_reduced(reds[k]);
+        if (recs) lpp_free_postsolve(recs[k]);
+    }
+}
+
 }  // extern "C"

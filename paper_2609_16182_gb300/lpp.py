@@ -68,6 +68,7 @@ class ServerStats(C.Structure):
 SYMBOLS = ["lpp_opts_default", "lpp_presolve", "lpp_reduced_view", "lpp_reduced_csc", "lpp_reduced_maps",
            "lpp_result_info", "lpp_result_rows", "lpp_result_cols", "lpp_result_activity", "lpp_result_rounds",
            "lpp_result_kernels", "lpp_result_merges", "lpp_result_substitutions", "lpp_postsolve_primal", "lpp_free_reduced", "lpp_free_postsolve",
+           "lpp_free_results",
            "lpp_last_error", "lpp_presolve_batch", "lpp_server_create", "lpp_server_submit", "lpp_server_take",
            "lpp_server_stats_get", "lpp_server_destroy", "lpp_row_activity_noalloc"]
 
@@ -94,6 +95,8 @@ def load():
     L.lpp_presolve.argtypes = [C.POINTER(LpStruct), C.POINTER(Opts), PP, PP]
     L.lpp_presolve_batch.argtypes = [C.POINTER(LpStruct), C.c_int32, C.POINTER(Opts), PP, PP,
                                      C.POINTER(C.c_int32)]
+    L.lpp_free_results.argtypes = [PP, PP, C.c_int32]
+    L.lpp_free_results.restype = None
     L.lpp_reduced_view.argtypes = [P, C.POINTER(LpStruct), C.c_int32]
     L.lpp_reduced_csc.argtypes = [P, PP, PP, PP, C.c_int32]
     L.lpp_reduced_maps.argtypes = [P, PP, PP, C.c_int32]
@@ -120,8 +123,8 @@ def load():
     L.lpp_server_destroy.argtypes = [P]
     L.lpp_server_destroy.restype = None
     for name in SYMBOLS:
-        if name not in ("lpp_opts_default", "lpp_free_reduced", "lpp_free_postsolve", "lpp_last_error",
-                        "lpp_server_destroy"):
+        if name not in ("lpp_opts_default", "lpp_free_reduced", "lpp_free_postsolve", "lpp_free_results",
+                        "lpp_last_error", "lpp_server_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -211,25 +214,34 @@ class Reduced:
 
 
 class Result:
-    """Owns the C handles of one presolve; frees them when collected."""
+    """Owns the C handles of one presolve; frees them when collected.  The
+    summary (lpp_result_info) is read on first use."""
 
-    def __init__(self, red, rec):
+    def __init__(self, red, rec, batch=None, slot=-1):
         self._red = red
         self._rec = rec
-        L = load()
-        info = Info()
-        _check(L.lpp_result_info(rec, C.byref(info)))
-        self.info = info
-        self.status = info.status
-        self.where = info.where
-        self.index = info.index
-        self.round = info.round
-        self.rounds = info.rounds
-        self.s5_left = info.s5_left
+        self._batch = batch  # a BatchResults whose handle slot this result owns
+        self._slot = slot
+        self._info = None
         self._rounds_data = None
         self._kernels = None
         self._reduced = None
         self._records = None
+
+    @property
+    def info(self):
+        if self._info is None:
+            info = Info()
+            _check(load().lpp_result_info(self._rec, C.byref(info)))
+            self._info = info
+        return self._info
+
+    status = property(lambda self: self.info.status)
+    where = property(lambda self: self.info.where)
+    index = property(lambda self: self.info.index)
+    round = property(lambda self: self.info.round)
+    rounds = property(lambda self: self.info.rounds)
+    s5_left = property(lambda self: self.info.s5_left)
 
     _RECORD_FIELDS = ("row_kind", "row_round", "row_aux", "row_val", "col_kind", "col_round", "col_val", "col_lb",
                       "col_ub", "act_min", "act_max", "ninf_min", "ninf_max", "col_aux", "col_pass", "col_mrg",
@@ -362,10 +374,71 @@ class Result:
                 L.lpp_free_postsolve(self._rec)
         self._red = None
         self._rec = None
+        if self._batch is not None:
+            self._batch._forget(self._slot)
+            self._batch = None
 
     def __del__(self):
         try:
             self.close()
+        except Exception:
+            pass
+
+
+class BatchResults:
+    """The results of one lpp_presolve_batch call, a sequence of Result made
+    on first access; close() frees every handle not yet freed in one call."""
+
+    def __init__(self, reds, recs, count):
+        self._reds = reds
+        self._recs = recs
+        self._count = count
+        self._items = [None] * count
+
+    def __len__(self):
+        return self._count
+
+    def __getitem__(self, k):
+        if isinstance(k, slice):
+            return [self[q] for q in range(*k.indices(self._count))]
+        if k < 0:
+            k += self._count
+        if not 0 <= k < self._count:
+            raise IndexError(k)
+        r = self._items[k]
+        if r is None:
+            if not self._recs[k]:
+                raise ValueError("result already freed")
+            r = Result(self._reds[k], self._recs[k], self, k)
+            self._items[k] = r
+        return r
+
+    def __iter__(self):
+        for k in range(self._count):
+            yield self[k]
+
+    def _forget(self, k):
+        self._reds[k] = None
+        self._recs[k] = None
+
+    def close(self):
+        """Frees every result of the batch (those handed out become unusable)."""
+        L = _lib
+        for r in self._items:
+            if r is not None:
+                r._red = r._rec = None
+                r._batch = None
+        if L is not None and self._count:
+            L.lpp_free_results(self._reds, self._recs, self._count)
+        for k in range(self._count):
+            self._reds[k] = None
+            self._recs[k] = None
+        self._items = [None] * self._count
+
+    def __del__(self):
+        try:
+            if any(self._recs[k] for k in range(self._count)):
+                self.close()
         except Exception:
             pass
 
@@ -401,9 +474,9 @@ def pack_lps(lps) -> PackedLPs:
     return PackedLPs(lps)
 
 
-def presolve_batch(lps, options: Opts | None = None, **kw) -> list[Result]:
+def presolve_batch(lps, options: Opts | None = None, **kw) -> BatchResults:
     """lpp_presolve_batch on a list of LPs (all host or all device), or on a
-    PackedLPs built by pack_lps."""
+    PackedLPs built by pack_lps; one Result per LP, in order."""
     L = load()
     o = options if options is not None else opts(**kw)
     packed = lps if isinstance(lps, PackedLPs) else PackedLPs(lps)
@@ -412,7 +485,7 @@ def presolve_batch(lps, options: Opts | None = None, **kw) -> list[Result]:
     recs = (C.c_void_p * max(cnt, 1))()
     per = (C.c_int32 * max(cnt, 1))()
     _check(L.lpp_presolve_batch(packed.arr, cnt, C.byref(o), reds, recs, per))
-    return [Result(reds[k], recs[k]) for k in range(cnt)]
+    return BatchResults(reds, recs, cnt)
 
 
 class Server:

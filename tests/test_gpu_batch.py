@@ -150,3 +150,22 @@ def test_persistent_batch_with_empty_and_degenerate_members():
         same_result(f, solo)
         same_result(a, solo)
         compare(f, oracle.presolve(lp), lp)
+
+
+def test_batch_results_free_each_or_all():
+    """BatchResults: results made on first access (the same object again),
+    slices and negative indices, a result closed on its own, then every other
+    handle freed by one lpp_free_results call."""
+    lps = synth.batch_mix(31, count=6, m_lo=50, m_hi=300)
+    res = lpp.presolve_batch(lps)
+    assert len(res) == 6 and res[1] is res[1] and len(res[2:5]) == 3 and res[-1] is res[5]
+    for r, lp in zip(res, lps):
+        same_result(r, lpp.presolve(lp))
+    res[0].close()
+    assert not res._recs[0] and res._recs[1]
+    r3 = res[3]
+    res.close()
+    assert all(not res._recs[k] for k in range(len(res)))
+    assert r3._rec is None  # handed out before the close: now empty
+    with pytest.raises(ValueError):
+        res[2]
