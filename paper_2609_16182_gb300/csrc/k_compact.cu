@@ -187,11 +187,11 @@ __global__ void __launch_bounds__(kBlock) k_colkeep(Ctx C, CompactCtx K) {
     const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     int32_t fixed = 0;
     if (j < C.n) {
-        if (C.t_orig && C.cinv[j] < 0) {
-            K.c_keep[j] = 0;
-            K.c_len[j] = 0;
-            K.contrib[j] = 0.0;
-            K.c_new[j] = -1;
+        if (C.t_orig && (C.cinv[j] < 0 || (C.ckind[j] == CK_KEPT && K.c_len[j] > 0 && !K.lp_dead[lp_of_col(C, j)]))) {
+            // columns in place: one that left earlier keeps the flags it got
+            // then (its contribution was consumed by the objective sum), and a
+            // kept column with entries that S4 did not fix stays as it is
+            // (no S6 test applies to it, its contribution is zero)
         } else {
             fixed = colkeep_one(C, K, j);
             if (C.t_orig) {
@@ -590,12 +590,18 @@ __global__ void __launch_bounds__(kBlock) k_scatter_flat(FlatArgs F) {
 
 // ---------------------------------------------------------- objective constant
 // one LP: tiles of kScanTile columns summed in a fixed order, then the tiles
-__global__ void __launch_bounds__(kBlock) k_offset_tiles(const double *contrib, int32_t n, double *part) {
+// the contributions are consumed: reset to zero once read (a column whose
+// flags are not recomputed in a later round then contributes nothing)
+__global__ void __launch_bounds__(kBlock) k_offset_tiles(double *contrib, int32_t n, double *part) {
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     double s = 0.0;
     for (int t = threadIdx.x; t < kScanTile; t += kBlock) {
         const int64_t j = base + t;
-        if (j < n) s += contrib[j];
+        if (j < n) {
+            const double v = contrib[j];
+            s += v;
+            if (v != 0.0) contrib[j] = 0.0;
+        }
     }
     s = block_sum_dbl(s);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
@@ -615,13 +621,17 @@ __global__ void k_lp_ranges(const int32_t *lp_col, int32_t n, int32_t *first, in
     if (j == 0 || lp_col[j - 1] != lp) first[lp] = j;
     if (j == n - 1 || lp_col[j + 1] != lp) last[lp] = j + 1;
 }
-__global__ void k_offset_lps(const double *contrib, const int32_t *first, const int32_t *last, int32_t nlp,
+__global__ void k_offset_lps(double *contrib, const int32_t *first, const int32_t *last, int32_t nlp,
                              double *offset) {
     const int32_t lp = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (lp >= nlp) return;
     double s = 0.0;
-    for (int32_t j = first[lp] + lane; j < last[lp]; j += 32) s += contrib[j];
+    for (int32_t j = first[lp] + lane; j < last[lp]; j += 32) {  // consumed as in k_offset_tiles
+        const double v = contrib[j];
+        s += v;
+        if (v != 0.0) contrib[j] = 0.0;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) offset[lp] += s;

@@ -600,6 +600,10 @@ void Engine::prepare() {
         iota(rinv, m0, 0, s);
         iota(cinv, n0, 0, s);
         ptr_diff(tp[0], n0, clive, s);
+        // every column starts kept at its own slot, with no contribution
+        fill_i32(K.c_keep, n0, 1, s);
+        iota(K.c_new, n0, 0, s);
+        LPP_CUDA(cudaMemsetAsync(K.contrib, 0, sizeof(double) * (size_t)std::max(n0, 1), s));
     }
     fill_u64(cand_l, n0, kEncNegInf, s);
     fill_u64(cand_u, n0, kEncPosInf, s);
