@@ -368,6 +368,8 @@ class Result:
     def close(self):
         L = _lib
         if L is not None:
+            if self._rec and self._info is None:  # the summary stays readable after close
+                self.info
             if self._red:
                 L.lpp_free_reduced(self._red)
             if self._rec:
@@ -426,6 +428,8 @@ class BatchResults:
         L = _lib
         for r in self._items:
             if r is not None:
+                if r._rec and r._info is None:  # handed out: its summary stays readable
+                    r.info
                 r._red = r._rec = None
                 r._batch = None
         if L is not None and self._count:
