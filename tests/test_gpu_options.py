@@ -95,3 +95,38 @@ def test_round_reduced_only_by_a_later_parallel_pass(cap):
     g, o = both(lp, par_max_iter=cap)
     assert o.row_kind[2] == lpp.ROW_PARALLEL and o.row_round[2] == 2
     compare(g, o, lp)
+
+
+# --------------------------------- input CSC and columns kept vs compacted
+# With every opt-in step off, the rounds keep the input's CSC and leave the
+# columns in their slots, compacting both once at the end.  With parallel
+# columns on, both are compacted every round.  When that step merges nothing
+# the two runs must agree bit for bit: every record, the reduced CSR and CSC,
+# the maps, the bounds, the activities and the per-round counters.
+
+def same_everything(a, b):
+    assert (a.status, a.where, a.index, a.round, a.rounds, a.s5_left) == \
+           (b.status, b.where, b.index, b.round, b.rounds, b.s5_left)
+    for f in ("row_kind", "row_round", "row_aux", "row_val", "col_kind", "col_round", "col_val", "col_lb", "col_ub",
+              "act_min", "act_max", "ninf_min", "ninf_max", "round_nnz", "round_rows_removed", "round_cols_fixed",
+              "round_bounds_changed"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f), err_msg=f)
+    ra, rb = a.reduced(), b.reduced()
+    for f in ("row_ptr", "col_idx", "val", "c", "lhs", "rhs", "lb", "ub", "row_map", "col_map", "csc_ptr", "csc_idx",
+              "csc_val"):
+        np.testing.assert_array_equal(getattr(ra, f), getattr(rb, f), err_msg=f)
+    assert ra.obj_offset == pytest.approx(rb.obj_offset, rel=1e-12, abs=1e-12)
+
+
+@pytest.mark.parametrize("make_lp", [lambda: synth.mix(11), lambda: synth.mix(12), lambda: synth.tiny(13),
+                                     lambda: synth.late_parallel(3),
+                                     lambda: synth.skewed(5, m=30_000, n=45_000, target_nnz=300_000,
+                                                          row_cap=8_000)],
+                         ids=["mix11", "mix12", "tiny13", "late_parallel3", "skewed30k"])
+def test_columns_kept_in_place_equal_per_round_compaction(make_lp):
+    lp = make_lp()
+    kept = lpp.presolve(lp)
+    eager = lpp.presolve(lp, parallel_cols=1)
+    if np.any(eager.col_kind == lpp.COL_PARALLEL):
+        pytest.skip("the parallel-column step merged columns: the runs differ by design")
+    same_everything(kept, eager)
