@@ -55,7 +55,7 @@ __device__ __forceinline__ int32_t colkeep_one(const Ctx &C, const CompactCtx &K
             C.rec_ck[o] = CK_EMPTY;
             C.rec_cr[o] = lp_round(C, lp);
             C.rec_cv[o] = v;
-            C.lp_changed[lp] = 1;
+            mark_lp_changed(C, lp);
             fixed = 1;
         }
     }

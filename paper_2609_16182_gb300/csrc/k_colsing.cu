@@ -212,7 +212,7 @@ __device__ __forceinline__ void s5d_record(const Ctx &C, int32_t i, int32_t j, d
     C.rec_ck[oj] = CK_SUBST;
     C.rec_cr[oj] = lp_round(C, lp);
     C.rec_cv[oj] = b / a;
-    C.lp_changed[lp] = 1;
+    mark_lp_changed(C, lp);
 }
 
 // short eligible rows: applied when first in each of their columns

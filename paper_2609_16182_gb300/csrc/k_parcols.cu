@@ -373,7 +373,7 @@ __device__ int32_t s5c_group_warp(const Ctx &C, const int32_t *cols, const Mem *
         __syncwarp();
         if (nm > 0 && lane == 0) {
             C.lu[L.k] = y;
-            C.lp_changed[lp_of_col(C, L.k)] = 1;
+            mark_lp_changed(C, lp_of_col(C, L.k));
         }
         live -= nm;
         merged += nm;
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(kLargeThreads) k_s5c_large(Ctx C, const int32_
                 }
                 if (lane == 0) {
                     C.lu[L.k] = y;
-                    C.lp_changed[lp_of_col(C, L.k)] = 1;
+                    mark_lp_changed(C, lp_of_col(C, L.k));
                 }
             }
             __syncthreads();

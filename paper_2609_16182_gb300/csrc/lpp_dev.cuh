@@ -319,6 +319,12 @@ __device__ __forceinline__ int32_t lp_of_col(const Ctx &C, int32_t j) { return C
 __device__ __forceinline__ int32_t lp_round(const Ctx &C, int32_t lp) {
     return C.lp_round0 ? C.round - C.lp_round0[lp] + 1 : C.round;
 }
+// LP lp changed this round.  The flag is stored only while it reads 0:
+// nearly every row and column of a single-LP arena sets the same byte, and
+// repeated stores to one address serialise in L2.
+__device__ __forceinline__ void mark_lp_changed(const Ctx &C, int32_t lp) {
+    if (!C.lp_changed[lp]) C.lp_changed[lp] = 1;  // a stale 0 only repeats the store
+}
 
 // Which class / block-in-class a block of a group launch serves.
 struct GroupGrid {

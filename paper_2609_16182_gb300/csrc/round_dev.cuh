@@ -340,7 +340,7 @@ __device__ __forceinline__ int32_t finish_row(const Ctx &C, int32_t i, int32_t b
     const int32_t o = C.rmap[i];
     C.rec_rk[o] = kind;
     C.rec_rr[o] = lp_round(C, lp);
-    C.lp_changed[lp] = 1;
+    mark_lp_changed(C, lp);
     if (kind == RK_SINGLETON) {
         // L <= a x_j <= U becomes a bound on x_j, always applied (no threshold)
         sa = C.A.val[beg];
@@ -518,7 +518,7 @@ __device__ __forceinline__ void colfin_one(const Ctx &C, int32_t j, bool full, i
                 C.lu[j] = make_double2(nl, nu);
                 changed++;
                 chg = 1;
-                C.lp_changed[lp] = 1;
+                mark_lp_changed(C, lp);
             }
             if (nl == nu) {
                 kind = CK_FIXED;
@@ -528,7 +528,7 @@ __device__ __forceinline__ void colfin_one(const Ctx &C, int32_t j, bool full, i
                 C.rec_ck[o] = CK_FIXED;
                 C.rec_cr[o] = lp_round(C, lp);
                 C.rec_cv[o] = nl;
-                C.lp_changed[lp] = 1;
+                mark_lp_changed(C, lp);
             }
         }
     }
@@ -579,7 +579,7 @@ __device__ __forceinline__ void s5_accept(const Ctx &C, int32_t i, int32_t li, d
     C.rec_rr[o] = lp_round(C, lp);
     C.rec_ra[o] = C.rmap[li];
     C.rec_rv[o] = lam;
-    C.lp_changed[lp] = 1;
+    mark_lp_changed(C, lp);
     const double Lj = C.L[i], Uj = C.U[i];
     double lo, hi;
     if (!is_neg(lam)) {
