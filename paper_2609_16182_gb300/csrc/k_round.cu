@@ -55,8 +55,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_prop_groups(Ctx C, GroupGrid g) {
     tq_flush(C, tq, q);
     cq_flush(C, q);
     block_add(removed, &C.st->rows_removed);
-    block_add(evaluated, &C.st->nnz_eval);
-    block_add(tested, &C.st->sides_tested);
+    if (C.count_work) {  // statistics of a timed run only: each block_add is two block barriers
+        block_add(evaluated, &C.st->nnz_eval);
+        block_add(tested, &C.st->sides_tested);
+    }
 }
 
 // fixed-order block reduction (warp butterflies, then warps in order)

@@ -160,6 +160,7 @@ struct Ctx {
     double feas_tol, bound_tol, max_implied, par_tol;
     int32_t dual;
     int32_t dualfix;                // S6 by locks (opts.dual_fixing)
+    int32_t count_work;             // the activity kernels count evaluated nonzeros and tested sides (timing)
 };
 
 // Compaction work (S6, S7) beyond Ctx.

@@ -782,6 +782,7 @@ Ctx Engine::ctx(int32_t round) const {
     C.par_tol = o.par_tol;
     C.dual = o.dual_reductions;
     C.dualfix = o.dual_fixing;
+    C.count_work = o.timing ? 1 : 0;
     return C;
 }
 
