@@ -126,6 +126,7 @@ __device__ void set_ctx(BlockState &S, const FusedArgs &F, const FusedLP &P) {
     C.n = S.n;
     C.nlp = 1;
     C.round = S.round;
+    C.list_touched = S.round > 1 ? 1 : 0;  // round 1's S3' checks every column
     C.L = F.L[b];
     C.U = F.U[b];
     C.rmap = F.rmap[b];

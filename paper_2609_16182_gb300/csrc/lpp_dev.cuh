@@ -161,6 +161,7 @@ struct Ctx {
     int32_t dual;
     int32_t dualfix;                // S6 by locks (opts.dual_fixing)
     int32_t count_work;             // the activity kernels count evaluated nonzeros and tested sides (timing)
+    int32_t list_touched;           // S3' runs on the listed columns (not on all of them): list them
 };
 
 // Compaction work (S6, S7) beyond Ctx.

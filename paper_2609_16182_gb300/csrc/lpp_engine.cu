@@ -783,6 +783,7 @@ Ctx Engine::ctx(int32_t round) const {
     C.dual = o.dual_reductions;
     C.dualfix = o.dual_fixing;
     C.count_work = o.timing ? 1 : 0;
+    C.list_touched = 1;
     return C;
 }
 
@@ -867,6 +868,7 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
         LPP_CUDA(cudaMemsetAsync(cchg, 0, (size_t)n, s));
     }
     Ctx C = ctx(r);
+    C.list_touched = first_round ? 0 : 1;  // a first round's S3' checks every column
     tbegin(F_PROP, 0.0);  // bytes and ops set once the evaluated nonzeros are known
     const size_t prop_mark = marks.size();
     launch_prop(C, s);

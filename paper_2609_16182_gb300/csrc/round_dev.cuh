@@ -26,7 +26,9 @@ __device__ __forceinline__ void coalesced_append(int32_t v, int32_t *cnt, int32_
 }
 
 // column j received a candidate: list it once per round for S3'
+// (not needed when S3' checks every column this round)
 __device__ __forceinline__ void touch_col(const Ctx &C, int32_t j) {
+    if (!C.list_touched) return;
     if (C.ctouch[j] == 0u && atomicExch(&C.ctouch[j], 1u) == 0u) coalesced_append(j, C.tl_cnt, C.tl_list);
 }
 
