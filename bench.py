@@ -454,23 +454,28 @@ def serving_leg(lpp, synth, torch, dev, pool_size=16, requests=2000, nnz_hi=1e7,
 
             def submitter():
                 for k in range(requests):
-                    while time.perf_counter() - t0 < arr[k]:
-                        time.sleep(0.00005)
+                    dt = arr[k] - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
                     tickets[k] = srv.submit(dpool[pick[k]])
                     nsub[0] = k + 1
 
             th = threading.Thread(target=submitter)
             th.start()
-            # poll the submitted requests not yet taken (oldest first)
+            # wait on the oldest request not yet taken (in the library, without
+            # the interpreter lock and without spinning), then sweep the others
             pending, nxt = [], 0
             while nxt < requests or pending:
                 while nxt < nsub[0]:
                     pending.append(nxt)
                     nxt += 1
+                if not pending:
+                    time.sleep(0.00005)
+                    continue
                 still = []
-                for k in pending:
+                for q, k in enumerate(pending):
                     try:
-                        r = srv.take(tickets[k], 0)
+                        r = srv.take(tickets[k], 1 if q == 0 else 0)
                     except lpp.LppError as e:
                         if e.status == lpp.ERR_TIMEOUT:
                             still.append(k)
@@ -479,7 +484,6 @@ def serving_leg(lpp, synth, torch, dev, pool_size=16, requests=2000, nnz_hi=1e7,
                     done_at[k] = time.perf_counter() - t0
                     r.close()
                 pending = still
-                time.sleep(0.00005)
             th.join()
             lat = [done_at[k] - arr[k] for k in range(requests)]
             span = max(done_at)

@@ -587,6 +587,13 @@ bool tick(lpp_server *S, std::vector<std::pair<int32_t, lpp_server::Req *>> &adm
 }
 
 // a request presolved alone on the worker's stream (lpp_presolve's engine)
+// The longest queue an idle server still serves one request at a time (each
+// presolved alone, back to back); a longer one joins the arena.  Served one
+// by one a request waits for the ones before it; in the arena every resident
+// LP advances one round per tick, which pays off only when enough of them
+// share the ticks.
+constexpr size_t kSoloQueue = 64;
+
 void run_solo(lpp_server *S, lpp_server::Req *q) {
     lpp_opts o = S->o;
     o.stream = S->E.s;
@@ -617,10 +624,10 @@ void worker_main(lpp_server *S) {
                 };
                 S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty() || busy(); });
                 if (S->stop) break;
-                // an idle server with one or two requests queued: presolve the
-                // oldest at once, rounds back to back, instead of one round
-                // per tick (a longer queue is batched)
-                if (!busy() && S->queue.size() <= 2) {
+                // an idle arena with a short queue: presolve the oldest at
+                // once, rounds back to back, instead of one round per tick;
+                // a queue longer than kSoloQueue (an overload) is batched
+                if (!busy() && S->queue.size() <= kSoloQueue) {
                     solo = S->queue.front();
                     S->queue.pop_front();
                     S->stats.admitted++;

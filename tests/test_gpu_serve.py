@@ -38,14 +38,17 @@ def same_result(a, b):
 
 
 def test_served_results_equal_solo_results_with_staggered_arrivals():
-    lps = [synth.mix(s, m=int(m), n=int(1.5 * m)) for s, m in zip(range(12), [200, 800, 3000, 60, 500] * 3)]
-    lps.insert(3, synth.skewed(2, m=20_000, n=30_000, target_nnz=200_000, row_cap=6000))
+    # a burst longer than the queue an idle server still serves one at a time
+    # (64) fills the arena; the later arrivals join running rounds
+    lps = [synth.tiny(100 + s) for s in range(72)]
+    lps += [synth.mix(s, m=int(m), n=int(1.5 * m)) for s, m in zip(range(12), [200, 800, 3000, 60, 500] * 3)]
+    lps.insert(75, synth.skewed(2, m=20_000, n=30_000, target_nnz=200_000, row_cap=6000))
     solo = [lpp.presolve(lp) for lp in lps]
     with lpp.Server(2 << 30) as srv:
         tickets = []
         for k, lp in enumerate(lps):
             tickets.append(srv.submit(lp))
-            if k % 4 == 3:
+            if k >= 72 and k % 4 == 3:
                 time.sleep(0.002)  # later arrivals join running rounds
         res = [srv.take(t, 60_000) for t in tickets]
         st = srv.stats()
