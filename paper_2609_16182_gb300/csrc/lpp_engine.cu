@@ -907,7 +907,9 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
         pm.ops = 2.0 * st_h->nnz_eval + 2.0 * st_h->sides_tested;
     }
     // later passes on the list of unmatched rows, without a host sync per
-    // pass: chunks of 2, 4, 8, ... passes, then one read of the list size
+    // pass: one block for a short list, else one cooperative launch with grid
+    // barriers (launched chunks of 2, 4, 8, ... passes if that launch is not
+    // possible), then one read of the list size
     const int32_t n1 = run_s5 ? st_h->unmatched : 0;
     bool resolved = n1 == 0;
     if (n1 > 0 && o.par_max_iter > 1) {

@@ -4,7 +4,7 @@ The default-option paths are covered by test_gpu_parity.py; here the
 tolerances, the dual rule, the pass cap of the parallel-row iteration and
 the round cap change, on the 200-row mix and on a small LP-relaxation-like
 instance.  A hand-built LP whose parallel rows need ten leader passes
-exercises the later S5 passes (their chunks of 2, 4, 8 passes), the cap
+exercises the later S5 passes (one block, or one cooperative launch), the cap
 carrying the iteration over into the next round, and the skip of S5 once
 every group is resolved.
 """
