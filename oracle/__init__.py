@@ -61,6 +61,7 @@ _OUT_FIELDS = [
     ("col_kind", C.c_void_p), ("col_round", C.c_void_p), ("col_val", C.c_void_p),
     ("col_aux", C.c_void_p), ("col_pass", C.c_void_p), ("col_mrg", C.c_void_p),
     ("col_lb", C.c_void_p), ("col_ub", C.c_void_p),
+    ("col_lsrc", C.c_void_p), ("col_lrnd", C.c_void_p), ("col_usrc", C.c_void_p), ("col_urnd", C.c_void_p),
     ("sub_beg", C.c_void_p), ("sub_len", C.c_void_p), ("sub_rhs", C.c_void_p), ("sub_col", C.c_void_p),
     ("sub_val", C.c_void_p), ("sub_used", C.c_int64),
     ("act_min", C.c_void_p), ("act_max", C.c_void_p), ("act_scale_min", C.c_void_p),
@@ -156,6 +157,10 @@ class Result:
     col_mrg: np.ndarray    # [n, 4]: the leader's bounds and the column's just before the merge
     col_lb: np.ndarray
     col_ub: np.ndarray
+    col_lsrc: np.ndarray   # original row whose implied / singleton bound set the final lower bound, else -1
+    col_lrnd: np.ndarray   # ... and its round (0: the input bound)
+    col_usrc: np.ndarray   # the same for the upper bound
+    col_urnd: np.ndarray
     sub_beg: np.ndarray    # column-singleton substitutions, per original row: start in the store,
     sub_len: np.ndarray    # entries, and the row's right-hand side b; the store holds the row's
     sub_rhs: np.ndarray    # other columns (original indices) and coefficients
@@ -200,7 +205,8 @@ def presolve(lp, opts: Opts | None = None) -> Result:
                            ("row_aux", m, np.int32), ("row_val", m, np.float64), ("col_kind", n, np.int32),
                            ("col_round", n, np.int32), ("col_val", n, np.float64), ("col_aux", n, np.int32),
                            ("col_pass", n, np.int32), ("col_mrg", 4 * n, np.float64), ("col_lb", n, np.float64),
-                           ("col_ub", n, np.float64), ("sub_beg", m, np.int64), ("sub_len", m, np.int32),
+                           ("col_ub", n, np.float64), ("col_lsrc", n, np.int32), ("col_lrnd", n, np.int32),
+                           ("col_usrc", n, np.int32), ("col_urnd", n, np.int32), ("sub_beg", m, np.int64), ("sub_len", m, np.int32),
                            ("sub_rhs", m, np.float64), ("sub_col", nnz, np.int32), ("sub_val", nnz, np.float64),
                            ("act_min", m, np.float64), ("act_max", m, np.float64),
                            ("act_scale_min", m, np.float64), ("act_scale_max", m, np.float64),
@@ -223,6 +229,8 @@ def presolve(lp, opts: Opts | None = None) -> Result:
         row_val=arr["row_val"][:m], col_kind=arr["col_kind"][:n], col_round=arr["col_round"][:n],
         col_val=arr["col_val"][:n], col_aux=arr["col_aux"][:n], col_pass=arr["col_pass"][:n],
         col_mrg=arr["col_mrg"][:4 * n].reshape(n, 4), col_lb=arr["col_lb"][:n], col_ub=arr["col_ub"][:n],
+        col_lsrc=arr["col_lsrc"][:n], col_lrnd=arr["col_lrnd"][:n], col_usrc=arr["col_usrc"][:n],
+        col_urnd=arr["col_urnd"][:n],
         sub_beg=arr["sub_beg"][:m], sub_len=arr["sub_len"][:m], sub_rhs=arr["sub_rhs"][:m],
         sub_col=arr["sub_col"][:out.sub_used].copy(), sub_val=arr["sub_val"][:out.sub_used].copy(),
         act_min=arr["act_min"][:m], act_max=arr["act_max"][:m], act_scale_min=arr["act_scale_min"][:m],

@@ -254,6 +254,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     int32_t *nmn = NULL, *nmx = NULL, *kind = NULL, *fixed = NULL, *colcnt = NULL;
     double *nl = NULL, *nu = NULL, *ebnl = NULL, *ebnu = NULL, *fixv = NULL;
     int32_t *srcl = NULL, *srcu = NULL; /* tie audit: the singleton row that set nl / nu, else -1 */
+    int32_t *bsl = NULL, *bsu = NULL;   /* this round's source row of nl / nu (S3 or singleton), else -1 */
     double *mL = NULL, *mU = NULL, *ebmL = NULL, *ebmU = NULL;
     int32_t *hasf = NULL, *alive = NULL, *nrow = NULL, *ncol = NULL;
     pkey_t *keys = NULL;
@@ -300,7 +301,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     ALLOC(mna, m0); ALLOC(mxa, m0); ALLOC(smn, m0); ALLOC(smx, m0); ALLOC(ebmn, m0); ALLOC(ebmx, m0);
     ALLOC(nmn, m0); ALLOC(nmx, m0); ALLOC(kind, m0); ALLOC(fixed, n0); ALLOC(colcnt, n0);
     ALLOC(nl, n0); ALLOC(nu, n0); ALLOC(ebnl, n0); ALLOC(ebnu, n0); ALLOC(fixv, n0);
-    ALLOC(srcl, n0); ALLOC(srcu, n0);
+    ALLOC(srcl, n0); ALLOC(srcu, n0); ALLOC(bsl, n0); ALLOC(bsu, n0);
     ALLOC(mL, m0); ALLOC(mU, m0); ALLOC(ebmL, m0); ALLOC(ebmU, m0);
     ALLOC(hasf, m0); ALLOC(alive, m0); ALLOC(nrow, m0); ALLOC(ncol, n0);
     ALLOC(keys, m0); ALLOC(qbuf, lp->nnz);
@@ -323,6 +324,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
         if (out->col_pass) out->col_pass[j] = 0;
         if (out->col_mrg) { out->col_mrg[4 * j] = 0.0; out->col_mrg[4 * j + 1] = 0.0;
                             out->col_mrg[4 * j + 2] = 0.0; out->col_mrg[4 * j + 3] = 0.0; }
+        if (out->col_lsrc) { out->col_lsrc[j] = -1; out->col_lrnd[j] = 0; out->col_usrc[j] = -1; out->col_urnd[j] = 0; }
     }
     out->where = LPPO_WHERE_NONE; out->index = -1; out->round = 0; out->rounds = 0;
     out->s5_left = 0; out->s5_capped_groups = 0;
@@ -426,6 +428,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                and the accepted ones are combined by min / max. */
         for (j = 0; j < n; j++) {
             nl[j] = s.l[j]; nu[j] = s.u[j]; ebnl[j] = s.ebl[j]; ebnu[j] = s.ebu[j]; srcl[j] = -1; srcu[j] = -1;
+            bsl[j] = -1; bsu[j] = -1;
         }
         for (i = 0; i < m; i++) {
             const double L = s.L[i], U = s.U[i];
@@ -474,14 +477,14 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                             audit(&au, cv - thr, ebc[t] + s.ebu[jj] + 2 * UROUND * fabs(thr));
                             if (!(cv < thr)) continue;
                         }
-                        if (cv < nu[jj]) { nu[jj] = cv; ebnu[jj] = ebc[t]; }
+                        if (cv < nu[jj]) { nu[jj] = cv; ebnu[jj] = ebc[t]; bsu[jj] = i; }
                     } else {
                         if (isfin(s.l[jj])) {
                             double thr = s.l[jj] + o->bound_tol * dmax(1.0, fabs(s.l[jj]));
                             audit(&au, cv - thr, ebc[t] + s.ebl[jj] + 2 * UROUND * fabs(thr));
                             if (!(cv > thr)) continue;
                         }
-                        if (cv > nl[jj]) { nl[jj] = cv; ebnl[jj] = ebc[t]; }
+                        if (cv > nl[jj]) { nl[jj] = cv; ebnl[jj] = ebc[t]; bsl[jj] = i; }
                     }
                 }
             }
@@ -508,6 +511,13 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
             else if (isfin(cl) && nl[j] - cl <= ebcl + ebnl[j]) srcl[j] = -2;
             if (cu < nu[j]) srcu[j] = isfin(nu[j]) && nu[j] - cu <= ebcu + ebnu[j] ? -2 : i;
             else if (isfin(cu) && cu - nu[j] <= ebcu + ebnu[j]) srcu[j] = -2;
+            /* source row: rows are visited in increasing order, so a
+               singleton row equal to this round's bound replaces an S3 row
+               only if it comes first */
+            if (cl > nl[j]) bsl[j] = i;
+            else if (cl == nl[j] && bsl[j] > i) bsl[j] = i;
+            if (cu < nu[j]) bsu[j] = i;
+            else if (cu == nu[j] && bsu[j] > i) bsu[j] = i;
             if (cl > nl[j]) { nl[j] = cl; ebnl[j] = ebcl; }
             if (cu < nu[j]) { nu[j] = cu; ebnu[j] = ebcu; }
         }
@@ -531,6 +541,10 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
                     lp_ = up_ = mid; ebnl[j] = ebnu[j] = e;
                 }
             }
+            /* a side moved by a candidate records its source (a side moved
+               only by the snap keeps its earlier source) */
+            if (out->col_lsrc && bsl[j] >= 0) { out->col_lsrc[s.cmap[j]] = s.rmap[bsl[j]]; out->col_lrnd[s.cmap[j]] = r; }
+            if (out->col_usrc && bsu[j] >= 0) { out->col_usrc[s.cmap[j]] = s.rmap[bsu[j]]; out->col_urnd[s.cmap[j]] = r; }
             if (lp_ != s.l[j] || up_ != s.u[j]) bchanged++;
             s.l[j] = lp_; s.u[j] = up_; s.ebl[j] = ebnl[j]; s.ebu[j] = ebnu[j];
         }
@@ -1170,7 +1184,7 @@ int lppo_presolve(const lppo_lp *lp, const lppo_opts *o, lppo_out *out)
     free(s.rmap); free(s.cmap); free(s.ebL); free(s.ebU); free(s.ebl); free(s.ebu);
     free(mna); free(mxa); free(smn); free(smx); free(ebmn); free(ebmx); free(nmn); free(nmx);
     free(kind); free(fixed); free(colcnt); free(nl); free(nu); free(ebnl); free(ebnu); free(fixv);
-    free(srcl); free(srcu);
+    free(srcl); free(srcu); free(bsl); free(bsu);
     free(mL); free(mU); free(ebmL); free(ebmU); free(hasf); free(alive); free(nrow); free(ncol);
     free(keys); free(qbuf); free(nrp); free(nci); free(nv);
     free(tcp); free(tri); free(tvl); free(tfill); free(calive); free(ckeys); free(cqbuf);
@@ -1182,7 +1196,7 @@ oom:
     free(s.rmap); free(s.cmap); free(s.ebL); free(s.ebU); free(s.ebl); free(s.ebu);
     free(mna); free(mxa); free(smn); free(smx); free(ebmn); free(ebmx); free(nmn); free(nmx);
     free(kind); free(fixed); free(colcnt); free(nl); free(nu); free(ebnl); free(ebnu); free(fixv);
-    free(srcl); free(srcu);
+    free(srcl); free(srcu); free(bsl); free(bsu);
     free(mL); free(mU); free(ebmL); free(ebmU); free(hasf); free(alive); free(nrow); free(ncol);
     free(keys); free(qbuf); free(nrp); free(nci); free(nv);
     free(tcp); free(tri); free(tvl); free(tfill); free(calive); free(ckeys); free(cqbuf);

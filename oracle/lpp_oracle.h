@@ -99,6 +99,12 @@ typedef struct {
        the merged column just before the merge (lk, uk, lj, uj) [4n] */
     int32_t *col_aux, *col_pass;  double *col_mrg;
     double  *col_lb, *col_ub;     /* final bounds (fixed columns: value) */
+    /* bound sources for the dual postsolve (may be NULL): per original
+       column, the original row whose implied bound (S3) or singleton-row
+       bound set the final lower / upper bound, the smallest such row when
+       several give that value, and the round it was set in; -1 and 0 where
+       the side is the input bound */
+    int32_t *col_lsrc, *col_lrnd, *col_usrc, *col_urnd;
     /* column-singleton substitutions (may be NULL when the step is off):
        per original row [m] the start and length of its entries in the store
        and its right-hand side b; the store [nnz] holds the row's other

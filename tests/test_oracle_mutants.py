@@ -25,6 +25,7 @@ S5D = ["tests/test_oracle_colsing.py", "-k",
 S5C = ["tests/test_oracle_parcols.py"]
 DUALFIX = ["tests/test_oracle_dualfix.py", "-k", "hand_worked or unbounded"]
 POST = ["tests/test_oracle_colsing.py", "-k", "optimum_kept and 0"]
+DUAL = ["tests/test_oracle_dual.py", "-k", "optimal or hand_case or records"]
 
 # (name, text in the oracle, its replacement, pins to run)
 MUTANTS = [
@@ -130,6 +131,11 @@ MUTANTS = [
      "if (hi < mU[li]) { mU[li] = hi;", "if (1) { mU[li] = hi;", S5P),
     ("S5: a group of two live rows not run",
      "if (cnt < 2) break;", "if (cnt < 3) break;", S5P),
+    ("dual records: a lower bound's source row written as the upper one's",
+     "if (out->col_lsrc && bsl[j] >= 0) { out->col_lsrc[s.cmap[j]] = s.rmap[bsl[j]];",
+     "if (out->col_lsrc && bsl[j] >= 0) { out->col_usrc[s.cmap[j]] = s.rmap[bsl[j]];", DUAL),
+    ("dual records: a singleton row never named as a source",
+     "            if (cu < nu[j]) bsu[j] = i;\n", "", DUAL),
     ("postsolve: a substituted column divided by the wrong coefficient",
      "x_orig[jj] = (sub_rhs[ii] - sum) / row_val[ii];", "x_orig[jj] = (sub_rhs[ii] - sum) * row_val[ii];", POST),
 ]
@@ -165,7 +171,7 @@ def source():
 def outcomes(source, tmp_path_factory):
     """Every mutant (and the control) built and run once, in parallel:
     name -> (return code, output tail)."""
-    jobs = [("control", source, RULES + S5P + ["tests/test_oracle_doubleton.py"])]
+    jobs = [("control", source, RULES + S5P + DUAL + ["tests/test_oracle_doubleton.py"])]
     for name, old, new, pins in MUTANTS:
         assert source.count(old) == 1, f"mutation site not unique or gone: {old!r}"
         jobs.append((name, source.replace(old, new), pins))
