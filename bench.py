@@ -349,6 +349,31 @@ def dualfix_leg(lpp, torch, dev, stream, lp):
                       lambda r: {"dual_fixed": int(np.count_nonzero(r.col_kind == lpp.COL_EMPTY))})
 
 
+def dualrec_leg(lpp, torch, dev, stream, lp):
+    """The benchmark LP with the bound-source records (dual_records) on and
+    off; their kernels run in the colfin family.  Outside the timed steps,
+    the host time of one primal-dual postsolve (lpp_postsolve_dual) of that
+    LP from a reduced pair: x at the middle of each finite range (else at its
+    finite end, else 0), y = 0, so every reduced cost c_j on a row-set side
+    is carried back to its row."""
+
+    def count(r):
+        red = r.reduced(csc=False)
+        lo, hi = red.lb, red.ub
+        fl, fh = np.abs(lo) < 1e20, np.abs(hi) < 1e20
+        lo0, hi0 = np.where(fl, lo, 0.0), np.where(fh, hi, 0.0)
+        xr = np.where(fl & fh, 0.5 * (lo0 + hi0), lo0 + hi0)
+        yr = np.zeros(r.info.m_red)
+        src = r.bound_sources()
+        t0 = time.perf_counter()
+        _, y, _ = r.postsolve_dual(lp, xr, yr)
+        dt = time.perf_counter() - t0
+        return {"sides_with_source": int((src["lsrc"] >= 0).sum() + (src["usrc"] >= 0).sum()),
+                "rows_given_a_dual": int(np.count_nonzero(y)), "postsolve_dual_host_ms": 1e3 * dt}
+
+    return opt_in_leg(lpp, torch, dev, stream, lp, "benchmark LP", "dual_records", "colfin", count)
+
+
 def doubleton_leg(lpp, synth, torch, dev, stream, q):
     """The LP-relaxation workload (500k rows, 1M columns, 7.8M nonzeros,
     4% doubleton equations, 10 dense columns) with the doubleton step on and
@@ -558,6 +583,7 @@ def main():
     ap.add_argument("--no-parcols", action="store_true", help="skip the parallel-columns leg")
     ap.add_argument("--no-colsing", action="store_true", help="skip the column-singletons leg")
     ap.add_argument("--no-dualfix", action="store_true", help="skip the dual-fixing leg")
+    ap.add_argument("--no-dualrec", action="store_true", help="skip the dual-records leg")
     ap.add_argument("--no-doubletons", action="store_true", help="skip the doubleton-equations leg")
     ap.add_argument("--no-lprelax", action="store_true", help="skip the LP-relaxation workload leg")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the LP (profiling runs only)")
@@ -695,6 +721,9 @@ def main():
     dualfix = None
     if not args.no_dualfix:
         dualfix = dualfix_leg(lpp, torch, dev, stream, lp)
+    dualrec = None
+    if not args.no_dualrec:
+        dualrec = dualrec_leg(lpp, torch, dev, stream, lp)
     lprelax = doubletons = None
     if not (args.no_lprelax and args.no_doubletons):
         q = synth.lprelax(0)
@@ -713,7 +742,8 @@ def main():
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
                 "batched": batched, "serving": serving, "parallel_cols": parcols, "col_singletons": colsing,
-                "dual_fixing": dualfix, "doubletons": doubletons, "lp_relaxation": lprelax}
+                "dual_fixing": dualfix, "dual_records": dualrec, "doubletons": doubletons,
+                "lp_relaxation": lprelax}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

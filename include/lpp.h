@@ -135,9 +135,14 @@ typedef struct lpp_opts {
     int32_t batch_persistent; /* [1]   lpp_presolve_batch: 1 runs every round of each LP in
                                        one persistent kernel (a thread block per LP, no host
                                        step between rounds) when every row and column has at
-                                       most 4096 entries and parallel_cols, col_singletons and
-                                       doubletons are 0; 0 (or an LP that does not qualify):
-                                       one set of kernel launches per round over all LPs      */
+                                       most 4096 entries and parallel_cols, col_singletons,
+                                       doubletons and dual_records are 0; 0 (or an LP that does
+                                       not qualify): one set of kernel launches per round over
+                                       all LPs                                                */
+    int32_t dual_records;   /* [0]     1: record, per column side, the row whose implied or
+                                       singleton-row bound set the final bound (S3), for
+                                       lpp_postsolve_dual; lpp_presolve and lpp_presolve_batch
+                                       only (a server rejects it)                             */
     int32_t timing;         /* [0]     1: time every kernel launch with CUDA events           */
     int32_t device;         /* [0]     CUDA device ordinal                                   */
     void *stream;           /* [NULL]  cudaStream_t to run on; NULL: a library-owned stream  */
@@ -252,6 +257,17 @@ lpp_status lpp_result_rounds(const lpp_postsolve *rec, int32_t cap, int64_t *nnz
 /* Kernel statistics (opts.timing = 1): up to cap entries, count in *count. */
 lpp_status lpp_result_kernels(const lpp_postsolve *rec, int32_t cap, lpp_kernel_stat *stats, int32_t *count);
 
+/* Bound sources (opts.dual_records = 1; Sec. 3.1 implied bounds).  Per
+ * original column (host arrays of n, any pointer may be NULL): lsrc[j] = the
+ * original row whose implied bound (S3) or singleton-row bound set the
+ * column's final lower bound, the smallest such row when several rows give
+ * the same value, and lrnd[j] = the round (1-based) it was set in; -1 and 0
+ * where the lower bound is the input's (or only the snap of S3' moved it).
+ * usrc, urnd: the same for the upper bound.  LPP_ERR_INVALID if the presolve
+ * ran without opts.dual_records. */
+lpp_status lpp_result_bound_sources(const lpp_postsolve *rec, int32_t *lsrc, int32_t *lrnd, int32_t *usrc,
+                                    int32_t *urnd);
+
 /* Primal postsolve on the CPU (Sec. 2.1 postsolver; Sec. 3.3): x_red[n_red]
  * -> x_orig[n] (host arrays): kept columns take their reduced value, fixed
  * columns their recorded value.  Merges and substitutions are undone latest
@@ -261,6 +277,31 @@ lpp_status lpp_result_kernels(const lpp_postsolve *rec, int32_t cap, lpp_kernel_
  * [l_j, u_j] that leaves v - lambda x_j inside [l_y, u_y] (the highest if that
  * range has no finite low end, 0 if it has neither), and y = v - lambda x_j. */
 lpp_status lpp_postsolve_primal(const lpp_postsolve *rec, const double *x_red, double *x_orig);
+
+/* Primal-dual postsolve on the CPU (Sec. 2.1 postsolver; Sec. 3.3: a
+ * primal-dual solution of the reduced LP back to one of the input LP).
+ * Sign convention of Eq. 1 (minimise): row duals y with y_i > 0 only at a
+ * finite lhs and y_i < 0 only at a finite rhs, reduced costs z = c - A^T y
+ * with z_j > 0 only at a finite lower and z_j < 0 only at a finite upper
+ * bound.  Inputs: the input LP `lp` as HOST arrays (the one presolved), the
+ * reduced solution x_red[n_red] and y_red[m_red] (reduced row order).
+ * Outputs (host arrays): x_orig[n] as lpp_postsolve_primal, y_orig[m],
+ * z_orig[n].  Steps: kept rows take y through the row map, removed rows 0;
+ * with z = c - A^T y, bound sides set by a row (lpp_result_bound_sources)
+ * are taken latest round first, then by column: a reduced cost on such a
+ * side (z_j < 0 on an upper, z_j > 0 on a lower bound) moves to the row,
+ * y_r += z_j / a_rj, z updated on the row's columns; then the dual Y of each
+ * family of parallel rows (a row and all rows merged into it, directly or
+ * through merges into those, each lambda times the family's root) is given
+ * whole to the member whose side of the orientation sign(Y) is tightest at
+ * x_orig (smallest |a x - side| / max(1, |side|), then smallest row), as
+ * Y / lambda; finally z = c - A^T y.  LPP_ERR_INVALID if the presolve ran
+ * without opts.dual_records, if its result is not LPP_OK, if the LP does not
+ * match the records (sizes), or if the records hold parallel-column merges,
+ * column-singleton substitutions or doubletons (no dual postsolve is kept
+ * for those steps). */
+lpp_status lpp_postsolve_dual(const lpp_postsolve *rec, const lpp_lp *lp, const double *x_red, const double *y_red,
+                              double *x_orig, double *y_orig, double *z_orig);
 
 void lpp_free_reduced(lpp_reduced *red);
 void lpp_free_postsolve(lpp_postsolve *rec);

@@ -174,6 +174,79 @@ __global__ void __launch_bounds__(kBlock) k_prop_long_tighten(Ctx C) {
     block_add(tested, &C.st->sides_tested);  // the whole block returned above or reaches here
 }
 
+// ------------------------------------------ S3 bound sources (dual records)
+// The dual postsolve moves a reduced cost on a tightened bound to the row
+// that implied it, so each accepted candidate needs its row.  Between S3 and
+// S3', every row S1-S3 evaluated this round (a dirty flag) runs over its
+// entries again, row by row as S3 does: an entry whose column received a
+// candidate re-derives its implied bound (or the singleton row's bound) on
+// the stored activities with the activity kernels' arithmetic, and a value
+// equal to the accepted candidate (encoded values compared: bit for bit)
+// offers its original row index to the column's side (atomicMin: the
+// smallest row wins).
+__device__ __forceinline__ void bsrc_offer(const Ctx &C, int32_t j, double x, double a, bool upper, bool capped,
+                                           unsigned long long el, unsigned long long eu, int32_t o) {
+    if (capped && gt0(fma(-C.max_implied, fabs(a), fabs(x)))) return;
+    const double v = x / a;
+    if (!is_fin(v)) return;
+    const unsigned long long e = enc_dbl(v);
+    if (upper) {
+        if (e == eu) atomicMin(&C.bsrc[j].y, o);
+    } else if (e == el) {
+        atomicMin(&C.bsrc[j].x, o);
+    }
+}
+
+// entries [k0, k1) of row i, every step-th from k0
+__device__ __forceinline__ void bsrc_row(const Ctx &C, int32_t i, int32_t k0, int32_t k1, int32_t step) {
+    const uint8_t kind = C.rkind[i];
+    const int32_t len = C.A.ptr[i + 1] - C.A.ptr[i];
+    if (!(kind == RK_SINGLETON || (kind == RK_KEPT && len >= 2))) return;
+    const double Lv = C.L[i], Uv = C.U[i];
+    const int32_t o = C.rmap[i];
+    const double2 act = C.act[i];
+    const int2 ni = C.ninf[i];
+    const bool up_row = is_fin(Uv) && ni.x <= 1, lo_row = is_fin(Lv) && ni.y <= 1;
+    const double dU = Uv - act.x, dL = Lv - act.y;
+    for (int32_t k = k0; k < k1; k += step) {
+        const int32_t j = C.A.idx[k];
+        const unsigned long long el = C.cand_l[j], eu = C.cand_u[j];
+        if (el == kEncNegInf && eu == kEncPosInf) continue;
+        const double a = C.A.val[k];
+        const bool neg = is_neg(a);
+        if (kind == RK_SINGLETON) {  // L <= a x_j <= U: bounds L/a and U/a (a < 0 swaps them), no cap
+            if (is_fin(Lv)) bsrc_offer(C, j, Lv, a, neg, false, el, eu, o);
+            if (is_fin(Uv)) bsrc_offer(C, j, Uv, a, !neg, false, el, eu, o);
+            continue;
+        }
+        const double2 b = C.lu[j];
+        const double bmin = neg ? b.y : b.x, bmax = neg ? b.x : b.y;
+        const bool fmn = is_fin(bmin), fmx = is_fin(bmax);
+        if (up_row && (fmn ? ni.x == 0 : ni.x == 1))  // a x_j <= U - (min activity of the others)
+            bsrc_offer(C, j, fmn ? fma(a, bmin, dU) : dU, a, !neg, true, el, eu, o);
+        if (lo_row && (fmx ? ni.y == 0 : ni.y == 1))  // a x_j >= L - (max activity of the others)
+            bsrc_offer(C, j, fmx ? fma(a, bmax, dL) : dL, a, neg, true, el, eu, o);
+    }
+}
+
+// rows of classes 0..5, 1 << class lanes per row (the grid of group_grid)
+__global__ void __launch_bounds__(kBlock) k_bsrc_groups(Ctx C, GroupGrid g) {
+    const int c = grid_class(g, blockIdx.x);
+    const int W = 1 << c;
+    const int32_t pos = C.A.cls_start[c] + (blockIdx.x - g.blk_start[c]) * (kBlock / W) + threadIdx.x / W;
+    if (pos >= C.A.cls_start[c + 1]) return;
+    const int32_t i = C.A.order[pos];
+    if (C.rdirty[i] == 0) return;
+    bsrc_row(C, i, C.A.ptr[i] + (int32_t)(threadIdx.x & (W - 1)), C.A.ptr[i + 1], W);
+}
+
+// the chunks of the long rows, a block per chunk
+__global__ void __launch_bounds__(kBlock) k_bsrc_chunks(Ctx C) {
+    const Chunk ch = C.A.chunks[blockIdx.x];
+    if (C.rdirty[ch.seg] == 0) return;
+    bsrc_row(C, ch.seg, ch.begin + threadIdx.x, ch.end, kBlock);
+}
+
 // ------------------------------------------------- S3' finalise + S4 fixing
 // every column (some LP in its first round)
 __global__ void __launch_bounds__(kBlock) k_colfin(Ctx C) {
@@ -519,6 +592,14 @@ void launch_prop(const Ctx &C, cudaStream_t s) {
         (k_prop_long_combine<<<blocks_for((int64_t)nlong * 32, kBlock), kBlock, 0, s>>>(C, C.ch_hash), note_launch());
         (k_prop_long_tighten<<<C.A.nchunks, kBlock, 0, s>>>(C), note_launch());
     }
+}
+
+void launch_bound_src(const Ctx &C, cudaStream_t s) {
+    if (C.m <= 0 || C.n <= 0) return;
+    const GroupGrid g = group_grid(C.A);
+    if (g.blk_start[6] > 0) (k_bsrc_groups<<<g.blk_start[6], kBlock, 0, s>>>(C, g), note_launch());
+    if (C.A.cls_start[7] > C.A.cls_start[6] && C.A.nchunks > 0)
+        (k_bsrc_chunks<<<C.A.nchunks, kBlock, 0, s>>>(C), note_launch());
 }
 
 void launch_colfin(const Ctx &C, bool full, cudaStream_t s) {

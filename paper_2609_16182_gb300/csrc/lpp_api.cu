@@ -57,7 +57,8 @@ lpp_opts resolve_opts(const lpp_opts *opts) {
     if (o.max_rounds < 0 || o.par_max_iter < 1 || !(o.feas_tol >= 0) || !(o.bound_tol >= 0) || !(o.huge > 0) ||
         !(o.max_implied > 0) || !(o.par_tol >= 0) || (o.parallel_cols != 0 && o.parallel_cols != 1) ||
         (o.col_singletons != 0 && o.col_singletons != 1) || (o.dual_fixing != 0 && o.dual_fixing != 1) ||
-        (o.doubletons != 0 && o.doubletons != 1) || (o.batch_persistent != 0 && o.batch_persistent != 1))
+        (o.doubletons != 0 && o.doubletons != 1) || (o.batch_persistent != 0 && o.batch_persistent != 1) ||
+        (o.dual_records != 0 && o.dual_records != 1))
         throw StatusError(LPP_ERR_INVALID, "bad options");
     return o;
 }
@@ -136,6 +137,7 @@ std::shared_ptr<DeviceRecords> take_records(Engine &E) {
     D->srhs = E.rec_srhs;
     D->scol = E.rec_scol;
     D->sval = E.rec_sval;
+    D->bs = E.rec_bs;
     if (E.sub_used) {
         unsigned long long used = 0;
         LPP_CUDA(cudaMemcpyAsync(&used, E.sub_used, sizeof used, cudaMemcpyDeviceToHost, E.s));
@@ -148,7 +150,7 @@ std::shared_ptr<DeviceRecords> take_records(Engine &E) {
     for (void *p : {(void *)D->rk, (void *)D->rr, (void *)D->ra, (void *)D->rv, (void *)D->ck, (void *)D->cr,
                     (void *)D->cv, (void *)D->lu, (void *)D->act, (void *)D->ninf, (void *)D->ca, (void *)D->cp,
                     (void *)D->cm, (void *)D->sb, (void *)D->sl, (void *)D->srhs, (void *)D->scol,
-                    (void *)D->sval}) {
+                    (void *)D->sval, (void *)D->bs}) {
         if (!p) continue;
         E.pool.forget(p);
         D->owned.push_back(p);
@@ -173,6 +175,7 @@ lpp_postsolve *make_postsolve(Engine &E, const std::shared_ptr<DeviceRecords> &D
     auto *P = new lpp_postsolve();
     const Member &mm = E.mem[k];
     P->dev = D;
+    P->huge = E.o.huge;
     P->r0 = mm.row_off;
     P->c0 = mm.col_off;
     P->cstart = cstart;
@@ -273,6 +276,20 @@ void materialize(lpp_postsolve *P) {
         P->col_aux.assign(n, -1);
         P->col_pass.assign(n, 0);
         P->col_mrg.assign(4 * (size_t)n, NAN);
+    }
+    if (D.bs) {  // bound sources: LP-local rows, round 0 where the side has no source
+        std::vector<int4> bs;
+        d2h_slice(bs, D.bs, c0, n);
+        P->col_lsrc.resize(n);
+        P->col_lrnd.resize(n);
+        P->col_usrc.resize(n);
+        P->col_urnd.resize(n);
+        for (int32_t j = 0; j < n; j++) {
+            P->col_lsrc[j] = bs[j].x >= 0 ? bs[j].x - r0 : bs[j].x;
+            P->col_lrnd[j] = bs[j].x == -1 ? 0 : bs[j].y;
+            P->col_usrc[j] = bs[j].z >= 0 ? bs[j].z - r0 : bs[j].z;
+            P->col_urnd[j] = bs[j].z == -1 ? 0 : bs[j].w;
+        }
     }
     // substitutions: this LP's rows and their entries, the store compacted to
     // them (LP-local column indices)
@@ -420,7 +437,8 @@ uint64_t tuner_key(int32_t count, int64_t nnz, int32_t dualfix) {
 bool batch_fused(Engine &E, const std::vector<Member> &mem, int32_t count, lpp_reduced **outs, lpp_postsolve **recs,
                  lpp_status *per_lp) {
     const lpp_opts &o = E.o;
-    if (!o.batch_persistent || o.parallel_cols || o.col_singletons || o.doubletons || o.timing || o.max_rounds <= 0)
+    if (!o.batch_persistent || o.parallel_cols || o.col_singletons || o.doubletons || o.dual_records || o.timing ||
+        o.max_rounds <= 0)
         return false;
     if (E.A.cls_start[7] != E.A.cls_start[6] || E.T.cls_start[7] != E.T.cls_start[6]) return false;
     cudaStream_t s = E.s;
@@ -658,6 +676,7 @@ void lpp_opts_default(lpp_opts *o) {
     o->dual_fixing = 0;
     o->doubletons = 0;
     o->batch_persistent = 1;
+    o->dual_records = 0;
     o->timing = 0;
     o->device = 0;
     o->stream = nullptr;
@@ -961,6 +980,22 @@ lpp_status lpp_result_merges(const lpp_postsolve *Pc, int32_t *leader, int32_t *
     return LPP_OK;
 }
 
+lpp_status lpp_result_bound_sources(const lpp_postsolve *Pc, int32_t *lsrc, int32_t *lrnd, int32_t *usrc,
+                                    int32_t *urnd) {
+    if (!Pc) return set_err(LPP_ERR_INVALID, "NULL record");
+    lpp_postsolve *P = const_cast<lpp_postsolve *>(Pc);
+    const lpp_status st = guarded([&]() -> lpp_status { materialize(P); return LPP_OK; });
+    if (st != LPP_OK) return st;
+    const size_t n = P->col_kind.size();
+    if (P->col_lsrc.size() != n || !P->dev->bs)
+        return set_err(LPP_ERR_INVALID, "no bound sources: the presolve ran without opts.dual_records");
+    if (lsrc && n) std::memcpy(lsrc, P->col_lsrc.data(), 4 * n);
+    if (lrnd && n) std::memcpy(lrnd, P->col_lrnd.data(), 4 * n);
+    if (usrc && n) std::memcpy(usrc, P->col_usrc.data(), 4 * n);
+    if (urnd && n) std::memcpy(urnd, P->col_urnd.data(), 4 * n);
+    return LPP_OK;
+}
+
 lpp_status lpp_result_substitutions(const lpp_postsolve *Pc, int64_t *beg, int32_t *len, double *rhs, int64_t cap,
                                     int32_t *col, double *val, int64_t *total) {
     if (!Pc || cap < 0) return set_err(LPP_ERR_INVALID, "bad argument");
@@ -1043,6 +1078,65 @@ lpp_status lpp_postsolve_primal(const lpp_postsolve *Pc, const double *x_red, do
     R.sub_val = P->sub_val.data();
     R.sub_size = (int64_t)P->sub_col.size();
     const char *err = postsolve_primal(R, x_red, x_orig);
+    return err ? set_err(LPP_ERR_INVALID, err) : LPP_OK;
+}
+
+lpp_status lpp_postsolve_dual(const lpp_postsolve *Pc, const lpp_lp *lp, const double *x_red, const double *y_red,
+                              double *x_orig, double *y_orig, double *z_orig) {
+    if (!Pc || !lp) return set_err(LPP_ERR_INVALID, "NULL argument");
+    lpp_postsolve *P = const_cast<lpp_postsolve *>(Pc);
+    const lpp_status st = guarded([&]() -> lpp_status { materialize(P); return LPP_OK; });
+    if (st != LPP_OK) return st;
+    if (!P->dev->bs || P->col_lsrc.size() != P->col_kind.size())
+        return set_err(LPP_ERR_INVALID, "no bound sources: the presolve ran without opts.dual_records");
+    if (P->info.status != LPP_OK) return set_err(LPP_ERR_INVALID, "the presolve did not end with LPP_OK");
+    const int64_t m = P->info.m, n = P->info.n;
+    if (lp->on_device) return set_err(LPP_ERR_INVALID, "lpp_postsolve_dual reads the LP from host memory");
+    if (lp->m != m || lp->n != n) return set_err(LPP_ERR_INVALID, "the LP's sizes differ from the presolved LP's");
+    if ((m && (!lp->row_ptr || !lp->lhs || !lp->rhs || !y_orig)) || (n && (!lp->c || !x_orig || !z_orig)) ||
+        (lp->nnz && (!lp->col_idx || !lp->val)))
+        return set_err(LPP_ERR_INVALID, "NULL argument");
+    if ((P->info.m_red && !y_red) || (P->info.n_red && !x_red)) return set_err(LPP_ERR_INVALID, "NULL argument");
+    if (m && (lp->row_ptr[0] != 0 || lp->row_ptr[m] != lp->nnz))
+        return set_err(LPP_ERR_INVALID, "the LP's row pointers do not match its nonzero count");
+    for (int64_t i = 0; i < m; i++)
+        if (lp->row_ptr[i + 1] < lp->row_ptr[i]) return set_err(LPP_ERR_INVALID, "row pointers decrease");
+    for (int64_t k = 0; k < lp->nnz; k++)
+        if (lp->col_idx[k] < 0 || lp->col_idx[k] >= n) return set_err(LPP_ERR_INVALID, "column index out of range");
+    // the reduced rows are the kept rows in their input order
+    std::vector<int32_t> row_map;
+    row_map.reserve((size_t)P->info.m_red);
+    for (int64_t i = 0; i < m; i++)
+        if (P->row_kind[i] == LPP_ROW_KEPT) row_map.push_back((int32_t)i);
+    if ((int64_t)row_map.size() != P->info.m_red) return set_err(LPP_ERR_INVALID, "corrupt row records");
+    const lpp_status ps = lpp_postsolve_primal(Pc, x_red, x_orig);
+    if (ps != LPP_OK) return ps;
+    DualRecords D;
+    D.m = m;
+    D.n = n;
+    D.m_red = P->info.m_red;
+    D.row_ptr = lp->row_ptr;
+    D.col_idx = lp->col_idx;
+    D.val = lp->val;
+    D.c = lp->c;
+    D.lhs = lp->lhs;
+    D.rhs = lp->rhs;
+    D.huge = P->huge;
+    D.row_map = row_map.data();
+    D.row_kind = P->row_kind.data();
+    D.row_aux = P->row_aux.data();
+    D.row_val = P->row_val.data();
+    D.col_kind = P->col_kind.data();
+    D.lsrc = P->col_lsrc.data();
+    D.lrnd = P->col_lrnd.data();
+    D.usrc = P->col_usrc.data();
+    D.urnd = P->col_urnd.data();
+    const char *err = nullptr;
+    const lpp_status gs = guarded([&]() -> lpp_status {
+        err = postsolve_dual(D, x_orig, y_red, y_orig, z_orig);
+        return LPP_OK;
+    });
+    if (gs != LPP_OK) return gs;
     return err ? set_err(LPP_ERR_INVALID, err) : LPP_OK;
 }
 

@@ -162,6 +162,13 @@ struct Ctx {
     int32_t dualfix;                // S6 by locks (opts.dual_fixing)
     int32_t count_work;             // the activity kernels count evaluated nonzeros and tested sides (timing)
     int32_t list_touched;           // S3' runs on the listed columns (not on all of them): list them
+    // bound sources (opts.dual_records): per current column the smallest
+    // original row whose bound equals this round's accepted candidate
+    // (lower, upper; INT32_MAX: none), consumed by S3'; per original column
+    // the source row and round of the final lower and upper bound
+    int2 *bsrc;
+    int4 *rec_bs;
+    int32_t dual_rec;
 };
 
 // Compaction work (S6, S7) beyond Ctx.

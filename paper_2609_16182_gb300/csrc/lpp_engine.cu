@@ -386,6 +386,10 @@ void Engine::setup(const lpp_opts &opts, int32_t nlp_, const std::vector<Member>
     rec_ck = pool.alloc<int32_t>(n0);
     rec_cr = pool.alloc<int32_t>(n0);
     rec_cv = pool.alloc<double>(n0);
+    if (o.dual_records) {
+        rec_bs = pool.alloc<int4>(n0);
+        bsrc = pool.alloc<int2>(n0);
+    }
     if (o.parallel_cols) {
         cslot = pool.alloc<int32_t>(n0);
         ctcap_max = pow2_at_least(2 * (int64_t)std::max(n0, 1));
@@ -621,6 +625,10 @@ void Engine::prepare() {
     LPP_CUDA(cudaMemsetAsync(rec_ck, 0, sizeof(int32_t) * (size_t)std::max(n0, 1), s));
     LPP_CUDA(cudaMemsetAsync(rec_cr, 0, sizeof(int32_t) * (size_t)std::max(n0, 1), s));
     LPP_CUDA(cudaMemsetAsync(rec_cv, 0, sizeof(double) * (size_t)std::max(n0, 1), s));
+    if (o.dual_records) {  // no source (-1, round -1: read as 0); no candidate row yet
+        fill_i32(reinterpret_cast<int32_t *>(rec_bs), 4 * (int64_t)n0, -1, s);
+        fill_i32(reinterpret_cast<int32_t *>(bsrc), 2 * (int64_t)n0, INT32_MAX, s);
+    }
     if (o.parallel_cols) {
         // an empty column table: no key, no column
         LPP_CUDA(cudaMemsetAsync(ctkey, 0, sizeof(unsigned long long) * (size_t)ctcap_max, s));
@@ -784,6 +792,9 @@ Ctx Engine::ctx(int32_t round) const {
     C.dualfix = o.dual_fixing;
     C.count_work = o.timing ? 1 : 0;
     C.list_touched = 1;
+    C.dual_rec = o.dual_records ? 1 : 0;
+    C.bsrc = bsrc;
+    C.rec_bs = rec_bs;
     return C;
 }
 
@@ -874,6 +885,7 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     launch_prop(C, s);
     tend();
     tbegin(F_COLFIN, 33.0 * n);
+    if (o.dual_records) launch_bound_src(C, s);
     launch_colfin(C, first_round, s);
     launch_mark_dirty(C, nnz, s);
     tend();

@@ -159,6 +159,8 @@ struct Engine {
     int32_t *rec_sl = nullptr, *rec_scol = nullptr;
     double *rec_srhs = nullptr, *rec_sval = nullptr;
     unsigned long long *sub_used = nullptr;
+    int4 *rec_bs = nullptr;                         // bound sources (NULL unless opts.dual_records):
+    int2 *bsrc = nullptr;                           // per original column, and this round's per column
     DevStatus *st;
     DevStatus *st_h = nullptr;  // pinned mirror
     int32_t *verdict_h = nullptr;
@@ -279,6 +281,7 @@ struct DeviceRecords {
     int32_t *sl = nullptr, *scol = nullptr;
     double *srhs = nullptr, *sval = nullptr;
     int64_t sub_used = 0;                  // entries in the store
+    int4 *bs = nullptr;                    // bound sources (NULL without dual_records)
     std::once_flag store_once;             // the host copy of the store, made once
     std::vector<int32_t> h_scol;
     std::vector<double> h_sval;
@@ -297,6 +300,7 @@ struct DeviceRecords {
 struct lpp_postsolve {
     lpp_info info{};
     std::shared_ptr<lpp::DeviceRecords> dev;
+    double huge = 1e20;              // opts.huge of the presolve (infinite sides of the input LP)
     int32_t r0 = 0, c0 = 0;          // first original row / column of this LP in the arena
     int32_t cstart = 0;              // first kept column of this LP in the final arena
     int32_t astart = 0, acnt = 0;    // this LP's rows in the last round's numbering
@@ -307,6 +311,7 @@ struct lpp_postsolve {
     std::vector<int32_t> sub_len, sub_col;
     std::vector<double> sub_rhs, sub_val;
     std::vector<int32_t> ninf_min, ninf_max;
+    std::vector<int32_t> col_lsrc, col_lrnd, col_usrc, col_urnd;  // bound sources (empty without them)
     std::vector<int64_t> r_nnz;
     std::vector<int32_t> r_rows, r_cols, r_bounds;
     std::vector<float> r_ms;

@@ -13,6 +13,24 @@
 //   substitution or doubleton row i with eliminated column j (coefficient
 //     a_ij) and stored entries (k, a_ik) and right-hand side b:
 //     x_j = (b - sum_k a_ik x_k) / a_ij, the sum in stored order.
+//
+// postsolve_dual, the dual side (Sec. 2.1: the postsolve maps a primal-dual
+// solution of the reduced LP back; Sec. 3.3), for the reductions without a
+// column elimination.  Sign convention of Eq. 1 (minimise): y_i > 0 only at
+// a finite lhs, y_i < 0 only at a finite rhs, z = c - A^T y, z_j > 0 only at
+// a finite lower, z_j < 0 only at a finite upper bound.
+//   * kept rows take y through the row map, removed rows start at 0;
+//   * a bound side that a row's implied bound (S3) or singleton-row bound
+//     set is valid for the input LP only through that row: a reduced cost on
+//     it (z_j < 0 on an upper, z_j > 0 on a lower bound) moves to the row,
+//     y_r += z_j / a_rj, the row's columns' z updated (z_j becomes 0); sides
+//     latest round first, then by column, lower before upper;
+//   * a family of parallel rows (a root and every row merged into it, or
+//     into one of those; each is Lambda times the root row) acts as one
+//     dual Y = sum y_g Lambda_g on the root row; Y goes whole to the member
+//     whose own side of the orientation sign(Y) is tightest at x (smallest
+//     |a_g x - side| / max(1, |side|), then smallest row), as Y / Lambda_g;
+//   * finally z = c - A^T y over all columns (fixed and empty ones too).
 #pragma once
 #include <algorithm>
 #include <cmath>
@@ -86,6 +104,134 @@ inline const char *postsolve_primal(const PostsolveRecords &R, const double *x_r
             x_orig[j] = (R.sub_rhs[i] - sum) / R.row_val[i];
         }
     }
+    return nullptr;
+}
+
+// The dual postsolve's view of one LP: the input LP (host CSR; a side or
+// bound with |v| >= huge is infinite), the reduced LP's row map and the
+// records it reads (row kinds and parallel-row links, column kinds, bound
+// sources per column side with their rounds).
+struct DualRecords {
+    int64_t m, n, m_red;
+    const int32_t *row_ptr, *col_idx;
+    const double *val, *c, *lhs, *rhs;
+    double huge;
+    const int32_t *row_map;
+    const int32_t *row_kind, *row_aux;
+    const double *row_val;
+    const int32_t *col_kind;
+    const int32_t *lsrc, *lrnd, *usrc, *urnd;
+};
+
+// y[m], z[n] from the reduced row duals y_red[m_red] and the postsolved
+// primal x[n].  Returns nullptr, or the reason the records are unusable.
+inline const char *postsolve_dual(const DualRecords &D, const double *x, const double *y_red, double *y, double *z) {
+    constexpr int32_t kRowParallel = 4, kRowSubst = 5, kRowDoubleton = 6;
+    constexpr int32_t kColParallel = 3, kColSubst = 4, kColDoubleton = 5;
+    const int64_t m = D.m, n = D.n;
+    for (int64_t j = 0; j < n; j++)
+        if (D.col_kind[j] == kColParallel || D.col_kind[j] == kColSubst || D.col_kind[j] == kColDoubleton)
+            return "no dual postsolve for parallel columns, column singletons or doubletons";
+    for (int64_t i = 0; i < m; i++)
+        if (D.row_kind[i] == kRowSubst || D.row_kind[i] == kRowDoubleton)
+            return "no dual postsolve for parallel columns, column singletons or doubletons";
+    for (int64_t i = 0; i < m; i++) y[i] = 0.0;
+    for (int64_t k = 0; k < D.m_red; k++) {
+        const int32_t i = D.row_map[k];
+        if (i < 0 || i >= m) return "corrupt row map";
+        y[i] = y_red[k];
+    }
+    auto reduced_costs = [&]() {
+        for (int64_t j = 0; j < n; j++) z[j] = D.c[j];
+        for (int64_t i = 0; i < m; i++)
+            for (int32_t k = D.row_ptr[i]; k < D.row_ptr[i + 1]; k++) z[D.col_idx[k]] = z[D.col_idx[k]] - D.val[k] * y[i];
+    };
+    reduced_costs();
+
+    // sides set by rows: (round desc, column, lower before upper)
+    struct Side {
+        int32_t round, col, upper, row;
+    };
+    std::vector<Side> ev;
+    for (int64_t j = 0; j < n; j++) {
+        if (D.lsrc[j] >= 0) ev.push_back({D.lrnd[j], (int32_t)j, 0, D.lsrc[j]});
+        if (D.usrc[j] >= 0) ev.push_back({D.urnd[j], (int32_t)j, 1, D.usrc[j]});
+        if (D.lsrc[j] < -1 || D.usrc[j] < -1) return "a bound side without its source row";
+    }
+    std::sort(ev.begin(), ev.end(), [](const Side &a, const Side &b) {
+        if (a.round != b.round) return a.round > b.round;
+        if (a.col != b.col) return a.col < b.col;
+        return a.upper < b.upper;
+    });
+    for (const Side &e : ev) {
+        const double zj = z[e.col];
+        if (e.upper ? !(zj < 0.0) : !(zj > 0.0)) continue;
+        if (e.row >= m) return "corrupt bound source";
+        const int32_t b0 = D.row_ptr[e.row], b1 = D.row_ptr[e.row + 1];
+        double a = 0.0;
+        bool found = false;
+        for (int32_t k = b0; k < b1; k++)
+            if (D.col_idx[k] == e.col) {
+                a = D.val[k];
+                found = true;
+            }
+        if (!found || a == 0.0) return "a bound source row without the column";
+        const double d = zj / a;
+        y[e.row] = y[e.row] + d;
+        for (int32_t k = b0; k < b1; k++) z[D.col_idx[k]] = z[D.col_idx[k]] - D.val[k] * d;
+        z[e.col] = 0.0;
+    }
+
+    // parallel-row families: root and factor Lambda of every row (a_i =
+    // Lambda_i a_root: the merge factors multiplied up the links from i)
+    std::vector<double> lam(m, 1.0);
+    std::vector<std::pair<int32_t, int32_t>> fam;  // (root, member) of every family member
+    for (int64_t i = 0; i < m; i++) {
+        int64_t g = i, steps = 0;
+        double f = 1.0;
+        while (D.row_kind[g] == kRowParallel) {
+            f = f * D.row_val[g];
+            g = D.row_aux[g];
+            if (g < 0 || g >= m) return "corrupt parallel-row record";
+            if (++steps > m) return "a cycle of parallel-row merges";
+        }
+        lam[i] = f;
+        if (g != i) fam.push_back({(int32_t)g, (int32_t)i});
+    }
+    const size_t nf = fam.size();  // the roots join their families (once each)
+    for (size_t q = 0; q < nf; q++) fam.push_back({fam[q].first, fam[q].first});
+    std::sort(fam.begin(), fam.end());
+    fam.erase(std::unique(fam.begin(), fam.end()), fam.end());
+    const double inf = INFINITY;
+    auto side_of = [&](const double *v, int64_t i, double dflt) {
+        const double s = v[i];
+        return (s >= D.huge || s <= -D.huge) ? dflt : s;
+    };
+    for (size_t f0 = 0, f1; f0 < fam.size(); f0 = f1) {  // one family: fam[f0 .. f1), members in row order
+        for (f1 = f0 + 1; f1 < fam.size() && fam[f1].first == fam[f0].first;) f1++;
+        double Y = 0.0;
+        for (size_t q = f0; q < f1; q++) Y = Y + y[fam[q].second] * lam[fam[q].second];
+        for (size_t q = f0; q < f1; q++) y[fam[q].second] = 0.0;
+        if (Y == 0.0) continue;
+        int32_t best = -1;
+        double best_res = inf;
+        for (size_t q = f0; q < f1; q++) {
+            const int32_t g = fam[q].second;
+            const bool lower = (lam[g] > 0.0) == (Y > 0.0);
+            const double s = lower ? side_of(D.lhs, g, -inf) : side_of(D.rhs, g, inf);
+            if (!std::isfinite(s)) continue;
+            double act = 0.0;
+            for (int32_t k = D.row_ptr[g]; k < D.row_ptr[g + 1]; k++) act = act + D.val[k] * x[D.col_idx[k]];
+            const double res = std::fabs(act - s) / std::max(1.0, std::fabs(s));
+            if (res < best_res) {
+                best = g;
+                best_res = res;
+            }
+        }
+        if (best < 0) return "a parallel-row family without a finite side for its dual";
+        y[best] = Y / lam[best];
+    }
+    reduced_costs();
     return nullptr;
 }
 

@@ -516,6 +516,25 @@ __device__ __forceinline__ void colfin_one(const Ctx &C, int32_t j, bool full, i
         if (bad) {
             atomicMin(&C.verdict[lp * V_SLOTS + V_S3_COL], C.cmap[j]);
         } else {
+            if (C.dual_rec && has) {
+                // a side a candidate moved takes that candidate's row (a side
+                // moved only by the snap keeps its earlier source)
+                const int2 src = C.bsrc[j];
+                const double dl = dec_dbl(el), du = dec_dbl(eu);
+                if (dl > b.x || du < b.y) {
+                    int4 r = C.rec_bs[C.cmap[j]];
+                    if (dl > b.x) {
+                        r.x = src.x != INT32_MAX ? src.x : -2;  // -2: no row matched (never expected)
+                        r.y = lp_round(C, lp);
+                    }
+                    if (du < b.y) {
+                        r.z = src.y != INT32_MAX ? src.y : -2;
+                        r.w = lp_round(C, lp);
+                    }
+                    C.rec_bs[C.cmap[j]] = r;
+                }
+                C.bsrc[j] = make_int2(INT32_MAX, INT32_MAX);
+            }
             if (nl != b.x || nu != b.y) {
                 C.lu[j] = make_double2(nl, nu);
                 changed++;

@@ -40,7 +40,7 @@ class Opts(C.Structure):
                 ("max_implied", C.c_double), ("par_tol", C.c_double), ("max_rounds", C.c_int32),
                 ("dual_reductions", C.c_int32), ("par_max_iter", C.c_int32), ("parallel_cols", C.c_int32),
                 ("col_singletons", C.c_int32), ("dual_fixing", C.c_int32), ("doubletons", C.c_int32),
-                ("batch_persistent", C.c_int32), ("timing", C.c_int32),
+                ("batch_persistent", C.c_int32), ("dual_records", C.c_int32), ("timing", C.c_int32),
                 ("device", C.c_int32), ("stream", C.c_void_p)]
 
 
@@ -67,8 +67,8 @@ class ServerStats(C.Structure):
 # every symbol include/lpp.h declares
 SYMBOLS = ["lpp_opts_default", "lpp_presolve", "lpp_reduced_view", "lpp_reduced_csc", "lpp_reduced_maps",
            "lpp_result_info", "lpp_result_rows", "lpp_result_cols", "lpp_result_activity", "lpp_result_rounds",
-           "lpp_result_kernels", "lpp_result_merges", "lpp_result_substitutions", "lpp_postsolve_primal", "lpp_free_reduced", "lpp_free_postsolve",
-           "lpp_free_results",
+           "lpp_result_kernels", "lpp_result_merges", "lpp_result_substitutions", "lpp_result_bound_sources",
+           "lpp_postsolve_primal", "lpp_postsolve_dual", "lpp_free_reduced", "lpp_free_postsolve", "lpp_free_results",
            "lpp_last_error", "lpp_presolve_batch", "lpp_server_create", "lpp_server_submit", "lpp_server_take",
            "lpp_server_stats_get", "lpp_server_destroy", "lpp_row_activity_noalloc"]
 
@@ -109,6 +109,8 @@ def load():
     L.lpp_result_merges.argtypes = [P, P, P, P]
     L.lpp_result_substitutions.argtypes = [P, P, P, P, C.c_int64, P, P, C.POINTER(C.c_int64)]
     L.lpp_postsolve_primal.argtypes = [P, P, P]
+    L.lpp_result_bound_sources.argtypes = [P, P, P, P, P]
+    L.lpp_postsolve_dual.argtypes = [P, C.POINTER(LpStruct), P, P, P, P, P]
     L.lpp_free_reduced.argtypes = [P]
     L.lpp_free_reduced.restype = None
     L.lpp_free_postsolve.argtypes = [P]
@@ -364,6 +366,29 @@ class Result:
         xr = np.ascontiguousarray(x_red, np.float64)
         _check(load().lpp_postsolve_primal(self._rec, _p(xr), _p(x)))
         return x
+
+    def bound_sources(self) -> dict:
+        """Per original column the row (original index) whose implied or
+        singleton-row bound set the final lower / upper bound and its round
+        (-1 and 0: the input bound); needs dual_records=1."""
+        n = self.info.n
+        r = dict(lsrc=np.zeros(n, np.int32), lrnd=np.zeros(n, np.int32), usrc=np.zeros(n, np.int32),
+                 urnd=np.zeros(n, np.int32))
+        _check(load().lpp_result_bound_sources(self._rec, _p(r["lsrc"]), _p(r["lrnd"]), _p(r["usrc"]),
+                                               _p(r["urnd"])))
+        return r
+
+    def postsolve_dual(self, lp, x_red: np.ndarray, y_red: np.ndarray):
+        """(x, y, z) of the input LP `lp` (host arrays, the LP presolved)
+        from a reduced primal-dual pair; needs dual_records=1."""
+        m, n = self.info.m, self.info.n
+        x, y, z = np.zeros(n), np.zeros(m), np.zeros(n)
+        xr = np.ascontiguousarray(x_red, np.float64)
+        yr = np.ascontiguousarray(y_red, np.float64)
+        keep = []
+        s = lp_struct(lp, keep)
+        _check(load().lpp_postsolve_dual(self._rec, C.byref(s), _p(xr), _p(yr), _p(x), _p(y), _p(z)))
+        return x, y, z
 
     def close(self):
         L = _lib
