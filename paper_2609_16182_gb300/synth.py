@@ -700,6 +700,44 @@ def plant_doubletons(lp: LP, seed: int, count: int = 2, point=None) -> LP:
                    planted, f"{getattr(lp, 'name', 'lp')}+doubletons")
 
 
+def plant_dependent_rows(lp: LP, seed: int, count: int = 4, terms: int = 3, inconsistent: int = 0) -> LP:
+    """`lp` with `count` equality rows appended, each a combination of
+    `terms` of its equality rows (factors U[0.5, 2] with random signs,
+    coefficients summed per column, exact zeros dropped) with the same
+    combination of their right-hand sides; the last `inconsistent` of them
+    get 1 + |rhs| added to the rhs (a contradiction)."""
+    rng = np.random.default_rng(seed)
+    eq = np.flatnonzero(np.isfinite(lp.lhs) & (lp.lhs == lp.rhs) & (np.diff(lp.row_ptr) >= 2))
+    if len(eq) < terms or count <= 0:
+        return lp
+    rows = _row_of_entry(lp.row_ptr.astype(np.int64))
+    r2, c2, v2 = [rows], [lp.col_idx.astype(np.int64)], [lp.val]
+    lhs, rhs = list(lp.lhs), list(lp.rhs)
+    for t in range(count):
+        src = rng.choice(eq, size=terms, replace=False)
+        lam = rng.uniform(0.5, 2.0, size=terms) * rng.choice([-1.0, 1.0], size=terms)
+        acc: dict = {}
+        b = 0.0
+        for r, f in zip(src, lam):
+            for k in range(lp.row_ptr[r], lp.row_ptr[r + 1]):
+                acc[int(lp.col_idx[k])] = acc.get(int(lp.col_idx[k]), 0.0) + f * lp.val[k]
+            b += f * lp.rhs[r]
+        cols = np.array(sorted(j for j, v in acc.items() if v != 0.0), np.int64)
+        if t >= count - inconsistent:
+            b += 1.0 + abs(b)
+        r2.append(np.full(len(cols), lp.m + t, np.int64))
+        c2.append(cols)
+        v2.append(np.array([acc[j] for j in cols]))
+        lhs.append(b)
+        rhs.append(b)
+    m = lp.m + count
+    ptr, cc, vv = _sort_rows(np.concatenate(r2), np.concatenate(c2), np.concatenate(v2), m)
+    planted = dict(getattr(lp, "planted", None) or {})
+    planted.update(dependent_rows=np.arange(lp.m, m))
+    return _finish(m, lp.n, ptr, cc, vv, lp.c.copy(), np.array(lhs), np.array(rhs), lp.lb.copy(), lp.ub.copy(),
+                   planted, f"{getattr(lp, 'name', 'lp')}+dependent")
+
+
 # ----------------------------------------------------- vectorised 200-row mix
 def _distinct_columns(rng, lengths, n, pool=None):
     """Columns for rows of the given lengths, distinct inside each row, drawn
