@@ -374,6 +374,18 @@ def dualrec_leg(lpp, torch, dev, stream, lp):
     return opt_in_leg(lpp, torch, dev, stream, lp, "benchmark LP", "dual_records", "colfin", count)
 
 
+def deprows_leg(lpp, synth, torch, dev, stream, lp):
+    """The benchmark LP with 20 planted dependent equality rows (each a
+    combination of three of its equality rows), with the dependent-row step
+    (dep_rows: the reduced LP's equality rows eliminated on the host, the
+    rows found removed on the device) on and off."""
+    q = synth.plant_dependent_rows(lp, 0, count=20)
+    return opt_in_leg(lpp, torch, dev, stream, q, "benchmark LP + 20 planted dependent equality rows", "dep_rows",
+                      "compact_count",
+                      lambda r: {"dependent_rows": int(r.info.dep_rows), "pivot_rows": int(r.info.dep_pivots),
+                                 "stopped_at_fill_cap": int(r.info.dep_stopped)}, steps=5)
+
+
 def doubleton_leg(lpp, synth, torch, dev, stream, q):
     """The LP-relaxation workload (500k rows, 1M columns, 7.8M nonzeros,
     4% doubleton equations, 10 dense columns) with the doubleton step on and
@@ -584,6 +596,7 @@ def main():
     ap.add_argument("--no-colsing", action="store_true", help="skip the column-singletons leg")
     ap.add_argument("--no-dualfix", action="store_true", help="skip the dual-fixing leg")
     ap.add_argument("--no-dualrec", action="store_true", help="skip the dual-records leg")
+    ap.add_argument("--no-deprows", action="store_true", help="skip the dependent-rows leg")
     ap.add_argument("--no-doubletons", action="store_true", help="skip the doubleton-equations leg")
     ap.add_argument("--no-lprelax", action="store_true", help="skip the LP-relaxation workload leg")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the LP (profiling runs only)")
@@ -724,6 +737,9 @@ def main():
     dualrec = None
     if not args.no_dualrec:
         dualrec = dualrec_leg(lpp, torch, dev, stream, lp)
+    deprows = None
+    if not args.no_deprows:
+        deprows = deprows_leg(lpp, synth, torch, dev, stream, lp)
     lprelax = doubletons = None
     if not (args.no_lprelax and args.no_doubletons):
         q = synth.lprelax(0)
@@ -742,7 +758,7 @@ def main():
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
                 "batched": batched, "serving": serving, "parallel_cols": parcols, "col_singletons": colsing,
-                "dual_fixing": dualfix, "dual_records": dualrec, "doubletons": doubletons,
+                "dual_fixing": dualfix, "dual_records": dualrec, "dependent_rows": deprows, "doubletons": doubletons,
                 "lp_relaxation": lprelax}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline()

@@ -80,6 +80,8 @@ typedef enum lpp_status {
 #define LPP_ROW_PARALLEL 4    /* a multiple of a leader row, sides merged into it */
 #define LPP_ROW_SUBST 5       /* an equality row used to eliminate a column singleton */
 #define LPP_ROW_DOUBLETON 6   /* an equality a x_j + b x_k = c used to eliminate x_k  */
+#define LPP_ROW_DEPENDENT 7   /* an equality row that is a combination of other equality rows
+                                 (opts.dep_rows; Sec. 5)                            */
 /* Per-original-column record kinds. */
 #define LPP_COL_KEPT 0
 #define LPP_COL_FIXED 1       /* lb == ub: fixed at that value (primal)           */
@@ -143,6 +145,14 @@ typedef struct lpp_opts {
                                        singleton-row bound set the final bound (S3), for
                                        lpp_postsolve_dual; lpp_presolve and lpp_presolve_batch
                                        only (a server rejects it)                             */
+    int32_t dep_rows;       /* [0]     1: after the rounds, find the equality rows that are
+                                       combinations of other equality rows on the CPU
+                                       (pivoting Gaussian elimination, Sec. 5's hybrid design)
+                                       and remove them on the device with one more compaction
+                                       (S6 runs on the columns that leaves); a contradiction
+                                       among them is LPP_INFEASIBLE at its row.  Records of the
+                                       step carry round = rounds + 1.  lpp_presolve only (a
+                                       batch or a server rejects it)                          */
     int32_t timing;         /* [0]     1: time every kernel launch with CUDA events           */
     int32_t device;         /* [0]     CUDA device ordinal                                   */
     void *stream;           /* [NULL]  cudaStream_t to run on; NULL: a library-owned stream  */
@@ -168,6 +178,11 @@ typedef struct lpp_info {
     int64_t s5_left;      /* rows of S5 key groups still unmatched when the leader passes
                              stopped at opts.par_max_iter, summed over rounds (a batch:
                              the whole batch's; an LP served in the shared arena: -1)     */
+    int64_t dep_pivots;   /* opts.dep_rows: independent equality rows found (pivot rows)    */
+    int32_t dep_rows;     /* opts.dep_rows: dependent equality rows removed                 */
+    int32_t dep_stopped;  /* opts.dep_rows: 1 if the elimination stopped at its fill cap
+                             (8 stored entries per equality-row entry, at least 2^24):
+                             the rows not reached stay in the LP                         */
 } lpp_info;
 
 /* Time and traffic of one kernel family, summed over its launches

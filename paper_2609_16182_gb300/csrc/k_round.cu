@@ -247,6 +247,21 @@ __global__ void __launch_bounds__(kBlock) k_bsrc_chunks(Ctx C) {
     bsrc_row(C, ch.seg, ch.begin + threadIdx.x, ch.end, kBlock);
 }
 
+// ---------------------------------------- dependent equality rows (Sec. 5)
+// the rows the host found dependent leave with their records (the row kinds
+// of every other row were reset to kept before)
+__global__ void __launch_bounds__(kBlock) k_mark_dependent(Ctx C, const int32_t *list, int32_t cnt) {
+    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    const int32_t i = list[t];
+    C.rkind[i] = RK_DEPENDENT;
+    const int32_t o = C.rmap[i];
+    C.rec_rk[o] = RK_DEPENDENT;
+    C.rec_rr[o] = C.round;
+    C.rec_ra[o] = -1;
+    C.rec_rv[o] = 0.0;
+}
+
 // ------------------------------------------------- S3' finalise + S4 fixing
 // every column (some LP in its first round)
 __global__ void __launch_bounds__(kBlock) k_colfin(Ctx C) {
@@ -600,6 +615,10 @@ void launch_bound_src(const Ctx &C, cudaStream_t s) {
     if (g.blk_start[6] > 0) (k_bsrc_groups<<<g.blk_start[6], kBlock, 0, s>>>(C, g), note_launch());
     if (C.A.cls_start[7] > C.A.cls_start[6] && C.A.nchunks > 0)
         (k_bsrc_chunks<<<C.A.nchunks, kBlock, 0, s>>>(C), note_launch());
+}
+
+void launch_mark_dependent(const Ctx &C, const int32_t *list, int32_t cnt, cudaStream_t s) {
+    if (cnt > 0) (k_mark_dependent<<<blocks_for(cnt, kBlock), kBlock, 0, s>>>(C, list, cnt), note_launch());
 }
 
 void launch_colfin(const Ctx &C, bool full, cudaStream_t s) {

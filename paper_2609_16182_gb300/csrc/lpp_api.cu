@@ -58,7 +58,7 @@ lpp_opts resolve_opts(const lpp_opts *opts) {
         !(o.max_implied > 0) || !(o.par_tol >= 0) || (o.parallel_cols != 0 && o.parallel_cols != 1) ||
         (o.col_singletons != 0 && o.col_singletons != 1) || (o.dual_fixing != 0 && o.dual_fixing != 1) ||
         (o.doubletons != 0 && o.doubletons != 1) || (o.batch_persistent != 0 && o.batch_persistent != 1) ||
-        (o.dual_records != 0 && o.dual_records != 1))
+        (o.dual_records != 0 && o.dual_records != 1) || (o.dep_rows != 0 && o.dep_rows != 1))
         throw StatusError(LPP_ERR_INVALID, "bad options");
     return o;
 }
@@ -145,8 +145,8 @@ std::shared_ptr<DeviceRecords> take_records(Engine &E) {
         D->sub_used = (int64_t)used;
     }
     D->lu = E.lu[E.cur];
-    D->act = E.act[E.act_buf];
-    D->ninf = E.ninf[E.act_buf];
+    D->act = E.act_rec ? E.act_rec : E.act[E.act_buf];
+    D->ninf = E.ninf_rec ? E.ninf_rec : E.ninf[E.act_buf];
     for (void *p : {(void *)D->rk, (void *)D->rr, (void *)D->ra, (void *)D->rv, (void *)D->ck, (void *)D->cr,
                     (void *)D->cv, (void *)D->lu, (void *)D->act, (void *)D->ninf, (void *)D->ca, (void *)D->cp,
                     (void *)D->cm, (void *)D->sb, (void *)D->sl, (void *)D->srhs, (void *)D->scol,
@@ -164,7 +164,8 @@ std::shared_ptr<DeviceRecords> take_records(Engine &E) {
     D->owned.push_back(D->act_rmap);
     if (E.n) LPP_CUDA(cudaMemcpyAsync(D->cmap, E.cmap[E.cur], 4 * (size_t)E.n, cudaMemcpyDeviceToDevice, E.s));
     if (E.act_m)
-        LPP_CUDA(cudaMemcpyAsync(D->act_rmap, E.rmap[E.act_buf], 4 * (size_t)E.act_m, cudaMemcpyDeviceToDevice, E.s));
+        LPP_CUDA(cudaMemcpyAsync(D->act_rmap, E.rmap_rec ? E.rmap_rec : E.rmap[E.act_buf], 4 * (size_t)E.act_m,
+                                 cudaMemcpyDeviceToDevice, E.s));
     return D;
 }
 
@@ -198,6 +199,9 @@ lpp_postsolve *make_postsolve(Engine &E, const std::shared_ptr<DeviceRecords> &D
     I.nnz_processed = E.nnz_processed;
     I.launches = launch_count() - E.launches0;
     I.s5_left = E.s5_left;
+    I.dep_pivots = E.dep_pivots;
+    I.dep_rows = E.dep_found;
+    I.dep_stopped = E.dep_stopped;
     P->r_nnz = E.r_nnz;
     P->r_rows = E.r_rows;
     P->r_cols = E.r_cols;
@@ -677,6 +681,7 @@ void lpp_opts_default(lpp_opts *o) {
     o->doubletons = 0;
     o->batch_persistent = 1;
     o->dual_records = 0;
+    o->dep_rows = 0;
     o->timing = 0;
     o->device = 0;
     o->stream = nullptr;
@@ -756,6 +761,7 @@ lpp_status lpp_presolve_batch(const lpp_lp *ins, int32_t count, const lpp_opts *
             per_lp[k] = LPP_ERR_INVALID;
         }
         const lpp_opts o = resolve_opts(opts);
+        if (o.dep_rows) throw StatusError(LPP_ERR_INVALID, "dep_rows: lpp_presolve only");
         std::vector<Member> mem(count);
         int64_t ro = 0, co = 0, zo = 0;
         for (int32_t k = 0; k < count; k++) {

@@ -40,7 +40,8 @@ __host__ __device__ __forceinline__ int seg_class(int len) {
 
 // row record kinds (values of lpp.h)
 enum : uint8_t {
-    RK_KEPT = 0, RK_EMPTY = 1, RK_REDUNDANT = 2, RK_SINGLETON = 3, RK_PARALLEL = 4, RK_SUBST = 5, RK_DOUBLETON = 6
+    RK_KEPT = 0, RK_EMPTY = 1, RK_REDUNDANT = 2, RK_SINGLETON = 3, RK_PARALLEL = 4, RK_SUBST = 5, RK_DOUBLETON = 6,
+    RK_DEPENDENT = 7
 };
 // column kinds (CK_PARALLEL: merged into a parallel leader column, S5c;
 // CK_SUBST: a free column singleton eliminated through its row, S5d;

@@ -6,6 +6,7 @@
 #include <mutex>
 
 #include "lpp_engine.h"
+#include "deprows.h"
 
 namespace lpp {
 
@@ -1179,6 +1180,7 @@ void Engine::run() {
             }
         }
     }
+    if (o.dep_rows && nlp == 1 && lp_status[0] == LPP_OK) remove_dependent();
     if (t_orig) {
         finish_cols();
         finish_csc();
@@ -1188,6 +1190,86 @@ void Engine::run() {
     LPP_CUDA(cudaEventSynchronize(eend));
     LPP_CUDA(cudaEventElapsedTime(&lms, eloop, eend));
     loop_ms = lms;
+}
+
+// The dependent-row step (Sec. 5, the hybrid design): the current CSR and
+// sides go to the host, the elimination of deprows.h runs there, and the
+// rows it finds are removed on the device by one more compaction, whose S6
+// fixes the columns that then have no entry left (or every column no kept
+// row locks, with dual fixing).  Its records carry round rounds + 1; a
+// contradiction is a verdict of that round.
+void Engine::remove_dependent() {
+    const int32_t r = rounds + 1;
+    std::vector<int32_t> hp((size_t)m + 1), hi((size_t)nnz), hrmap((size_t)m);
+    std::vector<double> hv((size_t)nnz), hL((size_t)m), hU((size_t)m);
+    LPP_CUDA(cudaMemcpyAsync(hp.data(), rp[cur], 4 * ((size_t)m + 1), cudaMemcpyDeviceToHost, s));
+    if (nnz) {
+        LPP_CUDA(cudaMemcpyAsync(hi.data(), ci[cur], 4 * (size_t)nnz, cudaMemcpyDeviceToHost, s));
+        LPP_CUDA(cudaMemcpyAsync(hv.data(), rv[cur], 8 * (size_t)nnz, cudaMemcpyDeviceToHost, s));
+    }
+    if (m) {
+        LPP_CUDA(cudaMemcpyAsync(hL.data(), L[cur], 8 * (size_t)m, cudaMemcpyDeviceToHost, s));
+        LPP_CUDA(cudaMemcpyAsync(hU.data(), U[cur], 8 * (size_t)m, cudaMemcpyDeviceToHost, s));
+        LPP_CUDA(cudaMemcpyAsync(hrmap.data(), rmap[cur], 4 * (size_t)m, cudaMemcpyDeviceToHost, s));
+    }
+    LPP_CUDA(cudaStreamSynchronize(s));
+    int64_t eq_nnz = 0;
+    for (int64_t i = 0; i < m; i++)
+        if (std::isfinite(hL[i]) && hL[i] == hU[i]) eq_nnz += hp[i + 1] - hp[i];
+    DepRowsIn in{m, n, hp.data(), hi.data(), hv.data(), hL.data(), hU.data(), o.feas_tol,
+                 std::max<int64_t>(8 * eq_nnz, (int64_t)1 << 24)};
+    DepRowsOut out;
+    dependent_rows(in, out);
+    dep_pivots = out.pivots;
+    dep_stopped = out.stopped ? 1 : 0;
+    if (out.bad >= 0) {
+        lp_status[0] = LPP_INFEASIBLE;
+        lp_where[0] = LPP_WHERE_ROW;
+        lp_index[0] = hrmap[out.bad];
+        lp_round[0] = r;
+        return;
+    }
+    dep_found = (int32_t)out.dep.size();
+    if (out.dep.empty()) return;
+    int32_t *list = pool.alloc<int32_t>((int64_t)out.dep.size());
+    LPP_CUDA(cudaMemcpyAsync(list, out.dep.data(), 4 * out.dep.size(), cudaMemcpyHostToDevice, s));
+    LPP_CUDA(cudaMemsetAsync(st, 0, 8 * sizeof(int32_t), s));
+    LPP_CUDA(cudaMemsetAsync(rkind, 0, (size_t)std::max<int32_t>(m, 1), s));
+    if (n > 0) {
+        LPP_CUDA(cudaMemsetAsync(ckind, 0, (size_t)n, s));
+        LPP_CUDA(cudaMemsetAsync(cchg, 0, (size_t)n, s));
+    }
+    if (act_buf != cur) {
+        // the last round compacted: its activities and row map (the records'
+        // last-round activities) sit in the buffers this compaction writes,
+        // which therefore get fresh ones
+        act_rec = act[act_buf];
+        ninf_rec = ninf[act_buf];
+        rmap_rec = rmap[act_buf];
+        act[act_buf] = pool.alloc<double2>(m0);
+        ninf[act_buf] = pool.alloc<int2>(m0);
+        rmap[act_buf] = pool.alloc<int32_t>(m0);
+    }
+    const Ctx C = ctx(r);
+    launch_mark_dependent(C, list, (int32_t)out.dep.size(), s);
+    compact(r);
+    read_status();
+    if (st_h->err) throw StatusError(LPP_ERR_CUDA, "internal: compaction error");
+    const int32_t m_new = st_h->m_new, n_new = st_h->n_new, nnz_new = st_h->nnz_new;
+    if (nnz_new != st_h->nnz_new_t || m_new < 0 || m_new > m || n_new < 0 || n_new > n || nnz_new > nnz)
+        throw StatusError(LPP_ERR_CUDA, "internal: compaction sizes disagree");
+    m = m_new;
+    n = n_new;
+    nnz = nnz_new;
+    adopt_schedule();
+    for (int v = 0; v < V_SLOTS; v++)
+        if (verdict_h[v] != kNone) {  // S6 found an unbounded column
+            lp_status[0] = v == V_S6_COL ? LPP_UNBOUNDED : LPP_INFEASIBLE;
+            lp_where[0] = (v == V_S2_ROW || v == V_S5_ROW) ? LPP_WHERE_ROW : LPP_WHERE_COL;
+            lp_index[0] = verdict_h[v];
+            lp_round[0] = r;
+            break;
+        }
 }
 
 // The columns' one compaction when the rounds kept them in place: the

@@ -145,6 +145,14 @@ struct Engine {
     int32_t *rinv = nullptr, *cinv = nullptr, *clive = nullptr;
     uint8_t *rleft = nullptr;
     void finish_cols();  // the columns' one compaction (t_orig)
+    // opts.dep_rows: the equality rows' dependencies found on the host and
+    // the rows removed by one more compaction (single LP)
+    void remove_dependent();
+    double2 *act_rec = nullptr;  // the last round's activities and row map when that step's
+    int2 *ninf_rec = nullptr;    // compaction had to write over their buffers
+    int32_t *rmap_rec = nullptr;
+    int64_t dep_pivots = 0;
+    int32_t dep_found = 0, dep_stopped = 0;
     void finish_csc();   // the result's CSC from the input's (t_orig)
     // compaction work
     CompactCtx K;

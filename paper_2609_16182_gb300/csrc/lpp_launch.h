@@ -75,6 +75,8 @@ void split_lu(const double2 *lu, int32_t n, double *lb, double *ub, cudaStream_t
 void launch_prop(const Ctx &C, cudaStream_t s);
 // S3 bound sources (opts.dual_records), between S3 and S3'
 void launch_bound_src(const Ctx &C, cudaStream_t s);
+// rows list[0 .. cnt) (current indices) become dependent rows (kind and records, round C.round)
+void launch_mark_dependent(const Ctx &C, const int32_t *list, int32_t cnt, cudaStream_t s);
 void launch_colfin(const Ctx &C, bool full, cudaStream_t s);  // full: every column, else the touched list
 void launch_mark_dirty(const Ctx &C, int64_t nnz, cudaStream_t s);
 void launch_s5_pass(const Ctx &C, cudaStream_t s);

@@ -705,10 +705,10 @@ lpp_status lpp_server_create(size_t hbm_budget, const lpp_opts *opts, lpp_server
     if (opts) o = *opts;
     else lpp_opts_default(&o);
     if (hbm_budget < (size_t)(1 << 20)) return lpp_noalloc_fail(LPP_ERR_BUDGET, "budget below 1 MiB");
-    if (o.parallel_cols != 0 || o.col_singletons != 0 || o.doubletons != 0 || o.dual_records != 0)
+    if (o.parallel_cols != 0 || o.col_singletons != 0 || o.doubletons != 0 || o.dual_records != 0 || o.dep_rows != 0)
         return lpp_noalloc_fail(LPP_ERR_INVALID,
                                 "parallel_cols, col_singletons, doubletons, dual_records: lpp_presolve and "
-                                "lpp_presolve_batch only");
+                                "lpp_presolve_batch only; dep_rows: lpp_presolve only");
     auto *S = new lpp_server();
     try {
         S->o = o;

@@ -18,6 +18,7 @@ from . import _build
 OK, INFEASIBLE, UNBOUNDED = 0, 1, 2
 ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUDGET = -1, -2, -3, -4, -5
 ROW_KEPT, ROW_EMPTY, ROW_REDUNDANT, ROW_SINGLETON, ROW_PARALLEL, ROW_SUBST, ROW_DOUBLETON = 0, 1, 2, 3, 4, 5, 6
+ROW_DEPENDENT = 7
 COL_KEPT, COL_FIXED, COL_EMPTY, COL_PARALLEL, COL_SUBST, COL_DOUBLETON = 0, 1, 2, 3, 4, 5
 WHERE_NONE, WHERE_ROW, WHERE_COL = 0, 1, 2
 
@@ -40,7 +41,8 @@ class Opts(C.Structure):
                 ("max_implied", C.c_double), ("par_tol", C.c_double), ("max_rounds", C.c_int32),
                 ("dual_reductions", C.c_int32), ("par_max_iter", C.c_int32), ("parallel_cols", C.c_int32),
                 ("col_singletons", C.c_int32), ("dual_fixing", C.c_int32), ("doubletons", C.c_int32),
-                ("batch_persistent", C.c_int32), ("dual_records", C.c_int32), ("timing", C.c_int32),
+                ("batch_persistent", C.c_int32), ("dual_records", C.c_int32), ("dep_rows", C.c_int32),
+                ("timing", C.c_int32),
                 ("device", C.c_int32), ("stream", C.c_void_p)]
 
 
@@ -49,7 +51,8 @@ class Info(C.Structure):
                 ("rounds", C.c_int32), ("m", C.c_int32), ("n", C.c_int32), ("m_red", C.c_int32),
                 ("n_red", C.c_int32), ("nnz", C.c_int64), ("nnz_red", C.c_int64), ("obj_offset", C.c_double),
                 ("presolve_ms", C.c_double), ("nnz_processed", C.c_int64), ("launches", C.c_int64),
-                ("s5_left", C.c_int64)]
+                ("s5_left", C.c_int64), ("dep_pivots", C.c_int64), ("dep_rows", C.c_int32),
+                ("dep_stopped", C.c_int32)]
 
 
 class KernelStat(C.Structure):
