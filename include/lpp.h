@@ -302,8 +302,11 @@ lpp_status lpp_postsolve_primal(const lpp_postsolve *rec, const double *x_red, d
  * reduced solution x_red[n_red] and y_red[m_red] (reduced row order).
  * Outputs (host arrays): x_orig[n] as lpp_postsolve_primal, y_orig[m],
  * z_orig[n].  Steps: kept rows take y through the row map, removed rows 0;
- * with z = c - A^T y, bound sides set by a row (lpp_result_bound_sources)
- * are taken latest round first, then by column: a reduced cost on such a
+ * column-singleton substitution rows (opts.col_singletons), earliest round
+ * first, take (c_j - sum_r a_rj y_r) / a_ij for their eliminated column j;
+ * with z = c - A^T y, bound sides set by a row (lpp_result_bound_sources;
+ * not those of eliminated columns) are taken latest round first, then by
+ * column: a reduced cost on such a
  * side (z_j < 0 on an upper, z_j > 0 on a lower bound) moves to the row,
  * y_r += z_j / a_rj, z updated on the row's columns; then the dual Y of each
  * family of parallel rows (a row and all rows merged into it, directly or
@@ -312,9 +315,10 @@ lpp_status lpp_postsolve_primal(const lpp_postsolve *rec, const double *x_red, d
  * x_orig (smallest |a x - side| / max(1, |side|), then smallest row), as
  * Y / lambda; finally z = c - A^T y.  LPP_ERR_INVALID if the presolve ran
  * without opts.dual_records, if its result is not LPP_OK, if the LP does not
- * match the records (sizes), or if the records hold parallel-column merges,
- * column-singleton substitutions or doubletons (no dual postsolve is kept
- * for those steps). */
+ * match the records (sizes), or if the records hold doubletons (no dual
+ * postsolve is kept for that step).  Parallel-column merges need no step of
+ * their own: z = c - A^T y gives a merged column lambda times its leader's
+ * reduced cost. */
 lpp_status lpp_postsolve_dual(const lpp_postsolve *rec, const lpp_lp *lp, const double *x_red, const double *y_red,
                               double *x_orig, double *y_orig, double *z_orig);
 

@@ -35,16 +35,27 @@ of columns, Sec. 3.2 parallel rows) and for dual fixing, is:
     do not change.
   * Every other removed column (fixed, empty, dual-fixed) takes
     z_j = c_j - a_j^T y at the end, like the kept ones.
+  * Parallel columns (S5c): a column j merged into k (A_:j = lam A_:k,
+    c_j = lam c_k) gets z_j = lam z_k from the same definition, and the
+    primal postsolve puts x_k and x_j at the bounds of the merged column's
+    side when it sits at one, so no step of its own is needed.
+  * Column singletons (S5d): the substitution moved c_j(t) / a_ij times the
+    row into the other columns' costs (c_j(t): column j's cost when it went,
+    changed only by earlier substitutions).  So, before the transfers, the
+    substitution rows take, earliest round first (then by column),
+    y_i += (c_j - sum_r a_rj y_r) / a_ij over column j's input entries:
+    the eliminated (free) column keeps no reduced cost, and every other
+    column's z = c - A^T y equals its reduced-LP reduced cost.  Its own
+    bound sides are not transferred.
 
-Steps whose dual side is not restated here (parallel columns, column
-singletons, doubleton equations) make the function refuse the records.
+Doubleton equations have no dual side restated here: the function refuses
+their records.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import (COL_DOUBLETON, COL_PARALLEL, COL_SUBST, ROW_DOUBLETON, ROW_PARALLEL, ROW_SUBST,
-               postsolve_primal)
+from . import COL_DOUBLETON, COL_SUBST, ROW_DOUBLETON, ROW_PARALLEL, ROW_SUBST, postsolve_primal
 
 
 def _inf(v, huge=1e20):
@@ -63,18 +74,33 @@ def reduced_costs(lp, y):
 
 def postsolve_dual(lp, res, x_red, y_red, huge=1e20):
     """(x, y, z) of the input LP from a reduced primal-dual pair (x_red, y_red)."""
-    if (np.isin(res.col_kind, [COL_PARALLEL, COL_SUBST, COL_DOUBLETON]).any()
-            or np.isin(res.row_kind, [ROW_SUBST, ROW_DOUBLETON]).any()):
-        raise ValueError("no dual postsolve for parallel columns, column singletons or doubletons")
+    if (res.col_kind == COL_DOUBLETON).any() or (res.row_kind == ROW_DOUBLETON).any():
+        raise ValueError("no dual postsolve for doubletons")
     m, n = lp.m, lp.n
     x = postsolve_primal(res, x_red)
     y = np.zeros(m)
     y[np.asarray(res.row_map, np.int64)] = np.asarray(y_red, np.float64)
+
+    # column singletons (S5d), earliest round first, then by column: the
+    # substitution row takes the dual that leaves the eliminated column no
+    # reduced cost
+    colrows = {}
+    for i in range(m):
+        for k in range(int(lp.row_ptr[i]), int(lp.row_ptr[i + 1])):
+            colrows.setdefault(int(lp.col_idx[k]), []).append((i, float(lp.val[k])))
+    subs = sorted((int(res.row_round[i]), int(res.row_aux[i]), i) for i in range(m) if res.row_kind[i] == ROW_SUBST)
+    for _, j, i in subs:
+        zj = float(lp.c[j])
+        for r, a in colrows.get(j, []):
+            zj -= a * y[r]
+        y[i] += zj / float(res.row_val[i])
     z = reduced_costs(lp, y)
 
     # bound sides set by a row, latest round first, then column, lower first
     events = []
     for j in range(n):
+        if res.col_kind[j] == COL_SUBST:
+            continue  # its substitution row carries its reduced cost
         if res.col_lsrc[j] >= 0:
             events.append((-int(res.col_lrnd[j]), j, 0, int(res.col_lsrc[j])))
         if res.col_usrc[j] >= 0:

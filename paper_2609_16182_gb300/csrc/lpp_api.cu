@@ -1130,6 +1130,7 @@ lpp_status lpp_postsolve_dual(const lpp_postsolve *Pc, const lpp_lp *lp, const d
     D.huge = P->huge;
     D.row_map = row_map.data();
     D.row_kind = P->row_kind.data();
+    D.row_round = P->row_round.data();
     D.row_aux = P->row_aux.data();
     D.row_val = P->row_val.data();
     D.col_kind = P->col_kind.data();

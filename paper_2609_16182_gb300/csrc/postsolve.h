@@ -20,6 +20,11 @@
 // a finite lhs, y_i < 0 only at a finite rhs, z = c - A^T y, z_j > 0 only at
 // a finite lower, z_j < 0 only at a finite upper bound.
 //   * kept rows take y through the row map, removed rows start at 0;
+//   * column singletons (S5d), earliest round first: the substitution row
+//     takes (c_j - sum_r a_rj y_r) / a_ij, which leaves the eliminated
+//     (free) column no reduced cost and every other column the reduced
+//     LP's (the substitution moved c_j / a_ij times the row into their
+//     costs); its own bound sides are not transferred;
 //   * a bound side that a row's implied bound (S3) or singleton-row bound
 //     set is valid for the input LP only through that row: a reduced cost on
 //     it (z_j < 0 on an upper, z_j > 0 on a lower bound) moves to the row,
@@ -30,7 +35,11 @@
 //     dual Y = sum y_g Lambda_g on the root row; Y goes whole to the member
 //     whose own side of the orientation sign(Y) is tightest at x (smallest
 //     |a_g x - side| / max(1, |side|), then smallest row), as Y / Lambda_g;
-//   * finally z = c - A^T y over all columns (fixed and empty ones too).
+//   * finally z = c - A^T y over all columns (fixed and empty ones too); a
+//     column merged into a parallel leader (S5c) gets lam times the
+//     leader's z that way, and the primal postsolve has put both at the
+//     bounds of the merged column's side.
+//   Doubletons have no dual side here (refused).
 #pragma once
 #include <algorithm>
 #include <cmath>
@@ -109,15 +118,16 @@ inline const char *postsolve_primal(const PostsolveRecords &R, const double *x_r
 
 // The dual postsolve's view of one LP: the input LP (host CSR; a side or
 // bound with |v| >= huge is infinite), the reduced LP's row map and the
-// records it reads (row kinds and parallel-row links, column kinds, bound
-// sources per column side with their rounds).
+// records it reads (row kinds, rounds, parallel-row links and substitution
+// coefficients, column kinds, bound sources per column side with their
+// rounds).
 struct DualRecords {
     int64_t m, n, m_red;
     const int32_t *row_ptr, *col_idx;
     const double *val, *c, *lhs, *rhs;
     double huge;
     const int32_t *row_map;
-    const int32_t *row_kind, *row_aux;
+    const int32_t *row_kind, *row_round, *row_aux;
     const double *row_val;
     const int32_t *col_kind;
     const int32_t *lsrc, *lrnd, *usrc, *urnd;
@@ -127,19 +137,55 @@ struct DualRecords {
 // primal x[n].  Returns nullptr, or the reason the records are unusable.
 inline const char *postsolve_dual(const DualRecords &D, const double *x, const double *y_red, double *y, double *z) {
     constexpr int32_t kRowParallel = 4, kRowSubst = 5, kRowDoubleton = 6;
-    constexpr int32_t kColParallel = 3, kColSubst = 4, kColDoubleton = 5;
+    constexpr int32_t kColSubst = 4, kColDoubleton = 5;
     const int64_t m = D.m, n = D.n;
     for (int64_t j = 0; j < n; j++)
-        if (D.col_kind[j] == kColParallel || D.col_kind[j] == kColSubst || D.col_kind[j] == kColDoubleton)
-            return "no dual postsolve for parallel columns, column singletons or doubletons";
+        if (D.col_kind[j] == kColDoubleton) return "no dual postsolve for doubletons";
     for (int64_t i = 0; i < m; i++)
-        if (D.row_kind[i] == kRowSubst || D.row_kind[i] == kRowDoubleton)
-            return "no dual postsolve for parallel columns, column singletons or doubletons";
+        if (D.row_kind[i] == kRowDoubleton) return "no dual postsolve for doubletons";
     for (int64_t i = 0; i < m; i++) y[i] = 0.0;
     for (int64_t k = 0; k < D.m_red; k++) {
         const int32_t i = D.row_map[k];
         if (i < 0 || i >= m) return "corrupt row map";
         y[i] = y_red[k];
+    }
+    // column singletons (S5d), earliest round first, then by column: the
+    // substitution row takes (c_j - sum_r a_rj y_r) / a_ij over column j's
+    // input entries (rows in order), so the eliminated column keeps no
+    // reduced cost and every other column's z is its reduced-LP one
+    struct Sub {
+        int32_t round, col, row;
+    };
+    std::vector<Sub> subs;
+    for (int64_t i = 0; i < m; i++)
+        if (D.row_kind[i] == kRowSubst) {
+            if (D.row_aux[i] < 0 || D.row_aux[i] >= n || D.row_val[i] == 0.0) return "corrupt substitution record";
+            subs.push_back({D.row_round[i], D.row_aux[i], (int32_t)i});
+        }
+    if (!subs.empty()) {
+        std::sort(subs.begin(), subs.end(), [](const Sub &a, const Sub &b) {
+            if (a.round != b.round) return a.round < b.round;
+            return a.col < b.col;
+        });
+        // the input's columns (entries in row order): a counting sort by column
+        std::vector<int64_t> cp((size_t)n + 1, 0);
+        const int64_t nnz = D.row_ptr[m];
+        for (int64_t k = 0; k < nnz; k++) cp[(size_t)D.col_idx[k] + 1]++;
+        for (int64_t j = 0; j < n; j++) cp[(size_t)j + 1] += cp[(size_t)j];
+        std::vector<int64_t> fill(cp.begin(), cp.end() - 1);
+        std::vector<int32_t> crow((size_t)nnz);
+        std::vector<double> cval((size_t)nnz);
+        for (int64_t i = 0; i < m; i++)
+            for (int32_t k = D.row_ptr[i]; k < D.row_ptr[i + 1]; k++) {
+                const int64_t q = fill[(size_t)D.col_idx[k]]++;
+                crow[(size_t)q] = (int32_t)i;
+                cval[(size_t)q] = D.val[k];
+            }
+        for (const Sub &e : subs) {
+            double zj = D.c[e.col];
+            for (int64_t q = cp[(size_t)e.col]; q < cp[(size_t)e.col + 1]; q++) zj = zj - cval[(size_t)q] * y[crow[(size_t)q]];
+            y[e.row] = y[e.row] + zj / D.row_val[e.row];
+        }
     }
     auto reduced_costs = [&]() {
         for (int64_t j = 0; j < n; j++) z[j] = D.c[j];
@@ -154,6 +200,7 @@ inline const char *postsolve_dual(const DualRecords &D, const double *x, const d
     };
     std::vector<Side> ev;
     for (int64_t j = 0; j < n; j++) {
+        if (D.col_kind[j] == kColSubst) continue;  // its substitution row carries its reduced cost
         if (D.lsrc[j] >= 0) ev.push_back({D.lrnd[j], (int32_t)j, 0, D.lsrc[j]});
         if (D.usrc[j] >= 0) ev.push_back({D.urnd[j], (int32_t)j, 1, D.usrc[j]});
         if (D.lsrc[j] < -1 || D.usrc[j] < -1) return "a bound side without its source row";

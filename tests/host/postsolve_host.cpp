@@ -22,11 +22,12 @@ extern "C" int32_t postsolve_host(int64_t n, int64_t m, int64_t n_red, const int
 extern "C" int32_t postsolve_dual_host(int64_t m, int64_t n, int64_t m_red, const int32_t *row_ptr,
                                        const int32_t *col_idx, const double *val, const double *c,
                                        const double *lhs, const double *rhs, double huge, const int32_t *row_map,
-                                       const int32_t *row_kind, const int32_t *row_aux, const double *row_val,
+                                       const int32_t *row_kind, const int32_t *row_round,
+                                       const int32_t *row_aux, const double *row_val,
                                        const int32_t *col_kind, const int32_t *lsrc, const int32_t *lrnd,
                                        const int32_t *usrc, const int32_t *urnd, const double *x,
                                        const double *y_red, double *y, double *z) {
-    lpp::DualRecords D{m,       n,       m_red,    row_ptr,  col_idx, val,  c,    lhs,  rhs,  huge,
-                       row_map, row_kind, row_aux, row_val, col_kind, lsrc, lrnd, usrc, urnd};
+    lpp::DualRecords D{m,        n,         m_red,   row_ptr, col_idx,  val,  c,    lhs,  rhs, huge,
+                       row_map,  row_kind,  row_round, row_aux, row_val, col_kind, lsrc, lrnd, usrc, urnd};
     return lpp::postsolve_dual(D, x, y_red, y, z) ? -1 : 0;
 }

@@ -2,7 +2,8 @@
 lpp_postsolve_dual) built for the host and run on the oracle's records and a
 reduced optimum from HiGHS: the same duals and reduced costs as the oracle's
 dual postsolve (oracle/dual.py), bit for bit, and a KKT point of the input
-LP.  Refusals: records of steps without a dual postsolve.  No GPU needed."""
+LP, with and without parallel-column merges and column-singleton
+substitutions.  Refusal: records of doubletons (no dual postsolve).  No GPU needed."""
 import ctypes as C
 import os
 import shutil
@@ -38,7 +39,8 @@ def run(L, lp, o, x, y_red):
     assert np.array_equal(row_map, o.row_map)  # the reduced rows are the kept rows in order
     arrs = [a(lp.row_ptr, np.int32), a(lp.col_idx, np.int32), a(lp.val, float), a(lp.c, float), a(lp.lhs, float),
             a(lp.rhs, float)]
-    recs = [row_map, a(o.row_kind, np.int32), a(o.row_aux, np.int32), a(o.row_val, float), a(o.col_kind, np.int32),
+    recs = [row_map, a(o.row_kind, np.int32), a(o.row_round, np.int32), a(o.row_aux, np.int32), a(o.row_val, float),
+            a(o.col_kind, np.int32),
             a(o.col_lsrc, np.int32), a(o.col_lrnd, np.int32), a(o.col_usrc, np.int32), a(o.col_urnd, np.int32),
             a(x, float), a(y_red, float)]
     y, z = np.full(lp.m, np.nan), np.full(lp.n, np.nan)
@@ -58,7 +60,11 @@ class _Red:
 CASES = [("tiny", lambda s: synth.tiny(s), {}), ("mix", lambda s: synth.mix(s), {}),
          ("late_parallel", lambda s: synth.late_parallel(s, pairs=40), {}),
          ("dual_fixing", lambda s: synth.mix(s), {"dual_fixing": 1}),
-         ("skewed", lambda s: synth.skewed(s, m=3000, n=4500, target_nnz=30000, row_cap=2000), {})]
+         ("skewed", lambda s: synth.skewed(s, m=3000, n=4500, target_nnz=30000, row_cap=2000), {}),
+         ("parallel_cols", lambda s: synth.parcols(s), {"parallel_cols": 1}),
+         ("col_singletons", lambda s: synth.plant_col_singletons(synth.tiny(s), s), {"col_singletons": 1}),
+         ("all but doubletons", lambda s: synth.plant_col_singletons(synth.parcols(s), s),
+          {"col_singletons": 1, "parallel_cols": 1, "dual_fixing": 1})]
 
 
 @pytest.mark.parametrize("name, make_lp, kw", CASES, ids=[c[0] for c in CASES])
@@ -84,8 +90,8 @@ def test_matches_the_oracle_and_is_optimal(lib, name, make_lp, kw):
 
 
 def test_refuses_records_without_a_dual_postsolve(lib):
-    lp = synth.parcols(2)
-    o = oracle.presolve(lp, oracle.default_opts(parallel_cols=1))
-    assert (o.col_kind == oracle.COL_PARALLEL).any()
+    lp = synth.plant_doubletons(synth.tiny(5), 5, count=6)
+    o = oracle.presolve(lp, oracle.default_opts(doubletons=1))
+    assert (o.col_kind == oracle.COL_DOUBLETON).any()
     rc, _, _ = run(lib, lp, o, np.zeros(lp.n), np.zeros(o.m_red))
     assert rc == -1

@@ -38,6 +38,10 @@ def _cases():
             ("skewed_long", synth.skewed(4, m=8000, n=12000, target_nnz=90_000, row_cap=9000), {}),
             ("lprelax", synth.lprelax(1, m=3000, n=6000, target_nnz=40000, n_dense=2, dense_len=2500), {}),
             ("dualfix", synth.mix(5), {"dual_fixing": 1}),
+            ("parcols", synth.parcols(0), {"parallel_cols": 1}),
+            ("colsing", synth.plant_col_singletons(synth.tiny(0), 0), {"col_singletons": 1}),
+            ("colsing + parcols + dual fixing", synth.plant_col_singletons(synth.parcols(1), 1),
+             {"col_singletons": 1, "parallel_cols": 1, "dual_fixing": 1}),
             ("follower_transfer", make([{0: 1.0, 1: 1.0}, {0: 2.0, 1: 2.0}], [-INF, -INF], [10.0, 8.0], [0, 0],
                                        [10, 10], c=[-2.0, -1.0]), {})]
     return out
@@ -122,10 +126,11 @@ def test_refusals():
         r.bound_sources()
     with pytest.raises(lpp.LppError):
         r.postsolve_dual(lp, np.zeros(r.info.n_red), np.zeros(r.info.m_red))
-    p = lpp.presolve(synth.parcols(2), dual_records=1, parallel_cols=1)
-    assert (p.col_kind == lpp.COL_PARALLEL).any()
+    db = synth.plant_doubletons(synth.tiny(5), 5, count=6)
+    p = lpp.presolve(db, dual_records=1, doubletons=1)
+    assert (p.col_kind == lpp.COL_DOUBLETON).any()
     with pytest.raises(lpp.LppError):
-        p.postsolve_dual(synth.parcols(2), np.zeros(p.info.n_red), np.zeros(p.info.m_red))
+        p.postsolve_dual(db, np.zeros(p.info.n_red), np.zeros(p.info.m_red))
     d = lpp.presolve(lp, dual_records=1)
     with pytest.raises(lpp.LppError):  # another LP's sizes
         d.postsolve_dual(synth.micro(0), np.zeros(d.info.n_red), np.zeros(d.info.m_red))

@@ -42,7 +42,13 @@ def _cases():
     out += [(f"late{s}", synth.late_parallel(s, pairs=40), {}) for s in range(2)]
     out += [("skewed", synth.skewed(3, m=3000, n=4500, target_nnz=30000, row_cap=2000), {}),
             ("lprelax", synth.lprelax(1, m=3000, n=6000, target_nnz=40000, n_dense=2, dense_len=1000), {}),
-            ("dualfix", synth.mix(5), {"dual_fixing": 1})]
+            ("dualfix", synth.mix(5), {"dual_fixing": 1}),
+            ("parcols0", synth.parcols(0), {"parallel_cols": 1}),
+            ("parcols3 + planted", synth.plant_parallel_cols(synth.tiny(3), 3, frac=0.05), {"parallel_cols": 1}),
+            ("colsing0", synth.plant_col_singletons(synth.tiny(0), 0), {"col_singletons": 1}),
+            ("colsing2 free", synth.plant_col_singletons(synth.mix(3), 2, frac=0.5, free_frac=1.0), {"col_singletons": 1}),
+            ("colsing + parcols + dual fixing", synth.plant_col_singletons(synth.parcols(1), 1),
+             {"col_singletons": 1, "parallel_cols": 1, "dual_fixing": 1})]
     from lpmake import make
     # row 1 implies x0, x1 <= 4 in round 1 and is then merged into row 0
     # (twice row 0): a transfer lands on a merged row
@@ -236,6 +242,8 @@ _MUTANTS = [
     ("loosest member", "            if rres < best_res:\n", "            if best < 0 or rres > best_res:\n"),
     ("family dual summed unscaled", "        Y = sum(y[g] * lam[g] for g in mem)\n",
      "        Y = sum(y[g] for g in mem)\n"),
+    ("substitution rows keep no dual", "        y[i] += zj / float(res.row_val[i])\n", "        pass\n"),
+    ("substitution dual from the cost alone", "            zj -= a * y[r]\n", "            pass\n"),
 ]
 
 
