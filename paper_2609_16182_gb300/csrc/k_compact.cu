@@ -183,17 +183,17 @@ __global__ void __launch_bounds__(kBlock) k_locks_long(Ctx C, CompactCtx K) {
 // With the input CSC kept (Ctx::t_orig) the columns also stay in place: a
 // column that left in an earlier round (cinv < 0) is skipped, the others
 // keep their index (c_new = j), and one that leaves now gets cinv = -1.
+// (grid-stride over a grid of at most 8 blocks per SM: one block sum per block)
 __global__ void __launch_bounds__(kBlock) k_colkeep(Ctx C, CompactCtx K) {
-    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     int32_t fixed = 0;
-    if (j < C.n) {
+    for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < C.n; j += gridDim.x * blockDim.x) {
         if (C.t_orig && (C.cinv[j] < 0 || (C.ckind[j] == CK_KEPT && K.c_len[j] > 0 && !K.lp_dead[lp_of_col(C, j)]))) {
             // columns in place: one that left earlier keeps the flags it got
             // then (its contribution was consumed by the objective sum), and a
             // kept column with entries that S4 did not fix stays as it is
             // (no S6 test applies to it, its contribution is zero)
         } else {
-            fixed = colkeep_one(C, K, j);
+            fixed += colkeep_one(C, K, j);
             if (C.t_orig) {
                 const bool kp = K.c_keep[j] != 0;
                 K.c_new[j] = kp ? j : -1;
@@ -667,7 +667,7 @@ void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s) {
         if (gt.blk_start[6] > 0) (k_locks_groups<<<gt.blk_start[6], kBlock, 0, s>>>(C, K, gt), note_launch());
         if (tlong > 0 && C.T.nchunks > 0) (k_locks_long<<<C.T.nchunks, kBlock, 0, s>>>(C, K), note_launch());
     }
-    if (C.n > 0) (k_colkeep<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C, K), note_launch());
+    if (C.n > 0) (k_colkeep<<<std::min<unsigned>(blocks_for(C.n, kBlock), 8u * 152u), kBlock, 0, s>>>(C, K), note_launch());
     // 2. row counts over kept columns and the side shifts
     if (ga.blk_start[6] > 0) (k_csr_count_groups<<<ga.blk_start[6], kBlock, 0, s>>>(C, K, ga), note_launch());
     if (along > 0 && C.A.nchunks > 0) {

@@ -264,10 +264,12 @@ __global__ void __launch_bounds__(kBlock) k_mark_dependent(Ctx C, const int32_t 
 
 // ------------------------------------------------- S3' finalise + S4 fixing
 // every column (some LP in its first round)
+// (grid-stride over a grid of at most 8 blocks per SM: the block sums run
+// once per block, not once per 256 columns)
 __global__ void __launch_bounds__(kBlock) k_colfin(Ctx C) {
-    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     int32_t changed = 0, fixed = 0, chg_nnz = 0;
-    if (j < C.n) colfin_one(C, j, true, changed, fixed, chg_nnz);
+    for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < C.n; j += gridDim.x * blockDim.x)
+        colfin_one(C, j, true, changed, fixed, chg_nnz);
     block_add(changed, &C.st->bounds_changed);
     block_add(fixed, &C.st->cols_fixed);
     block_add(chg_nnz, C.cl_nnz);
@@ -287,15 +289,15 @@ __global__ void __launch_bounds__(kBlock) k_colfin_list(Ctx C) {
 
 // ------------------------------------------------------------ S5 parallel rows
 // first pass: rows kept by S2 with >= 2 entries take part
+// (grid-stride, one block sum per block)
 __global__ void __launch_bounds__(kBlock) k_s5_insert(Ctx C) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     int32_t part = 0;
-    if (i < C.m) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < C.m; i += gridDim.x * blockDim.x) {
         int32_t slot = -1;
         if (C.rkind[i] == RK_KEPT && C.A.ptr[i + 1] - C.A.ptr[i] >= 2) slot = s5_insert_row(C, i, (uint32_t)C.tcap);
         C.rslot[i] = slot;
         C.rwork[i] = slot >= 0 ? 1 : 0;
-        part = slot >= 0;
+        part += slot >= 0;
     }
     block_add(part, &C.st->participants);
 }
@@ -623,7 +625,7 @@ void launch_mark_dependent(const Ctx &C, const int32_t *list, int32_t cnt, cudaS
 
 void launch_colfin(const Ctx &C, bool full, cudaStream_t s) {
     if (C.n <= 0) return;
-    if (full) (k_colfin<<<blocks_for(C.n, kBlock), kBlock, 0, s>>>(C), note_launch());
+    if (full) (k_colfin<<<std::min<unsigned>(blocks_for(C.n, kBlock), 8u * 152u), kBlock, 0, s>>>(C), note_launch());
     else (k_colfin_list<<<std::min<unsigned>(blocks_for(C.n, kBlock), 8u * 152u), kBlock, 0, s>>>(C), note_launch());
 }
 
@@ -636,7 +638,7 @@ void launch_mark_dirty(const Ctx &C, int64_t nnz, cudaStream_t s) {
 
 void launch_s5_pass(const Ctx &C, cudaStream_t s) {
     if (C.m == 0) return;
-    (k_s5_insert<<<blocks_for(C.m, kBlock), kBlock, 0, s>>>(C), note_launch());
+    (k_s5_insert<<<std::min<unsigned>(blocks_for(C.m, kBlock), 8u * 152u), kBlock, 0, s>>>(C), note_launch());
     const GroupGrid g = group_grid(C.A);
     if (g.blk_start[6] > 0) (k_s5_match_groups<<<g.blk_start[6], kBlock, 0, s>>>(C, g), note_launch());
     const int32_t nlong = C.A.cls_start[7] - C.A.cls_start[6];
