@@ -383,6 +383,7 @@ def deprows_leg(lpp, synth, torch, dev, stream, lp):
     return opt_in_leg(lpp, torch, dev, stream, q, "benchmark LP + 20 planted dependent equality rows", "dep_rows",
                       "compact_count",
                       lambda r: {"dependent_rows": int(r.info.dep_rows), "pivot_rows": int(r.info.dep_pivots),
+                                 "peeled_rows": int(r.info.dep_peeled),
                                  "stopped_at_fill_cap": int(r.info.dep_stopped)}, steps=5)
 
 

@@ -147,7 +147,9 @@ typedef struct lpp_opts {
                                        only (a server rejects it)                             */
     int32_t dep_rows;       /* [0]     1: after the rounds, find the equality rows that are
                                        combinations of other equality rows on the CPU
-                                       (pivoting Gaussian elimination, Sec. 5's hybrid design)
+                                       (rows holding a column no other equality row holds
+                                       peeled, then pivoting Gaussian elimination, Sec. 5's
+                                       hybrid design)
                                        and remove them on the device with one more compaction
                                        (S6 runs on the columns that leaves); a contradiction
                                        among them is LPP_INFEASIBLE at its row.  Records of the
@@ -178,7 +180,9 @@ typedef struct lpp_info {
     int64_t s5_left;      /* rows of S5 key groups still unmatched when the leader passes
                              stopped at opts.par_max_iter, summed over rounds (a batch:
                              the whole batch's; an LP served in the shared arena: -1)     */
-    int64_t dep_pivots;   /* opts.dep_rows: independent equality rows found (pivot rows)    */
+    int64_t dep_pivots;   /* opts.dep_rows: pivot rows of the elimination                   */
+    int64_t dep_peeled;   /* opts.dep_rows: equality rows peeled before it (each holds a
+                             column no other equality row holds: in no dependency)        */
     int32_t dep_rows;     /* opts.dep_rows: dependent equality rows removed                 */
     int32_t dep_stopped;  /* opts.dep_rows: 1 if the elimination stopped at its fill cap
                              (8 stored entries per equality-row entry, at least 2^24):

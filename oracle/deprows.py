@@ -9,8 +9,12 @@ elimination (each pivot chosen numerically from the values the eliminations
 before it produced), and the result goes back for the rest of presolve.  The
 reading restated here, applied once after the presolve loop:
 
-  * The equality rows (finite lhs == rhs) of the reduced LP are taken in
-    row order.  Each is reduced against the pivot rows found so far, in the
+  * The equality rows (finite lhs == rhs) of the reduced LP are peeled
+    first: a row holding a column that no other equality row still holds
+    is in no linear dependency (that column's multiple would have to
+    vanish), so it leaves, and its columns' counts drop; this repeats until
+    every row left shares all its columns.  The rows left are taken in row
+    order.  Each is reduced against the pivot rows found so far, in the
     order they were found: for a pivot row p with pivot column q and the
     current row w with w_q != 0, f = w_q / p_q, w := w - f p (element by
     element), w_q := 0, b := b - f b_p.
@@ -38,15 +42,39 @@ from . import COL_EMPTY, COL_KEPT, INFEASIBLE, OK, ROW_KEPT, UNBOUNDED, WHERE_CO
 ROW_DEPENDENT = 7
 
 
+def core_rows(red):
+    """The equality rows left after peeling (in row order) and the number
+    peeled."""
+    m, n = len(red.lhs), len(red.c)
+    eq = [i for i in range(m) if np.isfinite(red.lhs[i]) and red.lhs[i] == red.rhs[i]]
+    cnt = np.zeros(n, np.int64)
+    for i in eq:
+        for k in range(int(red.row_ptr[i]), int(red.row_ptr[i + 1])):
+            cnt[red.col_idx[k]] += 1
+    alive = {i: True for i in eq}
+    changed = True
+    while changed:
+        changed = False
+        for i in eq:
+            if not alive[i]:
+                continue
+            cols = red.col_idx[int(red.row_ptr[i]):int(red.row_ptr[i + 1])]
+            if len(cols) and np.any(cnt[cols] == 1):
+                alive[i] = False
+                cnt[cols] -= 1
+                changed = True
+    core = [i for i in eq if alive[i]]
+    return core, len(eq) - len(core)
+
+
 def dependent_rows(red, dep_tol=1e-9):
     """(reduced indices of the dependent equality rows, the first
-    inconsistent one or -1, the number of pivot rows)."""
-    m, n = len(red.lhs), len(red.c)
+    inconsistent one or -1, the number of pivot rows among the rows left
+    after peeling)."""
+    n = len(red.c)
     pivots = []  # (column, dense row, rhs)
     dep, bad = [], -1
-    for i in range(m):
-        if not (np.isfinite(red.lhs[i]) and red.lhs[i] == red.rhs[i]):
-            continue
+    for i in core_rows(red)[0]:
         w = np.zeros(n)
         k0, k1 = int(red.row_ptr[i]), int(red.row_ptr[i + 1])
         w[red.col_idx[k0:k1]] = red.val[k0:k1]

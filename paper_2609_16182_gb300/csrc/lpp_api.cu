@@ -200,6 +200,7 @@ lpp_postsolve *make_postsolve(Engine &E, const std::shared_ptr<DeviceRecords> &D
     I.launches = launch_count() - E.launches0;
     I.s5_left = E.s5_left;
     I.dep_pivots = E.dep_pivots;
+    I.dep_peeled = E.dep_peeled;
     I.dep_rows = E.dep_found;
     I.dep_stopped = E.dep_stopped;
     P->r_nnz = E.r_nnz;

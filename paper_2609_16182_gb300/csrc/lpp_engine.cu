@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 
 #include "lpp_engine.h"
@@ -1193,34 +1194,39 @@ void Engine::run() {
 }
 
 // The dependent-row step (Sec. 5, the hybrid design): the current CSR and
-// sides go to the host, the elimination of deprows.h runs there, and the
+// sides go to the host, the peeling and elimination of deprows.h run there,
+// and the
 // rows it finds are removed on the device by one more compaction, whose S6
 // fixes the columns that then have no entry left (or every column no kept
 // row locks, with dual fixing).  Its records carry round rounds + 1; a
 // contradiction is a verdict of that round.
 void Engine::remove_dependent() {
     const int32_t r = rounds + 1;
-    std::vector<int32_t> hp((size_t)m + 1), hi((size_t)nnz), hrmap((size_t)m);
-    std::vector<double> hv((size_t)nnz), hL((size_t)m), hU((size_t)m);
-    LPP_CUDA(cudaMemcpyAsync(hp.data(), rp[cur], 4 * ((size_t)m + 1), cudaMemcpyDeviceToHost, s));
+    // host copies, left uninitialised until the copies fill them
+    std::unique_ptr<int32_t[]> hp(new int32_t[(size_t)m + 1]), hi(new int32_t[(size_t)nnz + 1]),
+        hrmap(new int32_t[(size_t)m + 1]);
+    std::unique_ptr<double[]> hv(new double[(size_t)nnz + 1]), hL(new double[(size_t)m + 1]),
+        hU(new double[(size_t)m + 1]);
+    LPP_CUDA(cudaMemcpyAsync(hp.get(), rp[cur], 4 * ((size_t)m + 1), cudaMemcpyDeviceToHost, s));
     if (nnz) {
-        LPP_CUDA(cudaMemcpyAsync(hi.data(), ci[cur], 4 * (size_t)nnz, cudaMemcpyDeviceToHost, s));
-        LPP_CUDA(cudaMemcpyAsync(hv.data(), rv[cur], 8 * (size_t)nnz, cudaMemcpyDeviceToHost, s));
+        LPP_CUDA(cudaMemcpyAsync(hi.get(), ci[cur], 4 * (size_t)nnz, cudaMemcpyDeviceToHost, s));
+        LPP_CUDA(cudaMemcpyAsync(hv.get(), rv[cur], 8 * (size_t)nnz, cudaMemcpyDeviceToHost, s));
     }
     if (m) {
-        LPP_CUDA(cudaMemcpyAsync(hL.data(), L[cur], 8 * (size_t)m, cudaMemcpyDeviceToHost, s));
-        LPP_CUDA(cudaMemcpyAsync(hU.data(), U[cur], 8 * (size_t)m, cudaMemcpyDeviceToHost, s));
-        LPP_CUDA(cudaMemcpyAsync(hrmap.data(), rmap[cur], 4 * (size_t)m, cudaMemcpyDeviceToHost, s));
+        LPP_CUDA(cudaMemcpyAsync(hL.get(), L[cur], 8 * (size_t)m, cudaMemcpyDeviceToHost, s));
+        LPP_CUDA(cudaMemcpyAsync(hU.get(), U[cur], 8 * (size_t)m, cudaMemcpyDeviceToHost, s));
+        LPP_CUDA(cudaMemcpyAsync(hrmap.get(), rmap[cur], 4 * (size_t)m, cudaMemcpyDeviceToHost, s));
     }
     LPP_CUDA(cudaStreamSynchronize(s));
     int64_t eq_nnz = 0;
     for (int64_t i = 0; i < m; i++)
         if (std::isfinite(hL[i]) && hL[i] == hU[i]) eq_nnz += hp[i + 1] - hp[i];
-    DepRowsIn in{m, n, hp.data(), hi.data(), hv.data(), hL.data(), hU.data(), o.feas_tol,
+    DepRowsIn in{m, n, hp.get(), hi.get(), hv.get(), hL.get(), hU.get(), o.feas_tol,
                  std::max<int64_t>(8 * eq_nnz, (int64_t)1 << 24)};
     DepRowsOut out;
     dependent_rows(in, out);
     dep_pivots = out.pivots;
+    dep_peeled = out.peeled;
     dep_stopped = out.stopped ? 1 : 0;
     if (out.bad >= 0) {
         lp_status[0] = LPP_INFEASIBLE;

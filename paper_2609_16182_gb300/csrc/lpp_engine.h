@@ -151,7 +151,7 @@ struct Engine {
     double2 *act_rec = nullptr;  // the last round's activities and row map when that step's
     int2 *ninf_rec = nullptr;    // compaction had to write over their buffers
     int32_t *rmap_rec = nullptr;
-    int64_t dep_pivots = 0;
+    int64_t dep_pivots = 0, dep_peeled = 0;
     int32_t dep_found = 0, dep_stopped = 0;
     void finish_csc();   // the result's CSC from the input's (t_orig)
     // compaction work

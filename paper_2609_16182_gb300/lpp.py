@@ -51,7 +51,7 @@ class Info(C.Structure):
                 ("rounds", C.c_int32), ("m", C.c_int32), ("n", C.c_int32), ("m_red", C.c_int32),
                 ("n_red", C.c_int32), ("nnz", C.c_int64), ("nnz_red", C.c_int64), ("obj_offset", C.c_double),
                 ("presolve_ms", C.c_double), ("nnz_processed", C.c_int64), ("launches", C.c_int64),
-                ("s5_left", C.c_int64), ("dep_pivots", C.c_int64), ("dep_rows", C.c_int32),
+                ("s5_left", C.c_int64), ("dep_pivots", C.c_int64), ("dep_peeled", C.c_int64), ("dep_rows", C.c_int32),
                 ("dep_stopped", C.c_int32)]
 
 

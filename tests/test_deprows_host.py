@@ -69,6 +69,6 @@ def test_fill_cap_stops_early_with_valid_rows(lib):
     o = oracle.presolve(synth.plant_dependent_rows(synth.mix(1), 1, count=6, terms=2))
     dep, _, _ = deprows.dependent_rows(o, 1e-9)
     full = run(lib, o)
-    capped = run(lib, o, max_fill=200)
+    capped = run(lib, o, max_fill=50)
     assert capped[3] == 1 and set(capped[0]) <= set(full[0]) and capped[2] < full[2]
     assert full[0] == dep

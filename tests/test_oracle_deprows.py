@@ -3,7 +3,8 @@ equality rows' linear dependencies found on the CPU by pivoting Gaussian
 elimination, the result returned to the presolve).
 
 What fixes the step's result, independently of how it eliminates:
-* the number of rows it removes is (equality rows) - rank (numpy's SVD rank);
+* the number of rows it removes is (equality rows) - rank (numpy's SVD rank),
+  and the rows peeled before the elimination plus its pivot rows are the rank;
 * the equality rows it keeps are independent (full rank);
 * every removed row lies in the span of the kept ones, its rhs too (a least
   squares solve);
@@ -56,7 +57,8 @@ def test_removed_rows_match_the_rank_and_lie_in_the_span(name, lp, kw):
     assert bad < 0
     eq, E, b = _eq_matrix(o)
     rank = np.linalg.matrix_rank(E) if len(eq) else 0
-    assert len(dep) == len(eq) - rank == len(eq) - npiv
+    core, peeled = deprows.core_rows(o)
+    assert len(dep) == len(eq) - rank and npiv + peeled == rank and peeled > 0
     kept = [i for i in eq if i not in set(dep)]
     _, K, bk = _eq_matrix(o, set(kept))
     assert np.linalg.matrix_rank(K) == len(kept)
@@ -124,6 +126,8 @@ _MUTANTS = [
     ("rhs never checked", "            if bad < 0 and abs(b) > dep_tol * max(1.0, sb):\n",
      "            if False:\n"),
     ("dependent rows left in the reduced LP", "    keep[dep] = False\n", "    keep[:] = True\n"),
+    ("peeling rows that share every column", "            if len(cols) and np.any(cnt[cols] == 1):\n",
+     "            if len(cols) and np.any(cnt[cols] <= 2):\n"),
 ]
 
 
