@@ -835,7 +835,9 @@ void Engine::compact(int32_t round) {
     scan_excl2(K.r_keep, K.r_len, K.r_pos, K.r_off, m, scan_tmp, s);
     if (!t_orig) scan_excl2(K.c_keep, K.c_len, K.c_pos, K.c_off, n, scan_tmp, s);
     tend();
-    launch_offset(C, K, s);
+    // the objective constant of the columns that left: with the columns in
+    // place (t_orig) each slot's contribution stays until one sum at the end
+    if (!t_orig) launch_offset(C, K, s);
     (k_sizes<<<1, 1, 0, s>>>(K, m, n, t_orig ? 1 : 0, st), note_launch());
     tbegin(F_SCATTER, 24.0 * nnz * 2 + 48.0 * (m + n));
     launch_compact_scatter(C, K, (int32_t)nnz, s);
@@ -1183,6 +1185,7 @@ void Engine::run() {
     }
     if (o.dep_rows && nlp == 1 && lp_status[0] == LPP_OK) remove_dependent();
     if (t_orig) {
+        launch_offset(ctx(rounds), K, s);  // every slot's contribution, once, in column order
         finish_cols();
         finish_csc();
     }
