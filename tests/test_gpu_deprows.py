@@ -118,3 +118,21 @@ def test_benchmark_lp_with_planted_dependencies():
     a, b = r.reduced(csc=False), p.reduced(csc=False)
     assert a.m == b.m - len(dep)
     np.testing.assert_array_equal(a.row_map, np.setdiff1d(b.row_map, dep))
+
+
+def test_edge_cases():
+    """No equality rows, an empty LP, rows only, and every row removed by the
+    rounds: the step finds nothing and the result is the plain run's."""
+    from lpmake import make
+    INF = np.inf
+    lps = [make([{0: 1.0, 1: 1.0}, {1: 2.0, 2: 1.0}], [-INF, 1.0], [4.0, INF], [0, 0, 0], [5, 5, 5],
+                c=[1.0, -1.0, 0.5]),                                    # inequalities only
+           make([], [], [], [], [], None, n=0),                         # nothing
+           make([{}, {}], [-1, 0], [1, 0], [], [], None, n=0),          # rows only, empty
+           make([{0: 1.0, 1: 2.0}], [3], [3], [1, 1], [1, 1], [1.0, 1.0])]  # all fixed on input
+    for lp in lps:
+        r, p = lpp.presolve(lp, dep_rows=1), lpp.presolve(lp)
+        assert (r.status, r.info.dep_rows) == (p.status, 0)
+        a, b = r.reduced(), p.reduced()
+        for f in ("row_ptr", "col_idx", "val", "lhs", "rhs", "row_map", "col_map"):
+            np.testing.assert_array_equal(getattr(a, f), getattr(b, f), err_msg=f)

@@ -180,3 +180,21 @@ def test_full_size_records_are_valid_at_sampled_columns():
             assert abs(v - got) <= 1e-9 * max(1.0, abs(got)) + 1e-12 * scale, (j, side, rr, v, got)
             checked += 1
     assert checked >= 100
+
+
+def test_edge_cases():
+    """An LP the rounds reduce to nothing (empty reduced pair), and an
+    infeasible LP (refused: no primal-dual solution to map)."""
+    from lpmake import INF, make
+    lp = make([{0: 1.0, 1: 2.0}], [3], [3], [1, 1], [1, 1], [1.0, 1.0])
+    r = lpp.presolve(lp, dual_records=1)
+    assert r.info.m_red == 0 and r.info.n_red == 0
+    x, y, z = r.postsolve_dual(lp, np.zeros(0), np.zeros(0))
+    np.testing.assert_array_equal(x, [1.0, 1.0])
+    k = lpsolve.kkt(lp, x, y, z)
+    assert max(k["primal"], k["sign"], k["compl"]) < 1e-12
+    bad = make([{0: 1.0, 1: 1.0}], lhs=[5], rhs=[INF], lb=[0, 0], ub=[1, 1])
+    rb = lpp.presolve(bad, dual_records=1)
+    assert rb.status == lpp.INFEASIBLE
+    with pytest.raises(lpp.LppError):
+        rb.postsolve_dual(bad, np.zeros(rb.info.n_red), np.zeros(rb.info.m_red))
