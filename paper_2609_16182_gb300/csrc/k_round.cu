@@ -210,6 +210,7 @@ __device__ __forceinline__ void bsrc_row(const Ctx &C, int32_t i, int32_t k0, in
     const double dU = Uv - act.x, dL = Lv - act.y;
     for (int32_t k = k0; k < k1; k += step) {
         const int32_t j = C.A.idx[k];
+        if (C.ctouch[j] == 0u) continue;  // no candidate this round (one 4-byte gather)
         const unsigned long long el = C.cand_l[j], eu = C.cand_u[j];
         if (el == kEncNegInf && eu == kEncPosInf) continue;
         const double a = C.A.val[k];

@@ -28,7 +28,13 @@ __device__ __forceinline__ void coalesced_append(int32_t v, int32_t *cnt, int32_
 // column j received a candidate: list it once per round for S3'
 // (not needed when S3' checks every column this round)
 __device__ __forceinline__ void touch_col(const Ctx &C, int32_t j) {
-    if (!C.list_touched) return;
+    if (!C.list_touched) {
+        // a first round lists nothing (S3' runs on every column); with dual
+        // records the flag alone lets the bound-source pass skip the columns
+        // without a candidate
+        if (C.dual_rec && C.ctouch[j] == 0u) C.ctouch[j] = 1u;
+        return;
+    }
     if (C.ctouch[j] == 0u && atomicExch(&C.ctouch[j], 1u) == 0u) coalesced_append(j, C.tl_cnt, C.tl_list);
 }
 
