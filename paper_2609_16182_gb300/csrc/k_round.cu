@@ -594,7 +594,7 @@ inline unsigned blocks_for(int64_t cnt, int threads) {
 
 }  // namespace
 
-void launch_prop(const Ctx &C, cudaStream_t s) {
+void launch_prop_short(const Ctx &C, cudaStream_t s) {
     GroupGrid g;  // blocks per class at prop_lanes(c) lanes per row
     int32_t acc = 0;
     for (int c = 0; c < 6; c++) {
@@ -604,12 +604,16 @@ void launch_prop(const Ctx &C, cudaStream_t s) {
     }
     g.blk_start[6] = acc;
     if (g.blk_start[6] > 0) (k_prop_groups<<<g.blk_start[6], kBlock, 0, s>>>(C, g), note_launch());
+}
+
+bool prop_has_long(const Ctx &C) { return C.A.cls_start[7] > C.A.cls_start[6] && C.A.nchunks > 0; }
+
+void launch_prop_long(const Ctx &C, cudaStream_t s) {
     const int32_t nlong = C.A.cls_start[7] - C.A.cls_start[6];
-    if (nlong > 0 && C.A.nchunks > 0) {
-        (k_prop_long_partial<<<C.A.nchunks, kBlock, 0, s>>>(C, C.ch_hash), note_launch());
-        (k_prop_long_combine<<<blocks_for((int64_t)nlong * 32, kBlock), kBlock, 0, s>>>(C, C.ch_hash), note_launch());
-        (k_prop_long_tighten<<<C.A.nchunks, kBlock, 0, s>>>(C), note_launch());
-    }
+    if (nlong <= 0 || C.A.nchunks <= 0) return;
+    (k_prop_long_partial<<<C.A.nchunks, kBlock, 0, s>>>(C, C.ch_hash), note_launch());
+    (k_prop_long_combine<<<blocks_for((int64_t)nlong * 32, kBlock), kBlock, 0, s>>>(C, C.ch_hash), note_launch());
+    (k_prop_long_tighten<<<C.A.nchunks, kBlock, 0, s>>>(C), note_launch());
 }
 
 void launch_bound_src(const Ctx &C, cudaStream_t s) {

@@ -219,6 +219,12 @@ Engine::~Engine() {
     for (auto e : ev_round)
         if (e) cudaEventDestroy(e);
     if (s2) cudaStreamSynchronize(s2);  // vector copies still in flight after an error
+    if (s_long) {
+        cudaStreamSynchronize(s_long);
+        cudaStreamDestroy(s_long);
+    }
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
     pool.release();
     if (s) cudaStreamSynchronize(s);
     pinned_put(st_h);
@@ -886,7 +892,22 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     C.list_touched = first_round ? 0 : 1;  // a first round's S3' checks every column
     tbegin(F_PROP, 0.0);  // bytes and ops set once the evaluated nonzeros are known
     const size_t prop_mark = marks.size();
-    launch_prop(C, s);
+    // the long rows' chunk kernels on a second stream, beside the short
+    // rows' kernel, joined before S3'
+    const bool long_rows = prop_has_long(C);
+    if (long_rows) {
+        if (!s_long) {
+            LPP_CUDA(cudaStreamCreateWithFlags(&s_long, cudaStreamNonBlocking));
+            LPP_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+            LPP_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+        }
+        LPP_CUDA(cudaEventRecord(ev_fork, s));
+        LPP_CUDA(cudaStreamWaitEvent(s_long, ev_fork, 0));
+        launch_prop_long(C, s_long);
+        LPP_CUDA(cudaEventRecord(ev_join, s_long));
+    }
+    launch_prop_short(C, s);
+    if (long_rows) LPP_CUDA(cudaStreamWaitEvent(s, ev_join, 0));
     tend();
     tbegin(F_COLFIN, 33.0 * n);
     if (o.dual_records) launch_bound_src(C, s);

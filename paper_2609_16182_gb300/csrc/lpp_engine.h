@@ -126,6 +126,8 @@ struct Engine {
     int32_t *de_cnt_h = nullptr;
     int32_t *t_hist = nullptr;
     cudaStream_t s2 = nullptr;                   // host inputs: the vectors' copies
+    cudaStream_t s_long = nullptr;               // S1-S3 of the long rows, beside the short rows' kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t ev_mat = nullptr, ev_vec = nullptr;
     bool vec_pending = false;                    // their check waits for the copies (prepare)
     uint32_t *ctouch = nullptr;                                      // S3' column lists

@@ -72,7 +72,12 @@ void fill_i32(int32_t *a, int64_t cnt, int32_t v, cudaStream_t s);
 void split_lu(const double2 *lu, int32_t n, double *lb, double *ub, cudaStream_t s);
 
 // ---------------------------------------------------------------- k_round.cu
-void launch_prop(const Ctx &C, cudaStream_t s);
+// S1-S3: the rows of classes 0-5 (launch_prop_short) and the chunked long
+// rows (launch_prop_long) touch disjoint rows and meet only in atomics, so
+// they may run on two streams at once
+void launch_prop_short(const Ctx &C, cudaStream_t s);
+void launch_prop_long(const Ctx &C, cudaStream_t s);
+bool prop_has_long(const Ctx &C);
 // S3 bound sources (opts.dual_records), between S3 and S3'
 void launch_bound_src(const Ctx &C, cudaStream_t s);
 // rows list[0 .. cnt) (current indices) become dependent rows (kind and records, round C.round)
