@@ -643,7 +643,7 @@ inline unsigned blocks_for(int64_t cnt, int threads) {
 
 }  // namespace
 
-void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s) {
+void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s, const SideStream *side) {
     (k_lp_dead<<<blocks_for(C.nlp, 256), 256, 0, s>>>(C, K), note_launch());
     // 1. column counts over kept rows, then S6 and the column keep flags
     const GroupGrid ga = group_grid(C.A);
@@ -668,12 +668,26 @@ void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s) {
         if (tlong > 0 && C.T.nchunks > 0) (k_locks_long<<<C.T.nchunks, kBlock, 0, s>>>(C, K), note_launch());
     }
     if (C.n > 0) (k_colkeep<<<std::min<unsigned>(blocks_for(C.n, kBlock), 8u * 152u), kBlock, 0, s>>>(C, K), note_launch());
-    // 2. row counts over kept columns and the side shifts
+    // 2. row counts over kept columns and the side shifts; the long rows'
+    // chunks (and their prefix) on the side stream when one is given: the
+    // two touch disjoint rows, and each tile start lies in one row
+    const bool long_rows = along > 0 && C.A.nchunks > 0;
+    const bool fork = long_rows && side && side->s;
+    cudaStream_t sl = s;
+    if (fork) {
+        cudaEventRecord(side->fork, s);
+        cudaStreamWaitEvent(side->s, side->fork, 0);
+        sl = side->s;
+    }
+    if (long_rows) {
+        (k_csr_count_long<<<C.A.nchunks, kBlock, 0, sl>>>(C, K), note_launch());
+        (k_long_prefix<<<blocks_for((int64_t)along * 32, 128), 128, 0, sl>>>(C.A, K.chr_cnt, K.chr_off, K.r_len,
+                                                                              K.chr_shift, K.shift), note_launch());
+    }
     if (ga.blk_start[6] > 0) (k_csr_count_groups<<<ga.blk_start[6], kBlock, 0, s>>>(C, K, ga), note_launch());
-    if (along > 0 && C.A.nchunks > 0) {
-        (k_csr_count_long<<<C.A.nchunks, kBlock, 0, s>>>(C, K), note_launch());
-        (k_long_prefix<<<blocks_for((int64_t)along * 32, 128), 128, 0, s>>>(C.A, K.chr_cnt, K.chr_off, K.r_len,
-                                                                             K.chr_shift, K.shift), note_launch());
+    if (fork) {
+        cudaEventRecord(side->join, side->s);
+        cudaStreamWaitEvent(s, side->join, 0);
     }
 }
 

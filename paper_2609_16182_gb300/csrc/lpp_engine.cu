@@ -835,7 +835,9 @@ void Engine::compact(int32_t round) {
     int32_t *own_clen = K.c_len;
     if (t_orig) K.c_len = clive;
     tbegin(F_COUNT, 4.0 * nnz * 2 + 8.0 * nnz + 24.0 * m + 40.0 * n);
-    launch_compact_counts(C, K, s);
+    ensure_side_stream();
+    const SideStream side{s_long, ev_fork, ev_join};
+    launch_compact_counts(C, K, s, &side);
     tend();
     tbegin(F_SCAN, 16.0 * (m + (t_orig ? 0 : n)) * 2);
     scan_excl2(K.r_keep, K.r_len, K.r_pos, K.r_off, m, scan_tmp, s);
@@ -862,6 +864,14 @@ void Engine::compact(int32_t round) {
     tbegin(F_SCHED, 8.0 * (m + n));
     schedule_current();
     tend();
+}
+
+// The second stream for the long rows' kernels (made on first use).
+void Engine::ensure_side_stream() {
+    if (s_long) return;
+    LPP_CUDA(cudaStreamCreateWithFlags(&s_long, cudaStreamNonBlocking));
+    LPP_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+    LPP_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
 }
 
 // One round (S1 .. S8) over the whole arena.  first_round: some LP is in
@@ -896,11 +906,7 @@ Engine::StepOut Engine::step(int32_t r, bool first_round, bool force) {
     // rows' kernel, joined before S3'
     const bool long_rows = prop_has_long(C);
     if (long_rows) {
-        if (!s_long) {
-            LPP_CUDA(cudaStreamCreateWithFlags(&s_long, cudaStreamNonBlocking));
-            LPP_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
-            LPP_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
-        }
+        ensure_side_stream();
         LPP_CUDA(cudaEventRecord(ev_fork, s));
         LPP_CUDA(cudaStreamWaitEvent(s_long, ev_fork, 0));
         launch_prop_long(C, s_long);

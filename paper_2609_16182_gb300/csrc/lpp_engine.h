@@ -126,8 +126,9 @@ struct Engine {
     int32_t *de_cnt_h = nullptr;
     int32_t *t_hist = nullptr;
     cudaStream_t s2 = nullptr;                   // host inputs: the vectors' copies
-    cudaStream_t s_long = nullptr;               // S1-S3 of the long rows, beside the short rows' kernel
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t s_long = nullptr;               // the long rows' kernels (S1-S3, row counts), beside
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // the short rows' kernel
+    void ensure_side_stream();
     cudaEvent_t ev_mat = nullptr, ev_vec = nullptr;
     bool vec_pending = false;                    // their check waits for the copies (prepare)
     uint32_t *ctouch = nullptr;                                      // S3' column lists

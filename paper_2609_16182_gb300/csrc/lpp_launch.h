@@ -210,7 +210,13 @@ int batch_fused_blocks_per_sm(int threads);
 void launch_batch_fused(const FusedArgs &F, int threads, int blocks, cudaStream_t s);
 
 // -------------------------------------------------------------- k_compact.cu
-void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s);
+// a second stream with its fork and join events (work on it starts after
+// the fork recorded on the main stream, which waits for the join)
+struct SideStream {
+    cudaStream_t s;
+    cudaEvent_t fork, join;
+};
+void launch_compact_counts(const Ctx &C, const CompactCtx &K, cudaStream_t s, const SideStream *side = nullptr);
 void launch_compact_scatter(const Ctx &C, const CompactCtx &K, int32_t nnz, cudaStream_t s);
 // the result's CSC from the input CSC when it was not compacted (Ctx::t_orig):
 // counts and keep flags, then (after the caller's column scan) the scatter
